@@ -1,0 +1,470 @@
+"""FP64 CPU oracle of the compress-and-eliminate (CE) factorization.
+
+TEST INFRASTRUCTURE ONLY.  This module is the plain, slow reference that the
+CUDA path is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and
+the CPU-baseline leg of ``bench.py`` may import it; the product library never
+does.  It shares no code with the CUDA path: the only common module is
+``workloads`` (seeded matrices, permutations, right-hand sides).
+
+It follows the paper (Sushnikova & Oseledets, "Compress and eliminate solver
+for symmetric positive definite sparse matrices") step by step, one block row
+at a time, with numpy/scipy dense primitives (SVD, Cholesky, triangular solve)
+as the library steps:
+
+* ``factorize``      -- Algorithm 1 (CE algorithm), the level loop and the
+                        coarse Cholesky of A_K (Section 2.5, Proposition CE_L).
+* ``_one_level``     -- Algorithm 2 (one level elimination): for every block
+                        row, the compression step of Section 2.2 (eq. rreav and
+                        eq. q) and the sub-row elimination of eq. sm_L.
+* ``_coarsen``       -- super-blocks of J consecutive blocks (Section 2.4,
+                        eq. bsp) that start the next level.
+* ``apply``          -- x = Q^T L^{-T} L^{-1} Q b (solve proposition, Sec. 2.5).
+* ``pcg``            -- preconditioned conjugate gradients with M = Q^T L L^T Q.
+
+Readings of points the paper leaves open (each also listed in the design doc):
+
+* Rank rule (CE(eps), Section 2.2 remark): the norm of E_i is the spectral
+  norm and the tolerance is relative to the far row, tau_i = eps * sigma_1(F_i);
+  r_i = #{k : sigma_k > tau_i} (a singular value equal to tau_i is dropped).
+  ``tol_mode='abs'`` uses tau_i = eps.  ``tol == 0`` uses
+  tau_i = n_i * eps_64 * sigma_1, which drops only numerically-zero directions.
+* Elimination order inside a level: colour-major order of a greedy distance-2
+  colouring of the level's block graph (ascending block index inside a colour).
+  The paper's natural order (Algorithm 2) is ``order='natural'``; both are
+  permutations P, which the paper leaves free (Section 2).
+* Basis first: the columns of U_i are the left singular vectors of F_i in
+  descending singular value order; the first r_i are the basis ("compressed")
+  dofs, the last n_i - r_i form the eliminated sub-row S_i = [0 I] R_i*.
+* Fill bookkeeping: the Schur update of block i allocates every pair of its
+  targets {basis of i} U close(i) (so the far pattern is the A^2 pattern,
+  Section 2.2); the next level's block graph keeps a pair of super-blocks when
+  some child pair with non-empty rows and columns lies inside it.
+* A block whose far row is empty (or all zero) gets r_i = 0 and is eliminated
+  whole, as in the first block row (Section 2.1).
+"""
+from __future__ import annotations
+
+import dataclasses
+
+import os
+
+# The oracle works on many tiny dense matrices; a multi-threaded BLAS spends
+# more time waking threads than computing.  Callers that import numpy first
+# should set OPENBLAS_NUM_THREADS=1 themselves (tests/conftest.py does).
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import numpy as np  # noqa: E402
+import scipy.linalg as sla  # noqa: E402
+import scipy.sparse as sp  # noqa: E402
+
+EPS64 = np.finfo(np.float64).eps
+
+
+class NotSPDError(RuntimeError):
+    """A pivot block D_nn was not positive definite (level, block in args)."""
+
+
+# --------------------------------------------------------------------------
+# block storage: dict of (i, k) -> dense block for i <= k
+# --------------------------------------------------------------------------
+def _get(S, i, k):
+    return S[(i, k)] if i <= k else S[(k, i)].T
+
+
+def _put(S, i, k, X):
+    if i <= k:
+        S[(i, k)] = X
+    else:
+        S[(k, i)] = X.T
+
+
+def _block_graph(S, M):
+    """Adjacency sets of the blocks (pairs present in S), diagonal included."""
+    nbr = [set([i]) for i in range(M)]
+    for (i, k) in S:
+        nbr[i].add(k)
+        nbr[k].add(i)
+    return nbr
+
+
+def distance2_colouring(nbr):
+    """Greedy distance-2 colouring in ascending block index.
+
+    Block i takes the smallest colour not held by any block j != i at graph
+    distance 1 or 2 that is already coloured.  Blocks of one colour then have
+    disjoint closed neighbourhoods, so their block rows can be compressed and
+    eliminated in any order without touching the same pair of blocks.
+    """
+    M = len(nbr)
+    colour = [-1] * M
+    for i in range(M):
+        seen = set()
+        for j in nbr[i]:
+            for k in nbr[j]:
+                if k != i and colour[k] >= 0:
+                    seen.add(colour[k])
+        c = 0
+        while c in seen:
+            c += 1
+        colour[i] = c
+    return colour
+
+
+# --------------------------------------------------------------------------
+# factor records
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class BlockStep:
+    """One compression + sub-row elimination step (block row i)."""
+
+    i: int
+    n: int                 # block size when the row was processed
+    r: int                 # kept (basis) rank
+    sigma: np.ndarray      # singular values of F_i (descending)
+    tau: float             # truncation threshold used
+    U: np.ndarray          # n x n orthogonal, basis columns first
+    Lhat: np.ndarray       # (n-r) x (n-r) lower Cholesky factor of S_ii
+    targets: list          # [(t, W_t)]: t == i is the basis of i, else close t
+    far: list              # far blocks whose columns formed F_i (non-empty)
+
+
+@dataclasses.dataclass
+class Level:
+    pairs: list            # block pairs (i <= k) of the level-start pattern
+    sizes: list            # block sizes at the start of the level
+    colour: list
+    order: list
+    steps: list            # BlockStep in elimination order
+    J: int
+    ranks: list            # r_i by block index
+
+
+@dataclasses.dataclass
+class Factor:
+    N: int
+    perm: np.ndarray
+    sizes0: list           # level-1 block sizes
+    levels: list
+    coarse_sizes: list     # remainder block sizes (index order)
+    coarse_L: np.ndarray   # dense lower Cholesky factor of A_K
+
+    @property
+    def nnz_L(self):
+        tot = self.coarse_L.shape[0] * (self.coarse_L.shape[0] + 1) // 2
+        for lev in self.levels:
+            for s in lev.steps:
+                m = s.n - s.r
+                tot += m * (m + 1) // 2 + sum(m * W.shape[1] for _, W in s.targets)
+        return tot
+
+
+# --------------------------------------------------------------------------
+# Algorithm 2: one level of compression and elimination
+# --------------------------------------------------------------------------
+def _random_orthogonal(rng, k):
+    if k == 0:
+        return np.zeros((0, 0))
+    Qr, Rr = np.linalg.qr(rng.standard_normal((k, k)))
+    return Qr * np.sign(np.diag(Rr))
+
+
+def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
+               rotate_rng=None, shuffle_rng=None):
+    M = len(sizes)
+    size = list(sizes)
+    close = _block_graph(S, M)          # level-start pattern = close blocks
+    nbr = [set(c) for c in close]       # grows with fill
+    if order_mode == "natural":
+        colour = [0] * M
+        order = list(range(M))
+    else:
+        colour = distance2_colouring(close)
+        order = sorted(range(M), key=lambda i: (colour[i], i))
+        if shuffle_rng is not None:     # self-test: any order inside a colour
+            order = []
+            for c in range(max(colour) + 1):
+                members = [i for i in range(M) if colour[i] == c]
+                order += [members[j] for j in shuffle_rng.permutation(len(members))]
+    ranks = [0] * M
+    steps = []
+    for i in order:
+        n = size[i]
+        # -- compression step (Section 2.2, eq. rreav) ----------------------
+        far = sorted(k for k in nbr[i] if k not in close[i] and size[k] > 0)
+        Fs = [_get(S, i, k) for k in far]
+        F = np.hstack(Fs) if Fs else np.zeros((n, 0))
+        if F.shape[1] == 0 or n == 0 or not np.any(F):
+            U = np.eye(n)
+            sig = np.zeros(0)
+            tau = 0.0
+            r = 0
+        else:
+            U, sig, _ = np.linalg.svd(F, full_matrices=True)
+            if tol == 0.0:
+                tau = n * EPS64 * sig[0]
+            elif tol_mode == "abs":
+                tau = tol
+            else:
+                tau = tol * sig[0]
+            r = int(np.count_nonzero(sig > tau))
+        if rotate_rng is not None:      # self-test: U is fixed only up to
+            U = U.copy()                # rotations inside basis / non-basis
+            U[:, :r] = U[:, :r] @ _random_orthogonal(rotate_rng, r)
+            U[:, r:] = U[:, r:] @ _random_orthogonal(rotate_rng, n - r)
+        # row and column transform by U_i (eq. q): U^T D U, U^T C, U^T F
+        _put(S, i, i, U.T @ _get(S, i, i) @ U)
+        for k in nbr[i]:
+            if k != i:
+                _put(S, i, k, U.T @ _get(S, i, k))
+        # -- elimination step (Section 2.2, eq. sm_L) -----------------------
+        D = _get(S, i, i)
+        targets = [i] + sorted(close[i] - {i})
+        Sn = {t: (D[r:, :r] if t == i else _get(S, i, t)[r:, :]) for t in targets}
+        Snn = D[r:, r:]
+        try:
+            Lh = np.linalg.cholesky(Snn) if n - r > 0 else np.zeros((0, 0))
+        except np.linalg.LinAlgError as e:
+            raise NotSPDError(level_no, i) from e
+        if n - r > 0 and not np.all(np.diag(Lh) > 0):
+            raise NotSPDError(level_no, i)
+        W = {t: sla.solve_triangular(Lh, Sn[t], lower=True) if n - r > 0
+             else np.zeros((0, Sn[t].shape[1])) for t in targets}
+        # block i keeps its basis rows; the far rows r: (E_i) are dropped and
+        # the close rows r: moved into W (they form the eliminated sub-row)
+        _put(S, i, i, D[:r, :r])
+        for k in nbr[i]:
+            if k != i:
+                _put(S, i, k, _get(S, i, k)[:r, :])
+        size[i] = r
+        ranks[i] = r
+        # Schur complement on the targets: A(s, t) -= W_s^T W_t
+        for a, s in enumerate(targets):
+            for t in targets[a:]:
+                upd = W[s].T @ W[t]
+                key = (min(s, t), max(s, t))
+                if key not in S:
+                    S[key] = np.zeros((size[key[0]], size[key[1]]))
+                    nbr[s].add(t)
+                    nbr[t].add(s)
+                _put(S, s, t, _get(S, s, t) - (upd if s != t else 0.5 * (upd + upd.T)))
+        steps.append(BlockStep(i, n, r, sig, tau, U, Lh,
+                               [(t, W[t]) for t in targets], far))
+    return S, size, colour, order, steps, ranks
+
+
+def _coarsen(S, size, J):
+    """Join J consecutive blocks into super-blocks (Section 2.4, eq. bsp).
+
+    Child pairs with an empty side are left out, so a super-block pair exists
+    when some child pair with non-empty rows and columns lies inside it.
+    """
+    M = len(size)
+    Mn = (M + J - 1) // J
+    off = [0] * M
+    nsize = [0] * Mn
+    for i in range(M):
+        I = i // J
+        off[i] = nsize[I]
+        nsize[I] += size[i]
+    T = {}
+    for (i, k), X in S.items():
+        if size[i] == 0 or size[k] == 0:
+            continue
+        I, K = i // J, k // J
+        if (I, K) not in T:
+            T[(I, K)] = np.zeros((nsize[I], nsize[K]))
+        T[(I, K)][off[i]:off[i] + size[i], off[k]:off[k] + size[k]] += X
+        if I == K and i != k:
+            T[(I, K)][off[k]:off[k] + size[k], off[i]:off[i] + size[i]] += X.T
+    for I in range(Mn):                 # every super-block keeps its diagonal
+        T.setdefault((I, I), np.zeros((nsize[I], nsize[I])))
+    return T, nsize
+
+
+def _dense_from_blocks(S, size):
+    off = np.concatenate([[0], np.cumsum(size)]).astype(int)
+    A = np.zeros((off[-1], off[-1]))
+    for (i, k), X in S.items():
+        A[off[i]:off[i + 1], off[k]:off[k + 1]] = X
+        if i != k:
+            A[off[k]:off[k + 1], off[i]:off[i + 1]] = X.T
+    return A
+
+
+def initial_blocks(A, perm, B):
+    """A_0 = P A P^T cut into blocks of B consecutive rows (eq. init_perm).
+
+    The last block is shorter when N is not a multiple of B.
+    """
+    A = sp.csr_matrix(A)
+    N = A.shape[0]
+    perm = np.asarray(perm, dtype=np.int64)
+    A0 = A[perm][:, perm].tocsr()
+    ptr = list(range(0, N, B)) + [N]
+    sizes = [ptr[j + 1] - ptr[j] for j in range(len(ptr) - 1)]
+    blk = np.repeat(np.arange(len(sizes)), sizes)
+    coo = A0.tocoo()
+    S = {}
+    for rr, cc, v in zip(coo.row, coo.col, coo.data):
+        bi, bk = blk[rr], blk[cc]
+        if bi > bk:
+            continue
+        if (bi, bk) not in S:
+            S[(bi, bk)] = np.zeros((sizes[bi], sizes[bk]))
+        S[(bi, bk)][rr - ptr[bi], cc - ptr[bk]] += v
+    # the diagonal pair of every block exists, even if its values are zero
+    for j in range(len(sizes)):
+        S.setdefault((j, j), np.zeros((sizes[j], sizes[j])))
+    return S, sizes
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1: CE factorization
+# --------------------------------------------------------------------------
+def factorize(A, perm, B, tol, levels, J=4, tol_mode="rel", order="colour",
+              rotate_rng=None, shuffle_rng=None):
+    """CE factorization A ~= Q^T L L^T Q (Algorithm 1, Proposition CE_L).
+
+    ``levels`` compression-elimination sweeps, each followed by coarsening by
+    J; the remainder A_K is factorized by dense Cholesky.  Raises
+    :class:`NotSPDError` when a pivot block is not positive definite.
+
+    ``rotate_rng`` / ``shuffle_rng`` are self-test hooks: a random rotation of
+    each U_i inside its basis and non-basis subspaces, and a random order of
+    the blocks inside each colour.  Neither may change M = Q^T L L^T Q.
+    """
+    N = A.shape[0]
+    S, sizes = initial_blocks(A, perm, B)
+    sizes0 = list(sizes)
+    recs = []
+    for lev in range(levels):
+        if len(sizes) == 0:
+            break
+        sizes_start = list(sizes)
+        pairs = sorted(S.keys())
+        S, size, colour, order_, steps, ranks = _one_level(
+            S, sizes, tol, tol_mode, order, lev, rotate_rng, shuffle_rng)
+        recs.append(Level(pairs, sizes_start, colour, order_, steps, J, ranks))
+        S, sizes = _coarsen(S, size, J)
+    Ac = _dense_from_blocks(S, sizes)
+    if Ac.shape[0]:
+        try:
+            Lc = np.linalg.cholesky(Ac)
+        except np.linalg.LinAlgError as e:
+            raise NotSPDError(levels, -1) from e
+    else:
+        Lc = np.zeros((0, 0))
+    return Factor(N, np.asarray(perm), sizes0, recs, list(sizes), Lc)
+
+
+# --------------------------------------------------------------------------
+# solve: x = Q^T L^{-T} L^{-1} Q b
+# --------------------------------------------------------------------------
+def _split(v, sizes):
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(int)
+    return [v[off[j]:off[j + 1]].copy() for j in range(len(sizes))]
+
+
+def apply(F: Factor, b):
+    """M^{-1} b with M = Q^T L L^T Q (solve proposition, Section 2.5).
+
+    Forward sweep: per level, in elimination order, y_i <- U_i^T y_i, the
+    eliminated part solves with L_hat_i and updates its targets; the basis parts
+    are joined into super-blocks.  The remainder is solved with the coarse
+    Cholesky factor; the backward sweep runs the transposed steps in reverse.
+    """
+    b = np.asarray(b, dtype=np.float64)
+    y = _split(b[F.perm], F.sizes0)
+    zs = []
+    for lev in F.levels:
+        z = {}
+        for st in lev.steps:
+            i, r = st.i, st.r
+            yi = st.U.T @ y[i]
+            zi = sla.solve_triangular(st.Lhat, yi[r:], lower=True) if st.n - r else yi[r:]
+            y[i] = yi[:r]
+            for t, W in st.targets:
+                y[t] = y[t] - W.T @ zi
+            z[i] = zi
+        zs.append(z)
+        J = lev.J
+        M = len(lev.sizes)
+        y = [np.concatenate([y[c] for c in range(I * J, min(I * J + J, M))])
+             for I in range((M + J - 1) // J)]
+    yc = np.concatenate(y) if y else np.zeros(0)
+    if F.coarse_L.shape[0]:
+        xc = sla.solve_triangular(F.coarse_L, yc, lower=True)
+        xc = sla.solve_triangular(F.coarse_L.T, xc, lower=False)
+    else:
+        xc = yc
+    sizes_next = F.coarse_sizes
+    x = _split(xc, sizes_next)
+    for lev, z in zip(reversed(F.levels), reversed(zs)):
+        J = lev.J
+        M = len(lev.sizes)
+        # split every super-block into its children's basis parts
+        xb = [None] * M
+        for I in range(len(x)):
+            o = 0
+            for c in range(I * J, min(I * J + J, M)):
+                rc = lev.ranks[c]
+                xb[c] = x[I][o:o + rc]
+                o += rc
+        for st in reversed(lev.steps):
+            i, r = st.i, st.r
+            rhs = z[i].copy()
+            for t, W in st.targets:
+                rhs -= W @ xb[t]
+            xn = sla.solve_triangular(st.Lhat.T, rhs, lower=False) if st.n - r else rhs
+            xb[i] = st.U @ np.concatenate([xb[i], xn])
+        x = xb
+    out = np.empty_like(b)
+    out[F.perm] = np.concatenate(x) if x else np.zeros(0)
+    return out
+
+
+# --------------------------------------------------------------------------
+# PCG (replaces the paper's MINRES; M is SPD whenever every pivot is)
+# --------------------------------------------------------------------------
+@dataclasses.dataclass
+class PCGResult:
+    x: np.ndarray
+    iters: int
+    relres: float
+    converged: bool
+    history: list
+
+
+def pcg(A, F, b, rtol=1e-8, maxit=1000, precond=None):
+    """Preconditioned CG, x0 = 0, stop when ||b - A x||_2 <= rtol ||b||_2.
+
+    ``precond`` defaults to ``apply(F, .)``; pass ``F=None`` and
+    ``precond=lambda r: r`` for plain CG.
+    """
+    A = sp.csr_matrix(A)
+    Minv = precond if precond is not None else (lambda v: apply(F, v))
+    b = np.asarray(b, dtype=np.float64)
+    x = np.zeros_like(b)
+    r = b.copy()
+    bn = np.linalg.norm(b)
+    hist = [1.0]
+    if bn == 0.0:
+        return PCGResult(x, 0, 0.0, True, hist)
+    z = Minv(r)
+    p = z.copy()
+    rz = r @ z
+    for it in range(1, maxit + 1):
+        Ap = A @ p
+        alpha = rz / (p @ Ap)
+        x += alpha * p
+        r -= alpha * Ap
+        rel = np.linalg.norm(r) / bn
+        hist.append(rel)
+        if rel <= rtol:
+            return PCGResult(x, it, rel, True, hist)
+        z = Minv(r)
+        rz_new = r @ z
+        p = z + (rz_new / rz) * p
+        rz = rz_new
+    return PCGResult(x, maxit, hist[-1], False, hist)

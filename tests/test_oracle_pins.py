@@ -1,0 +1,331 @@
+"""Pins of the FP64 oracle against what the paper and mathematics fix.
+
+Each test checks the oracle against something other than itself: the exact
+block Cholesky that CE reduces to when nothing is dropped (eq. bl_chol), the
+dense Cholesky solve, an independently written block IC(0), the structural
+worked example of Section 2, the pattern bounds of Section 2.4 (eq. L, eq.
+bsp, Proposition gl), invariances that any correct implementation has, and the
+trends of the paper's Tables err / num_it.
+"""
+import os
+
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import workloads as wl
+from oracle import ce
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _minv_dense(F, N):
+    return np.stack([ce.apply(F, e) for e in np.eye(N)], axis=1)
+
+
+def _problem(kind, n, box):
+    if kind == "p2":
+        A = wl.poisson2d(n)
+        perm = wl.box_perm((n, n), box)
+    else:
+        A = wl.poisson3d(n)
+        perm = wl.box_perm((n, n, n), box)
+    return A, perm, int(np.prod(box))
+
+
+# --------------------------------------------------------------------------
+# exactness: tol = 0 reduces CE to exact block Cholesky (eq. bl_chol)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("kind,n,box,levels,J", [
+    ("p2", 16, (4, 4), 2, 4),
+    ("p2", 32, (4, 4), 2, 4),
+    ("p3", 8, (2, 2, 2), 2, 8),
+])
+def test_tol0_reproduces_A(kind, n, box, levels, J):
+    A, perm, B = _problem(kind, n, box)
+    N = A.shape[0]
+    F = ce.factorize(A, perm, B, 0.0, levels, J)
+    Minv = _minv_dense(F, N)
+    M = np.linalg.inv(Minv)
+    Ad = A.toarray()
+    assert np.linalg.norm(M - Ad) / np.linalg.norm(Ad) < 1e-13
+    b = wl.rhs(N, 0)
+    x_ref = sla.cho_solve(sla.cho_factor(Ad), b)
+    assert np.linalg.norm(ce.apply(F, b) - x_ref) / np.linalg.norm(x_ref) < 1e-12
+    res = ce.pcg(A, F, b, 1e-8, 50)
+    assert res.converged and res.iters == 1
+
+
+def test_levels0_is_dense_cholesky():
+    A, perm, B = _problem("p2", 16, (4, 4))
+    F = ce.factorize(A, perm, B, 1e-2, 0, 4)
+    assert len(F.levels) == 0 and F.coarse_L.shape == (256, 256)
+    b = wl.rhs(256, 3)
+    x = ce.apply(F, b)
+    x_ref = sla.solve(A.toarray(), b, assume_a="pos")
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-13
+
+
+def test_single_block_is_exact():
+    A, perm, _ = _problem("p2", 8, (4, 4))
+    F = ce.factorize(A, perm, 64, 1e-2, 2, 4)      # B == N: one block
+    st = F.levels[0].steps[0]
+    assert st.r == 0 and st.far == []
+    b = wl.rhs(64, 1)
+    x_ref = sla.solve(A.toarray(), b, assume_a="pos")
+    assert np.linalg.norm(ce.apply(F, b) - x_ref) / np.linalg.norm(x_ref) < 1e-13
+
+
+def test_ragged_last_block_exact():
+    # N = 100, B = 16: six blocks of 16 and a last block of 4
+    A = wl.poisson2d(10)
+    perm = np.arange(100, dtype=np.int32)
+    F = ce.factorize(A, perm, 16, 0.0, 2, 2)
+    assert F.sizes0 == [16] * 6 + [4]
+    b = wl.rhs(100, 2)
+    x_ref = sla.solve(A.toarray(), b, assume_a="pos")
+    assert np.linalg.norm(ce.apply(F, b) - x_ref) / np.linalg.norm(x_ref) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# eps >= 1 drops every far block: CE is then block IC(0) in the same order
+# --------------------------------------------------------------------------
+def _block_ic0_minv(A0, sizes, pairs, order):
+    """Block incomplete Cholesky with no fill outside ``pairs`` (independent).
+
+    Dense bookkeeping in A_0 coordinates: process blocks in ``order``; the
+    pivot block is factorized, the column below scaled, and the Schur update
+    applied only where the block pair belongs to the pattern.
+    """
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(int)
+    sl = [slice(off[j], off[j + 1]) for j in range(len(sizes))]
+    pat = set(pairs) | {(k, i) for (i, k) in pairs}
+    A = A0.copy()
+    N = A.shape[0]
+    L = np.zeros((N, N))
+    done = set()
+    for i in order:
+        Lii = np.linalg.cholesky(A[sl[i], sl[i]])
+        L[sl[i], sl[i]] = Lii
+        nb = [k for k in range(len(sizes)) if (i, k) in pat and k != i and k not in done]
+        Lki = {k: sla.solve_triangular(Lii, A[sl[i], sl[k]], lower=True).T for k in nb}
+        for k in nb:
+            L[sl[k], sl[i]] = Lki[k]
+        for k in nb:
+            for l in nb:
+                if (k, l) in pat:
+                    A[sl[k], sl[l]] -= Lki[k] @ Lki[l].T
+        done.add(i)
+    return L
+
+
+def test_large_eps_is_block_ic0():
+    A, perm, B = _problem("p2", 16, (4, 4))
+    F = ce.factorize(A, perm, B, 2.0, 1, 4)
+    lev = F.levels[0]
+    assert all(r == 0 for r in lev.ranks)
+    A0 = A.toarray()[np.ix_(perm, perm)]
+    L = _block_ic0_minv(A0, lev.sizes, lev.pairs, lev.order)
+    M0 = L @ L.T
+    b = wl.rhs(256, 5)
+    x_ic = np.empty(256)
+    x_ic[perm] = np.linalg.solve(M0, b[perm])
+    x = ce.apply(F, b)
+    assert np.linalg.norm(x - x_ic) / np.linalg.norm(x_ic) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# per-step properties (Section 2.2): orthogonal U, rank rule, SPD pivots
+# --------------------------------------------------------------------------
+def test_step_properties_cfg_small():
+    w = wl.make_workload("poisson2d_64_B16")
+    F = ce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J)
+    nsteps = 0
+    for lev in F.levels:
+        assert sorted(st.i for st in lev.steps) == list(range(len(lev.sizes)))
+        for st in lev.steps:
+            nsteps += 1
+            assert np.abs(st.U.T @ st.U - np.eye(st.n)).max() < 1e-13
+            if st.sigma.size:
+                assert np.all(st.sigma[:st.r] > st.tau)
+                assert np.all(st.sigma[st.r:] <= st.tau)
+                assert st.tau == pytest.approx(w.tol * st.sigma[0])
+            else:
+                assert st.r == 0
+            if st.n - st.r:
+                assert np.all(np.diag(st.Lhat) > 0)
+    assert nsteps == sum(len(l.sizes) for l in F.levels)
+
+
+def test_first_colour_has_no_far_blocks():
+    # nothing is eliminated before the first colour: those rows are eliminated
+    # whole, as the first block row of Section 2.1
+    w = wl.make_workload("poisson2d_64_B16")
+    F = ce.factorize(w.A, w.perm, w.B, w.tol, 1, w.J)
+    lev = F.levels[0]
+    for st in lev.steps:
+        if lev.colour[st.i] == 0:
+            assert st.far == [] and st.r == 0
+
+
+def test_distance2_colouring_is_valid():
+    A, perm, B = _problem("p2", 32, (4, 4))
+    S, sizes = ce.initial_blocks(A, perm, B)
+    nbr = ce._block_graph(S, len(sizes))
+    col = ce.distance2_colouring(nbr)
+    for c in set(col):
+        members = [i for i in range(len(sizes)) if col[i] == c]
+        seen = set()
+        for i in members:
+            assert not (nbr[i] & seen)
+            seen |= nbr[i]
+    # 4-neighbour box grid: a perfect code needs at least 5 colours
+    assert max(col) + 1 >= 5
+
+
+# --------------------------------------------------------------------------
+# structural worked example (Section 2, 4 block rows)
+# --------------------------------------------------------------------------
+def _read_golden(name):
+    out = {}
+    for line in open(os.path.join(GOLDEN, name)):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        key, *vals = line.split()
+        out[key] = [tuple(int(x) - 1 for x in v.split("-")) for v in vals]
+    return out
+
+
+def test_four_block_worked_example():
+    g = _read_golden("four_block_example.txt")
+    Bs = 4
+    rng = np.random.default_rng(11)
+    A = np.zeros((16, 16))
+    for (i, k) in g["pattern"]:
+        X = rng.standard_normal((Bs, Bs))
+        if i == k:
+            X = X @ X.T + 4 * Bs * np.eye(Bs)
+        A[i * Bs:(i + 1) * Bs, k * Bs:(k + 1) * Bs] = X
+        A[k * Bs:(k + 1) * Bs, i * Bs:(i + 1) * Bs] = X.T
+    F = ce.factorize(sp.csr_matrix(A), np.arange(16), Bs, 1e-12, 2, J=1, order="natural")
+    lev = F.levels[0]
+    assert lev.order == [0, 1, 2, 3]
+    close = {}
+    for (i, k) in g["pattern"]:
+        close.setdefault(i, set()).add(k)
+        close.setdefault(k, set()).add(i)
+    far_seen = set()
+    for st in lev.steps:
+        # L_1 inherits the block structure of A_0 (eq. L)
+        assert {t for t, _ in st.targets} == close[st.i]
+        far_seen |= {(min(st.i, k), max(st.i, k)) for k in st.far}
+    assert far_seen == set(g["far"])
+    # block 1 has no far zone and is eliminated whole
+    assert lev.ranks[0] == 0
+    nxt = F.levels[1]
+    off = {(i, k) for (i, k) in nxt.pairs if i != k and nxt.sizes[i] and nxt.sizes[k]}
+    assert off == set(g["remainder_offdiag"])
+    x_ref = np.linalg.solve(A, np.ones(16))
+    x = ce.apply(F, np.ones(16))
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-8
+
+
+# --------------------------------------------------------------------------
+# pattern bounds (Section 2.4: eq. L, eq. bsp, Proposition gl) and dimensions
+# --------------------------------------------------------------------------
+def _square_pattern(pairs, M):
+    nbr = [set([i]) for i in range(M)]
+    for (i, k) in pairs:
+        nbr[i].add(k)
+        nbr[k].add(i)
+    out = set()
+    for j in range(M):
+        for a in nbr[j]:
+            for b in nbr[j]:
+                if a <= b:
+                    out.add((a, b))
+    return out
+
+
+def test_pattern_bounds_and_dimensions():
+    A, perm, B = _problem("p2", 32, (4, 4))
+    J = 4
+    F = ce.factorize(A, perm, B, 1e-3, 3, J)
+    N = A.shape[0]
+    eliminated = 0
+    for li, lev in enumerate(F.levels):
+        M = len(lev.sizes)
+        nonempty = {(i, k) for (i, k) in lev.pairs if lev.sizes[i] and lev.sizes[k]}
+        bsp = len(nonempty) * 2 - sum(1 for (i, k) in nonempty if i == k)
+        nL = sum(1 + len([t for t, W in st.targets if W.size]) for st in lev.steps if st.n - st.r)
+        assert nL <= 2 * bsp                                 # eq. L
+        if li + 1 < len(F.levels):
+            sq = _square_pattern(lev.pairs, M)
+            coarse_sq = {(i // J, k // J) for (i, k) in sq}
+            nxt = F.levels[li + 1]
+            assert set(nxt.pairs) - {(I, I) for I in range(len(nxt.sizes))} <= coarse_sq  # eq. bsp
+        eliminated += sum(st.n - st.r for st in lev.steps)
+    assert eliminated + F.coarse_L.shape[0] == N               # N = N_L1 + N_A1 + ...
+
+
+# --------------------------------------------------------------------------
+# invariances: U is fixed only up to rotations; order inside a colour is free
+# --------------------------------------------------------------------------
+def test_basis_rotation_invariance():
+    A, perm, B = _problem("p2", 32, (4, 4))
+    b = wl.rhs(A.shape[0], 7)
+    F1 = ce.factorize(A, perm, B, 1e-3, 2, 4)
+    F2 = ce.factorize(A, perm, B, 1e-3, 2, 4, rotate_rng=np.random.default_rng(1))
+    assert [l.ranks for l in F1.levels] == [l.ranks for l in F2.levels]
+    x1, x2 = ce.apply(F1, b), ce.apply(F2, b)
+    assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) < 1e-12
+
+
+def test_order_invariance_within_colour():
+    A, perm, B = _problem("p2", 32, (4, 4))
+    b = wl.rhs(A.shape[0], 8)
+    F1 = ce.factorize(A, perm, B, 1e-3, 2, 4)
+    F2 = ce.factorize(A, perm, B, 1e-3, 2, 4, shuffle_rng=np.random.default_rng(2))
+    assert F1.levels[0].order != F2.levels[0].order
+    x1, x2 = ce.apply(F1, b), ce.apply(F2, b)
+    assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# trends of the paper's tables (qualitative: other Krylov method and B)
+# --------------------------------------------------------------------------
+def test_direct_solve_error_falls_with_eps():
+    # Table err: relative accuracy eta of the direct CE solve falls with eps
+    A, perm, B = _problem("p2", 64, (4, 4))
+    b = wl.rhs(A.shape[0], 0)
+    x_ref = sla.solve(A.toarray(), b, assume_a="pos")
+    etas = []
+    for eps in (1e-1, 1e-2, 1e-3, 1e-4):
+        F = ce.factorize(A, perm, B, eps, 2, 4)
+        x = ce.apply(F, b)
+        etas.append(np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref))
+    assert all(etas[j + 1] < etas[j] for j in range(3)), etas
+
+
+def test_pcg_iterations_flat_in_N():
+    # Table num_it: for fixed eps the iteration count does not grow with N
+    its = []
+    for n in (32, 64, 128):
+        A, perm, B = _problem("p2", n, (4, 4))
+        F = ce.factorize(A, perm, B, 1e-3, 2, 4)
+        res = ce.pcg(A, F, wl.rhs(A.shape[0], 0), 1e-8, 100)
+        assert res.converged
+        its.append(res.iters)
+    assert max(its) - min(its) <= 2, its
+    plain = ce.pcg(wl.poisson2d(128), None, wl.rhs(128 * 128, 0), 1e-8, 2000,
+                   precond=lambda r: r)
+    assert plain.iters > 5 * max(its)
+
+
+def test_not_spd_is_reported():
+    A = wl.poisson2d(8).toarray()
+    A[10, 10] = -5.0
+    with pytest.raises(ce.NotSPDError):
+        ce.factorize(sp.csr_matrix(A), np.arange(64), 16, 1e-3, 1, 2)
