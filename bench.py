@@ -1,0 +1,308 @@
+#!/usr/bin/env python
+"""Time to a 1e-8 relative residual (CE factorization + FP64 PCG) on one GPU.
+
+One step = ce_factorize + pcg_solve of the 2D Poisson 512x512 system (B = 32,
+tol 1e-4, 4 levels, J = 4) with the matrix and right-hand side resident in
+HBM.  The chosen form (FP32 blocks and compression, FP64 PCG) is the headline
+value; the plain FP64 form is timed beside it.  Prints one JSON line.
+
+    python bench.py [--steps K] [--warmup W] [--impl ours|reference]
+"""
+import os
+
+os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+os.environ.setdefault("OMP_NUM_THREADS", "1")
+
+import argparse  # noqa: E402
+import json  # noqa: E402
+import statistics  # noqa: E402
+import subprocess  # noqa: E402
+import sys  # noqa: E402
+import threading  # noqa: E402
+import time  # noqa: E402
+
+import numpy as np  # noqa: E402
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads as wl  # noqa: E402
+
+METRIC = "time to 1e-8 residual (factor+PCG)"
+WORKLOAD = "poisson2d_512_B32"
+SAMPLE_GRID = 128        # oracle sample: 128x128 grid of the same kind
+RTOL = 1e-8
+PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+PEAK_FP64_TFLOPS = 1.25                             # GB300 nominal FP64
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--no-baseline", action="store_true", help="skip the oracle timing")
+    return p.parse_args()
+
+
+# --------------------------------------------------------------------------
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.th = threading.Thread(target=self._read, daemon=True)
+            self.th.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+def oracle_time(w, grid, levels):
+    """Oracle factorize + PCG on a grid x grid sample of the same kind (s)."""
+    from oracle import ce as oce
+    A = wl.poisson2d(grid)
+    box = (8, 4) if w.B == 32 else (4, 4)
+    perm = wl.box_perm((grid, grid), box)
+    b = wl.rhs(A.shape[0], 0)
+    t0 = time.perf_counter()
+    F = oce.factorize(A, perm, w.B, w.tol, levels, w.J)
+    res = oce.pcg(A, F, b, RTOL, 1000)
+    t1 = time.perf_counter()
+    assert res.converged
+    return t1 - t0, A.shape[0], res.iters
+
+
+def cpu_baseline(w, levels):
+    t, n, its = oracle_time(w, SAMPLE_GRID, levels)
+    N = w.A.shape[0]
+    return {"value": t * N / n, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle on the {SAMPLE_GRID}x{SAMPLE_GRID} grid of the same "
+                      f"problem ({n} unknowns, {levels} levels, {its} PCG iterations, "
+                      f"{t:.2f} s), scaled linearly to N={N} (O(N) cost, Corollary of "
+                      "Section 2.7); single-threaded BLAS"}
+
+
+def run_reference(args, rank):
+    w = wl.make_workload(args.workload)
+    if rank != 0:
+        return
+    levels = min(w.levels, 3)
+    for _ in range(args.warmup):
+        oracle_time(w, SAMPLE_GRID, levels)
+    ts = []
+    for _ in range(args.steps):
+        t, n, its = oracle_time(w, SAMPLE_GRID, levels)
+        ts.append(t * w.A.shape[0] / n)
+    v = statistics.mean(ts)
+    out = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "impl": "reference",
+           "config": {"workload": args.workload, "N": int(w.A.shape[0]), "B": w.B, "tol": w.tol,
+                      "levels": w.levels, "J": w.J},
+           "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
+                            "sample": f"each step: oracle factorize+PCG on {SAMPLE_GRID}x"
+                                      f"{SAMPLE_GRID}, scaled linearly to N"},
+           "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# --------------------------------------------------------------------------
+def run_ours(args, rank, world):
+    import torch
+    import paper_1603_09133_gb300 as ceg
+    from paper_1603_09133_gb300 import _lib, build as cebuild
+
+    cebuild.build()
+    lib = _lib.load()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
+    torch.cuda.set_device(dev)
+    w = wl.make_workload(args.workload)
+    N = w.A.shape[0]
+    csb = ceg.csb_build(w.A, w.perm, w.B)
+    b = torch.as_tensor(w.b, device=dev)
+    x = torch.zeros_like(b)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(prec):
+        F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision=prec)
+        it, rel, conv = ceg.pcg_solve(csb, F, b, x, RTOL, 1000)
+        return F, it, rel, conv
+
+    def timed(prec, k, w_):
+        for _ in range(w_):
+            step(prec)
+        times, last = [], None
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        l0 = lib.ce_launch_count()
+        for _ in range(k):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            last = step(prec)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+        launches = (lib.ce_launch_count() - l0) / k
+        if world > 1:
+            torch.distributed.barrier()
+        return times, last, launches
+
+    # plain FP64 form (the comparison) and the chosen form
+    other = "fp64" if args.precision == "fp32" else "fp32"
+    t_other, last_other, _ = timed(other, max(1, args.steps // 2), 1)
+    sampler = ClockSampler(dev.index)
+    sampler.start()
+    times, last, launches = timed(args.precision, args.steps, args.warmup)
+    clocks = sampler.stop()
+    F, it, rel, conv = last
+    xt = x.cpu().numpy()
+    true_rel = float(np.linalg.norm(w.b - w.A @ xt) / np.linalg.norm(w.b))
+    ms = statistics.mean(times)
+    if world > 1:
+        tt = torch.tensor([ms], device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        ms = float(tt.item())
+
+    # roofline of the dominant kernel (the per-colour row kernel)
+    info = F.info
+    nl = info.levels_done
+    lms = sum(info.level_ms[l] for l in range(nl))
+    lfl = sum(info.level_flops[l] for l in range(nl))
+    lby = sum(info.level_bytes[l] for l in range(nl))
+    peak = PEAK_FP32_TFLOPS if args.precision == "fp32" else PEAK_FP64_TFLOPS
+    achieved = lfl / (lms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None,
+                "kernel": f"ce_row_kernel<{'float' if args.precision == 'fp32' else 'double'}>",
+                "kernel_ms_per_step": lms, "algorithmic_flops": lfl,
+                "algorithmic_bytes": lby, "achieved_gbs": lby / (lms * 1e-3) / 1e9,
+                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
+                if args.precision == "fp32" else "GB300 nominal FP64"}
+
+    # end to end through the public API with host buffers
+    A = w.A.tocsr()
+    rp = np.ascontiguousarray(A.indptr, np.int64)
+    ci = np.ascontiguousarray(A.indices, np.int32)
+    va = np.ascontiguousarray(A.data, np.float64)
+    pm = np.ascontiguousarray(w.perm, np.int32)
+    b_host = torch.as_tensor(w.b).pin_memory()
+    x_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    e2e_t = []
+    for k in range(args.warmup + args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        csb2 = ceg.csb_build(A, pm, w.B)
+        F2 = ceg.ce_factorize(csb2, tol=w.tol, levels=w.levels, J=w.J, precision=args.precision)
+        bd = b_host.to(dev, non_blocking=True)
+        xd = torch.empty_like(bd)
+        ceg.pcg_solve(csb2, F2, bd, xd, RTOL, 1000)
+        x_host.copy_(xd, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        F2.close()
+        csb2.close()
+        if k >= args.warmup:
+            e2e_t.append(t1 - t0)
+    h2d = rp.nbytes + ci.nbytes + va.nbytes + pm.nbytes + w.b.nbytes
+    e2e = {"value": statistics.mean(e2e_t), "unit": "s", "h2d_bytes_per_step": int(h2d),
+           "d2h_bytes_per_step": int(N * 8)}
+
+    if rank != 0:
+        return
+    levels_cfg = {"blocks": [info.blocks[l] for l in range(nl)],
+                  "colours": [info.colours[l] for l in range(nl)],
+                  "max_block": [info.max_block[l] for l in range(nl)],
+                  "row_kernel_ms": [round(info.level_ms[l], 3) for l in range(nl)],
+                  "coarse_n": info.coarse_n, "coarse_ms": round(info.coarse_ms, 3),
+                  "factor_MB": round(info.factor_bytes / 2**20, 1)}
+    out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+           "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+           "config": {"workload": args.workload, "desc": w.desc, "N": int(N), "B": w.B,
+                      "tol": w.tol, "levels": w.levels, "J": w.J,
+                      "form": f"{args.precision} factor + fp64 PCG",
+                      "pcg_iters": it, "final_relres": true_rel,
+                      f"{other}_form_s": statistics.mean(t_other) / 1e3,
+                      f"{other}_form_pcg_iters": last_other[1],
+                      "l2": "256 MB buffer written between timed steps",
+                      "parallelism": "replicas" if world > 1 else "single GPU",
+                      "levels_detail": levels_cfg},
+           "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline}
+    if not args.no_baseline and world == 1:
+        out["cpu_baseline"] = cpu_baseline(w, min(w.levels, 3))
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        torch.distributed.init_process_group("nccl")
+    run_ours(args, rank, world)
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

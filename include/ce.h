@@ -1,0 +1,215 @@
+/*
+ * ce.h -- C ABI of the GB300 compress-and-eliminate (CE) solver.
+ *
+ * The library computes the approximate factorization A ~= Q^T L L^T Q of a
+ * sparse symmetric positive definite matrix A (Sushnikova & Oseledets,
+ * "Compress and eliminate solver for symmetric positive definite sparse
+ * matrices": problem statement Ax = b of Section 1, Algorithms 1-2 of
+ * Section 2.6, factorization statement Proposition CE_L) on one CUDA GPU, and
+ * uses it as the preconditioner of an FP64 conjugate-gradient solve.
+ *
+ * Conventions shared by every entry point
+ *   - Every call returns a ce_status; no C++ exception crosses this boundary.
+ *   - Pointers named *_dev are CUDA device pointers; every other pointer is a
+ *     host pointer.  The caller owns all arrays it passes; the library copies
+ *     what it keeps.  Handles (ce_csb, ce_factor) are owned by the library
+ *     until the matching *_destroy call.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Device work is ordered on that stream.
+ *   - There is no CPU fallback: if the CUDA runtime fails, CE_ERR_CUDA is
+ *     returned and ce_last_error() holds the CUDA error text.
+ *   - Indices are 0-based.  The matrix is given in CSR with both triangles.
+ */
+#ifndef CE_H
+#define CE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ce_csb ce_csb;       /* blocked matrix + symbolic plan (opaque) */
+typedef struct ce_factor ce_factor; /* factor L, Q on the device (opaque)       */
+
+typedef enum {
+  CE_OK = 0,
+  CE_ERR_INVALID_ARG = 1,   /* bad size, pointer, permutation, block size   */
+  CE_ERR_NOT_SPD = 2,       /* a pivot block was not positive definite      */
+  CE_ERR_NO_CONVERGENCE = 3,/* PCG reached maxit                            */
+  CE_ERR_OOM = 4,           /* device allocation failed                     */
+  CE_ERR_CUDA = 5,          /* CUDA runtime / launch error                  */
+  CE_ERR_LIMIT = 6          /* a block exceeded a compiled size limit       */
+} ce_status;
+
+/* Truncation rule of the compression step (Section 2.2, eq. rreav and the
+ * CE(eps) remark): r_i = #{k : sigma_k(F_i) > tau_i}. */
+enum {
+  CE_TOL_REL = 0, /* tau_i = tol * sigma_1(F_i); tol == 0: n_i*eps*sigma_1 */
+  CE_TOL_ABS = 1  /* tau_i = tol                                           */
+};
+
+/* Arithmetic of the factorization. */
+enum {
+  CE_PREC_FP64 = 0, /* blocks, compression and elimination in FP64       */
+  CE_PREC_FP32 = 1  /* FP32 blocks and compression; coarse level in FP64 */
+};
+
+typedef struct {
+  double tol;      /* eps of CE(eps)                                     */
+  int tol_mode;    /* CE_TOL_REL / CE_TOL_ABS                            */
+  int levels;      /* K, number of compress-and-eliminate sweeps         */
+  int J;           /* super-block size: J consecutive blocks join        */
+  int precision;   /* CE_PREC_*                                          */
+  int coloring;    /* 1: colour-major order (default); 0: natural order  */
+  void* stream;    /* cudaStream_t for all device work                   */
+} ce_opts;
+
+typedef struct {
+  int levels_done;     /* sweeps actually run                             */
+  int err_level;       /* for CE_ERR_NOT_SPD: level (K = coarse) ...      */
+  int err_block;       /* ... and block index (-1 = coarse)               */
+  int coarse_n;        /* size of the dense remainder A_K                 */
+  int64_t factor_bytes;/* device bytes held by the factor                 */
+  int blocks[16];      /* M_l, number of blocks per level (first 16)      */
+  int colours[16];     /* colours per level (first 16)                    */
+  int max_block[16];   /* largest block per level (first 16)              */
+  /* measurement, per level: device time of the row-kernel launches (CUDA
+   * events on `stream`), and the algorithmic flops / bytes of those
+   * launches counted from the actual sizes, ranks and widths */
+  double level_ms[16];
+  double level_flops[16];
+  double level_bytes[16];
+  double coarse_ms;    /* dense assembly + Cholesky of A_K               */
+} ce_info;
+
+typedef struct {
+  int iters;           /* PCG iterations run                              */
+  double relres;       /* ||b - A x||_2 / ||b||_2 at exit (recursive r)   */
+  int converged;       /* 1 if relres <= rtol                             */
+} ce_pcg_info;
+
+/* Defaults: tol 1e-4, CE_TOL_REL, levels 4, J 4, FP64, colouring on. */
+void ce_opts_default(ce_opts* o);
+
+/*
+ * csb_build -- A_0 = P A P^T in compressed sparse block form (Section 2,
+ * eq. init_perm and the CSB storage of Section 2.1).
+ *   n        number of rows of A (> 0)
+ *   rowptr   host, n+1 entries, CSR row pointers of A (both triangles)
+ *   col      host, rowptr[n] column indices
+ *   val      host, rowptr[n] values; A must be symmetric
+ *   perm     host, n entries: perm[k] = original index of row k of P A P^T
+ *   B        block size (> 0): blocks are consecutive runs of B rows of
+ *            P A P^T; the last block is shorter when B does not divide n
+ *   out      receives the handle
+ * Copies the matrix to the device (CSR for the CG products and the block
+ * pattern of level 1) and plans level 1 on the host (block graph, A^2
+ * pattern, distance-2 colouring).  CE_ERR_INVALID_ARG if perm is not a
+ * permutation, an index is out of range or A is not symmetric.
+ */
+ce_status csb_build(int64_t n, const int64_t* rowptr, const int32_t* col,
+                    const double* val, const int32_t* perm, int32_t B,
+                    ce_csb** out);
+
+/*
+ * ce_factorize -- Algorithm 1 (CE algorithm): `levels` sweeps of Algorithm 2
+ * (one level elimination: per block row the compression of the far blocks
+ * F_i by an SVD truncated at tau_i, the row/column transform by U_i and the
+ * Cholesky elimination of the non-basis sub-row S_i, eq. sm_L), each followed
+ * by joining J consecutive blocks into super-blocks (eq. bsp); then the dense
+ * Cholesky of the remainder A_K.  Blocks of one colour of a distance-2
+ * colouring are processed by one launch.
+ *   A     handle from csb_build (not modified)
+ *   o     options (NULL = defaults)
+ *   out   receives the factor
+ *   info  optional, filled on success and on CE_ERR_NOT_SPD
+ * Synchronizes the stream once per level (the next level's layout depends
+ * on the ranks).  CE_ERR_LIMIT if a block grows beyond 64 rows.
+ */
+ce_status ce_factorize(const ce_csb* A, const ce_opts* o, ce_factor** out,
+                       ce_info* info);
+
+/*
+ * ce_factorize_simple -- csb_build + ce_factorize with the paper's inputs
+ * (A, P, B, eps, K) and default J, FP64, relative tolerance.  The csb handle
+ * is kept inside the factor and released with it.
+ */
+ce_status ce_factorize_simple(int64_t n, const int64_t* rowptr,
+                              const int32_t* col, const double* val,
+                              const int32_t* perm, int32_t B, double tol,
+                              int levels, ce_factor** out);
+
+/*
+ * ce_apply -- z = M^{-1} r = Q^T L^{-T} L^{-1} Q r (solve proposition of
+ * Section 2.5).  r_dev and z_dev are device arrays of n doubles in the
+ * original ordering of A; they may alias.  All work is queued on `stream`
+ * (no host synchronization), so the call can be captured in a CUDA graph.
+ */
+ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev,
+                   void* stream);
+
+/*
+ * pcg_solve -- preconditioned conjugate gradients in FP64 with M = Q^T L L^T Q
+ * (replaces the paper's MINRES, Section 4; valid because M is SPD).
+ * x0 = 0; stops when ||r||_2 <= rtol ||b||_2 or after maxit iterations.
+ *   b_dev, x_dev  device arrays of n doubles (original ordering)
+ *   info          optional
+ * Reads the residual norm to the host once per iteration.
+ * CE_ERR_NO_CONVERGENCE if maxit is reached (x_dev holds the last iterate).
+ */
+ce_status pcg_solve(const ce_csb* A, const ce_factor* F, const double* b_dev,
+                    double* x_dev, double rtol, int maxit, ce_pcg_info* info,
+                    void* stream);
+
+/* Release a handle (NULL is ignored). */
+void ce_csb_destroy(ce_csb* A);
+void ce_factor_destroy(ce_factor* F);
+
+/* Number of kernels the library has launched so far (process-wide). */
+int64_t ce_launch_count(void);
+
+/* Static text of a status code; text of the last CUDA failure (per thread). */
+const char* ce_strerror(ce_status s);
+const char* ce_last_error(void);
+
+/*
+ * Introspection of a factor (host copies; for tests and reports).
+ *   ce_factor_levels       number of sweeps stored
+ *   ce_factor_level_size   M_l (blocks) of level l
+ *   ce_factor_get_level    per block of level l, each array host, M_l
+ *                          entries (any may be NULL): block size n_i,
+ *                          rank r_i, colour, and tau_i (double)
+ *   ce_factor_get_sigma    singular values of F_i for every block of level
+ *                          l, concatenated in block order (sum of n_i
+ *                          doubles; zeros where F_i had fewer columns)
+ */
+int ce_factor_levels(const ce_factor* F);
+int ce_factor_level_size(const ce_factor* F, int level);
+ce_status ce_factor_get_level(const ce_factor* F, int level, int32_t* n,
+                              int32_t* rank, int32_t* colour, double* tau);
+ce_status ce_factor_get_sigma(const ce_factor* F, int level, double* sigma);
+
+/*
+ * ce_plan_level1 -- host-only symbolic analysis of level 1 (no CUDA call):
+ * the block graph of P A P^T with blocks of B rows, its greedy distance-2
+ * colouring in ascending block index, and the number of block pairs of the
+ * squared pattern (close + far pairs, Section 2.2).  Arguments as csb_build
+ * (values are not needed).
+ *   colour    host, ceil(n/B) entries, may be NULL
+ *   ncolours  may be NULL
+ *   npairs    pairs (i <= k) of the squared pattern, may be NULL
+ *   nclose    pairs (i <= k) of the block pattern of P A P^T, may be NULL
+ */
+ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col,
+                         const int32_t* perm, int32_t B, int32_t* colour,
+                         int* ncolours, int64_t* npairs, int64_t* nclose);
+
+/* Level-1 plan of a csb handle: blocks, colours, colour of every block. */
+int csb_blocks(const ce_csb* A);
+ce_status csb_get_colours(const ce_csb* A, int32_t* colour, int* ncolours);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CE_H */

@@ -1,0 +1,201 @@
+"""GB300 compress-and-eliminate (CE) solver: Python binding of ``libcegpu.so``.
+
+Same call names as the C ABI (include/ce.h): ``csb_build``, ``ce_factorize``,
+``ce_apply``, ``pcg_solve``.  Device vectors are CUDA tensors (torch is used
+for device memory and streams only); every step runs in the library's CUDA
+kernels.  There is no CPU fallback: without the built library every call
+raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (  # noqa: F401
+    CE_ERR_CUDA,
+    CE_ERR_INVALID_ARG,
+    CE_ERR_LIMIT,
+    CE_ERR_NO_CONVERGENCE,
+    CE_ERR_NOT_SPD,
+    CE_ERR_OOM,
+    CE_OK,
+    CE_PREC_FP32,
+    CE_PREC_FP64,
+    CE_TOL_ABS,
+    CE_TOL_REL,
+)
+
+
+class CEError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = _lib.load()
+        msg = lib.ce_strerror(status).decode()
+        extra = lib.ce_last_error().decode()
+        super().__init__(f"{where}: {msg}" + (f" ({extra})" if extra else ""))
+        self.status = status
+
+
+def _check(status: int, where: str):
+    if status != CE_OK:
+        raise CEError(status, where)
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, what):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 \
+            or not t.is_contiguous():
+        raise TypeError(f"{what} must be a contiguous float64 CUDA tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class CSB:
+    """Handle of csb_build: A_0 = P A P^T in blocks of B (device copy + plan)."""
+
+    def __init__(self, handle, n, B):
+        self._h = handle
+        self.n = n
+        self.B = B
+
+    @property
+    def handle(self):
+        return self._h
+
+    def colours(self):
+        lib = _lib.load()
+        M = lib.csb_blocks(self._h)
+        col = np.zeros(M, dtype=np.int32)
+        nc = C.c_int(0)
+        _check(lib.csb_get_colours(self._h, col.ctypes.data_as(_lib.I32P), C.byref(nc)),
+               "csb_get_colours")
+        return col, nc.value
+
+    def close(self):
+        if self._h:
+            _lib.load().ce_csb_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Factor:
+    """Handle of ce_factorize (factor L, Q on the device)."""
+
+    def __init__(self, handle, info, csb):
+        self._h = handle
+        self.info = info
+        self._csb = csb       # keeps the permutation alive
+
+    @property
+    def handle(self):
+        return self._h
+
+    def levels(self):
+        return _lib.load().ce_factor_levels(self._h)
+
+    def level(self, l):
+        """Per-block arrays of level l: n, rank, colour, tau."""
+        lib = _lib.load()
+        M = lib.ce_factor_level_size(self._h, l)
+        n = np.zeros(M, np.int32)
+        r = np.zeros(M, np.int32)
+        col = np.zeros(M, np.int32)
+        tau = np.zeros(M, np.float64)
+        _check(lib.ce_factor_get_level(self._h, l, n.ctypes.data_as(_lib.I32P),
+                                       r.ctypes.data_as(_lib.I32P), col.ctypes.data_as(_lib.I32P),
+                                       tau.ctypes.data_as(_lib.DP)), "ce_factor_get_level")
+        return n, r, col, tau
+
+    def sigma(self, l):
+        """Singular values of every F_i of level l, concatenated (n_i each)."""
+        lib = _lib.load()
+        n, _, _, _ = self.level(l)
+        s = np.zeros(int(n.sum()), np.float64)
+        _check(lib.ce_factor_get_sigma(self._h, l, s.ctypes.data_as(_lib.DP)), "ce_factor_get_sigma")
+        return s
+
+    def close(self):
+        if self._h:
+            _lib.load().ce_factor_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def csb_build(A, perm, B: int) -> CSB:
+    """A (scipy sparse, symmetric), perm[k] = original index of row k, block B."""
+    import scipy.sparse as sp
+    lib = _lib.load()
+    A = sp.csr_matrix(A)
+    n = A.shape[0]
+    rowptr = np.ascontiguousarray(A.indptr, dtype=np.int64)
+    col = np.ascontiguousarray(A.indices, dtype=np.int32)
+    val = np.ascontiguousarray(A.data, dtype=np.float64)
+    pm = np.ascontiguousarray(perm, dtype=np.int32)
+    if pm.shape != (n,):
+        raise ValueError("perm must have one entry per row")
+    h = C.c_void_p()
+    _check(lib.csb_build(n, rowptr.ctypes.data_as(_lib.I64P), col.ctypes.data_as(_lib.I32P),
+                         val.ctypes.data_as(_lib.DP), pm.ctypes.data_as(_lib.I32P), int(B),
+                         C.byref(h)), "csb_build")
+    return CSB(h, n, int(B))
+
+
+def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",
+                 coloring=True, stream=None) -> Factor:
+    """Algorithm 1 on the device; returns the factor (raises CEError)."""
+    lib = _lib.load()
+    o = _lib.ce_opts()
+    lib.ce_opts_default(C.byref(o))
+    o.tol = float(tol)
+    o.tol_mode = CE_TOL_REL if tol_mode == "rel" else CE_TOL_ABS
+    o.levels = int(levels)
+    o.J = int(J)
+    o.precision = CE_PREC_FP64 if precision == "fp64" else CE_PREC_FP32
+    o.coloring = 1 if coloring else 0
+    o.stream = _stream_ptr(stream)
+    info = _lib.ce_info()
+    h = C.c_void_p()
+    st = lib.ce_factorize(csb.handle, C.byref(o), C.byref(h), C.byref(info))
+    if st != CE_OK:
+        err = CEError(st, "ce_factorize")
+        err.info = info
+        raise err
+    return Factor(h, info, csb)
+
+
+def ce_apply(F: Factor, r, z, stream=None):
+    """z = M^{-1} r on the device (r, z: float64 CUDA tensors, may alias)."""
+    lib = _lib.load()
+    _check(lib.ce_apply(F.handle, _dev_ptr(r, "r"), _dev_ptr(z, "z"), _stream_ptr(stream)),
+           "ce_apply")
+    return z
+
+
+def pcg_solve(csb: CSB, F: Factor, b, x, rtol=1e-8, maxit=1000, stream=None, check=True):
+    """FP64 PCG on the device; returns (iters, relres, converged)."""
+    lib = _lib.load()
+    info = _lib.ce_pcg_info()
+    st = lib.pcg_solve(csb.handle, F.handle, _dev_ptr(b, "b"), _dev_ptr(x, "x"), float(rtol),
+                       int(maxit), C.byref(info), _stream_ptr(stream))
+    if check and st not in (CE_OK, CE_ERR_NO_CONVERGENCE):
+        raise CEError(st, "pcg_solve")
+    return info.iters, info.relres, bool(info.converged)

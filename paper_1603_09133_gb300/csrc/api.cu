@@ -1,0 +1,786 @@
+// C ABI of the CE solver: handles, level loop (Algorithm 1), apply, PCG.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+using ce::CopyTask;
+using ce::LevelDev;
+using ce::LevelPlan;
+using ce::LevelStore;
+
+namespace ce {
+std::atomic<int64_t> g_launches{0};
+}
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct CudaFail {
+  cudaError_t e;
+};
+
+void check(cudaError_t e, const char* what) {
+  if (e != cudaSuccess) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    throw CudaFail{e};
+  }
+}
+
+ce_status status_of(const CudaFail& f) {
+  return f.e == cudaErrorMemoryAllocation ? CE_ERR_OOM : CE_ERR_CUDA;
+}
+
+void init_pool_once() {
+  static bool done = false;
+  if (done) return;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) {
+    cudaMemPool_t mp;
+    if (cudaDeviceGetDefaultMemPool(&mp, dev) == cudaSuccess) {
+      uint64_t thr = ~0ull;
+      cudaMemPoolSetAttribute(mp, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  done = true;
+}
+
+void* dalloc(size_t bytes, cudaStream_t s) {
+  void* p = nullptr;
+  if (bytes == 0) bytes = 16;
+  check(cudaMallocAsync(&p, bytes, s), "cudaMallocAsync");
+  return p;
+}
+
+void dfree(void* p, cudaStream_t s) {
+  if (p) cudaFreeAsync(p, s);
+}
+
+// Packs host arrays into one device allocation (one H2D copy).
+struct Packer {
+  std::vector<char> host;
+  size_t add(const void* src, size_t bytes) {
+    size_t off = (host.size() + 255) & ~size_t(255);
+    host.resize(off + bytes);
+    if (bytes && src) std::memcpy(host.data() + off, src, bytes);
+    return off;
+  }
+  template <typename V>
+  size_t addv(const std::vector<V>& v) {
+    return add(v.data(), v.size() * sizeof(V));
+  }
+  size_t zeros(size_t bytes) { return add(nullptr, bytes); }
+};
+
+int64_t pair_offset(const LevelPlan& P, int a, int b) {
+  if (a > b) std::swap(a, b);
+  auto lo = std::lower_bound(P.pair_i.begin(), P.pair_i.end(), a) - P.pair_i.begin();
+  auto hi = std::upper_bound(P.pair_i.begin(), P.pair_i.end(), a) - P.pair_i.begin();
+  auto it = std::lower_bound(P.pair_k.begin() + lo, P.pair_k.begin() + hi, b);
+  if (it == P.pair_k.begin() + hi || *it != b) return -1;
+  return P.pair_off[it - P.pair_k.begin()];
+}
+
+// Algorithmic flops and bytes of the row-kernel launches of one level,
+// counted per block from its size n, rank r (m = n - r) and the widths w of
+// its close and far neighbours when it is processed:
+//   flops = 2 mF n^2           (Householder R of F^T, mF far rows)
+//         + 12 n^3             (SVD of the n x n R with V, if mF > 0)
+//         + 4 n^3 + 2 n^2 Wc + 2 n r mF   (U^T D U, U^T C, U_b^T F)
+//         + m^3/3 + m^2 (r + Wc)           (Cholesky, TRSM)
+//         + m ((r + Wc)^2 + r^2 + sum w^2) (Schur W_p^T W_q, p <= q)
+//   bytes = e * (n^2 + n Wc + n mF                        reads D, C, F
+//              + n^2 + m^2 + m (r + Wc)                  writes U, L_hat, W
+//              + r^2 + r Wc + r mF                       writes kept rows
+//              + 2 sum_{p<=q close} w_p w_q)             Schur targets r+w
+void level_work(const LevelPlan& P, const std::vector<int>& rank, int es, double& flops,
+                double& bytes) {
+  flops = 0;
+  bytes = 0;
+  for (int i = 0; i < P.M; ++i) {
+    const double n = P.n[i], r = rank[i], m = n - r;
+    const int ci = P.colour[i];
+    auto wid = [&](int k) { return double(P.colour[k] < ci ? rank[k] : P.n[k]); };
+    double mF = 0, Wc = 0, W2 = 0, pairs = 0;
+    for (int f = P.far_ptr[i]; f < P.far_ptr[i + 1]; ++f) mF += wid(P.far_blk[f]);
+    std::vector<double> w;
+    for (int t = P.close_ptr[i]; t < P.close_ptr[i + 1]; ++t) w.push_back(wid(P.close_blk[t]));
+    for (double x : w) {
+      Wc += x;
+      W2 += x * x;
+    }
+    pairs = 0.5 * (Wc * Wc + W2);
+    flops += 2 * mF * n * n + (mF > 0 ? 12 * n * n * n : 0) + 4 * n * n * n + 2 * n * n * Wc +
+             2 * n * r * mF + m * m * m / 3 + m * m * (r + Wc) + m * ((r + Wc) * (r + Wc) + r * r + W2);
+    bytes += es * (n * n + n * Wc + n * mF + n * n + m * m + m * (r + Wc) + r * r + r * Wc + r * mF +
+                   2 * pairs);
+  }
+}
+
+int max_targets(const LevelPlan& P) {
+  int t = 0;
+  for (int i = 0; i < P.M; ++i) t = std::max(t, 1 + P.close_ptr[i + 1] - P.close_ptr[i]);
+  return t;
+}
+
+// Upload the metadata of a level plan and allocate its factor storage.
+void build_level_store(LevelStore& st, int esize, cudaStream_t s) {
+  const LevelPlan& P = st.plan;
+  Packer pk;
+  const size_t o_n = pk.addv(P.n), o_col = pk.addv(P.colour), o_rank = pk.zeros(P.M * sizeof(int)),
+               o_order = pk.addv(P.order), o_cp = pk.addv(P.close_ptr), o_cb = pk.addv(P.close_blk),
+               o_co = pk.addv(P.close_off), o_fp = pk.addv(P.far_ptr), o_fb = pk.addv(P.far_blk),
+               o_fo = pk.addv(P.far_off), o_do = pk.addv(P.diag_off), o_sp = pk.addv(P.schur_ptr),
+               o_so = pk.addv(P.schur_off), o_uo = pk.addv(P.u_off), o_lo = pk.addv(P.l_off),
+               o_wo = pk.addv(P.w_off), o_vo = pk.addv(P.vec_off),
+               o_gd = pk.zeros(P.M * sizeof(int64_t)), o_tau = pk.zeros(P.M * sizeof(double)),
+               o_sig = pk.zeros(P.vec_len * sizeof(double));
+  st.meta_bytes = pk.host.size();
+  st.meta = dalloc(st.meta_bytes, s);
+  check(cudaMemcpyAsync(st.meta, pk.host.data(), st.meta_bytes, cudaMemcpyHostToDevice, s),
+        "upload level metadata");
+  char* b = static_cast<char*>(st.meta);
+  LevelDev& D = st.dev;
+  D.M = P.M;
+  D.n = reinterpret_cast<const int*>(b + o_n);
+  D.colour = reinterpret_cast<const int*>(b + o_col);
+  D.rank = reinterpret_cast<int*>(b + o_rank);
+  D.order = reinterpret_cast<const int*>(b + o_order);
+  D.close_ptr = reinterpret_cast<const int*>(b + o_cp);
+  D.close_blk = reinterpret_cast<const int*>(b + o_cb);
+  D.close_off = reinterpret_cast<const int64_t*>(b + o_co);
+  D.far_ptr = reinterpret_cast<const int*>(b + o_fp);
+  D.far_blk = reinterpret_cast<const int*>(b + o_fb);
+  D.far_off = reinterpret_cast<const int64_t*>(b + o_fo);
+  D.diag_off = reinterpret_cast<const int64_t*>(b + o_do);
+  D.schur_ptr = reinterpret_cast<const int*>(b + o_sp);
+  D.schur_off = reinterpret_cast<const int64_t*>(b + o_so);
+  D.u_off = reinterpret_cast<const int64_t*>(b + o_uo);
+  D.l_off = reinterpret_cast<const int64_t*>(b + o_lo);
+  D.w_off = reinterpret_cast<const int64_t*>(b + o_wo);
+  D.vec_off = reinterpret_cast<const int64_t*>(b + o_vo);
+  D.gdst = reinterpret_cast<int64_t*>(b + o_gd);
+  D.tau = reinterpret_cast<double*>(b + o_tau);
+  D.sigma = reinterpret_cast<double*>(b + o_sig);
+  const size_t ub = P.u_elems * esize, lb = P.l_elems * esize, wb = P.w_elems * esize;
+  st.fac_bytes = ub + lb + wb + 3 * 256;
+  st.fac = dalloc(st.fac_bytes, s);
+  char* f = static_cast<char*>(st.fac);
+  D.U = f;
+  D.L = f + ((ub + 255) & ~size_t(255));
+  D.W = static_cast<char*>(D.L) + ((lb + 255) & ~size_t(255));
+  D.pool = nullptr;
+}
+
+// copy tasks: level pairs (kept corners) -> next level pairs
+std::vector<CopyTask> reassembly_tasks(const LevelPlan& P, const std::vector<int>& rank, int J,
+                                       const ce::NextLevel& nx, const LevelPlan& Pn) {
+  std::vector<CopyTask> tasks;
+  for (size_t p = 0; p < P.pair_i.size(); ++p) {
+    const int i = P.pair_i[p], k = P.pair_k[p];
+    if (rank[i] == 0 || rank[k] == 0) continue;
+    const int I = i / J, K = k / J;
+    const int64_t dst = pair_offset(Pn, I, K);
+    CopyTask t;
+    t.src_off = P.pair_off[p];
+    t.src_ld = P.n[k];
+    t.rows = rank[i];
+    t.cols = rank[k];
+    t.dst_off = dst;
+    t.dst_ld = Pn.n[K];
+    t.r0 = nx.child_off[i];
+    t.c0 = nx.child_off[k];
+    t.transpose = 0;
+    tasks.push_back(t);
+    if (I == K && i != k) {
+      t.r0 = nx.child_off[k];
+      t.c0 = nx.child_off[i];
+      t.transpose = 1;
+      tasks.push_back(t);
+    }
+  }
+  return tasks;
+}
+
+// copy tasks: close pairs of a level -> dense symmetric matrix
+std::vector<CopyTask> dense_tasks(const LevelPlan& P) {
+  std::vector<CopyTask> tasks;
+  const int nc = static_cast<int>(P.vec_len);
+  for (size_t p = 0; p < P.pair_i.size(); ++p) {
+    if (!P.pair_close[p]) continue;
+    const int i = P.pair_i[p], k = P.pair_k[p];
+    if (P.n[i] == 0 || P.n[k] == 0) continue;
+    CopyTask t;
+    t.src_off = P.pair_off[p];
+    t.src_ld = P.n[k];
+    t.rows = P.n[i];
+    t.cols = P.n[k];
+    t.dst_off = 0;
+    t.dst_ld = nc;
+    t.r0 = static_cast<int>(P.vec_off[i]);
+    t.c0 = static_cast<int>(P.vec_off[k]);
+    t.transpose = 0;
+    tasks.push_back(t);
+    if (i != k) {
+      t.r0 = static_cast<int>(P.vec_off[k]);
+      t.c0 = static_cast<int>(P.vec_off[i]);
+      t.transpose = 1;
+      tasks.push_back(t);
+    }
+  }
+  return tasks;
+}
+
+void run_copy_tasks(const std::vector<CopyTask>& tasks, int es, int ed, const void* src, void* dst,
+                    cudaStream_t s) {
+  if (tasks.empty()) return;
+  void* dt = dalloc(tasks.size() * sizeof(CopyTask), s);
+  check(cudaMemcpyAsync(dt, tasks.data(), tasks.size() * sizeof(CopyTask), cudaMemcpyHostToDevice, s),
+        "upload copy tasks");
+  check(ce::launch_copy_tasks(es, ed, static_cast<const CopyTask*>(dt), (int)tasks.size(), src, dst, s),
+        "copy tasks");
+  dfree(dt, s);
+}
+
+void free_factor(ce_factor* F, cudaStream_t s) {
+  if (!F) return;
+  for (auto& st : F->levels) {
+    dfree(st.meta, s);
+    dfree(st.fac, s);
+  }
+  dfree(F->d_coarse, s);
+  dfree(F->d_work, s);
+  dfree(F->d_status, s);
+  if (F->owned_csb) ce_csb_destroy(F->owned_csb);
+  delete F;
+}
+
+}  // namespace
+
+extern "C" {
+
+void ce_opts_default(ce_opts* o) {
+  if (!o) return;
+  o->tol = 1e-4;
+  o->tol_mode = CE_TOL_REL;
+  o->levels = 4;
+  o->J = 4;
+  o->precision = CE_PREC_FP64;
+  o->coloring = 1;
+  o->stream = nullptr;
+}
+
+const char* ce_strerror(ce_status s) {
+  switch (s) {
+    case CE_OK: return "ok";
+    case CE_ERR_INVALID_ARG: return "invalid argument";
+    case CE_ERR_NOT_SPD: return "pivot block not positive definite";
+    case CE_ERR_NO_CONVERGENCE: return "PCG did not converge";
+    case CE_ERR_OOM: return "device out of memory";
+    case CE_ERR_CUDA: return "CUDA error";
+    case CE_ERR_LIMIT: return "block size limit exceeded";
+  }
+  return "unknown status";
+}
+
+const char* ce_last_error(void) { return g_last_error.c_str(); }
+
+int64_t ce_launch_count(void) { return ce::g_launches.load(); }
+
+ce_status csb_build(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                    const int32_t* perm, int32_t B, ce_csb** out) {
+  if (!out || n <= 0 || !rowptr || !col || !val || !perm || B <= 0 || n > INT32_MAX)
+    return CE_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int64_t nnz = rowptr[n];
+  if (rowptr[0] != 0 || nnz < 0) return CE_ERR_INVALID_ARG;
+  for (int64_t a = 0; a < n; ++a)
+    if (rowptr[a + 1] < rowptr[a]) return CE_ERR_INVALID_ARG;
+  std::vector<int32_t> iperm(n, -1);
+  for (int64_t k = 0; k < n; ++k) {
+    if (perm[k] < 0 || perm[k] >= n || iperm[perm[k]] != -1) return CE_ERR_INVALID_ARG;
+    iperm[perm[k]] = static_cast<int32_t>(k);
+  }
+  // symmetry: every (a, b, v) has a matching (b, a, v)
+  std::vector<std::vector<std::pair<int32_t, double>>> rows(n);
+  for (int64_t a = 0; a < n; ++a) {
+    for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
+      if (col[e] < 0 || col[e] >= n) return CE_ERR_INVALID_ARG;
+      rows[a].emplace_back(col[e], val[e]);
+    }
+    std::sort(rows[a].begin(), rows[a].end());
+  }
+  for (int64_t a = 0; a < n; ++a)
+    for (auto& cv : rows[a]) {
+      auto& rb = rows[cv.first];
+      auto it = std::lower_bound(rb.begin(), rb.end(), std::make_pair((int32_t)a, -1e308));
+      if (it == rb.end() || it->first != a || it->second != cv.second) return CE_ERR_INVALID_ARG;
+    }
+  rows.clear();
+  rows.shrink_to_fit();
+
+  const int M = static_cast<int>((n + B - 1) / B);
+  std::vector<int> sizes(M, B);
+  sizes[M - 1] = static_cast<int>(n - (int64_t)(M - 1) * B);
+  std::vector<std::pair<int, int>> pairs;
+  pairs.reserve(nnz);
+  for (int64_t a = 0; a < n; ++a)
+    for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
+      int bi = iperm[a] / B, bk = iperm[col[e]] / B;
+      if (bi <= bk) pairs.emplace_back(bi, bk);
+    }
+  std::sort(pairs.begin(), pairs.end());
+  pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+
+  ce_csb* A = new (std::nothrow) ce_csb();
+  if (!A) return CE_ERR_OOM;
+  A->n = n;
+  A->B = B;
+  A->nnz = nnz;
+  try {
+    ce::plan_level(A->plan1, sizes, pairs, true);
+    std::vector<int64_t> scatter(nnz, -1);
+    for (int64_t a = 0; a < n; ++a)
+      for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
+        const int pa = iperm[a], pb = iperm[col[e]];
+        const int bi = pa / B, bk = pb / B;
+        if (bi > bk) continue;
+        const int64_t po = pair_offset(A->plan1, bi, bk);
+        scatter[e] = po + (int64_t)(pa - bi * B) * A->plan1.n[bk] + (pb - bk * B);
+      }
+    init_pool_once();
+    cudaStream_t s = nullptr;
+    A->d_rowptr = static_cast<int64_t*>(dalloc((n + 1) * sizeof(int64_t), s));
+    A->d_col = static_cast<int32_t*>(dalloc(nnz * sizeof(int32_t), s));
+    A->d_val = static_cast<double*>(dalloc(nnz * sizeof(double), s));
+    A->d_perm = static_cast<int32_t*>(dalloc(n * sizeof(int32_t), s));
+    A->d_scatter = static_cast<int64_t*>(dalloc(nnz * sizeof(int64_t), s));
+    check(cudaMemcpyAsync(A->d_rowptr, rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s), "H2D");
+    check(cudaMemcpyAsync(A->d_col, col, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s), "H2D");
+    check(cudaMemcpyAsync(A->d_val, val, nnz * sizeof(double), cudaMemcpyHostToDevice, s), "H2D");
+    check(cudaMemcpyAsync(A->d_perm, perm, n * sizeof(int32_t), cudaMemcpyHostToDevice, s), "H2D");
+    check(cudaMemcpyAsync(A->d_scatter, scatter.data(), nnz * sizeof(int64_t), cudaMemcpyHostToDevice, s),
+          "H2D");
+    check(cudaStreamSynchronize(s), "csb_build sync");
+  } catch (const CudaFail& f) {
+    ce_csb_destroy(A);
+    return status_of(f);
+  } catch (const std::bad_alloc&) {
+    ce_csb_destroy(A);
+    return CE_ERR_OOM;
+  } catch (const std::exception& ex) {
+    g_last_error = ex.what();
+    ce_csb_destroy(A);
+    return CE_ERR_INVALID_ARG;
+  }
+  *out = A;
+  return CE_OK;
+}
+
+void ce_csb_destroy(ce_csb* A) {
+  if (!A) return;
+  cudaStream_t s = nullptr;
+  dfree(A->d_rowptr, s);
+  dfree(A->d_col, s);
+  dfree(A->d_val, s);
+  dfree(A->d_perm, s);
+  dfree(A->d_scatter, s);
+  delete A;
+}
+
+ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm,
+                         int32_t B, int32_t* colour, int* ncolours, int64_t* npairs, int64_t* nclose) {
+  if (n <= 0 || !rowptr || !col || !perm || B <= 0 || n > INT32_MAX || rowptr[0] != 0)
+    return CE_ERR_INVALID_ARG;
+  std::vector<int32_t> iperm(n, -1);
+  for (int64_t k = 0; k < n; ++k) {
+    if (perm[k] < 0 || perm[k] >= n || iperm[perm[k]] != -1) return CE_ERR_INVALID_ARG;
+    iperm[perm[k]] = static_cast<int32_t>(k);
+  }
+  const int M = static_cast<int>((n + B - 1) / B);
+  std::vector<int> sizes(M, B);
+  sizes[M - 1] = static_cast<int>(n - (int64_t)(M - 1) * B);
+  std::vector<std::pair<int, int>> pairs;
+  for (int64_t a = 0; a < n; ++a)
+    for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
+      if (col[e] < 0 || col[e] >= n) return CE_ERR_INVALID_ARG;
+      int bi = iperm[a] / B, bk = iperm[col[e]] / B;
+      if (bi <= bk) pairs.emplace_back(bi, bk);
+    }
+  std::sort(pairs.begin(), pairs.end());
+  pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+  try {
+    LevelPlan P;
+    ce::plan_level(P, sizes, pairs, true);
+    if (colour) std::copy(P.colour.begin(), P.colour.end(), colour);
+    if (ncolours) *ncolours = P.ncolours;
+    if (npairs) *npairs = static_cast<int64_t>(P.pair_i.size());
+    if (nclose) {
+      int64_t c = 0;
+      for (char x : P.pair_close) c += x;
+      *nclose = c;
+    }
+  } catch (const std::bad_alloc&) {
+    return CE_ERR_OOM;
+  }
+  return CE_OK;
+}
+
+int csb_blocks(const ce_csb* A) { return A ? A->plan1.M : 0; }
+
+ce_status csb_get_colours(const ce_csb* A, int32_t* colour, int* ncolours) {
+  if (!A) return CE_ERR_INVALID_ARG;
+  if (colour) std::copy(A->plan1.colour.begin(), A->plan1.colour.end(), colour);
+  if (ncolours) *ncolours = A->plan1.ncolours;
+  return CE_OK;
+}
+
+ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce_info* info) {
+  if (!A || !out) return CE_ERR_INVALID_ARG;
+  ce_opts o;
+  ce_opts_default(&o);
+  if (o_in) o = *o_in;
+  if (o.levels < 0 || o.J < 1 || o.tol < 0 || (o.precision != CE_PREC_FP64 && o.precision != CE_PREC_FP32) ||
+      (o.tol_mode != CE_TOL_REL && o.tol_mode != CE_TOL_ABS))
+    return CE_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (info) std::memset(info, 0, sizeof(*info));
+  cudaStream_t s = static_cast<cudaStream_t>(o.stream);
+  init_pool_once();
+  ce_factor* F = new (std::nothrow) ce_factor();
+  if (!F) return CE_ERR_OOM;
+  F->N = A->n;
+  F->prec = o.precision;
+  F->esize = (o.precision == CE_PREC_FP64) ? 8 : 4;
+  F->d_perm = A->d_perm;
+  const int es = F->esize;
+  void* pool = nullptr;
+  ce_status ret = CE_OK;
+  try {
+    F->d_status = static_cast<int*>(dalloc(ce::kStatusWords * sizeof(int), s));
+    check(cudaMemsetAsync(F->d_status, 0, ce::kStatusWords * sizeof(int), s), "memset");
+    LevelPlan cur;
+    if (o.coloring) {
+      cur = A->plan1;
+    } else {
+      std::vector<std::pair<int, int>> pr;
+      for (size_t p = 0; p < A->plan1.pair_i.size(); ++p)
+        if (A->plan1.pair_close[p]) pr.emplace_back(A->plan1.pair_i[p], A->plan1.pair_k[p]);
+      ce::plan_level(cur, A->plan1.n, pr, false);
+    }
+    pool = dalloc(cur.pool_elems * es, s);
+    check(cudaMemsetAsync(pool, 0, cur.pool_elems * es, s), "memset pool");
+    check(ce::launch_scatter_csr(es, A->d_scatter, A->d_val, A->nnz, pool, s), "scatter");
+    int hstatus[ce::kStatusWords];
+    for (int l = 0; l < o.levels && cur.M > 0; ++l) {
+      if (cur.nmax > ce::kNMax || max_targets(cur) > 32) {
+        ret = CE_ERR_LIMIT;
+        if (info) info->err_level = l;
+        break;
+      }
+      F->levels.emplace_back();
+      LevelStore& st = F->levels.back();
+      st.plan = std::move(cur);
+      build_level_store(st, es, s);
+      st.dev.pool = pool;
+      const LevelPlan& P = st.plan;
+      cudaEvent_t ev0, ev1;
+      check(cudaEventCreate(&ev0), "event");
+      check(cudaEventCreate(&ev1), "event");
+      check(cudaEventRecord(ev0, s), "event");
+      for (int c = 0; c < P.ncolours; ++c)
+        check(ce::launch_row_kernel(es, st.dev, P.colour_ptr[c], P.colour_ptr[c + 1] - P.colour_ptr[c], l,
+                                    o.tol, o.tol_mode, F->d_status, s),
+              "row kernel");
+      check(cudaEventRecord(ev1, s), "event");
+      st.rank.resize(P.M);
+      check(cudaMemcpyAsync(st.rank.data(), st.dev.rank, P.M * sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
+      check(cudaMemcpyAsync(hstatus, F->d_status, sizeof(hstatus), cudaMemcpyDeviceToHost, s), "D2H");
+      check(cudaStreamSynchronize(s), "level sync");
+      float lms = 0.f;
+      cudaEventElapsedTime(&lms, ev0, ev1);
+      cudaEventDestroy(ev0);
+      cudaEventDestroy(ev1);
+      if (info && l < 16) {
+        info->level_ms[l] = lms;
+        level_work(P, st.rank, es, info->level_flops[l], info->level_bytes[l]);
+      }
+      if (hstatus[0] != 0) {
+        ret = static_cast<ce_status>(hstatus[0]);
+        if (info) {
+          info->err_level = hstatus[1];
+          info->err_block = hstatus[2];
+        }
+        break;
+      }
+      // coarsen (Section 2.4) and plan the next level
+      ce::NextLevel nx = ce::coarsen(P, st.rank, o.J);
+      LevelPlan nxt;
+      ce::plan_level(nxt, nx.n, nx.pairs, o.coloring != 0);
+      std::vector<int64_t> gd(P.M);
+      for (int i = 0; i < P.M; ++i) gd[i] = nxt.vec_off[i / o.J] + nx.child_off[i];
+      check(cudaMemcpyAsync(st.dev.gdst, gd.data(), P.M * sizeof(int64_t), cudaMemcpyHostToDevice, s), "H2D");
+      void* npool = dalloc(std::max<int64_t>(nxt.pool_elems, 1) * es, s);
+      check(cudaMemsetAsync(npool, 0, nxt.pool_elems * es, s), "memset pool");
+      run_copy_tasks(reassembly_tasks(P, st.rank, o.J, nx, nxt), es, es, pool, npool, s);
+      dfree(pool, s);
+      pool = npool;
+      st.dev.pool = nullptr;
+      cur = std::move(nxt);
+    }
+    if (ret == CE_OK) {
+      // dense remainder A_K and its Cholesky factor (FP64)
+      F->nc = static_cast<int>(cur.vec_len);
+      if (F->nc > 28000) {
+        ret = CE_ERR_LIMIT;
+      } else if (F->nc > 0) {
+        cudaEvent_t ev0, ev1;
+        check(cudaEventCreate(&ev0), "event");
+        check(cudaEventCreate(&ev1), "event");
+        check(cudaEventRecord(ev0, s), "event");
+        const size_t nb = (size_t)F->nc * F->nc * sizeof(double);
+        F->d_coarse = static_cast<double*>(dalloc(nb, s));
+        check(cudaMemsetAsync(F->d_coarse, 0, nb, s), "memset coarse");
+        run_copy_tasks(dense_tasks(cur), es, 8, pool, F->d_coarse, s);
+        check(ce::coarse_cholesky(F->d_coarse, F->nc, (int)F->levels.size(), F->d_status, s), "coarse chol");
+        check(cudaEventRecord(ev1, s), "event");
+        check(cudaMemcpyAsync(hstatus, F->d_status, sizeof(hstatus), cudaMemcpyDeviceToHost, s), "D2H");
+        check(cudaStreamSynchronize(s), "coarse sync");
+        float cms = 0.f;
+        cudaEventElapsedTime(&cms, ev0, ev1);
+        cudaEventDestroy(ev0);
+        cudaEventDestroy(ev1);
+        if (info) info->coarse_ms = cms;
+        if (hstatus[0] != 0) {
+          ret = static_cast<ce_status>(hstatus[0]);
+          if (info) {
+            info->err_level = hstatus[1];
+            info->err_block = hstatus[2];
+          }
+        }
+      }
+    }
+    dfree(pool, s);
+    pool = nullptr;
+    if (ret == CE_OK) {
+      int64_t tot = 0;
+      for (auto& st : F->levels) {
+        F->vec_base.push_back(tot);
+        tot += st.plan.vec_len;
+      }
+      F->coarse_base = tot;
+      tot += F->nc;
+      F->d_work = static_cast<double*>(dalloc(std::max<int64_t>(tot, 1) * sizeof(double), s));
+      check(cudaStreamSynchronize(s), "factor sync");
+      int64_t bytes = (int64_t)F->nc * F->nc * 8 + tot * 8;
+      for (auto& st : F->levels) bytes += st.fac_bytes + st.meta_bytes;
+      F->bytes = bytes;
+      if (info) {
+        info->levels_done = (int)F->levels.size();
+        info->coarse_n = F->nc;
+        info->factor_bytes = bytes;
+        for (size_t l = 0; l < F->levels.size() && l < 16; ++l) {
+          info->blocks[l] = F->levels[l].plan.M;
+          info->colours[l] = F->levels[l].plan.ncolours;
+          info->max_block[l] = F->levels[l].plan.nmax;
+        }
+      }
+    }
+  } catch (const CudaFail& f) {
+    ret = status_of(f);
+  } catch (const std::bad_alloc&) {
+    ret = CE_ERR_OOM;
+  } catch (const std::exception& ex) {
+    g_last_error = ex.what();
+    ret = CE_ERR_INVALID_ARG;
+  }
+  if (ret != CE_OK) {
+    dfree(pool, s);
+    cudaStreamSynchronize(s);
+    free_factor(F, s);
+    return ret;
+  }
+  *out = F;
+  return CE_OK;
+}
+
+ce_status ce_factorize_simple(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                              const int32_t* perm, int32_t B, double tol, int levels, ce_factor** out) {
+  ce_csb* A = nullptr;
+  ce_status st = csb_build(n, rowptr, col, val, perm, B, &A);
+  if (st != CE_OK) return st;
+  ce_opts o;
+  ce_opts_default(&o);
+  o.tol = tol;
+  o.levels = levels;
+  st = ce_factorize(A, &o, out, nullptr);
+  if (st != CE_OK) {
+    ce_csb_destroy(A);
+    return st;
+  }
+  (*out)->owned_csb = A;
+  return CE_OK;
+}
+
+void ce_factor_destroy(ce_factor* F) {
+  if (!F) return;
+  free_factor(F, nullptr);
+}
+
+ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev, void* stream) {
+  if (!F || !r_dev || !z_dev) return CE_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  try {
+    const int es = F->esize;
+    double* coarse = F->d_work + F->coarse_base;
+    const int nl = static_cast<int>(F->levels.size());
+    double* v0 = nl ? F->d_work + F->vec_base[0] : coarse;
+    check(ce::launch_perm(F->d_perm, F->N, r_dev, v0, 1, s), "perm gather");
+    for (int l = 0; l < nl; ++l) {
+      const LevelStore& st = F->levels[l];
+      double* v = F->d_work + F->vec_base[l];
+      double* vn = (l + 1 < nl) ? F->d_work + F->vec_base[l + 1] : coarse;
+      for (int c = 0; c < st.plan.ncolours; ++c)
+        check(ce::launch_apply_fwd(es, st.dev, st.plan.colour_ptr[c],
+                                   st.plan.colour_ptr[c + 1] - st.plan.colour_ptr[c], v, s),
+              "apply fwd");
+      check(ce::launch_level_move(st.dev, v, vn, 1, s), "level move");
+    }
+    check(ce::launch_coarse_solve(F->d_coarse, F->nc, coarse, s), "coarse solve");
+    for (int l = nl - 1; l >= 0; --l) {
+      const LevelStore& st = F->levels[l];
+      double* v = F->d_work + F->vec_base[l];
+      double* vn = (l + 1 < nl) ? F->d_work + F->vec_base[l + 1] : coarse;
+      check(ce::launch_level_move(st.dev, v, vn, 0, s), "level move");
+      for (int c = st.plan.ncolours - 1; c >= 0; --c)
+        check(ce::launch_apply_bwd(es, st.dev, st.plan.colour_ptr[c],
+                                   st.plan.colour_ptr[c + 1] - st.plan.colour_ptr[c], v, s),
+              "apply bwd");
+    }
+    check(ce::launch_perm(F->d_perm, F->N, v0, z_dev, 0, s), "perm scatter");
+  } catch (const CudaFail& f) {
+    return status_of(f);
+  }
+  return CE_OK;
+}
+
+ce_status pcg_solve(const ce_csb* A, const ce_factor* F, const double* b_dev, double* x_dev, double rtol,
+                    int maxit, ce_pcg_info* info, void* stream) {
+  if (!A || !F || !b_dev || !x_dev || maxit < 0 || rtol < 0 || A->n != F->N) return CE_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const int64_t n = A->n;
+  const int nparts = static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 4));
+  double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *part = nullptr, *scal = nullptr;
+  ce_status ret = CE_OK;
+  if (info) std::memset(info, 0, sizeof(*info));
+  try {
+    r = static_cast<double*>(dalloc(n * 8, s));
+    z = static_cast<double*>(dalloc(n * 8, s));
+    p = static_cast<double*>(dalloc(n * 8, s));
+    Ap = static_cast<double*>(dalloc(n * 8, s));
+    part = static_cast<double*>(dalloc(nparts * 8, s));
+    scal = static_cast<double*>(dalloc(8 * 8, s));
+    check(cudaMemsetAsync(x_dev, 0, n * 8, s), "memset x");
+    check(cudaMemcpyAsync(r, b_dev, n * 8, cudaMemcpyDeviceToDevice, s), "copy b");
+    check(ce::launch_dot(n, r, r, part, nparts, s), "dot");
+    check(ce::launch_reduce(part, nparts, scal + 3, s), "reduce");
+    double hb = 0;
+    check(cudaMemcpyAsync(&hb, scal + 3, 8, cudaMemcpyDeviceToHost, s), "D2H");
+    check(cudaStreamSynchronize(s), "sync");
+    const double bn = std::sqrt(hb);
+    double rel = 0.0;
+    int it = 0;
+    bool conv = (bn == 0.0);
+    if (!conv) {
+      ret = ce_apply(F, r, z, s);
+      if (ret != CE_OK) throw CudaFail{cudaErrorUnknown};
+      check(ce::launch_dot(n, r, z, part, nparts, s), "dot");
+      check(ce::launch_reduce(part, nparts, scal + 0, s), "reduce");
+      check(ce::launch_update_p(n, p, z, scal, 1, s), "p");
+      rel = 1.0;
+      for (it = 1; it <= maxit; ++it) {
+        check(ce::launch_spmv_dot(n, A->d_rowptr, A->d_col, A->d_val, p, Ap, part, nparts, s), "spmv");
+        check(ce::launch_reduce(part, nparts, scal + 1, s), "reduce");
+        check(ce::launch_pcg_scalars(scal, 0, s), "alpha");
+        check(ce::launch_update_xr(n, x_dev, r, p, Ap, scal, part, nparts, s), "xr");
+        check(ce::launch_reduce(part, nparts, scal + 3, s), "reduce");
+        double rr = 0;
+        check(cudaMemcpyAsync(&rr, scal + 3, 8, cudaMemcpyDeviceToHost, s), "D2H");
+        check(cudaStreamSynchronize(s), "sync");
+        rel = std::sqrt(rr) / bn;
+        if (rel <= rtol) {
+          conv = true;
+          break;
+        }
+        if (it == maxit) break;
+        ret = ce_apply(F, r, z, s);
+        if (ret != CE_OK) throw CudaFail{cudaErrorUnknown};
+        check(ce::launch_dot(n, r, z, part, nparts, s), "dot");
+        check(ce::launch_reduce(part, nparts, scal + 4, s), "reduce");
+        check(ce::launch_pcg_scalars(scal, 1, s), "beta");
+        check(ce::launch_update_p(n, p, z, scal, 0, s), "p");
+      }
+      if (it > maxit) it = maxit;
+    }
+    if (info) {
+      info->iters = conv && bn == 0.0 ? 0 : it;
+      info->relres = rel;
+      info->converged = conv ? 1 : 0;
+    }
+    if (!conv) ret = CE_ERR_NO_CONVERGENCE;
+  } catch (const CudaFail& f) {
+    if (ret == CE_OK) ret = status_of(f);
+  }
+  dfree(r, s);
+  dfree(z, s);
+  dfree(p, s);
+  dfree(Ap, s);
+  dfree(part, s);
+  dfree(scal, s);
+  return ret;
+}
+
+int ce_factor_levels(const ce_factor* F) { return F ? static_cast<int>(F->levels.size()) : 0; }
+
+int ce_factor_level_size(const ce_factor* F, int level) {
+  if (!F || level < 0 || level >= static_cast<int>(F->levels.size())) return -1;
+  return F->levels[level].plan.M;
+}
+
+ce_status ce_factor_get_level(const ce_factor* F, int level, int32_t* n, int32_t* rank, int32_t* colour,
+                              double* tau) {
+  if (!F || level < 0 || level >= static_cast<int>(F->levels.size())) return CE_ERR_INVALID_ARG;
+  const LevelStore& st = F->levels[level];
+  if (n) std::copy(st.plan.n.begin(), st.plan.n.end(), n);
+  if (rank) std::copy(st.rank.begin(), st.rank.end(), rank);
+  if (colour) std::copy(st.plan.colour.begin(), st.plan.colour.end(), colour);
+  if (tau) {
+    cudaError_t e = cudaMemcpy(tau, st.dev.tau, st.plan.M * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      g_last_error = cudaGetErrorString(e);
+      return CE_ERR_CUDA;
+    }
+  }
+  return CE_OK;
+}
+
+ce_status ce_factor_get_sigma(const ce_factor* F, int level, double* sigma) {
+  if (!F || !sigma || level < 0 || level >= static_cast<int>(F->levels.size())) return CE_ERR_INVALID_ARG;
+  const LevelStore& st = F->levels[level];
+  cudaError_t e = cudaMemcpy(sigma, st.dev.sigma, st.plan.vec_len * sizeof(double), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    g_last_error = cudaGetErrorString(e);
+    return CE_ERR_CUDA;
+  }
+  return CE_OK;
+}
+
+}  // extern "C"

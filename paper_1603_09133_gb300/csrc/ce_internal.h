@@ -1,0 +1,147 @@
+// Internal types of the CE library: host plans and device views.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/ce.h"
+
+namespace ce {
+
+constexpr int kNMax = 64;  // largest block the row kernel holds in shared memory
+
+// ---------------------------------------------------------------------------
+// Host plan of one level (Section 2.2-2.4): block sizes, the level-start
+// ("close") pattern, its square (close + far pairs, eq. bsp), a distance-2
+// colouring and every offset the kernels need.  Pairs are stored once, as
+// (i, k) with i <= k, row-major n_i x n_k in one value pool.
+// ---------------------------------------------------------------------------
+struct LevelPlan {
+  int M = 0;
+  std::vector<int> n;            // block sizes
+  std::vector<int> colour;
+  int ncolours = 0;
+  std::vector<int> order;        // colour-major elimination order
+  std::vector<int> colour_ptr;   // ncolours + 1 offsets into order
+
+  // all pairs of the squared pattern, sorted by (i, k), i <= k
+  std::vector<int> pair_i, pair_k;
+  std::vector<int64_t> pair_off;
+  std::vector<char> pair_close;
+  int64_t pool_elems = 0;
+
+  // per block (CSR-style arrays)
+  std::vector<int> close_ptr, close_blk;   // close(i) \ {i}, ascending
+  std::vector<int64_t> close_off;
+  std::vector<int> far_ptr, far_blk;       // far pairs live when i is processed
+  std::vector<int64_t> far_off;
+  std::vector<int64_t> diag_off;
+  std::vector<int> schur_ptr;              // t(t+1)/2 target pairs, t = 1+|close|
+  std::vector<int64_t> schur_off;
+
+  // factor and vector layout
+  std::vector<int64_t> u_off, l_off, w_off, vec_off;
+  int64_t u_elems = 0, l_elems = 0, w_elems = 0, vec_len = 0;
+  int nmax = 0;
+};
+
+// Build the plan of a level from its sizes and level-start pattern (pairs
+// with i <= k; the diagonal pairs are added if missing).
+void plan_level(LevelPlan& P, const std::vector<int>& n,
+                const std::vector<std::pair<int, int>>& close_pairs, bool coloring);
+
+// Reassembly of level l into level l+1 (Section 2.4): copy tasks for the
+// kept r_i x r_k corner of every pair into the super-block pairs.
+struct CopyTask {
+  int64_t src_off;   // element offset of the source block
+  int64_t dst_off;   // element offset of the destination block
+  int src_ld, dst_ld;
+  int rows, cols;    // rows x cols of the source corner
+  int r0, c0;        // destination position
+  int transpose;     // 1: dst[(r0+b), (c0+a)] = src[a, b]
+};
+
+struct NextLevel {
+  std::vector<int> n;                            // super-block sizes
+  std::vector<std::pair<int, int>> pairs;        // next close pattern
+  std::vector<int> child_off;                    // offset of child i in its super-block
+};
+
+NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J);
+
+// ---------------------------------------------------------------------------
+// Device view of a level for the kernels (all pointers device).
+// ---------------------------------------------------------------------------
+struct LevelDev {
+  int M;
+  const int* n;
+  const int* colour;
+  int* rank;
+  const int* order;
+  const int* close_ptr;
+  const int* close_blk;
+  const int64_t* close_off;
+  const int* far_ptr;
+  const int* far_blk;
+  const int64_t* far_off;
+  const int64_t* diag_off;
+  const int* schur_ptr;
+  const int64_t* schur_off;
+  const int64_t* u_off;
+  const int64_t* l_off;
+  const int64_t* w_off;
+  const int64_t* vec_off;
+  int64_t* gdst;        // position of block i's basis in the next vector
+  double* tau;          // per block
+  double* sigma;        // sum n_i (vec layout)
+  void* pool;           // pair values (T)
+  void* U;              // factor (T)
+  void* L;
+  void* W;
+};
+
+// One level kept in a factor.
+struct LevelStore {
+  LevelPlan plan;
+  std::vector<int> rank;        // host copy
+  LevelDev dev{};
+  void* meta = nullptr;         // device metadata block
+  void* fac = nullptr;          // device U, L, W block
+  size_t fac_bytes = 0;
+  size_t meta_bytes = 0;
+};
+
+}  // namespace ce
+
+struct ce_csb {
+  int64_t n = 0;
+  int B = 0;
+  int64_t nnz = 0;
+  // device CSR of A (original ordering) and the permutation
+  int64_t* d_rowptr = nullptr;
+  int32_t* d_col = nullptr;
+  double* d_val = nullptr;
+  int32_t* d_perm = nullptr;
+  // level-1 plan and the scatter map nnz -> element of the level-1 pool
+  ce::LevelPlan plan1;
+  int64_t* d_scatter = nullptr;
+};
+
+struct ce_factor {
+  int64_t N = 0;
+  int prec = CE_PREC_FP64;
+  int esize = 8;
+  std::vector<ce::LevelStore> levels;
+  int nc = 0;                   // coarse size
+  double* d_coarse = nullptr;   // nc x nc lower Cholesky factor (FP64)
+  int64_t* d_cgdst = nullptr;   // unused placeholder
+  int32_t* d_perm = nullptr;    // borrowed from the csb
+  double* d_work = nullptr;     // level vectors (FP64) + coarse vector
+  std::vector<int64_t> vec_base;// start of each level vector in d_work
+  int64_t coarse_base = 0;
+  int* d_status = nullptr;
+  int64_t bytes = 0;
+  ce_csb* owned_csb = nullptr;
+};

@@ -1,0 +1,52 @@
+// Launch wrappers of the CE kernels (defined in factor_kernels.cu and
+// apply_kernels.cu).  All launches are asynchronous on `s`.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "ce_internal.h"
+
+#include <atomic>
+
+namespace ce {
+
+// kernels launched by the library (process-wide)
+extern std::atomic<int64_t> g_launches;
+
+// status word layout: [0] = ce_status code, [1] = level, [2] = block
+constexpr int kStatusWords = 4;
+
+size_t row_kernel_smem(int esize);
+cudaError_t launch_row_kernel(int esize, const LevelDev& L, int first, int count, int level,
+                              double tol, int tol_mode, int* status, cudaStream_t s);
+cudaError_t launch_scatter_csr(int esize, const int64_t* scatter, const double* val, int64_t nnz,
+                               void* pool, cudaStream_t s);
+cudaError_t launch_copy_tasks(int esize_src, int esize_dst, const CopyTask* tasks, int ntasks,
+                              const void* src, void* dst, cudaStream_t s);
+cudaError_t coarse_cholesky(double* A, int n, int level, int* status, cudaStream_t s);
+
+// apply (x = Q^T L^{-T} L^{-1} Q r)
+cudaError_t launch_apply_fwd(int esize, const LevelDev& L, int first, int count, double* vec,
+                             cudaStream_t s);
+cudaError_t launch_apply_bwd(int esize, const LevelDev& L, int first, int count, double* vec,
+                             cudaStream_t s);
+cudaError_t launch_level_move(const LevelDev& L, double* cur, double* next, int forward,
+                              cudaStream_t s);
+cudaError_t launch_perm(const int32_t* perm, int64_t n, const double* in, double* out, int gather,
+                        cudaStream_t s);
+cudaError_t launch_coarse_solve(const double* Lc, int n, double* y, cudaStream_t s);
+
+// PCG building blocks (FP64)
+cudaError_t launch_spmv_dot(int64_t n, const int64_t* rowptr, const int32_t* col,
+                            const double* val, const double* x, double* y, double* partial,
+                            int nparts, cudaStream_t s);
+cudaError_t launch_dot(int64_t n, const double* a, const double* b, double* partial, int nparts,
+                       cudaStream_t s);
+cudaError_t launch_reduce(const double* partial, int nparts, double* out, cudaStream_t s);
+// scal[0]=rz, scal[1]=pAp, ... see apply_kernels.cu
+cudaError_t launch_update_xr(int64_t n, double* x, double* r, const double* p, const double* Ap,
+                             const double* scal, double* partial, int nparts, cudaStream_t s);
+cudaError_t launch_update_p(int64_t n, double* p, const double* z, const double* scal,
+                            int first, cudaStream_t s);
+cudaError_t launch_pcg_scalars(double* scal, int stage, cudaStream_t s);
+
+}  // namespace ce

@@ -1,0 +1,189 @@
+"""GPU parity: the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances (FP64 form): colours bit-exact; ranks identical except where an
+oracle singular value lies within 1e-5 relative of its threshold tau_i;
+||M_gpu^{-1} b - M_or^{-1} b|| / ||M_or^{-1} b|| <= 1e-10; PCG iterations
+within +-1 and a true final residual <= 1e-8.  FP32 form: apply error
+<= 1e-4 against the FP64 oracle, same PCG bar.
+"""
+import numpy as np
+import pytest
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+import workloads as wl
+from oracle import ce as oce
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ceg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_09133_gb300 import build
+    build.build()
+    import paper_1603_09133_gb300 as m
+    return m
+
+
+def _dev(x):
+    return torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64), device="cuda")
+
+
+def _gpu_apply(ceg, F, b):
+    r = _dev(b)
+    z = torch.empty_like(r)
+    ceg.ce_apply(F, r, z)
+    torch.cuda.synchronize()
+    return z.cpu().numpy()
+
+
+def _ranks_agree(lev_or, n_g, r_g, level_sigma_or, rel=1e-5):
+    """Ranks equal, or every differing block has an oracle sigma near tau."""
+    bad = []
+    for st in lev_or.steps:
+        i = st.i
+        if r_g[i] == st.r:
+            continue
+        lo, hi = sorted((r_g[i], st.r))
+        near = all(k < st.sigma.size and abs(st.sigma[k] - st.tau) <= rel * st.tau
+                   for k in range(lo, hi))
+        if not near:
+            bad.append((i, st.r, r_g[i]))
+    return bad
+
+
+def _compare(ceg, A, perm, B, tol, levels, J, b, apply_tol=1e-10, precision="fp64",
+             coloring=True):
+    Fo = oce.factorize(A, perm, B, tol, levels, J, order="colour" if coloring else "natural")
+    csb = ceg.csb_build(A, perm, B)
+    Fg = ceg.ce_factorize(csb, tol=tol, levels=levels, J=J, precision=precision,
+                          coloring=coloring)
+    # colours and ranks level by level while the structures agree
+    same_struct = True
+    for l, lev in enumerate(Fo.levels):
+        if not same_struct:
+            break
+        n_g, r_g, c_g, tau_g = Fg.level(l)
+        assert list(n_g) == list(lev.sizes)
+        if coloring:
+            assert list(c_g) == list(lev.colour)
+        if precision == "fp64":
+            assert _ranks_agree(lev, n_g, r_g, None) == []
+            for st in lev.steps:
+                if st.sigma.size:
+                    assert tau_g[st.i] == pytest.approx(st.tau, rel=1e-9)
+        same_struct = list(r_g) == list(lev.ranks)
+    x_or = oce.apply(Fo, b)
+    x_g = _gpu_apply(ceg, Fg, b)
+    err = np.linalg.norm(x_g - x_or) / np.linalg.norm(x_or)
+    assert err <= apply_tol, err
+    return Fo, Fg, csb, err
+
+
+def _pcg_check(ceg, A, csb, Fg, Fo, b, rtol=1e-8):
+    res_o = oce.pcg(A, Fo, b, rtol, 500)
+    x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+    it, rel, conv = ceg.pcg_solve(csb, Fg, _dev(b), x, rtol, 500)
+    torch.cuda.synchronize()
+    xh = x.cpu().numpy()
+    true_rel = np.linalg.norm(b - A @ xh) / np.linalg.norm(b)
+    assert conv and true_rel <= rtol * 1.01, (it, rel, true_rel)
+    assert abs(it - res_o.iters) <= 1, (it, res_o.iters)
+    return it
+
+
+def test_cfg_small_fp64(ceg):
+    w = wl.make_workload("poisson2d_64_B16")
+    Fo, Fg, csb, err = _compare(ceg, w.A, w.perm, w.B, w.tol, w.levels, w.J, w.b)
+    _pcg_check(ceg, w.A, csb, Fg, Fo, w.b)
+
+
+def test_tol0_matches_dense_solve(ceg):
+    A = wl.poisson2d(32)
+    perm = wl.box_perm((32, 32), (4, 4))
+    csb = ceg.csb_build(A, perm, 16)
+    F = ceg.ce_factorize(csb, tol=0.0, levels=2, J=4)
+    b = wl.rhs(1024, 4)
+    x_ref = sla.solve(A.toarray(), b, assume_a="pos")
+    x = _gpu_apply(ceg, F, b)
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-12
+
+
+def test_ragged_blocks(ceg):
+    A = wl.poisson2d(10)
+    perm = np.arange(100, dtype=np.int32)
+    _compare(ceg, A, perm, 16, 1e-3, 2, 2, wl.rhs(100, 6))
+
+
+def test_natural_order_four_blocks(ceg):
+    rng = np.random.default_rng(11)
+    Bs = 4
+    A = np.zeros((16, 16))
+    for (i, k) in [(0, 0), (1, 1), (2, 2), (3, 3), (0, 1), (0, 3), (1, 2)]:
+        X = rng.standard_normal((Bs, Bs))
+        if i == k:
+            X = X @ X.T + 4 * Bs * np.eye(Bs)
+        A[i * Bs:(i + 1) * Bs, k * Bs:(k + 1) * Bs] = X
+        A[k * Bs:(k + 1) * Bs, i * Bs:(i + 1) * Bs] = X.T
+    _compare(ceg, sp.csr_matrix(A), np.arange(16), Bs, 1e-12, 2, 1, np.ones(16),
+             coloring=False)
+
+
+def test_levels0_dense(ceg):
+    A = wl.poisson2d(16)
+    perm = wl.box_perm((16, 16), (4, 4))
+    csb = ceg.csb_build(A, perm, 16)
+    F = ceg.ce_factorize(csb, tol=1e-2, levels=0)
+    b = wl.rhs(256, 3)
+    x_ref = sla.solve(A.toarray(), b, assume_a="pos")
+    x = _gpu_apply(ceg, F, b)
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-12
+
+
+def test_single_block_and_large_eps(ceg):
+    A = wl.poisson2d(8)
+    perm = wl.box_perm((8, 8), (4, 4))
+    _compare(ceg, A, perm, 64, 1e-3, 2, 4, wl.rhs(64, 1))      # one block
+    _compare(ceg, A, perm, 16, 2.0, 1, 4, wl.rhs(64, 2))       # every r_i = 0
+
+
+def test_not_spd_reported(ceg):
+    A = wl.poisson2d(8).tolil()
+    A[10, 10] = -5.0
+    csb = ceg.csb_build(A.tocsr(), np.arange(64), 16)
+    with pytest.raises(ceg.CEError) as e:
+        ceg.ce_factorize(csb, tol=1e-3, levels=1, J=2)
+    assert e.value.status == ceg.CE_ERR_NOT_SPD
+    # the context is still usable
+    _compare(ceg, wl.poisson2d(8), np.arange(64), 16, 1e-3, 1, 2, wl.rhs(64, 0))
+
+
+def test_abs_tolerance_mode(ceg):
+    A = wl.poisson2d(32)
+    perm = wl.box_perm((32, 32), (4, 4))
+    Fo = oce.factorize(A, perm, 16, 1e-3, 2, 4, tol_mode="abs")
+    csb = ceg.csb_build(A, perm, 16)
+    Fg = ceg.ce_factorize(csb, tol=1e-3, levels=2, J=4, tol_mode="abs")
+    b = wl.rhs(1024, 9)
+    x_or, x_g = oce.apply(Fo, b), _gpu_apply(ceg, Fg, b)
+    assert np.linalg.norm(x_g - x_or) / np.linalg.norm(x_or) <= 1e-10
+
+
+def test_fp32_form_small(ceg):
+    w = wl.make_workload("poisson2d_64_B16")
+    Fo, Fg, csb, err = _compare(ceg, w.A, w.perm, w.B, w.tol, w.levels, w.J, w.b,
+                                apply_tol=1e-4, precision="fp32")
+    _pcg_check(ceg, w.A, csb, Fg, Fo, w.b)
+
+
+@pytest.mark.parametrize("precision,apply_tol", [("fp64", 1e-10), ("fp32", 1e-4)])
+def test_cfg_512_full_size(ceg, precision, apply_tol):
+    """512x512 Poisson, B=32, tol 1e-4, 4 levels: the benchmark's workload."""
+    w = wl.make_workload("poisson2d_512_B32")
+    Fo, Fg, csb, err = _compare(ceg, w.A, w.perm, w.B, w.tol, w.levels, w.J, w.b,
+                                apply_tol=apply_tol, precision=precision)
+    _pcg_check(ceg, w.A, csb, Fg, Fo, w.b)

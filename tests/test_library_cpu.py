@@ -1,0 +1,125 @@
+"""CPU checks of the C-ABI library: it loads, exports every declared symbol,
+validates arguments before any CUDA call, and its host planning (block graph,
+distance-2 colouring, squared pattern) matches the oracle's.
+"""
+import ctypes as C
+import os
+import re
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import workloads as wl
+from oracle import ce as oce
+from paper_1603_09133_gb300 import _lib, build as cebuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    cebuild.build()
+    return _lib.load()
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "ce.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b((?:ce|csb|pcg)_\w+)\s*\(", src))
+    return names
+
+
+def test_header_and_binding_agree():
+    assert _declared_functions() == set(_lib.SIGNATURES)
+
+
+def test_library_exports_every_symbol(lib):
+    for name in _declared_functions():
+        assert hasattr(lib, name), name
+
+
+def _csr_args(A, perm):
+    A = sp.csr_matrix(A)
+    rp = np.ascontiguousarray(A.indptr, np.int64)
+    ci = np.ascontiguousarray(A.indices, np.int32)
+    v = np.ascontiguousarray(A.data, np.float64)
+    pm = np.ascontiguousarray(perm, np.int32)
+    return A.shape[0], rp, ci, v, pm
+
+
+def _build(lib, A, perm, B):
+    n, rp, ci, v, pm = _csr_args(A, perm)
+    h = C.c_void_p()
+    st = lib.csb_build(n, rp.ctypes.data_as(_lib.I64P), ci.ctypes.data_as(_lib.I32P),
+                       v.ctypes.data_as(_lib.DP), pm.ctypes.data_as(_lib.I32P), B, C.byref(h))
+    return st, h
+
+
+def test_csb_build_rejects_bad_input(lib):
+    A = wl.poisson2d(8)
+    perm = np.arange(64)
+    # non-symmetric values
+    An = A.tolil()
+    An[0, 1] = -2.0
+    assert _build(lib, An, perm, 16)[0] == _lib.CE_ERR_INVALID_ARG
+    # not a permutation
+    bad = perm.copy()
+    bad[3] = 5
+    assert _build(lib, A, bad, 16)[0] == _lib.CE_ERR_INVALID_ARG
+    # block size
+    assert _build(lib, A, perm, 0)[0] == _lib.CE_ERR_INVALID_ARG
+    # null output
+    n, rp, ci, v, pm = _csr_args(A, perm)
+    assert lib.csb_build(n, rp.ctypes.data_as(_lib.I64P), ci.ctypes.data_as(_lib.I32P),
+                         v.ctypes.data_as(_lib.DP), pm.ctypes.data_as(_lib.I32P), 16,
+                         None) == _lib.CE_ERR_INVALID_ARG
+
+
+def test_strerror(lib):
+    for s in range(7):
+        assert lib.ce_strerror(s)
+
+
+def _plan(lib, A, perm, B):
+    n, rp, ci, v, pm = _csr_args(A, perm)
+    M = (n + B - 1) // B
+    col = np.zeros(M, np.int32)
+    nc = C.c_int()
+    npairs = C.c_int64()
+    nclose = C.c_int64()
+    st = lib.ce_plan_level1(n, rp.ctypes.data_as(_lib.I64P), ci.ctypes.data_as(_lib.I32P),
+                            pm.ctypes.data_as(_lib.I32P), B, col.ctypes.data_as(_lib.I32P),
+                            C.byref(nc), C.byref(npairs), C.byref(nclose))
+    assert st == _lib.CE_OK
+    return col, nc.value, npairs.value, nclose.value
+
+
+@pytest.mark.parametrize("name", ["poisson2d_64_B16", "poisson2d_512_B32", "poisson3d_64_B64"])
+def test_host_colouring_matches_oracle(lib, name):
+    w = wl.make_workload(name)
+    col, nc, npairs, nclose = _plan(lib, w.A, w.perm, w.B)
+    S, sizes = oce.initial_blocks(w.A, w.perm, w.B)
+    nbr = oce._block_graph(S, len(sizes))
+    ocol = np.array(oce.distance2_colouring(nbr))
+    assert np.array_equal(col, ocol)
+    assert nc == ocol.max() + 1
+    assert nclose == len(S)
+    # squared pattern: pairs with a common neighbour (or adjacent)
+    sq = set()
+    for j in range(len(sizes)):
+        for a in nbr[j]:
+            for b in nbr[j]:
+                if a <= b:
+                    sq.add((a, b))
+    assert npairs == len(sq)
+
+
+def test_host_plan_ragged_and_natural(lib):
+    A = wl.poisson2d(10)
+    col, nc, npairs, nclose = _plan(lib, A, np.arange(100), 16)
+    assert len(col) == 7
+    S, sizes = oce.initial_blocks(A, np.arange(100), 16)
+    assert sizes[-1] == 4
+    ocol = oce.distance2_colouring(oce._block_graph(S, len(sizes)))
+    assert list(col) == ocol
