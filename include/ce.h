@@ -69,6 +69,10 @@ typedef struct {
   int levels_done;     /* sweeps actually run                             */
   int err_level;       /* for CE_ERR_NOT_SPD: level (K = coarse) ...      */
   int err_block;       /* ... and block index (-1 = coarse)               */
+  int err_reason;      /* 1: pivot <= 0 (index err_pivot, value err_value);
+                          2: non-finite singular values of F_i            */
+  int err_pivot;
+  double err_value;
   int coarse_n;        /* size of the dense remainder A_K                 */
   int64_t factor_bytes;/* device bytes held by the factor                 */
   int blocks[16];      /* M_l, number of blocks per level (first 16)      */

@@ -19,6 +19,8 @@ as the library steps:
 * ``_coarsen``       -- super-blocks of J consecutive blocks (Section 2.4,
                         eq. bsp) that start the next level.
 * ``apply``          -- x = Q^T L^{-T} L^{-1} Q b (solve proposition, Sec. 2.5).
+* ``multiply``       -- M x = Q^T L L^T Q x (Proposition CE_L), independent
+                        of ``apply``.
 * ``pcg``            -- preconditioned conjugate gradients with M = Q^T L L^T Q.
 
 Readings of points the paper leaves open (each also listed in the design doc):
@@ -28,6 +30,9 @@ Readings of points the paper leaves open (each also listed in the design doc):
   r_i = #{k : sigma_k > tau_i} (a singular value equal to tau_i is dropped).
   ``tol_mode='abs'`` uses tau_i = eps.  ``tol == 0`` uses
   tau_i = n_i * eps_64 * sigma_1, which drops only numerically-zero directions.
+  In every mode tau_i is at least u * ||D_i||_F (u = unit roundoff of the
+  arithmetic, eps_64 here): a far row that is rounding noise of the block row
+  (fill that cancelled to roundoff) carries no direction worth keeping.
 * Elimination order inside a level: colour-major order of a greedy distance-2
   colouring of the level's block graph (ascending block index inside a colour).
   The paper's natural order (Algorithm 2) is ``order='natural'``; both are
@@ -207,6 +212,9 @@ def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
                 tau = tol
             else:
                 tau = tol * sig[0]
+            # rounding floor: singular values at the level of the rounding
+            # noise of the block row are never kept
+            tau = max(tau, EPS64 * np.linalg.norm(_get(S, i, i)))
             r = int(np.count_nonzero(sig > tau))
         if rotate_rng is not None:      # self-test: U is fixed only up to
             U = U.copy()                # rotations inside basis / non-basis
@@ -421,6 +429,59 @@ def apply(F: Factor, b):
         x = xb
     out = np.empty_like(b)
     out[F.perm] = np.concatenate(x) if x else np.zeros(0)
+    return out
+
+
+def multiply(F: Factor, x):
+    """M x with M = Q^T L L^T Q (the factorization of Proposition CE_L).
+
+    With G the forward sweep of :func:`apply` (M^{-1} = G^T G), M = G^{-1}
+    G^{-T}.  G^{-T} runs the steps forward: y_i <- U_i^T y_i, z_i = L_hat_i^T
+    y_i[r:] + sum_t W_t y_t, coarse c = L_K^T y_c.  G^{-1} runs them backward:
+    y_c = L_K c, then per step y_t += W_t^T z_i, y_i[r:] = L_hat_i z_i,
+    y_i <- U_i y_i.  This is an independent check of apply: M (M^{-1} b) = b,
+    and with nothing dropped M x = A x.
+    """
+    x = np.asarray(x, dtype=np.float64)
+    # ---- G^{-T} x
+    y = _split(x[F.perm], F.sizes0)
+    zs = []
+    for lev in F.levels:
+        z = {}
+        for st in lev.steps:
+            i, r = st.i, st.r
+            yi = st.U.T @ y[i]
+            zi = st.Lhat.T @ yi[r:]
+            y[i] = yi[:r]
+            for t, W in st.targets:
+                zi = zi + W @ y[t]
+            z[i] = zi
+        zs.append(z)
+        J, M = lev.J, len(lev.sizes)
+        y = [np.concatenate([y[c] for c in range(I * J, min(I * J + J, M))])
+             for I in range((M + J - 1) // J)]
+    yc = np.concatenate(y) if y else np.zeros(0)
+    c = F.coarse_L.T @ yc
+    # ---- G^{-1} (z, c)
+    xc = F.coarse_L @ c
+    xs = _split(xc, F.coarse_sizes)
+    for lev, z in zip(reversed(F.levels), reversed(zs)):
+        J, M = lev.J, len(lev.sizes)
+        xb = [None] * M
+        for I in range(len(xs)):
+            o = 0
+            for ch in range(I * J, min(I * J + J, M)):
+                rc = lev.ranks[ch]
+                xb[ch] = xs[I][o:o + rc]
+                o += rc
+        for st in reversed(lev.steps):
+            i = st.i
+            for t, W in st.targets:
+                xb[t] = xb[t] + W.T @ z[i]
+            xb[i] = st.U @ np.concatenate([xb[i], st.Lhat @ z[i]])
+        xs = xb
+    out = np.empty_like(x)
+    out[F.perm] = np.concatenate(xs) if xs else np.zeros(0)
     return out
 
 

@@ -176,7 +176,12 @@ def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="
     h = C.c_void_p()
     st = lib.ce_factorize(csb.handle, C.byref(o), C.byref(h), C.byref(info))
     if st != CE_OK:
-        err = CEError(st, "ce_factorize")
+        where = "ce_factorize"
+        if st == CE_ERR_NOT_SPD:
+            why = {1: f"pivot {info.err_pivot} = {info.err_value:.3e}",
+                   2: "non-finite singular values"}.get(info.err_reason, "")
+            where += f" (level {info.err_level}, block {info.err_block}; {why})"
+        err = CEError(st, where)
         err.info = info
         raise err
     return Factor(h, info, csb)

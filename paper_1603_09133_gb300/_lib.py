@@ -41,6 +41,9 @@ class ce_info(C.Structure):
         ("levels_done", C.c_int),
         ("err_level", C.c_int),
         ("err_block", C.c_int),
+        ("err_reason", C.c_int),
+        ("err_pivot", C.c_int),
+        ("err_value", C.c_double),
         ("coarse_n", C.c_int),
         ("factor_bytes", C.c_int64),
         ("blocks", C.c_int * 16),

@@ -518,6 +518,9 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
         if (info) {
           info->err_level = hstatus[1];
           info->err_block = hstatus[2];
+          info->err_reason = hstatus[3];
+          info->err_pivot = hstatus[4];
+          std::memcpy(&info->err_value, hstatus + 6, sizeof(double));
         }
         break;
       }
@@ -564,6 +567,9 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
           if (info) {
             info->err_level = hstatus[1];
             info->err_block = hstatus[2];
+            info->err_reason = hstatus[3];
+            info->err_pivot = hstatus[4];
+            std::memcpy(&info->err_value, hstatus + 6, sizeof(double));
           }
         }
       }

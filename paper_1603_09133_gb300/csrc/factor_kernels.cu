@@ -7,7 +7,8 @@
 //      (F_i F_i^T = R^T R, so F_i and R^T share left singular vectors);
 //   B. one-sided (Hestenes) Jacobi on the columns of R, warp per column pair,
 //      round-robin pair schedule: R V = U' S  =>  U_i = V, sigma = S, sorted
-//      descending; r_i = #{sigma_k > tau_i};
+//      descending; r_i = #{sigma_k > tau_i}, tau_i never below the rounding
+//      floor u ||D_i||_F of the block row;
 //   C. transform and elimination (eq. q, eq. sm_L): D <- U^T D U, close rows
 //      <- U^T C, far rows <- U_b^T F (the E_i rows are dropped), Cholesky of
 //      the non-basis block S_ii = L_hat L_hat^T, W = L_hat^{-1} S_i and the
@@ -44,6 +45,17 @@ struct Eps<float> {
 };
 
 template <typename T>
+struct Tiny;  // smallest normal number
+template <>
+struct Tiny<double> {
+  static constexpr double v = 2.2250738585072014e-308;
+};
+template <>
+struct Tiny<float> {
+  static constexpr float v = 1.1754943508222875e-38f;
+};
+
+template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -54,52 +66,72 @@ __device__ __forceinline__ int width_of(const LevelDev& L, int k, int ci) {
   return (L.colour[k] < ci) ? L.rank[k] : L.n[k];
 }
 
-__device__ void set_status(int* status, int code, int level, int block) {
+__device__ void set_status(int* status, int code, int level, int block, int reason = 0,
+                           int pivot = -1, double value = 0.0) {
   if (atomicCAS(status, 0, code) == 0) {
     status[1] = level;
     status[2] = block;
+    status[3] = reason;
+    status[4] = pivot;
+    *reinterpret_cast<double*>(status + 6) = value;
   }
 }
 
 // Householder QR update of the stacked matrix [R; C] (R: n x n upper
 // triangular, C: c x n): after the call R is the triangular factor of the
 // stack and C is annihilated (its contents are left undefined).
+// Reflector of column j in the unit-leading form H = I - tau v v^T,
+// v = [1; s C(:, j)], beta = -sign(x0) ||x||, tau = (beta - x0) / beta,
+// s = 1 / (x0 - beta): tau lies in [1, 2] and ||x|| is formed from the
+// column scaled by its largest entry, so fill at the level of rounding noise
+// (whose squares underflow) gives no inf or NaN.
 template <typename T>
-__device__ void householder_stack(T* R, T* C, int n, int c, T* s_v0, T* s_tau) {
+__device__ void householder_stack(T* R, T* C, int n, int c, T* s_scale, T* s_tau) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   for (int j = 0; j < n; ++j) {
     if (warp == 0) {
+      T amax = 0;
+      for (int q = lane; q < c; q += 32) amax = fmax(amax, fabs(C[q * LD + j]));
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      // a column whose largest entry is subnormal is rounding noise far
+      // below any truncation threshold: it is treated as zero
+      if (!(amax >= Tiny<T>::v)) amax = T(0);
       T s = 0;
-      for (int q = lane; q < c; q += 32) {
-        T x = C[q * LD + j];
-        s += x * x;
+      if (amax > T(0)) {
+        for (int q = lane; q < c; q += 32) {
+          T x = C[q * LD + j] / amax;
+          s += x * x;
+        }
       }
       s = warp_sum(s);
       if (lane == 0) {
-        T x0 = R[j * LD + j];
-        if (s == T(0)) {
+        if (amax == T(0)) {
           *s_tau = T(0);
-          *s_v0 = T(0);
+          *s_scale = T(0);
         } else {
-          T nrm = sqrt(x0 * x0 + s);
-          T alpha = (x0 >= T(0)) ? -nrm : nrm;
-          T v0 = x0 - alpha;
-          *s_v0 = v0;
-          *s_tau = T(2) / (v0 * v0 + s);
-          R[j * LD + j] = alpha;
+          const T x0 = R[j * LD + j];
+          const T a = fmax(amax, fabs(x0));
+          const T x0a = x0 / a, ca = amax / a;
+          const T nrm = a * sqrt(x0a * x0a + s * ca * ca);
+          const T beta = (x0 >= T(0)) ? -nrm : nrm;
+          *s_tau = (beta - x0) / beta;
+          *s_scale = T(1) / (x0 - beta);
+          R[j * LD + j] = beta;
         }
       }
     }
     __syncthreads();
-    const T tau = *s_tau, v0 = *s_v0;
+    const T tau = *s_tau, sc = *s_scale;
     if (tau != T(0)) {
       for (int l = j + 1 + warp; l < n; l += kWarps) {
         T d = 0;
         for (int q = lane; q < c; q += 32) d += C[q * LD + j] * C[q * LD + l];
         d = warp_sum(d);
-        d = (d + v0 * R[j * LD + l]) * tau;
-        if (lane == 0) R[j * LD + l] -= d * v0;
-        for (int q = lane; q < c; q += 32) C[q * LD + l] -= d * C[q * LD + j];
+        d = (R[j * LD + l] + sc * d) * tau;
+        if (lane == 0) R[j * LD + l] -= d;
+        const T ds = d * sc;
+        for (int q = lane; q < c; q += 32) C[q * LD + l] -= ds * C[q * LD + j];
       }
     }
     __syncthreads();
@@ -162,7 +194,7 @@ __global__ void __launch_bounds__(kThreads)
   T* bufD = bufC + kNMax * LD;
   T* sig = bufD + kNMax * LD;       // kNMax
   T* sig_tmp = sig + kNMax;         // kNMax
-  __shared__ T s_v0, s_tau;
+  __shared__ T s_scale, s_tau;
   __shared__ int s_flag;
   __shared__ int s_pos[kNMax];
   __shared__ int s_colst[kMaxTargets];
@@ -180,6 +212,19 @@ __global__ void __launch_bounds__(kThreads)
       L.tau[i] = 0.0;
     }
     return;
+  }
+
+  // Frobenius norm of D_i: the rounding floor u ||D_i||_F of the threshold
+  __shared__ double s_red[kWarps];
+  {
+    const T* Dg0 = pool + L.diag_off[i];
+    double ss = 0.0;
+    for (int e = tid; e < n * n; e += kThreads) {
+      double v = static_cast<double>(Dg0[e]);
+      ss += v * v;
+    }
+    ss = warp_sum(ss);
+    if (lane == 0) s_red[warp] = ss;
   }
 
   // ---------------- A. R factor of F_i^T --------------------------------
@@ -212,14 +257,14 @@ __global__ void __launch_bounds__(kThreads)
       total_rows += take;
       if (crow == kChunk) {
         __syncthreads();
-        householder_stack(R, C, n, crow, &s_v0, &s_tau);
+        householder_stack(R, C, n, crow, &s_scale, &s_tau);
         crow = 0;
       }
     }
   }
   if (crow > 0) {
     __syncthreads();
-    householder_stack(R, C, n, crow, &s_v0, &s_tau);
+    householder_stack(R, C, n, crow, &s_scale, &s_tau);
   }
 
   // ---------------- B. one-sided Jacobi on R ----------------------------
@@ -304,10 +349,17 @@ __global__ void __launch_bounds__(kThreads)
       U[a * LD + s_pos[j]] = V[a * LD + j];
     }
     const double smax = static_cast<double>(sig[0]);
+    if (!isfinite(smax)) {
+      if (tid == 0) set_status(status, CE_ERR_NOT_SPD, level, i, 2);
+      return;
+    }
     if (tol == 0.0)
       tau = n * static_cast<double>(Eps<T>::v) * smax;
     else
       tau = (tol_mode == CE_TOL_ABS) ? tol : tol * smax;
+    double dn2 = 0.0;
+    for (int w = 0; w < kWarps; ++w) dn2 += s_red[w];
+    tau = fmax(tau, static_cast<double>(Eps<T>::v) * sqrt(dn2));
     for (int k = 0; k < n; ++k) r += (static_cast<double>(sig[k]) > tau) ? 1 : 0;
   } else {
     for (int e = tid; e < n * LD; e += kThreads) {
@@ -355,7 +407,7 @@ __global__ void __launch_bounds__(kThreads)
   for (int k = 0; k < m; ++k) {
     const T piv = Tm[(r + k) * LD + r + k];
     if (!(piv > T(0))) {
-      if (tid == 0) set_status(status, CE_ERR_NOT_SPD, level, i);
+      if (tid == 0) set_status(status, CE_ERR_NOT_SPD, level, i, 1, k, static_cast<double>(piv));
       return;
     }
     const T d = sqrt(piv);
@@ -523,7 +575,7 @@ __global__ void potrf_tile_kernel(double* A, int n, int k0, int level, int* stat
   for (int k = 0; k < nb; ++k) {
     const double piv = t[k * NBL + k];
     if (!(piv > 0.0)) {
-      if (threadIdx.x == 0) set_status(status, CE_ERR_NOT_SPD, level, -1);
+      if (threadIdx.x == 0) set_status(status, CE_ERR_NOT_SPD, level, -1, 1, k0 + k, piv);
       return;
     }
     const double d = sqrt(piv);

@@ -12,8 +12,10 @@ namespace ce {
 // kernels launched by the library (process-wide)
 extern std::atomic<int64_t> g_launches;
 
-// status word layout: [0] = ce_status code, [1] = level, [2] = block
-constexpr int kStatusWords = 4;
+// status word layout: [0] = ce_status code, [1] = level, [2] = block,
+// [3] = reason (1 pivot <= 0, 2 non-finite sigma), [4] = pivot index,
+// [6..7] = pivot value (double bits)
+constexpr int kStatusWords = 8;
 
 size_t row_kernel_smem(int esize);
 cudaError_t launch_row_kernel(int esize, const LevelDev& L, int first, int count, int level,

@@ -57,6 +57,30 @@ def test_tol0_reproduces_A(kind, n, box, levels, J):
     assert res.converged and res.iters == 1
 
 
+@pytest.mark.parametrize("kind,n,box,levels,J", [
+    ("p2", 32, (4, 4), 2, 4),
+    ("p2", 32, (8, 4), 3, 4),
+    ("p3", 8, (2, 2, 2), 2, 8),
+])
+def test_forward_product_tol0_is_A(kind, n, box, levels, J):
+    # M x = Q^T L L^T Q x equals A x when nothing is dropped (eq. bl_chol),
+    # checked without any inverse
+    A, perm, B = _problem(kind, n, box)
+    F = ce.factorize(A, perm, B, 0.0, levels, J)
+    x = wl.rhs(A.shape[0], 12)
+    assert np.linalg.norm(ce.multiply(F, x) - A @ x) / np.linalg.norm(A @ x) < 1e-13
+
+
+def test_forward_product_inverts_apply():
+    w = wl.make_workload("poisson2d_64_B16")
+    F = ce.factorize(w.A, w.perm, w.B, 1e-2, w.levels, w.J)
+    b = w.b
+    assert np.linalg.norm(ce.multiply(F, ce.apply(F, b)) - b) / np.linalg.norm(b) < 1e-12
+    # and M approximates A to about the truncation level
+    rel = np.linalg.norm(ce.multiply(F, b) - w.A @ b) / np.linalg.norm(w.A @ b)
+    assert 0 < rel < 1e-2
+
+
 def test_levels0_is_dense_cholesky():
     A, perm, B = _problem("p2", 16, (4, 4))
     F = ce.factorize(A, perm, B, 1e-2, 0, 4)
