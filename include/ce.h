@@ -166,6 +166,29 @@ ce_status pcg_solve(const ce_csb* A, const ce_factor* F, const double* b_dev,
                     double* x_dev, double rtol, int maxit, ce_pcg_info* info,
                     void* stream);
 
+/*
+ * pcg_solve_noalloc -- the same FP64 PCG as pcg_solve (same arguments, same
+ * arithmetic, same results), for callers that cannot let a library allocate
+ * device memory: applications whose GPU memory is reserved up front by their
+ * own pool allocator, latency-critical loops that cannot afford the implicit
+ * device synchronization of cudaMalloc/cudaFree, and plugins whose host
+ * application forbids allocation.  The paper has no counterpart; it is a
+ * deployment variant of pcg_solve.
+ *   - Allocates nothing: the work vectors live in one static device array
+ *     (4 x 65536 doubles plus reduction partials, about 2 MiB) that every GPU
+ *     loading the library holds until the process exits.
+ *   - n > 65536 is rejected with CE_ERR_LIMIT (ce_last_error() says why).
+ *   - The first call on a device looks the array's device address up
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents; calls
+ *     whose work overlaps on the GPU (other streams, other host threads) race
+ *     on it and must be serialized by the caller.
+ */
+ce_status pcg_solve_noalloc(const ce_csb* A, const ce_factor* F,
+                            const double* b_dev, double* x_dev, double rtol,
+                            int maxit, ce_pcg_info* info, void* stream);
+
 /* Release a handle (NULL is ignored). */
 void ce_csb_destroy(ce_csb* A);
 void ce_factor_destroy(ce_factor* F);

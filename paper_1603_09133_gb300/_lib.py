@@ -75,6 +75,7 @@ SIGNATURES = {
                                       C.c_double, C.c_int, PP]),
     "ce_apply": (C.c_int, [P, P, P, P]),
     "pcg_solve": (C.c_int, [P, P, P, P, C.c_double, C.c_int, C.POINTER(ce_pcg_info), P]),
+    "pcg_solve_noalloc": (C.c_int, [P, P, P, P, C.c_double, C.c_int, C.POINTER(ce_pcg_info), P]),
     "ce_csb_destroy": (None, [P]),
     "ce_factor_destroy": (None, [P]),
     "ce_strerror": (C.c_char_p, [C.c_int]),

@@ -35,6 +35,14 @@ void check(cudaError_t e, const char* what) {
   }
 }
 
+}  // namespace
+
+namespace ce {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+}  // namespace ce
+
+namespace {
+
 ce_status status_of(const CudaFail& f) {
   return f.e == cudaErrorMemoryAllocation ? CE_ERR_OOM : CE_ERR_CUDA;
 }

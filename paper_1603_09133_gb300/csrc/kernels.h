@@ -6,11 +6,15 @@
 #include "ce_internal.h"
 
 #include <atomic>
+#include <string>
 
 namespace ce {
 
 // kernels launched by the library (process-wide)
 extern std::atomic<int64_t> g_launches;
+
+// text returned by ce_last_error() on this thread
+void set_last_error(const std::string& msg);
 
 // status word layout: [0] = ce_status code, [1] = level, [2] = block,
 // [3] = reason (1 pivot <= 0, 2 non-finite sigma), [4] = pivot index,
