@@ -506,7 +506,8 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       check(cudaEventRecord(ev0, s), "event");
       for (int c = 0; c < P.ncolours; ++c)
         check(ce::launch_row_kernel(es, st.dev, P.colour_ptr[c], P.colour_ptr[c + 1] - P.colour_ptr[c], l,
-                                    o.tol, o.tol_mode, F->d_status, s),
+                                    o.tol, o.tol_mode, F->d_status, P.nmax,
+                                    P.colour_ptr[c + 1] - P.colour_ptr[c], s),
               "row kernel");
       check(cudaEventRecord(ev1, s), "event");
       st.rank.resize(P.M);

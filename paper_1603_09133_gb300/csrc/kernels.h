@@ -22,8 +22,10 @@ void set_last_error(const std::string& msg);
 constexpr int kStatusWords = 8;
 
 size_t row_kernel_smem(int esize);
+// busy_ctas: rows in the launch (sets the shared-memory budget per CTA)
 cudaError_t launch_row_kernel(int esize, const LevelDev& L, int first, int count, int level,
-                              double tol, int tol_mode, int* status, cudaStream_t s);
+                              double tol, int tol_mode, int* status, int nmax, int busy_ctas,
+                              cudaStream_t s);
 cudaError_t launch_scatter_csr(int esize, const int64_t* scatter, const double* val, int64_t nnz,
                                void* pool, cudaStream_t s);
 cudaError_t launch_copy_tasks(int esize_src, int esize_dst, const CopyTask* tasks, int ntasks,

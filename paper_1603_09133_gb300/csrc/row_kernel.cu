@@ -1,0 +1,715 @@
+// ce_row_kernel: one CTA per block row i of one colour (Algorithm 2, one
+// iteration of its loop, for all rows of a colour at once).
+//
+//   0. ||D_i||_F (rounding floor of the truncation threshold)
+//   A. compression (Section 2.2, eq. rreav): R factor of F_i^T.  Rows of F_i^T
+//      are cut into chunks of 32; warp w reduces chunks w, w+QW, ... into its
+//      own triangular R_w with warp-synchronous Householder steps (no CTA
+//      barrier per column), then the R_w are merged pairwise (tree).  F_i F_i^T
+//      = R^T R, so F_i and R^T share their left singular vectors.
+//   B. one-sided (Hestenes) Jacobi on the columns of R: R V = U' S gives
+//      U_i = V and sigma = S (descending); half a warp per column pair, so all
+//      pairs of a round-robin round run at once; r_i = #{sigma_k > tau_i}.
+//   C. transform and elimination (eq. q, eq. sm_L): T = U^T D U, Cholesky of
+//      the non-basis block T_nn = L_hat L_hat^T, L_hat^{-1} formed once so every
+//      W = L_hat^{-1} S is a GEMM; close rows <- U^T C (kept rows minus the
+//      basis Schur term), far rows <- U_b^T F (rows r.. are E_i, dropped), and
+//      the Schur update A(p, q) -= W_p^T W_q between close targets.
+// Blocks of one colour have disjoint closed neighbourhoods (distance-2
+// colouring), so the CTAs of one launch touch disjoint block pairs.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "kernels.h"
+
+namespace ce {
+
+namespace {
+
+constexpr int kMaxWarps = 16;
+constexpr int kChunk = 32;       // rows of F_i^T per warp Householder pass
+constexpr int kMaxSweeps = 40;   // Jacobi sweep cap (bounded loop)
+constexpr int kMaxTargets = 32;
+constexpr int kMaxFar = 128;
+
+template <typename T>
+struct Eps;
+template <>
+struct Eps<double> {
+  static constexpr double v = 2.220446049250313e-16;
+};
+template <>
+struct Eps<float> {
+  static constexpr float v = 1.1920928955078125e-07f;
+};
+
+template <typename T>
+struct Tiny;  // smallest normal number
+template <>
+struct Tiny<double> {
+  static constexpr double v = 2.2250738585072014e-308;
+};
+template <>
+struct Tiny<float> {
+  static constexpr float v = 1.1754943508222875e-38f;
+};
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
+
+template <typename T>
+__device__ __forceinline__ T half_sum(T v) {  // sum over the 16 lanes of a half warp
+#pragma unroll
+  for (int o = 8; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ int width_of(const LevelDev& L, int k, int ci) {
+  return (L.colour[k] < ci) ? L.rank[k] : L.n[k];
+}
+
+__device__ void set_status(int* status, int code, int level, int block, int reason = 0,
+                           int pivot = -1, double value = 0.0) {
+  if (atomicCAS(status, 0, code) == 0) {
+    status[1] = level;
+    status[2] = block;
+    status[3] = reason;
+    status[4] = pivot;
+    *reinterpret_cast<double*>(status + 6) = value;
+  }
+}
+
+// Householder reflector of the column x = [x0; c] (c held as c_lo, c_hi by
+// each lane for rows lane and lane + 32), unit-leading form H = I - tau v v^T,
+// v = [1; sc c], beta = -sign(x0) ||x||.  Columns whose largest entry is
+// subnormal are rounding noise and give tau = 0.  Returns false for tau = 0.
+template <typename T>
+__device__ __forceinline__ bool reflector(T x0, T c_lo, T c_hi, T& beta, T& tau, T& sc) {
+  T amax = warp_max(fmax(fabs(c_lo), fabs(c_hi)));
+  if (!(amax >= Tiny<T>::v)) return false;
+  const T xl = c_lo / amax, xh = c_hi / amax;
+  const T s = warp_sum(xl * xl + xh * xh);
+  const T a = fmax(amax, fabs(x0));
+  const T x0a = x0 / a, ca = amax / a;
+  const T nrm = a * sqrt(x0a * x0a + s * ca * ca);
+  beta = (x0 >= T(0)) ? -nrm : nrm;
+  tau = (beta - x0) / beta;
+  sc = T(1) / (x0 - beta);
+  return true;
+}
+
+// Warp-synchronous QR update of [R; C]: R n x n upper triangular, C rows x n
+// (rows <= 32).  After the call R is the triangular factor of the stack.
+template <typename T>
+__device__ void warp_qr_stack(T* R, T* C, T* vb, int n, int rows, int LD) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < n; ++j) {
+    const T x = (lane < rows) ? C[lane * LD + j] : T(0);
+    T beta, tau, sc;
+    if (!reflector(R[j * LD + j], x, T(0), beta, tau, sc)) continue;
+    vb[lane] = x * sc;
+    __syncwarp();
+    if (lane == 0) R[j * LD + j] = beta;
+    for (int l = j + 1 + lane; l < n; l += 32) {
+      T d0 = R[j * LD + l], d1 = 0;
+      int q = 0;
+      for (; q + 1 < rows; q += 2) {
+        d0 += vb[q] * C[q * LD + l];
+        d1 += vb[q + 1] * C[(q + 1) * LD + l];
+      }
+      if (q < rows) d0 += vb[q] * C[q * LD + l];
+      const T d = (d0 + d1) * tau;
+      R[j * LD + l] -= d;
+      for (q = 0; q < rows; ++q) C[q * LD + l] -= d * vb[q];
+    }
+    __syncwarp();
+  }
+}
+
+// Warp-synchronous merge of two triangular factors: Ra <- R factor of
+// [Ra; Rb] (both n x n upper triangular; Rb is destroyed).
+template <typename T>
+__device__ void warp_qr_merge(T* Ra, T* Rb, T* vb, int n, int LD) {
+  const int lane = threadIdx.x & 31;
+  for (int j = 0; j < n; ++j) {
+    const T xl = (lane <= j) ? Rb[lane * LD + j] : T(0);
+    const T xh = (lane + 32 <= j) ? Rb[(lane + 32) * LD + j] : T(0);
+    T beta, tau, sc;
+    if (!reflector(Ra[j * LD + j], xl, xh, beta, tau, sc)) continue;
+    vb[lane] = xl * sc;
+    vb[lane + 32] = xh * sc;
+    __syncwarp();
+    if (lane == 0) Ra[j * LD + j] = beta;
+    const int rows = j + 1;
+    for (int l = j + 1 + lane; l < n; l += 32) {
+      T d0 = Ra[j * LD + l], d1 = 0;
+      int q = 0;
+      for (; q + 1 < rows; q += 2) {
+        d0 += vb[q] * Rb[q * LD + l];
+        d1 += vb[q + 1] * Rb[(q + 1) * LD + l];
+      }
+      if (q < rows) d0 += vb[q] * Rb[q * LD + l];
+      const T d = (d0 + d1) * tau;
+      Ra[j * LD + l] -= d;
+      for (q = 0; q < rows; ++q) Rb[q * LD + l] -= d * vb[q];
+    }
+    __syncwarp();
+  }
+}
+
+// out(a, b) op= sum_k A(a, k) B(k, b), a < M, b < N, k < K; 2 x 2 register
+// tiles over the CTA.  store(a, b, v) receives the sum.
+template <typename T, int NT, typename FA, typename FB, typename FS>
+__device__ __forceinline__ void cta_gemm(int M, int N, int K, FA A, FB B, FS store) {
+  const int tm = (M + 1) >> 1, tn = (N + 1) >> 1;
+  for (int t = threadIdx.x; t < tm * tn; t += NT) {
+    const int a0 = (t / tn) * 2, b0 = (t % tn) * 2;
+    const bool a1 = a0 + 1 < M, b1 = b0 + 1 < N;
+    T c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+    for (int k = 0; k < K; ++k) {
+      const T x0 = A(a0, k), x1 = a1 ? A(a0 + 1, k) : T(0);
+      const T y0 = B(k, b0), y1 = b1 ? B(k, b0 + 1) : T(0);
+      c00 += x0 * y0;
+      c01 += x0 * y1;
+      c10 += x1 * y0;
+      c11 += x1 * y1;
+    }
+    store(a0, b0, c00);
+    if (b1) store(a0, b0 + 1, c01);
+    if (a1) store(a0 + 1, b0, c10);
+    if (a1 && b1) store(a0 + 1, b0 + 1, c11);
+  }
+}
+
+// n x w tile of the pair (i, k) seen from row i -> sm (row-major, LD); the
+// pair is stored once as (min, max)
+template <typename T, int NT>
+__device__ void load_row_tile(T* sm, const T* X, int i, int k, int n, int nk, int w, int LD) {
+  if (i < k) {  // stored n x nk
+    for (int e = threadIdx.x; e < n * w; e += NT) {
+      int a = e / w, b = e - a * w;
+      sm[a * LD + b] = X[(int64_t)a * nk + b];
+    }
+  } else {      // stored nk x n, tile = X[0:w, :]^T
+    for (int e = threadIdx.x; e < n * w; e += NT) {
+      int b = e / n, a = e - b * n;
+      sm[a * LD + b] = X[(int64_t)b * n + a];
+    }
+  }
+}
+
+template <typename T, int NT>
+__device__ void store_row_tile(const T* sm, T* X, int i, int k, int n, int nk, int rows, int w, int LD) {
+  if (i < k) {
+    for (int e = threadIdx.x; e < rows * w; e += NT) {
+      int a = e / w, b = e - a * w;
+      X[(int64_t)a * nk + b] = sm[a * LD + b];
+    }
+  } else {
+    for (int e = threadIdx.x; e < rows * w; e += NT) {
+      int b = e / rows, a = e - b * rows;
+      X[(int64_t)b * n + a] = sm[a * LD + b];
+    }
+  }
+}
+
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
+    ce_row_kernel(LevelDev L, int first, int level, double tol, int tol_mode, int* status, int nmax,
+                  int LD, int QW) {
+  constexpr int kWarpsNT = NT / 32;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int NL = nmax * LD;
+  T* U = reinterpret_cast<T*>(smem_raw);            // persistent: U_i
+  T* sig = U + NL;                                   // nmax
+  T* sig_tmp = sig + nmax;                           // nmax
+  T* un = sig_tmp + nmax;                            // union region
+  const int per_warp = NL + kChunk * LD + 64;        // phase A: R_w, C_w, v_w
+  T* X = un;                                         // phase B: R (= R_0), V
+  T* V = un + NL;
+  T* Tm = un;                                        // phase C: T, L_hat^{-1}, Y, tile
+  T* Li = un + NL;
+  T* Y = un + 2 * NL;
+  T* Xt = un + 3 * NL;
+
+  __shared__ double s_red[kMaxWarps];
+  __shared__ int s_flag;
+  __shared__ T s_skip2;
+  __shared__ int s_pos[64];
+  __shared__ int s_colst[kMaxTargets], s_tgt[kMaxTargets], s_w[kMaxTargets];
+  __shared__ int s_fw[kMaxFar + 1], s_fpre[kMaxFar + 1], s_fk[kMaxFar];
+  __shared__ int64_t s_foff[kMaxFar];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int i = L.order[first + blockIdx.x];
+  const int n = L.n[i];
+  const int ci = L.colour[i];
+  T* pool = reinterpret_cast<T*>(L.pool);
+  if (n == 0) {
+    if (tid == 0) {
+      L.rank[i] = 0;
+      L.tau[i] = 0.0;
+    }
+    return;
+  }
+  const int f0 = L.far_ptr[i], nf = L.far_ptr[i + 1] - f0;
+  if (nf > kMaxFar) {
+    if (tid == 0) set_status(status, CE_ERR_LIMIT, level, i);
+    return;
+  }
+
+  // ---------------- 0. ||D_i||_F and the far-row layout -------------------
+  T* Dg = pool + L.diag_off[i];
+  {
+    double ss = 0.0;
+    for (int e = tid; e < n * n; e += NT) {
+      double v = static_cast<double>(Dg[e]);
+      ss += v * v;
+    }
+    ss = warp_sum(ss);
+    if (lane == 0) s_red[warp] = ss;
+  }
+  for (int f = tid; f < nf; f += NT) {
+    const int k = L.far_blk[f0 + f];
+    s_fk[f] = k;
+    s_fw[f] = width_of(L, k, ci);
+    s_foff[f] = L.far_off[f0 + f];
+  }
+  __syncthreads();
+  if (tid == 0) {
+    int acc = 0;
+    for (int f = 0; f < nf; ++f) {
+      s_fpre[f] = acc;
+      acc += s_fw[f];
+    }
+    s_fpre[nf] = acc;
+  }
+  __syncthreads();
+  const int mF = s_fpre[nf];
+
+  // ---------------- A. R factor of F_i^T (warp TSQR + tree merge) ----------
+  int r = 0;
+  double tau = 0.0;
+  if (mF > 0) {
+    const int nchunks = (mF + kChunk - 1) / kChunk;
+    const int qw = min(QW, nchunks);
+    if (warp < qw) {
+      T* Rw = un + warp * per_warp;
+      T* Cw = Rw + NL;
+      T* vb = Cw + kChunk * LD;
+      for (int e = lane; e < n * LD; e += 32) Rw[e] = T(0);
+      for (int c = warp; c < nchunks; c += qw) {
+        const int g0 = c * kChunk;
+        const int rows = min(kChunk, mF - g0);
+        // far block holding row g0 of F_i^T
+        int f = 0;
+        while (f + 1 < nf && s_fpre[f + 1] <= g0) ++f;
+        int q = g0 - s_fpre[f];
+        for (int rr = 0; rr < rows; ++rr) {
+          while (q >= s_fw[f]) {
+            ++f;
+            q = 0;
+          }
+          const int k = s_fk[f];
+          const T* Xg = pool + s_foff[f];
+          if (i < k) {   // F = X[:, :w]: row q of F^T = column q of X
+            const int nk = L.n[k];
+            for (int a = lane; a < n; a += 32) Cw[rr * LD + a] = Xg[(int64_t)a * nk + q];
+          } else {       // rows of F^T are rows of X
+            for (int a = lane; a < n; a += 32) Cw[rr * LD + a] = Xg[(int64_t)q * n + a];
+          }
+          ++q;
+        }
+        __syncwarp();
+        warp_qr_stack(Rw, Cw, vb, n, rows, LD);
+      }
+    }
+    __syncthreads();
+    for (int step = 1; step < qw; step *= 2) {
+      if (warp % (2 * step) == 0 && warp + step < qw) {
+        T* Ra = un + warp * per_warp;
+        T* Rb = un + (warp + step) * per_warp;
+        warp_qr_merge(Ra, Rb, Ra + NL + kChunk * LD, n, LD);
+      }
+      __syncthreads();
+    }
+
+    // ---------------- B. one-sided Jacobi on R (= X) ------------------------
+    for (int e = tid; e < n * n; e += NT) {
+      int a = e / n, b = e - a * n;
+      V[a * LD + b] = (a == b) ? T(1) : T(0);
+    }
+    __syncthreads();
+    const int nb = n + (n & 1);
+    const int npairs = nb / 2;
+    const int half = lane >> 4, hl = lane & 15;
+    const T tolJ = T(n) * Eps<T>::v;
+    const T tolJ2 = tolJ * tolJ;
+    double dn2 = 0.0;
+    for (int w = 0; w < kWarpsNT; ++w) dn2 += s_red[w];
+    const double floor_tau = static_cast<double>(Eps<T>::v) * sqrt(dn2);
+    const T floor_tau_t = static_cast<T>(floor_tau);
+    for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+      // Columns whose norm stays below tau_est / (2 sqrt n) form a group whose
+      // singular values are all below tau / 2: rotating two of them changes
+      // neither the kept subspace nor the rank, so such pairs are skipped.
+      // tau_est uses the largest current column norm (<= sigma_1).
+      for (int j = warp; j < n; j += kWarpsNT) {
+        T s = 0;
+        for (int row = lane; row < n; row += 32) s += X[row * LD + j] * X[row * LD + j];
+        s = warp_sum(s);
+        if (lane == 0) sig_tmp[j] = s;
+      }
+      __syncthreads();
+      if (warp == 0) {
+        T cm = fmax(lane < n ? sig_tmp[lane] : T(0), lane + 32 < n ? sig_tmp[lane + 32] : T(0));
+        cm = warp_max(cm);
+        if (lane == 0) {
+          const T sm = sqrt(cm);
+          T test = (tol == 0.0) ? T(n) * Eps<T>::v * sm
+                                : ((tol_mode == CE_TOL_ABS) ? T(tol) : T(tol) * sm);
+          test = fmax(test, floor_tau_t) * T(0.5) * fast_rsqrt(T(n));
+          s_skip2 = test * test;
+          s_flag = 0;
+        }
+      }
+      __syncthreads();
+      const T skip2 = s_skip2;
+      for (int rnd = 0; rnd < nb - 1; ++rnd) {
+        for (int tb = warp * 2; tb < npairs; tb += NT / 16) {
+          const int t = tb + half;
+          int p = nb - 1, q = rnd;
+          if (t != 0) {
+            p = rnd + t;
+            if (p >= nb - 1) p -= nb - 1;
+            q = rnd - t;
+            if (q < 0) q += nb - 1;
+          }
+          const bool valid = t < npairs && p < n && q < n;
+          T a = 0, b = 0, g = 0;
+          if (valid) {
+            for (int row = hl; row < n; row += 16) {
+              T xp = X[row * LD + p], xq = X[row * LD + q];
+              a += xp * xp;
+              b += xq * xq;
+              g += xp * xq;
+            }
+          }
+          a = half_sum(a);
+          b = half_sum(b);
+          g = half_sum(g);
+          if (valid && g != T(0) && (a >= skip2 || b >= skip2) && g * g > tolJ2 * a * b) {
+            // tan of the rotation angle, t = sign(z) / (|z| + sqrt(1 + z^2)),
+            // z = (b - a) / (2 g); cs = 1/sqrt(1 + t^2), sn = cs t is an exact
+            // rotation up to rounding whatever the accuracy of t
+            const T zeta = (b - a) * fast_rcp(T(2) * g);
+            const T az = fabs(zeta);
+            const T den = (az > T(1)) ? az * (T(1) + sqrt(T(1) + fast_rcp(az * az)))
+                                      : az + sqrt(T(1) + az * az);
+            const T tt = ((zeta >= T(0)) ? T(1) : T(-1)) * fast_rcp(den);
+            const T cs = fast_rsqrt(T(1) + tt * tt), sn = cs * tt;
+            for (int row = hl; row < n; row += 16) {
+              T xp = X[row * LD + p], xq = X[row * LD + q];
+              X[row * LD + p] = cs * xp - sn * xq;
+              X[row * LD + q] = sn * xp + cs * xq;
+              T vp = V[row * LD + p], vq = V[row * LD + q];
+              V[row * LD + p] = cs * vp - sn * vq;
+              V[row * LD + q] = sn * vp + cs * vq;
+            }
+            if (hl == 0) s_flag = 1;
+          }
+        }
+        __syncthreads();
+      }
+      const int rotated = s_flag;
+      __syncthreads();
+      if (!rotated) break;
+    }
+    for (int j = tid; j < n; j += NT) {
+      T s = 0;
+      for (int row = 0; row < n; ++row) s += X[row * LD + j] * X[row * LD + j];
+      sig_tmp[j] = sqrt(s);
+    }
+    __syncthreads();
+    for (int j = tid; j < n; j += NT) {
+      const T sj = sig_tmp[j];
+      int pos = 0;
+      for (int k = 0; k < n; ++k) pos += (sig_tmp[k] > sj) || (sig_tmp[k] == sj && k < j);
+      s_pos[j] = pos;
+      sig[pos] = sj;
+    }
+    __syncthreads();
+    for (int e = tid; e < n * n; e += NT) {
+      int a = e / n, j = e - a * n;
+      U[a * LD + s_pos[j]] = V[a * LD + j];
+    }
+    const double smax = static_cast<double>(sig[0]);
+    if (!isfinite(smax)) {
+      if (tid == 0) set_status(status, CE_ERR_NOT_SPD, level, i, 2);
+      return;
+    }
+    if (tol == 0.0)
+      tau = n * static_cast<double>(Eps<T>::v) * smax;
+    else
+      tau = (tol_mode == CE_TOL_ABS) ? tol : tol * smax;
+    tau = fmax(tau, floor_tau);
+    if (tid == 0) {
+      int rr = 0;
+      for (int k = 0; k < n; ++k) rr += (static_cast<double>(sig[k]) > tau) ? 1 : 0;
+      s_flag = rr;
+    }
+    __syncthreads();
+    r = s_flag;
+  } else {
+    for (int e = tid; e < n * n; e += NT) {
+      int a = e / n, b = e - a * n;
+      U[a * LD + b] = (a == b) ? T(1) : T(0);
+    }
+    for (int k = tid; k < n; k += NT) sig[k] = T(0);
+  }
+  __syncthreads();
+  const int m = n - r;
+  if (tid == 0) {
+    L.rank[i] = r;
+    L.tau[i] = tau;
+  }
+  for (int k = tid; k < n; k += NT) L.sigma[L.vec_off[i] + k] = static_cast<double>(sig[k]);
+  T* Ug = reinterpret_cast<T*>(L.U) + L.u_off[i];
+  for (int e = tid; e < n * n; e += NT) {
+    int a = e / n, b = e - a * n;
+    Ug[e] = U[a * LD + b];
+  }
+
+  // ---------------- C. transform + elimination ----------------------------
+  for (int e = tid; e < n * n; e += NT) {
+    int a = e / n, b = e - a * n;
+    Y[a * LD + b] = Dg[e];
+  }
+  __syncthreads();
+  cta_gemm<T, NT>(n, n, n, [&](int a, int k) { return Y[a * LD + k]; },        // Xt = D U
+              [&](int k, int b) { return U[k * LD + b]; },
+              [&](int a, int b, T v) { Xt[a * LD + b] = v; });
+  __syncthreads();
+  cta_gemm<T, NT>(n, n, n, [&](int a, int k) { return U[k * LD + a]; },        // Tm = U^T D U
+              [&](int k, int b) { return Xt[k * LD + b]; },
+              [&](int a, int b, T v) { Tm[a * LD + b] = v; });
+  __syncthreads();
+  // Cholesky of Tm[r:, r:]: right-looking, unscaled updates, one barrier per
+  // step; L_hat(a, k) = Tm(a, k) / sqrt(Tm(k, k)) at the end
+  T* Tn = Tm + r * LD + r;
+  for (int k = 0; k < m; ++k) {
+    const T piv = Tn[k * LD + k];
+    if (!(piv > T(0))) {
+      if (tid == 0) set_status(status, CE_ERR_NOT_SPD, level, i, 1, k, static_cast<double>(piv));
+      return;
+    }
+    const int rem = m - k - 1;
+    const T ip = T(1) / piv;
+    for (int e = tid; e < rem * rem; e += NT) {
+      const int a = k + 1 + e / rem, b = k + 1 + e % rem;
+      if (b <= a) Tn[a * LD + b] -= Tn[a * LD + k] * Tn[b * LD + k] * ip;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < m * m; e += NT) {
+    const int a = e / m, k = e - a * m;
+    if (k < a) Tn[a * LD + k] /= sqrt(Tn[k * LD + k]);
+  }
+  __syncthreads();
+  for (int k = tid; k < m; k += NT) Tn[k * LD + k] = sqrt(Tn[k * LD + k]);
+  __syncthreads();
+  T* Lg = reinterpret_cast<T*>(L.L) + L.l_off[i];
+  for (int e = tid; e < m * m; e += NT) {
+    int a = e / m, b = e - a * m;
+    Lg[e] = (b <= a) ? Tn[a * LD + b] : T(0);
+  }
+  // Li = L_hat^{-1} (lower), one column per thread
+  for (int j = tid; j < m; j += NT) {
+    for (int a = 0; a < j; ++a) Li[a * LD + j] = T(0);
+    for (int a = j; a < m; ++a) {
+      T x = (a == j) ? T(1) : T(0);
+      for (int k = j; k < a; ++k) x -= Tn[a * LD + k] * Li[k * LD + j];
+      Li[a * LD + j] = x / Tn[a * LD + a];
+    }
+  }
+  __syncthreads();
+  // W_b = L_hat^{-1} Tm[r:, :r] -> Y[0:m, 0:r], then back into Tm[r:, :r]
+  cta_gemm<T, NT>(m, r, m, [&](int a, int k) { return Li[a * LD + k]; },
+              [&](int k, int b) { return Tm[(r + k) * LD + b]; },
+              [&](int a, int b, T v) { Y[a * LD + b] = v; });
+  __syncthreads();
+  T* Wbase = reinterpret_cast<T*>(L.W) + L.w_off[i];
+  for (int e = tid; e < m * r; e += NT) {
+    int a = e / r, b = e - a * r;
+    const T v = Y[a * LD + b];
+    Tm[(r + a) * LD + b] = v;
+    Wbase[e] = v;
+  }
+  __syncthreads();
+  // basis diagonal block: Tm[:r, :r] - W_b^T W_b
+  cta_gemm<T, NT>(r, r, m, [&](int a, int k) { return Tm[(r + k) * LD + a]; },
+              [&](int k, int b) { return Tm[(r + k) * LD + b]; },
+              [&](int a, int b, T v) { Dg[(int64_t)a * n + b] = Tm[a * LD + b] - v; });
+  // target bookkeeping
+  const int c0 = L.close_ptr[i], c1 = L.close_ptr[i + 1];
+  const int nt = 1 + (c1 - c0);
+  if (nt > kMaxTargets) {
+    if (tid == 0) set_status(status, CE_ERR_LIMIT, level, i);
+    return;
+  }
+  if (tid == 0) {
+    s_tgt[0] = i;
+    s_w[0] = r;
+    s_colst[0] = 0;
+    int cs = n;
+    for (int t = 1; t < nt; ++t) {
+      int p = L.close_blk[c0 + t - 1];
+      s_tgt[t] = p;
+      s_w[t] = width_of(L, p, ci);
+      s_colst[t] = cs;
+      cs += L.n[p];
+    }
+  }
+  __syncthreads();
+  // close rows: Y = U^T X_ip; W_p = L_hat^{-1} Y[r:]; kept rows Y[:r] - W_b^T W_p
+  for (int t = 1; t < nt; ++t) {
+    const int p = s_tgt[t], w = s_w[t], np = L.n[p];
+    T* Xg = pool + L.close_off[c0 + t - 1];
+    load_row_tile<T, NT>(Xt, Xg, i, p, n, np, w, LD);
+    __syncthreads();
+    cta_gemm<T, NT>(n, w, n, [&](int a, int k) { return U[k * LD + a]; },
+                [&](int k, int b) { return Xt[k * LD + b]; },
+                [&](int a, int b, T v) { Y[a * LD + b] = v; });
+    __syncthreads();
+    T* Wp = Wbase + (int64_t)n * s_colst[t];
+    cta_gemm<T, NT>(m, w, m, [&](int a, int k) { return Li[a * LD + k]; },
+                [&](int k, int b) { return Y[(r + k) * LD + b]; },
+                [&](int a, int b, T v) {
+                  Xt[a * LD + b] = v;
+                  Wp[a * w + b] = v;
+                });
+    __syncthreads();
+    cta_gemm<T, NT>(r, w, m, [&](int a, int k) { return Tm[(r + k) * LD + a]; },
+                [&](int k, int b) { return Xt[k * LD + b]; },
+                [&](int a, int b, T v) { Y[a * LD + b] -= v; });
+    __syncthreads();
+    store_row_tile<T, NT>(Y, Xg, i, p, n, np, r, w, LD);
+    __syncthreads();
+  }
+  // far rows: keep U_b^T F (rows r.. of U^T F are E_i and are dropped)
+  for (int f = 0; f < nf; ++f) {
+    const int k = s_fk[f], w = s_fw[f];
+    if (w == 0 || r == 0) continue;
+    T* Xg = pool + s_foff[f];
+    load_row_tile<T, NT>(Xt, Xg, i, k, n, L.n[k], w, LD);
+    __syncthreads();
+    cta_gemm<T, NT>(r, w, n, [&](int a, int kk) { return U[kk * LD + a]; },
+                [&](int kk, int b) { return Xt[kk * LD + b]; },
+                [&](int a, int b, T v) { Y[a * LD + b] = v; });
+    __syncthreads();
+    store_row_tile<T, NT>(Y, Xg, i, k, n, L.n[k], r, w, LD);
+    __syncthreads();
+  }
+  // Schur update between close targets: A(p, q) -= W_p^T W_q
+  if (m > 0) {
+    int idx = L.schur_ptr[i] + nt;   // skip the row of the basis of i
+    for (int a = 1; a < nt; ++a) {
+      for (int b = a; b < nt; ++b, ++idx) {
+        const int wa = s_w[a], wb = s_w[b];
+        const T* Wa = Wbase + (int64_t)n * s_colst[a];
+        const T* Wb = Wbase + (int64_t)n * s_colst[b];
+        T* Xg = pool + L.schur_off[idx];
+        const int ld = L.n[s_tgt[b]];
+        cta_gemm<T, NT>(wa, wb, m, [&](int x, int k) { return Wa[k * wa + x]; },
+                    [&](int k, int y) { return Wb[k * wb + y]; },
+                    [&](int x, int y, T v) { Xg[(int64_t)x * ld + y] -= v; });
+      }
+    }
+  }
+}
+
+int choose_ld(int nmax) { return (nmax % 2 == 0) ? nmax + 1 : nmax; }
+
+size_t smem_bytes(int es, int nmax, int LD, int QW) {  // QW <= 16
+  const size_t NL = (size_t)nmax * LD;
+  const size_t per_warp = NL + kChunk * LD + 64;
+  const size_t un = std::max(QW * per_warp, 4 * NL);
+  return es * (NL + 2 * (size_t)nmax + un);
+}
+
+// Largest dynamic shared memory a CTA of ce_row_kernel<T, NT> may request
+// (the device's opt-in maximum minus the kernel's static shared memory); the
+// attribute is raised to it once.
+template <typename T, int NT>
+cudaError_t max_dyn_smem(size_t* out) {
+  static size_t limit = 0;
+  if (limit == 0) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, ce_row_kernel<T, NT>);
+    if (e != cudaSuccess) return e;
+    const size_t lim = static_cast<size_t>(optin) - fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(ce_row_kernel<T, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+    if (e != cudaSuccess) return e;
+    limit = lim;
+  }
+  *out = limit;
+  return cudaSuccess;
+}
+
+template <typename T, int NT>
+cudaError_t launch_nt(const LevelDev& L, int first, int count, int level, double tol, int tol_mode,
+                      int* status, int nmax, size_t budget, cudaStream_t s) {
+  const int LD = choose_ld(nmax);
+  size_t limit = 0;
+  cudaError_t e = max_dyn_smem<T, NT>(&limit);
+  if (e != cudaSuccess) return e;
+  budget = std::min(budget, limit);
+  int QW = NT / 32;
+  while (QW > 1 && smem_bytes(sizeof(T), nmax, LD, QW) > budget) --QW;
+  const size_t smem = smem_bytes(sizeof(T), nmax, LD, QW);
+  if (smem > limit) return cudaErrorInvalidValue;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  ce_row_kernel<T, NT><<<count, NT, smem, s>>>(L, first, level, tol, tol_mode, status, nmax, LD, QW);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+size_t row_kernel_smem(int esize) { return smem_bytes(esize, kNMax, choose_ld(kNMax), 1); }
+
+cudaError_t launch_row_kernel(int esize, const LevelDev& L, int first, int count, int level,
+                              double tol, int tol_mode, int* status, int nmax, int busy_ctas,
+                              cudaStream_t s) {
+  if (count <= 0) return cudaSuccess;
+  nmax = std::max(nmax, 1);
+  // many rows in the colour: 256-thread CTAs, about 3 per SM; few rows: one
+  // 512-thread CTA per SM with the whole shared memory
+  const bool busy = busy_ctas >= 2 * 152;
+  if (esize == 8)
+    return busy ? launch_nt<double, 256>(L, first, count, level, tol, tol_mode, status, nmax, 72 * 1024, s)
+                : launch_nt<double, 512>(L, first, count, level, tol, tol_mode, status, nmax, ~size_t(0), s);
+  return busy ? launch_nt<float, 256>(L, first, count, level, tol, tol_mode, status, nmax, 72 * 1024, s)
+              : launch_nt<float, 512>(L, first, count, level, tol, tol_mode, status, nmax, ~size_t(0), s);
+}
+
+}  // namespace ce
