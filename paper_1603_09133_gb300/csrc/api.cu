@@ -265,6 +265,7 @@ void free_factor(ce_factor* F, cudaStream_t s) {
     dfree(st.fac, s);
   }
   dfree(F->d_coarse, s);
+  dfree(F->d_cdinv, s);
   dfree(F->d_work, s);
   dfree(F->d_status, s);
   if (F->owned_csb) ce_csb_destroy(F->owned_csb);
@@ -563,6 +564,9 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
         check(cudaMemsetAsync(F->d_coarse, 0, nb, s), "memset coarse");
         run_copy_tasks(dense_tasks(cur), es, 8, pool, F->d_coarse, s);
         check(ce::coarse_cholesky(F->d_coarse, F->nc, (int)F->levels.size(), F->d_status, s), "coarse chol");
+        const int npan = (F->nc + 63) / 64;
+        F->d_cdinv = static_cast<double*>(dalloc((size_t)npan * 64 * 64 * sizeof(double), s));
+        check(ce::launch_coarse_dinv(F->d_coarse, F->nc, F->d_cdinv, s), "coarse diagonal inverses");
         check(cudaEventRecord(ev1, s), "event");
         check(cudaMemcpyAsync(hstatus, F->d_status, sizeof(hstatus), cudaMemcpyDeviceToHost, s), "D2H");
         check(cudaStreamSynchronize(s), "coarse sync");
@@ -665,11 +669,11 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev, void*
       double* vn = (l + 1 < nl) ? F->d_work + F->vec_base[l + 1] : coarse;
       for (int c = 0; c < st.plan.ncolours; ++c)
         check(ce::launch_apply_fwd(es, st.dev, st.plan.colour_ptr[c],
-                                   st.plan.colour_ptr[c + 1] - st.plan.colour_ptr[c], v, s),
+                                   st.plan.colour_ptr[c + 1] - st.plan.colour_ptr[c], st.plan.nmax, v, s),
               "apply fwd");
       check(ce::launch_level_move(st.dev, v, vn, 1, s), "level move");
     }
-    check(ce::launch_coarse_solve(F->d_coarse, F->nc, coarse, s), "coarse solve");
+    check(ce::launch_coarse_solve(F->d_coarse, F->d_cdinv, F->nc, coarse, s), "coarse solve");
     for (int l = nl - 1; l >= 0; --l) {
       const LevelStore& st = F->levels[l];
       double* v = F->d_work + F->vec_base[l];
@@ -677,7 +681,7 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev, void*
       check(ce::launch_level_move(st.dev, v, vn, 0, s), "level move");
       for (int c = st.plan.ncolours - 1; c >= 0; --c)
         check(ce::launch_apply_bwd(es, st.dev, st.plan.colour_ptr[c],
-                                   st.plan.colour_ptr[c + 1] - st.plan.colour_ptr[c], v, s),
+                                   st.plan.colour_ptr[c + 1] - st.plan.colour_ptr[c], st.plan.nmax, v, s),
               "apply bwd");
     }
     check(ce::launch_perm(F->d_perm, F->N, v0, z_dev, 0, s), "perm scatter");

@@ -9,15 +9,20 @@
 // The backward step is the transpose, in reverse order.
 #include <cuda_runtime.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace ce {
 
 namespace {
 
-constexpr int kApplyThreads = 128;
+constexpr int kApplyThreads = 256;
+constexpr int kMaxTgt = 32;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
 #pragma unroll
@@ -29,102 +34,142 @@ __device__ __forceinline__ int width_of_a(const LevelDev& L, int k, int ci) {
   return (L.colour[k] < ci) ? L.rank[k] : L.n[k];
 }
 
+// Targets of block i's W (basis of i first, then close blocks): width,
+// start of their W columns, offset of their values in the level vector and
+// the prefix of widths over the flattened column index.
+struct Targets {
+  int nt;
+  int w[kMaxTgt], pre[kMaxTgt + 1];
+  int64_t woff[kMaxTgt], voff[kMaxTgt];
+};
+
+__device__ void targets_of(const LevelDev& L, int i, int n, int r, Targets& T) {
+  const int ci = L.colour[i];
+  const int c0 = L.close_ptr[i], c1 = L.close_ptr[i + 1];
+  T.nt = min(1 + (c1 - c0), kMaxTgt);
+  T.w[0] = r;
+  T.woff[0] = 0;
+  T.voff[0] = L.vec_off[i];
+  T.pre[0] = 0;
+  int colst = n;
+  for (int t = 1; t < T.nt; ++t) {
+    const int p = L.close_blk[c0 + t - 1];
+    T.w[t] = width_of_a(L, p, ci);
+    T.woff[t] = (int64_t)n * colst;
+    T.voff[t] = L.vec_off[p];
+    colst += L.n[p];
+  }
+  for (int t = 0; t < T.nt; ++t) T.pre[t + 1] = T.pre[t] + T.w[t];
+}
+
+// Forward step of block i: y_i <- U_i^T y_i; z = L_hat^{-1} y_i[r:];
+// y_t[:w_t] -= W_t^T z for every target t (basis of i first); y_i[r:] = z.
+// U_i and L_hat_i^{-1} are staged in shared memory; the W columns of all
+// targets are spread over the CTA.
 template <typename T>
 __global__ void __launch_bounds__(kApplyThreads) apply_fwd_kernel(LevelDev L, int first, double* vec) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ double ys[kNMax], yt[kNMax], z[kNMax];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ Targets tg;
+  const int tid = threadIdx.x;
   const int i = L.order[first + blockIdx.x];
   const int n = L.n[i];
   if (n == 0) return;
-  const int r = L.rank[i], m = n - r, ci = L.colour[i];
+  const int r = L.rank[i], m = n - r;
+  T* Us = reinterpret_cast<T*>(sm_raw);
+  T* Ls = Us + n * n;
   double* v = vec + L.vec_off[i];
   const T* U = reinterpret_cast<const T*>(L.U) + L.u_off[i];
-  const T* Lh = reinterpret_cast<const T*>(L.L) + L.l_off[i];
+  const T* Li = reinterpret_cast<const T*>(L.L) + L.l_off[i];
   const T* W = reinterpret_cast<const T*>(L.W) + L.w_off[i];
+  for (int e = tid; e < n * n; e += kApplyThreads) Us[e] = U[e];
+  for (int e = tid; e < m * m; e += kApplyThreads) Ls[e] = Li[e];
   for (int a = tid; a < n; a += kApplyThreads) ys[a] = v[a];
+  if (tid == 0) targets_of(L, i, n, r, tg);
   __syncthreads();
   for (int a = tid; a < n; a += kApplyThreads) {
     double s = 0.0;
-    for (int k = 0; k < n; ++k) s += static_cast<double>(U[k * n + a]) * ys[k];
+    for (int k = 0; k < n; ++k) s += static_cast<double>(Us[k * n + a]) * ys[k];
     yt[a] = s;
   }
   __syncthreads();
-  if (warp == 0) {
-    for (int a = 0; a < m; ++a) {
-      double s = 0.0;
-      for (int k = lane; k < a; k += 32) s += static_cast<double>(Lh[a * m + k]) * z[k];
-      s = warp_sum_d(s);
-      if (lane == 0) z[a] = (yt[r + a] - s) / static_cast<double>(Lh[a * m + a]);
-      __syncwarp();
-    }
+  for (int a = tid; a < m; a += kApplyThreads) {
+    double s = 0.0;
+    for (int k = 0; k <= a; ++k) s += static_cast<double>(Ls[a * m + k]) * yt[r + k];
+    z[a] = s;
   }
   __syncthreads();
-  for (int b = tid; b < r; b += kApplyThreads) {
-    double s = yt[b];
-    for (int k = 0; k < m; ++k) s -= static_cast<double>(W[k * r + b]) * z[k];
-    v[b] = s;
-  }
   for (int a = tid; a < m; a += kApplyThreads) v[r + a] = z[a];
-  if (m == 0) return;
-  int colst = n;
-  for (int t = L.close_ptr[i]; t < L.close_ptr[i + 1]; ++t) {
-    const int p = L.close_blk[t];
-    const int w = width_of_a(L, p, ci);
-    const T* Wp = W + (int64_t)n * colst;
-    double* vp = vec + L.vec_off[p];
-    for (int c = tid; c < w; c += kApplyThreads) {
-      double s = 0.0;
-      for (int k = 0; k < m; ++k) s += static_cast<double>(Wp[k * w + c]) * z[k];
-      vp[c] -= s;
-    }
-    colst += L.n[p];
+  const int tot = tg.pre[tg.nt];
+  for (int f = tid; f < tot; f += kApplyThreads) {
+    int t = 0;
+    while (f >= tg.pre[t + 1]) ++t;
+    const int c = f - tg.pre[t], w = tg.w[t];
+    const T* Wt = W + tg.woff[t];
+    double s = 0.0;
+#pragma unroll 4
+    for (int k = 0; k < m; ++k) s += static_cast<double>(Wt[k * w + c]) * z[k];
+    if (t == 0)
+      v[c] = yt[c] - s;
+    else
+      vec[tg.voff[t] + c] -= s;
   }
 }
 
+// Backward step of block i (transpose, reverse order): rhs = z - W x_t over
+// all targets; x_n = L_hat^{-T} rhs; y_i <- U_i [x_b; x_n].
 template <typename T>
 __global__ void __launch_bounds__(kApplyThreads) apply_bwd_kernel(LevelDev L, int first, double* vec) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
   __shared__ double xf[kNMax], rhs[kNMax];
+  __shared__ double xt[kMaxTgt * kNMax];
+  __shared__ Targets tg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i = L.order[first + blockIdx.x];
   const int n = L.n[i];
   if (n == 0) return;
-  const int r = L.rank[i], m = n - r, ci = L.colour[i];
+  const int r = L.rank[i], m = n - r;
+  T* Us = reinterpret_cast<T*>(sm_raw);
+  T* Ls = Us + n * n;
   double* v = vec + L.vec_off[i];
   const T* U = reinterpret_cast<const T*>(L.U) + L.u_off[i];
-  const T* Lh = reinterpret_cast<const T*>(L.L) + L.l_off[i];
+  const T* Li = reinterpret_cast<const T*>(L.L) + L.l_off[i];
   const T* W = reinterpret_cast<const T*>(L.W) + L.w_off[i];
+  for (int e = tid; e < n * n; e += kApplyThreads) Us[e] = U[e];
+  for (int e = tid; e < m * m; e += kApplyThreads) Ls[e] = Li[e];
   for (int a = tid; a < n; a += kApplyThreads) xf[a] = v[a];   // [x_b; z]
+  if (tid == 0) targets_of(L, i, n, r, tg);
+  __syncthreads();
+  const int tot = tg.pre[tg.nt];
+  for (int f = tid; f < tot; f += kApplyThreads) {
+    int t = 0;
+    while (f >= tg.pre[t + 1]) ++t;
+    const int c = f - tg.pre[t];
+    xt[f] = (t == 0) ? xf[c] : vec[tg.voff[t] + c];
+  }
   __syncthreads();
   constexpr int nw = kApplyThreads / 32;
   for (int a = warp; a < m; a += nw) {
     double s = 0.0;
-    for (int b = lane; b < r; b += 32) s += static_cast<double>(W[a * r + b]) * xf[b];
-    int colst = n;
-    for (int t = L.close_ptr[i]; t < L.close_ptr[i + 1]; ++t) {
-      const int p = L.close_blk[t];
-      const int w = width_of_a(L, p, ci);
-      const T* Wp = W + (int64_t)n * colst;
-      const double* vp = vec + L.vec_off[p];
-      for (int c = lane; c < w; c += 32) s += static_cast<double>(Wp[a * w + c]) * vp[c];
-      colst += L.n[p];
+    for (int t = 0; t < tg.nt; ++t) {
+      const int w = tg.w[t];
+      const T* Wt = W + tg.woff[t] + (int64_t)a * w;
+      const double* x = xt + tg.pre[t];
+      for (int c = lane; c < w; c += 32) s += static_cast<double>(Wt[c]) * x[c];
     }
     s = warp_sum_d(s);
     if (lane == 0) rhs[a] = xf[r + a] - s;
   }
   __syncthreads();
-  if (warp == 0) {
-    for (int a = m - 1; a >= 0; --a) {
-      double s = 0.0;
-      for (int k = a + 1 + lane; k < m; k += 32) s += static_cast<double>(Lh[k * m + a]) * xf[r + k];
-      s = warp_sum_d(s);
-      if (lane == 0) xf[r + a] = (rhs[a] - s) / static_cast<double>(Lh[a * m + a]);
-      __syncwarp();
-    }
+  for (int a = tid; a < m; a += kApplyThreads) {
+    double s = 0.0;
+    for (int k = a; k < m; ++k) s += static_cast<double>(Ls[k * m + a]) * rhs[k];
+    xf[r + a] = s;
   }
   __syncthreads();
   for (int a = tid; a < n; a += kApplyThreads) {
     double s = 0.0;
-    for (int k = 0; k < n; ++k) s += static_cast<double>(U[a * n + k]) * xf[k];
+    for (int k = 0; k < n; ++k) s += static_cast<double>(Us[a * n + k]) * xf[k];
     v[a] = s;
   }
 }
@@ -153,58 +198,91 @@ __global__ void perm_kernel(const int32_t* perm, int64_t n, const double* in, do
   }
 }
 
-// dense lower-triangular solves with the coarse factor, one CTA
-constexpr int kCS = 1024;
+// Dense triangular solves with the coarse factor L_K (FP64), one grid of
+// CTAs cooperating through grid-wide barriers.  L_K is cut into panels of
+// kPan rows; Dinv holds the inverses of its diagonal kPan x kPan blocks, so
+// a panel is solved by CTA 0 as a small GEMV, and the remaining rows are
+// updated by all CTAs.
 constexpr int kPan = 64;
+constexpr int kCS = 256;
 
-__global__ void __launch_bounds__(kCS) coarse_solve_kernel(const double* Lc, int n, double* yg) {
-  extern __shared__ double y[];
+__global__ void __launch_bounds__(kCS) coarse_solve_kernel(const double* Lc, const double* Dinv, int n,
+                                                           double* y) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double yp[kPan], yq[kPan];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int nw = kCS / 32;
-  for (int a = tid; a < n; a += kCS) y[a] = yg[a];
-  __syncthreads();
+  const int gw = blockIdx.x * (kCS / 32) + warp, nwarps = gridDim.x * (kCS / 32);
+  const int npan = (n + kPan - 1) / kPan;
   // forward: L y = b
-  for (int s0 = 0; s0 < n; s0 += kPan) {
-    const int pe = min(n, s0 + kPan);
-    if (warp == 0) {
-      for (int a = s0; a < pe; ++a) {
+  for (int p = 0; p < npan; ++p) {
+    const int s0 = p * kPan, pe = min(n, s0 + kPan), h = pe - s0;
+    if (blockIdx.x == 0) {
+      for (int a = tid; a < h; a += kCS) yp[a] = y[s0 + a];
+      __syncthreads();
+      const double* D = Dinv + (size_t)p * kPan * kPan;
+      for (int a = tid; a < h; a += kCS) {
         double s = 0.0;
-        for (int k = s0 + lane; k < a; k += 32) s += Lc[(int64_t)a * n + k] * y[k];
-        s = warp_sum_d(s);
-        if (lane == 0) y[a] = (y[a] - s) / Lc[(int64_t)a * n + a];
-        __syncwarp();
+        for (int k = 0; k <= a; ++k) s += D[a * kPan + k] * yp[k];
+        yq[a] = s;
       }
+      __syncthreads();
+      for (int a = tid; a < h; a += kCS) y[s0 + a] = yq[a];
     }
-    __syncthreads();
-    for (int a = pe + warp; a < n; a += nw) {
+    grid.sync();
+    for (int a = pe + gw; a < n; a += nwarps) {
       double s = 0.0;
       for (int k = s0 + lane; k < pe; k += 32) s += Lc[(int64_t)a * n + k] * y[k];
       s = warp_sum_d(s);
       if (lane == 0) y[a] -= s;
     }
-    __syncthreads();
+    grid.sync();
   }
   // backward: L^T x = y
-  for (int pe = n; pe > 0; pe -= kPan) {
-    const int s0 = max(0, pe - kPan);
-    if (warp == 0) {
-      for (int a = pe - 1; a >= s0; --a) {
+  const int gt = blockIdx.x * kCS + tid, nthr = gridDim.x * kCS;
+  for (int p = npan - 1; p >= 0; --p) {
+    const int s0 = p * kPan, pe = min(n, s0 + kPan), h = pe - s0;
+    if (blockIdx.x == 0) {
+      for (int a = tid; a < h; a += kCS) yp[a] = y[s0 + a];
+      __syncthreads();
+      const double* D = Dinv + (size_t)p * kPan * kPan;
+      for (int a = tid; a < h; a += kCS) {
         double s = 0.0;
-        for (int k = a + 1 + lane; k < pe; k += 32) s += Lc[(int64_t)k * n + a] * y[k];
-        s = warp_sum_d(s);
-        if (lane == 0) y[a] = (y[a] - s) / Lc[(int64_t)a * n + a];
-        __syncwarp();
+        for (int k = a; k < h; ++k) s += D[k * kPan + a] * yp[k];
+        yq[a] = s;
       }
+      __syncthreads();
+      for (int a = tid; a < h; a += kCS) y[s0 + a] = yq[a];
     }
-    __syncthreads();
-    for (int c = tid; c < s0; c += kCS) {
+    grid.sync();
+    for (int c = gt; c < s0; c += nthr) {
       double s = 0.0;
       for (int a = s0; a < pe; ++a) s += Lc[(int64_t)a * n + c] * y[a];
       y[c] -= s;
     }
-    __syncthreads();
+    grid.sync();
   }
-  for (int a = tid; a < n; a += kCS) yg[a] = y[a];
+}
+
+// Inverses of the diagonal kPan x kPan blocks of L_K (one CTA per block,
+// one column of the inverse per thread).
+__global__ void __launch_bounds__(kPan) coarse_dinv_kernel(const double* Lc, int n, double* Dinv) {
+  __shared__ double Lb[kPan * (kPan + 1)];
+  const int p = blockIdx.x, s0 = p * kPan, h = min(n, s0 + kPan) - s0;
+  for (int e = threadIdx.x; e < h * h; e += kPan) {
+    int a = e / h, b = e - a * h;
+    Lb[a * (kPan + 1) + b] = Lc[(int64_t)(s0 + a) * n + s0 + b];
+  }
+  __syncthreads();
+  double* D = Dinv + (size_t)p * kPan * kPan;
+  const int j = threadIdx.x;
+  for (int a = 0; a < kPan; ++a) D[a * kPan + j] = 0.0;
+  if (j < h) {
+    for (int a = j; a < h; ++a) {
+      double x = (a == j) ? 1.0 : 0.0;
+      for (int k = j; k < a; ++k) x -= Lb[a * (kPan + 1) + k] * D[k * kPan + j];
+      D[a * kPan + j] = x / Lb[a * (kPan + 1) + a];
+    }
+  }
 }
 
 // ---------------- PCG building blocks -----------------------------------
@@ -290,29 +368,38 @@ __global__ void pcg_scalars_kernel(double* scal, int stage) {
 }
 
 template <typename T>
-cudaError_t apply_launch(const LevelDev& L, int first, int count, double* vec, cudaStream_t s,
-                         bool fwd) {
+cudaError_t apply_launch(const LevelDev& L, int first, int count, int nmax, double* vec,
+                         cudaStream_t s, bool fwd) {
   if (count <= 0) return cudaSuccess;
+  const size_t smem = 2 * sizeof(T) * (size_t)nmax * nmax;
+  static size_t attr_f = 0, attr_b = 0;
+  size_t& attr = fwd ? attr_f : attr_b;
+  if (smem > 40 * 1024 && smem > attr) {
+    cudaError_t e = fwd ? cudaFuncSetAttribute(apply_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+                        : cudaFuncSetAttribute(apply_bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = smem;
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (fwd)
-    apply_fwd_kernel<T><<<count, kApplyThreads, 0, s>>>(L, first, vec);
+    apply_fwd_kernel<T><<<count, kApplyThreads, smem, s>>>(L, first, vec);
   else
-    apply_bwd_kernel<T><<<count, kApplyThreads, 0, s>>>(L, first, vec);
+    apply_bwd_kernel<T><<<count, kApplyThreads, smem, s>>>(L, first, vec);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_apply_fwd(int esize, const LevelDev& L, int first, int count, double* vec,
+cudaError_t launch_apply_fwd(int esize, const LevelDev& L, int first, int count, int nmax, double* vec,
                              cudaStream_t s) {
-  return esize == 8 ? apply_launch<double>(L, first, count, vec, s, true)
-                    : apply_launch<float>(L, first, count, vec, s, true);
+  return esize == 8 ? apply_launch<double>(L, first, count, nmax, vec, s, true)
+                    : apply_launch<float>(L, first, count, nmax, vec, s, true);
 }
 
-cudaError_t launch_apply_bwd(int esize, const LevelDev& L, int first, int count, double* vec,
+cudaError_t launch_apply_bwd(int esize, const LevelDev& L, int first, int count, int nmax, double* vec,
                              cudaStream_t s) {
-  return esize == 8 ? apply_launch<double>(L, first, count, vec, s, false)
-                    : apply_launch<float>(L, first, count, vec, s, false);
+  return esize == 8 ? apply_launch<double>(L, first, count, nmax, vec, s, false)
+                    : apply_launch<float>(L, first, count, nmax, vec, s, false);
 }
 
 cudaError_t launch_level_move(const LevelDev& L, double* cur, double* next, int forward,
@@ -332,19 +419,28 @@ cudaError_t launch_perm(const int32_t* perm, int64_t n, const double* in, double
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_solve(const double* Lc, int n, double* y, cudaStream_t s) {
+cudaError_t launch_coarse_dinv(const double* Lc, int n, double* Dinv, cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * static_cast<size_t>(n);
-  static int attr_set = 0;
-  if (smem > 48 * 1024 && smem > static_cast<size_t>(attr_set)) {
-    cudaError_t e = cudaFuncSetAttribute(coarse_solve_kernel,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = static_cast<int>(smem);
-  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  coarse_solve_kernel<<<1, kCS, smem, s>>>(Lc, n, y);
+  coarse_dinv_kernel<<<(n + kPan - 1) / kPan, kPan, 0, s>>>(Lc, n, Dinv);
   return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_solve(const double* Lc, const double* Dinv, int n, double* y, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  static int grid = 0;
+  if (grid == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_solve_kernel, kCS, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorCooperativeLaunchTooLarge;
+    grid = sms;
+  }
+  void* args[] = {(void*)&Lc, (void*)&Dinv, (void*)&n, (void*)&y};
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaLaunchCooperativeKernel((const void*)coarse_solve_kernel, dim3(grid), dim3(kCS), args, 0, s);
 }
 
 cudaError_t launch_spmv_dot(int64_t n, const int64_t* rowptr, const int32_t* col,

@@ -97,8 +97,8 @@ struct LevelDev {
   double* tau;          // per block
   double* sigma;        // sum n_i (vec layout)
   void* pool;           // pair values (T)
-  void* U;              // factor (T)
-  void* L;
+  void* U;              // factor (T): U_i
+  void* L;              //   L_hat_i^{-1} (m_i x m_i, lower)
   void* W;
 };
 
@@ -136,6 +136,7 @@ struct ce_factor {
   std::vector<ce::LevelStore> levels;
   int nc = 0;                   // coarse size
   double* d_coarse = nullptr;   // nc x nc lower Cholesky factor (FP64)
+  double* d_cdinv = nullptr;    // inverses of its 64 x 64 diagonal blocks
   int64_t* d_cgdst = nullptr;   // unused placeholder
   int32_t* d_perm = nullptr;    // borrowed from the csb
   double* d_work = nullptr;     // level vectors (FP64) + coarse vector

@@ -33,15 +33,16 @@ cudaError_t launch_copy_tasks(int esize_src, int esize_dst, const CopyTask* task
 cudaError_t coarse_cholesky(double* A, int n, int level, int* status, cudaStream_t s);
 
 // apply (x = Q^T L^{-T} L^{-1} Q r)
-cudaError_t launch_apply_fwd(int esize, const LevelDev& L, int first, int count, double* vec,
+cudaError_t launch_apply_fwd(int esize, const LevelDev& L, int first, int count, int nmax, double* vec,
                              cudaStream_t s);
-cudaError_t launch_apply_bwd(int esize, const LevelDev& L, int first, int count, double* vec,
+cudaError_t launch_apply_bwd(int esize, const LevelDev& L, int first, int count, int nmax, double* vec,
                              cudaStream_t s);
 cudaError_t launch_level_move(const LevelDev& L, double* cur, double* next, int forward,
                               cudaStream_t s);
 cudaError_t launch_perm(const int32_t* perm, int64_t n, const double* in, double* out, int gather,
                         cudaStream_t s);
-cudaError_t launch_coarse_solve(const double* Lc, int n, double* y, cudaStream_t s);
+cudaError_t launch_coarse_dinv(const double* Lc, int n, double* Dinv, cudaStream_t s);
+cudaError_t launch_coarse_solve(const double* Lc, const double* Dinv, int n, double* y, cudaStream_t s);
 
 // PCG building blocks (FP64)
 cudaError_t launch_spmv_dot(int64_t n, const int64_t* rowptr, const int32_t* col,

@@ -535,12 +535,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
   __syncthreads();
   for (int k = tid; k < m; k += NT) Tn[k * LD + k] = sqrt(Tn[k * LD + k]);
   __syncthreads();
-  T* Lg = reinterpret_cast<T*>(L.L) + L.l_off[i];
-  for (int e = tid; e < m * m; e += NT) {
-    int a = e / m, b = e - a * m;
-    Lg[e] = (b <= a) ? Tn[a * LD + b] : T(0);
-  }
-  // Li = L_hat^{-1} (lower), one column per thread
+  // Li = L_hat^{-1} (lower), one column per thread; the factor keeps Li
   for (int j = tid; j < m; j += NT) {
     for (int a = 0; a < j; ++a) Li[a * LD + j] = T(0);
     for (int a = j; a < m; ++a) {
@@ -550,6 +545,11 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
     }
   }
   __syncthreads();
+  T* Lg = reinterpret_cast<T*>(L.L) + L.l_off[i];
+  for (int e = tid; e < m * m; e += NT) {
+    int a = e / m, b = e - a * m;
+    Lg[e] = (b <= a) ? Li[a * LD + b] : T(0);
+  }
   // W_b = L_hat^{-1} Tm[r:, :r] -> Y[0:m, 0:r], then back into Tm[r:, :r]
   cta_gemm<T, NT>(m, r, m, [&](int a, int k) { return Li[a * LD + k]; },
               [&](int k, int b) { return Tm[(r + k) * LD + b]; },
