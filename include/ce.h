@@ -49,6 +49,14 @@ enum {
   CE_TOL_ABS = 1  /* tau_i = tol                                           */
 };
 
+/* How the compression step finds U_i and r_i. */
+enum {
+  CE_RANK_SVD = 0,     /* exact: Householder R of F_i^T + one-sided Jacobi SVD     */
+  CE_RANK_LEARNED = 1  /* MLP-predicted width r_hat, randomized range finder of
+                          width r_hat + oversample, a-posteriori check, exact SVD
+                          for rows that fail it                                    */
+};
+
 /* Arithmetic of the factorization. */
 enum {
   CE_PREC_FP64 = 0, /* blocks, compression and elimination in FP64       */
@@ -63,6 +71,11 @@ typedef struct {
   int precision;   /* CE_PREC_*                                          */
   int coloring;    /* 1: colour-major order (default); 0: natural order  */
   void* stream;    /* cudaStream_t for all device work                   */
+  int rank_mode;   /* CE_RANK_SVD (default) / CE_RANK_LEARNED            */
+  const void* rank_model; /* device, ce_mlp_nparams() FP16 values from
+                             ce_mlp_pack (CE_RANK_LEARNED only)          */
+  int oversample;  /* p, sketch columns beyond r_hat (default 8)         */
+  uint64_t seed;   /* key of the sketch's counter-based Gaussians        */
 } ce_opts;
 
 typedef struct {
@@ -85,6 +98,8 @@ typedef struct {
   double level_flops[16];
   double level_bytes[16];
   double coarse_ms;    /* dense assembly + Cholesky of A_K               */
+  int learned_rows[16];  /* CE_RANK_LEARNED: rows whose sketch was accepted */
+  int fallback_rows[16]; /* ... and rows sent to the exact SVD             */
 } ce_info;
 
 typedef struct {
@@ -93,7 +108,8 @@ typedef struct {
   int converged;       /* 1 if relres <= rtol                             */
 } ce_pcg_info;
 
-/* Defaults: tol 1e-4, CE_TOL_REL, levels 4, J 4, FP64, colouring on. */
+/* Defaults: tol 1e-4, CE_TOL_REL, levels 4, J 4, FP64, colouring on,
+ * CE_RANK_SVD, oversample 8, seed 0. */
 void ce_opts_default(ce_opts* o);
 
 /*
@@ -192,6 +208,35 @@ ce_status pcg_solve_noalloc(const ce_csb* A, const ce_factor* F,
 /* Release a handle (NULL is ignored). */
 void ce_csb_destroy(ce_csb* A);
 void ce_factor_destroy(ce_factor* F);
+
+/*
+ * Rank predictor for the compression step.  The paper always runs a full
+ * SVD there; its conclusion names a cheaper rank-revealing factorization as
+ * the way to cut the time spent in it (Section 6).
+ * A 3-layer MLP (ce_mlp_nfeatures() -> 64 -> 64 -> 1, ReLU, sigmoid) maps the
+ * per-row features of the compression step to r_i / n_i.  Parameters are a
+ * flat FP32 device array of ce_mlp_nparams() values: W1 (64 x nfeat,
+ * row-major), b1 (64), W2 (64 x 64), b2 (64), w3 (64), b3 (1).
+ *   ce_mlp_init     He-normal weights from a counter-based generator, zero
+ *                   biases
+ *   ce_mlp_grad     full-batch gradient of 0.5 mean (y - t)^2 (deterministic)
+ *   ce_mlp_train    `steps` Adam steps (lr) on the full batch; allocates its
+ *                   optimizer state; *loss_out (host, optional) = final loss
+ *   ce_mlp_pack     FP32 parameters -> FP16 model for ce_opts.rank_model
+ *   ce_mlp_predict  FP16 inference, out[s] = prediction for row s of X
+ * X is ns x nfeat row-major (device), t has ns targets (device).
+ */
+int ce_mlp_nparams(void);
+int ce_mlp_nfeatures(void);
+ce_status ce_mlp_init(float* theta_dev, uint64_t seed, void* stream);
+ce_status ce_mlp_grad(const float* X_dev, const float* t_dev, int ns,
+                      const float* theta_dev, float* grad_dev, void* stream);
+ce_status ce_mlp_train(const float* X_dev, const float* t_dev, int ns,
+                       float* theta_dev, int steps, float lr, double* loss_out,
+                       void* stream);
+ce_status ce_mlp_pack(const float* theta_dev, void* model_dev, void* stream);
+ce_status ce_mlp_predict(const float* X_dev, int ns, const void* model_dev,
+                         float* out_dev, void* stream);
 
 /* Number of kernels the library has launched so far (process-wide). */
 int64_t ce_launch_count(void);

@@ -132,6 +132,7 @@ class BlockStep:
     Lhat: np.ndarray       # (n-r) x (n-r) lower Cholesky factor of S_ii
     targets: list          # [(t, W_t)]: t == i is the basis of i, else close t
     far: list              # far blocks whose columns formed F_i (non-empty)
+    features: np.ndarray = None  # rank-predictor features (block_features)
 
 
 @dataclasses.dataclass
@@ -167,6 +168,38 @@ class Factor:
 # --------------------------------------------------------------------------
 # Algorithm 2: one level of compression and elimination
 # --------------------------------------------------------------------------
+NFEAT = 11
+
+
+def _lg(x):
+    return np.log10(max(x, 1e-30)) / 10.0
+
+
+def block_features(level, n, J, D, C_blocks, F_blocks, tol):
+    """Cheap features of block row i when it is processed (rank predictor).
+
+    Computed from the row before compression: level, size, Frobenius norms of
+    the diagonal block D_i, of the close part C_i and of the far part F_i
+    (with the largest and mean far-block norms), the numbers of close and of
+    non-empty far blocks, the number of far columns, the mean rank of the J
+    children the block was joined from (0 on the first level) and the
+    tolerance.  Ratios are taken to ||D_i||_F so the features are scale free.
+    """
+    dn = np.linalg.norm(D)
+    cn = np.sqrt(sum(np.linalg.norm(X) ** 2 for X in C_blocks))
+    fb = [np.linalg.norm(X) for X in F_blocks if X.shape[1] > 0]
+    fn = np.sqrt(sum(v * v for v in fb))
+    mF = sum(X.shape[1] for X in F_blocks)
+    fmax = max(fb) if fb else 0.0
+    fmean = (sum(fb) / len(fb)) if fb else 0.0
+    d = dn if dn > 0 else 1.0
+    f = fn if fn > 0 else 1.0
+    parent = (n / J) if level > 0 else 0.0
+    return np.array([level / 4.0, n / 64.0, _lg(cn / d), _lg(fn / d), _lg(fmax / f),
+                     _lg(fmean / f), len(C_blocks) / 8.0, len(fb) / 16.0, parent / 32.0,
+                     mF / (16.0 * max(n, 1)), -np.log10(max(tol, 1e-30)) / 8.0])
+
+
 def _random_orthogonal(rng, k):
     if k == 0:
         return np.zeros((0, 0))
@@ -175,7 +208,7 @@ def _random_orthogonal(rng, k):
 
 
 def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
-               rotate_rng=None, shuffle_rng=None):
+               rotate_rng=None, shuffle_rng=None, J=4):
     M = len(sizes)
     size = list(sizes)
     close = _block_graph(S, M)          # level-start pattern = close blocks
@@ -198,6 +231,8 @@ def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
         # -- compression step (Section 2.2, eq. rreav) ----------------------
         far = sorted(k for k in nbr[i] if k not in close[i] and size[k] > 0)
         Fs = [_get(S, i, k) for k in far]
+        feats = block_features(level_no, n, J, _get(S, i, i),
+                               [_get(S, i, k) for k in sorted(close[i] - {i})], Fs, tol)
         F = np.hstack(Fs) if Fs else np.zeros((n, 0))
         if F.shape[1] == 0 or n == 0 or not np.any(F):
             U = np.eye(n)
@@ -257,7 +292,7 @@ def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
                     nbr[t].add(s)
                 _put(S, s, t, _get(S, s, t) - (upd if s != t else 0.5 * (upd + upd.T)))
         steps.append(BlockStep(i, n, r, sig, tau, U, Lh,
-                               [(t, W[t]) for t in targets], far))
+                               [(t, W[t]) for t in targets], far, feats))
     return S, size, colour, order, steps, ranks
 
 
@@ -352,7 +387,7 @@ def factorize(A, perm, B, tol, levels, J=4, tol_mode="rel", order="colour",
         sizes_start = list(sizes)
         pairs = sorted(S.keys())
         S, size, colour, order_, steps, ranks = _one_level(
-            S, sizes, tol, tol_mode, order, lev, rotate_rng, shuffle_rng)
+            S, sizes, tol, tol_mode, order, lev, rotate_rng, shuffle_rng, J)
         recs.append(Level(pairs, sizes_start, colour, order_, steps, J, ranks))
         S, sizes = _coarsen(S, size, J)
     Ac = _dense_from_blocks(S, sizes)

@@ -23,6 +23,8 @@ from ._lib import (  # noqa: F401
     CE_OK,
     CE_PREC_FP32,
     CE_PREC_FP64,
+    CE_RANK_LEARNED,
+    CE_RANK_SVD,
     CE_TOL_ABS,
     CE_TOL_REL,
 )
@@ -160,8 +162,12 @@ def csb_build(A, perm, B: int) -> CSB:
 
 
 def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",
-                 coloring=True, stream=None) -> Factor:
-    """Algorithm 1 on the device; returns the factor (raises CEError)."""
+                 coloring=True, stream=None, rank_model=None, oversample=8, seed=0) -> Factor:
+    """Algorithm 1 on the device; returns the factor (raises CEError).
+
+    ``rank_model`` (a :class:`RankModel`) switches the compression step to the
+    learned rank + randomized range finder with exact-SVD fallback.
+    """
     lib = _lib.load()
     o = _lib.ce_opts()
     lib.ce_opts_default(C.byref(o))
@@ -172,6 +178,11 @@ def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="
     o.precision = CE_PREC_FP64 if precision == "fp64" else CE_PREC_FP32
     o.coloring = 1 if coloring else 0
     o.stream = _stream_ptr(stream)
+    if rank_model is not None:
+        o.rank_mode = CE_RANK_LEARNED
+        o.rank_model = C.c_void_p(rank_model.model.data_ptr())
+        o.oversample = int(oversample)
+        o.seed = int(seed)
     info = _lib.ce_info()
     h = C.c_void_p()
     st = lib.ce_factorize(csb.handle, C.byref(o), C.byref(h), C.byref(info))
@@ -204,3 +215,78 @@ def pcg_solve(csb: CSB, F: Factor, b, x, rtol=1e-8, maxit=1000, stream=None, che
     if check and st not in (CE_OK, CE_ERR_NO_CONVERGENCE):
         raise CEError(st, "pcg_solve")
     return info.iters, info.relres, bool(info.converged)
+
+
+class RankModel:
+    """The rank-predictor MLP on the device: FP32 parameters + FP16 model."""
+
+    def __init__(self, seed=0, device="cuda"):
+        import torch
+        lib = _lib.load()
+        self.nparams = lib.ce_mlp_nparams()
+        self.nfeatures = lib.ce_mlp_nfeatures()
+        self.theta = torch.empty(self.nparams, dtype=torch.float32, device=device)
+        self.model = torch.empty(self.nparams, dtype=torch.float16, device=device)
+        _check(lib.ce_mlp_init(C.c_void_p(self.theta.data_ptr()), int(seed), _stream_ptr(None)),
+               "ce_mlp_init")
+        self.pack()
+
+    def set_params(self, theta):
+        import torch
+        self.theta.copy_(torch.as_tensor(np.asarray(theta, dtype=np.float32)))
+        self.pack()
+
+    def pack(self):
+        _check(_lib.load().ce_mlp_pack(C.c_void_p(self.theta.data_ptr()),
+                                       C.c_void_p(self.model.data_ptr()), _stream_ptr(None)),
+               "ce_mlp_pack")
+
+    def grad(self, X, t):
+        """Full-batch gradient of 0.5 mean (y - t)^2 (FP32, device)."""
+        import torch
+        Xd = torch.as_tensor(np.ascontiguousarray(X, np.float32), device=self.theta.device)
+        td = torch.as_tensor(np.ascontiguousarray(t, np.float32), device=self.theta.device)
+        g = torch.empty_like(self.theta)
+        _check(_lib.load().ce_mlp_grad(C.c_void_p(Xd.data_ptr()), C.c_void_p(td.data_ptr()),
+                                       Xd.shape[0], C.c_void_p(self.theta.data_ptr()),
+                                       C.c_void_p(g.data_ptr()), _stream_ptr(None)), "ce_mlp_grad")
+        return g
+
+    def train(self, X, t, steps=2000, lr=3e-3):
+        """Adam on the full batch; returns the final loss of the FP16 model."""
+        import torch
+        Xd = torch.as_tensor(np.ascontiguousarray(X, np.float32), device=self.theta.device)
+        td = torch.as_tensor(np.ascontiguousarray(t, np.float32), device=self.theta.device)
+        loss = C.c_double(0.0)
+        _check(_lib.load().ce_mlp_train(C.c_void_p(Xd.data_ptr()), C.c_void_p(td.data_ptr()),
+                                        Xd.shape[0], C.c_void_p(self.theta.data_ptr()), int(steps),
+                                        float(lr), C.byref(loss), _stream_ptr(None)), "ce_mlp_train")
+        self.pack()
+        return loss.value
+
+    def predict(self, X):
+        """FP16 inference (the code the compression step runs)."""
+        import torch
+        Xd = torch.as_tensor(np.ascontiguousarray(X, np.float32), device=self.theta.device)
+        out = torch.empty(Xd.shape[0], dtype=torch.float32, device=self.theta.device)
+        _check(_lib.load().ce_mlp_predict(C.c_void_p(Xd.data_ptr()), Xd.shape[0],
+                                          C.c_void_p(self.model.data_ptr()),
+                                          C.c_void_p(out.data_ptr()), _stream_ptr(None)),
+               "ce_mlp_predict")
+        return out
+
+
+def rank_training_data():
+    """(features, r/n) training set written from the oracle's ranks."""
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "models", "rank_train.npz")
+    d = np.load(path)
+    return d["X"], d["t"]
+
+
+def trained_rank_model(steps=3000, lr=3e-3, seed=0):
+    """Rank model trained on the GPU on the stored training set."""
+    X, t = rank_training_data()
+    m = RankModel(seed=seed)
+    m.loss = m.train(X, t, steps=steps, lr=lr)
+    return m

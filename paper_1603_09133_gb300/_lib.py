@@ -22,6 +22,8 @@ CE_TOL_REL = 0
 CE_TOL_ABS = 1
 CE_PREC_FP64 = 0
 CE_PREC_FP32 = 1
+CE_RANK_SVD = 0
+CE_RANK_LEARNED = 1
 
 
 class ce_opts(C.Structure):
@@ -33,6 +35,10 @@ class ce_opts(C.Structure):
         ("precision", C.c_int),
         ("coloring", C.c_int),
         ("stream", C.c_void_p),
+        ("rank_mode", C.c_int),
+        ("rank_model", C.c_void_p),
+        ("oversample", C.c_int),
+        ("seed", C.c_uint64),
     ]
 
 
@@ -53,6 +59,8 @@ class ce_info(C.Structure):
         ("level_flops", C.c_double * 16),
         ("level_bytes", C.c_double * 16),
         ("coarse_ms", C.c_double),
+        ("learned_rows", C.c_int * 16),
+        ("fallback_rows", C.c_int * 16),
     ]
 
 
@@ -65,6 +73,7 @@ PP = C.POINTER(C.c_void_p)
 I64P = C.POINTER(C.c_int64)
 I32P = C.POINTER(C.c_int32)
 DP = C.POINTER(C.c_double)
+FP = C.c_void_p
 
 # name -> (restype, argtypes); every extern "C" function of include/ce.h
 SIGNATURES = {
@@ -81,6 +90,13 @@ SIGNATURES = {
     "ce_strerror": (C.c_char_p, [C.c_int]),
     "ce_last_error": (C.c_char_p, []),
     "ce_launch_count": (C.c_int64, []),
+    "ce_mlp_nparams": (C.c_int, []),
+    "ce_mlp_nfeatures": (C.c_int, []),
+    "ce_mlp_init": (C.c_int, [FP, C.c_uint64, P]),
+    "ce_mlp_grad": (C.c_int, [P, P, C.c_int, P, P, P]),
+    "ce_mlp_train": (C.c_int, [P, P, C.c_int, P, C.c_int, C.c_float, DP, P]),
+    "ce_mlp_pack": (C.c_int, [P, P, P]),
+    "ce_mlp_predict": (C.c_int, [P, C.c_int, P, P, P]),
     "ce_factor_levels": (C.c_int, [P]),
     "ce_factor_level_size": (C.c_int, [P, C.c_int]),
     "ce_factor_get_level": (C.c_int, [P, C.c_int, I32P, I32P, I32P, DP]),

@@ -10,6 +10,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "mlp_infer.cuh"
 
 using ce::CopyTask;
 using ce::LevelDev;
@@ -285,6 +286,10 @@ void ce_opts_default(ce_opts* o) {
   o->precision = CE_PREC_FP64;
   o->coloring = 1;
   o->stream = nullptr;
+  o->rank_mode = CE_RANK_SVD;
+  o->rank_model = nullptr;
+  o->oversample = 8;
+  o->seed = 0;
 }
 
 const char* ce_strerror(ce_status s) {
@@ -303,6 +308,94 @@ const char* ce_strerror(ce_status s) {
 const char* ce_last_error(void) { return g_last_error.c_str(); }
 
 int64_t ce_launch_count(void) { return ce::g_launches.load(); }
+
+int ce_mlp_nparams(void) { return ce::kMlpParams; }
+int ce_mlp_nfeatures(void) { return ce::kMlpFeatures; }
+
+ce_status ce_mlp_init(float* theta_dev, uint64_t seed, void* stream) {
+  if (!theta_dev) return CE_ERR_INVALID_ARG;
+  try {
+    check(ce::mlp_init(theta_dev, seed, static_cast<cudaStream_t>(stream)), "mlp init");
+  } catch (const CudaFail& f) {
+    return status_of(f);
+  }
+  return CE_OK;
+}
+
+ce_status ce_mlp_grad(const float* X_dev, const float* t_dev, int ns, const float* theta_dev,
+                      float* grad_dev, void* stream) {
+  if (!X_dev || !t_dev || !theta_dev || !grad_dev || ns <= 0) return CE_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float* part = nullptr;
+  ce_status ret = CE_OK;
+  try {
+    part = static_cast<float*>(dalloc((size_t)ce::mlp_partial_blocks(ns) * ce::kMlpParams * 4, s));
+    check(ce::mlp_grad(X_dev, t_dev, ns, theta_dev, part, grad_dev, s), "mlp grad");
+  } catch (const CudaFail& f) {
+    ret = status_of(f);
+  }
+  dfree(part, s);
+  return ret;
+}
+
+ce_status ce_mlp_train(const float* X_dev, const float* t_dev, int ns, float* theta_dev, int steps,
+                       float lr, double* loss_out, void* stream) {
+  if (!X_dev || !t_dev || !theta_dev || ns <= 0 || steps < 0 || !(lr > 0.f)) return CE_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  float *part = nullptr, *m = nullptr, *v = nullptr, *pred = nullptr;
+  ce_status ret = CE_OK;
+  try {
+    part = static_cast<float*>(dalloc((size_t)ce::mlp_partial_blocks(ns) * ce::kMlpParams * 4, s));
+    m = static_cast<float*>(dalloc(ce::kMlpParams * 4, s));
+    v = static_cast<float*>(dalloc(ce::kMlpParams * 4, s));
+    check(cudaMemsetAsync(m, 0, ce::kMlpParams * 4, s), "memset");
+    check(cudaMemsetAsync(v, 0, ce::kMlpParams * 4, s), "memset");
+    for (int it = 1; it <= steps; ++it)
+      check(ce::mlp_adam_step(X_dev, t_dev, ns, theta_dev, part, m, v, lr, it, s), "mlp adam");
+    if (loss_out) {
+      // loss of the FP32 parameters through the FP16 model the row kernel uses
+      void* model = dalloc((size_t)ce::kMlpParams * 2, s);
+      pred = static_cast<float*>(dalloc((size_t)ns * 4, s));
+      check(ce::mlp_pack(theta_dev, model, s), "mlp pack");
+      check(ce::mlp_predict(X_dev, ns, model, pred, s), "mlp predict");
+      std::vector<float> hp(ns), ht(ns);
+      check(cudaMemcpyAsync(hp.data(), pred, ns * 4, cudaMemcpyDeviceToHost, s), "D2H");
+      check(cudaMemcpyAsync(ht.data(), t_dev, ns * 4, cudaMemcpyDeviceToHost, s), "D2H");
+      check(cudaStreamSynchronize(s), "sync");
+      double acc = 0;
+      for (int k = 0; k < ns; ++k) acc += 0.5 * double(hp[k] - ht[k]) * double(hp[k] - ht[k]);
+      *loss_out = acc / ns;
+      dfree(model, s);
+    }
+  } catch (const CudaFail& f) {
+    ret = status_of(f);
+  }
+  dfree(part, s);
+  dfree(m, s);
+  dfree(v, s);
+  dfree(pred, s);
+  return ret;
+}
+
+ce_status ce_mlp_pack(const float* theta_dev, void* model_dev, void* stream) {
+  if (!theta_dev || !model_dev) return CE_ERR_INVALID_ARG;
+  try {
+    check(ce::mlp_pack(theta_dev, model_dev, static_cast<cudaStream_t>(stream)), "mlp pack");
+  } catch (const CudaFail& f) {
+    return status_of(f);
+  }
+  return CE_OK;
+}
+
+ce_status ce_mlp_predict(const float* X_dev, int ns, const void* model_dev, float* out_dev, void* stream) {
+  if (!X_dev || !model_dev || !out_dev || ns < 0) return CE_ERR_INVALID_ARG;
+  try {
+    check(ce::mlp_predict(X_dev, ns, model_dev, out_dev, static_cast<cudaStream_t>(stream)), "mlp predict");
+  } catch (const CudaFail& f) {
+    return status_of(f);
+  }
+  return CE_OK;
+}
 
 ce_status csb_build(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
                     const int32_t* perm, int32_t B, ce_csb** out) {
@@ -458,7 +551,9 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
   ce_opts_default(&o);
   if (o_in) o = *o_in;
   if (o.levels < 0 || o.J < 1 || o.tol < 0 || (o.precision != CE_PREC_FP64 && o.precision != CE_PREC_FP32) ||
-      (o.tol_mode != CE_TOL_REL && o.tol_mode != CE_TOL_ABS))
+      (o.tol_mode != CE_TOL_REL && o.tol_mode != CE_TOL_ABS) ||
+      (o.rank_mode != CE_RANK_SVD && o.rank_mode != CE_RANK_LEARNED) ||
+      (o.rank_mode == CE_RANK_LEARNED && (!o.rank_model || o.oversample < 0)))
     return CE_ERR_INVALID_ARG;
   *out = nullptr;
   if (info) std::memset(info, 0, sizeof(*info));
@@ -474,8 +569,14 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
   void* pool = nullptr;
   ce_status ret = CE_OK;
   try {
-    F->d_status = static_cast<int*>(dalloc(ce::kStatusWords * sizeof(int), s));
-    check(cudaMemsetAsync(F->d_status, 0, ce::kStatusWords * sizeof(int), s), "memset");
+    F->d_status = static_cast<int*>(dalloc((ce::kStatusWords + 32) * sizeof(int), s));
+    check(cudaMemsetAsync(F->d_status, 0, (ce::kStatusWords + 32) * sizeof(int), s), "memset");
+    ce::LearnedArgs la;
+    if (o.rank_mode == CE_RANK_LEARNED) la.model = static_cast<const __half*>(o.rank_model);
+    la.oversample = o.oversample;
+    la.J = o.J;
+    la.seed = o.seed;
+    la.stats = F->d_status + ce::kStatusWords;
     LevelPlan cur;
     if (o.coloring) {
       cur = A->plan1;
@@ -508,7 +609,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       for (int c = 0; c < P.ncolours; ++c)
         check(ce::launch_row_kernel(es, st.dev, P.colour_ptr[c], P.colour_ptr[c + 1] - P.colour_ptr[c], l,
                                     o.tol, o.tol_mode, F->d_status, P.nmax,
-                                    P.colour_ptr[c + 1] - P.colour_ptr[c], s),
+                                    P.colour_ptr[c + 1] - P.colour_ptr[c], la, s),
               "row kernel");
       check(cudaEventRecord(ev1, s), "event");
       st.rank.resize(P.M);
@@ -602,7 +703,13 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       int64_t bytes = (int64_t)F->nc * F->nc * 8 + tot * 8;
       for (auto& st : F->levels) bytes += st.fac_bytes + st.meta_bytes;
       F->bytes = bytes;
+      int lstat[32];
+      check(cudaMemcpy(lstat, F->d_status + ce::kStatusWords, sizeof(lstat), cudaMemcpyDeviceToHost), "D2H");
       if (info) {
+        for (int l = 0; l < 16; ++l) {
+          info->learned_rows[l] = lstat[2 * l];
+          info->fallback_rows[l] = lstat[2 * l + 1];
+        }
         info->levels_done = (int)F->levels.size();
         info->coarse_n = F->nc;
         info->factor_bytes = bytes;

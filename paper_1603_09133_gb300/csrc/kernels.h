@@ -1,6 +1,7 @@
 // Launch wrappers of the CE kernels (defined in factor_kernels.cu and
 // apply_kernels.cu).  All launches are asynchronous on `s`.
 #pragma once
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "ce_internal.h"
@@ -21,11 +22,20 @@ void set_last_error(const std::string& msg);
 // [6..7] = pivot value (double bits)
 constexpr int kStatusWords = 8;
 
+// learned compression (randomized range finder with an MLP-predicted width)
+struct LearnedArgs {
+  const __half* model = nullptr;  // FP16 rank model; null: exact SVD for every row
+  int oversample = 8;             // p: sketch width k = r_hat + p
+  int J = 4;                      // children per super-block (parent-rank feature)
+  unsigned long long seed = 0;    // key of the counter-based sketch generator
+  int* stats = nullptr;           // per level: [rows accepted, rows sent to the exact SVD]
+};
+
 size_t row_kernel_smem(int esize);
 // busy_ctas: rows in the launch (sets the shared-memory budget per CTA)
 cudaError_t launch_row_kernel(int esize, const LevelDev& L, int first, int count, int level,
                               double tol, int tol_mode, int* status, int nmax, int busy_ctas,
-                              cudaStream_t s);
+                              const LearnedArgs& la, cudaStream_t s);
 cudaError_t launch_scatter_csr(int esize, const int64_t* scatter, const double* val, int64_t nnz,
                                void* pool, cudaStream_t s);
 cudaError_t launch_copy_tasks(int esize_src, int esize_dst, const CopyTask* tasks, int ntasks,
@@ -54,6 +64,16 @@ cudaError_t launch_reduce(const double* partial, int nparts, double* out, cudaSt
 // scal[0]=rz, scal[1]=pAp, ... see apply_kernels.cu
 cudaError_t launch_update_xr(int64_t n, double* x, double* r, const double* p, const double* Ap,
                              const double* scal, double* partial, int nparts, cudaStream_t s);
+// rank-predictor MLP (mlp.cu)
+cudaError_t mlp_init(float* theta, unsigned long long seed, cudaStream_t s);
+cudaError_t mlp_grad(const float* X, const float* t, int ns, const float* theta, float* partial,
+                     float* grad, cudaStream_t s);
+cudaError_t mlp_adam_step(const float* X, const float* t, int ns, float* theta, float* partial,
+                          float* m, float* v, float lr, int step, cudaStream_t s);
+int mlp_partial_blocks(int ns);
+cudaError_t mlp_pack(const float* theta, void* model, cudaStream_t s);
+cudaError_t mlp_predict(const float* X, int ns, const void* model, float* out, cudaStream_t s);
+
 cudaError_t launch_update_p(int64_t n, double* p, const double* z, const double* scal,
                             int first, cudaStream_t s);
 cudaError_t launch_pcg_scalars(double* scal, int stage, cudaStream_t s);

@@ -22,6 +22,8 @@
 #include <algorithm>
 
 #include "kernels.h"
+#include "mlp_infer.cuh"
+#include "rng.cuh"
 
 namespace ce {
 
@@ -233,7 +235,7 @@ __device__ void store_row_tile(const T* sm, T* X, int i, int k, int n, int nk, i
 template <typename T, int NT>
 __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
     ce_row_kernel(LevelDev L, int first, int level, double tol, int tol_mode, int* status, int nmax,
-                  int LD, int QW) {
+                  int LD, int QW, LearnedArgs la) {
   constexpr int kWarpsNT = NT / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NL = nmax * LD;
@@ -256,6 +258,10 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
   __shared__ int s_colst[kMaxTargets], s_tgt[kMaxTargets], s_w[kMaxTargets];
   __shared__ int s_fw[kMaxFar + 1], s_fpre[kMaxFar + 1], s_fk[kMaxFar];
   __shared__ int64_t s_foff[kMaxFar];
+  __shared__ float s_bn2[kMaxFar + kMaxTargets];   // block norms^2 (features)
+  __shared__ float s_x[kMlpFeatures], s_h[kMlpHidden];
+  __shared__ int s_k, s_rowf[kChunk], s_rowq[kChunk];
+  __shared__ T s_tq[64], s_probe[2];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i = L.order[first + blockIdx.x];
@@ -304,10 +310,408 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
   __syncthreads();
   const int mF = s_fpre[nf];
 
-  // ---------------- A. R factor of F_i^T (warp TSQR + tree merge) ----------
   int r = 0;
   double tau = 0.0;
-  if (mF > 0) {
+  bool have_u = false;
+  double dn2_all = 0.0;
+  for (int w = 0; w < kWarpsNT; ++w) dn2_all += s_red[w];
+  const double floor_all = static_cast<double>(Eps<T>::v) * sqrt(dn2_all);
+
+  // ---------------- L. learned rank + randomized range finder --------------
+  // Features -> FP16 MLP -> r_hat; sketch width k = r_hat + p.  Y = F [O | w1 w2]
+  // with Gaussian O (n x k) and two probe columns; Q = orth(Y[:, :k])
+  // (Householder, the probes carried along give ||(I - Q Q^T) F w||); TSQR
+  // of the rows of F^T Q and Jacobi on the k x k factor give the singular
+  // values and vectors of Q^T F.  Accepted when the sketch is not saturated
+  // (r < k) and the probe estimate of the out-of-sketch residual is at most
+  // tau / 2; otherwise the exact phases A-B run.
+  if (mF > 0 && la.model != nullptr) {
+    const int cc0 = L.close_ptr[i], nclose = L.close_ptr[i + 1] - cc0;
+    for (int f = warp; f < nf + nclose; f += kWarpsNT) {
+      int k, w;
+      const T* Xg;
+      if (f < nf) {
+        k = s_fk[f];
+        w = s_fw[f];
+        Xg = pool + s_foff[f];
+      } else {
+        k = L.close_blk[cc0 + f - nf];
+        w = width_of(L, k, ci);
+        Xg = pool + L.close_off[cc0 + f - nf];
+      }
+      const int nk = L.n[k];
+      float ss = 0.f;
+      for (int e = lane; e < n * w; e += 32) {
+        const int a = e / w, b = e - a * w;
+        const float v = static_cast<float>((i < k) ? Xg[(int64_t)a * nk + b] : Xg[(int64_t)b * n + a]);
+        ss += v * v;
+      }
+      ss = warp_sum(ss);
+      if (lane == 0) s_bn2[f] = ss;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      float cn2 = 0.f, fn2 = 0.f, fmax = 0.f, fsum = 0.f;
+      int nfl = 0;
+      for (int f = 0; f < nf; ++f)
+        if (s_fw[f] > 0) {
+          const float v = sqrtf(s_bn2[f]);
+          fn2 += s_bn2[f];
+          fmax = fmaxf(fmax, v);
+          fsum += v;
+          ++nfl;
+        }
+      for (int c = 0; c < nclose; ++c) cn2 += s_bn2[nf + c];
+      const float dn = static_cast<float>(sqrt(dn2_all)), fn = sqrtf(fn2), cn = sqrtf(cn2);
+      const float d = dn > 0.f ? dn : 1.f, fv = fn > 0.f ? fn : 1.f;
+      auto lg = [](float x) { return log10f(fmaxf(x, 1e-30f)) / 10.f; };
+      s_x[0] = level / 4.f;
+      s_x[1] = n / 64.f;
+      s_x[2] = lg(cn / d);
+      s_x[3] = lg(fn / d);
+      s_x[4] = lg(fmax / fv);
+      s_x[5] = lg((nfl ? fsum / nfl : 0.f) / fv);
+      s_x[6] = nclose / 8.f;
+      s_x[7] = nfl / 16.f;
+      s_x[8] = (level > 0 ? float(n) / la.J : 0.f) / 32.f;
+      s_x[9] = mF / (16.f * n);
+      s_x[10] = -log10f(fmaxf(static_cast<float>(tol), 1e-30f)) / 8.f;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      const float yh = mlp_infer_warp(la.model, s_x, s_h);
+      if (lane == 0) {
+        int rh = static_cast<int>(ceilf(yh * n));
+        rh = max(1, min(n, rh));
+        s_k = min(n, rh + la.oversample);
+      }
+    }
+    __syncthreads();
+    const int k = s_k;
+    const int kk = k + 2;
+    const int UNE = max(QW * per_warp, 4 * NL);          // union size (elements)
+    const int pwl = NL + 2 * kChunk * LD + 64;           // per warp: R, rows of F^T, projected rows
+    const int qwl = min(QW, (UNE - NL) / pwl);
+    if (4 * k <= 3 * n && qwl >= 1 && kk <= LD && k <= 2 * kChunk && NL + 2 * kChunk * LD <= UNE) {
+      T* Q = un;                 // n x kk (columns k, k+1: probes)
+      T* Cs = un + NL;           // 32 x LD rows of F^T
+      T* Om = Cs + kChunk * LD;  // 32 x kk
+      for (int e = tid; e < n * LD; e += NT) Q[e] = T(0);
+      __syncthreads();
+      for (int g0 = 0; g0 < mF; g0 += kChunk) {
+        const int rows = min(kChunk, mF - g0);
+        if (tid < rows) {
+          const int g = g0 + tid;
+          int f = 0;
+          while (f + 1 < nf && s_fpre[f + 1] <= g) ++f;
+          s_rowf[tid] = f;
+          s_rowq[tid] = g - s_fpre[f];
+        }
+        for (int e = tid; e < rows * kk; e += NT) {
+          const int q = e / kk, c = e - q * kk;
+          Om[q * kk + c] = static_cast<T>(gauss_from_key(sketch_key(la.seed, level, i, g0 + q, c)));
+        }
+        __syncthreads();
+        for (int e = tid; e < rows * n; e += NT) {
+          const int q = e / n, a = e - q * n;
+          const int f = s_rowf[q], k2 = s_fk[f], qq = s_rowq[q];
+          const T* Xg = pool + s_foff[f];
+          Cs[q * LD + a] = (i < k2) ? Xg[(int64_t)a * L.n[k2] + qq] : Xg[(int64_t)qq * n + a];
+        }
+        __syncthreads();
+        for (int e = tid; e < n * kk; e += NT) {
+          const int a = e / kk, c = e - a * kk;
+          T acc = Q[a * LD + c];
+          for (int q = 0; q < rows; ++q) acc += Cs[q * LD + a] * Om[q * kk + c];
+          Q[a * LD + c] = acc;
+        }
+        __syncthreads();
+      }
+      // Householder QR of Q[:, :k], applied to the probe columns as well
+      for (int j = 0; j < k; ++j) {
+        if (warp == 0) {
+          const T xl = (j + 1 + lane < n) ? Q[(j + 1 + lane) * LD + j] : T(0);
+          const T xh = (j + 33 + lane < n) ? Q[(j + 33 + lane) * LD + j] : T(0);
+          T beta, tq, sc;
+          const bool ok = reflector(Q[j * LD + j], xl, xh, beta, tq, sc);
+          if (ok) {
+            if (j + 1 + lane < n) Q[(j + 1 + lane) * LD + j] = xl * sc;
+            if (j + 33 + lane < n) Q[(j + 33 + lane) * LD + j] = xh * sc;
+          }
+          __syncwarp();
+          if (lane == 0) {
+            s_tq[j] = ok ? tq : T(0);
+            if (ok) Q[j * LD + j] = beta;
+          }
+        }
+        __syncthreads();
+        const T tq = s_tq[j];
+        if (tq != T(0)) {
+          for (int l = j + 1 + warp; l < kk; l += kWarpsNT) {
+            T d = 0;
+            for (int a = j + 1 + lane; a < n; a += 32) d += Q[a * LD + j] * Q[a * LD + l];
+            d = warp_sum(d);
+            d = (d + Q[j * LD + l]) * tq;
+            if (lane == 0) Q[j * LD + l] -= d;
+            for (int a = j + 1 + lane; a < n; a += 32) Q[a * LD + l] -= d * Q[a * LD + j];
+          }
+        }
+        __syncthreads();
+      }
+      if (warp < 2) {   // ||(I - Q Q^T) F w|| = norm of rows k.. of H^T (F w)
+        T sres = 0;
+        for (int a = k + lane; a < n; a += 32) sres += Q[a * LD + k + warp] * Q[a * LD + k + warp];
+        sres = warp_sum(sres);
+        if (lane == 0) s_probe[warp] = sqrt(sres);
+      }
+      // explicit Q (n x k) into Cs: H_0 ... H_{k-1} [I; 0]
+      T* Qx = Cs;   // n x LD (uses the Cs/Om space, NL >= n * LD)
+      for (int e = tid; e < n * k; e += NT) {
+        const int a = e / k, c = e - a * k;
+        Qx[a * LD + c] = (a == c) ? T(1) : T(0);
+      }
+      __syncthreads();
+      for (int j = k - 1; j >= 0; --j) {
+        const T tq = s_tq[j];
+        if (tq != T(0)) {
+          for (int l = j + warp; l < k; l += kWarpsNT) {
+            T d = 0;
+            for (int a = j + 1 + lane; a < n; a += 32) d += Q[a * LD + j] * Qx[a * LD + l];
+            d = warp_sum(d);
+            d = (d + Qx[j * LD + l]) * tq;
+            if (lane == 0) Qx[j * LD + l] -= d;
+            for (int a = j + 1 + lane; a < n; a += 32) Qx[a * LD + l] -= d * Q[a * LD + j];
+          }
+        }
+        __syncthreads();
+      }
+      for (int e = tid; e < n * LD; e += NT) Q[e] = Qx[e];   // Q <- explicit basis
+      __syncthreads();
+      // TSQR of the rows of F^T Q (k columns), one R per warp, tree merge
+      const int nchunks = (mF + kChunk - 1) / kChunk;
+      const int qw = min(qwl, nchunks);
+      T* wbase = un + NL;
+      if (warp < qw) {
+        T* Rw = wbase + warp * pwl;
+        T* Cw = Rw + NL;
+        T* Pw = Cw + kChunk * LD;
+        T* vb = Pw + kChunk * LD;
+        for (int e = lane; e < k * LD; e += 32) Rw[e] = T(0);
+        for (int c = warp; c < nchunks; c += qw) {
+          const int g0 = c * kChunk;
+          const int rows = min(kChunk, mF - g0);
+          int f = 0;
+          while (f + 1 < nf && s_fpre[f + 1] <= g0) ++f;
+          int q = g0 - s_fpre[f];
+          for (int rr = 0; rr < rows; ++rr) {
+            while (q >= s_fw[f]) {
+              ++f;
+              q = 0;
+            }
+            const int k2 = s_fk[f];
+            const T* Xg = pool + s_foff[f];
+            if (i < k2) {
+              const int nk = L.n[k2];
+              for (int a = lane; a < n; a += 32) Cw[rr * LD + a] = Xg[(int64_t)a * nk + q];
+            } else {
+              for (int a = lane; a < n; a += 32) Cw[rr * LD + a] = Xg[(int64_t)q * n + a];
+            }
+            ++q;
+          }
+          __syncwarp();
+          for (int e = lane; e < rows * k; e += 32) {
+            const int q2 = e / k, cc = e - q2 * k;
+            T acc = 0;
+            for (int a = 0; a < n; ++a) acc += Cw[q2 * LD + a] * Q[a * LD + cc];
+            Pw[q2 * LD + cc] = acc;
+          }
+          __syncwarp();
+          warp_qr_stack(Rw, Pw, vb, k, rows, LD);
+        }
+      }
+      __syncthreads();
+      for (int step = 1; step < qw; step *= 2) {
+        if (warp % (2 * step) == 0 && warp + step < qw) {
+          T* Ra = wbase + warp * pwl;
+          T* Rb = wbase + (warp + step) * pwl;
+          warp_qr_merge(Ra, Rb, Ra + NL + 2 * kChunk * LD, k, LD);
+        }
+        __syncthreads();
+      }
+      // one-sided Jacobi on the k x k factor R (= wbase), V in Vb
+      T* Xr = wbase;
+      T* Vb = wbase + NL;    // warp 0's row buffers (64 rows of LD), free now
+      for (int e = tid; e < k * k; e += NT) {
+        const int a = e / k, b = e - a * k;
+        Vb[a * LD + b] = (a == b) ? T(1) : T(0);
+      }
+      __syncthreads();
+      {
+        const int nb = k + (k & 1), npairs = nb / 2;
+        const int half = lane >> 4, hl = lane & 15;
+        const T tolJ = T(k) * Eps<T>::v, tolJ2 = tolJ * tolJ;
+        for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+          if (tid == 0) s_flag = 0;
+          __syncthreads();
+          for (int rnd = 0; rnd < nb - 1; ++rnd) {
+            for (int tb = warp * 2; tb < npairs; tb += NT / 16) {
+              const int t = tb + half;
+              int p = nb - 1, q = rnd;
+              if (t != 0) {
+                p = rnd + t;
+                if (p >= nb - 1) p -= nb - 1;
+                q = rnd - t;
+                if (q < 0) q += nb - 1;
+              }
+              const bool valid = t < npairs && p < k && q < k;
+              T a = 0, b = 0, g = 0;
+              if (valid) {
+                for (int row = hl; row < k; row += 16) {
+                  T xp = Xr[row * LD + p], xq = Xr[row * LD + q];
+                  a += xp * xp;
+                  b += xq * xq;
+                  g += xp * xq;
+                }
+              }
+              a = half_sum(a);
+              b = half_sum(b);
+              g = half_sum(g);
+              if (valid && g != T(0) && g * g > tolJ2 * a * b) {
+                const T zeta = (b - a) * fast_rcp(T(2) * g);
+                const T az = fabs(zeta);
+                const T den = (az > T(1)) ? az * (T(1) + sqrt(T(1) + fast_rcp(az * az)))
+                                          : az + sqrt(T(1) + az * az);
+                const T tt = ((zeta >= T(0)) ? T(1) : T(-1)) * fast_rcp(den);
+                const T cs = fast_rsqrt(T(1) + tt * tt), sn = cs * tt;
+                for (int row = hl; row < k; row += 16) {
+                  T xp = Xr[row * LD + p], xq = Xr[row * LD + q];
+                  Xr[row * LD + p] = cs * xp - sn * xq;
+                  Xr[row * LD + q] = sn * xp + cs * xq;
+                  T vp = Vb[row * LD + p], vq = Vb[row * LD + q];
+                  Vb[row * LD + p] = cs * vp - sn * vq;
+                  Vb[row * LD + q] = sn * vp + cs * vq;
+                }
+                if (hl == 0) s_flag = 1;
+              }
+            }
+            __syncthreads();
+          }
+          const int rotated = s_flag;
+          __syncthreads();
+          if (!rotated) break;
+        }
+      }
+      for (int j = tid; j < k; j += NT) {
+        T sv = 0;
+        for (int row = 0; row < k; ++row) sv += Xr[row * LD + j] * Xr[row * LD + j];
+        sig_tmp[j] = sqrt(sv);
+      }
+      __syncthreads();
+      for (int j = tid; j < k; j += NT) {
+        const T sj = sig_tmp[j];
+        int pos = 0;
+        for (int kq = 0; kq < k; ++kq) pos += (sig_tmp[kq] > sj) || (sig_tmp[kq] == sj && kq < j);
+        s_pos[j] = pos;
+        sig[pos] = sj;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        const double smax = static_cast<double>(sig[0]);
+        double tt = (tol == 0.0) ? n * static_cast<double>(Eps<T>::v) * smax
+                                 : ((tol_mode == CE_TOL_ABS) ? tol : tol * smax);
+        tt = fmax(tt, floor_all);
+        int rr = 0;
+        for (int kq = 0; kq < k; ++kq) rr += (static_cast<double>(sig[kq]) > tt) ? 1 : 0;
+        const double pr = fmax(static_cast<double>(s_probe[0]), static_cast<double>(s_probe[1]));
+        const bool ok = isfinite(smax) && rr < k && pr <= 0.5 * tt;
+        s_flag = ok ? rr : -1;
+        sig_tmp[0] = static_cast<T>(tt);
+      }
+      __syncthreads();
+      const int rl = s_flag;
+      if (rl >= 0) {
+        // U_b = Q V_B(:, sorted first rl)  ->  U[:, :rl]
+        for (int e = tid; e < n * rl; e += NT) {
+          const int a = e / rl, c = e - a * rl;
+          int j = 0;
+          while (s_pos[j] != c) ++j;
+          T acc = 0;
+          for (int q = 0; q < k; ++q) acc += Q[a * LD + q] * Vb[q * LD + j];
+          U[a * LD + c] = acc;
+        }
+        __syncthreads();
+        // complete U_b to an orthogonal U: Householder QR of U[:, :rl] and
+        // U = H_0 ... H_{rl-1} (its first rl columns span U_b)
+        for (int j = 0; j < rl; ++j) {
+          if (warp == 0) {
+            const T xl = (j + 1 + lane < n) ? U[(j + 1 + lane) * LD + j] : T(0);
+            const T xh = (j + 33 + lane < n) ? U[(j + 33 + lane) * LD + j] : T(0);
+            T beta, tq, sc;
+            const bool okr = reflector(U[j * LD + j], xl, xh, beta, tq, sc);
+            if (okr) {
+              if (j + 1 + lane < n) U[(j + 1 + lane) * LD + j] = xl * sc;
+              if (j + 33 + lane < n) U[(j + 33 + lane) * LD + j] = xh * sc;
+            }
+            __syncwarp();
+            if (lane == 0) {
+              s_tq[j] = okr ? tq : T(0);
+              if (okr) U[j * LD + j] = beta;
+            }
+          }
+          __syncthreads();
+          const T tq = s_tq[j];
+          if (tq != T(0)) {
+            for (int l = j + 1 + warp; l < rl; l += kWarpsNT) {
+              T d = 0;
+              for (int a = j + 1 + lane; a < n; a += 32) d += U[a * LD + j] * U[a * LD + l];
+              d = warp_sum(d);
+              d = (d + U[j * LD + l]) * tq;
+              if (lane == 0) U[j * LD + l] -= d;
+              for (int a = j + 1 + lane; a < n; a += 32) U[a * LD + l] -= d * U[a * LD + j];
+            }
+          }
+          __syncthreads();
+        }
+        T* Uf = Cs;   // n x n accumulation of the reflectors
+        for (int e = tid; e < n * n; e += NT) {
+          const int a = e / n, c = e - a * n;
+          Uf[a * LD + c] = (a == c) ? T(1) : T(0);
+        }
+        __syncthreads();
+        for (int j = rl - 1; j >= 0; --j) {
+          const T tq = s_tq[j];
+          if (tq != T(0)) {
+            for (int l = j + warp; l < n; l += kWarpsNT) {
+              T d = 0;
+              for (int a = j + 1 + lane; a < n; a += 32) d += U[a * LD + j] * Uf[a * LD + l];
+              d = warp_sum(d);
+              d = (d + Uf[j * LD + l]) * tq;
+              if (lane == 0) Uf[j * LD + l] -= d;
+              for (int a = j + 1 + lane; a < n; a += 32) Uf[a * LD + l] -= d * U[a * LD + j];
+            }
+          }
+          __syncthreads();
+        }
+        for (int e = tid; e < n * n; e += NT) {
+          const int a = e / n, c = e - a * n;
+          U[a * LD + c] = Uf[a * LD + c];
+        }
+        for (int j = k + tid; j < n; j += NT) sig[j] = T(0);
+        r = rl;
+        tau = static_cast<double>(sig_tmp[0]);
+        have_u = true;
+        if (tid == 0 && la.stats) atomicAdd(la.stats + 2 * level, 1);
+      } else if (tid == 0 && la.stats) {
+        atomicAdd(la.stats + 2 * level + 1, 1);
+      }
+      __syncthreads();
+    } else if (tid == 0 && la.stats) {
+      atomicAdd(la.stats + 2 * level + 1, 1);
+    }
+  }
+
+  // ---------------- A. R factor of F_i^T (warp TSQR + tree merge) ----------
+  if (mF > 0 && !have_u) {
     const int nchunks = (mF + kChunk - 1) / kChunk;
     const int qw = min(QW, nchunks);
     if (warp < qw) {
@@ -477,7 +881,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
     }
     __syncthreads();
     r = s_flag;
-  } else {
+  } else if (mF == 0) {
     for (int e = tid; e < n * n; e += NT) {
       int a = e / n, b = e - a * n;
       U[a * LD + b] = (a == b) ? T(1) : T(0);
@@ -678,7 +1082,7 @@ cudaError_t max_dyn_smem(size_t* out) {
 
 template <typename T, int NT>
 cudaError_t launch_nt(const LevelDev& L, int first, int count, int level, double tol, int tol_mode,
-                      int* status, int nmax, size_t budget, cudaStream_t s) {
+                      int* status, int nmax, size_t budget, const LearnedArgs& la, cudaStream_t s) {
   const int LD = choose_ld(nmax);
   size_t limit = 0;
   cudaError_t e = max_dyn_smem<T, NT>(&limit);
@@ -689,7 +1093,7 @@ cudaError_t launch_nt(const LevelDev& L, int first, int count, int level, double
   const size_t smem = smem_bytes(sizeof(T), nmax, LD, QW);
   if (smem > limit) return cudaErrorInvalidValue;
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  ce_row_kernel<T, NT><<<count, NT, smem, s>>>(L, first, level, tol, tol_mode, status, nmax, LD, QW);
+  ce_row_kernel<T, NT><<<count, NT, smem, s>>>(L, first, level, tol, tol_mode, status, nmax, LD, QW, la);
   return cudaGetLastError();
 }
 
@@ -699,17 +1103,17 @@ size_t row_kernel_smem(int esize) { return smem_bytes(esize, kNMax, choose_ld(kN
 
 cudaError_t launch_row_kernel(int esize, const LevelDev& L, int first, int count, int level,
                               double tol, int tol_mode, int* status, int nmax, int busy_ctas,
-                              cudaStream_t s) {
+                              const LearnedArgs& la, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   nmax = std::max(nmax, 1);
   // many rows in the colour: 256-thread CTAs, about 3 per SM; few rows: one
   // 512-thread CTA per SM with the whole shared memory
   const bool busy = busy_ctas >= 2 * 152;
   if (esize == 8)
-    return busy ? launch_nt<double, 256>(L, first, count, level, tol, tol_mode, status, nmax, 72 * 1024, s)
-                : launch_nt<double, 512>(L, first, count, level, tol, tol_mode, status, nmax, ~size_t(0), s);
-  return busy ? launch_nt<float, 256>(L, first, count, level, tol, tol_mode, status, nmax, 72 * 1024, s)
-              : launch_nt<float, 512>(L, first, count, level, tol, tol_mode, status, nmax, ~size_t(0), s);
+    return busy ? launch_nt<double, 256>(L, first, count, level, tol, tol_mode, status, nmax, 72 * 1024, la, s)
+                : launch_nt<double, 512>(L, first, count, level, tol, tol_mode, status, nmax, ~size_t(0), la, s);
+  return busy ? launch_nt<float, 256>(L, first, count, level, tol, tol_mode, status, nmax, 72 * 1024, la, s)
+              : launch_nt<float, 512>(L, first, count, level, tol, tol_mode, status, nmax, ~size_t(0), la, s);
 }
 
 }  // namespace ce
