@@ -3,8 +3,10 @@
 
 One step = ce_factorize + pcg_solve of the 2D Poisson 512x512 system (B = 32,
 tol 1e-4, 4 levels, J = 4) with the matrix and right-hand side resident in
-HBM.  The chosen form (FP32 blocks and compression, FP64 PCG) is the headline
-value; the plain FP64 form is timed beside it.  Prints one JSON line.
+HBM.  The chosen form (learned ranks with a randomized range finder, FP32
+blocks and compression, FP64 PCG) is the headline value; the plain FP64 form
+(exact SVD) is timed beside it.  The rank model is trained on the GPU before
+the timed region.  Prints one JSON line.
 
     python bench.py [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -43,6 +45,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    p.add_argument("--ranks", default="learned", choices=["learned", "svd"])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--no-baseline", action="store_true", help="skip the oracle timing")
     return p.parse_args()
@@ -171,15 +174,16 @@ def run_ours(args, rank, world):
     x = torch.zeros_like(b)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
+    model = ceg.trained_rank_model() if args.ranks == "learned" else None
 
-    def step(prec):
-        F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision=prec)
+    def step(prec, rm=None):
+        F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision=prec, rank_model=rm)
         it, rel, conv = ceg.pcg_solve(csb, F, b, x, RTOL, 1000)
         return F, it, rel, conv
 
-    def timed(prec, k, w_):
+    def timed(prec, k, w_, rm=None):
         for _ in range(w_):
-            step(prec)
+            step(prec, rm)
         times, last = [], None
         if world > 1:
             torch.distributed.barrier()
@@ -190,7 +194,7 @@ def run_ours(args, rank, world):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            last = step(prec)
+            last = step(prec, rm)
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
@@ -199,12 +203,11 @@ def run_ours(args, rank, world):
             torch.distributed.barrier()
         return times, last, launches
 
-    # plain FP64 form (the comparison) and the chosen form
-    other = "fp64" if args.precision == "fp32" else "fp32"
-    t_other, last_other, _ = timed(other, max(1, args.steps // 2), 1)
+    # plain FP64 form with exact SVDs (the comparison) and the chosen form
+    t_other, last_other, _ = timed("fp64", max(1, args.steps // 2), 1)
     sampler = ClockSampler(dev.index)
     sampler.start()
-    times, last, launches = timed(args.precision, args.steps, args.warmup)
+    times, last, launches = timed(args.precision, args.steps, args.warmup, model)
     clocks = sampler.stop()
     F, it, rel, conv = last
     xt = x.cpu().numpy()
@@ -245,7 +248,8 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         csb2 = ceg.csb_build(A, pm, w.B)
-        F2 = ceg.ce_factorize(csb2, tol=w.tol, levels=w.levels, J=w.J, precision=args.precision)
+        F2 = ceg.ce_factorize(csb2, tol=w.tol, levels=w.levels, J=w.J, precision=args.precision,
+                              rank_model=model)
         bd = b_host.to(dev, non_blocking=True)
         xd = torch.empty_like(bd)
         ceg.pcg_solve(csb2, F2, bd, xd, RTOL, 1000)
@@ -274,10 +278,13 @@ def run_ours(args, rank, world):
            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
            "config": {"workload": args.workload, "desc": w.desc, "N": int(N), "B": w.B,
                       "tol": w.tol, "levels": w.levels, "J": w.J,
-                      "form": f"{args.precision} factor + fp64 PCG",
+                      "form": f"{args.ranks} ranks + {args.precision} factor + fp64 PCG",
                       "pcg_iters": it, "final_relres": true_rel,
-                      f"{other}_form_s": statistics.mean(t_other) / 1e3,
-                      f"{other}_form_pcg_iters": last_other[1],
+                      "plain_fp64_form_s": statistics.mean(t_other) / 1e3,
+                      "plain_fp64_form_pcg_iters": last_other[1],
+                      "learned_rows": [info.learned_rows[l] for l in range(info.levels_done)],
+                      "fallback_rows": [info.fallback_rows[l] for l in range(info.levels_done)],
+                      "rank_model_train_loss": getattr(model, "loss", None),
                       "l2": "256 MB buffer written between timed steps",
                       "parallelism": "replicas" if world > 1 else "single GPU",
                       "levels_detail": levels_cfg},

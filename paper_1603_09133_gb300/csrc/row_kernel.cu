@@ -71,11 +71,6 @@ __device__ __forceinline__ T warp_max(T v) {
   return v;
 }
 
-__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
-__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
-__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
-__device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
-
 template <typename T>
 __device__ __forceinline__ T half_sum(T v) {  // sum over the 16 lanes of a half warp
 #pragma unroll
@@ -98,6 +93,11 @@ __device__ void set_status(int* status, int code, int level, int block, int reas
   }
 }
 
+__device__ __forceinline__ float fast_rcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double fast_rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float fast_rsqrt(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double fast_rsqrt(double x) { return rsqrt(x); }
+
 // Householder reflector of the column x = [x0; c] (c held as c_lo, c_hi by
 // each lane for rows lane and lane + 32), unit-leading form H = I - tau v v^T,
 // v = [1; sc c], beta = -sign(x0) ||x||.  Columns whose largest entry is
@@ -106,14 +106,16 @@ template <typename T>
 __device__ __forceinline__ bool reflector(T x0, T c_lo, T c_hi, T& beta, T& tau, T& sc) {
   T amax = warp_max(fmax(fabs(c_lo), fabs(c_hi)));
   if (!(amax >= Tiny<T>::v)) return false;
-  const T xl = c_lo / amax, xh = c_hi / amax;
+  const T ia = fast_rcp(amax);
+  const T xl = c_lo * ia, xh = c_hi * ia;
   const T s = warp_sum(xl * xl + xh * xh);
   const T a = fmax(amax, fabs(x0));
-  const T x0a = x0 / a, ca = amax / a;
+  const T ra = fast_rcp(a);
+  const T x0a = x0 * ra, ca = amax * ra;
   const T nrm = a * sqrt(x0a * x0a + s * ca * ca);
   beta = (x0 >= T(0)) ? -nrm : nrm;
-  tau = (beta - x0) / beta;
-  sc = T(1) / (x0 - beta);
+  tau = (beta - x0) * fast_rcp(beta);
+  sc = fast_rcp(x0 - beta);
   return true;
 }
 
@@ -130,15 +132,19 @@ __device__ void warp_qr_stack(T* R, T* C, T* vb, int n, int rows, int LD) {
     __syncwarp();
     if (lane == 0) R[j * LD + j] = beta;
     for (int l = j + 1 + lane; l < n; l += 32) {
-      T d0 = R[j * LD + l], d1 = 0;
+      T d0 = R[j * LD + l], d1 = 0, d2 = 0, d3 = 0;
       int q = 0;
-      for (; q + 1 < rows; q += 2) {
+#pragma unroll 2
+      for (; q + 3 < rows; q += 4) {
         d0 += vb[q] * C[q * LD + l];
         d1 += vb[q + 1] * C[(q + 1) * LD + l];
+        d2 += vb[q + 2] * C[(q + 2) * LD + l];
+        d3 += vb[q + 3] * C[(q + 3) * LD + l];
       }
-      if (q < rows) d0 += vb[q] * C[q * LD + l];
-      const T d = (d0 + d1) * tau;
+      for (; q < rows; ++q) d0 += vb[q] * C[q * LD + l];
+      const T d = ((d0 + d1) + (d2 + d3)) * tau;
       R[j * LD + l] -= d;
+#pragma unroll 8
       for (q = 0; q < rows; ++q) C[q * LD + l] -= d * vb[q];
     }
     __syncwarp();
@@ -161,19 +167,51 @@ __device__ void warp_qr_merge(T* Ra, T* Rb, T* vb, int n, int LD) {
     if (lane == 0) Ra[j * LD + j] = beta;
     const int rows = j + 1;
     for (int l = j + 1 + lane; l < n; l += 32) {
-      T d0 = Ra[j * LD + l], d1 = 0;
+      T d0 = Ra[j * LD + l], d1 = 0, d2 = 0, d3 = 0;
       int q = 0;
-      for (; q + 1 < rows; q += 2) {
+#pragma unroll 2
+      for (; q + 3 < rows; q += 4) {
         d0 += vb[q] * Rb[q * LD + l];
         d1 += vb[q + 1] * Rb[(q + 1) * LD + l];
+        d2 += vb[q + 2] * Rb[(q + 2) * LD + l];
+        d3 += vb[q + 3] * Rb[(q + 3) * LD + l];
       }
-      if (q < rows) d0 += vb[q] * Rb[q * LD + l];
-      const T d = (d0 + d1) * tau;
+      for (; q < rows; ++q) d0 += vb[q] * Rb[q * LD + l];
+      const T d = ((d0 + d1) + (d2 + d3)) * tau;
       Ra[j * LD + l] -= d;
+#pragma unroll 8
       for (q = 0; q < rows; ++q) Rb[q * LD + l] -= d * vb[q];
     }
     __syncwarp();
   }
+}
+
+// Rows g0 .. g0+rows-1 of F_i^T (rows <= 32) -> C (row-major, ldc) by one warp.
+// Lane q first finds the far block and the offset of row g0 + q, so the
+// element loads that follow are independent of each other.
+template <typename T>
+__device__ __forceinline__ void warp_load_far_rows(T* C, int ldc, const T* pool, const LevelDev& L, int i,
+                                                   int n, int g0, int rows, int nf, const int* fpre,
+                                                   const int* fk, const int64_t* foff, int* wf, int* wq) {
+  const int lane = threadIdx.x & 31;
+  if (lane < rows) {
+    const int g = g0 + lane;
+    int lo = 0, hi = nf - 1;          // last f with fpre[f] <= g (skips empty blocks)
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (fpre[mid] <= g) lo = mid; else hi = mid - 1;
+    }
+    wf[lane] = lo;
+    wq[lane] = g - fpre[lo];
+  }
+  __syncwarp();
+  for (int e = lane; e < rows * n; e += 32) {
+    const int q = e / n, a = e - q * n;
+    const int f = wf[q], k = fk[f], qq = wq[q];
+    const T* Xg = pool + foff[f];
+    C[q * ldc + a] = (i < k) ? Xg[(int64_t)a * L.n[k] + qq] : Xg[(int64_t)qq * n + a];
+  }
+  __syncwarp();
 }
 
 // out(a, b) op= sum_k A(a, k) B(k, b), a < M, b < N, k < K; 2 x 2 register
@@ -185,6 +223,7 @@ __device__ __forceinline__ void cta_gemm(int M, int N, int K, FA A, FB B, FS sto
     const int a0 = (t / tn) * 2, b0 = (t % tn) * 2;
     const bool a1 = a0 + 1 < M, b1 = b0 + 1 < N;
     T c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+#pragma unroll 4
     for (int k = 0; k < K; ++k) {
       const T x0 = A(a0, k), x1 = a1 ? A(a0 + 1, k) : T(0);
       const T y0 = B(k, b0), y1 = b1 ? B(k, b0 + 1) : T(0);
@@ -261,6 +300,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
   __shared__ float s_bn2[kMaxFar + kMaxTargets];   // block norms^2 (features)
   __shared__ float s_x[kMlpFeatures], s_h[kMlpHidden];
   __shared__ int s_k, s_rowf[kChunk], s_rowq[kChunk];
+  __shared__ int s_wf[kMaxWarps][kChunk], s_wq[kMaxWarps][kChunk];
   __shared__ T s_tq[64], s_probe[2];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -390,8 +430,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
     const int k = s_k;
     const int kk = k + 2;
     const int UNE = max(QW * per_warp, 4 * NL);          // union size (elements)
-    const int pwl = NL + 2 * kChunk * LD + 64;           // per warp: R, rows of F^T, projected rows
-    const int qwl = min(QW, (UNE - NL) / pwl);
+    const int LK = (k & 1) ? k : k + 1;                  // leading dimension of k-wide buffers
+    const int pwl = k * LK + kChunk * LD + kChunk * LK + 64;  // per warp: R, rows of F^T, projected rows
+    const int qwl = min(kWarpsNT, (UNE - NL) / pwl);
     if (4 * k <= 3 * n && qwl >= 1 && kk <= LD && k <= 2 * kChunk && NL + 2 * kChunk * LD <= UNE) {
       T* Q = un;                 // n x kk (columns k, k+1: probes)
       T* Cs = un + NL;           // 32 x LD rows of F^T
@@ -493,40 +534,34 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
       T* wbase = un + NL;
       if (warp < qw) {
         T* Rw = wbase + warp * pwl;
-        T* Cw = Rw + NL;
+        T* Cw = Rw + k * LK;
         T* Pw = Cw + kChunk * LD;
-        T* vb = Pw + kChunk * LD;
-        for (int e = lane; e < k * LD; e += 32) Rw[e] = T(0);
+        T* vb = Pw + kChunk * LK;
+        for (int e = lane; e < k * LK; e += 32) Rw[e] = T(0);
         for (int c = warp; c < nchunks; c += qw) {
           const int g0 = c * kChunk;
           const int rows = min(kChunk, mF - g0);
-          int f = 0;
-          while (f + 1 < nf && s_fpre[f + 1] <= g0) ++f;
-          int q = g0 - s_fpre[f];
-          for (int rr = 0; rr < rows; ++rr) {
-            while (q >= s_fw[f]) {
-              ++f;
-              q = 0;
+          warp_load_far_rows(Cw, LD, pool, L, i, n, g0, rows, nf, s_fpre, s_fk, s_foff, s_wf[warp], s_wq[warp]);
+          const int k4 = (k + 3) >> 2;
+          for (int e = lane; e < rows * k4; e += 32) {
+            const int q2 = e / k4, c0 = (e - q2 * k4) * 4;
+            T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll 4
+            for (int a = 0; a < n; ++a) {
+              const T cv = Cw[q2 * LD + a];
+              const T* qr = Q + a * LD + c0;
+              a0 += cv * qr[0];
+              a1 += cv * qr[1];
+              a2 += cv * qr[2];
+              a3 += cv * qr[3];
             }
-            const int k2 = s_fk[f];
-            const T* Xg = pool + s_foff[f];
-            if (i < k2) {
-              const int nk = L.n[k2];
-              for (int a = lane; a < n; a += 32) Cw[rr * LD + a] = Xg[(int64_t)a * nk + q];
-            } else {
-              for (int a = lane; a < n; a += 32) Cw[rr * LD + a] = Xg[(int64_t)q * n + a];
-            }
-            ++q;
+            Pw[q2 * LK + c0] = a0;
+            if (c0 + 1 < k) Pw[q2 * LK + c0 + 1] = a1;
+            if (c0 + 2 < k) Pw[q2 * LK + c0 + 2] = a2;
+            if (c0 + 3 < k) Pw[q2 * LK + c0 + 3] = a3;
           }
           __syncwarp();
-          for (int e = lane; e < rows * k; e += 32) {
-            const int q2 = e / k, cc = e - q2 * k;
-            T acc = 0;
-            for (int a = 0; a < n; ++a) acc += Cw[q2 * LD + a] * Q[a * LD + cc];
-            Pw[q2 * LD + cc] = acc;
-          }
-          __syncwarp();
-          warp_qr_stack(Rw, Pw, vb, k, rows, LD);
+          warp_qr_stack(Rw, Pw, vb, k, rows, LK);
         }
       }
       __syncthreads();
@@ -534,16 +569,16 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
         if (warp % (2 * step) == 0 && warp + step < qw) {
           T* Ra = wbase + warp * pwl;
           T* Rb = wbase + (warp + step) * pwl;
-          warp_qr_merge(Ra, Rb, Ra + NL + 2 * kChunk * LD, k, LD);
+          warp_qr_merge(Ra, Rb, Ra + k * LK + kChunk * LD + kChunk * LK, k, LK);
         }
         __syncthreads();
       }
       // one-sided Jacobi on the k x k factor R (= wbase), V in Vb
-      T* Xr = wbase;
-      T* Vb = wbase + NL;    // warp 0's row buffers (64 rows of LD), free now
+      T* Xr = wbase;                 // R (k x k, ld LK)
+      T* Vb = wbase + k * LK;        // warp 0's row buffers, free now (k x k, ld LK)
       for (int e = tid; e < k * k; e += NT) {
         const int a = e / k, b = e - a * k;
-        Vb[a * LD + b] = (a == b) ? T(1) : T(0);
+        Vb[a * LK + b] = (a == b) ? T(1) : T(0);
       }
       __syncthreads();
       {
@@ -551,8 +586,28 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
         const int half = lane >> 4, hl = lane & 15;
         const T tolJ = T(k) * Eps<T>::v, tolJ2 = tolJ * tolJ;
         for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-          if (tid == 0) s_flag = 0;
+          // same negligible-pair rule as the exact path, with k columns
+          for (int j = warp; j < k; j += kWarpsNT) {
+            T sv = 0;
+            for (int row = lane; row < k; row += 32) sv += Xr[row * LK + j] * Xr[row * LK + j];
+            sv = warp_sum(sv);
+            if (lane == 0) sig_tmp[j] = sv;
+          }
           __syncthreads();
+          if (warp == 0) {
+            T cm = fmax(lane < k ? sig_tmp[lane] : T(0), lane + 32 < k ? sig_tmp[lane + 32] : T(0));
+            cm = warp_max(cm);
+            if (lane == 0) {
+              const T sm = sqrt(cm);
+              T test = (tol == 0.0) ? T(n) * Eps<T>::v * sm
+                                    : ((tol_mode == CE_TOL_ABS) ? T(tol) : T(tol) * sm);
+              test = fmax(test, static_cast<T>(floor_all)) * T(0.5) * fast_rsqrt(T(k));
+              s_skip2 = test * test;
+              s_flag = 0;
+            }
+          }
+          __syncthreads();
+          const T skip2 = s_skip2;
           for (int rnd = 0; rnd < nb - 1; ++rnd) {
             for (int tb = warp * 2; tb < npairs; tb += NT / 16) {
               const int t = tb + half;
@@ -567,7 +622,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
               T a = 0, b = 0, g = 0;
               if (valid) {
                 for (int row = hl; row < k; row += 16) {
-                  T xp = Xr[row * LD + p], xq = Xr[row * LD + q];
+                  T xp = Xr[row * LK + p], xq = Xr[row * LK + q];
                   a += xp * xp;
                   b += xq * xq;
                   g += xp * xq;
@@ -576,7 +631,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
               a = half_sum(a);
               b = half_sum(b);
               g = half_sum(g);
-              if (valid && g != T(0) && g * g > tolJ2 * a * b) {
+              if (valid && g != T(0) && (a >= skip2 || b >= skip2) && g * g > tolJ2 * a * b) {
                 const T zeta = (b - a) * fast_rcp(T(2) * g);
                 const T az = fabs(zeta);
                 const T den = (az > T(1)) ? az * (T(1) + sqrt(T(1) + fast_rcp(az * az)))
@@ -584,12 +639,12 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
                 const T tt = ((zeta >= T(0)) ? T(1) : T(-1)) * fast_rcp(den);
                 const T cs = fast_rsqrt(T(1) + tt * tt), sn = cs * tt;
                 for (int row = hl; row < k; row += 16) {
-                  T xp = Xr[row * LD + p], xq = Xr[row * LD + q];
-                  Xr[row * LD + p] = cs * xp - sn * xq;
-                  Xr[row * LD + q] = sn * xp + cs * xq;
-                  T vp = Vb[row * LD + p], vq = Vb[row * LD + q];
-                  Vb[row * LD + p] = cs * vp - sn * vq;
-                  Vb[row * LD + q] = sn * vp + cs * vq;
+                  T xp = Xr[row * LK + p], xq = Xr[row * LK + q];
+                  Xr[row * LK + p] = cs * xp - sn * xq;
+                  Xr[row * LK + q] = sn * xp + cs * xq;
+                  T vp = Vb[row * LK + p], vq = Vb[row * LK + q];
+                  Vb[row * LK + p] = cs * vp - sn * vq;
+                  Vb[row * LK + q] = sn * vp + cs * vq;
                 }
                 if (hl == 0) s_flag = 1;
               }
@@ -603,7 +658,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
       }
       for (int j = tid; j < k; j += NT) {
         T sv = 0;
-        for (int row = 0; row < k; ++row) sv += Xr[row * LD + j] * Xr[row * LD + j];
+        for (int row = 0; row < k; ++row) sv += Xr[row * LK + j] * Xr[row * LK + j];
         sig_tmp[j] = sqrt(sv);
       }
       __syncthreads();
@@ -636,7 +691,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
           int j = 0;
           while (s_pos[j] != c) ++j;
           T acc = 0;
-          for (int q = 0; q < k; ++q) acc += Q[a * LD + q] * Vb[q * LD + j];
+          for (int q = 0; q < k; ++q) acc += Q[a * LD + q] * Vb[q * LK + j];
           U[a * LD + c] = acc;
         }
         __syncthreads();
@@ -722,26 +777,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
       for (int c = warp; c < nchunks; c += qw) {
         const int g0 = c * kChunk;
         const int rows = min(kChunk, mF - g0);
-        // far block holding row g0 of F_i^T
-        int f = 0;
-        while (f + 1 < nf && s_fpre[f + 1] <= g0) ++f;
-        int q = g0 - s_fpre[f];
-        for (int rr = 0; rr < rows; ++rr) {
-          while (q >= s_fw[f]) {
-            ++f;
-            q = 0;
-          }
-          const int k = s_fk[f];
-          const T* Xg = pool + s_foff[f];
-          if (i < k) {   // F = X[:, :w]: row q of F^T = column q of X
-            const int nk = L.n[k];
-            for (int a = lane; a < n; a += 32) Cw[rr * LD + a] = Xg[(int64_t)a * nk + q];
-          } else {       // rows of F^T are rows of X
-            for (int a = lane; a < n; a += 32) Cw[rr * LD + a] = Xg[(int64_t)q * n + a];
-          }
-          ++q;
-        }
-        __syncwarp();
+        warp_load_far_rows(Cw, LD, pool, L, i, n, g0, rows, nf, s_fpre, s_fk, s_foff, s_wf[warp], s_wq[warp]);
         warp_qr_stack(Rw, Cw, vb, n, rows, LD);
       }
     }
