@@ -133,6 +133,30 @@ ce_status csb_build(int64_t n, const int64_t* rowptr, const int32_t* col,
                     ce_csb** out);
 
 /*
+ * csb_build_batched -- many independent SPD systems as one block-diagonal
+ * matrix, so that each level's launches cover the block rows of all of them
+ * (the independent-set batching of Section 2.3 applied across systems; the
+ * paper factors one system at a time).
+ *   nsys     number of systems (> 0)
+ *   row_off  host, nsys+1 entries: system s owns rows and columns
+ *            [row_off[s], row_off[s+1]) of the stacked matrix; row_off[0] = 0
+ *   rowptr, col, val   host CSR of the stacked matrix (both triangles)
+ *   perm     host: the stacked permutation; for every system perm maps its
+ *            own rows to its own rows
+ *   B        host, nsys entries: block size of each system (> 0)
+ *   out      receives the handle
+ * Blocks never straddle two systems, super-blocks are formed within one
+ * system (J consecutive blocks of that system), and the coarse remainder is
+ * one dense matrix per system, so ce_factorize on the result gives, system
+ * by system, the factor of that system alone.  CE_ERR_INVALID_ARG also if a
+ * column or a permuted index leaves its system.
+ */
+ce_status csb_build_batched(int nsys, const int64_t* row_off,
+                            const int64_t* rowptr, const int32_t* col,
+                            const double* val, const int32_t* perm,
+                            const int32_t* B, ce_csb** out);
+
+/*
  * ce_factorize -- Algorithm 1 (CE algorithm): `levels` sweeps of Algorithm 2
  * (one level elimination: per block row the compression of the far blocks
  * F_i by an SVD truncated at tau_i, the row/column transform by U_i and the
@@ -181,6 +205,27 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev,
 ce_status pcg_solve(const ce_csb* A, const ce_factor* F, const double* b_dev,
                     double* x_dev, double rtol, int maxit, ce_pcg_info* info,
                     void* stream);
+
+/*
+ * pcg_solve_batched -- pcg_solve for a batch from csb_build_batched: one CG
+ * recurrence per system (its own step lengths, residual norm and stopping
+ * test ||r_s|| <= rtol ||b_s||); a converged system is frozen while the
+ * others iterate.  One iteration of all systems is captured once into a CUDA
+ * graph (kept in the factor together with its work vectors and reused by the
+ * next call with the same matrix handle; calls on one factor must not
+ * overlap) and replayed; the host reads the count of unconverged systems one
+ * iteration behind the GPU.
+ *   b_dev, x_dev  device arrays of n doubles (stacked original orderings)
+ *   iters, relres, converged   optional host arrays of nsys entries
+ *   info          optional: maximum iterations and residual, all converged
+ * pcg_solve on a batch handle calls this with the per-system arrays NULL.
+ * CE_ERR_NO_CONVERGENCE if some system reached maxit.
+ */
+ce_status pcg_solve_batched(const ce_csb* A, const ce_factor* F,
+                            const double* b_dev, double* x_dev, double rtol,
+                            int maxit, int32_t* iters, double* relres,
+                            int32_t* converged, ce_pcg_info* info,
+                            void* stream);
 
 /*
  * pcg_solve_noalloc -- the same FP64 PCG as pcg_solve (same arguments, same

@@ -142,6 +142,12 @@ class Factor:
             pass
 
 
+def launch_count() -> int:
+    """Kernels this library has launched in the process (graph replays
+    count every kernel node)."""
+    return int(_lib.load().ce_launch_count())
+
+
 def csb_build(A, perm, B: int) -> CSB:
     """A (scipy sparse, symmetric), perm[k] = original index of row k, block B."""
     import scipy.sparse as sp
@@ -159,6 +165,32 @@ def csb_build(A, perm, B: int) -> CSB:
                          val.ctypes.data_as(_lib.DP), pm.ctypes.data_as(_lib.I32P), int(B),
                          C.byref(h)), "csb_build")
     return CSB(h, n, int(B))
+
+
+def csb_build_batched(systems) -> CSB:
+    """Many independent systems [(A, perm, B), ...] as one block-diagonal
+    batch; rows are stacked in the order given."""
+    import scipy.sparse as sp
+    lib = _lib.load()
+    mats = [sp.csr_matrix(A) for A, _, _ in systems]
+    sizes = [m.shape[0] for m in mats]
+    row_off = np.zeros(len(mats) + 1, np.int64)
+    row_off[1:] = np.cumsum(sizes)
+    S = sp.block_diag(mats, format="csr")
+    pm = np.concatenate([np.asarray(p, np.int64) + row_off[s]
+                         for s, (_, p, _) in enumerate(systems)]).astype(np.int32)
+    Bs = np.asarray([B for _, _, B in systems], np.int32)
+    rowptr = np.ascontiguousarray(S.indptr, dtype=np.int64)
+    col = np.ascontiguousarray(S.indices, dtype=np.int32)
+    val = np.ascontiguousarray(S.data, dtype=np.float64)
+    h = C.c_void_p()
+    _check(lib.csb_build_batched(len(mats), row_off.ctypes.data_as(_lib.I64P),
+                                 rowptr.ctypes.data_as(_lib.I64P), col.ctypes.data_as(_lib.I32P),
+                                 val.ctypes.data_as(_lib.DP), pm.ctypes.data_as(_lib.I32P),
+                                 Bs.ctypes.data_as(_lib.I32P), C.byref(h)), "csb_build_batched")
+    csb = CSB(h, int(row_off[-1]), int(Bs[0]))
+    csb.row_off = row_off
+    return csb
 
 
 def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",
@@ -215,6 +247,23 @@ def pcg_solve(csb: CSB, F: Factor, b, x, rtol=1e-8, maxit=1000, stream=None, che
     if check and st not in (CE_OK, CE_ERR_NO_CONVERGENCE):
         raise CEError(st, "pcg_solve")
     return info.iters, info.relres, bool(info.converged)
+
+
+def pcg_solve_batched(csb: CSB, F: Factor, b, x, rtol=1e-8, maxit=1000, stream=None, check=True):
+    """Per-system FP64 PCG of a batch; returns (iters, relres, converged)
+    as numpy arrays with one entry per system."""
+    lib = _lib.load()
+    ns = len(csb.row_off) - 1
+    its = np.zeros(ns, np.int32)
+    rel = np.zeros(ns, np.float64)
+    conv = np.zeros(ns, np.int32)
+    info = _lib.ce_pcg_info()
+    st = lib.pcg_solve_batched(csb.handle, F.handle, _dev_ptr(b, "b"), _dev_ptr(x, "x"), float(rtol),
+                               int(maxit), its.ctypes.data_as(_lib.I32P), rel.ctypes.data_as(_lib.DP),
+                               conv.ctypes.data_as(_lib.I32P), C.byref(info), _stream_ptr(stream))
+    if check and st not in (CE_OK, CE_ERR_NO_CONVERGENCE):
+        raise CEError(st, "pcg_solve_batched")
+    return its, rel, conv.astype(bool)
 
 
 class RankModel:

@@ -6,6 +6,7 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -134,6 +135,48 @@ void level_work(const LevelPlan& P, const std::vector<int>& rank, int es, double
   }
 }
 
+// Block pairs (bi <= bk) of P A P^T with blocks [blkptr[b], blkptr[b+1]) of
+// rows: each block row collects its few distinct neighbour blocks in a small
+// buffer.  blk_of[r] is the block of permuted row r.
+std::vector<std::pair<int, int>> block_pairs(const int64_t* rowptr, const int32_t* col,
+                                             const int32_t* perm, const std::vector<int32_t>& iperm,
+                                             const std::vector<int64_t>& blkptr,
+                                             const std::vector<int>& blk_of) {
+  const int M = static_cast<int>(blkptr.size()) - 1;
+  std::vector<std::pair<int, int>> pairs;
+  std::vector<int> nb;
+  for (int bi = 0; bi < M; ++bi) {
+    nb.clear();
+    for (int64_t r = blkptr[bi]; r < blkptr[bi + 1]; ++r) {
+      const int a = perm[r];
+      for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
+        const int bk = blk_of[iperm[col[e]]];
+        if (bk >= bi && std::find(nb.begin(), nb.end(), bk) == nb.end()) nb.push_back(bk);
+      }
+    }
+    std::sort(nb.begin(), nb.end());
+    for (int bk : nb) pairs.emplace_back(bi, bk);
+  }
+  return pairs;
+}
+
+// A is symmetric: every (a, b, v) has a matching (b, a, v).  Rows are sorted
+// in one flat copy; lookups are binary searches.
+bool csr_symmetric(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val) {
+  const int64_t nnz = rowptr[n];
+  std::vector<std::pair<int32_t, double>> cv(nnz);
+  for (int64_t e = 0; e < nnz; ++e) cv[e] = {col[e], val[e]};
+  for (int64_t a = 0; a < n; ++a) std::sort(cv.begin() + rowptr[a], cv.begin() + rowptr[a + 1]);
+  for (int64_t a = 0; a < n; ++a)
+    for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
+      const int32_t b = cv[e].first;
+      auto lo = cv.begin() + rowptr[b], hi = cv.begin() + rowptr[b + 1];
+      auto it = std::lower_bound(lo, hi, std::make_pair((int32_t)a, -1e308));
+      if (it == hi || it->first != a || it->second != cv[e].second) return false;
+    }
+  return true;
+}
+
 int max_targets(const LevelPlan& P) {
   int t = 0;
   for (int i = 0; i < P.M; ++i) t = std::max(t, 1 + P.close_ptr[i + 1] - P.close_ptr[i]);
@@ -196,7 +239,7 @@ std::vector<CopyTask> reassembly_tasks(const LevelPlan& P, const std::vector<int
   for (size_t p = 0; p < P.pair_i.size(); ++p) {
     const int i = P.pair_i[p], k = P.pair_k[p];
     if (rank[i] == 0 || rank[k] == 0) continue;
-    const int I = i / J, K = k / J;
+    const int I = nx.parent[i], K = nx.parent[k];
     const int64_t dst = pair_offset(Pn, I, K);
     CopyTask t;
     t.src_off = P.pair_off[p];
@@ -219,28 +262,58 @@ std::vector<CopyTask> reassembly_tasks(const LevelPlan& P, const std::vector<int
   return tasks;
 }
 
-// copy tasks: close pairs of a level -> dense symmetric matrix
-std::vector<CopyTask> dense_tasks(const LevelPlan& P) {
+// Coarse systems of the last level: system s owns blocks [so[s], so[s+1]),
+// coarse rows [voff[s], voff[s] + nc[s]) and a dense nc x nc matrix at coff[s].
+struct CoarseSystems {
+  std::vector<int> so, sys_of;
+  std::vector<int64_t> nc, coff, voff, doff;
+  int64_t dense_elems = 0, dinv_elems = 0;
+  int nmax = 0;
+};
+
+CoarseSystems coarse_systems(const LevelPlan& P) {
+  CoarseSystems C;
+  C.so = P.sys_off.empty() ? std::vector<int>{0, P.M} : P.sys_off;
+  const int ns = static_cast<int>(C.so.size()) - 1;
+  C.sys_of.assign(P.M, 0);
+  for (int y = 0; y < ns; ++y) {
+    for (int i = C.so[y]; i < C.so[y + 1]; ++i) C.sys_of[i] = y;
+    const int64_t v0 = C.so[y] < P.M ? P.vec_off[C.so[y]] : P.vec_len;
+    const int64_t v1 = C.so[y + 1] < P.M ? P.vec_off[C.so[y + 1]] : P.vec_len;
+    C.voff.push_back(v0);
+    C.nc.push_back(v1 - v0);
+    C.coff.push_back(C.dense_elems);
+    C.doff.push_back(C.dinv_elems);
+    C.dense_elems += (v1 - v0) * (v1 - v0);
+    C.dinv_elems += (v1 - v0 + 63) / 64 * 64 * 64;
+    C.nmax = std::max<int>(C.nmax, static_cast<int>(v1 - v0));
+  }
+  return C;
+}
+
+// copy tasks: close pairs of a level -> one dense symmetric matrix per system
+std::vector<CopyTask> dense_tasks(const LevelPlan& P, const CoarseSystems& C) {
   std::vector<CopyTask> tasks;
-  const int nc = static_cast<int>(P.vec_len);
   for (size_t p = 0; p < P.pair_i.size(); ++p) {
     if (!P.pair_close[p]) continue;
     const int i = P.pair_i[p], k = P.pair_k[p];
     if (P.n[i] == 0 || P.n[k] == 0) continue;
+    const int y = C.sys_of[i];
+    if (C.sys_of[k] != y) throw std::logic_error("coupling between independent systems");
     CopyTask t;
     t.src_off = P.pair_off[p];
     t.src_ld = P.n[k];
     t.rows = P.n[i];
     t.cols = P.n[k];
-    t.dst_off = 0;
-    t.dst_ld = nc;
-    t.r0 = static_cast<int>(P.vec_off[i]);
-    t.c0 = static_cast<int>(P.vec_off[k]);
+    t.dst_off = C.coff[y];
+    t.dst_ld = static_cast<int>(C.nc[y]);
+    t.r0 = static_cast<int>(P.vec_off[i] - C.voff[y]);
+    t.c0 = static_cast<int>(P.vec_off[k] - C.voff[y]);
     t.transpose = 0;
     tasks.push_back(t);
     if (i != k) {
-      t.r0 = static_cast<int>(P.vec_off[k]);
-      t.c0 = static_cast<int>(P.vec_off[i]);
+      t.r0 = static_cast<int>(P.vec_off[k] - C.voff[y]);
+      t.c0 = static_cast<int>(P.vec_off[i] - C.voff[y]);
       t.transpose = 1;
       tasks.push_back(t);
     }
@@ -267,6 +340,12 @@ void free_factor(ce_factor* F, cudaStream_t s) {
   }
   dfree(F->d_coarse, s);
   dfree(F->d_cdinv, s);
+  dfree(F->d_csys, s);
+  if (F->pcg) {
+    cudaDeviceSynchronize();
+    ce::pcg_batch_release(F->pcg);
+    F->pcg = nullptr;
+  }
   dfree(F->d_work, s);
   dfree(F->d_status, s);
   if (F->owned_csb) ce_csb_destroy(F->owned_csb);
@@ -397,67 +476,54 @@ ce_status ce_mlp_predict(const float* X_dev, int ns, const void* model_dev, floa
   return CE_OK;
 }
 
-ce_status csb_build(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
-                    const int32_t* perm, int32_t B, ce_csb** out) {
-  if (!out || n <= 0 || !rowptr || !col || !val || !perm || B <= 0 || n > INT32_MAX)
-    return CE_ERR_INVALID_ARG;
-  *out = nullptr;
+}  // extern "C"
+
+namespace {
+
+// CSR + permutation + block pointers (+ systems) -> device CSB and level-1 plan.
+ce_status build_csb(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                    const int32_t* perm, const std::vector<int64_t>& blkptr,
+                    const std::vector<int>& sys_blk, const std::vector<int64_t>& sys_row, int B0,
+                    ce_csb** out) {
   const int64_t nnz = rowptr[n];
-  if (rowptr[0] != 0 || nnz < 0) return CE_ERR_INVALID_ARG;
-  for (int64_t a = 0; a < n; ++a)
-    if (rowptr[a + 1] < rowptr[a]) return CE_ERR_INVALID_ARG;
   std::vector<int32_t> iperm(n, -1);
   for (int64_t k = 0; k < n; ++k) {
     if (perm[k] < 0 || perm[k] >= n || iperm[perm[k]] != -1) return CE_ERR_INVALID_ARG;
     iperm[perm[k]] = static_cast<int32_t>(k);
   }
-  // symmetry: every (a, b, v) has a matching (b, a, v)
-  std::vector<std::vector<std::pair<int32_t, double>>> rows(n);
-  for (int64_t a = 0; a < n; ++a) {
-    for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
-      if (col[e] < 0 || col[e] >= n) return CE_ERR_INVALID_ARG;
-      rows[a].emplace_back(col[e], val[e]);
-    }
-    std::sort(rows[a].begin(), rows[a].end());
+  for (int64_t e = 0; e < nnz; ++e)
+    if (col[e] < 0 || col[e] >= n) return CE_ERR_INVALID_ARG;
+  if (!csr_symmetric(n, rowptr, col, val)) return CE_ERR_INVALID_ARG;
+  const int M = static_cast<int>(blkptr.size()) - 1;
+  std::vector<int> sizes(M);
+  std::vector<int> blk_of(n);
+  for (int b2 = 0; b2 < M; ++b2) {
+    sizes[b2] = static_cast<int>(blkptr[b2 + 1] - blkptr[b2]);
+    for (int64_t r = blkptr[b2]; r < blkptr[b2 + 1]; ++r) blk_of[r] = b2;
   }
-  for (int64_t a = 0; a < n; ++a)
-    for (auto& cv : rows[a]) {
-      auto& rb = rows[cv.first];
-      auto it = std::lower_bound(rb.begin(), rb.end(), std::make_pair((int32_t)a, -1e308));
-      if (it == rb.end() || it->first != a || it->second != cv.second) return CE_ERR_INVALID_ARG;
-    }
-  rows.clear();
-  rows.shrink_to_fit();
-
-  const int M = static_cast<int>((n + B - 1) / B);
-  std::vector<int> sizes(M, B);
-  sizes[M - 1] = static_cast<int>(n - (int64_t)(M - 1) * B);
-  std::vector<std::pair<int, int>> pairs;
-  pairs.reserve(nnz);
-  for (int64_t a = 0; a < n; ++a)
-    for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
-      int bi = iperm[a] / B, bk = iperm[col[e]] / B;
-      if (bi <= bk) pairs.emplace_back(bi, bk);
-    }
-  std::sort(pairs.begin(), pairs.end());
-  pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
-
+  std::vector<std::pair<int, int>> pairs = block_pairs(rowptr, col, perm, iperm, blkptr, blk_of);
   ce_csb* A = new (std::nothrow) ce_csb();
   if (!A) return CE_ERR_OOM;
   A->n = n;
-  A->B = B;
+  A->B = B0;
   A->nnz = nnz;
+  A->nsys = static_cast<int>(sys_row.size()) - 1;
+  A->sys_row = sys_row;
   try {
     ce::plan_level(A->plan1, sizes, pairs, true);
+    A->plan1.sys_off = sys_blk;
     std::vector<int64_t> scatter(nnz, -1);
     for (int64_t a = 0; a < n; ++a)
       for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
         const int pa = iperm[a], pb = iperm[col[e]];
-        const int bi = pa / B, bk = pb / B;
+        const int bi = blk_of[pa], bk = blk_of[pb];
         if (bi > bk) continue;
         const int64_t po = pair_offset(A->plan1, bi, bk);
-        scatter[e] = po + (int64_t)(pa - bi * B) * A->plan1.n[bk] + (pb - bk * B);
+        scatter[e] = po + (int64_t)(pa - blkptr[bi]) * A->plan1.n[bk] + (pb - blkptr[bk]);
       }
+    std::vector<int32_t> sys_of_row(n);
+    for (int s2 = 0; s2 < A->nsys; ++s2)
+      for (int64_t r = sys_row[s2]; r < sys_row[s2 + 1]; ++r) sys_of_row[r] = s2;
     init_pool_once();
     cudaStream_t s = nullptr;
     A->d_rowptr = static_cast<int64_t*>(dalloc((n + 1) * sizeof(int64_t), s));
@@ -465,11 +531,14 @@ ce_status csb_build(int64_t n, const int64_t* rowptr, const int32_t* col, const 
     A->d_val = static_cast<double*>(dalloc(nnz * sizeof(double), s));
     A->d_perm = static_cast<int32_t*>(dalloc(n * sizeof(int32_t), s));
     A->d_scatter = static_cast<int64_t*>(dalloc(nnz * sizeof(int64_t), s));
+    A->d_sys_of_row = static_cast<int32_t*>(dalloc(n * sizeof(int32_t), s));
     check(cudaMemcpyAsync(A->d_rowptr, rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s), "H2D");
     check(cudaMemcpyAsync(A->d_col, col, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s), "H2D");
     check(cudaMemcpyAsync(A->d_val, val, nnz * sizeof(double), cudaMemcpyHostToDevice, s), "H2D");
     check(cudaMemcpyAsync(A->d_perm, perm, n * sizeof(int32_t), cudaMemcpyHostToDevice, s), "H2D");
     check(cudaMemcpyAsync(A->d_scatter, scatter.data(), nnz * sizeof(int64_t), cudaMemcpyHostToDevice, s),
+          "H2D");
+    check(cudaMemcpyAsync(A->d_sys_of_row, sys_of_row.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s),
           "H2D");
     check(cudaStreamSynchronize(s), "csb_build sync");
   } catch (const CudaFail& f) {
@@ -487,6 +556,52 @@ ce_status csb_build(int64_t n, const int64_t* rowptr, const int32_t* col, const 
   return CE_OK;
 }
 
+}  // namespace
+
+extern "C" {
+
+ce_status csb_build(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val,
+                    const int32_t* perm, int32_t B, ce_csb** out) {
+  if (!out || n <= 0 || !rowptr || !col || !val || !perm || B <= 0 || n > INT32_MAX)
+    return CE_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (rowptr[0] != 0 || rowptr[n] < 0) return CE_ERR_INVALID_ARG;
+  for (int64_t a = 0; a < n; ++a)
+    if (rowptr[a + 1] < rowptr[a]) return CE_ERR_INVALID_ARG;
+  const int M = static_cast<int>((n + B - 1) / B);
+  std::vector<int64_t> blkptr(M + 1);
+  for (int b2 = 0; b2 <= M; ++b2) blkptr[b2] = std::min<int64_t>(n, (int64_t)b2 * B);
+  return build_csb(n, rowptr, col, val, perm, blkptr, {0, M}, {0, n}, B, out);
+}
+
+ce_status csb_build_batched(int nsys, const int64_t* row_off, const int64_t* rowptr, const int32_t* col,
+                            const double* val, const int32_t* perm, const int32_t* B, ce_csb** out) {
+  if (!out || nsys <= 0 || !row_off || !rowptr || !col || !val || !perm || !B) return CE_ERR_INVALID_ARG;
+  *out = nullptr;
+  const int64_t n = row_off[nsys];
+  if (row_off[0] != 0 || n <= 0 || n > INT32_MAX || rowptr[0] != 0) return CE_ERR_INVALID_ARG;
+  for (int64_t a = 0; a < n; ++a)
+    if (rowptr[a + 1] < rowptr[a]) return CE_ERR_INVALID_ARG;
+  std::vector<int64_t> blkptr{0};
+  std::vector<int> sys_blk{0};
+  std::vector<int64_t> sys_row(row_off, row_off + nsys + 1);
+  for (int s2 = 0; s2 < nsys; ++s2) {
+    const int64_t r0 = row_off[s2], r1 = row_off[s2 + 1];
+    if (r1 <= r0 || B[s2] <= 0) return CE_ERR_INVALID_ARG;
+    // the batch is block diagonal: each system's permutation and columns stay
+    // inside its own rows
+    for (int64_t k = r0; k < r1; ++k) {
+      if (perm[k] < r0 || perm[k] >= r1) return CE_ERR_INVALID_ARG;
+      for (int64_t e = rowptr[k]; e < rowptr[k + 1]; ++e)
+        if (col[e] < r0 || col[e] >= r1) return CE_ERR_INVALID_ARG;
+    }
+    for (int64_t r = r0 + B[s2]; r < r1; r += B[s2]) blkptr.push_back(r);
+    blkptr.push_back(r1);
+    sys_blk.push_back(static_cast<int>(blkptr.size()) - 1);
+  }
+  return build_csb(n, rowptr, col, val, perm, blkptr, sys_blk, sys_row, B[0], out);
+}
+
 void ce_csb_destroy(ce_csb* A) {
   if (!A) return;
   cudaStream_t s = nullptr;
@@ -495,6 +610,7 @@ void ce_csb_destroy(ce_csb* A) {
   dfree(A->d_val, s);
   dfree(A->d_perm, s);
   dfree(A->d_scatter, s);
+  dfree(A->d_sys_of_row, s);
   delete A;
 }
 
@@ -507,18 +623,16 @@ ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col, c
     if (perm[k] < 0 || perm[k] >= n || iperm[perm[k]] != -1) return CE_ERR_INVALID_ARG;
     iperm[perm[k]] = static_cast<int32_t>(k);
   }
+  for (int64_t e = 0; e < rowptr[n]; ++e)
+    if (col[e] < 0 || col[e] >= n) return CE_ERR_INVALID_ARG;
   const int M = static_cast<int>((n + B - 1) / B);
   std::vector<int> sizes(M, B);
   sizes[M - 1] = static_cast<int>(n - (int64_t)(M - 1) * B);
-  std::vector<std::pair<int, int>> pairs;
-  for (int64_t a = 0; a < n; ++a)
-    for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
-      if (col[e] < 0 || col[e] >= n) return CE_ERR_INVALID_ARG;
-      int bi = iperm[a] / B, bk = iperm[col[e]] / B;
-      if (bi <= bk) pairs.emplace_back(bi, bk);
-    }
-  std::sort(pairs.begin(), pairs.end());
-  pairs.erase(std::unique(pairs.begin(), pairs.end()), pairs.end());
+  std::vector<int64_t> blkptr(M + 1);
+  std::vector<int> blk_of(n);
+  for (int b2 = 0; b2 <= M; ++b2) blkptr[b2] = std::min<int64_t>(n, (int64_t)b2 * B);
+  for (int64_t r = 0; r < n; ++r) blk_of[r] = static_cast<int>(r / B);
+  std::vector<std::pair<int, int>> pairs = block_pairs(rowptr, col, perm, iperm, blkptr, blk_of);
   try {
     LevelPlan P;
     ce::plan_level(P, sizes, pairs, true);
@@ -585,6 +699,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       for (size_t p = 0; p < A->plan1.pair_i.size(); ++p)
         if (A->plan1.pair_close[p]) pr.emplace_back(A->plan1.pair_i[p], A->plan1.pair_k[p]);
       ce::plan_level(cur, A->plan1.n, pr, false);
+      cur.sys_off = A->plan1.sys_off;
     }
     pool = dalloc(cur.pool_elems * es, s);
     check(cudaMemsetAsync(pool, 0, cur.pool_elems * es, s), "memset pool");
@@ -639,8 +754,9 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       ce::NextLevel nx = ce::coarsen(P, st.rank, o.J);
       LevelPlan nxt;
       ce::plan_level(nxt, nx.n, nx.pairs, o.coloring != 0);
+      nxt.sys_off = nx.sys_off;
       std::vector<int64_t> gd(P.M);
-      for (int i = 0; i < P.M; ++i) gd[i] = nxt.vec_off[i / o.J] + nx.child_off[i];
+      for (int i = 0; i < P.M; ++i) gd[i] = nxt.vec_off[nx.parent[i]] + nx.child_off[i];
       check(cudaMemcpyAsync(st.dev.gdst, gd.data(), P.M * sizeof(int64_t), cudaMemcpyHostToDevice, s), "H2D");
       void* npool = dalloc(std::max<int64_t>(nxt.pool_elems, 1) * es, s);
       check(cudaMemsetAsync(npool, 0, nxt.pool_elems * es, s), "memset pool");
@@ -650,24 +766,37 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       st.dev.pool = nullptr;
       cur = std::move(nxt);
     }
+    int64_t coarse_elems = 0;
     if (ret == CE_OK) {
       // dense remainder A_K and its Cholesky factor (FP64)
       F->nc = static_cast<int>(cur.vec_len);
-      if (F->nc > 28000) {
+      const CoarseSystems C = coarse_systems(cur);
+      F->nsys = static_cast<int>(C.nc.size());
+      F->sys_nc = C.nc;
+      F->sys_coff = C.coff;
+      coarse_elems = C.dense_elems + C.dinv_elems;
+      if (C.nmax > 28000) {
         ret = CE_ERR_LIMIT;
       } else if (F->nc > 0) {
         cudaEvent_t ev0, ev1;
         check(cudaEventCreate(&ev0), "event");
         check(cudaEventCreate(&ev1), "event");
         check(cudaEventRecord(ev0, s), "event");
-        const size_t nb = (size_t)F->nc * F->nc * sizeof(double);
+        std::vector<int64_t> desc;
+        for (auto* v : {&C.nc, &C.coff, &C.voff, &C.doff}) desc.insert(desc.end(), v->begin(), v->end());
+        F->d_csys = static_cast<int64_t*>(dalloc(desc.size() * sizeof(int64_t), s));
+        check(cudaMemcpyAsync(F->d_csys, desc.data(), desc.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s),
+              "H2D");
+        const size_t nb = (size_t)C.dense_elems * sizeof(double);
         F->d_coarse = static_cast<double*>(dalloc(nb, s));
         check(cudaMemsetAsync(F->d_coarse, 0, nb, s), "memset coarse");
-        run_copy_tasks(dense_tasks(cur), es, 8, pool, F->d_coarse, s);
-        check(ce::coarse_cholesky(F->d_coarse, F->nc, (int)F->levels.size(), F->d_status, s), "coarse chol");
-        const int npan = (F->nc + 63) / 64;
-        F->d_cdinv = static_cast<double*>(dalloc((size_t)npan * 64 * 64 * sizeof(double), s));
-        check(ce::launch_coarse_dinv(F->d_coarse, F->nc, F->d_cdinv, s), "coarse diagonal inverses");
+        run_copy_tasks(dense_tasks(cur, C), es, 8, pool, F->d_coarse, s);
+        check(ce::coarse_cholesky(F->d_coarse, F->d_csys, F->nsys, C.nmax, (int)F->levels.size(), F->d_status,
+                                  s),
+              "coarse chol");
+        F->d_cdinv = static_cast<double*>(dalloc((size_t)C.dinv_elems * sizeof(double), s));
+        check(ce::launch_coarse_dinv(F->d_coarse, F->d_csys, F->nsys, C.nmax, F->d_cdinv, s),
+              "coarse diagonal inverses");
         check(cudaEventRecord(ev1, s), "event");
         check(cudaMemcpyAsync(hstatus, F->d_status, sizeof(hstatus), cudaMemcpyDeviceToHost, s), "D2H");
         check(cudaStreamSynchronize(s), "coarse sync");
@@ -700,7 +829,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       tot += F->nc;
       F->d_work = static_cast<double*>(dalloc(std::max<int64_t>(tot, 1) * sizeof(double), s));
       check(cudaStreamSynchronize(s), "factor sync");
-      int64_t bytes = (int64_t)F->nc * F->nc * 8 + tot * 8;
+      int64_t bytes = coarse_elems * 8 + tot * 8;
       for (auto& st : F->levels) bytes += st.fac_bytes + st.meta_bytes;
       F->bytes = bytes;
       int lstat[32];
@@ -780,7 +909,11 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev, void*
               "apply fwd");
       check(ce::launch_level_move(st.dev, v, vn, 1, s), "level move");
     }
-    check(ce::launch_coarse_solve(F->d_coarse, F->d_cdinv, F->nc, coarse, s), "coarse solve");
+    if (F->nsys == 1)
+      check(ce::launch_coarse_solve(F->d_coarse, F->d_cdinv, F->nc, coarse, s), "coarse solve");
+    else if (F->nc > 0)
+      check(ce::launch_coarse_solve_sys(F->d_coarse, F->d_cdinv, F->d_csys, F->nsys, coarse, s),
+            "coarse solve");
     for (int l = nl - 1; l >= 0; --l) {
       const LevelStore& st = F->levels[l];
       double* v = F->d_work + F->vec_base[l];
@@ -801,6 +934,7 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev, void*
 ce_status pcg_solve(const ce_csb* A, const ce_factor* F, const double* b_dev, double* x_dev, double rtol,
                     int maxit, ce_pcg_info* info, void* stream) {
   if (!A || !F || !b_dev || !x_dev || maxit < 0 || rtol < 0 || A->n != F->N) return CE_ERR_INVALID_ARG;
+  if (A->nsys > 1) return pcg_solve_batched(A, F, b_dev, x_dev, rtol, maxit, nullptr, nullptr, nullptr, info, stream);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t n = A->n;
   const int nparts = static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 4));

@@ -263,11 +263,70 @@ __global__ void __launch_bounds__(kCS) coarse_solve_kernel(const double* Lc, con
   }
 }
 
-// Inverses of the diagonal kPan x kPan blocks of L_K (one CTA per block,
-// one column of the inverse per thread).
-__global__ void __launch_bounds__(kPan) coarse_dinv_kernel(const double* Lc, int n, double* Dinv) {
+// Independent systems, one CTA each: the same panel solves with
+// __syncthreads in place of the grid barrier.  System y has its coarse size
+// at desc[y], its factor at desc[nsys + y], its slice of the coarse vector at
+// desc[2 nsys + y] and its diagonal inverses at desc[3 nsys + y].
+__global__ void __launch_bounds__(kCS) coarse_solve_sys_kernel(const double* Lc, const double* Dinv,
+                                                               const int64_t* desc, int nsys, double* y) {
+  __shared__ double yp[kPan];
+  const int sy = blockIdx.x;
+  const int n = static_cast<int>(desc[sy]);
+  Lc += desc[nsys + sy];
+  y += desc[2 * nsys + sy];
+  Dinv += desc[3 * nsys + sy];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int npan = (n + kPan - 1) / kPan;
+  for (int p = 0; p < npan; ++p) {
+    const int s0 = p * kPan, pe = min(n, s0 + kPan), h = pe - s0;
+    for (int a = tid; a < h; a += kCS) yp[a] = y[s0 + a];
+    __syncthreads();
+    const double* D = Dinv + (size_t)p * kPan * kPan;
+    for (int a = tid; a < h; a += kCS) {
+      double s = 0.0;
+      for (int k = 0; k <= a; ++k) s += D[a * kPan + k] * yp[k];
+      y[s0 + a] = s;
+    }
+    __syncthreads();
+    for (int a = pe + warp; a < n; a += kCS / 32) {
+      double s = 0.0;
+      for (int k = s0 + lane; k < pe; k += 32) s += Lc[(int64_t)a * n + k] * y[k];
+      s = warp_sum_d(s);
+      if (lane == 0) y[a] -= s;
+    }
+    __syncthreads();
+  }
+  for (int p = npan - 1; p >= 0; --p) {
+    const int s0 = p * kPan, pe = min(n, s0 + kPan), h = pe - s0;
+    for (int a = tid; a < h; a += kCS) yp[a] = y[s0 + a];
+    __syncthreads();
+    const double* D = Dinv + (size_t)p * kPan * kPan;
+    for (int a = tid; a < h; a += kCS) {
+      double s = 0.0;
+      for (int k = a; k < h; ++k) s += D[k * kPan + a] * yp[k];
+      y[s0 + a] = s;
+    }
+    __syncthreads();
+    for (int c = tid; c < s0; c += kCS) {
+      double s = 0.0;
+      for (int a = s0; a < pe; ++a) s += Lc[(int64_t)a * n + c] * y[a];
+      y[c] -= s;
+    }
+    __syncthreads();
+  }
+}
+
+// Inverses of the diagonal kPan x kPan blocks of L_K (one CTA per block and
+// system, one column of the inverse per thread).
+__global__ void __launch_bounds__(kPan) coarse_dinv_kernel(const double* Lc, const int64_t* desc, int nsys,
+                                                           double* Dinv) {
   __shared__ double Lb[kPan * (kPan + 1)];
-  const int p = blockIdx.x, s0 = p * kPan, h = min(n, s0 + kPan) - s0;
+  const int n = static_cast<int>(desc[blockIdx.y]);
+  Lc += desc[nsys + blockIdx.y];
+  Dinv += desc[3 * nsys + blockIdx.y];
+  const int p = blockIdx.x, s0 = p * kPan;
+  if (s0 >= n) return;
+  const int h = min(n, s0 + kPan) - s0;
   for (int e = threadIdx.x; e < h * h; e += kPan) {
     int a = e / h, b = e - a * h;
     Lb[a * (kPan + 1) + b] = Lc[(int64_t)(s0 + a) * n + s0 + b];
@@ -419,10 +478,19 @@ cudaError_t launch_perm(const int32_t* perm, int64_t n, const double* in, double
   return cudaGetLastError();
 }
 
-cudaError_t launch_coarse_dinv(const double* Lc, int n, double* Dinv, cudaStream_t s) {
-  if (n <= 0) return cudaSuccess;
+cudaError_t launch_coarse_dinv(const double* Lc, const int64_t* desc, int nsys, int nmax, double* Dinv,
+                               cudaStream_t s) {
+  if (nmax <= 0) return cudaSuccess;
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  coarse_dinv_kernel<<<(n + kPan - 1) / kPan, kPan, 0, s>>>(Lc, n, Dinv);
+  coarse_dinv_kernel<<<dim3((nmax + kPan - 1) / kPan, nsys), kPan, 0, s>>>(Lc, desc, nsys, Dinv);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_coarse_solve_sys(const double* Lc, const double* Dinv, const int64_t* desc, int nsys,
+                                    double* y, cudaStream_t s) {
+  if (nsys <= 0) return cudaSuccess;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  coarse_solve_sys_kernel<<<nsys, kCS, 0, s>>>(Lc, Dinv, desc, nsys, y);
   return cudaGetLastError();
 }
 

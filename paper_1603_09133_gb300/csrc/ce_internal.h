@@ -45,6 +45,9 @@ struct LevelPlan {
   std::vector<int64_t> u_off, l_off, w_off, vec_off;
   int64_t u_elems = 0, l_elems = 0, w_elems = 0, vec_len = 0;
   int nmax = 0;
+
+  // independent systems: blocks [sys_off[s], sys_off[s+1]) belong to system s
+  std::vector<int> sys_off;
 };
 
 // Build the plan of a level from its sizes and level-start pattern (pairs
@@ -67,9 +70,15 @@ struct NextLevel {
   std::vector<int> n;                            // super-block sizes
   std::vector<std::pair<int, int>> pairs;        // next close pattern
   std::vector<int> child_off;                    // offset of child i in its super-block
+  std::vector<int> parent;                       // super-block of child i
+  std::vector<int> sys_off;                      // super-blocks of each system
 };
 
 NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J);
+
+// graph, work vectors and chunk map of the batched PCG (pcg_batched.cu)
+struct PcgBatch;
+void pcg_batch_release(PcgBatch* P);
 
 // ---------------------------------------------------------------------------
 // Device view of a level for the kernels (all pointers device).
@@ -117,7 +126,10 @@ struct LevelStore {
 
 struct ce_csb {
   int64_t n = 0;
-  int B = 0;
+  int B = 0;                     // block size (first system's for a batch)
+  int nsys = 1;                  // independent systems (block-diagonal batch)
+  std::vector<int64_t> sys_row;  // rows of system s: [sys_row[s], sys_row[s+1])
+  int32_t* d_sys_of_row = nullptr;  // system of every row (batched PCG)
   int64_t nnz = 0;
   // device CSR of A (original ordering) and the permutation
   int64_t* d_rowptr = nullptr;
@@ -131,13 +143,16 @@ struct ce_csb {
 
 struct ce_factor {
   int64_t N = 0;
+  int nsys = 1;
+  std::vector<int64_t> sys_nc;  // coarse size of each system
+  std::vector<int64_t> sys_coff;// offset of its dense factor in d_coarse
+  int64_t* d_csys = nullptr;    // device copy: [nc(nsys), coff(nsys), voff(nsys), dinv_off(nsys)]
   int prec = CE_PREC_FP64;
   int esize = 8;
   std::vector<ce::LevelStore> levels;
   int nc = 0;                   // coarse size
   double* d_coarse = nullptr;   // nc x nc lower Cholesky factor (FP64)
   double* d_cdinv = nullptr;    // inverses of its 64 x 64 diagonal blocks
-  int64_t* d_cgdst = nullptr;   // unused placeholder
   int32_t* d_perm = nullptr;    // borrowed from the csb
   double* d_work = nullptr;     // level vectors (FP64) + coarse vector
   std::vector<int64_t> vec_base;// start of each level vector in d_work
@@ -145,4 +160,5 @@ struct ce_factor {
   int* d_status = nullptr;
   int64_t bytes = 0;
   ce_csb* owned_csb = nullptr;
+  mutable ce::PcgBatch* pcg = nullptr;  // batched PCG state, built on first use
 };

@@ -87,11 +87,22 @@ __global__ void copy_tasks_kernel(const CopyTask* tasks, const Ts* src, Td* dst)
 }
 
 // ---------------- coarse dense Cholesky (FP64, lower, row-major) -----------
+// One dense matrix per independent system: system y = blockIdx.y has size
+// desc[y] and starts at element desc[nsys + y] of the coarse storage.
 constexpr int NB = 64;
 constexpr int NBL = NB + 1;
 
-__global__ void potrf_tile_kernel(double* A, int n, int k0, int level, int* status) {
+__device__ __forceinline__ bool coarse_sys(double*& A, int& n, const int64_t* desc, int nsys, int k0) {
+  const int y = blockIdx.y;
+  n = static_cast<int>(desc[y]);
+  A += desc[nsys + y];
+  return k0 < n;
+}
+
+__global__ void potrf_tile_kernel(double* A, const int64_t* desc, int nsys, int k0, int level, int* status) {
   if (*status) return;
+  int n;
+  if (!coarse_sys(A, n, desc, nsys, k0)) return;
   __shared__ double t[NB * NBL];
   const int nb = min(NB, n - k0);
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
@@ -102,7 +113,7 @@ __global__ void potrf_tile_kernel(double* A, int n, int k0, int level, int* stat
   for (int k = 0; k < nb; ++k) {
     const double piv = t[k * NBL + k];
     if (!(piv > 0.0)) {
-      if (threadIdx.x == 0) set_status(status, CE_ERR_NOT_SPD, level, -1, 1, k0 + k, piv);
+      if (threadIdx.x == 0) set_status(status, CE_ERR_NOT_SPD, level, -1 - (int)blockIdx.y, 1, k0 + k, piv);
       return;
     }
     const double d = sqrt(piv);
@@ -128,13 +139,16 @@ __global__ void potrf_tile_kernel(double* A, int n, int k0, int level, int* stat
 }
 
 // L_ik = A_ik L_kk^{-T} for the row tiles below the diagonal tile k0
-__global__ void trsm_tile_kernel(double* A, int n, int k0, const int* status) {
+__global__ void trsm_tile_kernel(double* A, const int64_t* desc, int nsys, int k0, const int* status) {
   if (*status) return;
+  int n;
+  if (!coarse_sys(A, n, desc, nsys, k0)) return;
   extern __shared__ double tile_smem[];
   double* Lk = tile_smem;
   double* X = tile_smem + NB * NBL;
   const int nb = min(NB, n - k0);
   const int i0 = k0 + nb + blockIdx.x * NB;
+  if (i0 >= n) return;
   const int rows = min(NB, n - i0);
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     int a = e / nb, b = e - a * nb;
@@ -161,8 +175,10 @@ __global__ void trsm_tile_kernel(double* A, int n, int k0, const int* status) {
 }
 
 // A_ij -= L_ik L_jk^T for the trailing tiles j <= i
-__global__ void syrk_tile_kernel(double* A, int n, int k0, const int* status) {
+__global__ void syrk_tile_kernel(double* A, const int64_t* desc, int nsys, int k0, const int* status) {
   if (*status) return;
+  int n;
+  if (!coarse_sys(A, n, desc, nsys, k0)) return;
   extern __shared__ double tile_smem[];
   double* Li = tile_smem;
   double* Lj = tile_smem + NB * NBL;
@@ -176,6 +192,7 @@ __global__ void syrk_tile_kernel(double* A, int n, int k0, const int* status) {
   }
   const int tj = idx;
   const int i0 = t0 + ti * NB, j0 = t0 + tj * NB;
+  if (i0 >= n) return;
   const int ri = min(NB, n - i0), rj = min(NB, n - j0);
   for (int e = threadIdx.x; e < ri * nb; e += blockDim.x) {
     int a = e / nb, b = e - a * nb;
@@ -223,7 +240,8 @@ cudaError_t launch_copy_tasks(int esize_src, int esize_dst, const CopyTask* task
   return cudaGetLastError();
 }
 
-cudaError_t coarse_cholesky(double* A, int n, int level, int* status, cudaStream_t s) {
+cudaError_t coarse_cholesky(double* A, const int64_t* desc, int nsys, int nmax, int level, int* status,
+                            cudaStream_t s) {
   const int tile_bytes = 2 * NB * NBL * static_cast<int>(sizeof(double));
   static bool attr = false;
   if (!attr) {
@@ -234,17 +252,18 @@ cudaError_t coarse_cholesky(double* A, int n, int level, int* status, cudaStream
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  for (int k0 = 0; k0 < n; k0 += NB) {
+  // the grids cover the largest system; smaller ones return early
+  for (int k0 = 0; k0 < nmax; k0 += NB) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    potrf_tile_kernel<<<1, 256, 0, s>>>(A, n, k0, level, status);
-    const int nb = std::min(NB, n - k0);
-    const int below = n - k0 - nb;
+    potrf_tile_kernel<<<dim3(1, nsys), 256, 0, s>>>(A, desc, nsys, k0, level, status);
+    const int nb = std::min(NB, nmax - k0);
+    const int below = nmax - k0 - nb;
     if (below > 0) {
       const int tiles = (below + NB - 1) / NB;
       g_launches.fetch_add(1, std::memory_order_relaxed);
-      trsm_tile_kernel<<<tiles, 64, tile_bytes, s>>>(A, n, k0, status);
+      trsm_tile_kernel<<<dim3(tiles, nsys), 64, tile_bytes, s>>>(A, desc, nsys, k0, status);
       g_launches.fetch_add(1, std::memory_order_relaxed);
-      syrk_tile_kernel<<<tiles * (tiles + 1) / 2, 256, tile_bytes, s>>>(A, n, k0, status);
+      syrk_tile_kernel<<<dim3(tiles * (tiles + 1) / 2, nsys), 256, tile_bytes, s>>>(A, desc, nsys, k0, status);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;

@@ -40,7 +40,10 @@ cudaError_t launch_scatter_csr(int esize, const int64_t* scatter, const double* 
                                void* pool, cudaStream_t s);
 cudaError_t launch_copy_tasks(int esize_src, int esize_dst, const CopyTask* tasks, int ntasks,
                               const void* src, void* dst, cudaStream_t s);
-cudaError_t coarse_cholesky(double* A, int n, int level, int* status, cudaStream_t s);
+// Dense FP64 Cholesky of every system's coarse matrix (in place, lower);
+// desc = [n(nsys), offset(nsys), ...] per system.
+cudaError_t coarse_cholesky(double* A, const int64_t* desc, int nsys, int nmax, int level, int* status,
+                            cudaStream_t s);
 
 // apply (x = Q^T L^{-T} L^{-1} Q r)
 cudaError_t launch_apply_fwd(int esize, const LevelDev& L, int first, int count, int nmax, double* vec,
@@ -51,7 +54,10 @@ cudaError_t launch_level_move(const LevelDev& L, double* cur, double* next, int 
                               cudaStream_t s);
 cudaError_t launch_perm(const int32_t* perm, int64_t n, const double* in, double* out, int gather,
                         cudaStream_t s);
-cudaError_t launch_coarse_dinv(const double* Lc, int n, double* Dinv, cudaStream_t s);
+cudaError_t launch_coarse_dinv(const double* Lc, const int64_t* desc, int nsys, int nmax, double* Dinv,
+                               cudaStream_t s);
+cudaError_t launch_coarse_solve_sys(const double* Lc, const double* Dinv, const int64_t* desc, int nsys,
+                                    double* y, cudaStream_t s);
 cudaError_t launch_coarse_solve(const double* Lc, const double* Dinv, int n, double* y, cudaStream_t s);
 
 // PCG building blocks (FP64)

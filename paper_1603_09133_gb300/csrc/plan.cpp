@@ -188,18 +188,29 @@ void plan_level(LevelPlan& P, const std::vector<int>& n,
 NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J) {
   NextLevel nx;
   const int M = P.M;
-  const int Mn = (M + J - 1) / J;
-  nx.n.assign(Mn, 0);
+  std::vector<int> so = P.sys_off;
+  if (so.empty()) so = {0, M};
+  nx.parent.assign(M, 0);
   nx.child_off.assign(M, 0);
+  nx.sys_off.assign(so.size(), 0);
+  int next = 0;
+  for (size_t s = 0; s + 1 < so.size(); ++s) {
+    nx.sys_off[s] = next;
+    // J consecutive blocks of the same system form one super-block
+    for (int i = so[s]; i < so[s + 1]; ++i) nx.parent[i] = next + (i - so[s]) / J;
+    next += (so[s + 1] - so[s] + J - 1) / J;
+  }
+  nx.sys_off.back() = next;
+  nx.n.assign(next, 0);
   for (int i = 0; i < M; ++i) {
-    nx.child_off[i] = nx.n[i / J];
-    nx.n[i / J] += rank[i];
+    nx.child_off[i] = nx.n[nx.parent[i]];
+    nx.n[nx.parent[i]] += rank[i];
   }
   std::vector<std::pair<int, int>> pr;
   for (size_t p = 0; p < P.pair_i.size(); ++p) {
     int i = P.pair_i[p], k = P.pair_k[p];
     if (rank[i] == 0 || rank[k] == 0) continue;
-    pr.emplace_back(i / J, k / J);
+    pr.emplace_back(nx.parent[i], nx.parent[k]);
   }
   std::sort(pr.begin(), pr.end());
   pr.erase(std::unique(pr.begin(), pr.end()), pr.end());

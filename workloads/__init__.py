@@ -15,4 +15,6 @@ from .grids import (  # noqa: F401
     Workload,
     make_workload,
     WORKLOADS,
+    BATCH_SIDES,
+    make_batch,
 )
