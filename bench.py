@@ -3,7 +3,9 @@
 
 One step = ce_factorize + pcg_solve of the 2D Poisson 512x512 system (B = 32,
 tol 1e-4, 4 levels, J = 4) with the matrix and right-hand side resident in
-HBM.  The chosen form (learned ranks with a randomized range finder, FP32
+HBM.  ``--workload poisson2d_batch256`` times instead 256 independent 2D
+Poisson systems (sides drawn from {64, 96, 128, 192, 256}) factorized as one
+block-diagonal batch and solved by the per-system batched PCG.  The chosen form (learned ranks with a randomized range finder, FP32
 blocks and compression, FP64 PCG) is the headline value; the plain FP64 form
 (exact SVD) is timed beside it.  The rank model is trained on the GPU before
 the timed region.  Prints one JSON line.
@@ -32,6 +34,8 @@ import workloads as wl  # noqa: E402
 
 METRIC = "time to 1e-8 residual (factor+PCG)"
 WORKLOAD = "poisson2d_512_B32"
+BATCH = "poisson2d_batch256"
+BATCH_SYSTEMS = 256
 SAMPLE_GRID = 128        # oracle sample: 128x128 grid of the same kind
 RTOL = 1e-8
 PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
@@ -107,6 +111,62 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------------
+class Problem:
+    """One system, or a batch of independent ones, with its parameters."""
+
+    def __init__(self, name):
+        self.name = name
+        self.batched = name == BATCH
+        if self.batched:
+            self.ws = wl.make_batch(BATCH_SYSTEMS, seed=0)
+            w0 = self.ws[0]
+            self.tol, self.levels, self.J = w0.tol, w0.levels, w0.J
+            self.B = "16 (sides <= 96) / 32"
+            self.desc = (f"{BATCH_SYSTEMS} independent 2D Poisson 5-point systems, sides drawn "
+                         f"from {list(wl.BATCH_SIDES)}, Dirichlet")
+        else:
+            w = wl.make_workload(name)
+            self.ws = [w]
+            self.tol, self.levels, self.J, self.B, self.desc = w.tol, w.levels, w.J, w.B, w.desc
+        self.sizes = [w.A.shape[0] for w in self.ws]
+        self.off = np.concatenate([[0], np.cumsum(self.sizes)]).astype(np.int64)
+        self.N = int(self.off[-1])
+        self.b = np.concatenate([w.b for w in self.ws])
+
+    def host_arrays(self):
+        """Host arrays a user hands to the library (CSR, permutation, blocks)."""
+        import paper_1603_09133_gb300 as ceg
+        if self.batched:
+            return ceg.stack_systems([(w.A, w.perm, w.B) for w in self.ws])
+        w = self.ws[0]
+        A = w.A.tocsr()
+        return (np.ascontiguousarray(A.indptr, np.int64), np.ascontiguousarray(A.indices, np.int32),
+                np.ascontiguousarray(A.data, np.float64), np.ascontiguousarray(w.perm, np.int32),
+                w.B)
+
+    def build(self, arrays):
+        import paper_1603_09133_gb300 as ceg
+        if self.batched:
+            return ceg.csb_build_batched_csr(*arrays)
+        rp, ci, va, pm, B = arrays
+        import scipy.sparse as sp
+        A = sp.csr_matrix((va, ci, rp), shape=(self.N, self.N))
+        return ceg.csb_build(A, pm, B)
+
+    def solve(self, csb, F, b, x):
+        """PCG to RTOL; returns (max iterations, all converged)."""
+        import paper_1603_09133_gb300 as ceg
+        if self.batched:
+            its, rel, conv = ceg.pcg_solve_batched(csb, F, b, x, RTOL, 1000)
+            return int(its.max()), bool(conv.all())
+        it, rel, conv = ceg.pcg_solve(csb, F, b, x, RTOL, 1000)
+        return it, conv
+
+    def true_relres(self, x):
+        return max(float(np.linalg.norm(w.b - w.A @ x[self.off[s]:self.off[s + 1]])
+                         / np.linalg.norm(w.b)) for s, w in enumerate(self.ws))
+
+
 def oracle_time(w, grid, levels):
     """Oracle factorize + PCG on a grid x grid sample of the same kind (s)."""
     from oracle import ce as oce
@@ -122,37 +182,52 @@ def oracle_time(w, grid, levels):
     return t1 - t0, A.shape[0], res.iters
 
 
-def cpu_baseline(w, levels):
+def oracle_sample(pb):
+    """(seconds, unknowns, PCG iterations, what) of one bounded oracle run."""
+    if pb.batched:
+        # one 64x64 system of the batch, with the batch's own parameters
+        from oracle import ce as oce
+        w = next(w for w in pb.ws if w.A.shape[0] == 64 * 64)
+        t0 = time.perf_counter()
+        F = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J)
+        res = oce.pcg(w.A, F, w.b, RTOL, 1000)
+        t = time.perf_counter() - t0
+        assert res.converged
+        return t, w.A.shape[0], res.iters, f"one 64x64 system of the batch ({pb.levels} levels)"
+    w = pb.ws[0]
+    levels = min(w.levels, 3)
     t, n, its = oracle_time(w, SAMPLE_GRID, levels)
-    N = w.A.shape[0]
-    return {"value": t * N / n, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle on the {SAMPLE_GRID}x{SAMPLE_GRID} grid of the same "
-                      f"problem ({n} unknowns, {levels} levels, {its} PCG iterations, "
-                      f"{t:.2f} s), scaled linearly to N={N} (O(N) cost, Corollary of "
+    return t, n, its, f"the {SAMPLE_GRID}x{SAMPLE_GRID} grid of the same problem ({levels} levels)"
+
+
+def cpu_baseline(pb):
+    t, n, its, what = oracle_sample(pb)
+    return {"value": t * pb.N / n, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle on {what}: {n} unknowns, {its} PCG iterations, "
+                      f"{t:.2f} s, scaled linearly to N={pb.N} (O(N) cost, Corollary of "
                       "Section 2.7); single-threaded BLAS"}
 
 
 def run_reference(args, rank):
-    w = wl.make_workload(args.workload)
+    pb = Problem(args.workload)
     if rank != 0:
         return
-    levels = min(w.levels, 3)
     for _ in range(args.warmup):
-        oracle_time(w, SAMPLE_GRID, levels)
+        oracle_sample(pb)
     ts = []
     for _ in range(args.steps):
-        t, n, its = oracle_time(w, SAMPLE_GRID, levels)
-        ts.append(t * w.A.shape[0] / n)
+        t, n, its, what = oracle_sample(pb)
+        ts.append(t * pb.N / n)
     v = statistics.mean(ts)
     out = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
            "impl": "reference",
-           "config": {"workload": args.workload, "N": int(w.A.shape[0]), "B": w.B, "tol": w.tol,
-                      "levels": w.levels, "J": w.J},
+           "config": {"workload": args.workload, "N": pb.N, "B": pb.B, "tol": pb.tol,
+                      "levels": pb.levels, "J": pb.J},
            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                            "sample": f"each step: oracle factorize+PCG on {SAMPLE_GRID}x"
-                                      f"{SAMPLE_GRID}, scaled linearly to N"},
+                            "sample": f"each step: oracle factorize+PCG on {what}, "
+                                      "scaled linearly to N"},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -167,19 +242,20 @@ def run_ours(args, rank, world):
     lib = _lib.load()
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", 0)))
     torch.cuda.set_device(dev)
-    w = wl.make_workload(args.workload)
-    N = w.A.shape[0]
-    csb = ceg.csb_build(w.A, w.perm, w.B)
-    b = torch.as_tensor(w.b, device=dev)
+    pb = Problem(args.workload)
+    N = pb.N
+    arrays = pb.host_arrays()
+    csb = pb.build(arrays)
+    b = torch.as_tensor(pb.b, device=dev)
     x = torch.zeros_like(b)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     model = ceg.trained_rank_model() if args.ranks == "learned" else None
 
     def step(prec, rm=None):
-        F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision=prec, rank_model=rm)
-        it, rel, conv = ceg.pcg_solve(csb, F, b, x, RTOL, 1000)
-        return F, it, rel, conv
+        F = ceg.ce_factorize(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=prec, rank_model=rm)
+        it, conv = pb.solve(csb, F, b, x)
+        return F, it, conv
 
     def timed(prec, k, w_, rm=None):
         for _ in range(w_):
@@ -209,9 +285,8 @@ def run_ours(args, rank, world):
     sampler.start()
     times, last, launches = timed(args.precision, args.steps, args.warmup, model)
     clocks = sampler.stop()
-    F, it, rel, conv = last
-    xt = x.cpu().numpy()
-    true_rel = float(np.linalg.norm(w.b - w.A @ xt) / np.linalg.norm(w.b))
+    F, it, conv = last
+    true_rel = pb.true_relres(x.cpu().numpy())
     ms = statistics.mean(times)
     if world > 1:
         tt = torch.tensor([ms], device=dev)
@@ -235,24 +310,19 @@ def run_ours(args, rank, world):
                 if args.precision == "fp32" else "GB300 nominal FP64"}
 
     # end to end through the public API with host buffers
-    A = w.A.tocsr()
-    rp = np.ascontiguousarray(A.indptr, np.int64)
-    ci = np.ascontiguousarray(A.indices, np.int32)
-    va = np.ascontiguousarray(A.data, np.float64)
-    pm = np.ascontiguousarray(w.perm, np.int32)
-    b_host = torch.as_tensor(w.b).pin_memory()
+    b_host = torch.as_tensor(pb.b).pin_memory()
     x_host = torch.empty(N, dtype=torch.float64).pin_memory()
     e2e_t = []
     for k in range(args.warmup + args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        csb2 = ceg.csb_build(A, pm, w.B)
-        F2 = ceg.ce_factorize(csb2, tol=w.tol, levels=w.levels, J=w.J, precision=args.precision,
+        csb2 = pb.build(arrays)
+        F2 = ceg.ce_factorize(csb2, tol=pb.tol, levels=pb.levels, J=pb.J, precision=args.precision,
                               rank_model=model)
         bd = b_host.to(dev, non_blocking=True)
         xd = torch.empty_like(bd)
-        ceg.pcg_solve(csb2, F2, bd, xd, RTOL, 1000)
+        pb.solve(csb2, F2, bd, xd)
         x_host.copy_(xd, non_blocking=True)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
@@ -260,7 +330,7 @@ def run_ours(args, rank, world):
         csb2.close()
         if k >= args.warmup:
             e2e_t.append(t1 - t0)
-    h2d = rp.nbytes + ci.nbytes + va.nbytes + pm.nbytes + w.b.nbytes
+    h2d = sum(a.nbytes for a in arrays if isinstance(a, np.ndarray)) + pb.b.nbytes
     e2e = {"value": statistics.mean(e2e_t), "unit": "s", "h2d_bytes_per_step": int(h2d),
            "d2h_bytes_per_step": int(N * 8)}
 
@@ -276,8 +346,9 @@ def run_ours(args, rank, world):
            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
            "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-           "config": {"workload": args.workload, "desc": w.desc, "N": int(N), "B": w.B,
-                      "tol": w.tol, "levels": w.levels, "J": w.J,
+           "config": {"workload": args.workload, "desc": pb.desc, "N": int(N), "B": pb.B,
+                      "tol": pb.tol, "levels": pb.levels, "J": pb.J,
+                      "systems": len(pb.ws),
                       "form": f"{args.ranks} ranks + {args.precision} factor + fp64 PCG",
                       "pcg_iters": it, "final_relres": true_rel,
                       "plain_fp64_form_s": statistics.mean(t_other) / 1e3,
@@ -290,7 +361,7 @@ def run_ours(args, rank, world):
                       "levels_detail": levels_cfg},
            "clocks": clocks, "e2e": e2e, "gpu_launches": launches, "roofline": roofline}
     if not args.no_baseline and world == 1:
-        out["cpu_baseline"] = cpu_baseline(w, min(w.levels, 3))
+        out["cpu_baseline"] = cpu_baseline(pb)
     print(json.dumps(out), flush=True)
 
 

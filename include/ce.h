@@ -100,6 +100,10 @@ typedef struct {
   double coarse_ms;    /* dense assembly + Cholesky of A_K               */
   int learned_rows[16];  /* CE_RANK_LEARNED: rows whose sketch was accepted */
   int fallback_rows[16]; /* ... and rows sent to the exact SVD             */
+  double host_ms[16];  /* host time of level l while the GPU waits: its
+                          metadata upload, then the planning of level l+1
+                          (coarsening, pattern, colouring, reassembly)    */
+  double total_ms;     /* wall time of the whole call                     */
 } ce_info;
 
 typedef struct {

@@ -167,30 +167,45 @@ def csb_build(A, perm, B: int) -> CSB:
     return CSB(h, n, int(B))
 
 
-def csb_build_batched(systems) -> CSB:
-    """Many independent systems [(A, perm, B), ...] as one block-diagonal
-    batch; rows are stacked in the order given."""
+def stack_systems(systems):
+    """Stacked CSR arrays of independent systems [(A, perm, B), ...] in the
+    layout csb_build_batched_csr takes: (row_off, rowptr, col, val, perm, Bs)."""
     import scipy.sparse as sp
-    lib = _lib.load()
     mats = [sp.csr_matrix(A) for A, _, _ in systems]
-    sizes = [m.shape[0] for m in mats]
     row_off = np.zeros(len(mats) + 1, np.int64)
-    row_off[1:] = np.cumsum(sizes)
+    row_off[1:] = np.cumsum([m.shape[0] for m in mats])
     S = sp.block_diag(mats, format="csr")
     pm = np.concatenate([np.asarray(p, np.int64) + row_off[s]
                          for s, (_, p, _) in enumerate(systems)]).astype(np.int32)
-    Bs = np.asarray([B for _, _, B in systems], np.int32)
-    rowptr = np.ascontiguousarray(S.indptr, dtype=np.int64)
-    col = np.ascontiguousarray(S.indices, dtype=np.int32)
-    val = np.ascontiguousarray(S.data, dtype=np.float64)
+    return (row_off, np.ascontiguousarray(S.indptr, dtype=np.int64),
+            np.ascontiguousarray(S.indices, dtype=np.int32),
+            np.ascontiguousarray(S.data, dtype=np.float64), pm,
+            np.asarray([B for _, _, B in systems], np.int32))
+
+
+def csb_build_batched_csr(row_off, rowptr, col, val, perm, Bs) -> CSB:
+    """csb_build_batched on stacked host arrays (see stack_systems)."""
+    lib = _lib.load()
+    row_off = np.ascontiguousarray(row_off, np.int64)
+    rowptr = np.ascontiguousarray(rowptr, np.int64)
+    col = np.ascontiguousarray(col, np.int32)
+    val = np.ascontiguousarray(val, np.float64)
+    perm = np.ascontiguousarray(perm, np.int32)
+    Bs = np.ascontiguousarray(Bs, np.int32)
     h = C.c_void_p()
-    _check(lib.csb_build_batched(len(mats), row_off.ctypes.data_as(_lib.I64P),
+    _check(lib.csb_build_batched(len(row_off) - 1, row_off.ctypes.data_as(_lib.I64P),
                                  rowptr.ctypes.data_as(_lib.I64P), col.ctypes.data_as(_lib.I32P),
-                                 val.ctypes.data_as(_lib.DP), pm.ctypes.data_as(_lib.I32P),
+                                 val.ctypes.data_as(_lib.DP), perm.ctypes.data_as(_lib.I32P),
                                  Bs.ctypes.data_as(_lib.I32P), C.byref(h)), "csb_build_batched")
     csb = CSB(h, int(row_off[-1]), int(Bs[0]))
     csb.row_off = row_off
     return csb
+
+
+def csb_build_batched(systems) -> CSB:
+    """Many independent systems [(A, perm, B), ...] as one block-diagonal
+    batch; rows are stacked in the order given."""
+    return csb_build_batched_csr(*stack_systems(systems))
 
 
 def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",

@@ -61,6 +61,8 @@ class ce_info(C.Structure):
         ("coarse_ms", C.c_double),
         ("learned_rows", C.c_int * 16),
         ("fallback_rows", C.c_int * 16),
+        ("host_ms", C.c_double * 16),
+        ("total_ms", C.c_double),
     ]
 
 

@@ -2,6 +2,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cstdio>
 #include <cmath>
 #include <cstring>
@@ -74,30 +76,81 @@ void dfree(void* p, cudaStream_t s) {
   if (p) cudaFreeAsync(p, s);
 }
 
-// Packs host arrays into one device allocation (one H2D copy).
+// Pinned host staging buffers for the uploads of a factorization (grow-only,
+// one pair per host thread).  Slot 0 carries level metadata, slot 1 copy
+// tasks; a slot is reused only after its last copy has completed.
+struct Staging {
+  char* p = nullptr;
+  size_t cap = 0;
+  cudaEvent_t ev = nullptr;
+  bool pending = false;
+};
+thread_local Staging g_stage[2];
+
+char* stage_get(int slot, size_t bytes) {
+  Staging& S = g_stage[slot];
+  if (S.pending) {
+    check(cudaEventSynchronize(S.ev), "staging wait");
+    S.pending = false;
+  }
+  if (!S.ev) check(cudaEventCreateWithFlags(&S.ev, cudaEventDisableTiming), "event");
+  if (bytes > S.cap) {
+    if (S.p) cudaFreeHost(S.p);
+    S.p = nullptr;
+    S.cap = 0;
+    const size_t cap = ((std::max(bytes, size_t(1) << 20) + (size_t(1) << 20) - 1) >> 20) << 20;
+    check(cudaHostAlloc(reinterpret_cast<void**>(&S.p), cap, cudaHostAllocDefault), "cudaHostAlloc");
+    S.cap = cap;
+  }
+  return S.p;
+}
+
+void stage_upload(int slot, void* dst, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) return;
+  check(cudaMemcpyAsync(dst, g_stage[slot].p, bytes, cudaMemcpyHostToDevice, s), "H2D");
+  check(cudaEventRecord(g_stage[slot].ev, s), "event");
+  g_stage[slot].pending = true;
+}
+
+// Lays host arrays out in one device allocation: arrays first (one H2D copy
+// through the staging buffer), zero-filled regions last (one memset).
 struct Packer {
-  std::vector<char> host;
+  struct Item {
+    size_t off;
+    const void* src;
+    size_t bytes;
+  };
+  std::vector<Item> items;
+  size_t size = 0, data_end = 0;
+  static size_t align(size_t x) { return (x + 255) & ~size_t(255); }
   size_t add(const void* src, size_t bytes) {
-    size_t off = (host.size() + 255) & ~size_t(255);
-    host.resize(off + bytes);
-    if (bytes && src) std::memcpy(host.data() + off, src, bytes);
+    const size_t off = align(size);
+    items.push_back({off, src, bytes});
+    size = data_end = off + bytes;
     return off;
   }
   template <typename V>
   size_t addv(const std::vector<V>& v) {
     return add(v.data(), v.size() * sizeof(V));
   }
-  size_t zeros(size_t bytes) { return add(nullptr, bytes); }
+  size_t zeros(size_t bytes) {  // after every add()
+    const size_t off = align(size);
+    size = off + bytes;
+    return off;
+  }
+  void upload(void* dst, cudaStream_t s) {
+    char* h = stage_get(0, data_end);
+    ce::parallel_for(static_cast<int64_t>(items.size()), 1, [&](int64_t b, int64_t e) {
+      for (int64_t t = b; t < e; ++t)
+        if (items[t].bytes) std::memcpy(h + items[t].off, items[t].src, items[t].bytes);
+    });
+    stage_upload(0, dst, data_end, s);
+    if (size > data_end)
+      check(cudaMemsetAsync(static_cast<char*>(dst) + data_end, 0, size - data_end, s), "memset metadata");
+  }
 };
 
-int64_t pair_offset(const LevelPlan& P, int a, int b) {
-  if (a > b) std::swap(a, b);
-  auto lo = std::lower_bound(P.pair_i.begin(), P.pair_i.end(), a) - P.pair_i.begin();
-  auto hi = std::upper_bound(P.pair_i.begin(), P.pair_i.end(), a) - P.pair_i.begin();
-  auto it = std::lower_bound(P.pair_k.begin() + lo, P.pair_k.begin() + hi, b);
-  if (it == P.pair_k.begin() + hi || *it != b) return -1;
-  return P.pair_off[it - P.pair_k.begin()];
-}
+int64_t pair_offset(const LevelPlan& P, int a, int b) { return ce::find_pair(P, a, b); }
 
 // Algorithmic flops and bytes of the row-kernel launches of one level,
 // counted per block from its size n, rank r (m = n - r) and the widths w of
@@ -121,9 +174,8 @@ void level_work(const LevelPlan& P, const std::vector<int>& rank, int es, double
     auto wid = [&](int k) { return double(P.colour[k] < ci ? rank[k] : P.n[k]); };
     double mF = 0, Wc = 0, W2 = 0, pairs = 0;
     for (int f = P.far_ptr[i]; f < P.far_ptr[i + 1]; ++f) mF += wid(P.far_blk[f]);
-    std::vector<double> w;
-    for (int t = P.close_ptr[i]; t < P.close_ptr[i + 1]; ++t) w.push_back(wid(P.close_blk[t]));
-    for (double x : w) {
+    for (int t = P.close_ptr[i]; t < P.close_ptr[i + 1]; ++t) {
+      const double x = wid(P.close_blk[t]);
       Wc += x;
       W2 += x * x;
     }
@@ -143,20 +195,26 @@ std::vector<std::pair<int, int>> block_pairs(const int64_t* rowptr, const int32_
                                              const std::vector<int64_t>& blkptr,
                                              const std::vector<int>& blk_of) {
   const int M = static_cast<int>(blkptr.size()) - 1;
-  std::vector<std::pair<int, int>> pairs;
-  std::vector<int> nb;
-  for (int bi = 0; bi < M; ++bi) {
-    nb.clear();
-    for (int64_t r = blkptr[bi]; r < blkptr[bi + 1]; ++r) {
-      const int a = perm[r];
-      for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
-        const int bk = blk_of[iperm[col[e]]];
-        if (bk >= bi && std::find(nb.begin(), nb.end(), bk) == nb.end()) nb.push_back(bk);
+  const int nch = std::max(1, std::min(ce::host_threads() * 4, (M + 1023) / 1024));
+  std::vector<std::vector<std::pair<int, int>>> part(nch);
+  ce::parallel_for(nch, 1, [&](int64_t c0, int64_t c1) {
+    std::vector<int> nb;
+    for (int64_t c = c0; c < c1; ++c)
+      for (int bi = static_cast<int>((int64_t)M * c / nch); bi < (int64_t)M * (c + 1) / nch; ++bi) {
+        nb.clear();
+        for (int64_t r = blkptr[bi]; r < blkptr[bi + 1]; ++r) {
+          const int a = perm[r];
+          for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
+            const int bk = blk_of[iperm[col[e]]];
+            if (bk >= bi && std::find(nb.begin(), nb.end(), bk) == nb.end()) nb.push_back(bk);
+          }
+        }
+        std::sort(nb.begin(), nb.end());
+        for (int bk : nb) part[c].emplace_back(bi, bk);
       }
-    }
-    std::sort(nb.begin(), nb.end());
-    for (int bk : nb) pairs.emplace_back(bi, bk);
-  }
+  });
+  std::vector<std::pair<int, int>> pairs;
+  for (auto& v : part) pairs.insert(pairs.end(), v.begin(), v.end());
   return pairs;
 }
 
@@ -165,16 +223,26 @@ std::vector<std::pair<int, int>> block_pairs(const int64_t* rowptr, const int32_
 bool csr_symmetric(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val) {
   const int64_t nnz = rowptr[n];
   std::vector<std::pair<int32_t, double>> cv(nnz);
-  for (int64_t e = 0; e < nnz; ++e) cv[e] = {col[e], val[e]};
-  for (int64_t a = 0; a < n; ++a) std::sort(cv.begin() + rowptr[a], cv.begin() + rowptr[a + 1]);
-  for (int64_t a = 0; a < n; ++a)
-    for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
-      const int32_t b = cv[e].first;
-      auto lo = cv.begin() + rowptr[b], hi = cv.begin() + rowptr[b + 1];
-      auto it = std::lower_bound(lo, hi, std::make_pair((int32_t)a, -1e308));
-      if (it == hi || it->first != a || it->second != cv[e].second) return false;
+  ce::parallel_for(n, 8192, [&](int64_t a0, int64_t a1) {
+    for (int64_t a = a0; a < a1; ++a) {
+      for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) cv[e] = {col[e], val[e]};
+      std::sort(cv.begin() + rowptr[a], cv.begin() + rowptr[a + 1]);
     }
-  return true;
+  });
+  std::atomic<bool> ok{true};
+  ce::parallel_for(n, 8192, [&](int64_t a0, int64_t a1) {
+    for (int64_t a = a0; a < a1 && ok.load(std::memory_order_relaxed); ++a)
+      for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
+        const int32_t b = cv[e].first;
+        auto lo = cv.begin() + rowptr[b], hi = cv.begin() + rowptr[b + 1];
+        auto it = std::lower_bound(lo, hi, std::make_pair((int32_t)a, -1e308));
+        if (it == hi || it->first != a || it->second != cv[e].second) {
+          ok.store(false);
+          break;
+        }
+      }
+  });
+  return ok.load();
 }
 
 int max_targets(const LevelPlan& P) {
@@ -185,20 +253,19 @@ int max_targets(const LevelPlan& P) {
 
 // Upload the metadata of a level plan and allocate its factor storage.
 void build_level_store(LevelStore& st, int esize, cudaStream_t s) {
-  const LevelPlan& P = st.plan;
+  const LevelPlan& P = *st.plan;
   Packer pk;
-  const size_t o_n = pk.addv(P.n), o_col = pk.addv(P.colour), o_rank = pk.zeros(P.M * sizeof(int)),
-               o_order = pk.addv(P.order), o_cp = pk.addv(P.close_ptr), o_cb = pk.addv(P.close_blk),
-               o_co = pk.addv(P.close_off), o_fp = pk.addv(P.far_ptr), o_fb = pk.addv(P.far_blk),
-               o_fo = pk.addv(P.far_off), o_do = pk.addv(P.diag_off), o_sp = pk.addv(P.schur_ptr),
-               o_so = pk.addv(P.schur_off), o_uo = pk.addv(P.u_off), o_lo = pk.addv(P.l_off),
-               o_wo = pk.addv(P.w_off), o_vo = pk.addv(P.vec_off),
+  const size_t o_n = pk.addv(P.n), o_col = pk.addv(P.colour), o_order = pk.addv(P.order),
+               o_cp = pk.addv(P.close_ptr), o_cb = pk.addv(P.close_blk), o_co = pk.addv(P.close_off),
+               o_fp = pk.addv(P.far_ptr), o_fb = pk.addv(P.far_blk), o_fo = pk.addv(P.far_off),
+               o_do = pk.addv(P.diag_off), o_sp = pk.addv(P.schur_ptr), o_so = pk.addv(P.schur_off),
+               o_uo = pk.addv(P.u_off), o_lo = pk.addv(P.l_off), o_wo = pk.addv(P.w_off),
+               o_vo = pk.addv(P.vec_off), o_rank = pk.zeros(P.M * sizeof(int)),
                o_gd = pk.zeros(P.M * sizeof(int64_t)), o_tau = pk.zeros(P.M * sizeof(double)),
                o_sig = pk.zeros(P.vec_len * sizeof(double));
-  st.meta_bytes = pk.host.size();
+  st.meta_bytes = pk.size;
   st.meta = dalloc(st.meta_bytes, s);
-  check(cudaMemcpyAsync(st.meta, pk.host.data(), st.meta_bytes, cudaMemcpyHostToDevice, s),
-        "upload level metadata");
+  pk.upload(st.meta, s);
   char* b = static_cast<char*>(st.meta);
   LevelDev& D = st.dev;
   D.M = P.M;
@@ -235,30 +302,41 @@ void build_level_store(LevelStore& st, int esize, cudaStream_t s) {
 // copy tasks: level pairs (kept corners) -> next level pairs
 std::vector<CopyTask> reassembly_tasks(const LevelPlan& P, const std::vector<int>& rank, int J,
                                        const ce::NextLevel& nx, const LevelPlan& Pn) {
-  std::vector<CopyTask> tasks;
-  for (size_t p = 0; p < P.pair_i.size(); ++p) {
-    const int i = P.pair_i[p], k = P.pair_k[p];
-    if (rank[i] == 0 || rank[k] == 0) continue;
-    const int I = nx.parent[i], K = nx.parent[k];
-    const int64_t dst = pair_offset(Pn, I, K);
-    CopyTask t;
-    t.src_off = P.pair_off[p];
-    t.src_ld = P.n[k];
-    t.rows = rank[i];
-    t.cols = rank[k];
-    t.dst_off = dst;
-    t.dst_ld = Pn.n[K];
-    t.r0 = nx.child_off[i];
-    t.c0 = nx.child_off[k];
-    t.transpose = 0;
-    tasks.push_back(t);
-    if (I == K && i != k) {
-      t.r0 = nx.child_off[k];
-      t.c0 = nx.child_off[i];
-      t.transpose = 1;
-      tasks.push_back(t);
+  const int64_t np = static_cast<int64_t>(P.pair_i.size());
+  const int nch = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ce::host_threads() * 4, np / 8192)));
+  std::vector<std::vector<CopyTask>> part(nch);
+  ce::parallel_for(nch, 1, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; ++c) {
+      std::vector<CopyTask>& tasks = part[c];
+      for (int64_t p = np * c / nch; p < np * (c + 1) / nch; ++p) {
+        const int i = P.pair_i[p], k = P.pair_k[p];
+        if (rank[i] == 0 || rank[k] == 0) continue;
+        const int I = nx.parent[i], K = nx.parent[k];
+        CopyTask t;
+        t.src_off = P.pair_off[p];
+        t.src_ld = P.n[k];
+        t.rows = rank[i];
+        t.cols = rank[k];
+        t.dst_off = pair_offset(Pn, I, K);
+        t.dst_ld = Pn.n[K];
+        t.r0 = nx.child_off[i];
+        t.c0 = nx.child_off[k];
+        t.transpose = 0;
+        tasks.push_back(t);
+        if (I == K && i != k) {
+          t.r0 = nx.child_off[k];
+          t.c0 = nx.child_off[i];
+          t.transpose = 1;
+          tasks.push_back(t);
+        }
+      }
     }
-  }
+  });
+  std::vector<CopyTask> tasks;
+  size_t tot = 0;
+  for (auto& v : part) tot += v.size();
+  tasks.reserve(tot);
+  for (auto& v : part) tasks.insert(tasks.end(), v.begin(), v.end());
   return tasks;
 }
 
@@ -324,9 +402,10 @@ std::vector<CopyTask> dense_tasks(const LevelPlan& P, const CoarseSystems& C) {
 void run_copy_tasks(const std::vector<CopyTask>& tasks, int es, int ed, const void* src, void* dst,
                     cudaStream_t s) {
   if (tasks.empty()) return;
-  void* dt = dalloc(tasks.size() * sizeof(CopyTask), s);
-  check(cudaMemcpyAsync(dt, tasks.data(), tasks.size() * sizeof(CopyTask), cudaMemcpyHostToDevice, s),
-        "upload copy tasks");
+  const size_t bytes = tasks.size() * sizeof(CopyTask);
+  void* dt = dalloc(bytes, s);
+  std::memcpy(stage_get(1, bytes), tasks.data(), bytes);
+  stage_upload(1, dt, bytes, s);
   check(ce::launch_copy_tasks(es, ed, static_cast<const CopyTask*>(dt), (int)tasks.size(), src, dst, s),
         "copy tasks");
   dfree(dt, s);
@@ -510,17 +589,20 @@ ce_status build_csb(int64_t n, const int64_t* rowptr, const int32_t* col, const 
   A->nsys = static_cast<int>(sys_row.size()) - 1;
   A->sys_row = sys_row;
   try {
-    ce::plan_level(A->plan1, sizes, pairs, true);
-    A->plan1.sys_off = sys_blk;
+    A->plan1 = std::make_shared<LevelPlan>();
+    ce::plan_level(*A->plan1, sizes, pairs, true, sys_blk);
+    const LevelPlan& P1 = *A->plan1;
     std::vector<int64_t> scatter(nnz, -1);
-    for (int64_t a = 0; a < n; ++a)
-      for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
-        const int pa = iperm[a], pb = iperm[col[e]];
-        const int bi = blk_of[pa], bk = blk_of[pb];
-        if (bi > bk) continue;
-        const int64_t po = pair_offset(A->plan1, bi, bk);
-        scatter[e] = po + (int64_t)(pa - blkptr[bi]) * A->plan1.n[bk] + (pb - blkptr[bk]);
-      }
+    ce::parallel_for(n, 8192, [&](int64_t a0, int64_t a1) {
+      for (int64_t a = a0; a < a1; ++a)
+        for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
+          const int pa = iperm[a], pb = iperm[col[e]];
+          const int bi = blk_of[pa], bk = blk_of[pb];
+          if (bi > bk) continue;
+          const int64_t po = pair_offset(P1, bi, bk);
+          scatter[e] = po + (int64_t)(pa - blkptr[bi]) * P1.n[bk] + (pb - blkptr[bk]);
+        }
+    });
     std::vector<int32_t> sys_of_row(n);
     for (int s2 = 0; s2 < A->nsys; ++s2)
       for (int64_t r = sys_row[s2]; r < sys_row[s2 + 1]; ++r) sys_of_row[r] = s2;
@@ -650,12 +732,12 @@ ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col, c
   return CE_OK;
 }
 
-int csb_blocks(const ce_csb* A) { return A ? A->plan1.M : 0; }
+int csb_blocks(const ce_csb* A) { return A ? A->plan1->M : 0; }
 
 ce_status csb_get_colours(const ce_csb* A, int32_t* colour, int* ncolours) {
   if (!A) return CE_ERR_INVALID_ARG;
-  if (colour) std::copy(A->plan1.colour.begin(), A->plan1.colour.end(), colour);
-  if (ncolours) *ncolours = A->plan1.ncolours;
+  if (colour) std::copy(A->plan1->colour.begin(), A->plan1->colour.end(), colour);
+  if (ncolours) *ncolours = A->plan1->ncolours;
   return CE_OK;
 }
 
@@ -671,6 +753,11 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
     return CE_ERR_INVALID_ARG;
   *out = nullptr;
   if (info) std::memset(info, 0, sizeof(*info));
+  using clk = std::chrono::steady_clock;
+  auto ms_since = [](clk::time_point t) {
+    return std::chrono::duration<double, std::milli>(clk::now() - t).count();
+  };
+  const clk::time_point t_call = clk::now();
   cudaStream_t s = static_cast<cudaStream_t>(o.stream);
   init_pool_once();
   ce_factor* F = new (std::nothrow) ce_factor();
@@ -691,32 +778,36 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
     la.J = o.J;
     la.seed = o.seed;
     la.stats = F->d_status + ce::kStatusWords;
-    LevelPlan cur;
+    std::shared_ptr<const LevelPlan> curp;
     if (o.coloring) {
-      cur = A->plan1;
+      curp = A->plan1;
     } else {
+      const LevelPlan& P1 = *A->plan1;
       std::vector<std::pair<int, int>> pr;
-      for (size_t p = 0; p < A->plan1.pair_i.size(); ++p)
-        if (A->plan1.pair_close[p]) pr.emplace_back(A->plan1.pair_i[p], A->plan1.pair_k[p]);
-      ce::plan_level(cur, A->plan1.n, pr, false);
-      cur.sys_off = A->plan1.sys_off;
+      for (size_t p = 0; p < P1.pair_i.size(); ++p)
+        if (P1.pair_close[p]) pr.emplace_back(P1.pair_i[p], P1.pair_k[p]);
+      auto np = std::make_shared<LevelPlan>();
+      ce::plan_level(*np, P1.n, pr, false, P1.sys_off);
+      curp = np;
     }
-    pool = dalloc(cur.pool_elems * es, s);
-    check(cudaMemsetAsync(pool, 0, cur.pool_elems * es, s), "memset pool");
+    pool = dalloc(curp->pool_elems * es, s);
+    check(cudaMemsetAsync(pool, 0, curp->pool_elems * es, s), "memset pool");
     check(ce::launch_scatter_csr(es, A->d_scatter, A->d_val, A->nnz, pool, s), "scatter");
     int hstatus[ce::kStatusWords];
-    for (int l = 0; l < o.levels && cur.M > 0; ++l) {
-      if (cur.nmax > ce::kNMax || max_targets(cur) > 32) {
+    for (int l = 0; l < o.levels && curp->M > 0; ++l) {
+      if (curp->nmax > ce::kNMax || max_targets(*curp) > 32) {
         ret = CE_ERR_LIMIT;
         if (info) info->err_level = l;
         break;
       }
+      clk::time_point t_host = clk::now();
       F->levels.emplace_back();
       LevelStore& st = F->levels.back();
-      st.plan = std::move(cur);
+      st.plan = curp;
       build_level_store(st, es, s);
       st.dev.pool = pool;
-      const LevelPlan& P = st.plan;
+      const double host_ms = ms_since(t_host);
+      const LevelPlan& P = *st.plan;
       cudaEvent_t ev0, ev1;
       check(cudaEventCreate(&ev0), "event");
       check(cudaEventCreate(&ev1), "event");
@@ -731,6 +822,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       check(cudaMemcpyAsync(st.rank.data(), st.dev.rank, P.M * sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
       check(cudaMemcpyAsync(hstatus, F->d_status, sizeof(hstatus), cudaMemcpyDeviceToHost, s), "D2H");
       check(cudaStreamSynchronize(s), "level sync");
+      t_host = clk::now();
       float lms = 0.f;
       cudaEventElapsedTime(&lms, ev0, ev1);
       cudaEventDestroy(ev0);
@@ -752,9 +844,9 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       }
       // coarsen (Section 2.4) and plan the next level
       ce::NextLevel nx = ce::coarsen(P, st.rank, o.J);
-      LevelPlan nxt;
-      ce::plan_level(nxt, nx.n, nx.pairs, o.coloring != 0);
-      nxt.sys_off = nx.sys_off;
+      auto nxtp = std::make_shared<LevelPlan>();
+      LevelPlan& nxt = *nxtp;
+      ce::plan_level(nxt, nx.n, nx.pairs, o.coloring != 0, nx.sys_off);
       std::vector<int64_t> gd(P.M);
       for (int i = 0; i < P.M; ++i) gd[i] = nxt.vec_off[nx.parent[i]] + nx.child_off[i];
       check(cudaMemcpyAsync(st.dev.gdst, gd.data(), P.M * sizeof(int64_t), cudaMemcpyHostToDevice, s), "H2D");
@@ -764,11 +856,13 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       dfree(pool, s);
       pool = npool;
       st.dev.pool = nullptr;
-      cur = std::move(nxt);
+      curp = nxtp;
+      if (info && l < 16) info->host_ms[l] = host_ms + ms_since(t_host);
     }
     int64_t coarse_elems = 0;
     if (ret == CE_OK) {
       // dense remainder A_K and its Cholesky factor (FP64)
+      const LevelPlan& cur = *curp;
       F->nc = static_cast<int>(cur.vec_len);
       const CoarseSystems C = coarse_systems(cur);
       F->nsys = static_cast<int>(C.nc.size());
@@ -823,7 +917,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       int64_t tot = 0;
       for (auto& st : F->levels) {
         F->vec_base.push_back(tot);
-        tot += st.plan.vec_len;
+        tot += st.plan->vec_len;
       }
       F->coarse_base = tot;
       tot += F->nc;
@@ -843,9 +937,9 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
         info->coarse_n = F->nc;
         info->factor_bytes = bytes;
         for (size_t l = 0; l < F->levels.size() && l < 16; ++l) {
-          info->blocks[l] = F->levels[l].plan.M;
-          info->colours[l] = F->levels[l].plan.ncolours;
-          info->max_block[l] = F->levels[l].plan.nmax;
+          info->blocks[l] = F->levels[l].plan->M;
+          info->colours[l] = F->levels[l].plan->ncolours;
+          info->max_block[l] = F->levels[l].plan->nmax;
         }
       }
     }
@@ -864,6 +958,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
     return ret;
   }
   *out = F;
+  if (info) info->total_ms = ms_since(t_call);
   return CE_OK;
 }
 
@@ -903,9 +998,9 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev, void*
       const LevelStore& st = F->levels[l];
       double* v = F->d_work + F->vec_base[l];
       double* vn = (l + 1 < nl) ? F->d_work + F->vec_base[l + 1] : coarse;
-      for (int c = 0; c < st.plan.ncolours; ++c)
-        check(ce::launch_apply_fwd(es, st.dev, st.plan.colour_ptr[c],
-                                   st.plan.colour_ptr[c + 1] - st.plan.colour_ptr[c], st.plan.nmax, v, s),
+      for (int c = 0; c < st.plan->ncolours; ++c)
+        check(ce::launch_apply_fwd(es, st.dev, st.plan->colour_ptr[c],
+                                   st.plan->colour_ptr[c + 1] - st.plan->colour_ptr[c], st.plan->nmax, v, s),
               "apply fwd");
       check(ce::launch_level_move(st.dev, v, vn, 1, s), "level move");
     }
@@ -919,9 +1014,9 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev, void*
       double* v = F->d_work + F->vec_base[l];
       double* vn = (l + 1 < nl) ? F->d_work + F->vec_base[l + 1] : coarse;
       check(ce::launch_level_move(st.dev, v, vn, 0, s), "level move");
-      for (int c = st.plan.ncolours - 1; c >= 0; --c)
-        check(ce::launch_apply_bwd(es, st.dev, st.plan.colour_ptr[c],
-                                   st.plan.colour_ptr[c + 1] - st.plan.colour_ptr[c], st.plan.nmax, v, s),
+      for (int c = st.plan->ncolours - 1; c >= 0; --c)
+        check(ce::launch_apply_bwd(es, st.dev, st.plan->colour_ptr[c],
+                                   st.plan->colour_ptr[c + 1] - st.plan->colour_ptr[c], st.plan->nmax, v, s),
               "apply bwd");
     }
     check(ce::launch_perm(F->d_perm, F->N, v0, z_dev, 0, s), "perm scatter");
@@ -1012,18 +1107,18 @@ int ce_factor_levels(const ce_factor* F) { return F ? static_cast<int>(F->levels
 
 int ce_factor_level_size(const ce_factor* F, int level) {
   if (!F || level < 0 || level >= static_cast<int>(F->levels.size())) return -1;
-  return F->levels[level].plan.M;
+  return F->levels[level].plan->M;
 }
 
 ce_status ce_factor_get_level(const ce_factor* F, int level, int32_t* n, int32_t* rank, int32_t* colour,
                               double* tau) {
   if (!F || level < 0 || level >= static_cast<int>(F->levels.size())) return CE_ERR_INVALID_ARG;
   const LevelStore& st = F->levels[level];
-  if (n) std::copy(st.plan.n.begin(), st.plan.n.end(), n);
+  if (n) std::copy(st.plan->n.begin(), st.plan->n.end(), n);
   if (rank) std::copy(st.rank.begin(), st.rank.end(), rank);
-  if (colour) std::copy(st.plan.colour.begin(), st.plan.colour.end(), colour);
+  if (colour) std::copy(st.plan->colour.begin(), st.plan->colour.end(), colour);
   if (tau) {
-    cudaError_t e = cudaMemcpy(tau, st.dev.tau, st.plan.M * sizeof(double), cudaMemcpyDeviceToHost);
+    cudaError_t e = cudaMemcpy(tau, st.dev.tau, st.plan->M * sizeof(double), cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
       g_last_error = cudaGetErrorString(e);
       return CE_ERR_CUDA;
@@ -1035,7 +1130,7 @@ ce_status ce_factor_get_level(const ce_factor* F, int level, int32_t* n, int32_t
 ce_status ce_factor_get_sigma(const ce_factor* F, int level, double* sigma) {
   if (!F || !sigma || level < 0 || level >= static_cast<int>(F->levels.size())) return CE_ERR_INVALID_ARG;
   const LevelStore& st = F->levels[level];
-  cudaError_t e = cudaMemcpy(sigma, st.dev.sigma, st.plan.vec_len * sizeof(double), cudaMemcpyDeviceToHost);
+  cudaError_t e = cudaMemcpy(sigma, st.dev.sigma, st.plan->vec_len * sizeof(double), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) {
     g_last_error = cudaGetErrorString(e);
     return CE_ERR_CUDA;

@@ -21,7 +21,7 @@ namespace ce {
 
 namespace {
 
-constexpr int kApplyThreads = 256;
+constexpr int kApplyThreads = 128;
 constexpr int kMaxTgt = 32;
 
 __device__ __forceinline__ double warp_sum_d(double v) {
@@ -62,57 +62,92 @@ __device__ void targets_of(const LevelDev& L, int i, int n, int r, Targets& T) {
   for (int t = 0; t < T.nt; ++t) T.pre[t + 1] = T.pre[t] + T.w[t];
 }
 
+// Every factor element is read exactly once per apply, so U_i, L_hat_i^{-1}
+// and W_i are streamed from global memory (no staging) and the arithmetic is
+// done in the factor's own precision T: the FP32 form applies its
+// preconditioner in FP32 (the level vectors stay FP64 in memory, so PCG sees
+// an FP64 operator whose error is the FP32 rounding of M^{-1}, far below the
+// compression tolerance); the FP64 form stays FP64 throughout.
+
+// 4 independent partial sums of x[k] * M[k * stride] for k in [k0, k1)
+template <typename T>
+__device__ __forceinline__ T dot_strided(const T* __restrict__ M, int stride, const T* x, int k0, int k1) {
+  T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  int k = k0;
+  for (; k + 3 < k1; k += 4) {
+    s0 += M[(int64_t)k * stride] * x[k];
+    s1 += M[(int64_t)(k + 1) * stride] * x[k + 1];
+    s2 += M[(int64_t)(k + 2) * stride] * x[k + 2];
+    s3 += M[(int64_t)(k + 3) * stride] * x[k + 3];
+  }
+  for (; k < k1; ++k) s0 += M[(int64_t)k * stride] * x[k];
+  return (s0 + s1) + (s2 + s3);
+}
+
+template <typename T>
+__device__ __forceinline__ T warp_sum_t(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
 // Forward step of block i: y_i <- U_i^T y_i; z = L_hat^{-1} y_i[r:];
 // y_t[:w_t] -= W_t^T z for every target t (basis of i first); y_i[r:] = z.
-// U_i and L_hat_i^{-1} are staged in shared memory; the W columns of all
-// targets are spread over the CTA.
 template <typename T>
 __global__ void __launch_bounds__(kApplyThreads) apply_fwd_kernel(LevelDev L, int first, double* vec) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ double ys[kNMax], yt[kNMax], z[kNMax];
+  __shared__ T ys[kNMax], yt[kNMax], z[kNMax];
+  __shared__ T part[kApplyThreads];
   __shared__ Targets tg;
   const int tid = threadIdx.x;
   const int i = L.order[first + blockIdx.x];
   const int n = L.n[i];
   if (n == 0) return;
   const int r = L.rank[i], m = n - r;
-  T* Us = reinterpret_cast<T*>(sm_raw);
-  T* Ls = Us + n * n;
   double* v = vec + L.vec_off[i];
   const T* U = reinterpret_cast<const T*>(L.U) + L.u_off[i];
   const T* Li = reinterpret_cast<const T*>(L.L) + L.l_off[i];
   const T* W = reinterpret_cast<const T*>(L.W) + L.w_off[i];
-  for (int e = tid; e < n * n; e += kApplyThreads) Us[e] = U[e];
-  for (int e = tid; e < m * m; e += kApplyThreads) Ls[e] = Li[e];
-  for (int a = tid; a < n; a += kApplyThreads) ys[a] = v[a];
+  for (int a = tid; a < n; a += kApplyThreads) ys[a] = static_cast<T>(v[a]);
   if (tid == 0) targets_of(L, i, n, r, tg);
   __syncthreads();
-  for (int a = tid; a < n; a += kApplyThreads) {
-    double s = 0.0;
-    for (int k = 0; k < n; ++k) s += static_cast<double>(Us[k * n + a]) * ys[k];
-    yt[a] = s;
+  // yt = U^T ys: thread (a, g) sums rows k = g (mod G) of column a
+  {
+    const int G = kApplyThreads / n, a = tid % n, g = tid / n;
+    if (g < G) {
+      T s = 0;
+      for (int k = g; k < n; k += G) s += U[k * n + a] * ys[k];
+      part[g * n + a] = s;
+    }
+    __syncthreads();
+    if (tid < n) {
+      T s = 0;
+      for (int h = 0; h < G; ++h) s += part[h * n + tid];
+      yt[tid] = s;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int a = tid; a < m; a += kApplyThreads) {
-    double s = 0.0;
-    for (int k = 0; k <= a; ++k) s += static_cast<double>(Ls[a * m + k]) * yt[r + k];
-    z[a] = s;
+  // z = L_hat^{-1} yt[r:] (lower, row-major: one warp per row)
+  {
+    const int lane = tid & 31, warp = tid >> 5;
+    for (int a = warp; a < m; a += kApplyThreads / 32) {
+      T s = 0;
+      for (int k = lane; k <= a; k += 32) s += Li[a * m + k] * yt[r + k];
+      s = warp_sum_t(s);
+      if (lane == 0) z[a] = s;
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  for (int a = tid; a < m; a += kApplyThreads) v[r + a] = z[a];
+  for (int a = tid; a < m; a += kApplyThreads) v[r + a] = static_cast<double>(z[a]);
   const int tot = tg.pre[tg.nt];
   for (int f = tid; f < tot; f += kApplyThreads) {
     int t = 0;
     while (f >= tg.pre[t + 1]) ++t;
     const int c = f - tg.pre[t], w = tg.w[t];
-    const T* Wt = W + tg.woff[t];
-    double s = 0.0;
-#pragma unroll 4
-    for (int k = 0; k < m; ++k) s += static_cast<double>(Wt[k * w + c]) * z[k];
+    const T s = dot_strided(W + tg.woff[t] + c, w, z, 0, m);
     if (t == 0)
-      v[c] = yt[c] - s;
+      v[c] = static_cast<double>(yt[c] - s);
     else
-      vec[tg.voff[t] + c] -= s;
+      vec[tg.voff[t] + c] -= static_cast<double>(s);
   }
 }
 
@@ -120,24 +155,19 @@ __global__ void __launch_bounds__(kApplyThreads) apply_fwd_kernel(LevelDev L, in
 // all targets; x_n = L_hat^{-T} rhs; y_i <- U_i [x_b; x_n].
 template <typename T>
 __global__ void __launch_bounds__(kApplyThreads) apply_bwd_kernel(LevelDev L, int first, double* vec) {
-  extern __shared__ __align__(16) unsigned char sm_raw[];
-  __shared__ double xf[kNMax], rhs[kNMax];
-  __shared__ double xt[kMaxTgt * kNMax];
+  __shared__ T xf[kNMax], rhs[kNMax];
+  __shared__ T xt[kMaxTgt * kNMax];
   __shared__ Targets tg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int i = L.order[first + blockIdx.x];
   const int n = L.n[i];
   if (n == 0) return;
   const int r = L.rank[i], m = n - r;
-  T* Us = reinterpret_cast<T*>(sm_raw);
-  T* Ls = Us + n * n;
   double* v = vec + L.vec_off[i];
   const T* U = reinterpret_cast<const T*>(L.U) + L.u_off[i];
   const T* Li = reinterpret_cast<const T*>(L.L) + L.l_off[i];
   const T* W = reinterpret_cast<const T*>(L.W) + L.w_off[i];
-  for (int e = tid; e < n * n; e += kApplyThreads) Us[e] = U[e];
-  for (int e = tid; e < m * m; e += kApplyThreads) Ls[e] = Li[e];
-  for (int a = tid; a < n; a += kApplyThreads) xf[a] = v[a];   // [x_b; z]
+  for (int a = tid; a < n; a += kApplyThreads) xf[a] = static_cast<T>(v[a]);   // [x_b; z]
   if (tid == 0) targets_of(L, i, n, r, tg);
   __syncthreads();
   const int tot = tg.pre[tg.nt];
@@ -145,32 +175,31 @@ __global__ void __launch_bounds__(kApplyThreads) apply_bwd_kernel(LevelDev L, in
     int t = 0;
     while (f >= tg.pre[t + 1]) ++t;
     const int c = f - tg.pre[t];
-    xt[f] = (t == 0) ? xf[c] : vec[tg.voff[t] + c];
+    xt[f] = (t == 0) ? xf[c] : static_cast<T>(vec[tg.voff[t] + c]);
   }
   __syncthreads();
-  constexpr int nw = kApplyThreads / 32;
-  for (int a = warp; a < m; a += nw) {
-    double s = 0.0;
+  // rhs = z - W x_t: one warp per row of W (contiguous within each target)
+  for (int a = warp; a < m; a += kApplyThreads / 32) {
+    T s = 0;
     for (int t = 0; t < tg.nt; ++t) {
       const int w = tg.w[t];
       const T* Wt = W + tg.woff[t] + (int64_t)a * w;
-      const double* x = xt + tg.pre[t];
-      for (int c = lane; c < w; c += 32) s += static_cast<double>(Wt[c]) * x[c];
+      const T* x = xt + tg.pre[t];
+      for (int c = lane; c < w; c += 32) s += Wt[c] * x[c];
     }
-    s = warp_sum_d(s);
+    s = warp_sum_t(s);
     if (lane == 0) rhs[a] = xf[r + a] - s;
   }
   __syncthreads();
-  for (int a = tid; a < m; a += kApplyThreads) {
-    double s = 0.0;
-    for (int k = a; k < m; ++k) s += static_cast<double>(Ls[k * m + a]) * rhs[k];
-    xf[r + a] = s;
-  }
+  // x_n = L_hat^{-T} rhs: column a of L_hat^{-1}, contiguous across threads
+  for (int a = tid; a < m; a += kApplyThreads) xf[r + a] = dot_strided(Li + a, m, rhs, a, m);
   __syncthreads();
-  for (int a = tid; a < n; a += kApplyThreads) {
-    double s = 0.0;
-    for (int k = 0; k < n; ++k) s += static_cast<double>(Us[a * n + k]) * xf[k];
-    v[a] = s;
+  // y_i = U_i xf: one warp per row
+  for (int a = warp; a < n; a += kApplyThreads / 32) {
+    T s = 0;
+    for (int k = lane; k < n; k += 32) s += U[a * n + k] * xf[k];
+    s = warp_sum_t(s);
+    if (lane == 0) v[a] = static_cast<double>(s);
   }
 }
 
@@ -427,23 +456,13 @@ __global__ void pcg_scalars_kernel(double* scal, int stage) {
 }
 
 template <typename T>
-cudaError_t apply_launch(const LevelDev& L, int first, int count, int nmax, double* vec,
-                         cudaStream_t s, bool fwd) {
+cudaError_t apply_launch(const LevelDev& L, int first, int count, double* vec, cudaStream_t s, bool fwd) {
   if (count <= 0) return cudaSuccess;
-  const size_t smem = 2 * sizeof(T) * (size_t)nmax * nmax;
-  static size_t attr_f = 0, attr_b = 0;
-  size_t& attr = fwd ? attr_f : attr_b;
-  if (smem > 40 * 1024 && smem > attr) {
-    cudaError_t e = fwd ? cudaFuncSetAttribute(apply_fwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                        : cudaFuncSetAttribute(apply_bwd_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = smem;
-  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (fwd)
-    apply_fwd_kernel<T><<<count, kApplyThreads, smem, s>>>(L, first, vec);
+    apply_fwd_kernel<T><<<count, kApplyThreads, 0, s>>>(L, first, vec);
   else
-    apply_bwd_kernel<T><<<count, kApplyThreads, smem, s>>>(L, first, vec);
+    apply_bwd_kernel<T><<<count, kApplyThreads, 0, s>>>(L, first, vec);
   return cudaGetLastError();
 }
 
@@ -451,14 +470,14 @@ cudaError_t apply_launch(const LevelDev& L, int first, int count, int nmax, doub
 
 cudaError_t launch_apply_fwd(int esize, const LevelDev& L, int first, int count, int nmax, double* vec,
                              cudaStream_t s) {
-  return esize == 8 ? apply_launch<double>(L, first, count, nmax, vec, s, true)
-                    : apply_launch<float>(L, first, count, nmax, vec, s, true);
+  return esize == 8 ? apply_launch<double>(L, first, count, vec, s, true)
+                    : apply_launch<float>(L, first, count, vec, s, true);
 }
 
 cudaError_t launch_apply_bwd(int esize, const LevelDev& L, int first, int count, int nmax, double* vec,
                              cudaStream_t s) {
-  return esize == 8 ? apply_launch<double>(L, first, count, nmax, vec, s, false)
-                    : apply_launch<float>(L, first, count, nmax, vec, s, false);
+  return esize == 8 ? apply_launch<double>(L, first, count, vec, s, false)
+                    : apply_launch<float>(L, first, count, vec, s, false);
 }
 
 cudaError_t launch_level_move(const LevelDev& L, double* cur, double* next, int forward,

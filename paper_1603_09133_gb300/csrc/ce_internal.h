@@ -1,7 +1,12 @@
 // Internal types of the CE library: host plans and device views.
 #pragma once
+#include <algorithm>
 #include <cstdint>
+#include <exception>
+#include <memory>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include <cuda_runtime.h>
@@ -11,6 +16,37 @@
 namespace ce {
 
 constexpr int kNMax = 64;  // largest block the row kernel holds in shared memory
+
+// Host threads for the planning loops (hardware threads, at most 16).
+int host_threads();
+
+// f(begin, end) over [0, n) cut into at most host_threads() ranges of at
+// least `grain` items; the first exception thrown by a range is rethrown.
+template <class F>
+void parallel_for(int64_t n, int64_t grain, F&& f) {
+  if (n <= 0) return;
+  const int64_t T = std::min<int64_t>(host_threads(), (n + grain - 1) / std::max<int64_t>(grain, 1));
+  if (T <= 1) {
+    f(int64_t(0), n);
+    return;
+  }
+  std::exception_ptr err;
+  std::mutex mu;
+  auto run = [&](int64_t t) {
+    try {
+      f(n * t / T, n * (t + 1) / T);
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(mu);
+      if (!err) err = std::current_exception();
+    }
+  };
+  std::vector<std::thread> th;
+  th.reserve(T - 1);
+  for (int64_t t = 1; t < T; ++t) th.emplace_back(run, t);
+  run(0);
+  for (auto& x : th) x.join();
+  if (err) std::rethrow_exception(err);
+}
 
 // ---------------------------------------------------------------------------
 // Host plan of one level (Section 2.2-2.4): block sizes, the level-start
@@ -26,8 +62,9 @@ struct LevelPlan {
   std::vector<int> order;        // colour-major elimination order
   std::vector<int> colour_ptr;   // ncolours + 1 offsets into order
 
-  // all pairs of the squared pattern, sorted by (i, k), i <= k
-  std::vector<int> pair_i, pair_k;
+  // all pairs of the squared pattern, sorted by (i, k), i <= k; the pairs
+  // of row i are [pair_ptr[i], pair_ptr[i+1])
+  std::vector<int> pair_ptr, pair_i, pair_k;
   std::vector<int64_t> pair_off;
   std::vector<char> pair_close;
   int64_t pool_elems = 0;
@@ -51,9 +88,15 @@ struct LevelPlan {
 };
 
 // Build the plan of a level from its sizes and level-start pattern (pairs
-// with i <= k; the diagonal pairs are added if missing).
+// with i <= k; the diagonal pairs are added if missing).  sys_off (empty =
+// one system) gives the blocks of each independent system.
 void plan_level(LevelPlan& P, const std::vector<int>& n,
-                const std::vector<std::pair<int, int>>& close_pairs, bool coloring);
+                const std::vector<std::pair<int, int>>& close_pairs, bool coloring,
+                const std::vector<int>& sys_off = {});
+
+// Element offset of pair (a, b) (either order) in the level pool, -1 if the
+// pair is not in the squared pattern.
+int64_t find_pair(const LevelPlan& P, int a, int b);
 
 // Reassembly of level l into level l+1 (Section 2.4): copy tasks for the
 // kept r_i x r_k corner of every pair into the super-block pairs.
@@ -113,7 +156,7 @@ struct LevelDev {
 
 // One level kept in a factor.
 struct LevelStore {
-  LevelPlan plan;
+  std::shared_ptr<const LevelPlan> plan;  // level 1 may share the csb's plan
   std::vector<int> rank;        // host copy
   LevelDev dev{};
   void* meta = nullptr;         // device metadata block
@@ -137,7 +180,7 @@ struct ce_csb {
   double* d_val = nullptr;
   int32_t* d_perm = nullptr;
   // level-1 plan and the scatter map nnz -> element of the level-1 pool
-  ce::LevelPlan plan1;
+  std::shared_ptr<ce::LevelPlan> plan1;
   int64_t* d_scatter = nullptr;
 };
 

@@ -7,62 +7,142 @@
 // preallocated here.  Section 2.4 (eq. bsp): after a sweep, J consecutive
 // blocks join into one super-block; the next level's pattern is the
 // coarsened squared pattern restricted to blocks with a non-empty basis.
+//
+// Every structure is a flat CSR array and every per-block loop runs on a few
+// host threads (blocks are independent once the adjacency is known); the
+// greedy colouring is sequential within one system and runs systems in
+// parallel (blocks of different systems are never adjacent).
 #include <algorithm>
 #include <numeric>
 #include <stdexcept>
+#include <thread>
 
 #include "ce_internal.h"
 
 namespace ce {
 
-namespace {
-
-// sorted adjacency (diagonal included) from a list of pairs
-std::vector<std::vector<int>> adjacency(int M, const std::vector<std::pair<int, int>>& pairs) {
-  std::vector<std::vector<int>> adj(M);
-  for (int i = 0; i < M; ++i) adj[i].push_back(i);
-  for (auto& p : pairs) {
-    if (p.first == p.second) continue;
-    adj[p.first].push_back(p.second);
-    adj[p.second].push_back(p.first);
-  }
-  for (auto& a : adj) {
-    std::sort(a.begin(), a.end());
-    a.erase(std::unique(a.begin(), a.end()), a.end());
-  }
-  return adj;
+int host_threads() {
+  static const int t = [] {
+    const unsigned h = std::thread::hardware_concurrency();
+    return static_cast<int>(std::min(16u, std::max(1u, h)));
+  }();
+  return t;
 }
 
-bool contains(const std::vector<int>& v, int x) {
-  return std::binary_search(v.begin(), v.end(), x);
+namespace {
+
+struct Csr {
+  std::vector<int64_t> ptr;
+  std::vector<int> idx;
+  int deg(int i) const { return static_cast<int>(ptr[i + 1] - ptr[i]); }
+  const int* row(int i) const { return idx.data() + ptr[i]; }
+  bool has(int i, int k) const { return std::binary_search(row(i), row(i) + deg(i), k); }
+};
+
+// sorted adjacency (diagonal included) from a list of pairs
+Csr adjacency(int M, const std::vector<std::pair<int, int>>& pairs) {
+  Csr A;
+  std::vector<int64_t> cnt(M + 1, 0);
+  for (int i = 0; i < M; ++i) cnt[i + 1] = 1;
+  for (auto& p : pairs)
+    if (p.first != p.second) {
+      ++cnt[p.first + 1];
+      ++cnt[p.second + 1];
+    }
+  for (int i = 0; i < M; ++i) cnt[i + 1] += cnt[i];
+  std::vector<int> raw(cnt[M]);
+  std::vector<int64_t> fill(cnt.begin(), cnt.end() - 1);
+  for (int i = 0; i < M; ++i) raw[fill[i]++] = i;
+  for (auto& p : pairs)
+    if (p.first != p.second) {
+      raw[fill[p.first]++] = p.second;
+      raw[fill[p.second]++] = p.first;
+    }
+  // sort + unique per row, then compact
+  std::vector<int> len(M);
+  parallel_for(M, 2048, [&](int64_t b, int64_t e) {
+    for (int64_t i = b; i < e; ++i) {
+      int* s = raw.data() + cnt[i];
+      int* t = raw.data() + cnt[i + 1];
+      std::sort(s, t);
+      len[i] = static_cast<int>(std::unique(s, t) - s);
+    }
+  });
+  A.ptr.assign(M + 1, 0);
+  for (int i = 0; i < M; ++i) A.ptr[i + 1] = A.ptr[i] + len[i];
+  A.idx.resize(A.ptr[M]);
+  parallel_for(M, 4096, [&](int64_t b, int64_t e) {
+    for (int64_t i = b; i < e; ++i) std::copy_n(raw.data() + cnt[i], len[i], A.idx.data() + A.ptr[i]);
+  });
+  return A;
+}
+
+// greedy distance-2 colouring of blocks [b0, b1), ascending block index
+void colour_range(const Csr& adj, int b0, int b1, std::vector<int>& colour) {
+  std::vector<int> mark;  // mark[c] == i  <=> colour c is taken near i
+  for (int i = b0; i < b1; ++i) {
+    for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j)
+      for (const int* k = adj.row(*j); k != adj.row(*j) + adj.deg(*j); ++k)
+        if (*k != i && colour[*k] >= 0) {
+          const int c = colour[*k];
+          if (c >= static_cast<int>(mark.size())) mark.resize(c + 1, -1);
+          mark[c] = i;
+        }
+    int c = 0;
+    while (c < static_cast<int>(mark.size()) && mark[c] == i) ++c;
+    colour[i] = c;
+  }
+}
+
+// Per-block output lists filled by chunks of blocks in parallel and joined in
+// block order: a CSR pointer array plus one or two value arrays.
+template <typename A, typename B>
+void join_chunks(int M, int nch, const std::vector<std::vector<int>>& cnt, std::vector<std::vector<A>>& va,
+                 std::vector<std::vector<B>>* vb, std::vector<int>& ptr, std::vector<A>& outa,
+                 std::vector<B>* outb, const std::vector<int64_t>& cb) {
+  ptr.assign(M + 1, 0);
+  for (int c = 0; c < nch; ++c)
+    for (int64_t i = cb[c]; i < cb[c + 1]; ++i) ptr[i + 1] = cnt[c][i - cb[c]];
+  for (int i = 0; i < M; ++i) ptr[i + 1] += ptr[i];
+  outa.resize(ptr[M]);
+  if (outb) outb->resize(ptr[M]);
+  parallel_for(nch, 1, [&](int64_t b, int64_t e) {
+    for (int64_t c = b; c < e; ++c) {
+      std::copy(va[c].begin(), va[c].end(), outa.begin() + ptr[cb[c]]);
+      if (outb) std::copy((*vb)[c].begin(), (*vb)[c].end(), outb->begin() + ptr[cb[c]]);
+    }
+  });
 }
 
 }  // namespace
 
+int64_t find_pair(const LevelPlan& P, int a, int b) {
+  if (a > b) std::swap(a, b);
+  const int* lo = P.pair_k.data() + P.pair_ptr[a];
+  const int* hi = P.pair_k.data() + P.pair_ptr[a + 1];
+  const int* it = std::lower_bound(lo, hi, b);
+  if (it == hi || *it != b) return -1;
+  return P.pair_off[it - P.pair_k.data()];
+}
+
 void plan_level(LevelPlan& P, const std::vector<int>& n,
-                const std::vector<std::pair<int, int>>& close_pairs, bool coloring) {
+                const std::vector<std::pair<int, int>>& close_pairs, bool coloring,
+                const std::vector<int>& sys_off) {
   const int M = static_cast<int>(n.size());
   P = LevelPlan();
   P.M = M;
   P.n = n;
-  auto adj = adjacency(M, close_pairs);
+  P.sys_off = sys_off;
+  const Csr adj = adjacency(M, close_pairs);
 
   // ---- greedy distance-2 colouring, ascending block index ----------------
   P.colour.assign(M, -1);
   if (coloring) {
-    std::vector<int> mark;  // mark[c] == i  <=> colour c is taken near i
-    for (int i = 0; i < M; ++i) {
-      for (int j : adj[i])
-        for (int k : adj[j])
-          if (k != i && P.colour[k] >= 0) {
-            int c = P.colour[k];
-            if (c >= static_cast<int>(mark.size())) mark.resize(c + 1, -1);
-            mark[c] = i;
-          }
-      int c = 0;
-      while (c < static_cast<int>(mark.size()) && mark[c] == i) ++c;
-      P.colour[i] = c;
-    }
+    std::vector<int> so = sys_off.empty() ? std::vector<int>{0, M} : sys_off;
+    const int ns = static_cast<int>(so.size()) - 1;
+    parallel_for(ns, 1, [&](int64_t b, int64_t e) {
+      for (int64_t s = b; s < e; ++s) colour_range(adj, so[s], so[s + 1], P.colour);
+    });
   } else {
     // natural order: every block is its own step
     for (int i = 0; i < M; ++i) P.colour[i] = i;
@@ -76,86 +156,113 @@ void plan_level(LevelPlan& P, const std::vector<int>& n,
   for (int i = 0; i < M; ++i) P.colour_ptr[P.colour[i] + 1]++;
   for (int c = 0; c < P.ncolours; ++c) P.colour_ptr[c + 1] += P.colour_ptr[c];
 
+  // chunks of blocks for the parallel per-block passes
+  const int nch = std::max(1, std::min(host_threads() * 4, (M + 1023) / 1024));
+  std::vector<int64_t> cb(nch + 1);
+  for (int c = 0; c <= nch; ++c) cb[c] = (int64_t)M * c / nch;
+
   // ---- squared pattern (close + far), rows i, columns k >= i -------------
-  std::vector<std::vector<int>> sq(M);
-  for (int j = 0; j < M; ++j)
-    for (int a : adj[j])
-      for (int b : adj[j])
-        if (a <= b) sq[a].push_back(b);
-  std::vector<int> row_ptr(M + 1, 0);
-  for (int i = 0; i < M; ++i) {
-    auto& v = sq[i];
-    std::sort(v.begin(), v.end());
-    v.erase(std::unique(v.begin(), v.end()), v.end());
-    row_ptr[i + 1] = row_ptr[i] + static_cast<int>(v.size());
+  {
+    std::vector<std::vector<int>> cnt(nch), rows(nch);
+    parallel_for(nch, 1, [&](int64_t b, int64_t e) {
+      std::vector<int> buf;
+      for (int64_t c = b; c < e; ++c) {
+        cnt[c].resize(cb[c + 1] - cb[c]);
+        for (int64_t i = cb[c]; i < cb[c + 1]; ++i) {
+          buf.clear();
+          for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j)
+            for (const int* k = adj.row(*j); k != adj.row(*j) + adj.deg(*j); ++k)
+              if (*k >= i) buf.push_back(*k);
+          std::sort(buf.begin(), buf.end());
+          buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+          cnt[c][i - cb[c]] = static_cast<int>(buf.size());
+          rows[c].insert(rows[c].end(), buf.begin(), buf.end());
+        }
+      }
+    });
+    join_chunks<int, int>(M, nch, cnt, rows, nullptr, P.pair_ptr, P.pair_k, nullptr, cb);
   }
-  const int np = row_ptr[M];
+  const int np = P.pair_ptr[M];
   P.pair_i.resize(np);
-  P.pair_k.resize(np);
   P.pair_off.resize(np);
   P.pair_close.resize(np);
   int64_t off = 0;
   for (int i = 0; i < M; ++i)
-    for (int t = 0; t < static_cast<int>(sq[i].size()); ++t) {
-      int p = row_ptr[i] + t, k = sq[i][t];
+    for (int p = P.pair_ptr[i]; p < P.pair_ptr[i + 1]; ++p) {
       P.pair_i[p] = i;
-      P.pair_k[p] = k;
       P.pair_off[p] = off;
-      P.pair_close[p] = contains(adj[i], k);
-      off += static_cast<int64_t>(n[i]) * n[k];
+      off += static_cast<int64_t>(n[i]) * n[P.pair_k[p]];
     }
   P.pool_elems = off;
+  parallel_for(M, 2048, [&](int64_t b, int64_t e) {
+    for (int64_t i = b; i < e; ++i)
+      for (int p = P.pair_ptr[i]; p < P.pair_ptr[i + 1]; ++p) P.pair_close[p] = adj.has(i, P.pair_k[p]);
+  });
   auto pair_offset = [&](int a, int b) -> int64_t {
-    if (a > b) std::swap(a, b);
-    auto& v = sq[a];
-    auto it = std::lower_bound(v.begin(), v.end(), b);
-    if (it == v.end() || *it != b) throw std::logic_error("pair outside squared pattern");
-    return P.pair_off[row_ptr[a] + static_cast<int>(it - v.begin())];
+    const int64_t o = find_pair(P, a, b);
+    if (o < 0) throw std::logic_error("pair outside squared pattern");
+    return o;
   };
 
   // ---- per block lists ----------------------------------------------------
-  P.close_ptr.assign(M + 1, 0);
-  P.far_ptr.assign(M + 1, 0);
-  P.schur_ptr.assign(M + 1, 0);
   P.diag_off.resize(M);
-  for (int i = 0; i < M; ++i) {
-    P.diag_off[i] = pair_offset(i, i);
-    std::vector<int> cl;
-    for (int k : adj[i])
-      if (k != i) cl.push_back(k);
-    for (int k : cl) {
-      P.close_blk.push_back(k);
-      P.close_off.push_back(pair_offset(i, k));
-    }
-    P.close_ptr[i + 1] = static_cast<int>(P.close_blk.size());
-    // far blocks of row i that hold fill when i is processed: some common
-    // close neighbour j of i and k was eliminated earlier
-    std::vector<int> cand;
-    for (int j : adj[i])
-      for (int k : adj[j])
-        if (k != i && !contains(adj[i], k)) cand.push_back(k);
-    std::sort(cand.begin(), cand.end());
-    cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-    for (int k : cand) {
-      bool live = false;
-      for (int j : adj[i])
-        if (j != i && j != k && P.colour[j] < P.colour[i] && contains(adj[k], j)) {
-          live = true;
-          break;
+  {
+    std::vector<std::vector<int>> ccnt(nch), fcnt(nch), scnt(nch), cblk(nch), fblk(nch);
+    std::vector<std::vector<int64_t>> coff(nch), foff(nch), soff(nch);
+    parallel_for(nch, 1, [&](int64_t b, int64_t e) {
+      std::vector<int> cand, T;
+      for (int64_t c = b; c < e; ++c) {
+        const int64_t nb = cb[c + 1] - cb[c];
+        ccnt[c].resize(nb);
+        fcnt[c].resize(nb);
+        scnt[c].resize(nb);
+        for (int64_t ii = cb[c]; ii < cb[c + 1]; ++ii) {
+          const int i = static_cast<int>(ii);
+          P.diag_off[i] = pair_offset(i, i);
+          int nc = 0;
+          for (const int* k = adj.row(i); k != adj.row(i) + adj.deg(i); ++k)
+            if (*k != i) {
+              cblk[c].push_back(*k);
+              coff[c].push_back(pair_offset(i, *k));
+              ++nc;
+            }
+          ccnt[c][i - cb[c]] = nc;
+          // far blocks of row i that hold fill when i is processed: some
+          // common close neighbour j of i and k was eliminated earlier
+          cand.clear();
+          for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j)
+            for (const int* k = adj.row(*j); k != adj.row(*j) + adj.deg(*j); ++k)
+              if (*k != i && !adj.has(i, *k)) cand.push_back(*k);
+          std::sort(cand.begin(), cand.end());
+          cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
+          int nf = 0;
+          for (int k : cand) {
+            bool live = false;
+            for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j)
+              if (*j != i && *j != k && P.colour[*j] < P.colour[i] && adj.has(k, *j)) {
+                live = true;
+                break;
+              }
+            if (live) {
+              fblk[c].push_back(k);
+              foff[c].push_back(pair_offset(i, k));
+              ++nf;
+            }
+          }
+          fcnt[c][i - cb[c]] = nf;
+          // Schur targets T = [i] + close(i): all pairs (T[a], T[b]), a <= b
+          T.assign(1, i);
+          for (const int* k = adj.row(i); k != adj.row(i) + adj.deg(i); ++k)
+            if (*k != i) T.push_back(*k);
+          for (size_t a = 0; a < T.size(); ++a)
+            for (size_t bb = a; bb < T.size(); ++bb) soff[c].push_back(pair_offset(T[a], T[bb]));
+          scnt[c][i - cb[c]] = static_cast<int>(T.size() * (T.size() + 1) / 2);
         }
-      if (live) {
-        P.far_blk.push_back(k);
-        P.far_off.push_back(pair_offset(i, k));
       }
-    }
-    P.far_ptr[i + 1] = static_cast<int>(P.far_blk.size());
-    // Schur targets T = [i] + close(i): all pairs (T[a], T[b]), a <= b
-    std::vector<int> T;
-    T.push_back(i);
-    T.insert(T.end(), cl.begin(), cl.end());
-    for (size_t a = 0; a < T.size(); ++a)
-      for (size_t b = a; b < T.size(); ++b) P.schur_off.push_back(pair_offset(T[a], T[b]));
-    P.schur_ptr[i + 1] = static_cast<int>(P.schur_off.size());
+    });
+    join_chunks<int, int64_t>(M, nch, ccnt, cblk, &coff, P.close_ptr, P.close_blk, &P.close_off, cb);
+    join_chunks<int, int64_t>(M, nch, fcnt, fblk, &foff, P.far_ptr, P.far_blk, &P.far_off, cb);
+    join_chunks<int64_t, int>(M, nch, scnt, soff, nullptr, P.schur_ptr, P.schur_off, nullptr, cb);
   }
 
   // ---- factor and vector layout ------------------------------------------
@@ -193,12 +300,15 @@ NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J) {
   nx.parent.assign(M, 0);
   nx.child_off.assign(M, 0);
   nx.sys_off.assign(so.size(), 0);
+  std::vector<int> first_child{0};  // children of super-block I: [first_child[I], first_child[I+1])
   int next = 0;
   for (size_t s = 0; s + 1 < so.size(); ++s) {
     nx.sys_off[s] = next;
     // J consecutive blocks of the same system form one super-block
     for (int i = so[s]; i < so[s + 1]; ++i) nx.parent[i] = next + (i - so[s]) / J;
-    next += (so[s + 1] - so[s] + J - 1) / J;
+    const int cnt = (so[s + 1] - so[s] + J - 1) / J;
+    for (int t = 0; t < cnt; ++t) first_child.push_back(std::min(so[s + 1], so[s] + (t + 1) * J));
+    next += cnt;
   }
   nx.sys_off.back() = next;
   nx.n.assign(next, 0);
@@ -206,15 +316,31 @@ NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J) {
     nx.child_off[i] = nx.n[nx.parent[i]];
     nx.n[nx.parent[i]] += rank[i];
   }
-  std::vector<std::pair<int, int>> pr;
-  for (size_t p = 0; p < P.pair_i.size(); ++p) {
-    int i = P.pair_i[p], k = P.pair_k[p];
-    if (rank[i] == 0 || rank[k] == 0) continue;
-    pr.emplace_back(nx.parent[i], nx.parent[k]);
-  }
-  std::sort(pr.begin(), pr.end());
-  pr.erase(std::unique(pr.begin(), pr.end()), pr.end());
-  nx.pairs = std::move(pr);
+  // super-block rows in parallel: parents of the children's pairs with a
+  // non-empty basis on both sides (parent() is monotone, so K >= I)
+  const int nch = std::max(1, std::min(host_threads() * 4, (next + 511) / 512));
+  std::vector<std::vector<std::pair<int, int>>> part(nch);
+  parallel_for(nch, 1, [&](int64_t b, int64_t e) {
+    std::vector<int> buf;
+    for (int64_t c = b; c < e; ++c) {
+      const int I0 = static_cast<int>((int64_t)next * c / nch), I1 = static_cast<int>((int64_t)next * (c + 1) / nch);
+      for (int I = I0; I < I1; ++I) {
+        buf.clear();
+        for (int i = first_child[I]; i < first_child[I + 1]; ++i) {
+          if (rank[i] == 0) continue;
+          for (int p = P.pair_ptr[i]; p < P.pair_ptr[i + 1]; ++p)
+            if (rank[P.pair_k[p]] != 0) buf.push_back(nx.parent[P.pair_k[p]]);
+        }
+        std::sort(buf.begin(), buf.end());
+        buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
+        for (int K : buf) part[c].emplace_back(I, K);
+      }
+    }
+  });
+  size_t tot = 0;
+  for (auto& v : part) tot += v.size();
+  nx.pairs.reserve(tot);
+  for (auto& v : part) nx.pairs.insert(nx.pairs.end(), v.begin(), v.end());
   return nx;
 }
 
