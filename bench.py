@@ -251,6 +251,9 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     model = ceg.trained_rank_model() if args.ranks == "learned" else None
+    # row-kernel CTA shape per level, chosen by measurement (setup, untimed)
+    tune_ms = ceg.ce_autotune(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=args.precision,
+                              rank_model=model)
 
     def step(prec, rm=None):
         F = ceg.ce_factorize(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=prec, rank_model=rm)
@@ -340,6 +343,10 @@ def run_ours(args, rank, world):
                   "colours": [info.colours[l] for l in range(nl)],
                   "max_block": [info.max_block[l] for l in range(nl)],
                   "row_kernel_ms": [round(info.level_ms[l], 3) for l in range(nl)],
+                  "row_shape": [info.row_shape[l] for l in range(nl)],
+                  "autotune_ms": [[round(v, 3) for v in row] for row in tune_ms.tolist()],
+                  "host_ms": [round(info.host_ms[l], 3) for l in range(nl)],
+                  "factor_wall_ms": round(info.total_ms, 3),
                   "coarse_n": info.coarse_n, "coarse_ms": round(info.coarse_ms, 3),
                   "factor_MB": round(info.factor_bytes / 2**20, 1)}
     out = {"metric": METRIC, "value": ms / 1e3, "unit": "s", "n_gpus": world,

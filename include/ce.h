@@ -76,6 +76,11 @@ typedef struct {
                              ce_mlp_pack (CE_RANK_LEARNED only)          */
   int oversample;  /* p, sketch columns beyond r_hat (default 8)         */
   uint64_t seed;   /* key of the sketch's counter-based Gaussians        */
+  int row_shape;   /* CTA shape of the row kernel: -1 (default) the csb's
+                      autotuned choice per level (ce_autotune), else a
+                      heuristic; 0: 256 threads, 72 KB shared memory;
+                      1: 512 threads, all shared memory; 2: 128 threads,
+                      40 KB                                              */
 } ce_opts;
 
 typedef struct {
@@ -83,7 +88,9 @@ typedef struct {
   int err_level;       /* for CE_ERR_NOT_SPD: level (K = coarse) ...      */
   int err_block;       /* ... and block index (-1 = coarse)               */
   int err_reason;      /* 1: pivot <= 0 (index err_pivot, value err_value);
-                          2: non-finite singular values of F_i            */
+                          2: non-finite singular values of F_i;
+                          5: a row's wait for its neighbours timed out
+                          (CE_ERR_CUDA; never expected)                   */
   int err_pivot;
   double err_value;
   int coarse_n;        /* size of the dense remainder A_K                 */
@@ -104,6 +111,7 @@ typedef struct {
                           metadata upload, then the planning of level l+1
                           (coarsening, pattern, colouring, reassembly)    */
   double total_ms;     /* wall time of the whole call                     */
+  int row_shape[16];   /* CTA shape the row kernel used per level         */
 } ce_info;
 
 typedef struct {
@@ -187,6 +195,19 @@ ce_status ce_factorize_simple(int64_t n, const int64_t* rowptr,
                               const int32_t* col, const double* val,
                               const int32_t* perm, int32_t B, double tol,
                               int levels, ce_factor** out);
+
+/*
+ * ce_autotune -- choose the row kernel's CTA shape per level by measurement:
+ * factorizes A once with each shape (options o, row_shape ignored), times
+ * every level's launch with CUDA events and keeps the fastest shape per
+ * level in A, where later ce_factorize calls with row_shape = -1 and the same
+ * precision and rank mode find it.  A shape only changes how a row's work is
+ * spread over threads (and with it the rounding of in-row reductions), not
+ * what is computed.
+ *   level_ms  optional host array of 3 x 16 doubles: [shape][level] times
+ * Not part of the paper (launch configuration of this implementation).
+ */
+ce_status ce_autotune(ce_csb* A, const ce_opts* o, double* level_ms);
 
 /*
  * ce_apply -- z = M^{-1} r = Q^T L^{-T} L^{-1} Q r (solve proposition of

@@ -208,13 +208,8 @@ def csb_build_batched(systems) -> CSB:
     return csb_build_batched_csr(*stack_systems(systems))
 
 
-def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",
-                 coloring=True, stream=None, rank_model=None, oversample=8, seed=0) -> Factor:
-    """Algorithm 1 on the device; returns the factor (raises CEError).
-
-    ``rank_model`` (a :class:`RankModel`) switches the compression step to the
-    learned rank + randomized range finder with exact-SVD fallback.
-    """
+def _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed,
+          row_shape):
     lib = _lib.load()
     o = _lib.ce_opts()
     lib.ce_opts_default(C.byref(o))
@@ -230,6 +225,32 @@ def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="
         o.rank_model = C.c_void_p(rank_model.model.data_ptr())
         o.oversample = int(oversample)
         o.seed = int(seed)
+    o.row_shape = int(row_shape)
+    return o
+
+
+def ce_autotune(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",
+                coloring=True, stream=None, rank_model=None, oversample=8, seed=0):
+    """Time every row-kernel CTA shape per level and keep the fastest in the
+    csb; returns the [shape][level] times (ms) as a 3 x levels array."""
+    lib = _lib.load()
+    o = _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed, -1)
+    t = np.zeros(3 * 16, np.float64)
+    _check(lib.ce_autotune(csb.handle, C.byref(o), t.ctypes.data_as(_lib.DP)), "ce_autotune")
+    return t.reshape(3, 16)[:, :levels]
+
+
+def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",
+                 coloring=True, stream=None, rank_model=None, oversample=8, seed=0,
+                 row_shape=-1) -> Factor:
+    """Algorithm 1 on the device; returns the factor (raises CEError).
+
+    ``rank_model`` (a :class:`RankModel`) switches the compression step to the
+    learned rank + randomized range finder with exact-SVD fallback.
+    """
+    lib = _lib.load()
+    o = _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed,
+              row_shape)
     info = _lib.ce_info()
     h = C.c_void_p()
     st = lib.ce_factorize(csb.handle, C.byref(o), C.byref(h), C.byref(info))

@@ -39,6 +39,7 @@ class ce_opts(C.Structure):
         ("rank_model", C.c_void_p),
         ("oversample", C.c_int),
         ("seed", C.c_uint64),
+        ("row_shape", C.c_int),
     ]
 
 
@@ -63,6 +64,7 @@ class ce_info(C.Structure):
         ("fallback_rows", C.c_int * 16),
         ("host_ms", C.c_double * 16),
         ("total_ms", C.c_double),
+        ("row_shape", C.c_int * 16),
     ]
 
 
@@ -86,6 +88,7 @@ SIGNATURES = {
     "ce_factorize_simple": (C.c_int, [C.c_int64, I64P, I32P, DP, I32P, C.c_int32,
                                       C.c_double, C.c_int, PP]),
     "ce_apply": (C.c_int, [P, P, P, P]),
+    "ce_autotune": (C.c_int, [P, C.POINTER(ce_opts), DP]),
     "pcg_solve": (C.c_int, [P, P, P, P, C.c_double, C.c_int, C.POINTER(ce_pcg_info), P]),
     "pcg_solve_batched": (C.c_int, [P, P, P, P, C.c_double, C.c_int, I32P, DP, I32P,
                                     C.POINTER(ce_pcg_info), P]),

@@ -260,7 +260,9 @@ void build_level_store(LevelStore& st, int esize, cudaStream_t s) {
                o_fp = pk.addv(P.far_ptr), o_fb = pk.addv(P.far_blk), o_fo = pk.addv(P.far_off),
                o_do = pk.addv(P.diag_off), o_sp = pk.addv(P.schur_ptr), o_so = pk.addv(P.schur_off),
                o_uo = pk.addv(P.u_off), o_lo = pk.addv(P.l_off), o_wo = pk.addv(P.w_off),
-               o_vo = pk.addv(P.vec_off), o_rank = pk.zeros(P.M * sizeof(int)),
+               o_vo = pk.addv(P.vec_off), o_dp = pk.addv(P.dep_ptr), o_di = pk.addv(P.dep_idx),
+               o_rank = pk.zeros(P.M * sizeof(int)), o_done = pk.zeros(P.M * sizeof(int)),
+               o_q = pk.zeros(sizeof(int)),
                o_gd = pk.zeros(P.M * sizeof(int64_t)), o_tau = pk.zeros(P.M * sizeof(double)),
                o_sig = pk.zeros(P.vec_len * sizeof(double));
   st.meta_bytes = pk.size;
@@ -289,6 +291,10 @@ void build_level_store(LevelStore& st, int esize, cudaStream_t s) {
   D.gdst = reinterpret_cast<int64_t*>(b + o_gd);
   D.tau = reinterpret_cast<double*>(b + o_tau);
   D.sigma = reinterpret_cast<double*>(b + o_sig);
+  D.dep_ptr = reinterpret_cast<const int*>(b + o_dp);
+  D.dep_idx = reinterpret_cast<const int*>(b + o_di);
+  D.done = reinterpret_cast<int*>(b + o_done);
+  D.qnext = reinterpret_cast<int*>(b + o_q);
   const size_t ub = P.u_elems * esize, lb = P.l_elems * esize, wb = P.w_elems * esize;
   st.fac_bytes = ub + lb + wb + 3 * 256;
   st.fac = dalloc(st.fac_bytes, s);
@@ -448,6 +454,7 @@ void ce_opts_default(ce_opts* o) {
   o->rank_model = nullptr;
   o->oversample = 8;
   o->seed = 0;
+  o->row_shape = -1;
 }
 
 const char* ce_strerror(ce_status s) {
@@ -749,7 +756,8 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
   if (o.levels < 0 || o.J < 1 || o.tol < 0 || (o.precision != CE_PREC_FP64 && o.precision != CE_PREC_FP32) ||
       (o.tol_mode != CE_TOL_REL && o.tol_mode != CE_TOL_ABS) ||
       (o.rank_mode != CE_RANK_SVD && o.rank_mode != CE_RANK_LEARNED) ||
-      (o.rank_mode == CE_RANK_LEARNED && (!o.rank_model || o.oversample < 0)))
+      (o.rank_mode == CE_RANK_LEARNED && (!o.rank_model || o.oversample < 0)) || o.row_shape < -1 ||
+      o.row_shape > 2)
     return CE_ERR_INVALID_ARG;
   *out = nullptr;
   if (info) std::memset(info, 0, sizeof(*info));
@@ -812,11 +820,16 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       check(cudaEventCreate(&ev0), "event");
       check(cudaEventCreate(&ev1), "event");
       check(cudaEventRecord(ev0, s), "event");
-      for (int c = 0; c < P.ncolours; ++c)
-        check(ce::launch_row_kernel(es, st.dev, P.colour_ptr[c], P.colour_ptr[c + 1] - P.colour_ptr[c], l,
-                                    o.tol, o.tol_mode, F->d_status, P.nmax,
-                                    P.colour_ptr[c + 1] - P.colour_ptr[c], la, s),
-              "row kernel");
+      // CTA shape: forced, autotuned for this csb, or 256-thread CTAs when
+      // the average colour fills two waves of them
+      int shape = (P.ncolours > 0 && P.M / P.ncolours >= 2 * 152) ? 0 : 1;
+      if (o.row_shape >= 0)
+        shape = o.row_shape;
+      else if (l < A->tuned_levels && A->tuned_prec == o.precision && A->tuned_rank == o.rank_mode)
+        shape = A->tuned_shape[l];
+      if (info && l < 16) info->row_shape[l] = shape;
+      check(ce::launch_row_kernel(es, st.dev, P.M, l, o.tol, o.tol_mode, F->d_status, P.nmax, shape, la, s),
+            "row kernel");
       check(cudaEventRecord(ev1, s), "event");
       st.rank.resize(P.M);
       check(cudaMemcpyAsync(st.rank.data(), st.dev.rank, P.M * sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
@@ -959,6 +972,42 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
   }
   *out = F;
   if (info) info->total_ms = ms_since(t_call);
+  return CE_OK;
+}
+
+ce_status ce_autotune(ce_csb* A, const ce_opts* o_in, double* level_ms) {
+  if (!A) return CE_ERR_INVALID_ARG;
+  ce_opts o;
+  ce_opts_default(&o);
+  if (o_in) o = *o_in;
+  constexpr int kShapes = 3;
+  double t[kShapes][16];
+  int nl = 16;
+  for (int sh = 0; sh < kShapes; ++sh) {
+    o.row_shape = sh;
+    ce_factor* F = nullptr;
+    ce_info info;
+    // one untimed run first (allocator pools, staging buffers, model warm)
+    for (int rep = 0; rep < 2; ++rep) {
+      ce_status st = ce_factorize(A, &o, &F, &info);
+      if (st != CE_OK) return st;
+      ce_factor_destroy(F);
+    }
+    nl = std::min(nl, info.levels_done);
+    for (int l = 0; l < 16; ++l) t[sh][l] = l < info.levels_done ? info.level_ms[l] : 0.0;
+  }
+  for (int l = 0; l < nl; ++l) {
+    int best = 0;
+    for (int sh = 1; sh < kShapes; ++sh)
+      if (t[sh][l] < t[best][l]) best = sh;
+    A->tuned_shape[l] = best;
+  }
+  A->tuned_levels = nl;
+  A->tuned_prec = o.precision;
+  A->tuned_rank = o.rank_mode;
+  if (level_ms)
+    for (int sh = 0; sh < kShapes; ++sh)
+      for (int l = 0; l < 16; ++l) level_ms[sh * 16 + l] = t[sh][l];
   return CE_OK;
 }
 

@@ -85,6 +85,10 @@ struct LevelPlan {
 
   // independent systems: blocks [sys_off[s], sys_off[s+1]) belong to system s
   std::vector<int> sys_off;
+
+  // rows of a lower colour within distance 2 of row i (the rows that must
+  // finish before row i starts): [dep_ptr[i], dep_ptr[i+1]) of dep_idx
+  std::vector<int> dep_ptr, dep_idx;
 };
 
 // Build the plan of a level from its sizes and level-start pattern (pairs
@@ -148,6 +152,10 @@ struct LevelDev {
   int64_t* gdst;        // position of block i's basis in the next vector
   double* tau;          // per block
   double* sigma;        // sum n_i (vec layout)
+  const int* dep_ptr;   // lower-colour rows within distance 2 (CSR)
+  const int* dep_idx;
+  int* done;            // per row: 1 once eliminated (persistent launch)
+  int* qnext;           // next position of the persistent launch's queue
   void* pool;           // pair values (T)
   void* U;              // factor (T): U_i
   void* L;              //   L_hat_i^{-1} (m_i x m_i, lower)
@@ -181,6 +189,10 @@ struct ce_csb {
   int32_t* d_perm = nullptr;
   // level-1 plan and the scatter map nnz -> element of the level-1 pool
   std::shared_ptr<ce::LevelPlan> plan1;
+  // row-kernel CTA shape per level chosen by ce_autotune (for one precision
+  // and rank mode)
+  int tuned_levels = 0, tuned_prec = -1, tuned_rank = -1;
+  int tuned_shape[16] = {};
   int64_t* d_scatter = nullptr;
 };
 

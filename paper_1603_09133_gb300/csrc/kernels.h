@@ -32,10 +32,11 @@ struct LearnedArgs {
 };
 
 size_t row_kernel_smem(int esize);
-// busy_ctas: rows in the launch (sets the shared-memory budget per CTA)
-cudaError_t launch_row_kernel(int esize, const LevelDev& L, int first, int count, int level,
-                              double tol, int tol_mode, int* status, int nmax, int busy_ctas,
-                              const LearnedArgs& la, cudaStream_t s);
+// All `count` rows of a level (order[0, count)) in one persistent launch;
+// shape 0: 256-thread CTAs with a 72 KB budget, 1: 512-thread CTAs with the
+// whole shared memory.
+cudaError_t launch_row_kernel(int esize, const LevelDev& L, int count, int level, double tol, int tol_mode,
+                              int* status, int nmax, int shape, const LearnedArgs& la, cudaStream_t s);
 cudaError_t launch_scatter_csr(int esize, const int64_t* scatter, const double* val, int64_t nnz,
                                void* pool, cudaStream_t s);
 cudaError_t launch_copy_tasks(int esize_src, int esize_dst, const CopyTask* tasks, int ntasks,

@@ -265,6 +265,26 @@ void plan_level(LevelPlan& P, const std::vector<int>& n,
     join_chunks<int64_t, int>(M, nch, scnt, soff, nullptr, P.schur_ptr, P.schur_off, nullptr, cb);
   }
 
+  // ---- dependencies of the persistent launch ------------------------------
+  P.dep_ptr.assign(M + 1, 0);
+  for (int p = 0; p < np; ++p) {
+    const int i = P.pair_i[p], k = P.pair_k[p];
+    if (i == k) continue;
+    if (P.colour[k] < P.colour[i]) ++P.dep_ptr[i + 1];
+    else if (P.colour[i] < P.colour[k]) ++P.dep_ptr[k + 1];
+  }
+  for (int i = 0; i < M; ++i) P.dep_ptr[i + 1] += P.dep_ptr[i];
+  P.dep_idx.resize(P.dep_ptr[M]);
+  {
+    std::vector<int> fill(P.dep_ptr.begin(), P.dep_ptr.end() - 1);
+    for (int p = 0; p < np; ++p) {
+      const int i = P.pair_i[p], k = P.pair_k[p];
+      if (i == k) continue;
+      if (P.colour[k] < P.colour[i]) P.dep_idx[fill[i]++] = k;
+      else if (P.colour[i] < P.colour[k]) P.dep_idx[fill[k]++] = i;
+    }
+  }
+
   // ---- factor and vector layout ------------------------------------------
   P.u_off.resize(M);
   P.l_off.resize(M);

@@ -271,10 +271,10 @@ __device__ void store_row_tile(const T* sm, T* X, int i, int k, int n, int nk, i
   }
 }
 
+// One block row i of the level (Algorithm 2 for one i), by the whole CTA.
 template <typename T, int NT>
-__global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
-    ce_row_kernel(LevelDev L, int first, int level, double tol, int tol_mode, int* status, int nmax,
-                  int LD, int QW, LearnedArgs la) {
+__device__ __forceinline__ void row_block(const LevelDev& L, const int i, int level, double tol, int tol_mode,
+                                          int* status, int nmax, int LD, int QW, const LearnedArgs& la) {
   constexpr int kWarpsNT = NT / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NL = nmax * LD;
@@ -304,7 +304,6 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
   __shared__ T s_tq[64], s_probe[2];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int i = L.order[first + blockIdx.x];
   const int n = L.n[i];
   const int ci = L.colour[i];
   T* pool = reinterpret_cast<T*>(L.pool);
@@ -1085,6 +1084,81 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : 3))
   }
 }
 
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+constexpr unsigned long long kDepWaitNs = 2000000000ull;  // give up a dependency wait after 2 s
+constexpr int kDepWaitPolls = 1 << 24;                    // ... or after this many polls
+
+// Persistent level kernel.  CTAs take rows in the colour-major elimination
+// order from one counter; before row i starts, every row of a lower colour
+// within distance 2 of i (the rows whose eliminations write the pairs row i
+// reads or writes) must have finished.  Two rows of different colours that
+// touch a common pair are always within distance 2, so every pair sees its
+// updates in colour order, exactly as with one launch per colour, while rows
+// of later colours start as soon as their own neighbourhood is done.
+// A row only waits for rows taken earlier, which are held by running CTAs,
+// so the waits always end; they are still bounded (time and polls), and a
+// recorded error anywhere ends them.
+template <typename T, int NT>
+__global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : NT >= 256 ? 3 : 6))
+    ce_row_kernel(LevelDev L, int count, int level, double tol, int tol_mode, int* status, int nmax, int LD,
+                  int QW, LearnedArgs la) {
+  __shared__ int s_q;
+  const int tid = threadIdx.x;
+  for (;;) {
+    if (tid == 0) {
+      int q = atomicAdd(L.qnext, 1);
+      if (q >= count || ld_acquire(status) != 0) q = -1;
+      if (q >= 0) {
+        const int i = L.order[q];
+        const unsigned long long t0 = globaltimer_ns();
+        int polls = 0;
+        for (int d = L.dep_ptr[i]; d < L.dep_ptr[i + 1] && q >= 0; ++d) {
+          const int* flag = L.done + L.dep_idx[d];
+          while (ld_acquire(flag) == 0) {
+            if (ld_acquire(status) != 0) {
+              q = -1;
+              break;
+            }
+            if (++polls > kDepWaitPolls || globaltimer_ns() - t0 > kDepWaitNs) {
+              set_status(status, CE_ERR_CUDA, level, i, 5);
+              q = -1;
+              break;
+            }
+            __nanosleep(128);
+          }
+        }
+      }
+      s_q = q;
+    }
+    __syncthreads();
+    const int q = s_q;
+    if (q < 0) return;
+    __threadfence();
+    const int i = L.order[q];
+    row_block<T, NT>(L, i, level, tol, tol_mode, status, nmax, LD, QW, la);
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release(L.done + i, 1);
+    }
+  }
+}
+
 int choose_ld(int nmax) { return (nmax % 2 == 0) ? nmax + 1 : nmax; }
 
 size_t smem_bytes(int es, int nmax, int LD, int QW) {  // QW <= 16
@@ -1117,8 +1191,8 @@ cudaError_t max_dyn_smem(size_t* out) {
 }
 
 template <typename T, int NT>
-cudaError_t launch_nt(const LevelDev& L, int first, int count, int level, double tol, int tol_mode,
-                      int* status, int nmax, size_t budget, const LearnedArgs& la, cudaStream_t s) {
+cudaError_t launch_nt(const LevelDev& L, int count, int level, double tol, int tol_mode, int* status, int nmax,
+                      size_t budget, const LearnedArgs& la, cudaStream_t s) {
   const int LD = choose_ld(nmax);
   size_t limit = 0;
   cudaError_t e = max_dyn_smem<T, NT>(&limit);
@@ -1128,8 +1202,15 @@ cudaError_t launch_nt(const LevelDev& L, int first, int count, int level, double
   while (QW > 1 && smem_bytes(sizeof(T), nmax, LD, QW) > budget) --QW;
   const size_t smem = smem_bytes(sizeof(T), nmax, LD, QW);
   if (smem > limit) return cudaErrorInvalidValue;
+  // one resident wave of persistent CTAs
+  int dev = 0, sms = 0, per_sm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ce_row_kernel<T, NT>, NT, smem);
+  if (e != cudaSuccess) return e;
+  const int grid = std::max(1, std::min(count, std::max(per_sm, 1) * sms));
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  ce_row_kernel<T, NT><<<count, NT, smem, s>>>(L, first, level, tol, tol_mode, status, nmax, LD, QW, la);
+  ce_row_kernel<T, NT><<<grid, NT, smem, s>>>(L, count, level, tol, tol_mode, status, nmax, LD, QW, la);
   return cudaGetLastError();
 }
 
@@ -1137,19 +1218,20 @@ cudaError_t launch_nt(const LevelDev& L, int first, int count, int level, double
 
 size_t row_kernel_smem(int esize) { return smem_bytes(esize, kNMax, choose_ld(kNMax), 1); }
 
-cudaError_t launch_row_kernel(int esize, const LevelDev& L, int first, int count, int level,
-                              double tol, int tol_mode, int* status, int nmax, int busy_ctas,
-                              const LearnedArgs& la, cudaStream_t s) {
+cudaError_t launch_row_kernel(int esize, const LevelDev& L, int count, int level, double tol, int tol_mode,
+                              int* status, int nmax, int shape, const LearnedArgs& la, cudaStream_t s) {
   if (count <= 0) return cudaSuccess;
   nmax = std::max(nmax, 1);
-  // many rows in the colour: 256-thread CTAs, about 3 per SM; few rows: one
-  // 512-thread CTA per SM with the whole shared memory
-  const bool busy = busy_ctas >= 2 * 152;
-  if (esize == 8)
-    return busy ? launch_nt<double, 256>(L, first, count, level, tol, tol_mode, status, nmax, 72 * 1024, la, s)
-                : launch_nt<double, 512>(L, first, count, level, tol, tol_mode, status, nmax, ~size_t(0), la, s);
-  return busy ? launch_nt<float, 256>(L, first, count, level, tol, tol_mode, status, nmax, 72 * 1024, la, s)
-              : launch_nt<float, 512>(L, first, count, level, tol, tol_mode, status, nmax, ~size_t(0), la, s);
+  // shape 0: 256-thread CTAs, about 3 per SM (72 KB each); 1: 512-thread
+  // CTAs with the whole shared memory; 2: 128-thread CTAs of 40 KB
+  if (esize == 8) {
+    if (shape == 0) return launch_nt<double, 256>(L, count, level, tol, tol_mode, status, nmax, 72 * 1024, la, s);
+    if (shape == 2) return launch_nt<double, 128>(L, count, level, tol, tol_mode, status, nmax, 40 * 1024, la, s);
+    return launch_nt<double, 512>(L, count, level, tol, tol_mode, status, nmax, ~size_t(0), la, s);
+  }
+  if (shape == 0) return launch_nt<float, 256>(L, count, level, tol, tol_mode, status, nmax, 72 * 1024, la, s);
+  if (shape == 2) return launch_nt<float, 128>(L, count, level, tol, tol_mode, status, nmax, 40 * 1024, la, s);
+  return launch_nt<float, 512>(L, count, level, tol, tol_mode, status, nmax, ~size_t(0), la, s);
 }
 
 }  // namespace ce

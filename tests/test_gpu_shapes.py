@@ -1,0 +1,61 @@
+"""GPU: every CTA shape of the persistent row kernel gives the oracle's
+factorization, and the autotuner keeps the fastest shape per level.
+
+A shape changes only how a row's work is spread over threads, so each one is
+held to the FP64 parity bar (ranks equal away from the threshold, apply within
+1e-10 of the oracle's); the autotuned choice is the argmin of its own timings.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import ce as oce
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ceg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_09133_gb300 import build
+    build.build()
+    import paper_1603_09133_gb300 as m
+    return m
+
+
+@pytest.fixture(scope="module")
+def problem():
+    w = wl.make_workload("poisson2d_64_B16")
+    Fo = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J)
+    return w, Fo, oce.apply(Fo, w.b)
+
+
+@pytest.mark.parametrize("shape", [0, 1, 2])
+def test_every_shape_matches_oracle(ceg, problem, shape):
+    w, Fo, zo = problem
+    csb = ceg.csb_build(w.A, w.perm, w.B)
+    F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, row_shape=shape)
+    assert list(F.info.row_shape[:w.levels]) == [shape] * w.levels
+    for l, lev in enumerate(Fo.levels):
+        n_g, r_g, c_g, _ = F.level(l)
+        assert list(c_g) == list(lev.colour)
+        assert list(r_g) == list(lev.ranks)
+    z = torch.empty(w.A.shape[0], dtype=torch.float64, device="cuda")
+    ceg.ce_apply(F, torch.as_tensor(w.b, device="cuda"), z)
+    err = np.linalg.norm(z.cpu().numpy() - zo) / np.linalg.norm(zo)
+    assert err <= 1e-10, err
+
+
+def test_autotune_keeps_fastest_shape(ceg, problem):
+    w, _, _ = problem
+    csb = ceg.csb_build(w.A, w.perm, w.B)
+    t = ceg.ce_autotune(csb, tol=w.tol, levels=w.levels, J=w.J)
+    assert t.shape == (3, w.levels) and (t > 0).all()
+    F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J)
+    assert list(F.info.row_shape[:w.levels]) == [int(np.argmin(t[:, l])) for l in range(w.levels)]
+    # another precision has no tuned table: the heuristic decides
+    F32 = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision="fp32")
+    assert all(s in (0, 1) for s in F32.info.row_shape[:w.levels])
