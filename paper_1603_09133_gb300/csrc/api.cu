@@ -261,7 +261,9 @@ void build_level_store(LevelStore& st, int esize, cudaStream_t s) {
                o_do = pk.addv(P.diag_off), o_sp = pk.addv(P.schur_ptr), o_so = pk.addv(P.schur_off),
                o_uo = pk.addv(P.u_off), o_lo = pk.addv(P.l_off), o_wo = pk.addv(P.w_off),
                o_vo = pk.addv(P.vec_off), o_dp = pk.addv(P.dep_ptr), o_di = pk.addv(P.dep_idx),
+               o_rp = pk.addv(P.rdep_ptr), o_ri = pk.addv(P.rdep_idx),
                o_rank = pk.zeros(P.M * sizeof(int)), o_done = pk.zeros(P.M * sizeof(int)),
+               o_fd = pk.zeros(P.M * sizeof(int)), o_bd = pk.zeros(P.M * sizeof(int)),
                o_q = pk.zeros(sizeof(int)),
                o_gd = pk.zeros(P.M * sizeof(int64_t)), o_tau = pk.zeros(P.M * sizeof(double)),
                o_sig = pk.zeros(P.vec_len * sizeof(double));
@@ -295,6 +297,12 @@ void build_level_store(LevelStore& st, int esize, cudaStream_t s) {
   D.dep_idx = reinterpret_cast<const int*>(b + o_di);
   D.done = reinterpret_cast<int*>(b + o_done);
   D.qnext = reinterpret_cast<int*>(b + o_q);
+  D.rdep_ptr = reinterpret_cast<const int*>(b + o_rp);
+  D.rdep_idx = reinterpret_cast<const int*>(b + o_ri);
+  D.fdone = reinterpret_cast<int*>(b + o_fd);
+  D.bdone = reinterpret_cast<int*>(b + o_bd);
+  D.aq = nullptr;
+  D.epoch = nullptr;
   const size_t ub = P.u_elems * esize, lb = P.l_elems * esize, wb = P.w_elems * esize;
   st.fac_bytes = ub + lb + wb + 3 * 256;
   st.fac = dalloc(st.fac_bytes, s);
@@ -426,6 +434,7 @@ void free_factor(ce_factor* F, cudaStream_t s) {
   dfree(F->d_coarse, s);
   dfree(F->d_cdinv, s);
   dfree(F->d_csys, s);
+  dfree(F->d_apply, s);
   if (F->pcg) {
     cudaDeviceSynchronize();
     ce::pcg_batch_release(F->pcg);
@@ -934,6 +943,13 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       }
       F->coarse_base = tot;
       tot += F->nc;
+      const int nlv = static_cast<int>(F->levels.size());
+      F->d_apply = static_cast<int*>(dalloc((2 * nlv + 1) * sizeof(int), s));
+      check(cudaMemsetAsync(F->d_apply, 0, (2 * nlv + 1) * sizeof(int), s), "memset apply state");
+      for (int l = 0; l < nlv; ++l) {
+        F->levels[l].dev.aq = F->d_apply + 2 * l;
+        F->levels[l].dev.epoch = F->d_apply + 2 * nlv;
+      }
       F->d_work = static_cast<double*>(dalloc(std::max<int64_t>(tot, 1) * sizeof(double), s));
       check(cudaStreamSynchronize(s), "factor sync");
       int64_t bytes = coarse_elems * 8 + tot * 8;
@@ -1042,15 +1058,13 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev, void*
     double* coarse = F->d_work + F->coarse_base;
     const int nl = static_cast<int>(F->levels.size());
     double* v0 = nl ? F->d_work + F->vec_base[0] : coarse;
+    if (nl) check(ce::launch_apply_prep(F->d_apply, 2 * nl, F->d_apply + 2 * nl, s), "apply prep");
     check(ce::launch_perm(F->d_perm, F->N, r_dev, v0, 1, s), "perm gather");
     for (int l = 0; l < nl; ++l) {
       const LevelStore& st = F->levels[l];
       double* v = F->d_work + F->vec_base[l];
       double* vn = (l + 1 < nl) ? F->d_work + F->vec_base[l + 1] : coarse;
-      for (int c = 0; c < st.plan->ncolours; ++c)
-        check(ce::launch_apply_fwd(es, st.dev, st.plan->colour_ptr[c],
-                                   st.plan->colour_ptr[c + 1] - st.plan->colour_ptr[c], st.plan->nmax, v, s),
-              "apply fwd");
+      check(ce::launch_apply_fwd(es, st.dev, v, F->d_status, s), "apply fwd");
       check(ce::launch_level_move(st.dev, v, vn, 1, s), "level move");
     }
     if (F->nsys == 1)
@@ -1063,10 +1077,7 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev, void*
       double* v = F->d_work + F->vec_base[l];
       double* vn = (l + 1 < nl) ? F->d_work + F->vec_base[l + 1] : coarse;
       check(ce::launch_level_move(st.dev, v, vn, 0, s), "level move");
-      for (int c = st.plan->ncolours - 1; c >= 0; --c)
-        check(ce::launch_apply_bwd(es, st.dev, st.plan->colour_ptr[c],
-                                   st.plan->colour_ptr[c + 1] - st.plan->colour_ptr[c], st.plan->nmax, v, s),
-              "apply bwd");
+      check(ce::launch_apply_bwd(es, st.dev, v, F->d_status, s), "apply bwd");
     }
     check(ce::launch_perm(F->d_perm, F->N, v0, z_dev, 0, s), "perm scatter");
   } catch (const CudaFail& f) {

@@ -43,23 +43,41 @@ struct Targets {
   int64_t woff[kMaxTgt], voff[kMaxTgt];
 };
 
-__device__ void targets_of(const LevelDev& L, int i, int n, int r, Targets& T) {
+// Filled by the 32 lanes of one warp, lane t for target t (the loads of all
+// targets in flight at once; prefix sums by warp scans).
+__device__ void targets_of(const LevelDev& L, int i, int n, int r, Targets& T, int lane) {
   const int ci = L.colour[i];
   const int c0 = L.close_ptr[i], c1 = L.close_ptr[i + 1];
-  T.nt = min(1 + (c1 - c0), kMaxTgt);
-  T.w[0] = r;
-  T.woff[0] = 0;
-  T.voff[0] = L.vec_off[i];
-  T.pre[0] = 0;
-  int colst = n;
-  for (int t = 1; t < T.nt; ++t) {
-    const int p = L.close_blk[c0 + t - 1];
-    T.w[t] = width_of_a(L, p, ci);
-    T.woff[t] = (int64_t)n * colst;
-    T.voff[t] = L.vec_off[p];
-    colst += L.n[p];
+  const int nt = min(1 + (c1 - c0), kMaxTgt);
+  int w = 0, np = 0;
+  int64_t vo = 0;
+  if (lane == 0) {
+    w = r;
+    np = n;
+    vo = L.vec_off[i];
+  } else if (lane < nt) {
+    const int p = L.close_blk[c0 + lane - 1];
+    w = width_of_a(L, p, ci);
+    np = L.n[p];
+    vo = L.vec_off[p];
   }
-  for (int t = 0; t < T.nt; ++t) T.pre[t + 1] = T.pre[t] + T.w[t];
+  int sw = w, sn = np;  // inclusive scans of the widths and of the block sizes
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int a = __shfl_up_sync(0xffffffffu, sw, o), b = __shfl_up_sync(0xffffffffu, sn, o);
+    if (lane >= o) {
+      sw += a;
+      sn += b;
+    }
+  }
+  if (lane < nt) {
+    T.w[lane] = w;
+    T.woff[lane] = (int64_t)n * (sn - np);  // W columns of target t start after n + sizes before it
+    T.voff[lane] = vo;
+    T.pre[lane] = sw - w;
+  }
+  if (lane == nt - 1) T.pre[nt] = sw;
+  if (lane == 0) T.nt = nt;
 }
 
 // Every factor element is read exactly once per apply, so U_i, L_hat_i^{-1}
@@ -69,21 +87,6 @@ __device__ void targets_of(const LevelDev& L, int i, int n, int r, Targets& T) {
 // an FP64 operator whose error is the FP32 rounding of M^{-1}, far below the
 // compression tolerance); the FP64 form stays FP64 throughout.
 
-// 4 independent partial sums of x[k] * M[k * stride] for k in [k0, k1)
-template <typename T>
-__device__ __forceinline__ T dot_strided(const T* __restrict__ M, int stride, const T* x, int k0, int k1) {
-  T s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-  int k = k0;
-  for (; k + 3 < k1; k += 4) {
-    s0 += M[(int64_t)k * stride] * x[k];
-    s1 += M[(int64_t)(k + 1) * stride] * x[k + 1];
-    s2 += M[(int64_t)(k + 2) * stride] * x[k + 2];
-    s3 += M[(int64_t)(k + 3) * stride] * x[k + 3];
-  }
-  for (; k < k1; ++k) s0 += M[(int64_t)k * stride] * x[k];
-  return (s0 + s1) + (s2 + s3);
-}
-
 template <typename T>
 __device__ __forceinline__ T warp_sum_t(T v) {
 #pragma unroll
@@ -91,15 +94,66 @@ __device__ __forceinline__ T warp_sum_t(T v) {
   return v;
 }
 
+// A strided vector of the factor: element k is p[k * s].
+template <typename T>
+struct Strided {
+  const T* p;
+  int64_t s;
+};
+
+// sum_{k in [k0, k1)} M.p[k M.s] x[k] with 8 independent partial sums, so a
+// thread keeps 8 loads of the factor in flight
+template <typename T>
+__device__ __forceinline__ T dot8(Strided<T> M, const T* x, int k0, int k1) {
+  T s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  int k = k0;
+  for (; k + 7 < k1; k += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) s[u] += M.p[(k + u) * M.s] * x[k + u];
+  }
+  for (; k < k1; ++k) s[0] += M.p[k * M.s] * x[k];
+  return ((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7]));
+}
+
+// CTA GEMV: out(a, sum_{k in [lo(a), hi(a))} row(a)[k] x[k]) for a < A.
+// With A <= NT / 2 the k range of each output is split over G = NT / A
+// threads (partial sums in part[G * A], added in slice order); otherwise one
+// thread per output.  Ends with a barrier.
+template <typename T, int NT, class Row, class Lo, class Hi, class Out>
+__device__ __forceinline__ void cta_gemv(int A, Row row, const T* x, Lo lo, Hi hi, Out out, T* part) {
+  const int tid = threadIdx.x;
+  if (A > NT / 2) {
+    for (int a = tid; a < A; a += NT) out(a, dot8<T>(row(a), x, lo(a), hi(a)));
+  } else if (A > 0) {
+    const int G = NT / A, a = tid % A, g = tid / A;
+    if (g < G) {
+      const int l0 = lo(a), len = hi(a) - l0;
+      part[g * A + a] = dot8<T>(row(a), x, l0 + len * g / G, l0 + len * (g + 1) / G);
+    }
+    __syncthreads();
+    for (int b = tid; b < A; b += NT) {
+      T acc = 0;
+      for (int h = 0; h < G; ++h) acc += part[h * A + b];
+      out(b, acc);
+    }
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int target_of(const Targets& tg, int f) {
+  int t = 0;
+  while (f >= tg.pre[t + 1]) ++t;
+  return t;
+}
+
 // Forward step of block i: y_i <- U_i^T y_i; z = L_hat^{-1} y_i[r:];
 // y_t[:w_t] -= W_t^T z for every target t (basis of i first); y_i[r:] = z.
-template <typename T>
-__global__ void __launch_bounds__(kApplyThreads) apply_fwd_kernel(LevelDev L, int first, double* vec) {
+template <typename T, int NT>
+__device__ __forceinline__ void fwd_block(const LevelDev& L, const int i, double* vec) {
   __shared__ T ys[kNMax], yt[kNMax], z[kNMax];
-  __shared__ T part[kApplyThreads];
+  __shared__ T part[NT];
   __shared__ Targets tg;
   const int tid = threadIdx.x;
-  const int i = L.order[first + blockIdx.x];
   const int n = L.n[i];
   if (n == 0) return;
   const int r = L.rank[i], m = n - r;
@@ -107,59 +161,50 @@ __global__ void __launch_bounds__(kApplyThreads) apply_fwd_kernel(LevelDev L, in
   const T* U = reinterpret_cast<const T*>(L.U) + L.u_off[i];
   const T* Li = reinterpret_cast<const T*>(L.L) + L.l_off[i];
   const T* W = reinterpret_cast<const T*>(L.W) + L.w_off[i];
-  for (int a = tid; a < n; a += kApplyThreads) ys[a] = static_cast<T>(v[a]);
-  if (tid == 0) targets_of(L, i, n, r, tg);
+  for (int a = tid; a < n; a += NT) ys[a] = static_cast<T>(v[a]);
+  if (tid < 32) targets_of(L, i, n, r, tg, tid);
   __syncthreads();
-  // yt = U^T ys: thread (a, g) sums rows k = g (mod G) of column a
-  {
-    const int G = kApplyThreads / n, a = tid % n, g = tid / n;
-    if (g < G) {
-      T s = 0;
-      for (int k = g; k < n; k += G) s += U[k * n + a] * ys[k];
-      part[g * n + a] = s;
-    }
-    __syncthreads();
-    if (tid < n) {
-      T s = 0;
-      for (int h = 0; h < G; ++h) s += part[h * n + tid];
-      yt[tid] = s;
-    }
-    __syncthreads();
-  }
-  // z = L_hat^{-1} yt[r:] (lower, row-major: one warp per row)
-  {
-    const int lane = tid & 31, warp = tid >> 5;
-    for (int a = warp; a < m; a += kApplyThreads / 32) {
-      T s = 0;
-      for (int k = lane; k <= a; k += 32) s += Li[a * m + k] * yt[r + k];
-      s = warp_sum_t(s);
-      if (lane == 0) z[a] = s;
-    }
-    __syncthreads();
-  }
-  for (int a = tid; a < m; a += kApplyThreads) v[r + a] = static_cast<double>(z[a]);
-  const int tot = tg.pre[tg.nt];
-  for (int f = tid; f < tot; f += kApplyThreads) {
-    int t = 0;
-    while (f >= tg.pre[t + 1]) ++t;
-    const int c = f - tg.pre[t], w = tg.w[t];
-    const T s = dot_strided(W + tg.woff[t] + c, w, z, 0, m);
-    if (t == 0)
-      v[c] = static_cast<double>(yt[c] - s);
-    else
-      vec[tg.voff[t] + c] -= static_cast<double>(s);
-  }
+  auto zero = [](int) { return 0; };
+  // yt = U^T ys: column a of U
+  cta_gemv<T, NT>(
+      n, [&](int a) { return Strided<T>{U + a, n}; }, ys, zero, [&](int) { return n; },
+      [&](int a, T s) { yt[a] = s; }, part);
+  // z = L_hat^{-1} yt[r:]: row a of the lower factor, k <= a
+  cta_gemv<T, NT>(
+      m, [&](int a) { return Strided<T>{Li + a * m, 1}; }, yt + r, zero, [](int a) { return a + 1; },
+      [&](int a, T s) {
+        z[a] = s;
+        v[r + a] = static_cast<double>(s);
+      },
+      part);
+  // every target column c of W_t: y_t[c] -= (W_t^T z)[c]; the basis of i gets yt - W_b^T z
+  cta_gemv<T, NT>(
+      tg.pre[tg.nt],
+      [&](int f) {
+        const int t = target_of(tg, f);
+        return Strided<T>{W + tg.woff[t] + (f - tg.pre[t]), tg.w[t]};
+      },
+      z, zero, [&](int) { return m; },
+      [&](int f, T s) {
+        const int t = target_of(tg, f), c = f - tg.pre[t];
+        if (t == 0)
+          v[c] = static_cast<double>(yt[c] - s);
+        else
+          vec[tg.voff[t] + c] -= static_cast<double>(s);
+      },
+      part);
 }
 
 // Backward step of block i (transpose, reverse order): rhs = z - W x_t over
 // all targets; x_n = L_hat^{-T} rhs; y_i <- U_i [x_b; x_n].
-template <typename T>
-__global__ void __launch_bounds__(kApplyThreads) apply_bwd_kernel(LevelDev L, int first, double* vec) {
+template <typename T, int NT>
+__device__ __forceinline__ void bwd_block(const LevelDev& L, const int i, double* vec) {
   __shared__ T xf[kNMax], rhs[kNMax];
   __shared__ T xt[kMaxTgt * kNMax];
+  __shared__ T pt[kNMax * kMaxTgt];  // (W_t x_t)[a] per row a and target t
+  __shared__ T part[NT];
   __shared__ Targets tg;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int i = L.order[first + blockIdx.x];
   const int n = L.n[i];
   if (n == 0) return;
   const int r = L.rank[i], m = n - r;
@@ -167,40 +212,146 @@ __global__ void __launch_bounds__(kApplyThreads) apply_bwd_kernel(LevelDev L, in
   const T* U = reinterpret_cast<const T*>(L.U) + L.u_off[i];
   const T* Li = reinterpret_cast<const T*>(L.L) + L.l_off[i];
   const T* W = reinterpret_cast<const T*>(L.W) + L.w_off[i];
-  for (int a = tid; a < n; a += kApplyThreads) xf[a] = static_cast<T>(v[a]);   // [x_b; z]
-  if (tid == 0) targets_of(L, i, n, r, tg);
+  for (int a = tid; a < n; a += NT) xf[a] = static_cast<T>(v[a]);   // [x_b; z]
+  if (warp == 0) targets_of(L, i, n, r, tg, lane);
   __syncthreads();
-  const int tot = tg.pre[tg.nt];
-  for (int f = tid; f < tot; f += kApplyThreads) {
-    int t = 0;
-    while (f >= tg.pre[t + 1]) ++t;
-    const int c = f - tg.pre[t];
+  const int nt = tg.nt, tot = tg.pre[nt];
+  for (int f = tid; f < tot; f += NT) {
+    const int t = target_of(tg, f), c = f - tg.pre[t];
     xt[f] = (t == 0) ? xf[c] : static_cast<T>(vec[tg.voff[t] + c]);
   }
   __syncthreads();
-  // rhs = z - W x_t: one warp per row of W (contiguous within each target)
-  for (int a = warp; a < m; a += kApplyThreads / 32) {
-    T s = 0;
-    for (int t = 0; t < tg.nt; ++t) {
-      const int w = tg.w[t];
-      const T* Wt = W + tg.woff[t] + (int64_t)a * w;
-      const T* x = xt + tg.pre[t];
-      for (int c = lane; c < w; c += 32) s += Wt[c] * x[c];
+  auto zero = [](int) { return 0; };
+  // (W_t x_t)[a] for every (row a, target t): row a of W_t against xt[pre[t]:pre[t+1]]
+  cta_gemv<T, NT>(
+      m * nt,
+      [&](int e) {
+        const int a = e / nt, t = e - a * nt;
+        return Strided<T>{W + tg.woff[t] + (int64_t)a * tg.w[t] - tg.pre[t], 1};
+      },
+      xt, [&](int e) { return tg.pre[e % nt]; }, [&](int e) { return tg.pre[e % nt + 1]; },
+      [&](int e, T s) { pt[e] = s; }, part);
+  for (int a = tid; a < m; a += NT) {
+    T acc = 0;
+    for (int t = 0; t < nt; ++t) acc += pt[a * nt + t];
+    rhs[a] = xf[r + a] - acc;
+  }
+  __syncthreads();
+  // x_n = L_hat^{-T} rhs: column a of the lower factor, k >= a
+  cta_gemv<T, NT>(
+      m, [&](int a) { return Strided<T>{Li + a, m}; }, rhs, [](int a) { return a; }, [&](int) { return m; },
+      [&](int a, T s) { xf[r + a] = s; }, part);
+  // y_i = U_i xf: row a of U
+  cta_gemv<T, NT>(
+      n, [&](int a) { return Strided<T>{U + (int64_t)a * n, 1}; }, xf, zero, [&](int) { return n; },
+      [&](int a, T s) { v[a] = static_cast<double>(s); }, part);
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+constexpr unsigned long long kWaitNs = 2000000000ull;  // a dependency wait gives up after 2 s
+constexpr int kWaitPolls = 1 << 24;                    // ... or after this many polls
+
+// Warp-wide wait until flag[idx[d]] == want for every d in [d0, d1): each
+// lane polls its own flags, the warp votes.  Ends early (false) on a
+// recorded error or after kWaitNs / kWaitPolls, recording reason 6.
+__device__ bool wait_flags(const int* flag, const int* idx, int d0, int d1, int want, int* status, int row,
+                           int lane) {
+  const unsigned long long t0 = globaltimer_ns();
+  int polls = 0;
+  for (int base = d0; base < d1; base += 32) {
+    const int d = base + lane;
+    const int* f = d < d1 ? flag + idx[d] : nullptr;
+    for (;;) {
+      const bool ok = f == nullptr || ld_acquire(f) == want;
+      if (__all_sync(0xffffffffu, ok)) break;
+      int bad = 0;
+      if (lane == 0) {
+        if (ld_acquire(status) != 0)
+          bad = 1;
+        else if (++polls > kWaitPolls || globaltimer_ns() - t0 > kWaitNs)
+          bad = 2;
+        if (bad == 2 && atomicCAS(status, 0, CE_ERR_CUDA) == 0) {
+          status[2] = row;
+          status[3] = 6;
+        }
+      }
+      if (__shfl_sync(0xffffffffu, bad, 0)) return false;
+      __nanosleep(64);
     }
-    s = warp_sum_t(s);
-    if (lane == 0) rhs[a] = xf[r + a] - s;
   }
-  __syncthreads();
-  // x_n = L_hat^{-T} rhs: column a of L_hat^{-1}, contiguous across threads
-  for (int a = tid; a < m; a += kApplyThreads) xf[r + a] = dot_strided(Li + a, m, rhs, a, m);
-  __syncthreads();
-  // y_i = U_i xf: one warp per row
-  for (int a = warp; a < n; a += kApplyThreads / 32) {
-    T s = 0;
-    for (int k = lane; k < n; k += 32) s += U[a * n + k] * xf[k];
-    s = warp_sum_t(s);
-    if (lane == 0) v[a] = static_cast<double>(s);
+  return true;
+}
+
+// One persistent launch per level and direction.  Rows are taken from a
+// counter in the level's elimination order (forward) or its reverse
+// (backward); a row waits until every row of an earlier step within distance
+// 2 (lower colour forward, higher colour backward) carries this apply's epoch
+// in its flag, so every vector entry sees its updates in the colour order of
+// the per-colour schedule.  Rows only wait for rows taken earlier, held by
+// running CTAs; waits are bounded anyway and end on a recorded error.  The
+// epoch and counters live in device memory (advanced by apply_prep_kernel),
+// so the launches can be replayed from a CUDA graph.
+template <typename T, int NT, bool kFwd>
+__global__ void __launch_bounds__(NT) apply_level_kernel(LevelDev L, double* vec, int* status) {
+  __shared__ int s_q;
+  const int tid = threadIdx.x;
+  const int count = L.M;
+  const int ep = *L.epoch;
+  int* qctr = L.aq + (kFwd ? 0 : 1);
+  int* flag = kFwd ? L.fdone : L.bdone;
+  const int* dp = kFwd ? L.dep_ptr : L.rdep_ptr;
+  const int* di = kFwd ? L.dep_idx : L.rdep_idx;
+  const int lane = tid & 31;
+  for (;;) {
+    if (tid < 32) {
+      int q = 0;
+      if (lane == 0) {
+        q = atomicAdd(qctr, 1);
+        if (q >= count || ld_acquire(status) != 0) q = -1;
+      }
+      q = __shfl_sync(0xffffffffu, q, 0);
+      if (q >= 0) {
+        const int i = L.order[kFwd ? q : count - 1 - q];
+        if (!wait_flags(flag, di, dp[i], dp[i + 1], ep, status, i, lane)) q = -1;
+      }
+      if (lane == 0) s_q = q;
+    }
+    __syncthreads();
+    const int q = s_q;
+    if (q < 0) return;
+    __threadfence();
+    const int i = L.order[kFwd ? q : count - 1 - q];
+    if (kFwd)
+      fwd_block<T, NT>(L, i, vec);
+    else
+      bwd_block<T, NT>(L, i, vec);
+    __syncthreads();
+    if (tid == 0) {
+      __threadfence();
+      st_release(flag + i, ep);
+    }
   }
+}
+
+// start of an apply: next epoch, queue counters of every level back to 0
+__global__ void apply_prep_kernel(int* q, int nq, int* epoch) {
+  for (int t = threadIdx.x; t < nq; t += blockDim.x) q[t] = 0;
+  if (threadIdx.x == 0) *epoch += 1;
 }
 
 // basis parts between a level vector and the next (forward: gather)
@@ -239,6 +390,7 @@ __global__ void __launch_bounds__(kCS) coarse_solve_kernel(const double* Lc, con
                                                            double* y) {
   cg::grid_group grid = cg::this_grid();
   __shared__ double yp[kPan], yq[kPan];
+  __shared__ double Ds[kPan * (kPan + 1)];  // one diagonal inverse, loaded coalesced
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gw = blockIdx.x * (kCS / 32) + warp, nwarps = gridDim.x * (kCS / 32);
   const int npan = (n + kPan - 1) / kPan;
@@ -247,11 +399,12 @@ __global__ void __launch_bounds__(kCS) coarse_solve_kernel(const double* Lc, con
     const int s0 = p * kPan, pe = min(n, s0 + kPan), h = pe - s0;
     if (blockIdx.x == 0) {
       for (int a = tid; a < h; a += kCS) yp[a] = y[s0 + a];
-      __syncthreads();
       const double* D = Dinv + (size_t)p * kPan * kPan;
+      for (int e = tid; e < kPan * kPan; e += kCS) Ds[(e / kPan) * (kPan + 1) + e % kPan] = D[e];
+      __syncthreads();
       for (int a = tid; a < h; a += kCS) {
         double s = 0.0;
-        for (int k = 0; k <= a; ++k) s += D[a * kPan + k] * yp[k];
+        for (int k = 0; k <= a; ++k) s += Ds[a * (kPan + 1) + k] * yp[k];
         yq[a] = s;
       }
       __syncthreads();
@@ -272,11 +425,12 @@ __global__ void __launch_bounds__(kCS) coarse_solve_kernel(const double* Lc, con
     const int s0 = p * kPan, pe = min(n, s0 + kPan), h = pe - s0;
     if (blockIdx.x == 0) {
       for (int a = tid; a < h; a += kCS) yp[a] = y[s0 + a];
-      __syncthreads();
       const double* D = Dinv + (size_t)p * kPan * kPan;
+      for (int e = tid; e < kPan * kPan; e += kCS) Ds[(e / kPan) * (kPan + 1) + e % kPan] = D[e];
+      __syncthreads();
       for (int a = tid; a < h; a += kCS) {
         double s = 0.0;
-        for (int k = a; k < h; ++k) s += D[k * kPan + a] * yp[k];
+        for (int k = a; k < h; ++k) s += Ds[k * (kPan + 1) + a] * yp[k];
         yq[a] = s;
       }
       __syncthreads();
@@ -299,6 +453,7 @@ __global__ void __launch_bounds__(kCS) coarse_solve_kernel(const double* Lc, con
 __global__ void __launch_bounds__(kCS) coarse_solve_sys_kernel(const double* Lc, const double* Dinv,
                                                                const int64_t* desc, int nsys, double* y) {
   __shared__ double yp[kPan];
+  __shared__ double Ds[kPan * (kPan + 1)];
   const int sy = blockIdx.x;
   const int n = static_cast<int>(desc[sy]);
   Lc += desc[nsys + sy];
@@ -309,11 +464,12 @@ __global__ void __launch_bounds__(kCS) coarse_solve_sys_kernel(const double* Lc,
   for (int p = 0; p < npan; ++p) {
     const int s0 = p * kPan, pe = min(n, s0 + kPan), h = pe - s0;
     for (int a = tid; a < h; a += kCS) yp[a] = y[s0 + a];
-    __syncthreads();
     const double* D = Dinv + (size_t)p * kPan * kPan;
+    for (int e = tid; e < kPan * kPan; e += kCS) Ds[(e / kPan) * (kPan + 1) + e % kPan] = D[e];
+    __syncthreads();
     for (int a = tid; a < h; a += kCS) {
       double s = 0.0;
-      for (int k = 0; k <= a; ++k) s += D[a * kPan + k] * yp[k];
+      for (int k = 0; k <= a; ++k) s += Ds[a * (kPan + 1) + k] * yp[k];
       y[s0 + a] = s;
     }
     __syncthreads();
@@ -328,11 +484,12 @@ __global__ void __launch_bounds__(kCS) coarse_solve_sys_kernel(const double* Lc,
   for (int p = npan - 1; p >= 0; --p) {
     const int s0 = p * kPan, pe = min(n, s0 + kPan), h = pe - s0;
     for (int a = tid; a < h; a += kCS) yp[a] = y[s0 + a];
-    __syncthreads();
     const double* D = Dinv + (size_t)p * kPan * kPan;
+    for (int e = tid; e < kPan * kPan; e += kCS) Ds[(e / kPan) * (kPan + 1) + e % kPan] = D[e];
+    __syncthreads();
     for (int a = tid; a < h; a += kCS) {
       double s = 0.0;
-      for (int k = a; k < h; ++k) s += D[k * kPan + a] * yp[k];
+      for (int k = a; k < h; ++k) s += Ds[k * (kPan + 1) + a] * yp[k];
       y[s0 + a] = s;
     }
     __syncthreads();
@@ -455,29 +612,48 @@ __global__ void pcg_scalars_kernel(double* scal, int stage) {
   }
 }
 
-template <typename T>
-cudaError_t apply_launch(const LevelDev& L, int first, int count, double* vec, cudaStream_t s, bool fwd) {
-  if (count <= 0) return cudaSuccess;
+template <typename T, int NT, bool kFwd>
+cudaError_t apply_launch_nt(const LevelDev& L, double* vec, int* status, cudaStream_t s) {
+  static int cap = 0;
+  if (cap == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, apply_level_kernel<T, NT, kFwd>, NT, 0);
+    if (e != cudaSuccess) return e;
+    cap = std::max(per_sm, 1) * sms;
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  if (fwd)
-    apply_fwd_kernel<T><<<count, kApplyThreads, 0, s>>>(L, first, vec);
-  else
-    apply_bwd_kernel<T><<<count, kApplyThreads, 0, s>>>(L, first, vec);
+  apply_level_kernel<T, NT, kFwd><<<std::min(L.M, cap), NT, 0, s>>>(L, vec, status);
   return cudaGetLastError();
+}
+
+// CTA width by level size: many small rows want many CTAs in flight, a
+// coarse level (few rows on its critical path) wants wide CTAs
+template <typename T, bool kFwd>
+cudaError_t apply_launch(const LevelDev& L, double* vec, int* status, cudaStream_t s) {
+  if (L.M <= 0) return cudaSuccess;
+  if (L.M >= 4096) return apply_launch_nt<T, 128, kFwd>(L, vec, status, s);
+  if (L.M >= 1024) return apply_launch_nt<T, 256, kFwd>(L, vec, status, s);
+  return apply_launch_nt<T, 512, kFwd>(L, vec, status, s);
 }
 
 }  // namespace
 
-cudaError_t launch_apply_fwd(int esize, const LevelDev& L, int first, int count, int nmax, double* vec,
-                             cudaStream_t s) {
-  return esize == 8 ? apply_launch<double>(L, first, count, vec, s, true)
-                    : apply_launch<float>(L, first, count, vec, s, true);
+cudaError_t launch_apply_prep(int* q, int nq, int* epoch, cudaStream_t s) {
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  apply_prep_kernel<<<1, 64, 0, s>>>(q, nq, epoch);
+  return cudaGetLastError();
 }
 
-cudaError_t launch_apply_bwd(int esize, const LevelDev& L, int first, int count, int nmax, double* vec,
-                             cudaStream_t s) {
-  return esize == 8 ? apply_launch<double>(L, first, count, vec, s, false)
-                    : apply_launch<float>(L, first, count, vec, s, false);
+cudaError_t launch_apply_fwd(int esize, const LevelDev& L, double* vec, int* status, cudaStream_t s) {
+  return esize == 8 ? apply_launch<double, true>(L, vec, status, s) : apply_launch<float, true>(L, vec, status, s);
+}
+
+cudaError_t launch_apply_bwd(int esize, const LevelDev& L, double* vec, int* status, cudaStream_t s) {
+  return esize == 8 ? apply_launch<double, false>(L, vec, status, s)
+                    : apply_launch<float, false>(L, vec, status, s);
 }
 
 cudaError_t launch_level_move(const LevelDev& L, double* cur, double* next, int forward,

@@ -89,6 +89,8 @@ struct LevelPlan {
   // rows of a lower colour within distance 2 of row i (the rows that must
   // finish before row i starts): [dep_ptr[i], dep_ptr[i+1]) of dep_idx
   std::vector<int> dep_ptr, dep_idx;
+  // the transpose: rows of a higher colour within distance 2 (backward apply)
+  std::vector<int> rdep_ptr, rdep_idx;
 };
 
 // Build the plan of a level from its sizes and level-start pattern (pairs
@@ -156,6 +158,12 @@ struct LevelDev {
   const int* dep_idx;
   int* done;            // per row: 1 once eliminated (persistent launch)
   int* qnext;           // next position of the persistent launch's queue
+  const int* rdep_ptr;  // higher-colour rows within distance 2 (CSR)
+  const int* rdep_idx;
+  int* fdone;           // per row: epoch of the last forward apply step done
+  int* bdone;           // ... and of the last backward step
+  int* aq;              // queue counters of the apply launches (fwd, bwd)
+  const int* epoch;     // epoch of the running apply
   void* pool;           // pair values (T)
   void* U;              // factor (T): U_i
   void* L;              //   L_hat_i^{-1} (m_i x m_i, lower)
@@ -213,6 +221,7 @@ struct ce_factor {
   std::vector<int64_t> vec_base;// start of each level vector in d_work
   int64_t coarse_base = 0;
   int* d_status = nullptr;
+  int* d_apply = nullptr;       // apply queue counters (2 per level) + epoch
   int64_t bytes = 0;
   ce_csb* owned_csb = nullptr;
   mutable ce::PcgBatch* pcg = nullptr;  // batched PCG state, built on first use

@@ -47,10 +47,11 @@ cudaError_t coarse_cholesky(double* A, const int64_t* desc, int nsys, int nmax, 
                             cudaStream_t s);
 
 // apply (x = Q^T L^{-T} L^{-1} Q r)
-cudaError_t launch_apply_fwd(int esize, const LevelDev& L, int first, int count, int nmax, double* vec,
-                             cudaStream_t s);
-cudaError_t launch_apply_bwd(int esize, const LevelDev& L, int first, int count, int nmax, double* vec,
-                             cudaStream_t s);
+// one persistent launch per level and direction (see apply_kernels.cu);
+// launch_apply_prep starts an apply (next epoch, queue counters zeroed)
+cudaError_t launch_apply_prep(int* q, int nq, int* epoch, cudaStream_t s);
+cudaError_t launch_apply_fwd(int esize, const LevelDev& L, double* vec, int* status, cudaStream_t s);
+cudaError_t launch_apply_bwd(int esize, const LevelDev& L, double* vec, int* status, cudaStream_t s);
 cudaError_t launch_level_move(const LevelDev& L, double* cur, double* next, int forward,
                               cudaStream_t s);
 cudaError_t launch_perm(const int32_t* perm, int64_t n, const double* in, double* out, int gather,

@@ -285,6 +285,16 @@ void plan_level(LevelPlan& P, const std::vector<int>& n,
     }
   }
 
+  P.rdep_ptr.assign(M + 1, 0);
+  for (int k : P.dep_idx) ++P.rdep_ptr[k + 1];
+  for (int i = 0; i < M; ++i) P.rdep_ptr[i + 1] += P.rdep_ptr[i];
+  P.rdep_idx.resize(P.dep_idx.size());
+  {
+    std::vector<int> fill(P.rdep_ptr.begin(), P.rdep_ptr.end() - 1);
+    for (int i = 0; i < M; ++i)
+      for (int d = P.dep_ptr[i]; d < P.dep_ptr[i + 1]; ++d) P.rdep_idx[fill[P.dep_idx[d]]++] = i;
+  }
+
   // ---- factor and vector layout ------------------------------------------
   P.u_off.resize(M);
   P.l_off.resize(M);

@@ -1013,17 +1013,24 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     if (tid == 0) set_status(status, CE_ERR_LIMIT, level, i);
     return;
   }
-  if (tid == 0) {
-    s_tgt[0] = i;
-    s_w[0] = r;
-    s_colst[0] = 0;
-    int cs = n;
-    for (int t = 1; t < nt; ++t) {
-      int p = L.close_blk[c0 + t - 1];
-      s_tgt[t] = p;
-      s_w[t] = width_of(L, p, ci);
-      s_colst[t] = cs;
-      cs += L.n[p];
+  if (warp == 0) {  // lane t: target t (loads in flight together, column starts by a scan)
+    int p = i, w = r, np = n;
+    if (lane > 0 && lane < nt) {
+      p = L.close_blk[c0 + lane - 1];
+      w = width_of(L, p, ci);
+      np = L.n[p];
+    }
+    if (lane >= nt) np = 0;
+    int cs = np;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, cs, o);
+      if (lane >= o) cs += v;
+    }
+    if (lane < nt) {
+      s_tgt[lane] = p;
+      s_w[lane] = w;
+      s_colst[lane] = lane == 0 ? 0 : cs - np;
     }
   }
   __syncthreads();
@@ -1118,24 +1125,34 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : NT >= 256 ? 3 : 6))
     ce_row_kernel(LevelDev L, int count, int level, double tol, int tol_mode, int* status, int nmax, int LD,
                   int QW, LearnedArgs la) {
   __shared__ int s_q;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
   for (;;) {
-    if (tid == 0) {
-      int q = atomicAdd(L.qnext, 1);
-      if (q >= count || ld_acquire(status) != 0) q = -1;
+    if (tid < 32) {  // warp 0 takes the next row and waits for its neighbourhood
+      int q = 0;
+      if (lane == 0) {
+        q = atomicAdd(L.qnext, 1);
+        if (q >= count || ld_acquire(status) != 0) q = -1;
+      }
+      q = __shfl_sync(0xffffffffu, q, 0);
       if (q >= 0) {
         const int i = L.order[q];
         const unsigned long long t0 = globaltimer_ns();
         int polls = 0;
-        for (int d = L.dep_ptr[i]; d < L.dep_ptr[i + 1] && q >= 0; ++d) {
-          const int* flag = L.done + L.dep_idx[d];
-          while (ld_acquire(flag) == 0) {
-            if (ld_acquire(status) != 0) {
-              q = -1;
-              break;
+        for (int base = L.dep_ptr[i]; base < L.dep_ptr[i + 1] && q >= 0; base += 32) {
+          const int d = base + lane;
+          const int* flag = d < L.dep_ptr[i + 1] ? L.done + L.dep_idx[d] : nullptr;
+          for (;;) {
+            const bool ok = flag == nullptr || ld_acquire(flag) != 0;
+            if (__all_sync(0xffffffffu, ok)) break;
+            int bad = 0;
+            if (lane == 0) {
+              if (ld_acquire(status) != 0)
+                bad = 1;
+              else if (++polls > kDepWaitPolls || globaltimer_ns() - t0 > kDepWaitNs)
+                bad = 2;
+              if (bad == 2) set_status(status, CE_ERR_CUDA, level, i, 5);
             }
-            if (++polls > kDepWaitPolls || globaltimer_ns() - t0 > kDepWaitNs) {
-              set_status(status, CE_ERR_CUDA, level, i, 5);
+            if (__shfl_sync(0xffffffffu, bad, 0)) {
               q = -1;
               break;
             }
@@ -1143,7 +1160,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : NT >= 256 ? 3 : 6))
           }
         }
       }
-      s_q = q;
+      if (lane == 0) s_q = q;
     }
     __syncthreads();
     const int q = s_q;
