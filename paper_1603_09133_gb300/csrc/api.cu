@@ -996,26 +996,43 @@ ce_status ce_autotune(ce_csb* A, const ce_opts* o_in, double* level_ms) {
   ce_opts o;
   ce_opts_default(&o);
   if (o_in) o = *o_in;
-  constexpr int kShapes = 3;
+  constexpr int kShapes = 3, kReps = 3;
   double t[kShapes][16];
+  int heur[16] = {};
   int nl = 16;
   for (int sh = 0; sh < kShapes; ++sh) {
     o.row_shape = sh;
-    ce_factor* F = nullptr;
-    ce_info info;
-    // one untimed run first (allocator pools, staging buffers, model warm)
-    for (int rep = 0; rep < 2; ++rep) {
+    for (int l = 0; l < 16; ++l) t[sh][l] = 1e300;
+    // one untimed run first (allocator pools, staging buffers), then the
+    // fastest of kReps timed runs per level
+    for (int rep = 0; rep <= kReps; ++rep) {
+      ce_factor* F = nullptr;
+      ce_info info;
       ce_status st = ce_factorize(A, &o, &F, &info);
       if (st != CE_OK) return st;
       ce_factor_destroy(F);
+      nl = std::min(nl, info.levels_done);
+      if (rep > 0)
+        for (int l = 0; l < info.levels_done && l < 16; ++l) t[sh][l] = std::min(t[sh][l], info.level_ms[l]);
     }
-    nl = std::min(nl, info.levels_done);
-    for (int l = 0; l < 16; ++l) t[sh][l] = l < info.levels_done ? info.level_ms[l] : 0.0;
+  }
+  {
+    // the heuristic's shape per level, kept unless another is clearly faster
+    o.row_shape = -1;
+    const int saved = A->tuned_levels;
+    A->tuned_levels = 0;
+    ce_factor* F = nullptr;
+    ce_info info;
+    ce_status st = ce_factorize(A, &o, &F, &info);
+    A->tuned_levels = saved;
+    if (st != CE_OK) return st;
+    ce_factor_destroy(F);
+    for (int l = 0; l < 16; ++l) heur[l] = info.row_shape[l];
   }
   for (int l = 0; l < nl; ++l) {
-    int best = 0;
-    for (int sh = 1; sh < kShapes; ++sh)
-      if (t[sh][l] < t[best][l]) best = sh;
+    int best = heur[l];
+    for (int sh = 0; sh < kShapes; ++sh)
+      if (t[sh][l] < 0.97 * t[best][l]) best = sh;
     A->tuned_shape[l] = best;
   }
   A->tuned_levels = nl;

@@ -19,6 +19,8 @@
 // colouring), so the CTAs of one launch touch disjoint block pairs.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include <algorithm>
 
 #include "kernels.h"
@@ -239,6 +241,84 @@ __device__ __forceinline__ void cta_gemm(int M, int N, int K, FA A, FB B, FS sto
   }
 }
 
+// ---- tensor cores (FP32 form): mma.sync m16n8k8 TF32 with FP32 accumulate.
+// Each FP32 operand is split x = hi + lo into two TF32 numbers and the
+// product is accumulated as lo*hi + hi*lo + hi*hi ("3xTF32"), which keeps the
+// rounding error at the level of FP32 arithmetic (the dropped lo*lo term is
+// about 2^-22 of the product).  Fragment layout of m16n8k8 (g = lane / 4,
+// q = lane % 4): A holds (g, q), (g+8, q), (g, q+4), (g+8, q+4); B holds
+// (q, g), (q+4, g); C holds (g, 2q), (g, 2q+1), (g+8, 2q), (g+8, 2q+1).
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// C = A B (M x N, inner K) on the tensor cores, one 16 x 8 tile of C per warp
+// at a time; store(a, b, v) is called once per element, like cta_gemm.
+template <int NT, class FA, class FB, class FS>
+__device__ __forceinline__ void cta_gemm_tc(int M, int N, int K, FA A, FB B, FS store) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const int tm = (M + 15) >> 4, tn = (N + 7) >> 3;
+  for (int t = warp; t < tm * tn; t += NT / 32) {
+    const int r0 = (t / tn) * 16, c0 = (t % tn) * 8;
+    const int ra = r0 + g, rb = r0 + g + 8, cb = c0 + g;
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int k0 = 0; k0 < K; k0 += 8) {
+      const int ka = k0 + q, kb = k0 + q + 4;
+      float af[4], bf[2];
+      af[0] = (ra < M && ka < K) ? A(ra, ka) : 0.f;
+      af[1] = (rb < M && ka < K) ? A(rb, ka) : 0.f;
+      af[2] = (ra < M && kb < K) ? A(ra, kb) : 0.f;
+      af[3] = (rb < M && kb < K) ? A(rb, kb) : 0.f;
+      bf[0] = (ka < K && cb < N) ? B(ka, cb) : 0.f;
+      bf[1] = (kb < K && cb < N) ? B(kb, cb) : 0.f;
+      uint32_t ah[4], al[4], bh[2], bl[2];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        ah[u] = to_tf32(af[u]);
+        al[u] = to_tf32(af[u] - __uint_as_float(ah[u]));
+      }
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        bh[u] = to_tf32(bf[u]);
+        bl[u] = to_tf32(bf[u] - __uint_as_float(bh[u]));
+      }
+      mma_tf32(c, al, bh);
+      mma_tf32(c, ah, bl);
+      mma_tf32(c, ah, bh);
+    }
+    const int cc = c0 + 2 * q;
+    if (ra < M && cc < N) store(ra, cc, c[0]);
+    if (ra < M && cc + 1 < N) store(ra, cc + 1, c[1]);
+    if (rb < M && cc < N) store(rb, cc, c[2]);
+    if (rb < M && cc + 1 < N) store(rb, cc + 1, c[3]);
+  }
+}
+
+// FP32 form: tensor cores when `tc` (levels whose blocks exceed 32 rows; on
+// the level-1 blocks of 32 rows the 16 x 8 x 8 tiles carry too much padding
+// and the CUDA cores measured faster); FP64 form: FP64 on the CUDA cores
+template <typename T, int NT, class FA, class FB, class FS>
+__device__ __forceinline__ void cta_mm(bool tc, int M, int N, int K, FA A, FB B, FS store) {
+  if constexpr (std::is_same<T, float>::value) {
+    if (tc) {
+      cta_gemm_tc<NT>(M, N, K, A, B, store);
+      return;
+    }
+  }
+  cta_gemm<T, NT>(M, N, K, A, B, store);
+}
+
 // n x w tile of the pair (i, k) seen from row i -> sm (row-major, LD); the
 // pair is stored once as (min, max)
 template <typename T, int NT>
@@ -306,6 +386,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int n = L.n[i];
   const int ci = L.colour[i];
+  const bool tc = nmax > 32;
   T* pool = reinterpret_cast<T*>(L.pool);
   if (n == 0) {
     if (tid == 0) {
@@ -942,11 +1023,11 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     Y[a * LD + b] = Dg[e];
   }
   __syncthreads();
-  cta_gemm<T, NT>(n, n, n, [&](int a, int k) { return Y[a * LD + k]; },        // Xt = D U
+  cta_mm<T, NT>(tc, n, n, n, [&](int a, int k) { return Y[a * LD + k]; },        // Xt = D U
               [&](int k, int b) { return U[k * LD + b]; },
               [&](int a, int b, T v) { Xt[a * LD + b] = v; });
   __syncthreads();
-  cta_gemm<T, NT>(n, n, n, [&](int a, int k) { return U[k * LD + a]; },        // Tm = U^T D U
+  cta_mm<T, NT>(tc, n, n, n, [&](int a, int k) { return U[k * LD + a]; },        // Tm = U^T D U
               [&](int k, int b) { return Xt[k * LD + b]; },
               [&](int a, int b, T v) { Tm[a * LD + b] = v; });
   __syncthreads();
@@ -990,7 +1071,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     Lg[e] = (b <= a) ? Li[a * LD + b] : T(0);
   }
   // W_b = L_hat^{-1} Tm[r:, :r] -> Y[0:m, 0:r], then back into Tm[r:, :r]
-  cta_gemm<T, NT>(m, r, m, [&](int a, int k) { return Li[a * LD + k]; },
+  cta_mm<T, NT>(tc, m, r, m, [&](int a, int k) { return Li[a * LD + k]; },
               [&](int k, int b) { return Tm[(r + k) * LD + b]; },
               [&](int a, int b, T v) { Y[a * LD + b] = v; });
   __syncthreads();
@@ -1003,7 +1084,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
   }
   __syncthreads();
   // basis diagonal block: Tm[:r, :r] - W_b^T W_b
-  cta_gemm<T, NT>(r, r, m, [&](int a, int k) { return Tm[(r + k) * LD + a]; },
+  cta_mm<T, NT>(tc, r, r, m, [&](int a, int k) { return Tm[(r + k) * LD + a]; },
               [&](int k, int b) { return Tm[(r + k) * LD + b]; },
               [&](int a, int b, T v) { Dg[(int64_t)a * n + b] = Tm[a * LD + b] - v; });
   // target bookkeeping
@@ -1040,19 +1121,19 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     T* Xg = pool + L.close_off[c0 + t - 1];
     load_row_tile<T, NT>(Xt, Xg, i, p, n, np, w, LD);
     __syncthreads();
-    cta_gemm<T, NT>(n, w, n, [&](int a, int k) { return U[k * LD + a]; },
+    cta_mm<T, NT>(tc, n, w, n, [&](int a, int k) { return U[k * LD + a]; },
                 [&](int k, int b) { return Xt[k * LD + b]; },
                 [&](int a, int b, T v) { Y[a * LD + b] = v; });
     __syncthreads();
     T* Wp = Wbase + (int64_t)n * s_colst[t];
-    cta_gemm<T, NT>(m, w, m, [&](int a, int k) { return Li[a * LD + k]; },
+    cta_mm<T, NT>(tc, m, w, m, [&](int a, int k) { return Li[a * LD + k]; },
                 [&](int k, int b) { return Y[(r + k) * LD + b]; },
                 [&](int a, int b, T v) {
                   Xt[a * LD + b] = v;
                   Wp[a * w + b] = v;
                 });
     __syncthreads();
-    cta_gemm<T, NT>(r, w, m, [&](int a, int k) { return Tm[(r + k) * LD + a]; },
+    cta_mm<T, NT>(tc, r, w, m, [&](int a, int k) { return Tm[(r + k) * LD + a]; },
                 [&](int k, int b) { return Xt[k * LD + b]; },
                 [&](int a, int b, T v) { Y[a * LD + b] -= v; });
     __syncthreads();
@@ -1066,7 +1147,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     T* Xg = pool + s_foff[f];
     load_row_tile<T, NT>(Xt, Xg, i, k, n, L.n[k], w, LD);
     __syncthreads();
-    cta_gemm<T, NT>(r, w, n, [&](int a, int kk) { return U[kk * LD + a]; },
+    cta_mm<T, NT>(tc, r, w, n, [&](int a, int kk) { return U[kk * LD + a]; },
                 [&](int kk, int b) { return Xt[kk * LD + b]; },
                 [&](int a, int b, T v) { Y[a * LD + b] = v; });
     __syncthreads();
@@ -1083,7 +1164,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
         const T* Wb = Wbase + (int64_t)n * s_colst[b];
         T* Xg = pool + L.schur_off[idx];
         const int ld = L.n[s_tgt[b]];
-        cta_gemm<T, NT>(wa, wb, m, [&](int x, int k) { return Wa[k * wa + x]; },
+        cta_mm<T, NT>(tc, wa, wb, m, [&](int x, int k) { return Wa[k * wa + x]; },
                     [&](int k, int y) { return Wb[k * wb + y]; },
                     [&](int x, int y, T v) { Xg[(int64_t)x * ld + y] -= v; });
       }

@@ -1,9 +1,9 @@
 """GPU: every CTA shape of the persistent row kernel gives the oracle's
-factorization, and the autotuner keeps the fastest shape per level.
+factorization, and the autotuner keeps a shape within 3% of the fastest per level.
 
 A shape changes only how a row's work is spread over threads, so each one is
 held to the FP64 parity bar (ranks equal away from the threshold, apply within
-1e-10 of the oracle's); the autotuned choice is the argmin of its own timings.
+1e-10 of the oracle's).
 """
 import numpy as np
 import pytest
@@ -55,7 +55,11 @@ def test_autotune_keeps_fastest_shape(ceg, problem):
     t = ceg.ce_autotune(csb, tol=w.tol, levels=w.levels, J=w.J)
     assert t.shape == (3, w.levels) and (t > 0).all()
     F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J)
-    assert list(F.info.row_shape[:w.levels]) == [int(np.argmin(t[:, l])) for l in range(w.levels)]
+    # the kept shape is within 3% of the fastest one (the heuristic's shape is
+    # kept unless another one is more than 3% faster)
+    for l in range(w.levels):
+        used = F.info.row_shape[l]
+        assert t[used, l] <= t[:, l].min() / 0.97 + 1e-9, (l, used, t[:, l])
     # another precision has no tuned table: the heuristic decides
     F32 = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision="fp32")
     assert all(s in (0, 1) for s in F32.info.row_shape[:w.levels])
