@@ -112,6 +112,10 @@ typedef struct {
                           (coarsening, pattern, colouring, reassembly)    */
   double total_ms;     /* wall time of the whole call                     */
   int row_shape[16];   /* CTA shape the row kernel used per level         */
+  int spec_miss[16];   /* blocks of level l whose r_l = 0 or r_l > 0 the
+                          speculative planning of level l+1 guessed wrong
+                          (0: the pattern planned during the GPU work is
+                          kept; otherwise it is planned again)            */
 } ce_info;
 
 typedef struct {

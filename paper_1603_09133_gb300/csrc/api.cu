@@ -85,7 +85,7 @@ struct Staging {
   cudaEvent_t ev = nullptr;
   bool pending = false;
 };
-thread_local Staging g_stage[2];
+thread_local Staging g_stage[3];  // 2: device-to-host reads of ranks and status
 
 char* stage_get(int slot, size_t bytes) {
   Staging& S = g_stage[slot];
@@ -840,11 +840,22 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       check(ce::launch_row_kernel(es, st.dev, P.M, l, o.tol, o.tol_mode, F->d_status, P.nmax, shape, la, s),
             "row kernel");
       check(cudaEventRecord(ev1, s), "event");
-      st.rank.resize(P.M);
-      check(cudaMemcpyAsync(st.rank.data(), st.dev.rank, P.M * sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
-      check(cudaMemcpyAsync(hstatus, F->d_status, sizeof(hstatus), cudaMemcpyDeviceToHost, s), "D2H");
+      // ranks and status into pinned memory, so the host runs on meanwhile
+      int* hread = reinterpret_cast<int*>(stage_get(2, (P.M + ce::kStatusWords) * sizeof(int)));
+      check(cudaMemcpyAsync(hread, st.dev.rank, P.M * sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
+      check(cudaMemcpyAsync(hread + P.M, F->d_status, sizeof(hstatus), cudaMemcpyDeviceToHost, s), "D2H");
+      // While the GPU eliminates this level, plan the pattern of the next one
+      // from the expected set of blocks that keep a basis (those with live
+      // far blocks); checked against the actual ranks below.
+      std::vector<char> guess(P.M);
+      for (int i = 0; i < P.M; ++i) guess[i] = P.n[i] > 0 && P.far_ptr[i + 1] > P.far_ptr[i];
+      ce::NextLevel nx = ce::coarsen_structure(P, guess, o.J);
+      auto nxtp = std::make_shared<LevelPlan>();
+      ce::plan_structure(*nxtp, nx.M, nx.pairs, o.coloring != 0, nx.sys_off);
       check(cudaStreamSynchronize(s), "level sync");
       t_host = clk::now();
+      st.rank.assign(hread, hread + P.M);
+      std::memcpy(hstatus, hread + P.M, sizeof(hstatus));
       float lms = 0.f;
       cudaEventElapsedTime(&lms, ev0, ev1);
       cudaEventDestroy(ev0);
@@ -865,10 +876,23 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
         break;
       }
       // coarsen (Section 2.4) and plan the next level
-      ce::NextLevel nx = ce::coarsen(P, st.rank, o.J);
-      auto nxtp = std::make_shared<LevelPlan>();
+      {
+        std::vector<char> live(P.M);
+        bool same = true;
+        for (int i = 0; i < P.M; ++i) {
+          live[i] = st.rank[i] != 0;
+          same = same && live[i] == guess[i];
+        }
+        if (info && l < 16)
+          for (int i = 0; i < P.M; ++i) info->spec_miss[l] += live[i] != guess[i];
+        if (!same) {
+          nx = ce::coarsen_structure(P, live, o.J);
+          ce::plan_structure(*nxtp, nx.M, nx.pairs, o.coloring != 0, nx.sys_off);
+        }
+      }
+      ce::coarsen_sizes(P, st.rank, nx);
       LevelPlan& nxt = *nxtp;
-      ce::plan_level(nxt, nx.n, nx.pairs, o.coloring != 0, nx.sys_off);
+      ce::plan_layout(nxt, nx.n);
       std::vector<int64_t> gd(P.M);
       for (int i = 0; i < P.M; ++i) gd[i] = nxt.vec_off[nx.parent[i]] + nx.child_off[i];
       check(cudaMemcpyAsync(st.dev.gdst, gd.data(), P.M * sizeof(int64_t), cudaMemcpyHostToDevice, s), "H2D");

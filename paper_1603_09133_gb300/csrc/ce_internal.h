@@ -69,13 +69,18 @@ struct LevelPlan {
   std::vector<char> pair_close;
   int64_t pool_elems = 0;
 
-  // per block (CSR-style arrays)
+  // per block (CSR-style arrays); *_pidx are indices into the pair arrays
+  // (pattern only), *_off the pool offsets of those pairs (after the sizes)
   std::vector<int> close_ptr, close_blk;   // close(i) \ {i}, ascending
+  std::vector<int> close_pidx;
   std::vector<int64_t> close_off;
   std::vector<int> far_ptr, far_blk;       // far pairs live when i is processed
+  std::vector<int> far_pidx;
   std::vector<int64_t> far_off;
+  std::vector<int> diag_pidx;
   std::vector<int64_t> diag_off;
   std::vector<int> schur_ptr;              // t(t+1)/2 target pairs, t = 1+|close|
+  std::vector<int> schur_pidx;
   std::vector<int64_t> schur_off;
 
   // factor and vector layout
@@ -95,10 +100,17 @@ struct LevelPlan {
 
 // Build the plan of a level from its sizes and level-start pattern (pairs
 // with i <= k; the diagonal pairs are added if missing).  sys_off (empty =
-// one system) gives the blocks of each independent system.
+// one system) gives the blocks of each independent system.  plan_structure
+// does everything that depends on the pattern alone (colouring, squared
+// pattern, lists, dependencies), plan_layout what depends on the sizes
+// (pool, factor and vector offsets); plan_level is both.
 void plan_level(LevelPlan& P, const std::vector<int>& n,
                 const std::vector<std::pair<int, int>>& close_pairs, bool coloring,
                 const std::vector<int>& sys_off = {});
+void plan_structure(LevelPlan& P, int M, const std::vector<std::pair<int, int>>& close_pairs, bool coloring,
+                    const std::vector<int>& sys_off);
+void plan_layout(LevelPlan& P, const std::vector<int>& n);
+int find_pair_idx(const LevelPlan& P, int a, int b);
 
 // Element offset of pair (a, b) (either order) in the level pool, -1 if the
 // pair is not in the squared pattern.
@@ -116,6 +128,7 @@ struct CopyTask {
 };
 
 struct NextLevel {
+  int M = 0;                                     // super-blocks
   std::vector<int> n;                            // super-block sizes
   std::vector<std::pair<int, int>> pairs;        // next close pattern
   std::vector<int> child_off;                    // offset of child i in its super-block
@@ -124,6 +137,10 @@ struct NextLevel {
 };
 
 NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J);
+// the same in two steps: the pattern from which blocks keep a basis
+// (live[i] = r_i > 0), then the super-block sizes and child offsets
+NextLevel coarsen_structure(const LevelPlan& P, const std::vector<char>& live, int J);
+void coarsen_sizes(const LevelPlan& P, const std::vector<int>& rank, NextLevel& nx);
 
 // graph, work vectors and chunk map of the batched PCG (pcg_batched.cu)
 struct PcgBatch;

@@ -202,8 +202,7 @@ void pcg_batch_release(PcgBatch* P) {
   if (P->graph) cudaGraphDestroy(P->graph);
   for (auto& e : P->ev)
     if (e) cudaEventDestroy(e);
-  if (P->h_rem) cudaFreeHost(P->h_rem);
-  if (P->mem) cudaFree(P->mem);
+  if (P->mem) cudaFreeAsync(P->mem, nullptr);
   delete P;
 }
 
@@ -224,7 +223,14 @@ void enqueue_iteration(const ce_csb* A, const ce_factor* F, PcgBatch& P, cudaStr
   ok(cudaGetLastError());
 }
 
-PcgBatch* make_batch(const ce_csb* A, const ce_factor* F) {
+// two pinned counters per host thread, kept for the life of the process
+int32_t* pinned_counters() {
+  thread_local int32_t* p = nullptr;
+  if (!p) ok(cudaHostAlloc(reinterpret_cast<void**>(&p), 2 * sizeof(int32_t), cudaHostAllocDefault));
+  return p;
+}
+
+PcgBatch* make_batch(const ce_csb* A, const ce_factor* F, cudaStream_t s) {
   PcgBatch* P = new PcgBatch();
   try {
     P->A = A;
@@ -244,7 +250,7 @@ PcgBatch* make_batch(const ce_csb* A, const ce_factor* F) {
     P->nchunks = static_cast<int>(chunk_sys.size());
     const int64_t n = A->n, nc = P->nchunks, ns = P->nsys;
     const size_t bytes = (5 * n + nc + ns * kSc + 1) * 8 + (nc + 1) * 8 + (3 * ns + 1 + nc + ns + 1) * 4 + 64;
-    ok(cudaMalloc(&P->mem, bytes));
+    ok(cudaMallocAsync(&P->mem, bytes, s));
     char* q = static_cast<char*>(P->mem);
     auto take = [&](size_t b) {
       char* r = q;
@@ -265,11 +271,11 @@ PcgBatch* make_batch(const ce_csb* A, const ce_factor* F) {
     P->remaining = reinterpret_cast<int32_t*>(take(4));
     P->chunk_sys = reinterpret_cast<int32_t*>(take(nc * 4));
     P->sys_chunk = reinterpret_cast<int32_t*>(take((ns + 1) * 4));
-    ok(cudaMemcpy(P->chunk_row, chunk_row.data(), (nc + 1) * 8, cudaMemcpyHostToDevice));
-    ok(cudaMemcpy(P->chunk_sys, chunk_sys.data(), nc * 4, cudaMemcpyHostToDevice));
-    ok(cudaMemcpy(P->sys_chunk, sys_chunk.data(), (ns + 1) * 4, cudaMemcpyHostToDevice));
-    ok(cudaMemset(P->p, 0, n * 8));
-    ok(cudaHostAlloc(&P->h_rem, 2 * sizeof(int32_t), cudaHostAllocDefault));
+    ok(cudaMemcpyAsync(P->chunk_row, chunk_row.data(), (nc + 1) * 8, cudaMemcpyHostToDevice, s));
+    ok(cudaMemcpyAsync(P->chunk_sys, chunk_sys.data(), nc * 4, cudaMemcpyHostToDevice, s));
+    ok(cudaMemcpyAsync(P->sys_chunk, sys_chunk.data(), (ns + 1) * 4, cudaMemcpyHostToDevice, s));
+    ok(cudaMemsetAsync(P->p, 0, n * 8, s));
+    P->h_rem = pinned_counters();
     for (auto& e : P->ev) ok(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     // capture one iteration on a private stream; the launch counter keeps
     // only real launches, so the captured ones are taken back out
@@ -330,7 +336,7 @@ extern "C" ce_status pcg_solve_batched(const ce_csb* A, const ce_factor* F, cons
     }
     if (!P) {
       ok(cudaStreamSynchronize(s));
-      F->pcg = P = make_batch(A, F);
+      F->pcg = P = make_batch(A, F, s);
     }
     const int nc = P->nchunks, ns = P->nsys;
     const int64_t n = A->n;

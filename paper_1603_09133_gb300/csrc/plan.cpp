@@ -116,22 +116,24 @@ void join_chunks(int M, int nch, const std::vector<std::vector<int>>& cnt, std::
 
 }  // namespace
 
-int64_t find_pair(const LevelPlan& P, int a, int b) {
+int find_pair_idx(const LevelPlan& P, int a, int b) {
   if (a > b) std::swap(a, b);
   const int* lo = P.pair_k.data() + P.pair_ptr[a];
   const int* hi = P.pair_k.data() + P.pair_ptr[a + 1];
   const int* it = std::lower_bound(lo, hi, b);
   if (it == hi || *it != b) return -1;
-  return P.pair_off[it - P.pair_k.data()];
+  return static_cast<int>(it - P.pair_k.data());
 }
 
-void plan_level(LevelPlan& P, const std::vector<int>& n,
-                const std::vector<std::pair<int, int>>& close_pairs, bool coloring,
-                const std::vector<int>& sys_off) {
-  const int M = static_cast<int>(n.size());
+int64_t find_pair(const LevelPlan& P, int a, int b) {
+  const int p = find_pair_idx(P, a, b);
+  return p < 0 ? -1 : P.pair_off[p];
+}
+
+void plan_structure(LevelPlan& P, int M, const std::vector<std::pair<int, int>>& close_pairs, bool coloring,
+                    const std::vector<int>& sys_off) {
   P = LevelPlan();
   P.M = M;
-  P.n = n;
   P.sys_off = sys_off;
   const Csr adj = adjacency(M, close_pairs);
 
@@ -157,7 +159,7 @@ void plan_level(LevelPlan& P, const std::vector<int>& n,
   for (int c = 0; c < P.ncolours; ++c) P.colour_ptr[c + 1] += P.colour_ptr[c];
 
   // chunks of blocks for the parallel per-block passes
-  const int nch = std::max(1, std::min(host_threads() * 4, (M + 1023) / 1024));
+  const int nch = std::max(1, std::min(host_threads() * 4, (M + 127) / 128));
   std::vector<int64_t> cb(nch + 1);
   for (int c = 0; c <= nch; ++c) cb[c] = (int64_t)M * c / nch;
 
@@ -184,31 +186,25 @@ void plan_level(LevelPlan& P, const std::vector<int>& n,
   }
   const int np = P.pair_ptr[M];
   P.pair_i.resize(np);
-  P.pair_off.resize(np);
   P.pair_close.resize(np);
-  int64_t off = 0;
-  for (int i = 0; i < M; ++i)
-    for (int p = P.pair_ptr[i]; p < P.pair_ptr[i + 1]; ++p) {
-      P.pair_i[p] = i;
-      P.pair_off[p] = off;
-      off += static_cast<int64_t>(n[i]) * n[P.pair_k[p]];
-    }
-  P.pool_elems = off;
   parallel_for(M, 2048, [&](int64_t b, int64_t e) {
     for (int64_t i = b; i < e; ++i)
-      for (int p = P.pair_ptr[i]; p < P.pair_ptr[i + 1]; ++p) P.pair_close[p] = adj.has(i, P.pair_k[p]);
+      for (int p = P.pair_ptr[i]; p < P.pair_ptr[i + 1]; ++p) {
+        P.pair_i[p] = static_cast<int>(i);
+        P.pair_close[p] = adj.has(static_cast<int>(i), P.pair_k[p]);
+      }
   });
-  auto pair_offset = [&](int a, int b) -> int64_t {
-    const int64_t o = find_pair(P, a, b);
-    if (o < 0) throw std::logic_error("pair outside squared pattern");
-    return o;
+  auto pair_idx = [&](int a, int b) -> int {
+    const int p = find_pair_idx(P, a, b);
+    if (p < 0) throw std::logic_error("pair outside squared pattern");
+    return p;
   };
 
-  // ---- per block lists ----------------------------------------------------
-  P.diag_off.resize(M);
+  // ---- per block lists (as pair indices) ---------------------------------
+  P.diag_pidx.resize(M);
   {
-    std::vector<std::vector<int>> ccnt(nch), fcnt(nch), scnt(nch), cblk(nch), fblk(nch);
-    std::vector<std::vector<int64_t>> coff(nch), foff(nch), soff(nch);
+    std::vector<std::vector<int>> ccnt(nch), fcnt(nch), scnt(nch), cblk(nch), fblk(nch), cpi(nch), fpi(nch),
+        spi(nch);
     parallel_for(nch, 1, [&](int64_t b, int64_t e) {
       std::vector<int> cand, T;
       for (int64_t c = b; c < e; ++c) {
@@ -218,54 +214,57 @@ void plan_level(LevelPlan& P, const std::vector<int>& n,
         scnt[c].resize(nb);
         for (int64_t ii = cb[c]; ii < cb[c + 1]; ++ii) {
           const int i = static_cast<int>(ii);
-          P.diag_off[i] = pair_offset(i, i);
-          int nc = 0;
-          for (const int* k = adj.row(i); k != adj.row(i) + adj.deg(i); ++k)
+          const int* ai = adj.row(i);
+          const int di = adj.deg(i);
+          P.diag_pidx[i] = pair_idx(i, i);
+          T.assign(1, i);
+          for (const int* k = ai; k != ai + di; ++k)
             if (*k != i) {
               cblk[c].push_back(*k);
-              coff[c].push_back(pair_offset(i, *k));
-              ++nc;
+              cpi[c].push_back(pair_idx(i, *k));
+              T.push_back(*k);
             }
-          ccnt[c][i - cb[c]] = nc;
-          // far blocks of row i that hold fill when i is processed: some
-          // common close neighbour j of i and k was eliminated earlier
+          ccnt[c][i - cb[c]] = di - 1;
+          // far blocks of row i that hold fill when i is processed: a close
+          // neighbour j of i of an earlier colour also neighbours k, and k
+          // is not close to i
           cand.clear();
-          for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j)
+          for (const int* j = ai; j != ai + di; ++j) {
+            if (*j == i || P.colour[*j] >= P.colour[i]) continue;
             for (const int* k = adj.row(*j); k != adj.row(*j) + adj.deg(*j); ++k)
-              if (*k != i && !adj.has(i, *k)) cand.push_back(*k);
+              if (*k != i && !std::binary_search(ai, ai + di, *k)) cand.push_back(*k);
+          }
           std::sort(cand.begin(), cand.end());
           cand.erase(std::unique(cand.begin(), cand.end()), cand.end());
-          int nf = 0;
           for (int k : cand) {
-            bool live = false;
-            for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j)
-              if (*j != i && *j != k && P.colour[*j] < P.colour[i] && adj.has(k, *j)) {
-                live = true;
-                break;
+            fblk[c].push_back(k);
+            fpi[c].push_back(pair_idx(i, k));
+          }
+          fcnt[c][i - cb[c]] = static_cast<int>(cand.size());
+          // Schur targets T = [i] + close(i): all pairs (T[a], T[b]), a <= b.
+          // T[1:] ascends, so row T[a]'s pairs are walked once for all b.
+          for (size_t x = 0; x < T.size(); ++x) {
+            int p = P.pair_ptr[T[x]];
+            for (size_t y = x; y < T.size(); ++y) {
+              if (x == 0 && y > 0 && T[y] < T[0]) {  // pair stored under row T[y]
+                spi[c].push_back(pair_idx(T[0], T[y]));
+                continue;
               }
-            if (live) {
-              fblk[c].push_back(k);
-              foff[c].push_back(pair_offset(i, k));
-              ++nf;
+              while (p < P.pair_ptr[T[x] + 1] && P.pair_k[p] < T[y]) ++p;
+              if (p >= P.pair_ptr[T[x] + 1] || P.pair_k[p] != T[y]) throw std::logic_error("pair outside squared pattern");
+              spi[c].push_back(p);
             }
           }
-          fcnt[c][i - cb[c]] = nf;
-          // Schur targets T = [i] + close(i): all pairs (T[a], T[b]), a <= b
-          T.assign(1, i);
-          for (const int* k = adj.row(i); k != adj.row(i) + adj.deg(i); ++k)
-            if (*k != i) T.push_back(*k);
-          for (size_t a = 0; a < T.size(); ++a)
-            for (size_t bb = a; bb < T.size(); ++bb) soff[c].push_back(pair_offset(T[a], T[bb]));
           scnt[c][i - cb[c]] = static_cast<int>(T.size() * (T.size() + 1) / 2);
         }
       }
     });
-    join_chunks<int, int64_t>(M, nch, ccnt, cblk, &coff, P.close_ptr, P.close_blk, &P.close_off, cb);
-    join_chunks<int, int64_t>(M, nch, fcnt, fblk, &foff, P.far_ptr, P.far_blk, &P.far_off, cb);
-    join_chunks<int64_t, int>(M, nch, scnt, soff, nullptr, P.schur_ptr, P.schur_off, nullptr, cb);
+    join_chunks<int, int>(M, nch, ccnt, cblk, &cpi, P.close_ptr, P.close_blk, &P.close_pidx, cb);
+    join_chunks<int, int>(M, nch, fcnt, fblk, &fpi, P.far_ptr, P.far_blk, &P.far_pidx, cb);
+    join_chunks<int, int>(M, nch, scnt, spi, nullptr, P.schur_ptr, P.schur_pidx, nullptr, cb);
   }
 
-  // ---- dependencies of the persistent launch ------------------------------
+  // ---- dependencies of the persistent launches ----------------------------
   P.dep_ptr.assign(M + 1, 0);
   for (int p = 0; p < np; ++p) {
     const int i = P.pair_i[p], k = P.pair_k[p];
@@ -284,7 +283,6 @@ void plan_level(LevelPlan& P, const std::vector<int>& n,
       else if (P.colour[i] < P.colour[k]) P.dep_idx[fill[k]++] = i;
     }
   }
-
   P.rdep_ptr.assign(M + 1, 0);
   for (int k : P.dep_idx) ++P.rdep_ptr[k + 1];
   for (int i = 0; i < M; ++i) P.rdep_ptr[i + 1] += P.rdep_ptr[i];
@@ -294,7 +292,29 @@ void plan_level(LevelPlan& P, const std::vector<int>& n,
     for (int i = 0; i < M; ++i)
       for (int d = P.dep_ptr[i]; d < P.dep_ptr[i + 1]; ++d) P.rdep_idx[fill[P.dep_idx[d]]++] = i;
   }
+}
 
+void plan_layout(LevelPlan& P, const std::vector<int>& n) {
+  const int M = P.M;
+  P.n = n;
+  const int np = static_cast<int>(P.pair_k.size());
+  P.pair_off.resize(np);
+  int64_t off = 0;
+  for (int p = 0; p < np; ++p) {
+    P.pair_off[p] = off;
+    off += static_cast<int64_t>(n[P.pair_i[p]]) * n[P.pair_k[p]];
+  }
+  P.pool_elems = off;
+  auto gather = [&](const std::vector<int>& idx, std::vector<int64_t>& out) {
+    out.resize(idx.size());
+    parallel_for(static_cast<int64_t>(idx.size()), 65536, [&](int64_t b, int64_t e) {
+      for (int64_t t = b; t < e; ++t) out[t] = P.pair_off[idx[t]];
+    });
+  };
+  gather(P.close_pidx, P.close_off);
+  gather(P.far_pidx, P.far_off);
+  gather(P.schur_pidx, P.schur_off);
+  gather(P.diag_pidx, P.diag_off);
   // ---- factor and vector layout ------------------------------------------
   P.u_off.resize(M);
   P.l_off.resize(M);
@@ -322,13 +342,19 @@ void plan_level(LevelPlan& P, const std::vector<int>& n,
   P.vec_len = vo;
 }
 
-NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J) {
+void plan_level(LevelPlan& P, const std::vector<int>& n,
+                const std::vector<std::pair<int, int>>& close_pairs, bool coloring,
+                const std::vector<int>& sys_off) {
+  plan_structure(P, static_cast<int>(n.size()), close_pairs, coloring, sys_off);
+  plan_layout(P, n);
+}
+
+NextLevel coarsen_structure(const LevelPlan& P, const std::vector<char>& live, int J) {
   NextLevel nx;
   const int M = P.M;
   std::vector<int> so = P.sys_off;
   if (so.empty()) so = {0, M};
   nx.parent.assign(M, 0);
-  nx.child_off.assign(M, 0);
   nx.sys_off.assign(so.size(), 0);
   std::vector<int> first_child{0};  // children of super-block I: [first_child[I], first_child[I+1])
   int next = 0;
@@ -341,14 +367,10 @@ NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J) {
     next += cnt;
   }
   nx.sys_off.back() = next;
-  nx.n.assign(next, 0);
-  for (int i = 0; i < M; ++i) {
-    nx.child_off[i] = nx.n[nx.parent[i]];
-    nx.n[nx.parent[i]] += rank[i];
-  }
+  nx.M = next;
   // super-block rows in parallel: parents of the children's pairs with a
   // non-empty basis on both sides (parent() is monotone, so K >= I)
-  const int nch = std::max(1, std::min(host_threads() * 4, (next + 511) / 512));
+  const int nch = std::max(1, std::min(host_threads() * 4, (next + 127) / 128));
   std::vector<std::vector<std::pair<int, int>>> part(nch);
   parallel_for(nch, 1, [&](int64_t b, int64_t e) {
     std::vector<int> buf;
@@ -357,9 +379,9 @@ NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J) {
       for (int I = I0; I < I1; ++I) {
         buf.clear();
         for (int i = first_child[I]; i < first_child[I + 1]; ++i) {
-          if (rank[i] == 0) continue;
+          if (!live[i]) continue;
           for (int p = P.pair_ptr[i]; p < P.pair_ptr[i + 1]; ++p)
-            if (rank[P.pair_k[p]] != 0) buf.push_back(nx.parent[P.pair_k[p]]);
+            if (live[P.pair_k[p]]) buf.push_back(nx.parent[P.pair_k[p]]);
         }
         std::sort(buf.begin(), buf.end());
         buf.erase(std::unique(buf.begin(), buf.end()), buf.end());
@@ -371,6 +393,23 @@ NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J) {
   for (auto& v : part) tot += v.size();
   nx.pairs.reserve(tot);
   for (auto& v : part) nx.pairs.insert(nx.pairs.end(), v.begin(), v.end());
+  return nx;
+}
+
+void coarsen_sizes(const LevelPlan& P, const std::vector<int>& rank, NextLevel& nx) {
+  nx.n.assign(nx.M, 0);
+  nx.child_off.assign(P.M, 0);
+  for (int i = 0; i < P.M; ++i) {
+    nx.child_off[i] = nx.n[nx.parent[i]];
+    nx.n[nx.parent[i]] += rank[i];
+  }
+}
+
+NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J) {
+  std::vector<char> live(P.M);
+  for (int i = 0; i < P.M; ++i) live[i] = rank[i] != 0;
+  NextLevel nx = coarsen_structure(P, live, J);
+  coarsen_sizes(P, rank, nx);
   return nx;
 }
 
