@@ -931,9 +931,11 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
         F->d_coarse = static_cast<double*>(dalloc(nb, s));
         check(cudaMemsetAsync(F->d_coarse, 0, nb, s), "memset coarse");
         run_copy_tasks(dense_tasks(cur, C), es, 8, pool, F->d_coarse, s);
+        void* tinv = dalloc(ce::coarse_tile_scratch(F->nsys), s);
         check(ce::coarse_cholesky(F->d_coarse, F->d_csys, F->nsys, C.nmax, (int)F->levels.size(), F->d_status,
-                                  s),
+                                  static_cast<double*>(tinv), s),
               "coarse chol");
+        dfree(tinv, s);
         F->d_cdinv = static_cast<double*>(dalloc((size_t)C.dinv_elems * sizeof(double), s));
         check(ce::launch_coarse_dinv(F->d_coarse, F->d_csys, F->nsys, C.nmax, F->d_cdinv, s),
               "coarse diagonal inverses");

@@ -379,10 +379,12 @@ __global__ void perm_kernel(const int32_t* perm, int64_t n, const double* in, do
 }
 
 // Dense triangular solves with the coarse factor L_K (FP64), one grid of
-// CTAs cooperating through grid-wide barriers.  L_K is cut into panels of
-// kPan rows; Dinv holds the inverses of its diagonal kPan x kPan blocks, so
-// a panel is solved by CTA 0 as a small GEMV, and the remaining rows are
-// updated by all CTAs.
+// CTAs cooperating through grid-wide barriers, one barrier per panel of kPan
+// rows.  Dinv holds the inverses of the diagonal kPan x kPan blocks; every
+// CTA solves the current panel itself (a small GEMV from shared memory) and
+// then updates its share of the rows still to come with that solution.  CTA
+// 0 stores a panel's solution one step later, when no CTA reads the panel's
+// right-hand side any more.
 constexpr int kPan = 64;
 constexpr int kCS = 256;
 
@@ -393,57 +395,68 @@ __global__ void __launch_bounds__(kCS) coarse_solve_kernel(const double* Lc, con
   __shared__ double Ds[kPan * (kPan + 1)];  // one diagonal inverse, loaded coalesced
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int gw = blockIdx.x * (kCS / 32) + warp, nwarps = gridDim.x * (kCS / 32);
+  const int gt = blockIdx.x * kCS + tid, nthr = gridDim.x * kCS;
   const int npan = (n + kPan - 1) / kPan;
+  const bool lead = blockIdx.x == 0;
+  int prev0 = -1, prevh = 0;  // panel whose solution CTA 0 still has to store
   // forward: L y = b
   for (int p = 0; p < npan; ++p) {
     const int s0 = p * kPan, pe = min(n, s0 + kPan), h = pe - s0;
-    if (blockIdx.x == 0) {
-      for (int a = tid; a < h; a += kCS) yp[a] = y[s0 + a];
-      const double* D = Dinv + (size_t)p * kPan * kPan;
-      for (int e = tid; e < kPan * kPan; e += kCS) Ds[(e / kPan) * (kPan + 1) + e % kPan] = D[e];
-      __syncthreads();
-      for (int a = tid; a < h; a += kCS) {
-        double s = 0.0;
-        for (int k = 0; k <= a; ++k) s += Ds[a * (kPan + 1) + k] * yp[k];
-        yq[a] = s;
-      }
-      __syncthreads();
-      for (int a = tid; a < h; a += kCS) y[s0 + a] = yq[a];
+    if (lead && prev0 >= 0)
+      for (int a = tid; a < prevh; a += kCS) y[prev0 + a] = yq[a];
+    __syncthreads();
+    for (int a = tid; a < h; a += kCS) yp[a] = y[s0 + a];
+    const double* D = Dinv + (size_t)p * kPan * kPan;
+    for (int e = tid; e < kPan * kPan; e += kCS) Ds[(e / kPan) * (kPan + 1) + e % kPan] = D[e];
+    __syncthreads();
+    for (int a = tid; a < h; a += kCS) {
+      double s = 0.0;
+      for (int k = 0; k <= a; ++k) s += Ds[a * (kPan + 1) + k] * yp[k];
+      yq[a] = s;
     }
-    grid.sync();
+    __syncthreads();
     for (int a = pe + gw; a < n; a += nwarps) {
       double s = 0.0;
-      for (int k = s0 + lane; k < pe; k += 32) s += Lc[(int64_t)a * n + k] * y[k];
+      for (int k = lane; k < h; k += 32) s += Lc[(int64_t)a * n + s0 + k] * yq[k];
       s = warp_sum_d(s);
       if (lane == 0) y[a] -= s;
     }
+    prev0 = s0;
+    prevh = h;
     grid.sync();
   }
-  // backward: L^T x = y
-  const int gt = blockIdx.x * kCS + tid, nthr = gridDim.x * kCS;
+  // backward: L^T x = y (the last panel's right-hand side is the yq just solved)
+  prev0 = -1;
   for (int p = npan - 1; p >= 0; --p) {
     const int s0 = p * kPan, pe = min(n, s0 + kPan), h = pe - s0;
-    if (blockIdx.x == 0) {
+    if (p == npan - 1) {
+      for (int a = tid; a < h; a += kCS) yp[a] = yq[a];
+    } else {
+      if (lead && prev0 >= 0)
+        for (int a = tid; a < prevh; a += kCS) y[prev0 + a] = yq[a];
+      __syncthreads();
       for (int a = tid; a < h; a += kCS) yp[a] = y[s0 + a];
-      const double* D = Dinv + (size_t)p * kPan * kPan;
-      for (int e = tid; e < kPan * kPan; e += kCS) Ds[(e / kPan) * (kPan + 1) + e % kPan] = D[e];
-      __syncthreads();
-      for (int a = tid; a < h; a += kCS) {
-        double s = 0.0;
-        for (int k = a; k < h; ++k) s += Ds[k * (kPan + 1) + a] * yp[k];
-        yq[a] = s;
-      }
-      __syncthreads();
-      for (int a = tid; a < h; a += kCS) y[s0 + a] = yq[a];
     }
-    grid.sync();
+    const double* D = Dinv + (size_t)p * kPan * kPan;
+    for (int e = tid; e < kPan * kPan; e += kCS) Ds[(e / kPan) * (kPan + 1) + e % kPan] = D[e];
+    __syncthreads();
+    for (int a = tid; a < h; a += kCS) {
+      double s = 0.0;
+      for (int k = a; k < h; ++k) s += Ds[k * (kPan + 1) + a] * yp[k];
+      yq[a] = s;
+    }
+    __syncthreads();
     for (int c = gt; c < s0; c += nthr) {
       double s = 0.0;
-      for (int a = s0; a < pe; ++a) s += Lc[(int64_t)a * n + c] * y[a];
+      for (int a = 0; a < h; ++a) s += Lc[(int64_t)(s0 + a) * n + c] * yq[a];
       y[c] -= s;
     }
+    prev0 = s0;
+    prevh = h;
     grid.sync();
   }
+  if (lead)
+    for (int a = tid; a < prevh; a += kCS) y[prev0 + a] = yq[a];
 }
 
 // Independent systems, one CTA each: the same panel solves with
@@ -503,10 +516,13 @@ __global__ void __launch_bounds__(kCS) coarse_solve_sys_kernel(const double* Lc,
 }
 
 // Inverses of the diagonal kPan x kPan blocks of L_K (one CTA per block and
-// system, one column of the inverse per thread).
+// system, one column of the inverse per thread, built in shared memory by
+// forward substitution and written out row by row).
 __global__ void __launch_bounds__(kPan) coarse_dinv_kernel(const double* Lc, const int64_t* desc, int nsys,
                                                            double* Dinv) {
-  __shared__ double Lb[kPan * (kPan + 1)];
+  extern __shared__ double dinv_smem[];     // 2 kPan (kPan + 1) doubles
+  double* Lb = dinv_smem;
+  double* X = dinv_smem + kPan * (kPan + 1);
   const int n = static_cast<int>(desc[blockIdx.y]);
   Lc += desc[nsys + blockIdx.y];
   Dinv += desc[3 * nsys + blockIdx.y];
@@ -518,16 +534,23 @@ __global__ void __launch_bounds__(kPan) coarse_dinv_kernel(const double* Lc, con
     Lb[a * (kPan + 1) + b] = Lc[(int64_t)(s0 + a) * n + s0 + b];
   }
   __syncthreads();
-  double* D = Dinv + (size_t)p * kPan * kPan;
   const int j = threadIdx.x;
-  for (int a = 0; a < kPan; ++a) D[a * kPan + j] = 0.0;
+  for (int a = 0; a < kPan; ++a) X[a * (kPan + 1) + j] = 0.0;
   if (j < h) {
     for (int a = j; a < h; ++a) {
-      double x = (a == j) ? 1.0 : 0.0;
-      for (int k = j; k < a; ++k) x -= Lb[a * (kPan + 1) + k] * D[k * kPan + j];
-      D[a * kPan + j] = x / Lb[a * (kPan + 1) + a];
+      double x0 = (a == j) ? 1.0 : 0.0, x1 = 0.0;
+      int k = j;
+      for (; k + 1 < a; k += 2) {
+        x0 -= Lb[a * (kPan + 1) + k] * X[k * (kPan + 1) + j];
+        x1 -= Lb[a * (kPan + 1) + k + 1] * X[(k + 1) * (kPan + 1) + j];
+      }
+      if (k < a) x0 -= Lb[a * (kPan + 1) + k] * X[k * (kPan + 1) + j];
+      X[a * (kPan + 1) + j] = (x0 + x1) / Lb[a * (kPan + 1) + a];
     }
   }
+  __syncthreads();
+  double* D = Dinv + (size_t)p * kPan * kPan;
+  for (int a = 0; a < kPan; ++a) D[a * kPan + j] = X[a * (kPan + 1) + j];
 }
 
 // ---------------- PCG building blocks -----------------------------------
@@ -676,8 +699,15 @@ cudaError_t launch_perm(const int32_t* perm, int64_t n, const double* in, double
 cudaError_t launch_coarse_dinv(const double* Lc, const int64_t* desc, int nsys, int nmax, double* Dinv,
                                cudaStream_t s) {
   if (nmax <= 0) return cudaSuccess;
+  constexpr int smem = 2 * kPan * (kPan + 1) * sizeof(double);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(coarse_dinv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   g_launches.fetch_add(1, std::memory_order_relaxed);
-  coarse_dinv_kernel<<<dim3((nmax + kPan - 1) / kPan, nsys), kPan, 0, s>>>(Lc, desc, nsys, Dinv);
+  coarse_dinv_kernel<<<dim3((nmax + kPan - 1) / kPan, nsys), kPan, smem, s>>>(Lc, desc, nsys, Dinv);
   return cudaGetLastError();
 }
 

@@ -89,7 +89,13 @@ __global__ void copy_tasks_kernel(const CopyTask* tasks, const Ts* src, Td* dst)
 // ---------------- coarse dense Cholesky (FP64, lower, row-major) -----------
 // One dense matrix per independent system: system y = blockIdx.y has size
 // desc[y] and starts at element desc[nsys + y] of the coarse storage.
-constexpr int NB = 64;
+// Right-looking, panels of NB = 32 columns: POTRF of the diagonal tile (one
+// CTA), TRSM of the rows below (one CTA per 32 rows), SYRK of the trailing
+// lower triangle (one CTA per 32 x 32 tile).  FP64 runs at about 2 fused
+// multiply-adds per clock per SM on this GPU, so the panel is kept narrow
+// (short serial chains) and the trailing update is cut into many small tiles
+// to spread it over all SMs.
+constexpr int NB = 32;
 constexpr int NBL = NB + 1;
 
 __device__ __forceinline__ bool coarse_sys(double*& A, int& n, const int64_t* desc, int nsys, int k0) {
@@ -99,11 +105,15 @@ __device__ __forceinline__ bool coarse_sys(double*& A, int& n, const int64_t* de
   return k0 < n;
 }
 
-__global__ void potrf_tile_kernel(double* A, const int64_t* desc, int nsys, int k0, int level, int* status) {
+// Cholesky of the diagonal tile, then its inverse (for the TRSM below):
+// tile inverse of system y at Tinv[y * NB * NB] (row-major, lower)
+__global__ void __launch_bounds__(256) potrf_tile_kernel(double* A, const int64_t* desc, int nsys, int k0,
+                                                         int level, int* status, double* Tinv) {
   if (*status) return;
   int n;
   if (!coarse_sys(A, n, desc, nsys, k0)) return;
   __shared__ double t[NB * NBL];
+  __shared__ double x[NB * NBL];
   const int nb = min(NB, n - k0);
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     int a = e / nb, b = e - a * nb;
@@ -116,72 +126,99 @@ __global__ void potrf_tile_kernel(double* A, const int64_t* desc, int nsys, int 
       if (threadIdx.x == 0) set_status(status, CE_ERR_NOT_SPD, level, -1 - (int)blockIdx.y, 1, k0 + k, piv);
       return;
     }
-    const double d = sqrt(piv);
-    __syncthreads();
-    for (int a = k + threadIdx.x; a < nb; a += blockDim.x) {
-      if (a == k)
-        t[k * NBL + k] = d;
-      else
-        t[a * NBL + k] /= d;
-    }
-    __syncthreads();
+    const double inv = rsqrt(piv);
+    // column k below the pivot (each thread scales the entries it reads next)
     const int rem = nb - k - 1;
     for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-      int a = k + 1 + e / rem, b = k + 1 + e % rem;
-      if (b <= a) t[a * NBL + b] -= t[a * NBL + k] * t[b * NBL + k];
+      const int a = k + 1 + e / rem, b = k + 1 + e % rem;
+      if (b <= a) t[a * NBL + b] -= (t[a * NBL + k] * inv) * (t[b * NBL + k] * inv);
     }
+    __syncthreads();
+    for (int a = k + 1 + threadIdx.x; a < nb; a += blockDim.x) t[a * NBL + k] *= inv;
+    if (threadIdx.x == 0) t[k * NBL + k] = piv * inv;
     __syncthreads();
   }
   for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
     int a = e / nb, b = e - a * nb;
     A[(int64_t)(k0 + a) * n + k0 + b] = (b <= a) ? t[a * NBL + b] : 0.0;
   }
+  // inverse of the lower tile: column j by forward substitution (thread j)
+  const int j = threadIdx.x;
+  if (j < nb) {
+    for (int a = 0; a < j; ++a) x[a * NBL + j] = 0.0;
+    for (int a = j; a < nb; ++a) {
+      double s0 = (a == j) ? 1.0 : 0.0, s1 = 0.0;
+      int k = j;
+      for (; k + 1 < a; k += 2) {
+        s0 -= t[a * NBL + k] * x[k * NBL + j];
+        s1 -= t[a * NBL + k + 1] * x[(k + 1) * NBL + j];
+      }
+      if (k < a) s0 -= t[a * NBL + k] * x[k * NBL + j];
+      x[a * NBL + j] = (s0 + s1) / t[a * NBL + a];
+    }
+  }
+  __syncthreads();
+  double* Ti = Tinv + (size_t)blockIdx.y * NB * NB;
+  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+    int a = e / nb, b = e - a * nb;
+    Ti[a * NB + b] = x[a * NBL + b];
+  }
 }
 
-// L_ik = A_ik L_kk^{-T} for the row tiles below the diagonal tile k0
-__global__ void trsm_tile_kernel(double* A, const int64_t* desc, int nsys, int k0, const int* status) {
+// L_ik = A_ik L_kk^{-T} for the 32-row tiles below the diagonal tile k0, as a
+// product with the tile inverse: L_ik[a][b] = sum_{c <= b} A_ik[a][c] Tinv[b][c]
+__global__ void __launch_bounds__(256) trsm_tile_kernel(double* A, const int64_t* desc, int nsys, int k0,
+                                                        const int* status, const double* Tinv) {
   if (*status) return;
   int n;
   if (!coarse_sys(A, n, desc, nsys, k0)) return;
-  extern __shared__ double tile_smem[];
-  double* Lk = tile_smem;
-  double* X = tile_smem + NB * NBL;
+  __shared__ double Ti[NB * NBL];
+  __shared__ double X[NB * NBL];
   const int nb = min(NB, n - k0);
   const int i0 = k0 + nb + blockIdx.x * NB;
   if (i0 >= n) return;
   const int rows = min(NB, n - i0);
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
+  const double* T = Tinv + (size_t)blockIdx.y * NB * NB;
+  for (int e = threadIdx.x; e < nb * nb; e += 256) {
     int a = e / nb, b = e - a * nb;
-    Lk[a * NBL + b] = A[(int64_t)(k0 + a) * n + k0 + b];
+    Ti[a * NBL + b] = T[a * NB + b];
   }
-  for (int e = threadIdx.x; e < rows * nb; e += blockDim.x) {
+  for (int e = threadIdx.x; e < rows * nb; e += 256) {
     int a = e / nb, b = e - a * nb;
     X[a * NBL + b] = A[(int64_t)(i0 + a) * n + k0 + b];
   }
   __syncthreads();
-  // row a of X solves  x L^T = a  ->  x_b = (a_b - sum_{c<b} x_c L_bc) / L_bb
-  for (int a = threadIdx.x; a < rows; a += blockDim.x) {
-    for (int b = 0; b < nb; ++b) {
-      double s = X[a * NBL + b];
-      for (int c = 0; c < b; ++c) s -= X[a * NBL + c] * Lk[b * NBL + c];
-      X[a * NBL + b] = s / Lk[b * NBL + b];
+  double out[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = threadIdx.x + u * 256, a = e / NB, b = e % NB;
+    double s0 = 0.0, s1 = 0.0;
+    if (a < rows && b < nb) {
+      int c = 0;
+      for (; c + 1 <= b; c += 2) {
+        s0 += X[a * NBL + c] * Ti[b * NBL + c];
+        s1 += X[a * NBL + c + 1] * Ti[b * NBL + c + 1];
+      }
+      if (c <= b) s0 += X[a * NBL + c] * Ti[b * NBL + c];
     }
+    out[u] = s0 + s1;
   }
-  __syncthreads();
-  for (int e = threadIdx.x; e < rows * nb; e += blockDim.x) {
-    int a = e / nb, b = e - a * nb;
-    A[(int64_t)(i0 + a) * n + k0 + b] = X[a * NBL + b];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) {
+    const int e = threadIdx.x + u * 256, a = e / NB, b = e % NB;
+    if (a < rows && b < nb) A[(int64_t)(i0 + a) * n + k0 + b] = out[u];
   }
 }
 
-// A_ij -= L_ik L_jk^T for the trailing tiles j <= i
-__global__ void syrk_tile_kernel(double* A, const int64_t* desc, int nsys, int k0, const int* status) {
+// A_ij -= L_ik L_jk^T for the trailing 32 x 32 tiles j <= i (2 x 2 outputs
+// per thread)
+__global__ void __launch_bounds__(256) syrk_tile_kernel(double* A, const int64_t* desc, int nsys, int k0,
+                                                        const int* status) {
   if (*status) return;
   int n;
   if (!coarse_sys(A, n, desc, nsys, k0)) return;
-  extern __shared__ double tile_smem[];
-  double* Li = tile_smem;
-  double* Lj = tile_smem + NB * NBL;
+  __shared__ double Li[NB * NBL];
+  __shared__ double Lj[NB * NBL];
   const int nb = min(NB, n - k0);
   const int t0 = k0 + nb;
   // blockIdx.x enumerates the lower-triangular tile pairs (ti >= tj)
@@ -194,21 +231,27 @@ __global__ void syrk_tile_kernel(double* A, const int64_t* desc, int nsys, int k
   const int i0 = t0 + ti * NB, j0 = t0 + tj * NB;
   if (i0 >= n) return;
   const int ri = min(NB, n - i0), rj = min(NB, n - j0);
-  for (int e = threadIdx.x; e < ri * nb; e += blockDim.x) {
+  for (int e = threadIdx.x; e < NB * nb; e += 256) {
     int a = e / nb, b = e - a * nb;
-    Li[a * NBL + b] = A[(int64_t)(i0 + a) * n + k0 + b];
-  }
-  for (int e = threadIdx.x; e < rj * nb; e += blockDim.x) {
-    int a = e / nb, b = e - a * nb;
-    Lj[a * NBL + b] = A[(int64_t)(j0 + a) * n + k0 + b];
+    Li[a * NBL + b] = a < ri ? A[(int64_t)(i0 + a) * n + k0 + b] : 0.0;
+    Lj[a * NBL + b] = a < rj ? A[(int64_t)(j0 + a) * n + k0 + b] : 0.0;
   }
   __syncthreads();
-  for (int e = threadIdx.x; e < ri * rj; e += blockDim.x) {
-    int a = e / rj, b = e - a * rj;
-    double s = 0.0;
-    for (int c = 0; c < nb; ++c) s += Li[a * NBL + c] * Lj[b * NBL + c];
-    A[(int64_t)(i0 + a) * n + j0 + b] -= s;
+  const int a0 = (threadIdx.x / 16) * 2, b0 = (threadIdx.x % 16) * 2;
+  double c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+  for (int c = 0; c < nb; ++c) {
+    const double x0 = Li[a0 * NBL + c], x1 = Li[(a0 + 1) * NBL + c];
+    const double y0 = Lj[b0 * NBL + c], y1 = Lj[(b0 + 1) * NBL + c];
+    c00 += x0 * y0;
+    c01 += x0 * y1;
+    c10 += x1 * y0;
+    c11 += x1 * y1;
   }
+  double* C = A + (int64_t)i0 * n + j0;
+  if (a0 < ri && b0 < rj) C[(int64_t)a0 * n + b0] -= c00;
+  if (a0 < ri && b0 + 1 < rj) C[(int64_t)a0 * n + b0 + 1] -= c01;
+  if (a0 + 1 < ri && b0 < rj) C[(int64_t)(a0 + 1) * n + b0] -= c10;
+  if (a0 + 1 < ri && b0 + 1 < rj) C[(int64_t)(a0 + 1) * n + b0 + 1] -= c11;
 }
 
 }  // namespace
@@ -241,34 +284,25 @@ cudaError_t launch_copy_tasks(int esize_src, int esize_dst, const CopyTask* task
 }
 
 cudaError_t coarse_cholesky(double* A, const int64_t* desc, int nsys, int nmax, int level, int* status,
-                            cudaStream_t s) {
-  const int tile_bytes = 2 * NB * NBL * static_cast<int>(sizeof(double));
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(trsm_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         tile_bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(syrk_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_bytes);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+                            double* tinv, cudaStream_t s) {
   // the grids cover the largest system; smaller ones return early
   for (int k0 = 0; k0 < nmax; k0 += NB) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    potrf_tile_kernel<<<dim3(1, nsys), 256, 0, s>>>(A, desc, nsys, k0, level, status);
+    potrf_tile_kernel<<<dim3(1, nsys), 256, 0, s>>>(A, desc, nsys, k0, level, status, tinv);
     const int nb = std::min(NB, nmax - k0);
     const int below = nmax - k0 - nb;
     if (below > 0) {
       const int tiles = (below + NB - 1) / NB;
-      g_launches.fetch_add(1, std::memory_order_relaxed);
-      trsm_tile_kernel<<<dim3(tiles, nsys), 64, tile_bytes, s>>>(A, desc, nsys, k0, status);
-      g_launches.fetch_add(1, std::memory_order_relaxed);
-      syrk_tile_kernel<<<dim3(tiles * (tiles + 1) / 2, nsys), 256, tile_bytes, s>>>(A, desc, nsys, k0, status);
+      g_launches.fetch_add(2, std::memory_order_relaxed);
+      trsm_tile_kernel<<<dim3(tiles, nsys), 256, 0, s>>>(A, desc, nsys, k0, status, tinv);
+      syrk_tile_kernel<<<dim3(tiles * (tiles + 1) / 2, nsys), 256, 0, s>>>(A, desc, nsys, k0, status);
     }
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
+
+size_t coarse_tile_scratch(int nsys) { return (size_t)nsys * NB * NB * sizeof(double); }
 
 }  // namespace ce

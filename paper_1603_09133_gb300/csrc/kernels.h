@@ -44,7 +44,9 @@ cudaError_t launch_copy_tasks(int esize_src, int esize_dst, const CopyTask* task
 // Dense FP64 Cholesky of every system's coarse matrix (in place, lower);
 // desc = [n(nsys), offset(nsys), ...] per system.
 cudaError_t coarse_cholesky(double* A, const int64_t* desc, int nsys, int nmax, int level, int* status,
-                            cudaStream_t s);
+                            double* tinv, cudaStream_t s);
+// bytes of the tinv scratch coarse_cholesky needs (one diagonal-tile inverse per system)
+size_t coarse_tile_scratch(int nsys);
 
 // apply (x = Q^T L^{-T} L^{-1} Q r)
 // one persistent launch per level and direction (see apply_kernels.cu);
