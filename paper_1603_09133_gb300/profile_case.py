@@ -1,0 +1,43 @@
+"""One factorization (and optionally one PCG solve) of a named workload, for
+profiler captures of single launches:
+
+    python -m paper_1603_09133_gb300.profile_case --workload poisson2d_256_B32 \
+        --precision fp32 [--solve]
+
+Each level's row kernel is one launch, so ``ncu -k regex:ce_row_kernel -s L -c 1``
+on this command captures level L + 1.  Prints the per-level row-kernel times.
+"""
+import argparse
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--workload", default="poisson2d_256_B32")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--row-shape", type=int, default=-1)
+    ap.add_argument("--solve", action="store_true")
+    args = ap.parse_args()
+    import torch
+    import workloads as wl
+    import paper_1603_09133_gb300 as ceg
+    w = wl.make_workload(args.workload)
+    csb = ceg.csb_build(w.A, w.perm, w.B)
+    F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision=args.precision,
+                         row_shape=args.row_shape)
+    nl = F.info.levels_done
+    print("row kernel ms per level:", [round(F.info.level_ms[l], 3) for l in range(nl)],
+          "shapes:", list(F.info.row_shape[:nl]))
+    if args.solve:
+        b = torch.as_tensor(w.b, device="cuda")
+        x = torch.zeros_like(b)
+        it, rel, conv = ceg.pcg_solve(csb, F, b, x, 1e-8, 500)
+        xh = x.cpu().numpy()
+        print("PCG iterations", it, "true residual",
+              float(np.linalg.norm(w.b - w.A @ xh) / np.linalg.norm(w.b)))
+    torch.cuda.synchronize()
+
+
+if __name__ == "__main__":
+    main()
