@@ -847,8 +847,19 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       // While the GPU eliminates this level, plan the pattern of the next one
       // from the expected set of blocks that keep a basis (those with live
       // far blocks); checked against the actual ranks below.
-      std::vector<char> guess(P.M);
-      for (int i = 0; i < P.M; ++i) guess[i] = P.n[i] > 0 && P.far_ptr[i + 1] > P.far_ptr[i];
+      // r_i > 0 expected iff row i has a far column when it is processed: a far
+      // neighbour k counts when it has rows left (w_k = r_k for an earlier colour,
+      // n_k otherwise), decided in the elimination order
+      std::vector<char> guess(P.M, 0);
+      for (int q = 0; q < P.M; ++q) {
+        const int i = P.order[q];
+        bool far_cols = false;
+        for (int f = P.far_ptr[i]; f < P.far_ptr[i + 1] && !far_cols; ++f) {
+          const int k = P.far_blk[f];
+          far_cols = P.colour[k] < P.colour[i] ? guess[k] != 0 : P.n[k] > 0;
+        }
+        guess[i] = P.n[i] > 0 && far_cols;
+      }
       ce::NextLevel nx = ce::coarsen_structure(P, guess, o.J);
       auto nxtp = std::make_shared<LevelPlan>();
       ce::plan_structure(*nxtp, nx.M, nx.pairs, o.coloring != 0, nx.sys_off);

@@ -105,6 +105,19 @@ __device__ __forceinline__ bool coarse_sys(double*& A, int& n, const int64_t* de
   return k0 < n;
 }
 
+// 1 / sqrt(x) for x > 0 in FP64: a single-precision estimate refined by two
+// Newton-Raphson steps y <- y (3 - x y^2) / 2 (each doubles the correct bits,
+// 24 -> 48 -> beyond 53); inputs outside the float range take the library
+// function.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+  if (!(x > 1e-30 && x < 1e30)) return rsqrt(x);
+  double y = static_cast<double>(rsqrtf(static_cast<float>(x)));
+  const double hx = 0.5 * x;
+  y = y * (1.5 - hx * y * y);
+  y = y * (1.5 - hx * y * y);
+  return y;
+}
+
 // Cholesky of the diagonal tile, then its inverse (for the TRSM below):
 // tile inverse of system y at Tinv[y * NB * NB] (row-major, lower)
 __global__ void __launch_bounds__(256) potrf_tile_kernel(double* A, const int64_t* desc, int nsys, int k0,
@@ -126,7 +139,7 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(double* A, const int64_
       if (threadIdx.x == 0) set_status(status, CE_ERR_NOT_SPD, level, -1 - (int)blockIdx.y, 1, k0 + k, piv);
       return;
     }
-    const double inv = rsqrt(piv);
+    const double inv = rsqrt_nr(piv);
     // column k below the pivot (each thread scales the entries it reads next)
     const int rem = nb - k - 1;
     for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
@@ -142,7 +155,11 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(double* A, const int64_
     int a = e / nb, b = e - a * nb;
     A[(int64_t)(k0 + a) * n + k0 + b] = (b <= a) ? t[a * NBL + b] : 0.0;
   }
-  // inverse of the lower tile: column j by forward substitution (thread j)
+  // inverse of the lower tile: column j by forward substitution (thread j),
+  // with the reciprocals of the diagonal formed once, in parallel
+  __shared__ double rd[NB];
+  if (threadIdx.x < nb) rd[threadIdx.x] = 1.0 / t[threadIdx.x * NBL + threadIdx.x];
+  __syncthreads();
   const int j = threadIdx.x;
   if (j < nb) {
     for (int a = 0; a < j; ++a) x[a * NBL + j] = 0.0;
@@ -154,7 +171,7 @@ __global__ void __launch_bounds__(256) potrf_tile_kernel(double* A, const int64_
         s1 -= t[a * NBL + k + 1] * x[(k + 1) * NBL + j];
       }
       if (k < a) s0 -= t[a * NBL + k] * x[k * NBL + j];
-      x[a * NBL + j] = (s0 + s1) / t[a * NBL + a];
+      x[a * NBL + j] = (s0 + s1) * rd[a];
     }
   }
   __syncthreads();
