@@ -16,7 +16,8 @@ as the library steps:
 * ``_one_level``     -- Algorithm 2 (one level elimination): for every block
                         row, the compression step of Section 2.2 (eq. rreav and
                         eq. q) and the sub-row elimination of eq. sm_L.
-* ``_coarsen``       -- super-blocks of J consecutive blocks (Section 2.4,
+* ``_coarsen``       -- super-blocks of J consecutive blocks, optionally capped
+                        at nmax rows (Section 2.4,
                         eq. bsp) that start the next level.
 * ``apply``          -- x = Q^T L^{-T} L^{-1} Q b (solve proposition, Sec. 2.5).
 * ``multiply``       -- M x = Q^T L L^T Q x (Proposition CE_L), independent
@@ -144,6 +145,7 @@ class Level:
     steps: list            # BlockStep in elimination order
     J: int
     ranks: list            # r_i by block index
+    groups: list = None    # super-blocks of the next level: child ranges [a, b)
 
 
 @dataclasses.dataclass
@@ -296,25 +298,46 @@ def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
     return S, size, colour, order, steps, ranks
 
 
-def _coarsen(S, size, J):
-    """Join J consecutive blocks into super-blocks (Section 2.4, eq. bsp).
+def _groups(size, J, nmax=None):
+    """Super-blocks as ranges [a, b) of consecutive blocks: J blocks join
+    (Section 2.4); with ``nmax`` a group also closes before the next block
+    would make it larger than nmax rows (a group always takes one block)."""
+    M, groups, a = len(size), [], 0
+    while a < M:
+        b, tot = a + 1, size[a]
+        while b < M and b - a < J and (nmax is None or tot + size[b] <= nmax):
+            tot += size[b]
+            b += 1
+        groups.append((a, b))
+        a = b
+    return groups
+
+
+def _coarsen(S, size, J, nmax=None):
+    """Join consecutive blocks into super-blocks (Section 2.4, eq. bsp).
 
     Child pairs with an empty side are left out, so a super-block pair exists
     when some child pair with non-empty rows and columns lies inside it.
+    Returns the next level's pairs, sizes and the child ranges.
     """
     M = len(size)
-    Mn = (M + J - 1) // J
+    groups = _groups(size, J, nmax)
+    Mn = len(groups)
+    parent = [0] * M
+    for I, (a, b) in enumerate(groups):
+        for i in range(a, b):
+            parent[i] = I
     off = [0] * M
     nsize = [0] * Mn
     for i in range(M):
-        I = i // J
+        I = parent[i]
         off[i] = nsize[I]
         nsize[I] += size[i]
     T = {}
     for (i, k), X in S.items():
         if size[i] == 0 or size[k] == 0:
             continue
-        I, K = i // J, k // J
+        I, K = parent[i], parent[k]
         if (I, K) not in T:
             T[(I, K)] = np.zeros((nsize[I], nsize[K]))
         T[(I, K)][off[i]:off[i] + size[i], off[k]:off[k] + size[k]] += X
@@ -322,7 +345,7 @@ def _coarsen(S, size, J):
             T[(I, K)][off[k]:off[k] + size[k], off[i]:off[i] + size[i]] += X.T
     for I in range(Mn):                 # every super-block keeps its diagonal
         T.setdefault((I, I), np.zeros((nsize[I], nsize[I])))
-    return T, nsize
+    return T, nsize, groups
 
 
 def _dense_from_blocks(S, size):
@@ -366,12 +389,15 @@ def initial_blocks(A, perm, B):
 # Algorithm 1: CE factorization
 # --------------------------------------------------------------------------
 def factorize(A, perm, B, tol, levels, J=4, tol_mode="rel", order="colour",
-              rotate_rng=None, shuffle_rng=None):
+              rotate_rng=None, shuffle_rng=None, nmax=None):
     """CE factorization A ~= Q^T L L^T Q (Algorithm 1, Proposition CE_L).
 
     ``levels`` compression-elimination sweeps, each followed by coarsening by
     J; the remainder A_K is factorized by dense Cholesky.  Raises
     :class:`NotSPDError` when a pivot block is not positive definite.
+
+    ``nmax`` caps the super-block size: a group of J consecutive blocks closes
+    early when the next block would take it past nmax rows.
 
     ``rotate_rng`` / ``shuffle_rng`` are self-test hooks: a random rotation of
     each U_i inside its basis and non-basis subspaces, and a random order of
@@ -388,8 +414,8 @@ def factorize(A, perm, B, tol, levels, J=4, tol_mode="rel", order="colour",
         pairs = sorted(S.keys())
         S, size, colour, order_, steps, ranks = _one_level(
             S, sizes, tol, tol_mode, order, lev, rotate_rng, shuffle_rng, J)
-        recs.append(Level(pairs, sizes_start, colour, order_, steps, J, ranks))
-        S, sizes = _coarsen(S, size, J)
+        S, sizes, groups = _coarsen(S, size, J, nmax)
+        recs.append(Level(pairs, sizes_start, colour, order_, steps, J, ranks, groups))
     Ac = _dense_from_blocks(S, sizes)
     if Ac.shape[0]:
         try:
@@ -431,10 +457,7 @@ def apply(F: Factor, b):
                 y[t] = y[t] - W.T @ zi
             z[i] = zi
         zs.append(z)
-        J = lev.J
-        M = len(lev.sizes)
-        y = [np.concatenate([y[c] for c in range(I * J, min(I * J + J, M))])
-             for I in range((M + J - 1) // J)]
+        y = [np.concatenate([y[c] for c in range(g0, g1)]) for g0, g1 in lev.groups]
     yc = np.concatenate(y) if y else np.zeros(0)
     if F.coarse_L.shape[0]:
         xc = sla.solve_triangular(F.coarse_L, yc, lower=True)
@@ -444,13 +467,12 @@ def apply(F: Factor, b):
     sizes_next = F.coarse_sizes
     x = _split(xc, sizes_next)
     for lev, z in zip(reversed(F.levels), reversed(zs)):
-        J = lev.J
         M = len(lev.sizes)
         # split every super-block into its children's basis parts
         xb = [None] * M
-        for I in range(len(x)):
+        for I, (g0, g1) in enumerate(lev.groups):
             o = 0
-            for c in range(I * J, min(I * J + J, M)):
+            for c in range(g0, g1):
                 rc = lev.ranks[c]
                 xb[c] = x[I][o:o + rc]
                 o += rc
@@ -492,20 +514,18 @@ def multiply(F: Factor, x):
                 zi = zi + W @ y[t]
             z[i] = zi
         zs.append(z)
-        J, M = lev.J, len(lev.sizes)
-        y = [np.concatenate([y[c] for c in range(I * J, min(I * J + J, M))])
-             for I in range((M + J - 1) // J)]
+        y = [np.concatenate([y[c] for c in range(g0, g1)]) for g0, g1 in lev.groups]
     yc = np.concatenate(y) if y else np.zeros(0)
     c = F.coarse_L.T @ yc
     # ---- G^{-1} (z, c)
     xc = F.coarse_L @ c
     xs = _split(xc, F.coarse_sizes)
     for lev, z in zip(reversed(F.levels), reversed(zs)):
-        J, M = lev.J, len(lev.sizes)
+        M = len(lev.sizes)
         xb = [None] * M
-        for I in range(len(xs)):
+        for I, (g0, g1) in enumerate(lev.groups):
             o = 0
-            for ch in range(I * J, min(I * J + J, M)):
+            for ch in range(g0, g1):
                 rc = lev.ranks[ch]
                 xb[ch] = xs[I][o:o + rc]
                 o += rc

@@ -353,3 +353,32 @@ def test_not_spd_is_reported():
     A[10, 10] = -5.0
     with pytest.raises(ce.NotSPDError):
         ce.factorize(sp.csr_matrix(A), np.arange(64), 16, 1e-3, 1, 2)
+
+
+# --------------------------------------------------------------------------
+# capped super-blocks: J consecutive blocks join (Section 2.4), a group
+# closing early before it would pass nmax rows
+# --------------------------------------------------------------------------
+def test_group_rule_by_hand():
+    # sizes 10 20 | 30 5 | 64 | 1 1  with J = 4, nmax = 40 (worked by hand)
+    assert ce._groups([10, 20, 30, 5, 64, 1, 1], 4, 40) == [(0, 2), (2, 4), (4, 5), (5, 7)]
+    # without a cap: plain runs of J
+    assert ce._groups([10, 20, 30, 5, 64, 1, 1], 4) == [(0, 4), (4, 7)]
+    assert ce._groups([3] * 9, 4, 100) == [(0, 4), (4, 8), (8, 9)]
+
+
+def test_capped_coarsening_stays_exact():
+    # tol = 0 keeps M = A whatever the grouping; super-blocks respect the cap
+    A, perm, B = _problem("p2", 32, (4, 4))
+    F = ce.factorize(A, perm, B, 0.0, 3, 4, nmax=24)
+    for lev in F.levels:
+        for g0, g1 in lev.groups:
+            sz = sum(lev.ranks[g0:g1])
+            assert g1 - g0 <= 4 and (sz <= 24 or g1 - g0 == 1)
+    assert any(g1 - g0 < 4 for lev in F.levels for g0, g1 in lev.groups[:-1])   # the cap acted
+    x = wl.rhs(A.shape[0], 3)
+    Ax = A @ x
+    assert np.linalg.norm(ce.multiply(F, x) - Ax) / np.linalg.norm(Ax) < 1e-13
+    b = wl.rhs(A.shape[0], 4)
+    x_ref = sla.cho_solve(sla.cho_factor(A.toarray()), b)
+    assert np.linalg.norm(ce.apply(F, b) - x_ref) / np.linalg.norm(x_ref) < 1e-12
