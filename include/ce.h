@@ -90,7 +90,10 @@ typedef struct {
   int err_reason;      /* 1: pivot <= 0 (index err_pivot, value err_value);
                           2: non-finite singular values of F_i;
                           5: a row's wait for its neighbours timed out
-                          (CE_ERR_CUDA; never expected)                   */
+                          (CE_ERR_CUDA; never expected);
+                          CE_ERR_LIMIT: 3 a block over 64 rows, 4 a row
+                          with over 32 close blocks, 7 a row with over 128
+                          far blocks (err_pivot: the size or count)      */
   int err_pivot;
   double err_value;
   int coarse_n;        /* size of the dense remainder A_K                 */

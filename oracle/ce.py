@@ -299,17 +299,23 @@ def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
 
 
 def _groups(size, J, nmax=None):
-    """Super-blocks as ranges [a, b) of consecutive blocks: J blocks join
-    (Section 2.4); with ``nmax`` a group also closes before the next block
-    would make it larger than nmax rows (a group always takes one block)."""
-    M, groups, a = len(size), [], 0
-    while a < M:
-        b, tot = a + 1, size[a]
-        while b < M and b - a < J and (nmax is None or tot + size[b] <= nmax):
-            tot += size[b]
-            b += 1
-        groups.append((a, b))
-        a = b
+    """Super-blocks as ranges [a, b) of consecutive blocks: runs of J blocks
+    join (Section 2.4).  With ``nmax``, a run whose sizes add up to more than
+    nmax rows is halved (first half ceil(len/2) blocks), recursively, until
+    every part fits or is a single block, so the parts stay aligned with the
+    runs of J (geometric siblings under the box ordering)."""
+    M, groups = len(size), []
+
+    def split(a, b):
+        if b - a == 1 or nmax is None or sum(size[a:b]) <= nmax:
+            groups.append((a, b))
+            return
+        mid = a + (b - a + 1) // 2
+        split(a, mid)
+        split(mid, b)
+
+    for a in range(0, M, J):
+        split(a, min(a + J, M))
     return groups
 
 

@@ -814,7 +814,12 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
     for (int l = 0; l < o.levels && curp->M > 0; ++l) {
       if (curp->nmax > ce::kNMax || max_targets(*curp) > 32) {
         ret = CE_ERR_LIMIT;
-        if (info) info->err_level = l;
+        if (info) {
+          info->err_level = l;
+          info->err_reason = curp->nmax > ce::kNMax ? 3 : 4;
+          info->err_pivot = curp->nmax > ce::kNMax ? curp->nmax : max_targets(*curp);
+          info->levels_done = l;
+        }
         break;
       }
       clk::time_point t_host = clk::now();
@@ -896,8 +901,11 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
         }
         if (info && l < 16)
           for (int i = 0; i < P.M; ++i) info->spec_miss[l] += live[i] != guess[i];
+        // super-blocks capped at the row kernel's limit: the speculative runs
+        // of J stand only if no run passes it
+        if (ce::coarsen_parents(P, o.J, &st.rank, ce::kNMax) != nx.parent) same = false;
         if (!same) {
-          nx = ce::coarsen_structure(P, live, o.J);
+          nx = ce::coarsen_structure(P, live, o.J, &st.rank, ce::kNMax);
           ce::plan_structure(*nxtp, nx.M, nx.pairs, o.coloring != 0, nx.sys_off);
         }
       }

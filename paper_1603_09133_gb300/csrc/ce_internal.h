@@ -136,10 +136,19 @@ struct NextLevel {
   std::vector<int> sys_off;                      // super-blocks of each system
 };
 
-NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J);
+// Super-blocks: runs of J consecutive blocks of one system; a run whose ranks
+// add up to more than nmax rows (the row kernel's limit) is halved until its
+// parts fit, so the parts stay aligned with the runs.
+NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J, int nmax);
 // the same in two steps: the pattern from which blocks keep a basis
-// (live[i] = r_i > 0), then the super-block sizes and child offsets
-NextLevel coarsen_structure(const LevelPlan& P, const std::vector<char>& live, int J);
+// (live[i] = r_i > 0; without ranks the groups are plain runs of J), then the
+// super-block sizes and child offsets
+NextLevel coarsen_structure(const LevelPlan& P, const std::vector<char>& live, int J,
+                            const std::vector<int>* rank = nullptr, int nmax = 0);
+// the super-block of every block under that rule (and optionally each
+// super-block's first child and the super-blocks of each system)
+std::vector<int> coarsen_parents(const LevelPlan& P, int J, const std::vector<int>* rank, int nmax,
+                                 std::vector<int>* first_child = nullptr, std::vector<int>* sys_off = nullptr);
 void coarsen_sizes(const LevelPlan& P, const std::vector<int>& rank, NextLevel& nx);
 
 // graph, work vectors and chunk map of the batched PCG (pcg_batched.cu)

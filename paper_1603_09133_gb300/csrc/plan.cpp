@@ -349,24 +349,52 @@ void plan_level(LevelPlan& P, const std::vector<int>& n,
   plan_layout(P, n);
 }
 
-NextLevel coarsen_structure(const LevelPlan& P, const std::vector<char>& live, int J) {
-  NextLevel nx;
+std::vector<int> coarsen_parents(const LevelPlan& P, int J, const std::vector<int>* rank, int nmax,
+                                 std::vector<int>* first_child, std::vector<int>* sys_off) {
   const int M = P.M;
   std::vector<int> so = P.sys_off;
   if (so.empty()) so = {0, M};
-  nx.parent.assign(M, 0);
-  nx.sys_off.assign(so.size(), 0);
-  std::vector<int> first_child{0};  // children of super-block I: [first_child[I], first_child[I+1])
+  std::vector<int> parent(M, 0);
+  if (first_child) first_child->assign(1, 0);
+  if (sys_off) sys_off->assign(so.size(), 0);
   int next = 0;
+  // emit [a, b) as one super-block, or halve it (first half ceil(len/2)) while
+  // its ranks add up to more than nmax rows
+  std::vector<std::pair<int, int>> stack;
+  auto emit_run = [&](int a0, int b0) {
+    stack.assign(1, {a0, b0});
+    while (!stack.empty()) {
+      const auto [a, b] = stack.back();
+      stack.pop_back();
+      int tot = 0;
+      if (rank)
+        for (int i = a; i < b; ++i) tot += (*rank)[i];
+      if (b - a == 1 || !rank || tot <= nmax) {
+        for (int i = a; i < b; ++i) parent[i] = next;
+        if (first_child) first_child->push_back(b);
+        ++next;
+      } else {
+        const int mid = a + (b - a + 1) / 2;
+        stack.push_back({mid, b});  // the first half is emitted first
+        stack.push_back({a, mid});
+      }
+    }
+  };
   for (size_t s = 0; s + 1 < so.size(); ++s) {
-    nx.sys_off[s] = next;
-    // J consecutive blocks of the same system form one super-block
-    for (int i = so[s]; i < so[s + 1]; ++i) nx.parent[i] = next + (i - so[s]) / J;
-    const int cnt = (so[s + 1] - so[s] + J - 1) / J;
-    for (int t = 0; t < cnt; ++t) first_child.push_back(std::min(so[s + 1], so[s] + (t + 1) * J));
-    next += cnt;
+    if (sys_off) (*sys_off)[s] = next;
+    // runs of J consecutive blocks of the same system
+    for (int a = so[s]; a < so[s + 1]; a += J) emit_run(a, std::min(a + J, so[s + 1]));
   }
-  nx.sys_off.back() = next;
+  if (sys_off) sys_off->back() = next;
+  return parent;
+}
+
+NextLevel coarsen_structure(const LevelPlan& P, const std::vector<char>& live, int J, const std::vector<int>* rank,
+                            int nmax) {
+  NextLevel nx;
+  std::vector<int> first_child;  // children of super-block I: [first_child[I], first_child[I+1])
+  nx.parent = coarsen_parents(P, J, rank, nmax, &first_child, &nx.sys_off);
+  const int next = static_cast<int>(first_child.size()) - 1;
   nx.M = next;
   // super-block rows in parallel: parents of the children's pairs with a
   // non-empty basis on both sides (parent() is monotone, so K >= I)
@@ -405,10 +433,10 @@ void coarsen_sizes(const LevelPlan& P, const std::vector<int>& rank, NextLevel& 
   }
 }
 
-NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J) {
+NextLevel coarsen(const LevelPlan& P, const std::vector<int>& rank, int J, int nmax) {
   std::vector<char> live(P.M);
   for (int i = 0; i < P.M; ++i) live[i] = rank[i] != 0;
-  NextLevel nx = coarsen_structure(P, live, J);
+  NextLevel nx = coarsen_structure(P, live, J, &rank, nmax);
   coarsen_sizes(P, rank, nx);
   return nx;
 }

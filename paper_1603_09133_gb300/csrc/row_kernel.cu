@@ -397,7 +397,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
   }
   const int f0 = L.far_ptr[i], nf = L.far_ptr[i + 1] - f0;
   if (nf > kMaxFar) {
-    if (tid == 0) set_status(status, CE_ERR_LIMIT, level, i);
+    if (tid == 0) set_status(status, CE_ERR_LIMIT, level, i, 7, nf);
     return;
   }
 
@@ -1091,7 +1091,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
   const int c0 = L.close_ptr[i], c1 = L.close_ptr[i + 1];
   const int nt = 1 + (c1 - c0);
   if (nt > kMaxTargets) {
-    if (tid == 0) set_status(status, CE_ERR_LIMIT, level, i);
+    if (tid == 0) set_status(status, CE_ERR_LIMIT, level, i, 4, nt);
     return;
   }
   if (warp == 0) {  // lane t: target t (loads in flight together, column starts by a scan)

@@ -1,0 +1,88 @@
+"""GPU: the variable-coefficient diffusion workload (k = exp(s g), g a Gaussian
+random field, max k / min k = 1e4).
+
+Small grid: every level against the FP64 oracle (colours bit-exact, ranks equal
+away from the threshold, apply within 1e-10, PCG iterations +-1).  Full
+1024 x 1024 grid (1.05 M rows, learned ranks + FP32 blocks + FP64 PCG): what
+holds at any size -- blocks within the row kernel's 64 rows (the capped
+coarsening), PCG to a true residual <= 1e-8, and most rows served by the
+learned sketch.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import ce as oce
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ceg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_09133_gb300 import build
+    build.build()
+    import paper_1603_09133_gb300 as m
+    return m
+
+
+def _ranks_ok(lev, r_g, rel=1e-5):
+    for st in lev.steps:
+        if r_g[st.i] == st.r:
+            continue
+        lo, hi = sorted((r_g[st.i], st.r))
+        if not all(k < st.sigma.size and abs(st.sigma[k] - st.tau) <= rel * st.tau for k in range(lo, hi)):
+            return False
+    return True
+
+
+def test_grf_small_matches_oracle(ceg):
+    n = 128
+    A = wl.diffusion2d(wl.grf2d(n, 3))
+    perm = wl.box_perm((n, n), (8, 4))
+    b = wl.rhs(A.shape[0], 5)
+    Fo = oce.factorize(A, perm, 32, 1e-4, 3, 4, nmax=64)
+    csb = ceg.csb_build(A, perm, 32)
+    F = ceg.ce_factorize(csb, tol=1e-4, levels=3, J=4)
+    same = True
+    for l, lev in enumerate(Fo.levels):
+        if not same:
+            break
+        n_g, r_g, c_g, _ = F.level(l)
+        assert list(n_g) == list(lev.sizes)
+        assert list(c_g) == list(lev.colour)
+        assert _ranks_ok(lev, r_g)
+        same = list(r_g) == list(lev.ranks)
+    z = torch.empty(A.shape[0], dtype=torch.float64, device="cuda")
+    ceg.ce_apply(F, torch.as_tensor(b, device="cuda"), z)
+    zo = oce.apply(Fo, b)
+    err = np.linalg.norm(z.cpu().numpy() - zo) / np.linalg.norm(zo)
+    assert err <= 1e-10, err
+    res_o = oce.pcg(A, Fo, b, 1e-8, 500)
+    x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+    it, rel, conv = ceg.pcg_solve(csb, F, torch.as_tensor(b, device="cuda"), x, 1e-8, 500)
+    true = np.linalg.norm(b - A @ x.cpu().numpy()) / np.linalg.norm(b)
+    assert conv and true <= 1e-8 * 1.01 and abs(it - res_o.iters) <= 1, (it, res_o.iters, true)
+
+
+def test_grf_1024_full_size(ceg):
+    w = wl.make_workload("grf2d_1024_B32")
+    model = ceg.trained_rank_model(steps=1500)
+    csb = ceg.csb_build(w.A, w.perm, w.B)
+    F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision="fp32", rank_model=model)
+    nl = F.info.levels_done
+    assert nl == w.levels
+    assert max(F.info.max_block[l] for l in range(nl)) <= 64
+    acc = sum(F.info.learned_rows[l] for l in range(nl))
+    fb = sum(F.info.fallback_rows[l] for l in range(nl))
+    b = torch.as_tensor(w.b, device="cuda")
+    x = torch.zeros_like(b)
+    it, rel, conv = ceg.pcg_solve(csb, F, b, x, 1e-8, 500)
+    true = np.linalg.norm(w.b - w.A @ x.cpu().numpy()) / np.linalg.norm(w.b)
+    print(f"GRF 1024^2: PCG {it} its, true residual {true:.2e}, learned rows {acc}, fallback {fb}, "
+          f"coarse n {F.info.coarse_n}")
+    assert conv and true <= 1e-8 * 1.01
+    assert acc > fb

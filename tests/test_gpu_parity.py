@@ -146,6 +146,22 @@ def test_tol0_matches_dense_solve(ceg):
     assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) < 1e-12
 
 
+@pytest.mark.parametrize("n,tol,levels", [(96, 1e-6, 3), (64, 1e-8, 3)])
+def test_capped_super_blocks(ceg, n, tol, levels):
+    """Tolerances where runs of J = 4 blocks would pass the row kernel's 64-row
+    limit: the groups close early on both sides (oracle with nmax = 64)."""
+    A = wl.poisson2d(n)
+    perm = wl.box_perm((n, n), (8, 4))
+    b = wl.rhs(A.shape[0], 7)
+    Fo = oce.factorize(A, perm, 32, tol, levels, 4, nmax=64)
+    assert any(g1 - g0 < 4 for lev in Fo.levels for g0, g1 in lev.groups[:-1])
+    Fo_free = oce.factorize(A, perm, 32, tol, levels, 4)
+    assert max(max(lev.sizes) for lev in Fo_free.levels) > 64 or max(Fo_free.coarse_sizes or [0]) > 64
+    _, Fg, csb, err = _compare(ceg, A, perm, 32, tol, levels, 4, b, oracle=Fo)
+    assert max(Fg.info.max_block[l] for l in range(levels)) <= 64
+    _pcg_check(ceg, A, csb, Fg, Fo, b)
+
+
 def test_ragged_blocks(ceg):
     A = wl.poisson2d(10)
     perm = np.arange(100, dtype=np.int32)

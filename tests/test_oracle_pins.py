@@ -356,12 +356,14 @@ def test_not_spd_is_reported():
 
 
 # --------------------------------------------------------------------------
-# capped super-blocks: J consecutive blocks join (Section 2.4), a group
-# closing early before it would pass nmax rows
+# capped super-blocks: runs of J consecutive blocks join (Section 2.4), a run
+# over nmax rows being halved until its parts fit
 # --------------------------------------------------------------------------
 def test_group_rule_by_hand():
-    # sizes 10 20 | 30 5 | 64 | 1 1  with J = 4, nmax = 40 (worked by hand)
-    assert ce._groups([10, 20, 30, 5, 64, 1, 1], 4, 40) == [(0, 2), (2, 4), (4, 5), (5, 7)]
+    # sizes 10 20 30 5 | 64 1 1 with J = 4, nmax = 40 (worked by hand): the first
+    # run (65 rows) halves into 10 20 | 30 5; the last run (66 rows, 3 blocks)
+    # halves into 64 1 | 1, and 64 1 once more into 64 | 1
+    assert ce._groups([10, 20, 30, 5, 64, 1, 1], 4, 40) == [(0, 2), (2, 4), (4, 5), (5, 6), (6, 7)]
     # without a cap: plain runs of J
     assert ce._groups([10, 20, 30, 5, 64, 1, 1], 4) == [(0, 4), (4, 7)]
     assert ce._groups([3] * 9, 4, 100) == [(0, 4), (4, 8), (8, 9)]
