@@ -188,7 +188,9 @@ ce_status csb_build_batched(int nsys, const int64_t* row_off,
  *   out   receives the factor
  *   info  optional, filled on success and on CE_ERR_NOT_SPD
  * Synchronizes the stream once per level (the next level's layout depends
- * on the ranks).  CE_ERR_LIMIT if a block grows beyond 64 rows.
+ * on the ranks).  CE_ERR_LIMIT if a block grows beyond 64 rows, a row has
+ * more than 32 close or 128 far blocks.  The factor uses device memory of A
+ * (the permutation and the level-1 plan): destroy the factor before A.
  */
 ce_status ce_factorize(const ce_csb* A, const ce_opts* o, ce_factor** out,
                        ce_info* info);

@@ -251,54 +251,96 @@ int max_targets(const LevelPlan& P) {
   return t;
 }
 
-// Upload the metadata of a level plan and allocate its factor storage.
-void build_level_store(LevelStore& st, int esize, cudaStream_t s) {
-  const LevelPlan& P = *st.plan;
+// Device metadata of a level plan: the arrays fixed by the plan (uploaded
+// once per plan; level 1's is kept in the csb and shared by every factor) and
+// the per-factorization state (ranks, flags, counters; zero-filled).
+using ce::StaticMeta;
+
+void* upload_static_meta(const LevelPlan& P, StaticMeta& m, size_t& bytes, cudaStream_t s) {
   Packer pk;
-  const size_t o_n = pk.addv(P.n), o_col = pk.addv(P.colour), o_order = pk.addv(P.order),
-               o_cp = pk.addv(P.close_ptr), o_cb = pk.addv(P.close_blk), o_co = pk.addv(P.close_off),
-               o_fp = pk.addv(P.far_ptr), o_fb = pk.addv(P.far_blk), o_fo = pk.addv(P.far_off),
-               o_do = pk.addv(P.diag_off), o_sp = pk.addv(P.schur_ptr), o_so = pk.addv(P.schur_off),
-               o_uo = pk.addv(P.u_off), o_lo = pk.addv(P.l_off), o_wo = pk.addv(P.w_off),
-               o_vo = pk.addv(P.vec_off), o_dp = pk.addv(P.dep_ptr), o_di = pk.addv(P.dep_idx),
-               o_rp = pk.addv(P.rdep_ptr), o_ri = pk.addv(P.rdep_idx),
-               o_rank = pk.zeros(P.M * sizeof(int)), o_done = pk.zeros(P.M * sizeof(int)),
-               o_fd = pk.zeros(P.M * sizeof(int)), o_bd = pk.zeros(P.M * sizeof(int)),
-               o_q = pk.zeros(sizeof(int)),
-               o_gd = pk.zeros(P.M * sizeof(int64_t)), o_tau = pk.zeros(P.M * sizeof(double)),
-               o_sig = pk.zeros(P.vec_len * sizeof(double));
-  st.meta_bytes = pk.size;
-  st.meta = dalloc(st.meta_bytes, s);
-  pk.upload(st.meta, s);
-  char* b = static_cast<char*>(st.meta);
+  m.o_n = pk.addv(P.n);
+  m.o_col = pk.addv(P.colour);
+  m.o_order = pk.addv(P.order);
+  m.o_cp = pk.addv(P.close_ptr);
+  m.o_cb = pk.addv(P.close_blk);
+  m.o_co = pk.addv(P.close_off);
+  m.o_fp = pk.addv(P.far_ptr);
+  m.o_fb = pk.addv(P.far_blk);
+  m.o_fo = pk.addv(P.far_off);
+  m.o_do = pk.addv(P.diag_off);
+  m.o_sp = pk.addv(P.schur_ptr);
+  m.o_so = pk.addv(P.schur_off);
+  m.o_uo = pk.addv(P.u_off);
+  m.o_lo = pk.addv(P.l_off);
+  m.o_wo = pk.addv(P.w_off);
+  m.o_vo = pk.addv(P.vec_off);
+  m.o_dp = pk.addv(P.dep_ptr);
+  m.o_di = pk.addv(P.dep_idx);
+  m.o_rp = pk.addv(P.rdep_ptr);
+  m.o_ri = pk.addv(P.rdep_idx);
+  bytes = pk.size;
+  void* d = dalloc(bytes, s);
+  pk.upload(d, s);
+  return d;
+}
+
+void set_static(LevelDev& D, const void* meta, const StaticMeta& m) {
+  const char* b = static_cast<const char*>(meta);
+  D.n = reinterpret_cast<const int*>(b + m.o_n);
+  D.colour = reinterpret_cast<const int*>(b + m.o_col);
+  D.order = reinterpret_cast<const int*>(b + m.o_order);
+  D.close_ptr = reinterpret_cast<const int*>(b + m.o_cp);
+  D.close_blk = reinterpret_cast<const int*>(b + m.o_cb);
+  D.close_off = reinterpret_cast<const int64_t*>(b + m.o_co);
+  D.far_ptr = reinterpret_cast<const int*>(b + m.o_fp);
+  D.far_blk = reinterpret_cast<const int*>(b + m.o_fb);
+  D.far_off = reinterpret_cast<const int64_t*>(b + m.o_fo);
+  D.diag_off = reinterpret_cast<const int64_t*>(b + m.o_do);
+  D.schur_ptr = reinterpret_cast<const int*>(b + m.o_sp);
+  D.schur_off = reinterpret_cast<const int64_t*>(b + m.o_so);
+  D.u_off = reinterpret_cast<const int64_t*>(b + m.o_uo);
+  D.l_off = reinterpret_cast<const int64_t*>(b + m.o_lo);
+  D.w_off = reinterpret_cast<const int64_t*>(b + m.o_wo);
+  D.vec_off = reinterpret_cast<const int64_t*>(b + m.o_vo);
+  D.dep_ptr = reinterpret_cast<const int*>(b + m.o_dp);
+  D.dep_idx = reinterpret_cast<const int*>(b + m.o_di);
+  D.rdep_ptr = reinterpret_cast<const int*>(b + m.o_rp);
+  D.rdep_idx = reinterpret_cast<const int*>(b + m.o_ri);
+}
+
+// Metadata and factor storage of a level.  `shared` (level 1 of a csb) holds
+// the plan's fixed arrays already on the device; otherwise they are uploaded
+// into the level's own block.
+void build_level_store(LevelStore& st, int esize, cudaStream_t s, const void* shared = nullptr,
+                       const StaticMeta* shared_m = nullptr) {
+  const LevelPlan& P = *st.plan;
   LevelDev& D = st.dev;
   D.M = P.M;
-  D.n = reinterpret_cast<const int*>(b + o_n);
-  D.colour = reinterpret_cast<const int*>(b + o_col);
+  size_t sbytes = 0;
+  if (shared) {
+    st.smeta = nullptr;
+    set_static(D, shared, *shared_m);
+  } else {
+    StaticMeta m;
+    st.smeta = upload_static_meta(P, m, sbytes, s);
+    set_static(D, st.smeta, m);
+  }
+  // per-factorization state, one zero-filled block
+  Packer pk;
+  const size_t o_rank = pk.zeros(P.M * sizeof(int)), o_done = pk.zeros(P.M * sizeof(int)),
+               o_fd = pk.zeros(P.M * sizeof(int)), o_bd = pk.zeros(P.M * sizeof(int)), o_q = pk.zeros(sizeof(int)),
+               o_gd = pk.zeros(P.M * sizeof(int64_t)), o_tau = pk.zeros(P.M * sizeof(double)),
+               o_sig = pk.zeros(P.vec_len * sizeof(double));
+  st.meta_bytes = pk.size + sbytes;
+  st.meta = dalloc(pk.size, s);
+  check(cudaMemsetAsync(st.meta, 0, pk.size, s), "memset level state");
+  char* b = static_cast<char*>(st.meta);
   D.rank = reinterpret_cast<int*>(b + o_rank);
-  D.order = reinterpret_cast<const int*>(b + o_order);
-  D.close_ptr = reinterpret_cast<const int*>(b + o_cp);
-  D.close_blk = reinterpret_cast<const int*>(b + o_cb);
-  D.close_off = reinterpret_cast<const int64_t*>(b + o_co);
-  D.far_ptr = reinterpret_cast<const int*>(b + o_fp);
-  D.far_blk = reinterpret_cast<const int*>(b + o_fb);
-  D.far_off = reinterpret_cast<const int64_t*>(b + o_fo);
-  D.diag_off = reinterpret_cast<const int64_t*>(b + o_do);
-  D.schur_ptr = reinterpret_cast<const int*>(b + o_sp);
-  D.schur_off = reinterpret_cast<const int64_t*>(b + o_so);
-  D.u_off = reinterpret_cast<const int64_t*>(b + o_uo);
-  D.l_off = reinterpret_cast<const int64_t*>(b + o_lo);
-  D.w_off = reinterpret_cast<const int64_t*>(b + o_wo);
-  D.vec_off = reinterpret_cast<const int64_t*>(b + o_vo);
   D.gdst = reinterpret_cast<int64_t*>(b + o_gd);
   D.tau = reinterpret_cast<double*>(b + o_tau);
   D.sigma = reinterpret_cast<double*>(b + o_sig);
-  D.dep_ptr = reinterpret_cast<const int*>(b + o_dp);
-  D.dep_idx = reinterpret_cast<const int*>(b + o_di);
   D.done = reinterpret_cast<int*>(b + o_done);
   D.qnext = reinterpret_cast<int*>(b + o_q);
-  D.rdep_ptr = reinterpret_cast<const int*>(b + o_rp);
-  D.rdep_idx = reinterpret_cast<const int*>(b + o_ri);
   D.fdone = reinterpret_cast<int*>(b + o_fd);
   D.bdone = reinterpret_cast<int*>(b + o_bd);
   D.aq = nullptr;
@@ -429,6 +471,7 @@ void free_factor(ce_factor* F, cudaStream_t s) {
   if (!F) return;
   for (auto& st : F->levels) {
     dfree(st.meta, s);
+    dfree(st.smeta, s);
     dfree(st.fac, s);
   }
   dfree(F->d_coarse, s);
@@ -638,6 +681,8 @@ ce_status build_csb(int64_t n, const int64_t* rowptr, const int32_t* col, const 
           "H2D");
     check(cudaMemcpyAsync(A->d_sys_of_row, sys_of_row.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s),
           "H2D");
+    size_t mb = 0;
+    A->d_meta1 = upload_static_meta(*A->plan1, A->meta1_off, mb, s);
     check(cudaStreamSynchronize(s), "csb_build sync");
   } catch (const CudaFail& f) {
     ce_csb_destroy(A);
@@ -709,6 +754,7 @@ void ce_csb_destroy(ce_csb* A) {
   dfree(A->d_perm, s);
   dfree(A->d_scatter, s);
   dfree(A->d_sys_of_row, s);
+  dfree(A->d_meta1, s);
   delete A;
 }
 
@@ -826,7 +872,10 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       F->levels.emplace_back();
       LevelStore& st = F->levels.back();
       st.plan = curp;
-      build_level_store(st, es, s);
+      if (l == 0 && curp == A->plan1 && A->d_meta1)
+        build_level_store(st, es, s, A->d_meta1, &A->meta1_off);
+      else
+        build_level_store(st, es, s);
       st.dev.pool = pool;
       const double host_ms = ms_since(t_host);
       const LevelPlan& P = *st.plan;

@@ -196,12 +196,19 @@ struct LevelDev {
   void* W;
 };
 
+// Byte offsets of a plan's fixed arrays inside its device metadata block.
+struct StaticMeta {
+  size_t o_n, o_col, o_order, o_cp, o_cb, o_co, o_fp, o_fb, o_fo, o_do, o_sp, o_so, o_uo, o_lo, o_wo, o_vo, o_dp,
+      o_di, o_rp, o_ri;
+};
+
 // One level kept in a factor.
 struct LevelStore {
   std::shared_ptr<const LevelPlan> plan;  // level 1 may share the csb's plan
   std::vector<int> rank;        // host copy
   LevelDev dev{};
-  void* meta = nullptr;         // device metadata block
+  void* meta = nullptr;         // device per-factorization state (ranks, flags, ...)
+  void* smeta = nullptr;        // device arrays fixed by the plan (null: shared)
   void* fac = nullptr;          // device U, L, W block
   size_t fac_bytes = 0;
   size_t meta_bytes = 0;
@@ -228,6 +235,9 @@ struct ce_csb {
   int tuned_levels = 0, tuned_prec = -1, tuned_rank = -1;
   int tuned_shape[16] = {};
   int64_t* d_scatter = nullptr;
+  // level-1 plan's fixed arrays on the device, shared by every factorization
+  void* d_meta1 = nullptr;
+  ce::StaticMeta meta1_off{};
 };
 
 struct ce_factor {
