@@ -344,7 +344,8 @@ def run_ours(args, rank, world):
                   "max_block": [info.max_block[l] for l in range(nl)],
                   "row_kernel_ms": [round(info.level_ms[l], 3) for l in range(nl)],
                   "row_shape": [info.row_shape[l] for l in range(nl)],
-                  "autotune_ms": [[round(v, 3) for v in row] for row in tune_ms.tolist()],
+                  "row_learned": [info.row_learned[l] for l in range(nl)],
+                  "autotune_ms": np.round(tune_ms, 3).tolist(),
                   "host_ms": [round(info.host_ms[l], 3) for l in range(nl)],
                   "factor_wall_ms": round(info.total_ms, 3),
                   "coarse_n": info.coarse_n, "coarse_ms": round(info.coarse_ms, 3),

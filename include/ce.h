@@ -115,6 +115,7 @@ typedef struct {
                           (coarsening, pattern, colouring, reassembly)    */
   double total_ms;     /* wall time of the whole call                     */
   int row_shape[16];   /* CTA shape the row kernel used per level         */
+  int row_learned[16]; /* 1: level l ran the learned compression            */
   int spec_miss[16];   /* blocks of level l whose r_l = 0 or r_l > 0 the
                           speculative planning of level l+1 guessed wrong
                           (0: the pattern planned during the GPU work is
@@ -206,14 +207,19 @@ ce_status ce_factorize_simple(int64_t n, const int64_t* rowptr,
                               int levels, ce_factor** out);
 
 /*
- * ce_autotune -- choose the row kernel's CTA shape per level by measurement:
- * factorizes A once with each shape (options o, row_shape ignored), times
- * every level's launch with CUDA events and keeps the fastest shape per
- * level in A, where later ce_factorize calls with row_shape = -1 and the same
- * precision and rank mode find it.  A shape only changes how a row's work is
- * spread over threads (and with it the rounding of in-row reductions), not
- * what is computed.
- *   level_ms  optional host array of 3 x 16 doubles: [shape][level] times
+ * ce_autotune -- choose, per level and by measurement, the row kernel's CTA
+ * shape and (with o->rank_mode = CE_RANK_LEARNED) whether the learned
+ * compression or the exact SVD runs: factorizes A with every combination
+ * (options o, row_shape ignored), times every level's launch with CUDA
+ * events, and keeps the fastest per level in A (the default -- learned
+ * compression, heuristic shape -- unless another is more than 3 % faster).
+ * Later ce_factorize calls with row_shape = -1 and the same precision and
+ * rank mode use it.  A shape only changes how a row's work is spread over
+ * threads (and the rounding of in-row reductions); the exact SVD instead of
+ * the learned sketch on a level gives ranks at least as tight under the same
+ * tolerance.
+ *   level_ms  optional host array of 2 x 3 x 16 doubles:
+ *             [learned, exact][shape][level] times (ms)
  * Not part of the paper (launch configuration of this implementation).
  */
 ce_status ce_autotune(ce_csb* A, const ce_opts* o, double* level_ms);

@@ -65,6 +65,7 @@ class ce_info(C.Structure):
         ("host_ms", C.c_double * 16),
         ("total_ms", C.c_double),
         ("row_shape", C.c_int * 16),
+        ("row_learned", C.c_int * 16),
         ("spec_miss", C.c_int * 16),
     ]
 

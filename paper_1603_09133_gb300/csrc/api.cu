@@ -673,14 +673,31 @@ ce_status build_csb(int64_t n, const int64_t* rowptr, const int32_t* col, const 
     A->d_perm = static_cast<int32_t*>(dalloc(n * sizeof(int32_t), s));
     A->d_scatter = static_cast<int64_t*>(dalloc(nnz * sizeof(int64_t), s));
     A->d_sys_of_row = static_cast<int32_t*>(dalloc(n * sizeof(int32_t), s));
-    check(cudaMemcpyAsync(A->d_rowptr, rowptr, (n + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, s), "H2D");
-    check(cudaMemcpyAsync(A->d_col, col, nnz * sizeof(int32_t), cudaMemcpyHostToDevice, s), "H2D");
-    check(cudaMemcpyAsync(A->d_val, val, nnz * sizeof(double), cudaMemcpyHostToDevice, s), "H2D");
-    check(cudaMemcpyAsync(A->d_perm, perm, n * sizeof(int32_t), cudaMemcpyHostToDevice, s), "H2D");
-    check(cudaMemcpyAsync(A->d_scatter, scatter.data(), nnz * sizeof(int64_t), cudaMemcpyHostToDevice, s),
-          "H2D");
-    check(cudaMemcpyAsync(A->d_sys_of_row, sys_of_row.data(), n * sizeof(int32_t), cudaMemcpyHostToDevice, s),
-          "H2D");
+    // all arrays through one pinned staging buffer (copied in parallel)
+    struct Up {
+      void* dst;
+      const void* src;
+      size_t bytes;
+    } ups[] = {{A->d_rowptr, rowptr, (n + 1) * sizeof(int64_t)},
+               {A->d_col, col, nnz * sizeof(int32_t)},
+               {A->d_val, val, nnz * sizeof(double)},
+               {A->d_perm, perm, n * sizeof(int32_t)},
+               {A->d_scatter, scatter.data(), nnz * sizeof(int64_t)},
+               {A->d_sys_of_row, sys_of_row.data(), n * sizeof(int32_t)}};
+    size_t off[7] = {0};
+    for (int u = 0; u < 6; ++u) off[u + 1] = off[u] + ((ups[u].bytes + 255) & ~size_t(255));
+    char* h = stage_get(1, off[6]);
+    ce::parallel_for(6 * 16, 1, [&](int64_t b, int64_t e) {
+      for (int64_t t = b; t < e; ++t) {  // 16 slices per array
+        const int u = static_cast<int>(t / 16), q = static_cast<int>(t % 16);
+        const size_t lo = ups[u].bytes * q / 16, hi = ups[u].bytes * (q + 1) / 16;
+        std::memcpy(h + off[u] + lo, static_cast<const char*>(ups[u].src) + lo, hi - lo);
+      }
+    });
+    for (int u = 0; u < 6; ++u)
+      check(cudaMemcpyAsync(ups[u].dst, h + off[u], ups[u].bytes, cudaMemcpyHostToDevice, s), "H2D");
+    check(cudaEventRecord(g_stage[1].ev, s), "event");
+    g_stage[1].pending = true;
     size_t mb = 0;
     A->d_meta1 = upload_static_meta(*A->plan1, A->meta1_off, mb, s);
     check(cudaStreamSynchronize(s), "csb_build sync");
@@ -891,7 +908,14 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       else if (l < A->tuned_levels && A->tuned_prec == o.precision && A->tuned_rank == o.rank_mode)
         shape = A->tuned_shape[l];
       if (info && l < 16) info->row_shape[l] = shape;
-      check(ce::launch_row_kernel(es, st.dev, P.M, l, o.tol, o.tol_mode, F->d_status, P.nmax, shape, la, s),
+      // learned compression on this level unless the autotuner measured the
+      // exact SVD faster here
+      ce::LearnedArgs la_l = la;
+      if (o.row_shape < 0 && l < A->tuned_levels && A->tuned_prec == o.precision && A->tuned_rank == o.rank_mode &&
+          !A->tuned_learned[l])
+        la_l.model = nullptr;
+      if (info && l < 16) info->row_learned[l] = la_l.model != nullptr;
+      check(ce::launch_row_kernel(es, st.dev, P.M, l, o.tol, o.tol_mode, F->d_status, P.nmax, shape, la_l, s),
             "row kernel");
       check(cudaEventRecord(ev1, s), "event");
       // ranks and status into pinned memory, so the host runs on meanwhile
@@ -1090,26 +1114,34 @@ ce_status ce_autotune(ce_csb* A, const ce_opts* o_in, double* level_ms) {
   ce_opts o;
   ce_opts_default(&o);
   if (o_in) o = *o_in;
+  // configurations: CTA shape x (learned compression on | exact SVD), the
+  // latter only when a rank model is given
   constexpr int kShapes = 3, kReps = 3;
-  double t[kShapes][16];
+  const bool learned = o.rank_mode == CE_RANK_LEARNED;
+  const int nmodes = learned ? 2 : 1;
+  double t[2][kShapes][16];
   int heur[16] = {};
   int nl = 16;
-  for (int sh = 0; sh < kShapes; ++sh) {
-    o.row_shape = sh;
-    for (int l = 0; l < 16; ++l) t[sh][l] = 1e300;
-    // one untimed run first (allocator pools, staging buffers), then the
-    // fastest of kReps timed runs per level
-    for (int rep = 0; rep <= kReps; ++rep) {
-      ce_factor* F = nullptr;
-      ce_info info;
-      ce_status st = ce_factorize(A, &o, &F, &info);
-      if (st != CE_OK) return st;
-      ce_factor_destroy(F);
-      nl = std::min(nl, info.levels_done);
-      if (rep > 0)
-        for (int l = 0; l < info.levels_done && l < 16; ++l) t[sh][l] = std::min(t[sh][l], info.level_ms[l]);
+  for (int md = 0; md < nmodes; ++md)
+    for (int sh = 0; sh < kShapes; ++sh) {
+      ce_opts oc = o;
+      oc.row_shape = sh;
+      if (md == 1) oc.rank_mode = CE_RANK_SVD;
+      for (int l = 0; l < 16; ++l) t[md][sh][l] = 1e300;
+      // one untimed run first (allocator pools, staging buffers), then the
+      // fastest of kReps timed runs per level
+      for (int rep = 0; rep <= kReps; ++rep) {
+        ce_factor* F = nullptr;
+        ce_info info;
+        ce_status st = ce_factorize(A, &oc, &F, &info);
+        if (st != CE_OK) return st;
+        ce_factor_destroy(F);
+        nl = std::min(nl, info.levels_done);
+        if (rep > 0)
+          for (int l = 0; l < info.levels_done && l < 16; ++l)
+            t[md][sh][l] = std::min(t[md][sh][l], info.level_ms[l]);
+      }
     }
-  }
   {
     // the heuristic's shape per level, kept unless another is clearly faster
     o.row_shape = -1;
@@ -1124,17 +1156,23 @@ ce_status ce_autotune(ce_csb* A, const ce_opts* o_in, double* level_ms) {
     for (int l = 0; l < 16; ++l) heur[l] = info.row_shape[l];
   }
   for (int l = 0; l < nl; ++l) {
-    int best = heur[l];
-    for (int sh = 0; sh < kShapes; ++sh)
-      if (t[sh][l] < 0.97 * t[best][l]) best = sh;
-    A->tuned_shape[l] = best;
+    int bm = 0, bs = heur[l];  // the default: learned (if given) with the heuristic shape
+    for (int md = 0; md < nmodes; ++md)
+      for (int sh = 0; sh < kShapes; ++sh)
+        if (t[md][sh][l] < 0.97 * t[bm][bs][l]) {
+          bm = md;
+          bs = sh;
+        }
+    A->tuned_shape[l] = bs;
+    A->tuned_learned[l] = learned && bm == 0;
   }
   A->tuned_levels = nl;
   A->tuned_prec = o.precision;
   A->tuned_rank = o.rank_mode;
   if (level_ms)
-    for (int sh = 0; sh < kShapes; ++sh)
-      for (int l = 0; l < 16; ++l) level_ms[sh * 16 + l] = t[sh][l];
+    for (int md = 0; md < 2; ++md)
+      for (int sh = 0; sh < kShapes; ++sh)
+        for (int l = 0; l < 16; ++l) level_ms[(md * kShapes + sh) * 16 + l] = md < nmodes ? t[md][sh][l] : 0.0;
   return CE_OK;
 }
 

@@ -234,6 +234,7 @@ struct ce_csb {
   // and rank mode)
   int tuned_levels = 0, tuned_prec = -1, tuned_rank = -1;
   int tuned_shape[16] = {};
+  int tuned_learned[16] = {};    // learned compression measured faster on level l
   int64_t* d_scatter = nullptr;
   // level-1 plan's fixed arrays on the device, shared by every factorization
   void* d_meta1 = nullptr;

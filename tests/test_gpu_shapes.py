@@ -53,13 +53,34 @@ def test_autotune_keeps_fastest_shape(ceg, problem):
     w, _, _ = problem
     csb = ceg.csb_build(w.A, w.perm, w.B)
     t = ceg.ce_autotune(csb, tol=w.tol, levels=w.levels, J=w.J)
-    assert t.shape == (3, w.levels) and (t > 0).all()
+    assert t.shape == (2, 3, w.levels) and (t[0] > 0).all() and (t[1] == 0).all()
     F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J)
     # the kept shape is within 3% of the fastest one (the heuristic's shape is
     # kept unless another one is more than 3% faster)
     for l in range(w.levels):
         used = F.info.row_shape[l]
-        assert t[used, l] <= t[:, l].min() / 0.97 + 1e-9, (l, used, t[:, l])
+        assert t[0, used, l] <= t[0, :, l].min() / 0.97 + 1e-9, (l, used, t[0, :, l])
     # another precision has no tuned table: the heuristic decides
     F32 = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision="fp32")
     assert all(s in (0, 1) for s in F32.info.row_shape[:w.levels])
+
+
+def test_autotune_learned_or_exact_per_level(ceg):
+    """With a rank model the tuner also decides per level between the learned
+    sketch and the exact SVD; the kept configuration is within 3% of the
+    fastest, and the factorization still meets the FP32 form's bar."""
+    w = wl.make_workload("poisson2d_64_B16")
+    model = ceg.trained_rank_model(steps=500)
+    csb = ceg.csb_build(w.A, w.perm, w.B)
+    t = ceg.ce_autotune(csb, tol=w.tol, levels=w.levels, J=w.J, precision="fp32", rank_model=model)
+    assert t.shape == (2, 3, w.levels) and (t > 0).all()
+    F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision="fp32", rank_model=model)
+    for l in range(w.levels):
+        md = 0 if F.info.row_learned[l] else 1
+        used = t[md, F.info.row_shape[l], l]
+        assert used <= t[:, :, l].min() / 0.97 + 1e-9, (l, md, t[:, :, l])
+    b = torch.as_tensor(w.b, device="cuda")
+    x = torch.zeros_like(b)
+    it, rel, conv = ceg.pcg_solve(csb, F, b, x, 1e-8, 200)
+    true = np.linalg.norm(w.b - w.A @ x.cpu().numpy()) / np.linalg.norm(w.b)
+    assert conv and true <= 1e-8 * 1.01
