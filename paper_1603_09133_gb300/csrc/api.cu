@@ -140,9 +140,17 @@ struct Packer {
   }
   void upload(void* dst, cudaStream_t s) {
     char* h = stage_get(0, data_end);
-    ce::parallel_for(static_cast<int64_t>(items.size()), 1, [&](int64_t b, int64_t e) {
-      for (int64_t t = b; t < e; ++t)
-        if (items[t].bytes) std::memcpy(h + items[t].off, items[t].src, items[t].bytes);
+    // slices of at most 1 MB, copied in parallel
+    constexpr size_t kSlice = size_t(1) << 20;
+    std::vector<std::pair<int, size_t>> sl;
+    for (size_t t = 0; t < items.size(); ++t)
+      for (size_t o = 0; o < items[t].bytes; o += kSlice) sl.emplace_back(static_cast<int>(t), o);
+    ce::parallel_for(static_cast<int64_t>(sl.size()), 4, [&](int64_t b, int64_t e) {
+      for (int64_t q = b; q < e; ++q) {
+        const Item& it = items[sl[q].first];
+        const size_t o = sl[q].second, nb = std::min(kSlice, it.bytes - o);
+        std::memcpy(h + it.off + o, static_cast<const char*>(it.src) + o, nb);
+      }
     });
     stage_upload(0, dst, data_end, s);
     if (size > data_end)
@@ -356,7 +364,7 @@ void build_level_store(LevelStore& st, int esize, cudaStream_t s, const void* sh
 }
 
 // copy tasks: level pairs (kept corners) -> next level pairs
-std::vector<CopyTask> reassembly_tasks(const LevelPlan& P, const std::vector<int>& rank, int J,
+std::vector<std::vector<CopyTask>> reassembly_tasks(const LevelPlan& P, const std::vector<int>& rank, int J,
                                        const ce::NextLevel& nx, const LevelPlan& Pn) {
   const int64_t np = static_cast<int64_t>(P.pair_i.size());
   const int nch = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ce::host_threads() * 4, np / 8192)));
@@ -388,12 +396,7 @@ std::vector<CopyTask> reassembly_tasks(const LevelPlan& P, const std::vector<int
       }
     }
   });
-  std::vector<CopyTask> tasks;
-  size_t tot = 0;
-  for (auto& v : part) tot += v.size();
-  tasks.reserve(tot);
-  for (auto& v : part) tasks.insert(tasks.end(), v.begin(), v.end());
-  return tasks;
+  return part;
 }
 
 // Coarse systems of the last level: system s owns blocks [so[s], so[s+1]),
@@ -455,16 +458,28 @@ std::vector<CopyTask> dense_tasks(const LevelPlan& P, const CoarseSystems& C) {
   return tasks;
 }
 
+// copy tasks given in parts (filled by separate host threads), gathered into
+// the pinned staging buffer in parallel and run by one launch
+void run_copy_tasks(const std::vector<std::vector<CopyTask>>& parts, int es, int ed, const void* src, void* dst,
+                    cudaStream_t s) {
+  std::vector<size_t> off(parts.size() + 1, 0);
+  for (size_t c = 0; c < parts.size(); ++c) off[c + 1] = off[c] + parts[c].size();
+  const size_t ntasks = off.back();
+  if (ntasks == 0) return;
+  const size_t bytes = ntasks * sizeof(CopyTask);
+  void* dt = dalloc(bytes, s);
+  CopyTask* h = reinterpret_cast<CopyTask*>(stage_get(1, bytes));
+  ce::parallel_for(static_cast<int64_t>(parts.size()), 1, [&](int64_t b, int64_t e) {
+    for (int64_t c = b; c < e; ++c) std::copy(parts[c].begin(), parts[c].end(), h + off[c]);
+  });
+  stage_upload(1, dt, bytes, s);
+  check(ce::launch_copy_tasks(es, ed, static_cast<const CopyTask*>(dt), (int)ntasks, src, dst, s), "copy tasks");
+  dfree(dt, s);
+}
+
 void run_copy_tasks(const std::vector<CopyTask>& tasks, int es, int ed, const void* src, void* dst,
                     cudaStream_t s) {
-  if (tasks.empty()) return;
-  const size_t bytes = tasks.size() * sizeof(CopyTask);
-  void* dt = dalloc(bytes, s);
-  std::memcpy(stage_get(1, bytes), tasks.data(), bytes);
-  stage_upload(1, dt, bytes, s);
-  check(ce::launch_copy_tasks(es, ed, static_cast<const CopyTask*>(dt), (int)tasks.size(), src, dst, s),
-        "copy tasks");
-  dfree(dt, s);
+  run_copy_tasks(std::vector<std::vector<CopyTask>>{tasks}, es, ed, src, dst, s);
 }
 
 void free_factor(ce_factor* F, cudaStream_t s) {
