@@ -77,20 +77,40 @@ Csr adjacency(int M, const std::vector<std::pair<int, int>>& pairs) {
   return A;
 }
 
-// greedy distance-2 colouring of blocks [b0, b1), ascending block index
+// greedy distance-2 colouring of blocks [b0, b1), visited in breadth-first
+// order: every component starts at its block of least degree (lowest index on
+// ties), neighbours are queued in ascending index
 void colour_range(const Csr& adj, int b0, int b1, std::vector<int>& colour) {
+  const int nb = b1 - b0;
+  std::vector<int> roots(nb);
+  std::iota(roots.begin(), roots.end(), b0);
+  std::stable_sort(roots.begin(), roots.end(), [&](int a, int b) { return adj.deg(a) < adj.deg(b); });
+  std::vector<char> seen(nb, 0);
+  std::vector<int> queue;
+  queue.reserve(nb);
   std::vector<int> mark;  // mark[c] == i  <=> colour c is taken near i
-  for (int i = b0; i < b1; ++i) {
-    for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j)
-      for (const int* k = adj.row(*j); k != adj.row(*j) + adj.deg(*j); ++k)
-        if (*k != i && colour[*k] >= 0) {
-          const int c = colour[*k];
-          if (c >= static_cast<int>(mark.size())) mark.resize(c + 1, -1);
-          mark[c] = i;
+  for (int root : roots) {
+    if (seen[root - b0]) continue;
+    seen[root - b0] = 1;
+    queue.assign(1, root);
+    for (size_t h = 0; h < queue.size(); ++h) {
+      const int i = queue[h];
+      for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j)
+        for (const int* k = adj.row(*j); k != adj.row(*j) + adj.deg(*j); ++k)
+          if (*k != i && colour[*k] >= 0) {
+            const int c = colour[*k];
+            if (c >= static_cast<int>(mark.size())) mark.resize(c + 1, -1);
+            mark[c] = i;
+          }
+      int c = 0;
+      while (c < static_cast<int>(mark.size()) && mark[c] == i) ++c;
+      colour[i] = c;
+      for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j)
+        if (!seen[*j - b0]) {
+          seen[*j - b0] = 1;
+          queue.push_back(*j);
         }
-    int c = 0;
-    while (c < static_cast<int>(mark.size()) && mark[c] == i) ++c;
-    colour[i] = c;
+    }
   }
 }
 

@@ -93,7 +93,7 @@ def test_learned_factorization_small(ceg, trained, precision):
     assert conv_l and res_l <= 1e-8 * 1.01
     assert it_l <= it_e + 2, (it_e, it_l)
     # the learned M against the oracle's operator (normwise backward error)
-    Fo = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J)
+    Fo = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J, nmax=64)
     z = _apply(ceg, Fl, w.b)
     import scipy.sparse.linalg as spla
     anorm = float(spla.eigsh(w.A, k=1, which="LA", return_eigenvectors=False)[0])
