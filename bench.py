@@ -181,12 +181,12 @@ class Problem:
 def oracle_time(w, grid, levels):
     """Oracle factorize + PCG on a grid x grid sample of the same kind (s)."""
     from oracle import ce as oce
-    A = wl.poisson2d(grid)
+    A = wl.diffusion2d(wl.grf2d(grid, 0)) if w.name.startswith("grf") else wl.poisson2d(grid)
     box = (8, 4) if w.B == 32 else (4, 4)
     perm = wl.box_perm((grid, grid), box)
     b = wl.rhs(A.shape[0], 0)
     t0 = time.perf_counter()
-    F = oce.factorize(A, perm, w.B, w.tol, levels, w.J)
+    F = oce.factorize(A, perm, w.B, w.tol, levels, w.J, nmax=64)
     res = oce.pcg(A, F, b, RTOL, 1000)
     t1 = time.perf_counter()
     assert res.converged
@@ -200,7 +200,7 @@ def oracle_sample(pb):
         from oracle import ce as oce
         w = next(w for w in pb.ws if w.A.shape[0] == 64 * 64)
         t0 = time.perf_counter()
-        F = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J)
+        F = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J, nmax=64)
         res = oce.pcg(w.A, F, w.b, RTOL, 1000)
         t = time.perf_counter() - t0
         assert res.converged
