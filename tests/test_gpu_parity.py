@@ -162,6 +162,19 @@ def test_capped_super_blocks(ceg, n, tol, levels):
     _pcg_check(ceg, A, csb, Fg, Fo, b)
 
 
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_largest_blocks(ceg, precision):
+    """Level-1 blocks of 64 rows (8 x 8 boxes), the row kernel's largest."""
+    n = 128
+    A = wl.poisson2d(n)
+    perm = wl.box_perm((n, n), (8, 8))
+    b = wl.rhs(A.shape[0], 11)
+    Fo, Fg, csb, err = _compare(ceg, A, perm, 64, 1e-4, 2, 4, b,
+                                apply_tol=1e-10 if precision == "fp64" else 1e-4, precision=precision)
+    assert Fg.info.max_block[0] == 64
+    _pcg_check(ceg, A, csb, Fg, Fo, b, slack=None if precision == "fp64" else 2)
+
+
 def test_ragged_blocks(ceg):
     A = wl.poisson2d(10)
     perm = np.arange(100, dtype=np.int32)
