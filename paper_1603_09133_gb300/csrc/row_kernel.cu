@@ -262,15 +262,13 @@ __device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], 
       : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
 }
 
-// C = A B (M x N, inner K) on the tensor cores, one 16 x 8 tile of C per warp
-// at a time; store(a, b, v) is called once per element, like cta_gemm.
-template <int NT, class FA, class FB, class FS>
-__device__ __forceinline__ void cta_gemm_tc(int M, int N, int K, FA A, FB B, FS store) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+// The 16 x 8 tile of C = A B (M x N, inner K) at (r0, c0), by one warp on the
+// tensor cores; store(a, b, v) is called once per element of the tile.
+template <class FA, class FB, class FS>
+__device__ __forceinline__ void warp_tile_tc(int M, int N, int K, FA A, FB B, FS store, int r0, int c0) {
+  const int lane = threadIdx.x & 31;
   const int g = lane >> 2, q = lane & 3;
-  const int tm = (M + 15) >> 4, tn = (N + 7) >> 3;
-  for (int t = warp; t < tm * tn; t += NT / 32) {
-    const int r0 = (t / tn) * 16, c0 = (t % tn) * 8;
+  {
     const int ra = r0 + g, rb = r0 + g + 8, cb = c0 + g;
     float c[4] = {0.f, 0.f, 0.f, 0.f};
     for (int k0 = 0; k0 < K; k0 += 8) {
@@ -303,6 +301,15 @@ __device__ __forceinline__ void cta_gemm_tc(int M, int N, int K, FA A, FB B, FS 
     if (rb < M && cc < N) store(rb, cc, c[2]);
     if (rb < M && cc + 1 < N) store(rb, cc + 1, c[3]);
   }
+}
+
+// C = A B (M x N, inner K) on the tensor cores, one 16 x 8 tile of C per warp
+// at a time; store(a, b, v) is called once per element, like cta_gemm.
+template <int NT, class FA, class FB, class FS>
+__device__ __forceinline__ void cta_gemm_tc(int M, int N, int K, FA A, FB B, FS store) {
+  const int warp = threadIdx.x >> 5;
+  const int tn = (N + 7) >> 3, tiles = ((M + 15) >> 4) * tn;
+  for (int t = warp; t < tiles; t += NT / 32) warp_tile_tc(M, N, K, A, B, store, (t / tn) * 16, (t % tn) * 8);
 }
 
 // FP32 form: tensor cores when `tc` (levels whose blocks exceed 32 rows; on
@@ -1155,7 +1162,47 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     __syncthreads();
   }
   // Schur update between close targets: A(p, q) -= W_p^T W_q
-  if (m > 0) {
+  if (m > 0 && std::is_same<T, float>::value && tc) {
+    // tensor cores: the 16 x 8 tiles of all pairs (p, q) in one list, so the
+    // warps share them evenly whatever the pair sizes
+    __shared__ int s_pt[kMaxTargets * (kMaxTargets + 1) / 2 + 1];
+    const int np1 = nt - 1, npairs = np1 * (np1 + 1) / 2;
+    if (tid == 0) {
+      int acc = 0, p = 0;
+      for (int a = 1; a < nt; ++a)
+        for (int b = a; b < nt; ++b, ++p) {
+          s_pt[p] = acc;
+          acc += ((s_w[a] + 15) >> 4) * ((s_w[b] + 7) >> 3);
+        }
+      s_pt[npairs] = acc;
+    }
+    __syncthreads();
+    const int total = s_pt[npairs];
+    for (int t = warp; t < total; t += kWarpsNT) {
+      int lo = 0, hi = npairs - 1;  // pair p: the last one starting at or before tile t
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_pt[mid] <= t) lo = mid; else hi = mid - 1;
+      }
+      const int p = lo;
+      int a = 1, rem = p;
+      while (rem >= nt - a) {
+        rem -= nt - a;
+        ++a;
+      }
+      const int b = a + rem;
+      const int wa = s_w[a], wb = s_w[b];
+      const T* Wa = Wbase + (int64_t)n * s_colst[a];
+      const T* Wb = Wbase + (int64_t)n * s_colst[b];
+      T* Xg = pool + L.schur_off[L.schur_ptr[i] + nt + p];
+      const int ld = L.n[s_tgt[b]];
+      const int tt = t - s_pt[p], tn = (wb + 7) >> 3;
+      warp_tile_tc(wa, wb, m, [&](int x, int k) { return static_cast<float>(Wa[k * wa + x]); },
+                   [&](int k, int y) { return static_cast<float>(Wb[k * wb + y]); },
+                   [&](int x, int y, float v) { Xg[(int64_t)x * ld + y] -= static_cast<T>(v); }, (tt / tn) * 16,
+                   (tt % tn) * 8);
+    }
+  } else if (m > 0) {
     int idx = L.schur_ptr[i] + nt;   // skip the row of the basis of i
     for (int a = 1; a < nt; ++a) {
       for (int b = a; b < nt; ++b, ++idx) {
