@@ -303,7 +303,7 @@ def run_ours(args, rank, world):
     true_rel = pb.true_relres(x.cpu().numpy())
     ms = max_over_ranks(statistics.mean(times), world, dev)
 
-    # roofline of the dominant kernel (the per-colour row kernel)
+    # roofline of the dominant kernel (the persistent row kernel, one launch per level)
     info = F.info
     nl = info.levels_done
     lms = sum(info.level_ms[l] for l in range(nl))

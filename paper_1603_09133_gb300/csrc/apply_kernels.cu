@@ -2,11 +2,12 @@
 // Section 2.5) and of the FP64 conjugate-gradient loop around it.
 //
 // The level vector of level l holds block i at [vec_off[i], vec_off[i]+n_i).
-// Forward step of block i (same order as the factorization, one launch per
-// colour): y_i <- U_i^T y_i; z = L_hat^{-1} y_i[r:]; y_i[:r] -= W_b^T z;
-// y_p[:w_p] -= W_p^T z for every close p; z is stored in y_i[r:].  The basis
-// parts then move to the next level's vector (super-blocks of J children).
-// The backward step is the transpose, in reverse order.
+// Forward step of block i (in the factorization's colour order, one persistent
+// launch per level): y_i <- U_i^T y_i; z = L_hat^{-1} y_i[r:];
+// y_i[:r] -= W_b^T z; y_p[:w_p] -= W_p^T z for every close p; z is stored in
+// y_i[r:].  The basis parts then move to the next level's vector
+// (super-blocks of consecutive children).  The backward step is the
+// transpose, in reverse order.
 #include <cuda_runtime.h>
 
 #include <cooperative_groups.h>

@@ -1,5 +1,6 @@
-// ce_row_kernel: one CTA per block row i of one colour (Algorithm 2, one
-// iteration of its loop, for all rows of a colour at once).
+// ce_row_kernel: Algorithm 2 for the block rows of one level, one CTA per
+// block row at a time (one iteration of its loop per row; a persistent
+// launch per level, see below).
 //
 //   0. ||D_i||_F (rounding floor of the truncation threshold)
 //   A. compression (Section 2.2, eq. rreav): R factor of F_i^T.  Rows of F_i^T
@@ -15,8 +16,11 @@
 //      W = L_hat^{-1} S is a GEMM; close rows <- U^T C (kept rows minus the
 //      basis Schur term), far rows <- U_b^T F (rows r.. are E_i, dropped), and
 //      the Schur update A(p, q) -= W_p^T W_q between close targets.
+// L. (learned ranks) an MLP-predicted width, a randomized range finder and an
+//    a-posteriori check replace A-B for the rows that pass it.
 // Blocks of one colour have disjoint closed neighbourhoods (distance-2
-// colouring), so the CTAs of one launch touch disjoint block pairs.
+// colouring); a row waits for the lower-colour rows within distance 2, so
+// rows running at the same time touch disjoint block pairs.
 #include <cuda_runtime.h>
 
 #include <type_traits>
