@@ -129,7 +129,7 @@ class Problem:
         self.name = name
         self.batched = name == BATCH
         if self.batched:
-            self.ws = wl.make_batch(BATCH_SYSTEMS, seed=0)
+            self.ws = wl.make_batch(BATCH_SYSTEMS)
             w0 = self.ws[0]
             self.tol, self.levels, self.J = w0.tol, w0.levels, w0.J
             self.B = "16 (sides <= 96) / 32"

@@ -177,6 +177,15 @@ ce_status csb_build_batched(int nsys, const int64_t* row_off,
                             const int32_t* B, ce_csb** out);
 
 /*
+ * ce_factorize_batched -- ce_factorize for a handle from csb_build_batched
+ * (the same call; the name states the intent): every system of the batch is
+ * factorized as if alone, all systems sharing each level's launches.
+ * CE_ERR_INVALID_ARG if A was not built by csb_build_batched.
+ */
+ce_status ce_factorize_batched(const ce_csb* A, const ce_opts* o,
+                               ce_factor** out, ce_info* info);
+
+/*
  * ce_factorize -- Algorithm 1 (CE algorithm): `levels` sweeps of Algorithm 2
  * (one level elimination: per block row the compression of the far blocks
  * F_i by an SVD truncated at tau_i, the row/column transform by U_i and the

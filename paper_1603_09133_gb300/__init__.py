@@ -244,7 +244,7 @@ def ce_autotune(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="r
 
 def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",
                  coloring=True, stream=None, rank_model=None, oversample=8, seed=0,
-                 row_shape=-1) -> Factor:
+                 row_shape=-1, batched=False) -> Factor:
     """Algorithm 1 on the device; returns the factor (raises CEError).
 
     ``rank_model`` (a :class:`RankModel`) switches the compression step to the
@@ -255,7 +255,8 @@ def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="
               row_shape)
     info = _lib.ce_info()
     h = C.c_void_p()
-    st = lib.ce_factorize(csb.handle, C.byref(o), C.byref(h), C.byref(info))
+    entry = lib.ce_factorize_batched if batched else lib.ce_factorize
+    st = entry(csb.handle, C.byref(o), C.byref(h), C.byref(info))
     if st != CE_OK:
         where = "ce_factorize"
         if st == CE_ERR_NOT_SPD:
@@ -266,6 +267,12 @@ def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="
         err.info = info
         raise err
     return Factor(h, info, csb)
+
+
+def ce_factorize_batched(csb: CSB, **kw) -> Factor:
+    """ce_factorize through the batch entry point (the handle must come from
+    csb_build_batched)."""
+    return ce_factorize(csb, batched=True, **kw)
 
 
 def ce_apply(F: Factor, r, z, stream=None):

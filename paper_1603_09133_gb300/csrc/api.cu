@@ -774,7 +774,9 @@ ce_status csb_build_batched(int nsys, const int64_t* row_off, const int64_t* row
     blkptr.push_back(r1);
     sys_blk.push_back(static_cast<int>(blkptr.size()) - 1);
   }
-  return build_csb(n, rowptr, col, val, perm, blkptr, sys_blk, sys_row, B[0], out);
+  const ce_status st = build_csb(n, rowptr, col, val, perm, blkptr, sys_blk, sys_row, B[0], out);
+  if (st == CE_OK) (*out)->batched = true;
+  return st;
 }
 
 void ce_csb_destroy(ce_csb* A) {
@@ -1122,6 +1124,11 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
   *out = F;
   if (info) info->total_ms = ms_since(t_call);
   return CE_OK;
+}
+
+ce_status ce_factorize_batched(const ce_csb* A, const ce_opts* o, ce_factor** out, ce_info* info) {
+  if (!A || !A->batched) return CE_ERR_INVALID_ARG;
+  return ce_factorize(A, o, out, info);
 }
 
 ce_status ce_autotune(ce_csb* A, const ce_opts* o_in, double* level_ms) {

@@ -220,6 +220,7 @@ struct ce_csb {
   int64_t n = 0;
   int B = 0;                     // block size (first system's for a batch)
   int nsys = 1;                  // independent systems (block-diagonal batch)
+  bool batched = false;          // built by csb_build_batched
   std::vector<int64_t> sys_row;  // rows of system s: [sys_row[s], sys_row[s+1])
   int32_t* d_sys_of_row = nullptr;  // system of every row (batched PCG)
   int64_t nnz = 0;

@@ -68,7 +68,7 @@ def small_batch():
 def test_batched_fp64_matches_oracle_per_system(ceg, small_batch):
     ws, Fos = small_batch
     csb = ceg.csb_build_batched([(w.A, w.perm, w.B) for w in ws])
-    F = ceg.ce_factorize(csb, tol=ws[0].tol, levels=ws[0].levels, J=ws[0].J)
+    F = ceg.ce_factorize_batched(csb, tol=ws[0].tol, levels=ws[0].levels, J=ws[0].J)
     sl = _slices(ws)
     # level by level: the batch's blocks are the systems' blocks in order
     for l in range(ws[0].levels):
@@ -184,6 +184,10 @@ def test_batched_invalid_coupling_rejected(ceg):
                                np.ascontiguousarray(A.data, np.float64).ctypes.data_as(_lib.DP),
                                pm.ctypes.data_as(_lib.I32P), Bs.ctypes.data_as(_lib.I32P), C.byref(h))
     assert st == ceg.CE_ERR_INVALID_ARG
+    # the batch entry point refuses a handle of one system
+    single = ceg.csb_build(ws[0].A, ws[0].perm, 16)
+    with pytest.raises(ceg.CEError):
+        ceg.ce_factorize_batched(single, tol=1e-4, levels=2)
 
 
 def test_batched_full_size_256_systems(ceg):
@@ -191,7 +195,7 @@ def test_batched_full_size_256_systems(ceg):
     learned ranks + FP32 blocks + FP64 PCG: every system reaches a true
     residual <= 1e-8; two sampled systems (one of each block size) are checked
     against the oracle's operator on that system alone."""
-    ws = wl.make_batch(256, seed=0)
+    ws = wl.make_batch(256)
     model = ceg.trained_rank_model(steps=1500)
     csb = ceg.csb_build_batched([(w.A, w.perm, w.B) for w in ws])
     F = ceg.ce_factorize(csb, tol=1e-4, levels=4, J=4, precision="fp32", rank_model=model)
