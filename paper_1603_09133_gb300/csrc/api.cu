@@ -160,6 +160,25 @@ struct Packer {
 
 int64_t pair_offset(const LevelPlan& P, int a, int b) { return ce::find_pair(P, a, b); }
 
+// Streams and events for the size buckets' concurrent launches (created once
+// per host thread, on the current device).
+struct SideStreams {
+  cudaStream_t st[ce::kBuckets] = {};
+  cudaEvent_t fork = nullptr, join[ce::kBuckets] = {};
+};
+
+SideStreams& side_streams() {
+  thread_local SideStreams ss;
+  if (!ss.fork) {
+    for (int b = 0; b < ce::kBuckets; ++b) {
+      check(cudaStreamCreateWithFlags(&ss.st[b], cudaStreamNonBlocking), "stream");
+      check(cudaEventCreateWithFlags(&ss.join[b], cudaEventDisableTiming), "event");
+    }
+    check(cudaEventCreateWithFlags(&ss.fork, cudaEventDisableTiming), "event");
+  }
+  return ss;
+}
+
 // Algorithmic flops and bytes of the row-kernel launches of one level,
 // counted per block from its size n, rank r (m = n - r) and the widths w of
 // its close and far neighbours when it is processed:
@@ -336,7 +355,8 @@ void build_level_store(LevelStore& st, int esize, cudaStream_t s, const void* sh
   // per-factorization state, one zero-filled block
   Packer pk;
   const size_t o_rank = pk.zeros(P.M * sizeof(int)), o_done = pk.zeros(P.M * sizeof(int)),
-               o_fd = pk.zeros(P.M * sizeof(int)), o_bd = pk.zeros(P.M * sizeof(int)), o_q = pk.zeros(sizeof(int)),
+               o_fd = pk.zeros(P.M * sizeof(int)), o_bd = pk.zeros(P.M * sizeof(int)),
+               o_q = pk.zeros(ce::kBuckets * sizeof(int)),
                o_gd = pk.zeros(P.M * sizeof(int64_t)), o_tau = pk.zeros(P.M * sizeof(double)),
                o_sig = pk.zeros(P.vec_len * sizeof(double));
   st.meta_bytes = pk.size + sbytes;
@@ -932,8 +952,27 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
           !A->tuned_learned[l])
         la_l.model = nullptr;
       if (info && l < 16) info->row_learned[l] = la_l.model != nullptr;
-      check(ce::launch_row_kernel(es, st.dev, P.M, l, o.tol, o.tol_mode, F->d_status, P.nmax, shape, la_l, s),
-            "row kernel");
+      const int nbkt = static_cast<int>(P.bucket_nmax.size());
+      if (nbkt <= 1) {
+        check(ce::launch_row_kernel(es, st.dev, P.M, l, o.tol, o.tol_mode, F->d_status, P.nmax, shape, la_l, s),
+              "row kernel");
+      } else {
+        // one persistent launch per size bucket, side by side on their own
+        // streams (the buckets never wait for each other)
+        SideStreams& ss = side_streams();
+        check(cudaEventRecord(ss.fork, s), "event");
+        for (int b = 0; b < nbkt; ++b) {
+          LevelDev Lb = st.dev;
+          Lb.order += P.bucket_ptr[b];
+          Lb.qnext += b;
+          check(cudaStreamWaitEvent(ss.st[b], ss.fork, 0), "stream wait");
+          check(ce::launch_row_kernel(es, Lb, P.bucket_ptr[b + 1] - P.bucket_ptr[b], l, o.tol, o.tol_mode,
+                                      F->d_status, P.bucket_nmax[b], shape, la_l, ss.st[b]),
+                "row kernel");
+          check(cudaEventRecord(ss.join[b], ss.st[b]), "event");
+          check(cudaStreamWaitEvent(s, ss.join[b], 0), "stream wait");
+        }
+      }
       check(cudaEventRecord(ev1, s), "event");
       // ranks and status into pinned memory, so the host runs on meanwhile
       int* hread = reinterpret_cast<int*>(stage_get(2, (P.M + ce::kStatusWords) * sizeof(int)));

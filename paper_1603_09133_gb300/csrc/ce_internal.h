@@ -16,6 +16,7 @@
 namespace ce {
 
 constexpr int kNMax = 64;  // largest block the row kernel holds in shared memory
+constexpr int kBuckets = 3;  // size buckets of a batch's rows (<= 16, <= 32, <= 64 rows)
 
 // Host threads for the planning loops (hardware threads, at most 16).
 int host_threads();
@@ -96,6 +97,11 @@ struct LevelPlan {
   std::vector<int> dep_ptr, dep_idx;
   // the transpose: rows of a higher colour within distance 2 (backward apply)
   std::vector<int> rdep_ptr, rdep_idx;
+
+  // size buckets of a batch (whole systems, by their largest block: <= 16,
+  // <= 32, larger rows): order[bucket_ptr[b], bucket_ptr[b+1]) holds bucket
+  // b's rows, colour-major; no row depends on a row of another bucket
+  std::vector<int> bucket_ptr, bucket_nmax;
 };
 
 // Build the plan of a level from its sizes and level-start pattern (pairs

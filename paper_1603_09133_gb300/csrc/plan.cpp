@@ -360,6 +360,39 @@ void plan_layout(LevelPlan& P, const std::vector<int>& n) {
   P.l_elems = lo;
   P.w_elems = wo;
   P.vec_len = vo;
+
+  // size buckets (batches only): a system goes by its largest block; the
+  // colour-major order is partitioned stably by bucket
+  P.bucket_ptr.assign(1, 0);
+  P.bucket_nmax.clear();
+  if (P.sys_off.size() > 2) {
+    std::vector<int> bkt(M, 0);
+    for (size_t s = 0; s + 1 < P.sys_off.size(); ++s) {
+      int mx = 0;
+      for (int i = P.sys_off[s]; i < P.sys_off[s + 1]; ++i) mx = std::max(mx, n[i]);
+      const int b = mx <= 16 ? 0 : (mx <= 32 ? 1 : 2);
+      for (int i = P.sys_off[s]; i < P.sys_off[s + 1]; ++i) bkt[i] = b;
+    }
+    std::vector<int> ord;
+    ord.reserve(M);
+    for (int b = 0; b < kBuckets; ++b) {
+      int mx = 0;
+      const size_t start = ord.size();
+      for (int i : P.order)
+        if (bkt[i] == b) {
+          ord.push_back(i);
+          mx = std::max(mx, n[i]);
+        }
+      if (ord.size() > start) {
+        P.bucket_ptr.push_back(static_cast<int>(ord.size()));
+        P.bucket_nmax.push_back(mx);
+      }
+    }
+    P.order = std::move(ord);
+  } else {
+    P.bucket_ptr.push_back(M);
+    P.bucket_nmax.push_back(P.nmax);
+  }
 }
 
 void plan_level(LevelPlan& P, const std::vector<int>& n,
