@@ -22,7 +22,6 @@ namespace ce {
 
 namespace {
 
-constexpr int kApplyThreads = 128;
 constexpr int kMaxTgt = 32;
 
 __device__ __forceinline__ double warp_sum_d(double v) {

@@ -31,7 +31,6 @@ struct LearnedArgs {
   int* stats = nullptr;           // per level: [rows accepted, rows sent to the exact SVD]
 };
 
-size_t row_kernel_smem(int esize);
 // All `count` rows of a level (order[0, count)) in one persistent launch;
 // shape 0: 256-thread CTAs with a 72 KB budget, 1: 512-thread CTAs with the
 // whole shared memory.

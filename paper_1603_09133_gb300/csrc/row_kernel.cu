@@ -1365,7 +1365,6 @@ cudaError_t launch_nt(const LevelDev& L, int count, int level, double tol, int t
 
 }  // namespace
 
-size_t row_kernel_smem(int esize) { return smem_bytes(esize, kNMax, choose_ld(kNMax), 1); }
 
 cudaError_t launch_row_kernel(int esize, const LevelDev& L, int count, int level, double tol, int tol_mode,
                               int* status, int nmax, int shape, const LearnedArgs& la, cudaStream_t s) {
