@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <cstdint>
 #include <exception>
+#include <functional>
 #include <memory>
 #include <mutex>
 #include <string>
@@ -21,6 +22,11 @@ constexpr int kBuckets = 3;  // size buckets of a batch's rows (<= 16, <= 32, <=
 // Host threads for the planning loops (hardware threads, at most 16).
 int host_threads();
 
+// Runs job(t) for t in [0, tasks) on a pool of host threads kept for the
+// life of the process (and the calling thread); returns when all are done.
+// While the pool serves another caller the tasks run on the calling thread.
+void run_tasks(int64_t tasks, const std::function<void(int64_t)>& job);
+
 // f(begin, end) over [0, n) cut into at most host_threads() ranges of at
 // least `grain` items; the first exception thrown by a range is rethrown.
 template <class F>
@@ -33,19 +39,14 @@ void parallel_for(int64_t n, int64_t grain, F&& f) {
   }
   std::exception_ptr err;
   std::mutex mu;
-  auto run = [&](int64_t t) {
+  run_tasks(T, [&](int64_t t) {
     try {
       f(n * t / T, n * (t + 1) / T);
     } catch (...) {
       std::lock_guard<std::mutex> lk(mu);
       if (!err) err = std::current_exception();
     }
-  };
-  std::vector<std::thread> th;
-  th.reserve(T - 1);
-  for (int64_t t = 1; t < T; ++t) th.emplace_back(run, t);
-  run(0);
-  for (auto& x : th) x.join();
+  });
   if (err) std::rethrow_exception(err);
 }
 

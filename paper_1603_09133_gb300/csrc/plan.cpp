@@ -16,6 +16,11 @@
 #include <numeric>
 #include <stdexcept>
 #include <thread>
+#include <atomic>
+#include <condition_variable>
+#include <mutex>
+
+#include <unistd.h>
 
 #include "ce_internal.h"
 
@@ -27,6 +32,84 @@ int host_threads() {
     return static_cast<int>(std::min(16u, std::max(1u, h)));
   }();
   return t;
+}
+
+namespace {
+
+// Worker threads waiting for jobs; a job is a task count and a function,
+// tasks are taken from an atomic counter by the workers and the caller.
+struct Pool {
+  std::mutex busy;                 // one job at a time
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  const std::function<void(int64_t)>* job = nullptr;
+  int64_t tasks = 0;
+  std::atomic<int64_t> next{0};
+  int active = 0;                  // workers still inside the current job
+  uint64_t generation = 0;
+  int nworkers = 0;
+
+  explicit Pool(int n) : nworkers(n) {
+    for (int w = 0; w < n; ++w) std::thread([this] { loop(); }).detach();
+  }
+
+  void drain() {
+    for (int64_t t; (t = next.fetch_add(1)) < tasks;) (*job)(t);
+  }
+
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_work.wait(lk, [&] { return generation != seen; });
+        seen = generation;
+      }
+      drain();
+      std::lock_guard<std::mutex> lk(mu);
+      if (--active == 0) cv_done.notify_one();
+    }
+  }
+
+  void run(int64_t n, const std::function<void(int64_t)>& f) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      job = &f;
+      tasks = n;
+      next.store(0);
+      active = nworkers;
+      ++generation;
+    }
+    cv_work.notify_all();
+    drain();
+    std::unique_lock<std::mutex> lk(mu);
+    cv_done.wait(lk, [&] { return active == 0; });
+    job = nullptr;
+  }
+};
+
+std::mutex g_pool_mu;
+Pool* g_pool = nullptr;   // kept for the life of the process
+pid_t g_pool_pid = 0;     // a forked child starts a pool of its own
+
+}  // namespace
+
+void run_tasks(int64_t tasks, const std::function<void(int64_t)>& job) {
+  Pool* pool = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    if (!g_pool || g_pool_pid != getpid()) {
+      g_pool = new Pool(host_threads() - 1);
+      g_pool_pid = getpid();
+    }
+    pool = g_pool;
+  }
+  std::unique_lock<std::mutex> lk(pool->busy, std::try_to_lock);
+  if (!lk.owns_lock() || pool->nworkers == 0) {
+    for (int64_t t = 0; t < tasks; ++t) job(t);
+    return;
+  }
+  pool->run(tasks, job);
 }
 
 namespace {
