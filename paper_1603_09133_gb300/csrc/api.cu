@@ -659,13 +659,18 @@ ce_status build_csb(int64_t n, const int64_t* rowptr, const int32_t* col, const 
                     const std::vector<int>& sys_blk, const std::vector<int64_t>& sys_row, int B0,
                     ce_csb** out) {
   const int64_t nnz = rowptr[n];
+  // perm is a permutation; every column in range (read-only, in parallel)
   std::vector<int32_t> iperm(n, -1);
   for (int64_t k = 0; k < n; ++k) {
     if (perm[k] < 0 || perm[k] >= n || iperm[perm[k]] != -1) return CE_ERR_INVALID_ARG;
     iperm[perm[k]] = static_cast<int32_t>(k);
   }
-  for (int64_t e = 0; e < nnz; ++e)
-    if (col[e] < 0 || col[e] >= n) return CE_ERR_INVALID_ARG;
+  std::atomic<bool> bad{false};
+  ce::parallel_for(nnz, 1 << 18, [&](int64_t b, int64_t e) {
+    for (int64_t q = b; q < e && !bad.load(std::memory_order_relaxed); ++q)
+      if (col[q] < 0 || col[q] >= n) bad.store(true);
+  });
+  if (bad.load()) return CE_ERR_INVALID_ARG;
   if (!csr_symmetric(n, rowptr, col, val)) return CE_ERR_INVALID_ARG;
   const int M = static_cast<int>(blkptr.size()) - 1;
   std::vector<int> sizes(M);
@@ -780,16 +785,24 @@ ce_status csb_build_batched(int nsys, const int64_t* row_off, const int64_t* row
   std::vector<int64_t> blkptr{0};
   std::vector<int> sys_blk{0};
   std::vector<int64_t> sys_row(row_off, row_off + nsys + 1);
+  for (int s2 = 0; s2 < nsys; ++s2)
+    if (row_off[s2 + 1] <= row_off[s2] || B[s2] <= 0) return CE_ERR_INVALID_ARG;
+  // the batch is block diagonal: each system's permutation and columns stay
+  // inside its own rows (systems checked in parallel)
+  std::atomic<bool> bad{false};
+  ce::parallel_for(nsys, 1, [&](int64_t s0, int64_t s1) {
+    for (int64_t s2 = s0; s2 < s1 && !bad.load(std::memory_order_relaxed); ++s2) {
+      const int64_t r0 = row_off[s2], r1 = row_off[s2 + 1];
+      for (int64_t k = r0; k < r1; ++k) {
+        if (perm[k] < r0 || perm[k] >= r1) bad.store(true);
+        for (int64_t e = rowptr[k]; e < rowptr[k + 1]; ++e)
+          if (col[e] < r0 || col[e] >= r1) bad.store(true);
+      }
+    }
+  });
+  if (bad.load()) return CE_ERR_INVALID_ARG;
   for (int s2 = 0; s2 < nsys; ++s2) {
     const int64_t r0 = row_off[s2], r1 = row_off[s2 + 1];
-    if (r1 <= r0 || B[s2] <= 0) return CE_ERR_INVALID_ARG;
-    // the batch is block diagonal: each system's permutation and columns stay
-    // inside its own rows
-    for (int64_t k = r0; k < r1; ++k) {
-      if (perm[k] < r0 || perm[k] >= r1) return CE_ERR_INVALID_ARG;
-      for (int64_t e = rowptr[k]; e < rowptr[k + 1]; ++e)
-        if (col[e] < r0 || col[e] >= r1) return CE_ERR_INVALID_ARG;
-    }
     for (int64_t r = r0 + B[s2]; r < r1; r += B[s2]) blkptr.push_back(r);
     blkptr.push_back(r1);
     sys_blk.push_back(static_cast<int>(blkptr.size()) - 1);
