@@ -193,24 +193,37 @@ SideStreams& side_streams() {
 //              + 2 sum_{p<=q close} w_p w_q)             Schur targets r+w
 void level_work(const LevelPlan& P, const std::vector<int>& rank, int es, double& flops,
                 double& bytes) {
+  // fixed chunks summed in chunk order: the totals do not depend on timing
+  constexpr int kChunks = 64;
+  double pf[kChunks] = {}, pb[kChunks] = {};
+  ce::parallel_for(kChunks, 1, [&](int64_t c0, int64_t c1) {
+    for (int64_t c = c0; c < c1; ++c) {
+      const int i0 = static_cast<int>((int64_t)P.M * c / kChunks);
+      const int i1 = static_cast<int>((int64_t)P.M * (c + 1) / kChunks);
+      for (int i = i0; i < i1; ++i) {
+        const double n = P.n[i], r = rank[i], m = n - r;
+        const int ci = P.colour[i];
+        auto wid = [&](int k) { return double(P.colour[k] < ci ? rank[k] : P.n[k]); };
+        double mF = 0, Wc = 0, W2 = 0;
+        for (int f = P.far_ptr[i]; f < P.far_ptr[i + 1]; ++f) mF += wid(P.far_blk[f]);
+        for (int t = P.close_ptr[i]; t < P.close_ptr[i + 1]; ++t) {
+          const double x = wid(P.close_blk[t]);
+          Wc += x;
+          W2 += x * x;
+        }
+        const double pairs = 0.5 * (Wc * Wc + W2);
+        pf[c] += 2 * mF * n * n + (mF > 0 ? 12 * n * n * n : 0) + 4 * n * n * n + 2 * n * n * Wc +
+                 2 * n * r * mF + m * m * m / 3 + m * m * (r + Wc) + m * ((r + Wc) * (r + Wc) + r * r + W2);
+        pb[c] += es * (n * n + n * Wc + n * mF + n * n + m * m + m * (r + Wc) + r * r + r * Wc + r * mF +
+                       2 * pairs);
+      }
+    }
+  });
   flops = 0;
   bytes = 0;
-  for (int i = 0; i < P.M; ++i) {
-    const double n = P.n[i], r = rank[i], m = n - r;
-    const int ci = P.colour[i];
-    auto wid = [&](int k) { return double(P.colour[k] < ci ? rank[k] : P.n[k]); };
-    double mF = 0, Wc = 0, W2 = 0, pairs = 0;
-    for (int f = P.far_ptr[i]; f < P.far_ptr[i + 1]; ++f) mF += wid(P.far_blk[f]);
-    for (int t = P.close_ptr[i]; t < P.close_ptr[i + 1]; ++t) {
-      const double x = wid(P.close_blk[t]);
-      Wc += x;
-      W2 += x * x;
-    }
-    pairs = 0.5 * (Wc * Wc + W2);
-    flops += 2 * mF * n * n + (mF > 0 ? 12 * n * n * n : 0) + 4 * n * n * n + 2 * n * n * Wc +
-             2 * n * r * mF + m * m * m / 3 + m * m * (r + Wc) + m * ((r + Wc) * (r + Wc) + r * r + W2);
-    bytes += es * (n * n + n * Wc + n * mF + n * n + m * m + m * (r + Wc) + r * r + r * Wc + r * mF +
-                   2 * pairs);
+  for (int c = 0; c < kChunks; ++c) {
+    flops += pf[c];
+    bytes += pb[c];
   }
 }
 
