@@ -24,7 +24,7 @@ as the library steps:
                         of ``apply``.
 * ``pcg``            -- preconditioned conjugate gradients with M = Q^T L L^T Q.
 
-Readings of points the paper leaves open (each also listed in the design doc):
+Readings of points the paper leaves open:
 
 * Rank rule (CE(eps), Section 2.2 remark): the norm of E_i is the spectral
   norm and the tolerance is relative to the far row, tau_i = eps * sigma_1(F_i);
@@ -35,9 +35,13 @@ Readings of points the paper leaves open (each also listed in the design doc):
   arithmetic, eps_64 here): a far row that is rounding noise of the block row
   (fill that cancelled to roundoff) carries no direction worth keeping.
 * Elimination order inside a level: colour-major order of a greedy distance-2
-  colouring of the level's block graph (ascending block index inside a colour).
-  The paper's natural order (Algorithm 2) is ``order='natural'``; both are
-  permutations P, which the paper leaves free (Section 2).
+  colouring of the level's block graph, the blocks visited breadth-first from a
+  block of least degree (ascending block index inside a colour).  The paper's
+  natural order (Algorithm 2) is ``order='natural'``; both are permutations P,
+  which the paper leaves free (Section 2).
+* Super-blocks: runs of J consecutive blocks (Section 2.4); with ``nmax`` a run
+  over nmax rows is halved until its parts fit (they stay aligned with the
+  runs).
 * Basis first: the columns of U_i are the left singular vectors of F_i in
   descending singular value order; the first r_i are the basis ("compressed")
   dofs, the last n_i - r_i form the eliminated sub-row S_i = [0 I] R_i*.
