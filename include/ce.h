@@ -153,6 +153,21 @@ ce_status csb_build(int64_t n, const int64_t* rowptr, const int32_t* col,
                     ce_csb** out);
 
 /*
+ * csb_update_values -- new values for the same pattern (numeric
+ * refactorization): replaces the values of A in place, so the next
+ * ce_factorize skips all symbolic work (pattern, colouring, level-1 plan).
+ *   val     host, nnz values in the order of the CSR given to csb_build;
+ *           the matrix must stay symmetric (checked: CE_ERR_INVALID_ARG)
+ *   stream  cudaStream_t of the copy; the call returns after it completes.
+ *           No work that reads A (ce_factorize, pcg_solve) may run on
+ *           another stream meanwhile.
+ * Factors made before the call stay valid and unchanged (they hold their
+ * own values).
+ * Not part of the paper (a usage pattern of repeated solves).
+ */
+ce_status csb_update_values(ce_csb* A, const double* val, void* stream);
+
+/*
  * csb_build_batched -- many independent SPD systems as one block-diagonal
  * matrix, so that each level's launches cover the block rows of all of them
  * (the independent-set batching of Section 2.3 applied across systems; the

@@ -64,10 +64,11 @@ def _dev_ptr(t, what):
 class CSB:
     """Handle of csb_build: A_0 = P A P^T in blocks of B (device copy + plan)."""
 
-    def __init__(self, handle, n, B):
+    def __init__(self, handle, n, B, nnz=None):
         self._h = handle
         self.n = n
         self.B = B
+        self.nnz = nnz
 
     @property
     def handle(self):
@@ -164,7 +165,21 @@ def csb_build(A, perm, B: int) -> CSB:
     _check(lib.csb_build(n, rowptr.ctypes.data_as(_lib.I64P), col.ctypes.data_as(_lib.I32P),
                          val.ctypes.data_as(_lib.DP), pm.ctypes.data_as(_lib.I32P), int(B),
                          C.byref(h)), "csb_build")
-    return CSB(h, n, int(B))
+    return CSB(h, n, int(B), int(A.nnz))
+
+
+def csb_update_values(csb: CSB, A, stream=None):
+    """New values for the csb's pattern (A: scipy sparse with the same CSR
+    pattern as the matrix given to csb_build); the next ce_factorize reuses
+    all symbolic work."""
+    import scipy.sparse as sp
+    lib = _lib.load()
+    A = sp.csr_matrix(A)
+    if A.shape != (csb.n, csb.n) or csb.nnz is None or A.nnz != csb.nnz:
+        raise ValueError("A must have the shape and number of stored entries of the csb's matrix")
+    val = np.ascontiguousarray(A.data, dtype=np.float64)
+    _check(lib.csb_update_values(csb.handle, val.ctypes.data_as(_lib.DP), _stream_ptr(stream)),
+           "csb_update_values")
 
 
 def stack_systems(systems):
@@ -197,7 +212,7 @@ def csb_build_batched_csr(row_off, rowptr, col, val, perm, Bs) -> CSB:
                                  rowptr.ctypes.data_as(_lib.I64P), col.ctypes.data_as(_lib.I32P),
                                  val.ctypes.data_as(_lib.DP), perm.ctypes.data_as(_lib.I32P),
                                  Bs.ctypes.data_as(_lib.I32P), C.byref(h)), "csb_build_batched")
-    csb = CSB(h, int(row_off[-1]), int(Bs[0]))
+    csb = CSB(h, int(row_off[-1]), int(Bs[0]), int(rowptr[-1]))
     csb.row_off = row_off
     return csb
 

@@ -698,6 +698,8 @@ ce_status build_csb(int64_t n, const int64_t* rowptr, const int32_t* col, const 
   A->n = n;
   A->B = B0;
   A->nnz = nnz;
+  A->h_rowptr.assign(rowptr, rowptr + n + 1);
+  A->h_col.assign(col, col + nnz);
   A->nsys = static_cast<int>(sys_row.size()) - 1;
   A->sys_row = sys_row;
   try {
@@ -1188,6 +1190,27 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
   }
   *out = F;
   if (info) info->total_ms = ms_since(t_call);
+  return CE_OK;
+}
+
+ce_status csb_update_values(ce_csb* A, const double* val, void* stream) {
+  if (!A || !val) return CE_ERR_INVALID_ARG;
+  if (!csr_symmetric(A->n, A->h_rowptr.data(), A->h_col.data(), val)) return CE_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  try {
+    const size_t bytes = A->nnz * sizeof(double);
+    char* h = stage_get(1, bytes);
+    ce::parallel_for(16, 1, [&](int64_t b, int64_t e) {
+      for (int64_t q = b; q < e; ++q) {
+        const size_t lo = bytes * q / 16, hi = bytes * (q + 1) / 16;
+        std::memcpy(h + lo, reinterpret_cast<const char*>(val) + lo, hi - lo);
+      }
+    });
+    stage_upload(1, A->d_val, bytes, s);
+    check(cudaStreamSynchronize(s), "csb_update_values sync");
+  } catch (const CudaFail& f) {
+    return status_of(f);
+  }
   return CE_OK;
 }
 

@@ -231,6 +231,9 @@ struct ce_csb {
   std::vector<int64_t> sys_row;  // rows of system s: [sys_row[s], sys_row[s+1])
   int32_t* d_sys_of_row = nullptr;  // system of every row (batched PCG)
   int64_t nnz = 0;
+  // host copy of the pattern (value updates are checked against it)
+  std::vector<int64_t> h_rowptr;
+  std::vector<int32_t> h_col;
   // device CSR of A (original ordering) and the permutation
   int64_t* d_rowptr = nullptr;
   int32_t* d_col = nullptr;
