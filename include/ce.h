@@ -45,8 +45,13 @@ typedef enum {
 /* Truncation rule of the compression step (Section 2.2, eq. rreav and the
  * CE(eps) remark): r_i = #{k : sigma_k(F_i) > tau_i}. */
 enum {
-  CE_TOL_REL = 0, /* tau_i = tol * sigma_1(F_i); tol == 0: n_i*eps*sigma_1 */
-  CE_TOL_ABS = 1  /* tau_i = tol                                           */
+  CE_TOL_REL = 0,  /* tau_i = tol * sigma_1(F_i); tol == 0: n_i*eps*sigma_1 */
+  CE_TOL_ABS = 1,  /* tau_i = tol                                           */
+  CE_TOL_FIXED = 2 /* CE(r) of the Section 2.2 remark: r_i = min(r, numerical
+                      rank of F_i), r = ce_opts.rank; singular values within
+                      1e-3 relative of sigma_r are kept with it (a tied
+                      cluster is kept whole, so the kept subspace is unique).
+                      tol is ignored; not with CE_RANK_LEARNED               */
 };
 
 /* How the compression step finds U_i and r_i. */
@@ -65,7 +70,7 @@ enum {
 
 typedef struct {
   double tol;      /* eps of CE(eps)                                     */
-  int tol_mode;    /* CE_TOL_REL / CE_TOL_ABS                            */
+  int tol_mode;    /* CE_TOL_REL / CE_TOL_ABS / CE_TOL_FIXED             */
   int levels;      /* K, number of compress-and-eliminate sweeps         */
   int J;           /* super-block size: J consecutive blocks join        */
   int precision;   /* CE_PREC_*                                          */
@@ -81,6 +86,7 @@ typedef struct {
                       heuristic; 0: 256 threads, 72 KB shared memory;
                       1: 512 threads, all shared memory; 2: 128 threads,
                       40 KB                                              */
+  int rank;        /* r of CE(r) (CE_TOL_FIXED only; >= 0, default 16)    */
 } ce_opts;
 
 typedef struct {

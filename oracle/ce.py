@@ -29,7 +29,11 @@ Readings of points the paper leaves open:
 * Rank rule (CE(eps), Section 2.2 remark): the norm of E_i is the spectral
   norm and the tolerance is relative to the far row, tau_i = eps * sigma_1(F_i);
   r_i = #{k : sigma_k > tau_i} (a singular value equal to tau_i is dropped).
-  ``tol_mode='abs'`` uses tau_i = eps.  ``tol == 0`` uses
+  ``tol_mode='abs'`` uses tau_i = eps.  CE(r) (``tol_mode='fixed'``, the
+  remark's fixed-rank strategy) keeps r_i = min(r, numerical rank of F_i)
+  directions; a singular value within 1e-3 relative of sigma_r is kept with
+  it, so a tied cluster (grids are symmetric) is never split and the kept
+  subspace is unique.  ``tol == 0`` uses
   tau_i = n_i * eps_64 * sigma_1, which drops only numerically-zero directions.
   In every mode tau_i is at least u * ||D_i||_F (u = unit roundoff of the
   arithmetic, eps_64 here): a far row that is rounding noise of the block row
@@ -70,6 +74,7 @@ import scipy.linalg as sla  # noqa: E402
 import scipy.sparse as sp  # noqa: E402
 
 EPS64 = np.finfo(np.float64).eps
+TIE_REL = 1e-3      # CE(r): singular values within this of sigma_r stay with it
 
 
 class NotSPDError(RuntimeError):
@@ -275,7 +280,16 @@ def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
             r = 0
         else:
             U, sig, _ = np.linalg.svd(F, full_matrices=True)
-            if tol == 0.0:
+            if tol_mode == "fixed":
+                # CE(r): tol carries r; the r leading directions, a cluster
+                # tied with sigma_r kept whole, rounding noise never kept
+                rk = int(tol)
+                tau = n * EPS64 * sig[0]
+                if rk == 0:
+                    tau = sig[0]
+                elif rk < sig.size:
+                    tau = max(tau, (1.0 - TIE_REL) * sig[rk - 1])
+            elif tol == 0.0:
                 tau = n * EPS64 * sig[0]
             elif tol_mode == "abs":
                 tau = tol
@@ -427,7 +441,7 @@ def initial_blocks(A, perm, B):
 # Algorithm 1: CE factorization
 # --------------------------------------------------------------------------
 def factorize(A, perm, B, tol, levels, J=4, tol_mode="rel", order="colour",
-              rotate_rng=None, shuffle_rng=None, nmax=None):
+              rotate_rng=None, shuffle_rng=None, nmax=None, rank=None):
     """CE factorization A ~= Q^T L L^T Q (Algorithm 1, Proposition CE_L).
 
     ``levels`` compression-elimination sweeps, each followed by coarsening by
@@ -437,11 +451,17 @@ def factorize(A, perm, B, tol, levels, J=4, tol_mode="rel", order="colour",
     ``nmax`` caps the super-block size: a group of J consecutive blocks closes
     early when the next block would take it past nmax rows.
 
+    ``tol_mode='fixed'`` is CE(r) with r = ``rank`` (``tol`` is unused).
+
     ``rotate_rng`` / ``shuffle_rng`` are self-test hooks: a random rotation of
     each U_i inside its basis and non-basis subspaces, and a random order of
     the blocks inside each colour.  Neither may change M = Q^T L L^T Q.
     """
     N = A.shape[0]
+    if tol_mode == "fixed":
+        if rank is None or rank < 0:
+            raise ValueError("CE(r) needs rank >= 0")
+        tol = float(rank)
     S, sizes = initial_blocks(A, perm, B)
     sizes0 = list(sizes)
     recs = []

@@ -26,6 +26,7 @@ from ._lib import (  # noqa: F401
     CE_RANK_LEARNED,
     CE_RANK_SVD,
     CE_TOL_ABS,
+    CE_TOL_FIXED,
     CE_TOL_REL,
 )
 
@@ -223,13 +224,19 @@ def csb_build_batched(systems) -> CSB:
     return csb_build_batched_csr(*stack_systems(systems))
 
 
+_TOL_MODES = {"rel": CE_TOL_REL, "abs": CE_TOL_ABS, "fixed": CE_TOL_FIXED}
+
+
 def _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed,
-          row_shape):
+          row_shape, rank=16):
     lib = _lib.load()
     o = _lib.ce_opts()
     lib.ce_opts_default(C.byref(o))
     o.tol = float(tol)
-    o.tol_mode = CE_TOL_REL if tol_mode == "rel" else CE_TOL_ABS
+    if tol_mode not in _TOL_MODES:
+        raise ValueError(f"tol_mode must be one of {sorted(_TOL_MODES)}")
+    o.tol_mode = _TOL_MODES[tol_mode]
+    o.rank = int(rank)
     o.levels = int(levels)
     o.J = int(J)
     o.precision = CE_PREC_FP64 if precision == "fp64" else CE_PREC_FP32
@@ -259,15 +266,16 @@ def ce_autotune(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="r
 
 def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",
                  coloring=True, stream=None, rank_model=None, oversample=8, seed=0,
-                 row_shape=-1, batched=False) -> Factor:
+                 row_shape=-1, batched=False, rank=16) -> Factor:
     """Algorithm 1 on the device; returns the factor (raises CEError).
 
     ``rank_model`` (a :class:`RankModel`) switches the compression step to the
     learned rank + randomized range finder with exact-SVD fallback.
+    ``tol_mode="fixed"`` is CE(r) with r = ``rank`` (``tol`` unused).
     """
     lib = _lib.load()
     o = _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed,
-              row_shape)
+              row_shape, rank)
     info = _lib.ce_info()
     h = C.c_void_p()
     entry = lib.ce_factorize_batched if batched else lib.ce_factorize

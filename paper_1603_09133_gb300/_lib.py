@@ -20,6 +20,7 @@ CE_ERR_CUDA = 5
 CE_ERR_LIMIT = 6
 CE_TOL_REL = 0
 CE_TOL_ABS = 1
+CE_TOL_FIXED = 2
 CE_PREC_FP64 = 0
 CE_PREC_FP32 = 1
 CE_RANK_SVD = 0
@@ -40,6 +41,7 @@ class ce_opts(C.Structure):
         ("oversample", C.c_int),
         ("seed", C.c_uint64),
         ("row_shape", C.c_int),
+        ("rank", C.c_int),
     ]
 
 

@@ -555,6 +555,7 @@ void ce_opts_default(ce_opts* o) {
   o->oversample = 8;
   o->seed = 0;
   o->row_shape = -1;
+  o->rank = 16;
 }
 
 const char* ce_strerror(ce_status s) {
@@ -891,11 +892,14 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
   ce_opts_default(&o);
   if (o_in) o = *o_in;
   if (o.levels < 0 || o.J < 1 || o.tol < 0 || (o.precision != CE_PREC_FP64 && o.precision != CE_PREC_FP32) ||
-      (o.tol_mode != CE_TOL_REL && o.tol_mode != CE_TOL_ABS) ||
+      (o.tol_mode != CE_TOL_REL && o.tol_mode != CE_TOL_ABS && o.tol_mode != CE_TOL_FIXED) ||
+      (o.tol_mode == CE_TOL_FIXED && (o.rank < 0 || o.rank_mode != CE_RANK_SVD)) ||
       (o.rank_mode != CE_RANK_SVD && o.rank_mode != CE_RANK_LEARNED) ||
       (o.rank_mode == CE_RANK_LEARNED && (!o.rank_model || o.oversample < 0)) || o.row_shape < -1 ||
       o.row_shape > 2)
     return CE_ERR_INVALID_ARG;
+  // CE(r): the row kernel takes r in place of the tolerance
+  if (o.tol_mode == CE_TOL_FIXED) o.tol = static_cast<double>(o.rank);
   *out = nullptr;
   if (info) std::memset(info, 0, sizeof(*info));
   using clk = std::chrono::steady_clock;

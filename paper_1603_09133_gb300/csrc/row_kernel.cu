@@ -40,6 +40,7 @@ constexpr int kChunk = 32;       // rows of F_i^T per warp Householder pass
 constexpr int kMaxSweeps = 40;   // Jacobi sweep cap (bounded loop)
 constexpr int kMaxTargets = 32;
 constexpr int kMaxFar = 128;
+constexpr double kTieRel = 1e-3; // CE(r): singular values this close to sigma_r stay with it
 
 template <typename T>
 struct Eps;
@@ -690,7 +691,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
             cm = warp_max(cm);
             if (lane == 0) {
               const T sm = sqrt(cm);
-              T test = (tol == 0.0) ? T(n) * Eps<T>::v * sm
+              T test = (tol == 0.0 || tol_mode == CE_TOL_FIXED) ? T(n) * Eps<T>::v * sm
                                     : ((tol_mode == CE_TOL_ABS) ? T(tol) : T(tol) * sm);
               test = fmax(test, static_cast<T>(floor_all)) * T(0.5) * fast_rsqrt(T(k));
               s_skip2 = test * test;
@@ -763,7 +764,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
       __syncthreads();
       if (tid == 0) {
         const double smax = static_cast<double>(sig[0]);
-        double tt = (tol == 0.0) ? n * static_cast<double>(Eps<T>::v) * smax
+        double tt = (tol == 0.0 || tol_mode == CE_TOL_FIXED) ? n * static_cast<double>(Eps<T>::v) * smax
                                  : ((tol_mode == CE_TOL_ABS) ? tol : tol * smax);
         tt = fmax(tt, floor_all);
         int rr = 0;
@@ -914,7 +915,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
         cm = warp_max(cm);
         if (lane == 0) {
           const T sm = sqrt(cm);
-          T test = (tol == 0.0) ? T(n) * Eps<T>::v * sm
+          T test = (tol == 0.0 || tol_mode == CE_TOL_FIXED) ? T(n) * Eps<T>::v * sm
                                 : ((tol_mode == CE_TOL_ABS) ? T(tol) : T(tol) * sm);
           test = fmax(test, floor_tau_t) * T(0.5) * fast_rsqrt(T(n));
           s_skip2 = test * test;
@@ -996,10 +997,21 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
       if (tid == 0) set_status(status, CE_ERR_NOT_SPD, level, i, 2);
       return;
     }
-    if (tol == 0.0)
+    if (tol_mode == CE_TOL_FIXED) {
+      // CE(r) (Section 2.2 remark): the r leading directions, with every
+      // singular value tied with sigma_r (within kTieRel) and none that is
+      // rounding noise; tol carries r
+      const int rf = static_cast<int>(tol);
       tau = n * static_cast<double>(Eps<T>::v) * smax;
-    else
+      if (rf == 0)
+        tau = fmax(tau, smax);
+      else if (rf < n)
+        tau = fmax(tau, (1.0 - kTieRel) * static_cast<double>(sig[rf - 1]));
+    } else if (tol == 0.0) {
+      tau = n * static_cast<double>(Eps<T>::v) * smax;
+    } else {
       tau = (tol_mode == CE_TOL_ABS) ? tol : tol * smax;
+    }
     tau = fmax(tau, floor_tau);
     if (tid == 0) {
       int rr = 0;
