@@ -380,7 +380,9 @@ ce_status ce_factor_get_sigma(const ce_factor* F, int level, double* sigma);
 /*
  * ce_plan_level1 -- host-only symbolic analysis of level 1 (no CUDA call):
  * the block graph of P A P^T with blocks of B rows, its greedy distance-2
- * colouring in ascending block index, and the number of block pairs of the
+ * colouring (blocks visited breadth-first from a block of least degree,
+ * ascending neighbours; smallest colour free within distance 2), and the
+ * number of block pairs of the
  * squared pattern (close + far pairs, Section 2.2).  Arguments as csb_build
  * (values are not needed).
  *   colour    host, ceil(n/B) entries, may be NULL
@@ -391,6 +393,22 @@ ce_status ce_factor_get_sigma(const ce_factor* F, int level, double* sigma);
 ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col,
                          const int32_t* perm, int32_t B, int32_t* colour,
                          int* ncolours, int64_t* npairs, int64_t* nclose);
+
+/*
+ * ce_plan_groups -- host-only (no CUDA call): the super-blocks that
+ * ce_factorize forms from one level's blocks (Section 2.4).  Runs of J
+ * consecutive blocks join; a run whose ranks add up to more than nmax rows is
+ * halved, first half ceil(len/2) blocks, recursively, until every part fits or
+ * is one block (ce_factorize uses nmax = 64, the row kernel's limit).
+ *   M            blocks of the level
+ *   rank         host, M kept sizes r_i (>= 0)
+ *   first_child  host, room for M + 1 entries: super-block I holds blocks
+ *                [first_child[I], first_child[I + 1])
+ *   ngroups      number of super-blocks
+ * CE_ERR_INVALID_ARG for M < 1, J < 1, nmax < 0, a negative rank or a NULL
+ * pointer.
+ */
+ce_status ce_plan_groups(int M, const int32_t* rank, int J, int nmax, int32_t* first_child, int* ngroups);
 
 /* Level-1 plan of a csb handle: blocks, colours, colour of every block. */
 int csb_blocks(const ce_csb* A);

@@ -841,6 +841,24 @@ void ce_csb_destroy(ce_csb* A) {
   delete A;
 }
 
+ce_status ce_plan_groups(int M, const int32_t* rank, int J, int nmax, int32_t* first_child, int* ngroups) {
+  if (M < 1 || J < 1 || nmax < 0 || !rank || !first_child || !ngroups) return CE_ERR_INVALID_ARG;
+  for (int i = 0; i < M; ++i)
+    if (rank[i] < 0) return CE_ERR_INVALID_ARG;
+  try {
+    ce::LevelPlan P;
+    P.M = M;
+    const std::vector<int> r(rank, rank + M);
+    std::vector<int> fc;
+    ce::coarsen_parents(P, J, &r, nmax, &fc, nullptr);
+    std::copy(fc.begin(), fc.end(), first_child);
+    *ngroups = static_cast<int>(fc.size()) - 1;
+  } catch (const std::bad_alloc&) {
+    return CE_ERR_OOM;
+  }
+  return CE_OK;
+}
+
 ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm,
                          int32_t B, int32_t* colour, int* ncolours, int64_t* npairs, int64_t* nclose) {
   if (n <= 0 || !rowptr || !col || !perm || B <= 0 || n > INT32_MAX || rowptr[0] != 0)

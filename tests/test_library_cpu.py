@@ -123,3 +123,38 @@ def test_host_plan_ragged_and_natural(lib):
     assert sizes[-1] == 4
     ocol = oce.distance2_colouring(oce._block_graph(S, len(sizes)))
     assert list(col) == ocol
+
+
+def _groups_c(lib, rank, J, nmax):
+    rank = np.ascontiguousarray(rank, np.int32)
+    fc = np.zeros(rank.size + 1, np.int32)
+    ng = C.c_int()
+    st = lib.ce_plan_groups(rank.size, rank.ctypes.data_as(_lib.I32P), J, nmax,
+                            fc.ctypes.data_as(_lib.I32P), C.byref(ng))
+    assert st == _lib.CE_OK
+    return [(int(fc[g]), int(fc[g + 1])) for g in range(ng.value)]
+
+
+def test_host_groups_match_oracle(lib):
+    """The library's super-blocks (Section 2.4, with the 64-row cap) equal the
+    oracle's on ragged and random rank vectors, bit for bit."""
+    rng = np.random.default_rng(11)
+    cases = [([16] * 8, 4, 64), ([16] * 7, 4, 64), ([40, 30, 20, 10, 5], 4, 64),
+             ([64, 64, 1, 0, 0], 4, 64), ([0, 0, 0], 8, 0), ([33] * 9, 8, 64)]
+    for _ in range(200):
+        M = int(rng.integers(1, 40))
+        J = int(rng.choice([1, 2, 4, 8]))
+        cases.append((list(rng.integers(0, 40, M)), J, int(rng.choice([0, 16, 64, 10 ** 6]))))
+    for rank, J, nmax in cases:
+        assert _groups_c(lib, rank, J, nmax) == oce._groups(list(rank), J, nmax), (rank, J, nmax)
+
+
+def test_host_groups_reject_bad_input(lib):
+    r = np.array([1, -1, 2], np.int32)
+    fc = np.zeros(4, np.int32)
+    ng = C.c_int()
+    assert lib.ce_plan_groups(3, r.ctypes.data_as(_lib.I32P), 4, 64, fc.ctypes.data_as(_lib.I32P),
+                              C.byref(ng)) == _lib.CE_ERR_INVALID_ARG
+    r[1] = 1
+    assert lib.ce_plan_groups(3, r.ctypes.data_as(_lib.I32P), 0, 64, fc.ctypes.data_as(_lib.I32P),
+                              C.byref(ng)) == _lib.CE_ERR_INVALID_ARG
