@@ -51,6 +51,26 @@ ce_status status_of(const CudaFail& f) {
   return f.e == cudaErrorMemoryAllocation ? CE_ERR_OOM : CE_ERR_CUDA;
 }
 
+// Status of the exception in flight (called from a catch block): no exception
+// crosses the C ABI.  Host allocation failures read as CE_ERR_OOM, a rejected
+// input found by a host routine as CE_ERR_INVALID_ARG.
+ce_status status_of_exception() {
+  try {
+    throw;
+  } catch (const CudaFail& f) {
+    return status_of(f);
+  } catch (const std::bad_alloc&) {
+    g_last_error = "host allocation failed";
+    return CE_ERR_OOM;
+  } catch (const std::exception& ex) {
+    g_last_error = ex.what();
+    return CE_ERR_INVALID_ARG;
+  } catch (...) {
+    g_last_error = "unknown host exception";
+    return CE_ERR_CUDA;
+  }
+}
+
 void init_pool_once() {
   static bool done = false;
   if (done) return;
@@ -582,8 +602,8 @@ ce_status ce_mlp_init(float* theta_dev, uint64_t seed, void* stream) {
   if (!theta_dev) return CE_ERR_INVALID_ARG;
   try {
     check(ce::mlp_init(theta_dev, seed, static_cast<cudaStream_t>(stream)), "mlp init");
-  } catch (const CudaFail& f) {
-    return status_of(f);
+  } catch (...) {
+    return status_of_exception();
   }
   return CE_OK;
 }
@@ -597,8 +617,8 @@ ce_status ce_mlp_grad(const float* X_dev, const float* t_dev, int ns, const floa
   try {
     part = static_cast<float*>(dalloc((size_t)ce::mlp_partial_blocks(ns) * ce::kMlpParams * 4, s));
     check(ce::mlp_grad(X_dev, t_dev, ns, theta_dev, part, grad_dev, s), "mlp grad");
-  } catch (const CudaFail& f) {
-    ret = status_of(f);
+  } catch (...) {
+    ret = status_of_exception();
   }
   dfree(part, s);
   return ret;
@@ -633,8 +653,8 @@ ce_status ce_mlp_train(const float* X_dev, const float* t_dev, int ns, float* th
       *loss_out = acc / ns;
       dfree(model, s);
     }
-  } catch (const CudaFail& f) {
-    ret = status_of(f);
+  } catch (...) {
+    ret = status_of_exception();
   }
   dfree(part, s);
   dfree(m, s);
@@ -647,8 +667,8 @@ ce_status ce_mlp_pack(const float* theta_dev, void* model_dev, void* stream) {
   if (!theta_dev || !model_dev) return CE_ERR_INVALID_ARG;
   try {
     check(ce::mlp_pack(theta_dev, model_dev, static_cast<cudaStream_t>(stream)), "mlp pack");
-  } catch (const CudaFail& f) {
-    return status_of(f);
+  } catch (...) {
+    return status_of_exception();
   }
   return CE_OK;
 }
@@ -657,8 +677,8 @@ ce_status ce_mlp_predict(const float* X_dev, int ns, const void* model_dev, floa
   if (!X_dev || !model_dev || !out_dev || ns < 0) return CE_ERR_INVALID_ARG;
   try {
     check(ce::mlp_predict(X_dev, ns, model_dev, out_dev, static_cast<cudaStream_t>(stream)), "mlp predict");
-  } catch (const CudaFail& f) {
-    return status_of(f);
+  } catch (...) {
+    return status_of_exception();
   }
   return CE_OK;
 }
@@ -853,8 +873,8 @@ ce_status ce_plan_groups(int M, const int32_t* rank, int J, int nmax, int32_t* f
     ce::coarsen_parents(P, J, &r, nmax, &fc, nullptr);
     std::copy(fc.begin(), fc.end(), first_child);
     *ngroups = static_cast<int>(fc.size()) - 1;
-  } catch (const std::bad_alloc&) {
-    return CE_ERR_OOM;
+  } catch (...) {
+    return status_of_exception();
   }
   return CE_OK;
 }
@@ -889,8 +909,8 @@ ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col, c
       for (char x : P.pair_close) c += x;
       *nclose = c;
     }
-  } catch (const std::bad_alloc&) {
-    return CE_ERR_OOM;
+  } catch (...) {
+    return status_of_exception();
   }
   return CE_OK;
 }
@@ -1196,13 +1216,8 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
         }
       }
     }
-  } catch (const CudaFail& f) {
-    ret = status_of(f);
-  } catch (const std::bad_alloc&) {
-    ret = CE_ERR_OOM;
-  } catch (const std::exception& ex) {
-    g_last_error = ex.what();
-    ret = CE_ERR_INVALID_ARG;
+  } catch (...) {
+    ret = status_of_exception();
   }
   if (ret != CE_OK) {
     dfree(pool, s);
@@ -1217,9 +1232,9 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
 
 ce_status csb_update_values(ce_csb* A, const double* val, void* stream) {
   if (!A || !val) return CE_ERR_INVALID_ARG;
-  if (!csr_symmetric(A->n, A->h_rowptr.data(), A->h_col.data(), val)) return CE_ERR_INVALID_ARG;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   try {
+    if (!csr_symmetric(A->n, A->h_rowptr.data(), A->h_col.data(), val)) return CE_ERR_INVALID_ARG;
     const size_t bytes = A->nnz * sizeof(double);
     char* h = stage_get(1, bytes);
     ce::parallel_for(16, 1, [&](int64_t b, int64_t e) {
@@ -1230,8 +1245,8 @@ ce_status csb_update_values(ce_csb* A, const double* val, void* stream) {
     });
     stage_upload(1, A->d_val, bytes, s);
     check(cudaStreamSynchronize(s), "csb_update_values sync");
-  } catch (const CudaFail& f) {
-    return status_of(f);
+  } catch (...) {
+    return status_of_exception();
   }
   return CE_OK;
 }
@@ -1361,8 +1376,8 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev, void*
       check(ce::launch_apply_bwd(es, st.dev, v, F->d_status, s), "apply bwd");
     }
     check(ce::launch_perm(F->d_perm, F->N, v0, z_dev, 0, s), "perm scatter");
-  } catch (const CudaFail& f) {
-    return status_of(f);
+  } catch (...) {
+    return status_of_exception();
   }
   return CE_OK;
 }
@@ -1432,8 +1447,8 @@ ce_status pcg_solve(const ce_csb* A, const ce_factor* F, const double* b_dev, do
       info->converged = conv ? 1 : 0;
     }
     if (!conv) ret = CE_ERR_NO_CONVERGENCE;
-  } catch (const CudaFail& f) {
-    if (ret == CE_OK) ret = status_of(f);
+  } catch (...) {
+    if (ret == CE_OK) ret = status_of_exception();
   }
   dfree(r, s);
   dfree(z, s);

@@ -401,5 +401,8 @@ extern "C" ce_status pcg_solve_batched(const ce_csb* A, const ce_factor* F, cons
     return f.e == cudaErrorMemoryAllocation ? CE_ERR_OOM : CE_ERR_CUDA;
   } catch (const std::bad_alloc&) {
     return CE_ERR_OOM;
+  } catch (const std::exception& ex) {
+    set_last_error(std::string("pcg_solve_batched: ") + ex.what());
+    return CE_ERR_INVALID_ARG;
   }
 }
