@@ -395,6 +395,25 @@ ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col,
                          int* ncolours, int64_t* npairs, int64_t* nclose);
 
 /*
+ * ce_plan_level1_deps -- host-only (no CUDA call): the waits of level 1's
+ * persistent row launch.  The rows of one colour are independent (the
+ * distance-2 colouring makes each colour an independent set in the sense of
+ * Section 2.3); row i waits for every row k of a lower colour with (i, k) in
+ * the squared pattern, i.e. within distance 2 in the block graph, which
+ * covers every row whose Schur update writes a pair that row i reads or
+ * writes.  Arguments as ce_plan_level1.
+ *   dep_ptr  host, M + 1 offsets (may be NULL)
+ *   dep_idx  host, cap entries (may be NULL): the rows k of row i are
+ *            dep_idx[dep_ptr[i] .. dep_ptr[i+1])
+ *   ndeps    total number of waits (may be NULL)
+ * CE_ERR_INVALID_ARG as ce_plan_level1, or when dep_idx is given with
+ * cap < *ndeps (call once with dep_idx = NULL to size it).
+ */
+ce_status ce_plan_level1_deps(int64_t n, const int64_t* rowptr, const int32_t* col,
+                              const int32_t* perm, int32_t B, int64_t* dep_ptr,
+                              int32_t* dep_idx, int64_t cap, int64_t* ndeps);
+
+/*
  * ce_plan_groups -- host-only (no CUDA call): the super-blocks that
  * ce_factorize forms from one level's blocks (Section 2.4).  Runs of J
  * consecutive blocks join; a run whose ranks add up to more than nmax rows is

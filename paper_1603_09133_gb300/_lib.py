@@ -89,6 +89,8 @@ SIGNATURES = {
     "csb_build": (C.c_int, [C.c_int64, I64P, I32P, DP, I32P, C.c_int32, PP]),
     "csb_build_batched": (C.c_int, [C.c_int, I64P, I64P, I32P, DP, I32P, I32P, PP]),
     "csb_update_values": (C.c_int, [P, DP, P]),
+    "ce_plan_level1_deps": (C.c_int, [C.c_int64, I64P, I32P, I32P, C.c_int32, I64P, I32P, C.c_int64,
+                                      I64P]),
     "ce_plan_groups": (C.c_int, [C.c_int, I32P, C.c_int, C.c_int, I32P, C.POINTER(C.c_int)]),
     "ce_factorize_batched": (C.c_int, [P, C.POINTER(ce_opts), PP, C.POINTER(ce_info)]),
     "ce_factorize": (C.c_int, [P, C.POINTER(ce_opts), PP, C.POINTER(ce_info)]),

@@ -879,8 +879,14 @@ ce_status ce_plan_groups(int M, const int32_t* rank, int J, int nmax, int32_t* f
   return CE_OK;
 }
 
-ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm,
-                         int32_t B, int32_t* colour, int* ncolours, int64_t* npairs, int64_t* nclose) {
+}  // extern "C"
+
+namespace {
+
+// Level-1 symbolic plan of host CSR + permutation, no CUDA call (the host
+// introspection entry points below); may throw std::bad_alloc.
+ce_status plan1_host(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, int32_t B,
+                     LevelPlan& P) {
   if (n <= 0 || !rowptr || !col || !perm || B <= 0 || n > INT32_MAX || rowptr[0] != 0)
     return CE_ERR_INVALID_ARG;
   std::vector<int32_t> iperm(n, -1);
@@ -898,9 +904,20 @@ ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col, c
   for (int b2 = 0; b2 <= M; ++b2) blkptr[b2] = std::min<int64_t>(n, (int64_t)b2 * B);
   for (int64_t r = 0; r < n; ++r) blk_of[r] = static_cast<int>(r / B);
   std::vector<std::pair<int, int>> pairs = block_pairs(rowptr, col, perm, iperm, blkptr, blk_of);
+  ce::plan_level(P, sizes, pairs, true);
+  return CE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm,
+                         int32_t B, int32_t* colour, int* ncolours, int64_t* npairs, int64_t* nclose) {
   try {
     LevelPlan P;
-    ce::plan_level(P, sizes, pairs, true);
+    const ce_status st = plan1_host(n, rowptr, col, perm, B, P);
+    if (st != CE_OK) return st;
     if (colour) std::copy(P.colour.begin(), P.colour.end(), colour);
     if (ncolours) *ncolours = P.ncolours;
     if (npairs) *npairs = static_cast<int64_t>(P.pair_i.size());
@@ -909,6 +926,23 @@ ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col, c
       for (char x : P.pair_close) c += x;
       *nclose = c;
     }
+  } catch (...) {
+    return status_of_exception();
+  }
+  return CE_OK;
+}
+
+ce_status ce_plan_level1_deps(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm,
+                              int32_t B, int64_t* dep_ptr, int32_t* dep_idx, int64_t cap, int64_t* ndeps) {
+  try {
+    LevelPlan P;
+    const ce_status st = plan1_host(n, rowptr, col, perm, B, P);
+    if (st != CE_OK) return st;
+    const int64_t total = P.dep_ptr[P.M];
+    if (ndeps) *ndeps = total;
+    if (dep_idx && cap < total) return CE_ERR_INVALID_ARG;
+    if (dep_ptr) std::copy(P.dep_ptr.begin(), P.dep_ptr.end(), dep_ptr);
+    if (dep_idx) std::copy(P.dep_idx.begin(), P.dep_idx.end(), dep_idx);
   } catch (...) {
     return status_of_exception();
   }

@@ -158,3 +158,61 @@ def test_host_groups_reject_bad_input(lib):
     r[1] = 1
     assert lib.ce_plan_groups(3, r.ctypes.data_as(_lib.I32P), 0, 64, fc.ctypes.data_as(_lib.I32P),
                               C.byref(ng)) == _lib.CE_ERR_INVALID_ARG
+
+
+def _deps_c(lib, A, perm, B):
+    n, rp, ci, v, pm = _csr_args(A, perm)
+    M = (n + B - 1) // B
+    ptr = np.zeros(M + 1, np.int64)
+    nd = C.c_int64()
+    args = (n, rp.ctypes.data_as(_lib.I64P), ci.ctypes.data_as(_lib.I32P), pm.ctypes.data_as(_lib.I32P), B)
+    assert lib.ce_plan_level1_deps(*args, ptr.ctypes.data_as(_lib.I64P), None, 0, C.byref(nd)) == _lib.CE_OK
+    idx = np.zeros(max(nd.value, 1), np.int32)
+    if nd.value:
+        assert lib.ce_plan_level1_deps(*args, None, idx.ctypes.data_as(_lib.I32P), nd.value - 1,
+                                       None) == _lib.CE_ERR_INVALID_ARG
+    assert lib.ce_plan_level1_deps(*args, ptr.ctypes.data_as(_lib.I64P), idx.ctypes.data_as(_lib.I32P),
+                                   idx.size, C.byref(nd)) == _lib.CE_OK
+    return ptr, idx[:nd.value]
+
+
+def _random_spd_pattern(n, seed):
+    rng = np.random.default_rng(seed)
+    R = sp.random(n, n, density=3.0 / n, random_state=rng, format="csr")
+    A = (R + R.T + sp.identity(n)).tocsr()
+    A.data[:] = 1.0
+    return A, rng.permutation(n)
+
+
+@pytest.mark.parametrize("case", ["poisson2d_64_B16", "poisson2d_512_B32", "poisson3d_64_B64", "random"])
+def test_host_row_waits_cover_every_conflict(lib, case):
+    """Level 1's persistent launch is race-free: any two rows whose work can
+    touch a common block pair (distance <= 2 in the block graph: a shared
+    Schur target, or one row's target inside the other's row) have different
+    colours, and the later colour waits for the earlier one; no other waits."""
+    if case == "random":
+        A, perm = _random_spd_pattern(3000, 4)
+        B = 16
+    else:
+        w = wl.make_workload(case)
+        A, perm, B = w.A, w.perm, w.B
+    n = A.shape[0]
+    M = (n + B - 1) // B
+    col, _, _, _ = _plan(lib, A, perm, B)
+    ptr, idx = _deps_c(lib, A, perm, B)
+    # block graph of P A P^T (with the diagonal) and its square, brute force
+    iperm = np.empty(n, np.int64)
+    iperm[np.asarray(perm)] = np.arange(n)
+    Ac = sp.coo_matrix(A)
+    G = sp.csr_matrix((np.ones(Ac.nnz), (iperm[Ac.row] // B, iperm[Ac.col] // B)), shape=(M, M))
+    G = ((G + sp.identity(M)) > 0).astype(np.int64)
+    G2 = sp.coo_matrix((G @ G) > 0)
+    conflicts = {(int(i), int(k)) for i, k in zip(G2.row, G2.col) if i != k}
+    assert all(col[i] != col[k] for i, k in conflicts)
+    want = [set() for _ in range(M)]
+    for i, k in conflicts:
+        if col[k] < col[i]:
+            want[i].add(k)
+    got = [set(idx[ptr[i]:ptr[i + 1]].tolist()) for i in range(M)]
+    assert all(len(idx[ptr[i]:ptr[i + 1]]) == len(got[i]) for i in range(M))   # no duplicates
+    assert got == want
