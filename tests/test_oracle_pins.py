@@ -320,17 +320,40 @@ def test_order_invariance_within_colour():
 # --------------------------------------------------------------------------
 # trends of the paper's tables (qualitative: other Krylov method and B)
 # --------------------------------------------------------------------------
+def _factor_words(F):
+    # stored factor: L (coarse triangle, every L-hat and W) and Q (every U_i)
+    return F.nnz_L + sum(st.n * st.n for lev in F.levels for st in lev.steps)
+
+
 def test_direct_solve_error_falls_with_eps():
-    # Table err: relative accuracy eta of the direct CE solve falls with eps
+    # Table err (Section 4, CE(eps) as a direct solver): the accuracy eta of the
+    # direct solve falls as eps falls while the memory the factor needs grows
     A, perm, B = _problem("p2", 64, (4, 4))
     b = wl.rhs(A.shape[0], 0)
     x_ref = sla.solve(A.toarray(), b, assume_a="pos")
-    etas = []
+    etas, words = [], []
     for eps in (1e-1, 1e-2, 1e-3, 1e-4):
         F = ce.factorize(A, perm, B, eps, 2, 4)
         x = ce.apply(F, b)
         etas.append(np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref))
+        words.append(_factor_words(F))
     assert all(etas[j + 1] < etas[j] for j in range(3)), etas
+    assert all(words[j + 1] > words[j] for j in range(3)), words
+
+
+def test_fixed_rank_is_no_direct_solver():
+    # Section 4: CE(r) with r = B/2 is not accurate enough to solve directly,
+    # CE(eps) with a small eps is
+    A, perm, B = _problem("p2", 64, (4, 4))
+    b = wl.rhs(A.shape[0], 0)
+    x_ref = sla.solve(A.toarray(), b, assume_a="pos")
+
+    def eta(F):
+        return np.linalg.norm(ce.apply(F, b) - x_ref) / np.linalg.norm(x_ref)
+
+    e_r = eta(ce.factorize(A, perm, B, 0.0, 2, 4, tol_mode="fixed", rank=B // 2))
+    e_eps = eta(ce.factorize(A, perm, B, 1e-6, 2, 4))
+    assert e_r > 1e-3 > 1e-5 > e_eps, (e_r, e_eps)
 
 
 def test_pcg_iterations_flat_in_N():
