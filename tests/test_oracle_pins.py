@@ -407,3 +407,29 @@ def test_capped_coarsening_stays_exact():
     b = wl.rhs(A.shape[0], 4)
     x_ref = sla.cho_solve(sla.cho_factor(A.toarray()), b)
     assert np.linalg.norm(ce.apply(F, b) - x_ref) / np.linalg.norm(x_ref) < 1e-12
+
+
+@pytest.mark.slow
+def test_paper_experiment_iteration_trends():
+    """Table num_it on the paper's own problem (Section 4: -div(k grad u) = 1 on
+    [0, 1]^3, k = diag(x_d^2 + 0.5), N = 8192 and 16384 on 16x16x32 and
+    16x32x32 grids), with PCG to 1e-10 in place of MINRES.  B = 8 (2^3 boxes)
+    so that the table's CE(r), r = 4, is r = B/2; J = 8, 3 levels.  The paper's
+    trends: plain CG needs many more iterations and more as N grows; CE(1e-3)
+    needs a handful (4-6 there), flat in N; CE(4) needs more than CE(1e-3) and
+    grows mildly (23 -> 25 there)."""
+    its = {"cg": [], "eps": [], "r": []}
+    for shape in [(16, 16, 32), (16, 32, 32)]:
+        A = wl.diffusion3d_tensor(*shape)
+        perm = wl.box_perm(shape, (2, 2, 2))
+        b = np.ones(A.shape[0])
+        its["cg"].append(ce.pcg(A, None, b, 1e-10, 5000, precond=lambda r: r).iters)
+        F = ce.factorize(A, perm, 8, 1e-3, 3, 8)
+        its["eps"].append(ce.pcg(A, F, b, 1e-10, 500).iters)
+        F = ce.factorize(A, perm, 8, 0.0, 3, 8, tol_mode="fixed", rank=4)
+        its["r"].append(ce.pcg(A, F, b, 1e-10, 500).iters)
+    cg, e, r = its["cg"], its["eps"], its["r"]
+    assert cg[1] > cg[0] > 5 * max(r), its
+    assert max(e) <= 6 and abs(e[1] - e[0]) <= 1, its
+    assert all(r[j] > e[j] for j in range(2)), its
+    assert r[0] <= r[1] <= 1.5 * r[0], its

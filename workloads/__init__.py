@@ -9,6 +9,7 @@ from .grids import (  # noqa: F401
     poisson2d,
     poisson3d,
     diffusion2d,
+    diffusion3d_tensor,
     grf2d,
     box_perm,
     rhs,

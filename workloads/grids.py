@@ -132,6 +132,36 @@ def diffusion2d(k: np.ndarray) -> sp.csr_matrix:
     return _stencil_csr((nx, ny), coef)
 
 
+def diffusion3d_tensor(nx: int, ny: int, nz: int) -> sp.csr_matrix:
+    """7-point discretisation of -div(k grad u) on [0, 1]^3, u = 0 on the
+    boundary, with the diagonal tensor k(x) = diag(x_1^2 + 0.5, x_2^2 + 0.5,
+    x_3^2 + 0.5) of the paper's experiments (Section 4).
+
+    ``n_d`` equidistant interior nodes per axis, spacing h_d = 1 / (n_d + 1);
+    the face between two nodes along axis d carries k_d at the face midpoint
+    over h_d^2 (so the operator is the usual second difference, scaled).
+    """
+    shape = (nx, ny, nz)
+    h = [1.0 / (n + 1) for n in shape]
+
+    def coef(ax):
+        if isinstance(ax, tuple):
+            _, a, side = ax
+            xf = 0.5 * h[a] if side == 0 else 1.0 - 0.5 * h[a]
+            out = np.empty(tuple(1 if d == a else shape[d] for d in range(3)))
+            out[...] = (xf * xf + 0.5) / (h[a] * h[a])
+            return out
+        xf = (np.arange(1, shape[ax]) + 0.5) * h[ax]      # faces between nodes i and i+1
+        c = (xf * xf + 0.5) / (h[ax] * h[ax])
+        sh = [1, 1, 1]
+        sh[ax] = shape[ax] - 1
+        full = [shape[0], shape[1], shape[2]]
+        full[ax] = shape[ax] - 1
+        return np.broadcast_to(c.reshape(sh), full).copy()
+
+    return _stencil_csr(shape, coef)
+
+
 def grf2d(n: int, seed: int, corr_frac: float = 1.0 / 32.0, contrast: float = 1.0e4):
     """Coefficient field k = exp(s * g) on an n x n grid.
 
