@@ -4,6 +4,7 @@ With maxit below what the preconditioner needs, pcg_solve returns
 CE_ERR_NO_CONVERGENCE with converged = 0, iters = maxit and the residual of
 the last iterate; that iterate is the oracle's PCG iterate after the same
 number of steps (x_0 = 0, the same M), within the FP64 apply tolerance.
+(The file sorts after the other GPU tests so that a failure here stops none.)
 """
 import ctypes as C
 
