@@ -135,7 +135,8 @@ typedef struct {
 } ce_pcg_info;
 
 /* Defaults: tol 1e-4, CE_TOL_REL, levels 4, J 4, FP64, colouring on,
- * CE_RANK_SVD, oversample 8, seed 0. */
+ * CE_RANK_SVD, oversample 8, seed 0, row_shape -1 (autotuned, else a
+ * heuristic), rank 16. */
 void ce_opts_default(ce_opts* o);
 
 /*
@@ -150,7 +151,8 @@ void ce_opts_default(ce_opts* o);
  *            P A P^T; the last block is shorter when B does not divide n
  *   out      receives the handle
  * Copies the matrix to the device (CSR for the CG products and the block
- * pattern of level 1) and plans level 1 on the host (block graph, A^2
+ * pattern of level 1), keeps a host copy of the pattern (for
+ * csb_update_values) and plans level 1 on the host (block graph, A^2
  * pattern, distance-2 colouring).  CE_ERR_INVALID_ARG if perm is not a
  * permutation, an index is out of range or A is not symmetric.
  */
@@ -212,8 +214,11 @@ ce_status ce_factorize_batched(const ce_csb* A, const ce_opts* o,
  * F_i by an SVD truncated at tau_i, the row/column transform by U_i and the
  * Cholesky elimination of the non-basis sub-row S_i, eq. sm_L), each followed
  * by joining J consecutive blocks into super-blocks (eq. bsp); then the dense
- * Cholesky of the remainder A_K.  Blocks of one colour of a distance-2
- * colouring are processed by one launch.
+ * Cholesky of the remainder A_K.  The block rows of a level run in one
+ * persistent launch in the colour-major order of a distance-2 colouring: a
+ * row starts once every row of a lower colour within distance 2 of it has
+ * finished (ce_plan_level1_deps lists these waits for level 1), which gives
+ * the same arithmetic as one launch per colour.
  *   A     handle from csb_build (not modified)
  *   o     options (NULL = defaults)
  *   out   receives the factor
