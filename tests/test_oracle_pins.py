@@ -433,3 +433,22 @@ def test_paper_experiment_iteration_trends():
     assert max(e) <= 6 and abs(e[1] - e[0]) <= 1, its
     assert all(r[j] > e[j] for j in range(2)), its
     assert r[0] <= r[1] <= 1.5 * r[0], its
+
+
+def test_pcg_is_the_library_cg():
+    # the oracle's PCG (Section 4 uses a Krylov method around M; this build
+    # uses CG) against SciPy's CG with the same preconditioner: the same
+    # recurrence, so the same iterates after every number of steps
+    import scipy.sparse.linalg as spla
+    w = wl.make_workload("poisson2d_64_B16")
+    F = ce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J)
+    N = w.A.shape[0]
+    Mop = spla.LinearOperator((N, N), matvec=lambda v: ce.apply(F, v))
+    for k in (1, 2, 3):
+        xs, _ = spla.cg(w.A, w.b, x0=np.zeros(N), rtol=1e-14, atol=0.0, maxiter=k, M=Mop)
+        res = ce.pcg(w.A, F, w.b, 1e-14, k)
+        assert np.linalg.norm(xs - res.x) <= 1e-12 * np.linalg.norm(res.x), k
+    for k in (1, 5, 20):
+        xs, _ = spla.cg(w.A, w.b, x0=np.zeros(N), rtol=1e-14, atol=0.0, maxiter=k)
+        res = ce.pcg(w.A, None, w.b, 1e-14, k, precond=lambda r: r)
+        assert np.linalg.norm(xs - res.x) <= 1e-12 * np.linalg.norm(res.x), k
