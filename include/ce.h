@@ -264,6 +264,10 @@ ce_status ce_autotune(ce_csb* A, const ce_opts* o, double* level_ms);
  * Section 2.5).  r_dev and z_dev are device arrays of n doubles in the
  * original ordering of A; they may alias.  All work is queued on `stream`
  * (no host synchronization), so the call can be captured in a CUDA graph.
+ * The apply's scheduling state (queue counters, per-row flags, an epoch)
+ * lives in the factor: calls on one factor must not overlap on the GPU
+ * (issue them on one stream, or serialize them); different factors are
+ * independent.
  */
 ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev,
                    void* stream);
@@ -274,7 +278,8 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev,
  * x0 = 0; stops when ||r||_2 <= rtol ||b||_2 or after maxit iterations.
  *   b_dev, x_dev  device arrays of n doubles (original ordering)
  *   info          optional
- * Reads the residual norm to the host once per iteration.
+ * Reads the residual norm to the host once per iteration.  Applies F, so
+ * it must not overlap other work on F (see ce_apply).
  * CE_ERR_NO_CONVERGENCE if maxit is reached (x_dev holds the last iterate).
  */
 ce_status pcg_solve(const ce_csb* A, const ce_factor* F, const double* b_dev,
