@@ -263,7 +263,9 @@ ce_status ce_autotune(ce_csb* A, const ce_opts* o, double* level_ms);
  * ce_apply -- z = M^{-1} r = Q^T L^{-T} L^{-1} Q r (solve proposition of
  * Section 2.5).  r_dev and z_dev are device arrays of n doubles in the
  * original ordering of A; they may alias.  All work is queued on `stream`
- * (no host synchronization), so the call can be captured in a CUDA graph.
+ * with no host synchronization (on a batch handle pcg_solve_batched replays
+ * it from a captured CUDA graph; a single system's coarse solve is a
+ * cooperative launch).
  * The apply's scheduling state (queue counters, per-row flags, an epoch)
  * lives in the factor: calls on one factor must not overlap on the GPU
  * (issue them on one stream, or serialize them); different factors are
