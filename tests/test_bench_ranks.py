@@ -56,3 +56,31 @@ def test_single_rank_and_reference_arm_rank(capsys):
         gpus = 2
     bench.run_reference(Args(), rank=1)           # a non-zero rank does no work
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_json_line(capsys):
+    """bench.py --impl reference on rank 0: one JSON line timing the oracle on
+    the host, with the keys of the bench contract (the line's own value in
+    cpu_baseline and e2e, no host<->device bytes)."""
+    import json
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class Args:
+        workload = "poisson2d_64_B16"
+        steps = 1
+        warmup = 0
+        gpus = 1
+    bench.run_reference(Args(), rank=0)
+    lines = [ln for ln in capsys.readouterr().out.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    out = json.loads(lines[0])
+    for key in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+                "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert key in out, key
+    assert out["impl"] == "reference" and out["higher_is_better"] is False
+    assert out["value"] > 0 and out["config"]["workload"] == "poisson2d_64_B16"
+    cb = out["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["sample"] and cb["value"] == out["value"]
+    assert out["e2e"] == {"value": out["value"], "unit": out["unit"], "h2d_bytes_per_step": 0,
+                          "d2h_bytes_per_step": 0}
