@@ -1,5 +1,5 @@
 """Pins of the oracle's CE(r), the fixed-rank strategy of the Section 2.2
-remark (r_i = r directions kept per block row, typically r = B/2).
+remark: r_i = r directions kept per block row, r = B/2 the usual choice.
 
 * r at least the block size keeps every direction that is not rounding noise:
   CE reduces to exact block Cholesky (eq. bl_chol), so M = A and the solve is
