@@ -426,6 +426,25 @@ ce_status ce_plan_level1_deps(int64_t n, const int64_t* rowptr, const int32_t* c
                               int32_t* dep_idx, int64_t cap, int64_t* ndeps);
 
 /*
+ * ce_plan_next_level -- host-only (no CUDA call): the symbolic plan of level
+ * 2 that ce_factorize derives from level 1 and its ranks (Section 2.4, eq.
+ * bsp): super-blocks as ce_plan_groups forms them, sizes = sums of the
+ * children's ranks, a pair of super-blocks kept when some pair of the level-1
+ * squared pattern with non-empty ranks on both sides lies inside it, and the
+ * distance-2 colouring of that pattern.  Arguments as ce_plan_level1, plus
+ *   rank         host, ceil(n/B) entries, 0 <= r_i <= n_i (level-1 ranks)
+ *   J, nmax      as ce_plan_groups (ce_factorize: nmax = 64)
+ *   next_n       host, room for ceil(n/B) entries (may be NULL): sizes
+ *   next_colour  host, room for ceil(n/B) entries (may be NULL)
+ *   next_M       number of level-2 blocks
+ *   next_nclose  pairs (I <= K) of the level-2 block pattern (may be NULL)
+ */
+ce_status ce_plan_next_level(int64_t n, const int64_t* rowptr, const int32_t* col,
+                             const int32_t* perm, int32_t B, const int32_t* rank, int J,
+                             int nmax, int32_t* next_n, int32_t* next_colour, int* next_M,
+                             int64_t* next_nclose);
+
+/*
  * ce_plan_groups -- host-only (no CUDA call): the super-blocks that
  * ce_factorize forms from one level's blocks (Section 2.4).  Runs of J
  * consecutive blocks join; a run whose ranks add up to more than nmax rows is

@@ -949,6 +949,34 @@ ce_status ce_plan_level1_deps(int64_t n, const int64_t* rowptr, const int32_t* c
   return CE_OK;
 }
 
+ce_status ce_plan_next_level(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm,
+                             int32_t B, const int32_t* rank, int J, int nmax, int32_t* next_n,
+                             int32_t* next_colour, int* next_M, int64_t* next_nclose) {
+  if (!rank || J < 1 || nmax < 0 || !next_M) return CE_ERR_INVALID_ARG;
+  try {
+    LevelPlan P;
+    const ce_status st = plan1_host(n, rowptr, col, perm, B, P);
+    if (st != CE_OK) return st;
+    std::vector<int> r(rank, rank + P.M);
+    for (int i = 0; i < P.M; ++i)
+      if (r[i] < 0 || r[i] > P.n[i]) return CE_ERR_INVALID_ARG;
+    const ce::NextLevel nx = ce::coarsen(P, r, J, nmax);
+    LevelPlan P2;
+    ce::plan_level(P2, nx.n, nx.pairs, true);
+    *next_M = P2.M;
+    if (next_n) std::copy(nx.n.begin(), nx.n.end(), next_n);
+    if (next_colour) std::copy(P2.colour.begin(), P2.colour.end(), next_colour);
+    if (next_nclose) {
+      int64_t c = 0;
+      for (char x : P2.pair_close) c += x;
+      *next_nclose = c;
+    }
+  } catch (...) {
+    return status_of_exception();
+  }
+  return CE_OK;
+}
+
 int csb_blocks(const ce_csb* A) { return A ? A->plan1->M : 0; }
 
 ce_status csb_get_colours(const ce_csb* A, int32_t* colour, int* ncolours) {

@@ -216,3 +216,80 @@ def test_host_row_waits_cover_every_conflict(lib, case):
     got = [set(idx[ptr[i]:ptr[i + 1]].tolist()) for i in range(M)]
     assert all(len(idx[ptr[i]:ptr[i + 1]]) == len(got[i]) for i in range(M))   # no duplicates
     assert got == want
+
+
+def _next_level_c(lib, A, perm, B, rank, J, nmax):
+    n, rp, ci, v, pm = _csr_args(A, perm)
+    M = (n + B - 1) // B
+    r = np.ascontiguousarray(rank, np.int32)
+    nn = np.zeros(M, np.int32)
+    col = np.zeros(M, np.int32)
+    nM = C.c_int()
+    ncl = C.c_int64()
+    st = lib.ce_plan_next_level(n, rp.ctypes.data_as(_lib.I64P), ci.ctypes.data_as(_lib.I32P),
+                                pm.ctypes.data_as(_lib.I32P), B, r.ctypes.data_as(_lib.I32P), J, nmax,
+                                nn.ctypes.data_as(_lib.I32P), col.ctypes.data_as(_lib.I32P), C.byref(nM),
+                                C.byref(ncl))
+    assert st == _lib.CE_OK
+    return nn[:nM.value], col[:nM.value], ncl.value
+
+
+@pytest.mark.parametrize("kind,n,box,tol,J", [("p2", 64, (4, 4), 1e-3, 4), ("p2", 128, (8, 4), 1e-4, 4),
+                                              ("p3", 16, (4, 4, 4), 1e-4, 8), ("grf", 64, (4, 4), 1e-4, 4)])
+def test_host_next_level_matches_oracle(lib, kind, n, box, tol, J):
+    """Level 2 as the library plans it from level 1 and the oracle's level-1
+    ranks (super-blocks capped at 64 rows, sizes, block pattern, colouring)
+    equals the oracle's own level 2, bit for bit."""
+    if kind == "p3":
+        A, perm = wl.poisson3d(n), wl.box_perm((n, n, n), box)
+    elif kind == "grf":
+        A, perm = wl.diffusion2d(wl.grf2d(n, 3)), wl.box_perm((n, n), box)
+    else:
+        A, perm = wl.poisson2d(n), wl.box_perm((n, n), box)
+    B = int(np.prod(box))
+    F = oce.factorize(A, perm, B, tol, 2, J, nmax=64)
+    lev1, lev2 = F.levels
+    nn, col, ncl = _next_level_c(lib, A, perm, B, lev1.ranks, J, 64)
+    assert list(nn) == list(lev2.sizes)
+    assert list(col) == list(lev2.colour)
+    assert ncl == len(lev2.pairs)
+
+
+def test_host_next_level_rule_on_random_ranks(lib):
+    """The coarsening rule restated by brute force on random ranks: sizes are
+    the children's rank sums; a super-block pair exists when a pair of the
+    level-1 squared pattern with non-zero ranks on both sides lies inside it,
+    and every super-block (an empty one too) keeps its diagonal."""
+    rng = np.random.default_rng(5)
+    A, perm = wl.poisson2d(64), wl.box_perm((64, 64), (4, 4))
+    B, J = 16, 4
+    S, sizes = oce.initial_blocks(A, perm, B)
+    M = len(sizes)
+    nbr = oce._block_graph(S, M)
+    sq = set()
+    for j in range(M):
+        for a in nbr[j]:
+            for b in nbr[j]:
+                if a <= b:
+                    sq.add((a, b))
+    for trial in range(5):
+        rank = rng.integers(0, B + 1, M)
+        rank[rng.random(M) < 0.2] = 0
+        for nmax in (64, 10 ** 6):
+            groups = oce._groups(list(rank), J, nmax)
+            parent = np.empty(M, int)
+            for g, (a, b) in enumerate(groups):
+                parent[a:b] = g
+            want_n = [int(rank[a:b].sum()) for a, b in groups]
+            pairs = {(parent[a], parent[b]) for a, b in sq if rank[a] > 0 and rank[b] > 0}
+            pairs |= {(g, g) for g in range(len(groups))}
+            nn, col, ncl = _next_level_c(lib, A, perm, B, rank, J, nmax)
+            assert list(nn) == want_n
+            assert ncl == len(pairs)
+            g_nbr = [set() for _ in groups]
+            for a, b in pairs:
+                g_nbr[a].add(b)
+                g_nbr[b].add(a)
+            for i in range(len(groups)):
+                g_nbr[i].add(i)
+            assert list(col) == oce.distance2_colouring(g_nbr)
