@@ -10,7 +10,9 @@
 //      = R^T R, so F_i and R^T share their left singular vectors.
 //   B. one-sided (Hestenes) Jacobi on the columns of R: R V = U' S gives
 //      U_i = V and sigma = S (descending); half a warp per column pair, so all
-//      pairs of a round-robin round run at once; r_i = #{sigma_k > tau_i}.
+//      pairs of a round-robin round run at once; r_i = #{sigma_k > tau_i},
+//      tau_i from the tolerance (CE(eps)) or just below sigma_r (CE(r), the
+//      fixed-rank strategy of the Section 2.2 remark).
 //   C. transform and elimination (eq. q, eq. sm_L): T = U^T D U, Cholesky of
 //      the non-basis block T_nn = L_hat L_hat^T, L_hat^{-1} formed once so every
 //      W = L_hat^{-1} S is a GEMM; close rows <- U^T C (kept rows minus the
