@@ -45,3 +45,48 @@ def test_paper_problem_anisotropic_grid_and_spd():
         h = 1.0 / (n + 1)
         interior &= (xd > 1.5 * h) & (xd < 1 - 1.5 * h)
     assert np.abs(rs[interior]).max() < 1e-9 * np.abs(rs).max()
+
+
+def test_constant_coefficient_diffusion_is_poisson():
+    # with k == 1 every face (harmonic mean of 1 and 1) carries 1: the 5-point
+    # Laplacian with Dirichlet faces, entry for entry; k scales the operator
+    assert abs(wl.diffusion2d(np.ones((12, 9))) - wl.poisson2d(12, 9)).max() == 0.0
+    k = np.random.default_rng(0).uniform(0.5, 2.0, (10, 10))
+    assert abs(wl.diffusion2d(3.0 * k) - 3.0 * wl.diffusion2d(k)).max() < 1e-12
+
+
+def test_grf_contrast_and_correlation_length():
+    """k = exp(s g): max k / min k is 1e4 exactly, and the normalised
+    autocorrelation of log k at one correlation length (n/32 grid steps) is
+    that of the squared-exponential covariance, exp(-1/2)."""
+    n = 256
+    k = wl.grf2d(n, seed=11)
+    assert abs(k.max() / k.min() / 1.0e4 - 1) < 1e-12
+    g = np.log(k)
+    g = g - g.mean()
+    lag = n // 32
+    rho_x = (g[:-lag, :] * g[lag:, :]).mean() / (g * g).mean()
+    rho_y = (g[:, :-lag] * g[:, lag:]).mean() / (g * g).mean()
+    assert abs(rho_x - np.exp(-0.5)) < 0.1 and abs(rho_y - np.exp(-0.5)) < 0.1, (rho_x, rho_y)
+    assert not np.array_equal(k, wl.grf2d(n, seed=12))
+
+
+def test_box_perm_boxes_and_morton_siblings():
+    """P: a permutation; block b of P A P^T is one geometric box of 8 x 4
+    points; the 4 boxes of every run of J = 4 consecutive blocks form a 2 x 2
+    square of boxes (Morton siblings, what joining J blocks relies on)."""
+    nx, ny, bx, by = 64, 32, 8, 4
+    p = wl.box_perm((nx, ny), (bx, by))
+    assert np.array_equal(np.sort(p), np.arange(nx * ny))
+    x, y = p % nx, p // nx
+    B = bx * by
+    boxes = []
+    for b in range(nx * ny // B):
+        xs, ys = x[b * B:(b + 1) * B], y[b * B:(b + 1) * B]
+        assert xs.max() - xs.min() == bx - 1 and ys.max() - ys.min() == by - 1
+        assert xs.min() % bx == 0 and ys.min() % by == 0
+        boxes.append((xs.min() // bx, ys.min() // by))
+    for g in range(0, len(boxes), 4):
+        q = np.array(boxes[g:g + 4])
+        assert q[:, 0].max() - q[:, 0].min() == 1 and q[:, 1].max() - q[:, 1].min() == 1
+        assert q[:, 0].min() % 2 == 0 and q[:, 1].min() % 2 == 0
