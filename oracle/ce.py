@@ -24,6 +24,27 @@ as the library steps:
                         of ``apply``.
 * ``pcg``            -- preconditioned conjugate gradients with M = Q^T L L^T Q.
 
+Pins (each function checked against something other than itself; the tests
+named are under tests/):
+
+* ``factorize`` / ``_one_level`` / ``apply`` / ``multiply``: tol = 0 (and
+  CE(r) with r above every block size) is exact block Cholesky -- M = A and the
+  solve is the dense Cholesky solve (test_oracle_pins, test_oracle_fixed_rank);
+  levels = 0 is dense Cholesky; eps >= 1 and CE(0) equal an independently
+  written block IC(0); the structural worked example of Section 2 (golden
+  fixture); per-step orthogonality, rank rule and positive pivots; invariance
+  under rotations inside the basis / non-basis subspaces and under reordering
+  inside a colour; the trends of Tables err and num_it (the latter on the
+  paper's own 3D problem).
+* ``distance2_colouring`` / ``bfs_order``: validity of the colouring
+  (test_oracle_pins); equality with the library's planner (test_library_cpu).
+* ``_groups`` / ``_coarsen``: the grouping rule worked by hand, the capped
+  coarsening exact at tol = 0, and the coarsening rule restated by brute force
+  (test_library_cpu).
+* ``block_features``: against their definitions on the oracle's own steps
+  (test_mlp_pins).
+* ``pcg``: its iterates equal SciPy's CG with the same preconditioner.
+
 Readings of points the paper leaves open:
 
 * Rank rule (CE(eps), Section 2.2 remark): the norm of E_i is the spectral
