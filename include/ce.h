@@ -445,6 +445,23 @@ ce_status ce_plan_next_level(int64_t n, const int64_t* rowptr, const int32_t* co
                              int64_t* next_nclose);
 
 /*
+ * ce_plan_level1_work -- host-only (no CUDA call): the algorithmic work of
+ * level 1's row kernel, as ce_info.level_flops / level_bytes count it, for
+ * given level-1 ranks.  Per block row (n, r, m = n - r, far columns mF and
+ * close columns Wc as they stand when the row runs: rows of an earlier colour
+ * keep only their r columns): 2 mF n^2 (R of F^T) + 12 n^3 (SVD of R, when
+ * mF > 0) + 4 n^3 + 2 n^2 Wc + 2 n r mF (transforms) + m^3/3 + m^2 (r + Wc)
+ * (Cholesky, TRSM) + m ((r + Wc)^2 + r^2 + sum w^2) (Schur) flops, and the
+ * bytes of the pairs read and written and of the factor written.
+ *   rank   host, ceil(n/B) entries, 0 <= r_i <= n_i
+ *   esize  4 (FP32 form) or 8 (FP64 form)
+ *   flops, bytes  receive the totals
+ */
+ce_status ce_plan_level1_work(int64_t n, const int64_t* rowptr, const int32_t* col,
+                              const int32_t* perm, int32_t B, const int32_t* rank,
+                              int esize, double* flops, double* bytes);
+
+/*
  * ce_plan_groups -- host-only (no CUDA call): the super-blocks that
  * ce_factorize forms from one level's blocks (Section 2.4).  Runs of J
  * consecutive blocks join; a run whose ranks add up to more than nmax rows is

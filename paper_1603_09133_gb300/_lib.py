@@ -93,6 +93,7 @@ SIGNATURES = {
                                       I64P]),
     "ce_plan_next_level": (C.c_int, [C.c_int64, I64P, I32P, I32P, C.c_int32, I32P, C.c_int, C.c_int, I32P,
                                      I32P, C.POINTER(C.c_int), I64P]),
+    "ce_plan_level1_work": (C.c_int, [C.c_int64, I64P, I32P, I32P, C.c_int32, I32P, C.c_int, DP, DP]),
     "ce_plan_groups": (C.c_int, [C.c_int, I32P, C.c_int, C.c_int, I32P, C.POINTER(C.c_int)]),
     "ce_factorize_batched": (C.c_int, [P, C.POINTER(ce_opts), PP, C.POINTER(ce_info)]),
     "ce_factorize": (C.c_int, [P, C.POINTER(ce_opts), PP, C.POINTER(ce_info)]),

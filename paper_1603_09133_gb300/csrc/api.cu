@@ -977,6 +977,23 @@ ce_status ce_plan_next_level(int64_t n, const int64_t* rowptr, const int32_t* co
   return CE_OK;
 }
 
+ce_status ce_plan_level1_work(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm,
+                              int32_t B, const int32_t* rank, int esize, double* flops, double* bytes) {
+  if (!rank || (esize != 4 && esize != 8) || !flops || !bytes) return CE_ERR_INVALID_ARG;
+  try {
+    LevelPlan P;
+    const ce_status st = plan1_host(n, rowptr, col, perm, B, P);
+    if (st != CE_OK) return st;
+    std::vector<int> r(rank, rank + P.M);
+    for (int i = 0; i < P.M; ++i)
+      if (r[i] < 0 || r[i] > P.n[i]) return CE_ERR_INVALID_ARG;
+    level_work(P, r, esize, *flops, *bytes);
+  } catch (...) {
+    return status_of_exception();
+  }
+  return CE_OK;
+}
+
 int csb_blocks(const ce_csb* A) { return A ? A->plan1->M : 0; }
 
 ce_status csb_get_colours(const ce_csb* A, int32_t* colour, int* ncolours) {

@@ -293,3 +293,50 @@ def test_host_next_level_rule_on_random_ranks(lib):
             for i in range(len(groups)):
                 g_nbr[i].add(i)
             assert list(col) == oce.distance2_colouring(g_nbr)
+
+
+def _work_formula(F, es):
+    """Algorithmic work of level 1 from the oracle's own steps: far blocks as
+    filled when the row ran, close widths from the W blocks it produced."""
+    lev = F.levels[0]
+    fl = by = 0.0
+    for st in lev.steps:
+        i, n, r = st.i, st.n, st.r
+        m = n - r
+
+        def wid(k):
+            return lev.ranks[k] if lev.colour[k] < lev.colour[i] else lev.sizes[k]
+        mF = sum(wid(k) for k in st.far)
+        ws = [W.shape[1] for t, W in st.targets if t != i]
+        Wc, W2 = sum(ws), sum(w * w for w in ws)
+        fl += (2 * mF * n * n + (12 * n ** 3 if mF > 0 else 0) + 4 * n ** 3 + 2 * n * n * Wc + 2 * n * r * mF
+               + m ** 3 / 3 + m * m * (r + Wc) + m * ((r + Wc) ** 2 + r * r + W2))
+        by += es * (2 * n * n + n * Wc + n * mF + m * m + m * (r + Wc) + r * r + r * Wc + r * mF
+                    + (Wc * Wc + W2))
+    return fl, by
+
+
+@pytest.mark.parametrize("kind,n,box,tol", [("p2", 64, (4, 4), 1e-3), ("p2", 96, (8, 4), 1e-4),
+                                            ("p3", 16, (4, 4, 4), 1e-4)])
+def test_host_work_count_matches_oracle_steps(lib, kind, n, box, tol):
+    """The algorithmic flops and bytes behind the roofline (ce_info.level_flops
+    / level_bytes) equal the stated per-row formula evaluated on the oracle's
+    own level-1 steps: the library's far lists hold exactly the fill present
+    when a row runs (no zero blocks counted), its close widths those of the W
+    blocks the oracle forms."""
+    if kind == "p3":
+        A, perm = wl.poisson3d(n), wl.box_perm((n, n, n), box)
+    else:
+        A, perm = wl.poisson2d(n), wl.box_perm((n, n), box)
+    B = int(np.prod(box))
+    F = oce.factorize(A, perm, B, tol, 1, 4, nmax=64)
+    nn, rp, ci, v, pm = _csr_args(A, perm)
+    rk = np.ascontiguousarray(F.levels[0].ranks, np.int32)
+    for es in (4, 8):
+        fl, by = C.c_double(), C.c_double()
+        st = lib.ce_plan_level1_work(nn, rp.ctypes.data_as(_lib.I64P), ci.ctypes.data_as(_lib.I32P),
+                                     pm.ctypes.data_as(_lib.I32P), B, rk.ctypes.data_as(_lib.I32P), es,
+                                     C.byref(fl), C.byref(by))
+        assert st == _lib.CE_OK
+        f2, b2 = _work_formula(F, es)
+        assert fl.value == pytest.approx(f2, rel=1e-12) and by.value == pytest.approx(b2, rel=1e-12)
