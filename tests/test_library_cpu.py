@@ -340,3 +340,34 @@ def test_host_work_count_matches_oracle_steps(lib, kind, n, box, tol):
         assert st == _lib.CE_OK
         f2, b2 = _work_formula(F, es)
         assert fl.value == pytest.approx(f2, rel=1e-12) and by.value == pytest.approx(b2, rel=1e-12)
+
+
+def test_host_exports_reject_bad_arguments(lib):
+    A, perm = wl.poisson2d(16), wl.box_perm((16, 16), (4, 4))
+    n, rp, ci, v, pm = _csr_args(A, perm)
+    M = n // 16
+    base = (n, rp.ctypes.data_as(_lib.I64P), ci.ctypes.data_as(_lib.I32P), pm.ctypes.data_as(_lib.I32P), 16)
+    fl, by = C.c_double(), C.c_double()
+    nM, ncl = C.c_int(), C.c_int64()
+    out = np.zeros(M, np.int32)
+    for bad in (np.full(M, 17, np.int32), np.full(M, -1, np.int32)):      # r_i outside [0, n_i]
+        assert lib.ce_plan_level1_work(*base, bad.ctypes.data_as(_lib.I32P), 8, C.byref(fl),
+                                       C.byref(by)) == _lib.CE_ERR_INVALID_ARG
+        assert lib.ce_plan_next_level(*base, bad.ctypes.data_as(_lib.I32P), 4, 64,
+                                      out.ctypes.data_as(_lib.I32P), out.ctypes.data_as(_lib.I32P),
+                                      C.byref(nM), C.byref(ncl)) == _lib.CE_ERR_INVALID_ARG
+    ok = np.full(M, 4, np.int32)
+    assert lib.ce_plan_level1_work(*base, ok.ctypes.data_as(_lib.I32P), 2, C.byref(fl),
+                                   C.byref(by)) == _lib.CE_ERR_INVALID_ARG          # element size
+    assert lib.ce_plan_next_level(*base, ok.ctypes.data_as(_lib.I32P), 0, 64, None, None, C.byref(nM),
+                                  None) == _lib.CE_ERR_INVALID_ARG                    # J
+    pm_bad = pm.copy()
+    pm_bad[0] = pm_bad[1]                                                             # not a permutation
+    nd = C.c_int64()
+    assert lib.ce_plan_level1_deps(n, rp.ctypes.data_as(_lib.I64P), ci.ctypes.data_as(_lib.I32P),
+                                   pm_bad.ctypes.data_as(_lib.I32P), 16, None, None, 0,
+                                   C.byref(nd)) == _lib.CE_ERR_INVALID_ARG
+    # valid: level 2 of 16 blocks of rank 4 joined by 4 is 4 blocks of 16 rows
+    assert lib.ce_plan_next_level(*base, ok.ctypes.data_as(_lib.I32P), 4, 64, out.ctypes.data_as(_lib.I32P),
+                                  None, C.byref(nM), None) == _lib.CE_OK
+    assert nM.value == 4 and list(out[:4]) == [16] * 4
