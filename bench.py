@@ -5,10 +5,13 @@ One step = ce_factorize + pcg_solve of the 2D Poisson 512x512 system (B = 32,
 tol 1e-4, 4 levels, J = 4) with the matrix and right-hand side resident in
 HBM.  ``--workload poisson2d_batch256`` times instead 256 independent 2D
 Poisson systems (sides drawn from {64, 96, 128, 192, 256}) factorized as one
-block-diagonal batch and solved by the per-system batched PCG.  The chosen form (learned ranks with a randomized range finder, FP32
-blocks and compression, FP64 PCG) is the headline value; the plain FP64 form
-(exact SVD) is timed beside it.  The rank model is trained on the GPU before
-the timed region.  Prints one JSON line.
+block-diagonal batch and solved by the per-system batched PCG.  The chosen
+form (learned ranks with a randomized range finder, FP32 blocks and
+compression, FP64 PCG) is the headline value; the plain FP64 form (exact SVD)
+is timed beside it, both autotuned and timed alike.  The rank model is trained
+on the GPU and the arithmetic peaks are measured before the timed region.
+``--impl reference`` times the FP64 CPU oracle on the same workload.  Prints
+one JSON line.
 
     python bench.py [--steps K] [--warmup W] [--impl ours|reference]
 """
@@ -36,10 +39,8 @@ METRIC = "time to 1e-8 residual (factor+PCG)"
 WORKLOAD = "poisson2d_512_B32"
 BATCH = "poisson2d_batch256"
 BATCH_SYSTEMS = 256
-SAMPLE_GRID = 128        # oracle sample: 128x128 grid of the same kind
+WARMUP_GRID = 64         # reference arm warm-up: a 64x64 grid of the same kind (untimed)
 RTOL = 1e-8
-PEAK_FP32_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
-PEAK_FP64_TFLOPS = 1.25                             # GB300 nominal FP64
 
 
 def parse():
@@ -178,45 +179,44 @@ class Problem:
                          / np.linalg.norm(w.b)) for s, w in enumerate(self.ws))
 
 
-def oracle_time(w, grid, levels):
-    """Oracle factorize + PCG on a grid x grid sample of the same kind (s)."""
+def oracle_solve(w):
+    """Oracle factorize + PCG of one workload (seconds, PCG iterations)."""
     from oracle import ce as oce
-    A = wl.diffusion2d(wl.grf2d(grid, 0)) if w.name.startswith("grf") else wl.poisson2d(grid)
-    box = (8, 4) if w.B == 32 else (4, 4)
-    perm = wl.box_perm((grid, grid), box)
-    b = wl.rhs(A.shape[0], 0)
     t0 = time.perf_counter()
-    F = oce.factorize(A, perm, w.B, w.tol, levels, w.J, nmax=64)
-    res = oce.pcg(A, F, b, RTOL, 1000)
-    t1 = time.perf_counter()
+    F = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J, nmax=64)
+    res = oce.pcg(w.A, F, w.b, RTOL, 1000)
+    t = time.perf_counter() - t0
     assert res.converged
-    return t1 - t0, A.shape[0], res.iters
+    return t, res.iters
 
 
-def oracle_sample(pb):
-    """(seconds, unknowns, PCG iterations, what) of one bounded oracle run."""
+def oracle_step(pb):
+    """(seconds for the workload, unknowns timed, PCG iterations, what) of one
+    oracle run: the whole workload for a single system; for the batch, one
+    64x64 system of it, scaled by N (a whole batch is ~250 s of CPU work)."""
     if pb.batched:
-        # one 64x64 system of the batch, with the batch's own parameters
-        from oracle import ce as oce
         w = next(w for w in pb.ws if w.A.shape[0] == 64 * 64)
-        t0 = time.perf_counter()
-        F = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J, nmax=64)
-        res = oce.pcg(w.A, F, w.b, RTOL, 1000)
-        t = time.perf_counter() - t0
-        assert res.converged
-        return t, w.A.shape[0], res.iters, f"one 64x64 system of the batch ({pb.levels} levels)"
-    w = pb.ws[0]
-    levels = min(w.levels, 3)
-    t, n, its = oracle_time(w, SAMPLE_GRID, levels)
-    return t, n, its, f"the {SAMPLE_GRID}x{SAMPLE_GRID} grid of the same problem ({levels} levels)"
+        t, its = oracle_solve(w)
+        return t * pb.N / w.A.shape[0], w.A.shape[0], its, \
+            f"one 64x64 system of the batch ({pb.levels} levels), scaled linearly to N={pb.N}"
+    t, its = oracle_solve(pb.ws[0])
+    return t, pb.N, its, f"the whole workload ({pb.desc}, {pb.levels} levels), one run, unscaled"
+
+
+def oracle_warmup(pb):
+    """Untimed warm-up of the oracle (imports, allocator): a small grid."""
+    from oracle import ce as oce
+    A = wl.poisson2d(WARMUP_GRID)
+    perm = wl.box_perm((WARMUP_GRID, WARMUP_GRID), (4, 4))
+    F = oce.factorize(A, perm, 16, 1e-3, 2, 4, nmax=64)
+    oce.pcg(A, F, wl.rhs(A.shape[0], 0), RTOL, 100)
 
 
 def cpu_baseline(pb):
-    t, n, its, what = oracle_sample(pb)
-    return {"value": t * pb.N / n, "unit": "s", "cores": 1, "kind": "oracle",
-            "sample": f"FP64 numpy oracle on {what}: {n} unknowns, {its} PCG iterations, "
-                      f"{t:.2f} s, scaled linearly to N={pb.N} (O(N) cost, Corollary of "
-                      "Section 2.7); single-threaded BLAS"}
+    t, n, its, what = oracle_step(pb)
+    return {"value": t, "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"FP64 numpy oracle (single-threaded BLAS) on {what}: {n} unknowns, "
+                      f"{its} PCG iterations"}
 
 
 def run_reference(args, rank):
@@ -224,11 +224,11 @@ def run_reference(args, rank):
     if rank != 0:
         return
     for _ in range(args.warmup):
-        oracle_sample(pb)
-    ts = []
+        oracle_warmup(pb)
+    ts, what = [], ""
     for _ in range(args.steps):
-        t, n, its, what = oracle_sample(pb)
-        ts.append(t * pb.N / n)
+        t, n, its, what = oracle_step(pb)
+        ts.append(t)
     v = statistics.mean(ts)
     out = {"metric": METRIC, "value": v, "unit": "s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": v * 1e3, "higher_is_better": False,
@@ -237,10 +237,36 @@ def run_reference(args, rank):
            "config": {"workload": args.workload, "N": pb.N, "B": pb.B, "tol": pb.tol,
                       "levels": pb.levels, "J": pb.J},
            "cpu_baseline": {"value": v, "unit": "s", "cores": 1, "kind": "oracle",
-                            "sample": f"each step: oracle factorize+PCG on {what}, "
-                                      "scaled linearly to N"},
+                            "sample": f"each step: oracle factorize+PCG on {what}; "
+                                      f"warm-up steps: a {WARMUP_GRID}x{WARMUP_GRID} grid"},
            "e2e": {"value": v, "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def committed_traffic(kernel, workload, precision):
+    """DRAM traffic per launch of `kernel` from the committed ncu summary
+    (profiles/ce_row_kernel_traffic.md), if that capture was taken of the
+    current kernel source (its SHA-256 is recorded with the numbers); None
+    otherwise.  Lines read: `source_sha256: <hex>`, and per captured form
+    `traffic: <kernel> <workload> <precision> <bytes per launch>`."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "ce_row_kernel_traffic.md")
+    src = os.path.join(ROOT, "paper_1603_09133_gb300", "csrc", "row_kernel.cu")
+    if not os.path.exists(path):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    rec_sha, val = None, None
+    for ln in open(path):
+        f = ln.strip().strip("`").split()
+        if len(f) == 2 and f[0] == "source_sha256:":
+            rec_sha = f[1]
+        if len(f) == 5 and f[0] == "traffic:" and f[1:4] == [kernel, workload, precision]:
+            val = float(f[4])
+    if rec_sha != sha or val is None:
+        return None
+    return {"bytes_per_launch": val,
+            "note": "dram__bytes_read.sum + dram__bytes_write.sum per launch, mean over the level "
+                    "launches of one factorization (profiles/ce_row_kernel_traffic.md)"}
 
 
 # --------------------------------------------------------------------------
@@ -262,9 +288,14 @@ def run_ours(args, rank, world):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     model = ceg.trained_rank_model() if args.ranks == "learned" else None
-    # row-kernel CTA shape per level, chosen by measurement (setup, untimed)
+    # measured arithmetic peaks of this GPU (the roofline denominators)
+    peaks = {k: ceg.measure_peak(k) for k in ("fp32_fma", "fp64_fma", "tf32_mma", "tf32x3_mma")}
+    # row-kernel CTA shape (and learned or exact per level) chosen by
+    # measurement for both forms (setup, untimed)
     tune_ms = ceg.ce_autotune(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=args.precision,
                               rank_model=model)
+    tune_ms_plain = ceg.ce_autotune(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision="fp64")
+    tuning = csb.tuning(args.precision, learned=model is not None)
 
     def step(prec, rm=None):
         F = ceg.ce_factorize(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=prec, rank_model=rm)
@@ -278,6 +309,8 @@ def run_ours(args, rank, world):
         if world > 1:
             torch.distributed.barrier()
         torch.cuda.synchronize()
+        sampler = ClockSampler(dev.index)
+        sampler.start()
         l0 = lib.ce_launch_count()
         for _ in range(k):
             flush.zero_()
@@ -289,37 +322,47 @@ def run_ours(args, rank, world):
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
         launches = (lib.ce_launch_count() - l0) / k
+        clocks = sampler.stop()
         if world > 1:
             torch.distributed.barrier()
-        return times, last, launches
+        return times, last, launches, clocks
 
-    # plain FP64 form with exact SVDs (the comparison) and the chosen form
-    t_other, last_other, _ = timed("fp64", max(1, args.steps // 2), 1)
-    sampler = ClockSampler(dev.index)
-    sampler.start()
-    times, last, launches = timed(args.precision, args.steps, args.warmup, model)
-    clocks = sampler.stop()
+    # plain FP64 form with exact SVDs (the comparison), then the chosen form,
+    # each autotuned and timed with the same steps, warm-up and clock sampling
+    t_other, last_other, _, clocks_other = timed("fp64", args.steps, args.warmup)
+    times, last, launches, clocks = timed(args.precision, args.steps, args.warmup, model)
     F, it, conv = last
     true_rel = pb.true_relres(x.cpu().numpy())
     ms = max_over_ranks(statistics.mean(times), world, dev)
 
-    # roofline of the dominant kernel (the persistent row kernel, one launch per level)
+    # roofline of the dominant kernel (the persistent row kernel, one launch
+    # per level): algorithmic flops (counted from the actual sizes, ranks,
+    # widths and sketch widths) over its CUDA-event time, against the measured
+    # FP32 FFMA (FP64: DFMA) rate of this GPU
     info = F.info
     nl = info.levels_done
     lms = sum(info.level_ms[l] for l in range(nl))
     lfl = sum(info.level_flops[l] for l in range(nl))
     lby = sum(info.level_bytes[l] for l in range(nl))
-    peak = PEAK_FP32_TFLOPS if args.precision == "fp32" else PEAK_FP64_TFLOPS
+    pk = "fp32_fma" if args.precision == "fp32" else "fp64_fma"
+    peak = peaks[pk]
     achieved = lfl / (lms * 1e-3) / 1e12
+    kname = f"ce_row_kernel<{'float' if args.precision == 'fp32' else 'double'}>"
+    traffic = committed_traffic(kname, args.workload, args.precision)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None,
-                "kernel": f"ce_row_kernel<{'float' if args.precision == 'fp32' else 'double'}>",
-                "kernel_ms_per_step": lms, "algorithmic_flops": lfl,
-                "algorithmic_bytes": lby, "achieved_gbs": lby / (lms * 1e-3) / 1e9,
-                "peak_note": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz"
-                if args.precision == "fp32" else "GB300 nominal FP64"}
+                "frac": achieved / peak,
+                "traffic": traffic["bytes_per_launch"] if traffic else None,
+                "kernel": kname, "launches_per_step": nl,
+                "kernel_ms_per_step": lms, "algorithmic_flops_per_launch": lfl / nl,
+                "algorithmic_bytes_per_launch": lby / nl, "achieved_gbs": lby / (lms * 1e-3) / 1e9,
+                "traffic_note": traffic["note"] if traffic else
+                "no ncu capture of this kernel source committed under profiles/",
+                "peak_note": f"of measured: ce_measure_peak {pk} on this GPU",
+                "measured_peaks_tflops": peaks}
 
-    # end to end through the public API with host buffers
+    # end to end through the public API with host buffers: csb_build from the
+    # host CSR (with the tuning measured above set on the new handle), the
+    # factorization, H2D of b from pinned memory, PCG, D2H of x
     b_host = torch.as_tensor(pb.b).pin_memory()
     x_host = torch.empty(N, dtype=torch.float64).pin_memory()
     e2e_t = []
@@ -328,6 +371,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         csb2 = pb.build(arrays)
+        csb2.set_tuning(tuning, args.precision, learned=model is not None)
         F2 = ceg.ce_factorize(csb2, tol=pb.tol, levels=pb.levels, J=pb.J, precision=args.precision,
                               rank_model=model)
         bd = b_host.to(dev, non_blocking=True)
@@ -354,6 +398,8 @@ def run_ours(args, rank, world):
                   "row_shape": [info.row_shape[l] for l in range(nl)],
                   "row_learned": [info.row_learned[l] for l in range(nl)],
                   "autotune_ms": np.round(tune_ms, 3).tolist(),
+                  "autotune_ms_plain_fp64": np.round(tune_ms_plain, 3).tolist(),
+                  "jacobi_capped": [info.jacobi_capped[l] for l in range(nl)],
                   "host_ms": [round(info.host_ms[l], 3) for l in range(nl)],
                   "factor_wall_ms": round(info.total_ms, 3),
                   "coarse_n": info.coarse_n, "coarse_ms": round(info.coarse_ms, 3),
@@ -369,6 +415,9 @@ def run_ours(args, rank, world):
                       "pcg_iters": it, "final_relres": true_rel,
                       "plain_fp64_form_s": statistics.mean(t_other) / 1e3,
                       "plain_fp64_form_pcg_iters": last_other[1],
+                      "plain_fp64_form_clocks": clocks_other,
+                      "plain_fp64_form_timing": "autotuned (exact SVD, FP64), same steps, warm-up, "
+                                                "L2 flush and clock sampling as the chosen form",
                       "learned_rows": [info.learned_rows[l] for l in range(info.levels_done)],
                       "fallback_rows": [info.fallback_rows[l] for l in range(info.levels_done)],
                       "rank_model_train_loss": getattr(model, "loss", None),

@@ -126,6 +126,10 @@ typedef struct {
                           speculative planning of level l+1 guessed wrong
                           (0: the pattern planned during the GPU work is
                           kept; otherwise it is planned again)            */
+  int jacobi_capped[16]; /* rows of level l whose Jacobi SVD stopped at its
+                          sweep cap (40 sweeps) with a pair still above the
+                          orthogonality threshold; their singular values
+                          and vectors are used as they stand             */
 } ce_info;
 
 typedef struct {
@@ -260,6 +264,21 @@ ce_status ce_factorize_simple(int64_t n, const int64_t* rowptr,
 ce_status ce_autotune(ce_csb* A, const ce_opts* o, double* level_ms);
 
 /*
+ * csb_get_tuning / csb_set_tuning -- the choices ce_autotune keeps in a csb
+ * for one precision (CE_PREC_*) and rank mode (CE_RANK_*), host-only: the
+ * number of tuned levels, and per level (16 entries each) the row kernel's CTA
+ * shape (0..2) and whether the learned compression runs (1) or the exact SVD
+ * (0).  A tuning measured on one csb can be set on another csb of the same
+ * matrix (e.g. one rebuilt from host arrays) so that it runs the same
+ * schedule.  CE_ERR_INVALID_ARG on a bad precision, mode, count or value.
+ * Not part of the paper (launch configuration of this implementation).
+ */
+ce_status csb_get_tuning(const ce_csb* A, int precision, int rank_mode, int* levels, int32_t* shape,
+                         int32_t* learned);
+ce_status csb_set_tuning(ce_csb* A, int precision, int rank_mode, int levels, const int32_t* shape,
+                         const int32_t* learned);
+
+/*
  * ce_apply -- z = M^{-1} r = Q^T L^{-T} L^{-1} Q r (solve proposition of
  * Section 2.5).  r_dev and z_dev are device arrays of n doubles in the
  * original ordering of A; they may alias.  All work is queued on `stream`
@@ -310,20 +329,25 @@ ce_status pcg_solve_batched(const ce_csb* A, const ce_factor* F,
                             void* stream);
 
 /*
- * pcg_solve_noalloc -- the same FP64 PCG as pcg_solve (same arguments, same
- * arithmetic, same results), for callers that cannot let a library allocate
- * device memory: applications whose GPU memory is reserved up front by their
- * own pool allocator, latency-critical loops that cannot afford the implicit
- * device synchronization of cudaMalloc/cudaFree, and plugins whose host
- * application forbids allocation.  The paper has no counterpart; it is a
- * deployment variant of pcg_solve.
+ * pcg_solve_noalloc -- the FP64 PCG of pcg_solve for one system (same
+ * arguments, same arithmetic, same results as pcg_solve on a handle from
+ * csb_build), for callers that cannot let a library allocate device memory:
+ * applications whose GPU memory is reserved up front by their own pool
+ * allocator, latency-critical loops that cannot afford the implicit device
+ * synchronization of cudaMalloc/cudaFree, and plugins whose host application
+ * forbids allocation.  The paper has no counterpart; it is a deployment
+ * variant of pcg_solve.
  *   - Allocates nothing: the work vectors live in one static device array
  *     (4 x 65536 doubles plus reduction partials, about 2 MiB) that every GPU
  *     loading the library holds until the process exits.
  *   - n > 65536 is rejected with CE_ERR_LIMIT (ce_last_error() says why).
- *   - The first call on a device looks the array's device address up
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture.
+ *   - A batch handle (csb_build_batched with more than one system) is
+ *     rejected with CE_ERR_INVALID_ARG: pcg_solve runs one CG recurrence per
+ *     system there, and the static array holds one recurrence.
+ *   - Every call looks the array's device address up (cudaGetSymbolAddress,
+ *     which allocates nothing) with the caller's device current, so it stays
+ *     valid across a cudaDeviceReset; make the first call on a device before
+ *     any stream capture (that lookup may load the module).
  *   - All calls share the array and it keeps the last call's contents; calls
  *     whose work overlaps on the GPU (other streams, other host threads) race
  *     on it and must be serialized by the caller.
@@ -368,6 +392,19 @@ ce_status ce_mlp_predict(const float* X_dev, int ns, const void* model_dev,
 /* Number of kernels the library has launched so far (process-wide). */
 int64_t ce_launch_count(void);
 
+/*
+ * ce_measure_peak -- measured arithmetic rate of one execution unit of the
+ * current device, the denominator of a roofline fraction (not part of the
+ * paper).  A kernel that keeps the unit busy on every SM (independent chains,
+ * full occupancy) runs a few milliseconds, three times after one warm-up; the
+ * best rate is returned in TFLOP/s (an FMA counts 2 flops).
+ *   kind  0: FP32 FFMA; 1: FP64 DFMA; 2: TF32 mma.sync m16n8k8 with FP32
+ *         accumulate; 3: the 3xTF32 product of the row kernel (operands split
+ *         into TF32 hi + lo, three MMAs counted as one product)
+ * Allocates and frees a few KB on `stream`; synchronizes it.
+ */
+ce_status ce_measure_peak(int kind, double* tflops, void* stream);
+
 /* Static text of a status code; text of the last CUDA failure (per thread). */
 const char* ce_strerror(ce_status s);
 const char* ce_last_error(void);
@@ -384,6 +421,17 @@ const char* ce_last_error(void);
  *                          doubles; zeros where F_i had fewer columns)
  */
 int ce_factor_levels(const ce_factor* F);
+/*
+ * ce_factor_get_features -- what the learned compression saw on level l, per
+ * block (host copies):
+ *   feat  M_l x ce_mlp_nfeatures() floats, row-major (may be NULL): the rank
+ *         model's input features of block i (zeros where the model did not
+ *         run: exact levels, rows without far blocks)
+ *   kw    M_l ints (may be NULL): sketch width k of the randomized range
+ *         finder, k > 0 accepted, -k rejected and sent to the exact SVD,
+ *         0 no sketch
+ */
+ce_status ce_factor_get_features(const ce_factor* F, int level, float* feat, int32_t* kw);
 int ce_factor_level_size(const ce_factor* F, int level);
 ce_status ce_factor_get_level(const ce_factor* F, int level, int32_t* n,
                               int32_t* rank, int32_t* colour, double* tau);
@@ -476,6 +524,21 @@ ce_status ce_plan_level1_work(int64_t n, const int64_t* rowptr, const int32_t* c
  * pointer.
  */
 ce_status ce_plan_groups(int M, const int32_t* rank, int J, int nmax, int32_t* first_child, int* ngroups);
+
+/*
+ * ce_debug_wait_expiry -- test of the failure path of the persistent
+ * launches' dependency waits (no counterpart in the paper).  Builds a level of
+ * two coupled 4-row blocks on the device and queues only the second, whose
+ * wait for the first (kernel 0: the row kernel of ce_factorize, reason 5;
+ * kernel 1: the forward apply of ce_apply, reason 6) can never be satisfied,
+ * with the wait limited to limit_ms (0 < limit_ms <= 2000; the library's own
+ * limit is 2 s).  The kernel gives up, records CE_ERR_CUDA with its reason and
+ * returns; the context stays usable.
+ *   status_out  host, 8 ints: the kernel's status words [code, level, block,
+ *               reason, ...]
+ * Returns CE_OK when the launch itself worked (whatever the kernel recorded).
+ */
+ce_status ce_debug_wait_expiry(int kernel, double limit_ms, int32_t* status_out, void* stream);
 
 /* Level-1 plan of a csb handle: blocks, colours, colour of every block. */
 int csb_blocks(const ce_csb* A);

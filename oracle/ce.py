@@ -192,6 +192,8 @@ class BlockStep:
     targets: list          # [(t, W_t)]: t == i is the basis of i, else close t
     far: list              # far blocks whose columns formed F_i (non-empty)
     features: np.ndarray = None  # rank-predictor features (block_features)
+    row: tuple = None      # (D_i, [C_ik], [F_ik]) before compression, kept
+                           # only with factorize(record_rows=True)
 
 
 @dataclasses.dataclass
@@ -268,7 +270,7 @@ def _random_orthogonal(rng, k):
 
 
 def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
-               rotate_rng=None, shuffle_rng=None, J=4):
+               rotate_rng=None, shuffle_rng=None, J=4, record_rows=False):
     M = len(sizes)
     size = list(sizes)
     close = _block_graph(S, M)          # level-start pattern = close blocks
@@ -291,8 +293,9 @@ def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
         # -- compression step (Section 2.2, eq. rreav) ----------------------
         far = sorted(k for k in nbr[i] if k not in close[i] and size[k] > 0)
         Fs = [_get(S, i, k) for k in far]
-        feats = block_features(level_no, n, J, _get(S, i, i),
-                               [_get(S, i, k) for k in sorted(close[i] - {i})], Fs, tol)
+        Cs = [_get(S, i, k) for k in sorted(close[i] - {i})]
+        feats = block_features(level_no, n, J, _get(S, i, i), Cs, Fs, tol)
+        row = (_get(S, i, i).copy(), [X.copy() for X in Cs], [X.copy() for X in Fs]) if record_rows else None
         F = np.hstack(Fs) if Fs else np.zeros((n, 0))
         if F.shape[1] == 0 or n == 0 or not np.any(F):
             U = np.eye(n)
@@ -361,7 +364,7 @@ def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
                     nbr[t].add(s)
                 _put(S, s, t, _get(S, s, t) - (upd if s != t else 0.5 * (upd + upd.T)))
         steps.append(BlockStep(i, n, r, sig, tau, U, Lh,
-                               [(t, W[t]) for t in targets], far, feats))
+                               [(t, W[t]) for t in targets], far, feats, row))
     return S, size, colour, order, steps, ranks
 
 
@@ -462,15 +465,22 @@ def initial_blocks(A, perm, B):
 # Algorithm 1: CE factorization
 # --------------------------------------------------------------------------
 def factorize(A, perm, B, tol, levels, J=4, tol_mode="rel", order="colour",
-              rotate_rng=None, shuffle_rng=None, nmax=None, rank=None):
+              rotate_rng=None, shuffle_rng=None, nmax=None, rank=None, record_rows=False):
     """CE factorization A ~= Q^T L L^T Q (Algorithm 1, Proposition CE_L).
 
     ``levels`` compression-elimination sweeps, each followed by coarsening by
     J; the remainder A_K is factorized by dense Cholesky.  Raises
     :class:`NotSPDError` when a pivot block is not positive definite.
 
-    ``nmax`` caps the super-block size: a group of J consecutive blocks closes
-    early when the next block would take it past nmax rows.
+    ``nmax`` caps the super-block size: a run of J consecutive blocks whose
+    sizes add up to more than nmax rows is halved (first half ceil(len/2)
+    blocks), recursively, until every part fits or is a single block
+    (``_groups``).  ``nmax=None`` (the default) is the paper's rule of plain
+    runs of J blocks (Section 2.4).
+
+    ``record_rows`` keeps, for every step, the blocks D_i, C_ik and F_ik of
+    its row as they stood before compression (memory grows with the problem;
+    for small test cases).
 
     ``tol_mode='fixed'`` is CE(r) with r = ``rank`` (``tol`` is unused).
 
@@ -492,7 +502,7 @@ def factorize(A, perm, B, tol, levels, J=4, tol_mode="rel", order="colour",
         sizes_start = list(sizes)
         pairs = sorted(S.keys())
         S, size, colour, order_, steps, ranks = _one_level(
-            S, sizes, tol, tol_mode, order, lev, rotate_rng, shuffle_rng, J)
+            S, sizes, tol, tol_mode, order, lev, rotate_rng, shuffle_rng, J, record_rows)
         S, sizes, groups = _coarsen(S, size, J, nmax)
         recs.append(Level(pairs, sizes_start, colour, order_, steps, J, ranks, groups))
     Ac = _dense_from_blocks(S, sizes)

@@ -84,6 +84,26 @@ class CSB:
                "csb_get_colours")
         return col, nc.value
 
+    def tuning(self, precision="fp32", learned=True):
+        """(levels, shape[16], learned[16]) kept by ce_autotune for a form."""
+        lib = _lib.load()
+        nl = C.c_int(0)
+        shape = np.zeros(16, np.int32)
+        lrn = np.zeros(16, np.int32)
+        _check(lib.csb_get_tuning(self._h, _prec(precision), int(bool(learned)), C.byref(nl),
+                                  shape.ctypes.data_as(_lib.I32P), lrn.ctypes.data_as(_lib.I32P)),
+               "csb_get_tuning")
+        return nl.value, shape, lrn
+
+    def set_tuning(self, tuning, precision="fp32", learned=True):
+        """Apply a tuning from another csb of the same matrix."""
+        nl, shape, lrn = tuning
+        shape = np.ascontiguousarray(shape, np.int32)
+        lrn = np.ascontiguousarray(lrn, np.int32)
+        _check(_lib.load().csb_set_tuning(self._h, _prec(precision), int(bool(learned)), int(nl),
+                                          shape.ctypes.data_as(_lib.I32P), lrn.ctypes.data_as(_lib.I32P)),
+               "csb_set_tuning")
+
     def close(self):
         if self._h:
             _lib.load().ce_csb_destroy(self._h)
@@ -124,6 +144,18 @@ class Factor:
                                        tau.ctypes.data_as(_lib.DP)), "ce_factor_get_level")
         return n, r, col, tau
 
+    def features(self, l):
+        """What the learned compression saw on level l: the rank model's
+        features (M_l x nfeat, zeros where the model did not run) and the
+        sketch width per block (k accepted, -k rejected, 0 none)."""
+        lib = _lib.load()
+        M = lib.ce_factor_level_size(self._h, l)
+        feat = np.zeros((M, lib.ce_mlp_nfeatures()), np.float32)
+        kw = np.zeros(M, np.int32)
+        _check(lib.ce_factor_get_features(self._h, l, feat.ctypes.data_as(C.c_void_p),
+                                          kw.ctypes.data_as(_lib.I32P)), "ce_factor_get_features")
+        return feat, kw
+
     def sigma(self, l):
         """Singular values of every F_i of level l, concatenated (n_i each)."""
         lib = _lib.load()
@@ -142,6 +174,18 @@ class Factor:
             self.close()
         except Exception:
             pass
+
+
+PEAK_KINDS = {"fp32_fma": 0, "fp64_fma": 1, "tf32_mma": 2, "tf32x3_mma": 3}
+
+
+def measure_peak(kind: str, stream=None) -> float:
+    """Measured rate (TFLOP/s) of one execution unit of the current GPU:
+    'fp32_fma', 'fp64_fma', 'tf32_mma' or 'tf32x3_mma' (ce_measure_peak)."""
+    out = C.c_double(0.0)
+    _check(_lib.load().ce_measure_peak(PEAK_KINDS[kind], C.byref(out), _stream_ptr(stream)),
+           "ce_measure_peak")
+    return out.value
 
 
 def launch_count() -> int:
@@ -225,6 +269,12 @@ def csb_build_batched(systems) -> CSB:
 
 
 _TOL_MODES = {"rel": CE_TOL_REL, "abs": CE_TOL_ABS, "fixed": CE_TOL_FIXED}
+
+
+def _prec(precision):
+    if precision not in ("fp64", "fp32"):
+        raise ValueError("precision must be 'fp64' or 'fp32'")
+    return CE_PREC_FP64 if precision == "fp64" else CE_PREC_FP32
 
 
 def _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed,

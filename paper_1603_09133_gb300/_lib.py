@@ -69,6 +69,7 @@ class ce_info(C.Structure):
         ("row_shape", C.c_int * 16),
         ("row_learned", C.c_int * 16),
         ("spec_miss", C.c_int * 16),
+        ("jacobi_capped", C.c_int * 16),
     ]
 
 
@@ -110,6 +111,7 @@ SIGNATURES = {
     "ce_strerror": (C.c_char_p, [C.c_int]),
     "ce_last_error": (C.c_char_p, []),
     "ce_launch_count": (C.c_int64, []),
+    "ce_measure_peak": (C.c_int, [C.c_int, DP, P]),
     "ce_mlp_nparams": (C.c_int, []),
     "ce_mlp_nfeatures": (C.c_int, []),
     "ce_mlp_init": (C.c_int, [FP, C.c_uint64, P]),
@@ -121,7 +123,11 @@ SIGNATURES = {
     "ce_factor_level_size": (C.c_int, [P, C.c_int]),
     "ce_factor_get_level": (C.c_int, [P, C.c_int, I32P, I32P, I32P, DP]),
     "ce_factor_get_sigma": (C.c_int, [P, C.c_int, DP]),
+    "ce_factor_get_features": (C.c_int, [P, C.c_int, FP, I32P]),
     "csb_blocks": (C.c_int, [P]),
+    "csb_get_tuning": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(C.c_int), I32P, I32P]),
+    "csb_set_tuning": (C.c_int, [P, C.c_int, C.c_int, C.c_int, I32P, I32P]),
+    "ce_debug_wait_expiry": (C.c_int, [C.c_int, C.c_double, I32P, P]),
     "ce_plan_level1": (C.c_int, [C.c_int64, I64P, I32P, I32P, C.c_int32, I32P,
                                  C.POINTER(C.c_int), I64P, I64P]),
     "csb_get_colours": (C.c_int, [P, I32P, C.POINTER(C.c_int)]),

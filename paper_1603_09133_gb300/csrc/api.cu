@@ -211,8 +211,16 @@ SideStreams& side_streams() {
 //              + n^2 + m^2 + m (r + Wc)                  writes U, L_hat, W
 //              + r^2 + r Wc + r mF                       writes kept rows
 //              + 2 sum_{p<=q close} w_p w_q)             Schur targets r+w
+//   A row that ran the learned compression (sketch width k = |kw_i|, k + 2
+//   columns with the probes) counts the sketch instead of the exact SVD:
+//         2 n mF (k + 2)       (Y = F [Omega | probes])
+//         + 4 n k^2             (Householder QR of Y, explicit Q)
+//         + 2 mF n k + 2 mF k^2 (rows of F^T Q, their TSQR)
+//         + 12 k^3              (SVD of the k x k factor with V)
+//         + 2 n k r + 2 n r^2 + 4 n^2 r   (U_b, its orthogonal completion)
+//   and a rejected row (kw_i < 0) counts both.
 void level_work(const LevelPlan& P, const std::vector<int>& rank, int es, double& flops,
-                double& bytes) {
+                double& bytes, const std::vector<int>* kw = nullptr) {
   // fixed chunks summed in chunk order: the totals do not depend on timing
   constexpr int kChunks = 64;
   double pf[kChunks] = {}, pb[kChunks] = {};
@@ -232,7 +240,13 @@ void level_work(const LevelPlan& P, const std::vector<int>& rank, int es, double
           W2 += x * x;
         }
         const double pairs = 0.5 * (Wc * Wc + W2);
-        pf[c] += 2 * mF * n * n + (mF > 0 ? 12 * n * n * n : 0) + 4 * n * n * n + 2 * n * n * Wc +
+        const int kwi = kw ? (*kw)[i] : 0;
+        const double k = kwi < 0 ? -kwi : kwi;
+        const double sketch = 2 * n * mF * (k + 2) + 4 * n * k * k + 2 * mF * n * k + 2 * mF * k * k +
+                              12 * k * k * k + 2 * n * k * r + 2 * n * r * r + 4 * n * n * r;
+        const double exact = 2 * mF * n * n + (mF > 0 ? 12 * n * n * n : 0);
+        const double compress = kwi > 0 ? sketch : (kwi < 0 ? sketch + exact : exact);
+        pf[c] += compress + 4 * n * n * n + 2 * n * n * Wc +
                  2 * n * r * mF + m * m * m / 3 + m * m * (r + Wc) + m * ((r + Wc) * (r + Wc) + r * r + W2);
         pb[c] += es * (n * n + n * Wc + n * mF + n * n + m * m + m * (r + Wc) + r * r + r * Wc + r * mF +
                        2 * pairs);
@@ -391,7 +405,8 @@ void build_level_store(LevelStore& st, int esize, cudaStream_t s, const void* sh
                o_fd = pk.zeros(P.M * sizeof(int)), o_bd = pk.zeros(P.M * sizeof(int)),
                o_q = pk.zeros(ce::kBuckets * sizeof(int)),
                o_gd = pk.zeros(P.M * sizeof(int64_t)), o_tau = pk.zeros(P.M * sizeof(double)),
-               o_sig = pk.zeros(P.vec_len * sizeof(double));
+               o_sig = pk.zeros(P.vec_len * sizeof(double)), o_kw = pk.zeros(P.M * sizeof(int)),
+               o_feat = pk.zeros((size_t)P.M * ce::kMlpFeatures * sizeof(float));
   st.meta_bytes = pk.size + sbytes;
   st.meta = dalloc(pk.size, s);
   check(cudaMemsetAsync(st.meta, 0, pk.size, s), "memset level state");
@@ -404,6 +419,9 @@ void build_level_store(LevelStore& st, int esize, cudaStream_t s, const void* sh
   D.qnext = reinterpret_cast<int*>(b + o_q);
   D.fdone = reinterpret_cast<int*>(b + o_fd);
   D.bdone = reinterpret_cast<int*>(b + o_bd);
+  D.wait_ns = 2000000000ull;  // 2 s: never reached unless a row's neighbours stall
+  D.kw = reinterpret_cast<int*>(b + o_kw);
+  D.feat = reinterpret_cast<float*>(b + o_feat);
   D.aq = nullptr;
   D.epoch = nullptr;
   const size_t ub = P.u_elems * esize, lb = P.l_elems * esize, wb = P.w_elems * esize;
@@ -594,6 +612,16 @@ const char* ce_strerror(ce_status s) {
 const char* ce_last_error(void) { return g_last_error.c_str(); }
 
 int64_t ce_launch_count(void) { return ce::g_launches.load(); }
+
+ce_status ce_measure_peak(int kind, double* tflops, void* stream) {
+  if (kind < 0 || kind > 3 || !tflops) return CE_ERR_INVALID_ARG;
+  try {
+    check(ce::measure_peak(kind, tflops, static_cast<cudaStream_t>(stream)), "peak probe");
+  } catch (...) {
+    return status_of_exception();
+  }
+  return CE_OK;
+}
 
 int ce_mlp_nparams(void) { return ce::kMlpParams; }
 int ce_mlp_nfeatures(void) { return ce::kMlpFeatures; }
@@ -994,6 +1022,32 @@ ce_status ce_plan_level1_work(int64_t n, const int64_t* rowptr, const int32_t* c
   return CE_OK;
 }
 
+ce_status csb_get_tuning(const ce_csb* A, int precision, int rank_mode, int* levels, int32_t* shape,
+                         int32_t* learned) {
+  if (!A || !levels || precision < 0 || precision > 1 || rank_mode < 0 || rank_mode > 1) return CE_ERR_INVALID_ARG;
+  *levels = A->tuned_levels[precision][rank_mode];
+  for (int l = 0; l < 16; ++l) {
+    if (shape) shape[l] = A->tuned_shape[precision][rank_mode][l];
+    if (learned) learned[l] = A->tuned_learned[precision][rank_mode][l];
+  }
+  return CE_OK;
+}
+
+ce_status csb_set_tuning(ce_csb* A, int precision, int rank_mode, int levels, const int32_t* shape,
+                         const int32_t* learned) {
+  if (!A || precision < 0 || precision > 1 || rank_mode < 0 || rank_mode > 1 || levels < 0 || levels > 16 ||
+      (levels > 0 && (!shape || !learned)))
+    return CE_ERR_INVALID_ARG;
+  for (int l = 0; l < levels; ++l)
+    if (shape[l] < 0 || shape[l] > 2 || (learned[l] != 0 && learned[l] != 1)) return CE_ERR_INVALID_ARG;
+  for (int l = 0; l < 16; ++l) {
+    A->tuned_shape[precision][rank_mode][l] = l < levels ? shape[l] : 0;
+    A->tuned_learned[precision][rank_mode][l] = l < levels ? learned[l] : 0;
+  }
+  A->tuned_levels[precision][rank_mode] = levels;
+  return CE_OK;
+}
+
 int csb_blocks(const ce_csb* A) { return A ? A->plan1->M : 0; }
 
 ce_status csb_get_colours(const ce_csb* A, int32_t* colour, int* ncolours) {
@@ -1036,8 +1090,8 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
   void* pool = nullptr;
   ce_status ret = CE_OK;
   try {
-    F->d_status = static_cast<int*>(dalloc((ce::kStatusWords + 32) * sizeof(int), s));
-    check(cudaMemsetAsync(F->d_status, 0, (ce::kStatusWords + 32) * sizeof(int), s), "memset");
+    F->d_status = static_cast<int*>(dalloc((ce::kStatusWords + ce::kStatsWords) * sizeof(int), s));
+    check(cudaMemsetAsync(F->d_status, 0, (ce::kStatusWords + ce::kStatsWords) * sizeof(int), s), "memset");
     ce::LearnedArgs la;
     if (o.rank_mode == CE_RANK_LEARNED) la.model = static_cast<const __half*>(o.rank_model);
     la.oversample = o.oversample;
@@ -1088,18 +1142,17 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       check(cudaEventRecord(ev0, s), "event");
       // CTA shape: forced, autotuned for this csb, or 256-thread CTAs when
       // the average colour fills two waves of them
-      int shape = (P.ncolours > 0 && P.M / P.ncolours >= 2 * 152) ? 0 : 1;
+      int shape = (P.ncolours > 0 && P.M / P.ncolours >= 2 * ce::device_sms()) ? 0 : 1;
+      const int tp = o.precision, tr = o.rank_mode;
       if (o.row_shape >= 0)
         shape = o.row_shape;
-      else if (l < A->tuned_levels && A->tuned_prec == o.precision && A->tuned_rank == o.rank_mode)
-        shape = A->tuned_shape[l];
+      else if (l < A->tuned_levels[tp][tr])
+        shape = A->tuned_shape[tp][tr][l];
       if (info && l < 16) info->row_shape[l] = shape;
       // learned compression on this level unless the autotuner measured the
       // exact SVD faster here
       ce::LearnedArgs la_l = la;
-      if (o.row_shape < 0 && l < A->tuned_levels && A->tuned_prec == o.precision && A->tuned_rank == o.rank_mode &&
-          !A->tuned_learned[l])
-        la_l.model = nullptr;
+      if (o.row_shape < 0 && l < A->tuned_levels[tp][tr] && !A->tuned_learned[tp][tr][l]) la_l.model = nullptr;
       if (info && l < 16) info->row_learned[l] = la_l.model != nullptr;
       const int nbkt = static_cast<int>(P.bucket_nmax.size());
       if (nbkt <= 1) {
@@ -1124,9 +1177,12 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       }
       check(cudaEventRecord(ev1, s), "event");
       // ranks and status into pinned memory, so the host runs on meanwhile
-      int* hread = reinterpret_cast<int*>(stage_get(2, (P.M + ce::kStatusWords) * sizeof(int)));
+      int* hread = reinterpret_cast<int*>(stage_get(2, (2 * P.M + ce::kStatusWords) * sizeof(int)));
       check(cudaMemcpyAsync(hread, st.dev.rank, P.M * sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
       check(cudaMemcpyAsync(hread + P.M, F->d_status, sizeof(hstatus), cudaMemcpyDeviceToHost, s), "D2H");
+      check(cudaMemcpyAsync(hread + P.M + ce::kStatusWords, st.dev.kw, P.M * sizeof(int), cudaMemcpyDeviceToHost,
+                            s),
+            "D2H");
       // While the GPU eliminates this level, plan the pattern of the next one
       // from the expected set of blocks that keep a basis (those with live
       // far blocks); checked against the actual ranks below.
@@ -1150,13 +1206,14 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       t_host = clk::now();
       st.rank.assign(hread, hread + P.M);
       std::memcpy(hstatus, hread + P.M, sizeof(hstatus));
+      st.kw.assign(hread + P.M + ce::kStatusWords, hread + 2 * P.M + ce::kStatusWords);
       float lms = 0.f;
       cudaEventElapsedTime(&lms, ev0, ev1);
       cudaEventDestroy(ev0);
       cudaEventDestroy(ev1);
       if (info && l < 16) {
         info->level_ms[l] = lms;
-        level_work(P, st.rank, es, info->level_flops[l], info->level_bytes[l]);
+        level_work(P, st.rank, es, info->level_flops[l], info->level_bytes[l], &st.kw);
       }
       if (hstatus[0] != 0) {
         ret = static_cast<ce_status>(hstatus[0]);
@@ -1278,12 +1335,13 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       int64_t bytes = coarse_elems * 8 + tot * 8;
       for (auto& st : F->levels) bytes += st.fac_bytes + st.meta_bytes;
       F->bytes = bytes;
-      int lstat[32];
+      int lstat[ce::kStatsWords];
       check(cudaMemcpy(lstat, F->d_status + ce::kStatusWords, sizeof(lstat), cudaMemcpyDeviceToHost), "D2H");
       if (info) {
         for (int l = 0; l < 16; ++l) {
           info->learned_rows[l] = lstat[2 * l];
           info->fallback_rows[l] = lstat[2 * l + 1];
+          info->jacobi_capped[l] = lstat[32 + l];
         }
         info->levels_done = (int)F->levels.size();
         info->coarse_n = F->nc;
@@ -1340,6 +1398,9 @@ ce_status ce_autotune(ce_csb* A, const ce_opts* o_in, double* level_ms) {
   ce_opts o;
   ce_opts_default(&o);
   if (o_in) o = *o_in;
+  if ((o.precision != CE_PREC_FP64 && o.precision != CE_PREC_FP32) ||
+      (o.rank_mode != CE_RANK_SVD && o.rank_mode != CE_RANK_LEARNED))
+    return CE_ERR_INVALID_ARG;
   // configurations: CTA shape x (learned compression on | exact SVD), the
   // latter only when a rank model is given
   constexpr int kShapes = 3, kReps = 3;
@@ -1371,12 +1432,12 @@ ce_status ce_autotune(ce_csb* A, const ce_opts* o_in, double* level_ms) {
   {
     // the heuristic's shape per level, kept unless another is clearly faster
     o.row_shape = -1;
-    const int saved = A->tuned_levels;
-    A->tuned_levels = 0;
+    const int saved = A->tuned_levels[o.precision][o.rank_mode];
+    A->tuned_levels[o.precision][o.rank_mode] = 0;
     ce_factor* F = nullptr;
     ce_info info;
     ce_status st = ce_factorize(A, &o, &F, &info);
-    A->tuned_levels = saved;
+    A->tuned_levels[o.precision][o.rank_mode] = saved;
     if (st != CE_OK) return st;
     ce_factor_destroy(F);
     for (int l = 0; l < 16; ++l) heur[l] = info.row_shape[l];
@@ -1389,12 +1450,10 @@ ce_status ce_autotune(ce_csb* A, const ce_opts* o_in, double* level_ms) {
           bm = md;
           bs = sh;
         }
-    A->tuned_shape[l] = bs;
-    A->tuned_learned[l] = learned && bm == 0;
+    A->tuned_shape[o.precision][o.rank_mode][l] = bs;
+    A->tuned_learned[o.precision][o.rank_mode][l] = learned && bm == 0;
   }
-  A->tuned_levels = nl;
-  A->tuned_prec = o.precision;
-  A->tuned_rank = o.rank_mode;
+  A->tuned_levels[o.precision][o.rank_mode] = nl;
   if (level_ms)
     for (int md = 0; md < 2; ++md)
       for (int sh = 0; sh < kShapes; ++sh)
@@ -1467,7 +1526,13 @@ ce_status pcg_solve(const ce_csb* A, const ce_factor* F, const double* b_dev, do
   if (A->nsys > 1) return pcg_solve_batched(A, F, b_dev, x_dev, rtol, maxit, nullptr, nullptr, nullptr, info, stream);
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const int64_t n = A->n;
-  const int nparts = static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 4));
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                 cudaSuccess || sms <= 0) {
+    g_last_error = "pcg_solve: cannot read the device's SM count";
+    return CE_ERR_CUDA;
+  }
+  const int nparts = static_cast<int>(std::min<int64_t>((n + 255) / 256, (int64_t)sms * 4));
   double *r = nullptr, *z = nullptr, *p = nullptr, *Ap = nullptr, *part = nullptr, *scal = nullptr;
   ce_status ret = CE_OK;
   if (info) std::memset(info, 0, sizeof(*info));
@@ -1554,6 +1619,80 @@ ce_status ce_factor_get_level(const ce_factor* F, int level, int32_t* n, int32_t
   if (colour) std::copy(st.plan->colour.begin(), st.plan->colour.end(), colour);
   if (tau) {
     cudaError_t e = cudaMemcpy(tau, st.dev.tau, st.plan->M * sizeof(double), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) {
+      g_last_error = cudaGetErrorString(e);
+      return CE_ERR_CUDA;
+    }
+  }
+  return CE_OK;
+}
+
+ce_status ce_debug_wait_expiry(int kernel, double limit_ms, int32_t* status_out, void* stream) {
+  if ((kernel != 0 && kernel != 1) || !(limit_ms > 0) || limit_ms > 2000 || !status_out) return CE_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  LevelStore st;
+  void* pool = nullptr;
+  int* status = nullptr;
+  int* apply_state = nullptr;
+  double* vec = nullptr;
+  ce_status ret = CE_OK;
+  try {
+    // two blocks of 4 rows coupled by one close pair: block 1 has the higher
+    // colour and waits for block 0, which is never queued
+    auto P = std::make_shared<LevelPlan>();
+    ce::plan_level(*P, {4, 4}, {{0, 1}}, true);
+    if (P->order.size() != 2 || P->order[1] != 1 || P->dep_ptr[2] - P->dep_ptr[1] != 1)
+      throw std::logic_error("unexpected two-block plan");
+    st.plan = P;
+    build_level_store(st, 8, s);
+    std::vector<double> hp(P->pool_elems, 0.0);
+    for (int i = 0; i < 2; ++i)
+      for (int a = 0; a < 4; ++a) hp[P->diag_off[i] + a * 4 + a] = 4.0;
+    pool = dalloc(hp.size() * sizeof(double), s);
+    check(cudaMemcpyAsync(pool, hp.data(), hp.size() * sizeof(double), cudaMemcpyHostToDevice, s), "H2D");
+    status = static_cast<int*>(dalloc((ce::kStatusWords + ce::kStatsWords) * sizeof(int), s));
+    check(cudaMemsetAsync(status, 0, (ce::kStatusWords + ce::kStatsWords) * sizeof(int), s), "memset");
+    LevelDev D = st.dev;
+    D.pool = pool;
+    D.order += 1;                       // only block 1 is queued
+    D.wait_ns = static_cast<unsigned long long>(limit_ms * 1e6);
+    if (kernel == 0) {
+      ce::LearnedArgs la;
+      check(ce::launch_row_kernel(8, D, 1, 0, 1e-3, CE_TOL_REL, status, P->nmax, 0, la, s), "row kernel");
+    } else {
+      apply_state = static_cast<int*>(dalloc(4 * sizeof(int), s));
+      const int init[4] = {0, 0, 1, 0};  // queue counters, epoch 1 (block 0's flag stays 0)
+      check(cudaMemcpyAsync(apply_state, init, sizeof(init), cudaMemcpyHostToDevice, s), "H2D");
+      D.aq = apply_state;
+      D.epoch = apply_state + 2;
+      D.M = 1;
+      vec = static_cast<double*>(dalloc(P->vec_len * sizeof(double), s));
+      check(cudaMemsetAsync(vec, 0, P->vec_len * sizeof(double), s), "memset");
+      check(ce::launch_apply_fwd(8, D, vec, status, s), "apply");
+    }
+    check(cudaMemcpyAsync(status_out, status, ce::kStatusWords * sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
+    check(cudaStreamSynchronize(s), "sync");
+  } catch (...) {
+    ret = status_of_exception();
+  }
+  cudaStreamSynchronize(s);
+  dfree(st.meta, s);
+  dfree(st.smeta, s);
+  dfree(st.fac, s);
+  dfree(pool, s);
+  dfree(status, s);
+  dfree(apply_state, s);
+  dfree(vec, s);
+  return ret;
+}
+
+ce_status ce_factor_get_features(const ce_factor* F, int level, float* feat, int32_t* kw) {
+  if (!F || level < 0 || level >= static_cast<int>(F->levels.size())) return CE_ERR_INVALID_ARG;
+  const LevelStore& st = F->levels[level];
+  if (kw) std::copy(st.kw.begin(), st.kw.end(), kw);
+  if (feat) {
+    cudaError_t e = cudaMemcpy(feat, st.dev.feat, (size_t)st.plan->M * ce::kMlpFeatures * sizeof(float),
+                               cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) {
       g_last_error = cudaGetErrorString(e);
       return CE_ERR_CUDA;

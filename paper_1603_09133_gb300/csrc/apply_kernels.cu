@@ -263,14 +263,13 @@ __device__ __forceinline__ unsigned long long globaltimer_ns() {
   return t;
 }
 
-constexpr unsigned long long kWaitNs = 2000000000ull;  // a dependency wait gives up after 2 s
-constexpr int kWaitPolls = 1 << 24;                    // ... or after this many polls
+constexpr int kWaitPolls = 1 << 24;  // a dependency wait gives up after wait_ns or this many polls
 
 // Warp-wide wait until flag[idx[d]] == want for every d in [d0, d1): each
 // lane polls its own flags, the warp votes.  Ends early (false) on a
-// recorded error or after kWaitNs / kWaitPolls, recording reason 6.
+// recorded error or after wait_ns / kWaitPolls, recording reason 6.
 __device__ bool wait_flags(const int* flag, const int* idx, int d0, int d1, int want, int* status, int row,
-                           int lane) {
+                           int lane, unsigned long long wait_ns) {
   const unsigned long long t0 = globaltimer_ns();
   int polls = 0;
   for (int base = d0; base < d1; base += 32) {
@@ -283,7 +282,7 @@ __device__ bool wait_flags(const int* flag, const int* idx, int d0, int d1, int 
       if (lane == 0) {
         if (ld_acquire(status) != 0)
           bad = 1;
-        else if (++polls > kWaitPolls || globaltimer_ns() - t0 > kWaitNs)
+        else if (++polls > kWaitPolls || globaltimer_ns() - t0 > wait_ns)
           bad = 2;
         if (bad == 2 && atomicCAS(status, 0, CE_ERR_CUDA) == 0) {
           status[2] = row;
@@ -327,7 +326,7 @@ __global__ void __launch_bounds__(NT) apply_level_kernel(LevelDev L, double* vec
       q = __shfl_sync(0xffffffffu, q, 0);
       if (q >= 0) {
         const int i = L.order[kFwd ? q : count - 1 - q];
-        if (!wait_flags(flag, di, dp[i], dp[i + 1], ep, status, i, lane)) q = -1;
+        if (!wait_flags(flag, di, dp[i], dp[i + 1], ep, status, i, lane, L.wait_ns)) q = -1;
       }
       if (lane == 0) s_q = q;
     }
@@ -690,7 +689,7 @@ cudaError_t launch_level_move(const LevelDev& L, double* cur, double* next, int 
 cudaError_t launch_perm(const int32_t* perm, int64_t n, const double* in, double* out, int gather,
                         cudaStream_t s) {
   if (n <= 0) return cudaSuccess;
-  const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 8));
+  const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, (int64_t)device_sms() * 8));
   g_launches.fetch_add(1, std::memory_order_relaxed);
   perm_kernel<<<grid, 256, 0, s>>>(perm, n, in, out, gather);
   return cudaGetLastError();
@@ -766,7 +765,7 @@ cudaError_t launch_update_xr(int64_t n, double* x, double* r, const double* p, c
 
 cudaError_t launch_update_p(int64_t n, double* p, const double* z, const double* scal, int first,
                             cudaStream_t s) {
-  const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, 152 * 8));
+  const int grid = static_cast<int>(std::min<int64_t>((n + 255) / 256, (int64_t)device_sms() * 8));
   g_launches.fetch_add(1, std::memory_order_relaxed);
   update_p_kernel<<<grid, 256, 0, s>>>(n, p, z, scal, first);
   return cudaGetLastError();

@@ -196,7 +196,11 @@ struct LevelDev {
   int* fdone;           // per row: epoch of the last forward apply step done
   int* bdone;           // ... and of the last backward step
   int* aq;              // queue counters of the apply launches (fwd, bwd)
+  float* feat;          // per row: the rank model's features (learned levels)
+  int* kw;              // per row: sketch width k of the learned compression
+                        // (k accepted, -k rejected for the exact SVD, 0 none)
   const int* epoch;     // epoch of the running apply
+  unsigned long long wait_ns;  // a row's wait for its neighbours gives up after this long
   void* pool;           // pair values (T)
   void* U;              // factor (T): U_i
   void* L;              //   L_hat_i^{-1} (m_i x m_i, lower)
@@ -213,6 +217,7 @@ struct StaticMeta {
 struct LevelStore {
   std::shared_ptr<const LevelPlan> plan;  // level 1 may share the csb's plan
   std::vector<int> rank;        // host copy
+  std::vector<int> kw;          // host copy of the per-row sketch widths
   LevelDev dev{};
   void* meta = nullptr;         // device per-factorization state (ranks, flags, ...)
   void* smeta = nullptr;        // device arrays fixed by the plan (null: shared)
@@ -241,11 +246,11 @@ struct ce_csb {
   int32_t* d_perm = nullptr;
   // level-1 plan and the scatter map nnz -> element of the level-1 pool
   std::shared_ptr<ce::LevelPlan> plan1;
-  // row-kernel CTA shape per level chosen by ce_autotune (for one precision
-  // and rank mode)
-  int tuned_levels = 0, tuned_prec = -1, tuned_rank = -1;
-  int tuned_shape[16] = {};
-  int tuned_learned[16] = {};    // learned compression measured faster on level l
+  // row-kernel CTA shape per level chosen by ce_autotune, one choice per
+  // precision (CE_PREC_*) and rank mode (CE_RANK_*)
+  int tuned_levels[2][2] = {};
+  int tuned_shape[2][2][16] = {};
+  int tuned_learned[2][2][16] = {};  // learned compression measured faster on level l
   int64_t* d_scatter = nullptr;
   // level-1 plan's fixed arrays on the device, shared by every factorization
   void* d_meta1 = nullptr;

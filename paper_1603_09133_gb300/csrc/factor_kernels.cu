@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(256) syrk_tile_kernel(double* A, const int64_t
 cudaError_t launch_scatter_csr(int esize, const int64_t* scatter, const double* val, int64_t nnz,
                                void* pool, cudaStream_t s) {
   if (nnz <= 0) return cudaSuccess;
-  const int grid = static_cast<int>(std::min<int64_t>((nnz + 255) / 256, 152 * 16));
+  const int grid = static_cast<int>(std::min<int64_t>((nnz + 255) / 256, (int64_t)device_sms() * 16));
   g_launches.fetch_add(1, std::memory_order_relaxed);
   if (esize == 8)
     scatter_csr_kernel<double><<<grid, 256, 0, s>>>(scatter, val, nnz, (double*)pool);

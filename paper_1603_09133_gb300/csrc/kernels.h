@@ -17,6 +17,19 @@ extern std::atomic<int64_t> g_launches;
 // text returned by ce_last_error() on this thread
 void set_last_error(const std::string& msg);
 
+// SMs of the current device (read once per host thread; 1 if unreadable, so
+// a grid sized from it stays valid)
+inline int device_sms() {
+  thread_local int sms = 0;
+  if (sms <= 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+      sms = 1;
+  }
+  return sms;
+}
+
 // status word layout: [0] = ce_status code, [1] = level, [2] = block,
 // [3] = reason (1 pivot <= 0, 2 non-finite sigma), [4] = pivot index,
 // [6..7] = pivot value (double bits)
@@ -28,8 +41,14 @@ struct LearnedArgs {
   int oversample = 8;             // p: sketch width k = r_hat + p
   int J = 4;                      // children per super-block (parent-rank feature)
   unsigned long long seed = 0;    // key of the counter-based sketch generator
-  int* stats = nullptr;           // per level: [rows accepted, rows sent to the exact SVD]
+  int* stats = nullptr;           // kStatsWords counters, see below
 };
+
+// per-level counters of a factorization (levels 0..15): [2 l] rows whose
+// sketch was accepted, [2 l + 1] rows sent to the exact SVD, [32 + l] rows
+// whose Jacobi iteration reached its sweep cap before every pair was
+// orthogonal (their singular values are still used)
+constexpr int kStatsWords = 48;
 
 // All `count` rows of a level (order[0, count)) in one persistent launch;
 // shape 0: 256-thread CTAs with a 72 KB budget, 1: 512-thread CTAs with the
@@ -82,6 +101,10 @@ cudaError_t mlp_adam_step(const float* X, const float* t, int ns, float* theta, 
 int mlp_partial_blocks(int ns);
 cudaError_t mlp_pack(const float* theta, void* model, cudaStream_t s);
 cudaError_t mlp_predict(const float* X, int ns, const void* model, float* out, cudaStream_t s);
+
+// arithmetic peak probes (probes.cu): 0 FP32 FFMA, 1 FP64 DFMA, 2 TF32
+// mma.sync m16n8k8, 3 the 3xTF32 product (three TF32 MMAs per product)
+cudaError_t measure_peak(int kind, double* tflops, cudaStream_t s);
 
 cudaError_t launch_update_p(int64_t n, double* p, const double* z, const double* scal,
                             int first, cudaStream_t s);

@@ -14,12 +14,15 @@
 // call's contents; calls whose work overlaps on the GPU (other streams, other
 // host threads) race on it.  Nothing in it needs clearing: every entry is
 // written before it is read within a call.
+//
+// One system per call: a batch handle (csb_build_batched with more than one
+// system) is rejected, because pcg_solve runs a separate CG recurrence per
+// system there while this entry point has room for one recurrence only.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "kernels.h"
@@ -29,29 +32,18 @@ namespace {
 constexpr int64_t kNoAllocMaxN = 65536;
 constexpr int kNoAllocParts = 256;
 constexpr int64_t kScratchDoubles = 4 * kNoAllocMaxN + kNoAllocParts + 8;
-constexpr int kMaxDevices = 64;
-
 static __device__ __align__(256) double g_pcg_scratch[kScratchDoubles];
 
-std::mutex g_scratch_mu;
-double* g_scratch_ptr[kMaxDevices] = {};
-
 // Device address of the static array on the current device.  Host code only
-// sees a host-side stand-in under the array's name, so the address is looked up
-// once per device (with that device current) and cached.
+// sees a host-side stand-in under the array's name, so the address is looked
+// up with the caller's device current.  It is looked up on every call (the
+// lookup allocates nothing): a cached address would dangle after a
+// cudaDeviceReset reloads the module.
 cudaError_t scratch_for_current_device(double** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_pcg_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lk(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_pcg_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<double*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+  *out = static_cast<double*>(p);
   return cudaSuccess;
 }
 
@@ -72,13 +64,22 @@ extern "C" ce_status pcg_solve_noalloc(const ce_csb* A, const ce_factor* F, cons
                                        double* x_dev, double rtol, int maxit, ce_pcg_info* info,
                                        void* stream) {
   if (!A || !F || !b_dev || !x_dev || maxit < 0 || rtol < 0 || A->n != F->N) return CE_ERR_INVALID_ARG;
-  const int64_t n = A->n;
-  if (n > kNoAllocMaxN) {
-    ce::set_last_error("pcg_solve_noalloc: n = " + std::to_string(n) +
-                       " exceeds the static work-array limit of " + std::to_string(kNoAllocMaxN) +
-                       " unknowns");
-    return CE_ERR_LIMIT;
+  try {  // the messages below build strings: no host exception crosses the C ABI
+    if (A->nsys > 1) {
+      ce::set_last_error("pcg_solve_noalloc: a batch of independent systems needs one CG recurrence per "
+                         "system; use pcg_solve_batched");
+      return CE_ERR_INVALID_ARG;
+    }
+    if (A->n > kNoAllocMaxN) {
+      ce::set_last_error("pcg_solve_noalloc: n = " + std::to_string(A->n) +
+                         " exceeds the static work-array limit of " + std::to_string(kNoAllocMaxN) +
+                         " unknowns");
+      return CE_ERR_LIMIT;
+    }
+  } catch (...) {
+    return A->nsys > 1 ? CE_ERR_INVALID_ARG : CE_ERR_LIMIT;
   }
+  const int64_t n = A->n;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   if (info) std::memset(info, 0, sizeof(*info));
   ce_status ret = CE_OK;
@@ -140,7 +141,9 @@ extern "C" ce_status pcg_solve_noalloc(const ce_csb* A, const ce_factor* F, cons
       info->converged = conv ? 1 : 0;
     }
     if (!conv) ret = CE_ERR_NO_CONVERGENCE;
-  } catch (const Fail& f) {
+  } catch (const Fail&) {
+    if (ret == CE_OK) ret = CE_ERR_CUDA;
+  } catch (...) {  // host exceptions (string building) never cross the C ABI
     if (ret == CE_OK) ret = CE_ERR_CUDA;
   }
   return ret;

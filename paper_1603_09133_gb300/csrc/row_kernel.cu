@@ -512,6 +512,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
       s_x[10] = -log10f(fmaxf(static_cast<float>(tol), 1e-30f)) / 8.f;
     }
     __syncthreads();
+    if (L.feat != nullptr && tid < kMlpFeatures) L.feat[(int64_t)i * kMlpFeatures + tid] = s_x[tid];
     if (warp == 0) {
       const float yh = mlp_infer_warp(la.model, s_x, s_h);
       if (lane == 0) {
@@ -523,6 +524,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     __syncthreads();
     const int k = s_k;
     const int kk = k + 2;
+    const bool lvl_ok = level < 16 && la.stats != nullptr;
     const int UNE = max(QW * per_warp, 4 * NL);          // union size (elements)
     const int LK = (k & 1) ? k : k + 1;                  // leading dimension of k-wide buffers
     const int pwl = k * LK + kChunk * LD + kChunk * LK + 64;  // per warp: R, rows of F^T, projected rows
@@ -679,6 +681,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
         const int nb = k + (k & 1), npairs = nb / 2;
         const int half = lane >> 4, hl = lane & 15;
         const T tolJ = T(k) * Eps<T>::v, tolJ2 = tolJ * tolJ;
+        bool jconv = false;
         for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
           // same negligible-pair rule as the exact path, with k columns
           for (int j = warp; j < k; j += kWarpsNT) {
@@ -747,8 +750,12 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
           }
           const int rotated = s_flag;
           __syncthreads();
-          if (!rotated) break;
+          if (!rotated) {
+            jconv = true;
+            break;
+          }
         }
+        if (!jconv && tid == 0 && lvl_ok) atomicAdd(la.stats + 32 + level, 1);
       }
       for (int j = tid; j < k; j += NT) {
         T sv = 0;
@@ -849,13 +856,16 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
         r = rl;
         tau = static_cast<double>(sig_tmp[0]);
         have_u = true;
-        if (tid == 0 && la.stats) atomicAdd(la.stats + 2 * level, 1);
-      } else if (tid == 0 && la.stats) {
-        atomicAdd(la.stats + 2 * level + 1, 1);
+        if (tid == 0 && lvl_ok) atomicAdd(la.stats + 2 * level, 1);
+        if (tid == 0 && L.kw) L.kw[i] = k;
+      } else if (tid == 0) {
+        if (lvl_ok) atomicAdd(la.stats + 2 * level + 1, 1);
+        if (L.kw) L.kw[i] = -k;
       }
       __syncthreads();
-    } else if (tid == 0 && la.stats) {
-      atomicAdd(la.stats + 2 * level + 1, 1);
+    } else if (tid == 0) {
+      if (lvl_ok) atomicAdd(la.stats + 2 * level + 1, 1);
+      if (L.kw) L.kw[i] = 0;
     }
   }
 
@@ -900,6 +910,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     for (int w = 0; w < kWarpsNT; ++w) dn2 += s_red[w];
     const double floor_tau = static_cast<double>(Eps<T>::v) * sqrt(dn2);
     const T floor_tau_t = static_cast<T>(floor_tau);
+    bool jconv = false;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
       // Columns whose norm stays below tau_est / (2 sqrt n) form a group whose
       // singular values are all below tau / 2: rotating two of them changes
@@ -974,8 +985,12 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
       }
       const int rotated = s_flag;
       __syncthreads();
-      if (!rotated) break;
+      if (!rotated) {
+        jconv = true;
+        break;
+      }
     }
+    if (!jconv && tid == 0 && level < 16 && la.stats) atomicAdd(la.stats + 32 + level, 1);
     for (int j = tid; j < n; j += NT) {
       T s = 0;
       for (int row = 0; row < n; ++row) s += X[row * LD + j] * X[row * LD + j];
@@ -1253,8 +1268,7 @@ __device__ __forceinline__ void st_release(int* p, int v) {
   asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-constexpr unsigned long long kDepWaitNs = 2000000000ull;  // give up a dependency wait after 2 s
-constexpr int kDepWaitPolls = 1 << 24;                    // ... or after this many polls
+constexpr int kDepWaitPolls = 1 << 24;  // a dependency wait gives up after L.wait_ns or this many polls
 
 // Persistent level kernel.  CTAs take rows in the colour-major elimination
 // order from one counter; before row i starts, every row of a lower colour
@@ -1294,7 +1308,7 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : NT >= 256 ? 3 : 6))
             if (lane == 0) {
               if (ld_acquire(status) != 0)
                 bad = 1;
-              else if (++polls > kDepWaitPolls || globaltimer_ns() - t0 > kDepWaitNs)
+              else if (++polls > kDepWaitPolls || globaltimer_ns() - t0 > L.wait_ns)
                 bad = 2;
               if (bad == 2) set_status(status, CE_ERR_CUDA, level, i, 5);
             }

@@ -76,6 +76,14 @@ def test_csb_build_rejects_bad_input(lib):
                          None) == _lib.CE_ERR_INVALID_ARG
 
 
+def test_wait_expiry_hook_validates_before_any_cuda_call(lib):
+    status = np.zeros(8, np.int32)
+    for kernel, ms in ((2, 20.0), (0, 0.0), (0, 5000.0), (1, -1.0)):
+        assert lib.ce_debug_wait_expiry(kernel, ms, status.ctypes.data_as(_lib.I32P), None) == \
+            _lib.CE_ERR_INVALID_ARG
+    assert lib.ce_debug_wait_expiry(0, 20.0, None, None) == _lib.CE_ERR_INVALID_ARG
+
+
 def test_strerror(lib):
     for s in range(7):
         assert lib.ce_strerror(s)

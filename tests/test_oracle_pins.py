@@ -452,3 +452,39 @@ def test_pcg_is_the_library_cg():
         xs, _ = spla.cg(w.A, w.b, x0=np.zeros(N), rtol=1e-14, atol=0.0, maxiter=k)
         res = ce.pcg(w.A, None, w.b, 1e-14, k, precond=lambda r: r)
         assert np.linalg.norm(xs - res.x) <= 1e-12 * np.linalg.norm(res.x), k
+
+
+@pytest.mark.parametrize("kind", ["poisson2d", "poisson3d"])
+def test_dropped_block_is_the_truncated_svd_tail(kind):
+    """The compression step of Section 2.2 drops E_i = U_i[:, r:]^T F_i with
+    ||E_i||_2 < eps: recomputed from the stored U_i and the far blocks as they
+    stood before the step, ||E_i||_2 equals sigma_{r+1}(F_i) (the tail of the
+    SVD, so basis and non-basis columns are not swapped) and is at most tau_i,
+    while the kept rows U_i[:, :r]^T F_i keep every singular value above tau_i."""
+    if kind == "poisson2d":
+        w = wl.make_workload("poisson2d_64_B16")
+        A, perm, B, tol, levels, J = w.A, w.perm, w.B, w.tol, w.levels, w.J
+    else:
+        A = wl.poisson3d(16)
+        perm = wl.box_perm((16, 16, 16), (4, 4, 4))
+        B, tol, levels, J = 64, 1e-4, 2, 8
+    F = ce.factorize(A, perm, B, tol, levels, J, record_rows=True)
+    checked = 0
+    for lev in F.levels:
+        for st in lev.steps:
+            D, Cs, Fs = st.row
+            if not Fs or st.sigma.size == 0:
+                continue
+            Fi = np.hstack(Fs)
+            U, r = st.U, st.r
+            assert np.abs(U.T @ U - np.eye(st.n)).max() < 1e-13
+            E = U[:, r:].T @ Fi
+            e2 = np.linalg.norm(E, 2) if E.size else 0.0
+            tail = st.sigma[r] if r < st.sigma.size else 0.0
+            assert abs(e2 - tail) <= 1e-12 * st.sigma[0] + 1e-13, (e2, tail)
+            assert e2 <= st.tau
+            if r > 0:
+                kept = np.linalg.svd(U[:, :r].T @ Fi, compute_uv=False)
+                assert kept.size == r and kept[-1] > st.tau
+            checked += 1
+    assert checked > 20
