@@ -87,6 +87,13 @@ typedef struct {
                       1: 512 threads, all shared memory; 2: 128 threads,
                       40 KB                                              */
   int rank;        /* r of CE(r) (CE_TOL_FIXED only; >= 0, default 16)    */
+  int nmax;        /* super-block cap: a run of J blocks whose sizes add up
+                      to more than nmax rows is halved until its parts fit
+                      (0, the default: plain runs of J blocks, the paper's
+                      rule of Section 2.4)                                 */
+  int record_features; /* 1: every row with far columns records the rank
+                      model's features (ce_factor_get_features), also on
+                      levels that run the exact SVD (default 0)           */
 } ce_opts;
 
 typedef struct {
@@ -97,9 +104,9 @@ typedef struct {
                           2: non-finite singular values of F_i;
                           5: a row's wait for its neighbours timed out
                           (CE_ERR_CUDA; never expected);
-                          CE_ERR_LIMIT: 3 a block over 64 rows, 4 a row
-                          with over 32 close blocks, 7 a row with over 128
-                          far blocks (err_pivot: the size or count)      */
+                          CE_ERR_LIMIT: 3 a block over 1536 rows, 4 a
+                          row with over 63 close blocks (err_pivot: the
+                          size or count)                                 */
   int err_pivot;
   double err_value;
   int coarse_n;        /* size of the dense remainder A_K                 */
@@ -126,6 +133,8 @@ typedef struct {
                           speculative planning of level l+1 guessed wrong
                           (0: the pattern planned during the GPU work is
                           kept; otherwise it is planned again)            */
+  int big_rows[16];    /* 1: level l ran the large-row path (blocks over 64
+                          rows, or over 32 close / 128 far blocks)        */
   int jacobi_capped[16]; /* rows of level l whose Jacobi SVD stopped at its
                           sweep cap (40 sweeps) with a pair still above the
                           orthogonality threshold; their singular values
@@ -140,7 +149,7 @@ typedef struct {
 
 /* Defaults: tol 1e-4, CE_TOL_REL, levels 4, J 4, FP64, colouring on,
  * CE_RANK_SVD, oversample 8, seed 0, row_shape -1 (autotuned, else a
- * heuristic), rank 16. */
+ * heuristic), rank 16, nmax 0 (no super-block cap), record_features 0. */
 void ce_opts_default(ce_opts* o);
 
 /*
@@ -227,10 +236,15 @@ ce_status ce_factorize_batched(const ce_csb* A, const ce_opts* o,
  *   o     options (NULL = defaults)
  *   out   receives the factor
  *   info  optional, filled on success and on CE_ERR_NOT_SPD
- * Synchronizes the stream once per level (the next level's layout depends
- * on the ranks).  CE_ERR_LIMIT if a block grows beyond 64 rows, a row has
- * more than 32 close or 128 far blocks.  The factor uses device memory of A
- * (the permutation and the level-1 plan): destroy the factor before A.
+ * Levels whose blocks outgrow the persistent row kernel (more than 64 rows,
+ * more than 32 close or 128 far blocks; 3D super-blocks) run the large-row
+ * path: one colour at a time, the steps of its rows as batched kernels with
+ * the row matrices in global memory (GEMM-shaped products on a grouped GEMM),
+ * synchronizing the stream once per colour.  Otherwise the stream is
+ * synchronized once per level (the next level's layout depends on the
+ * ranks).  CE_ERR_LIMIT if a block grows beyond 1536 rows or a row has more
+ * than 63 close blocks.  The factor uses device memory of A (the permutation
+ * and the level-1 plan): destroy the factor before A.
  */
 ce_status ce_factorize(const ce_csb* A, const ce_opts* o, ce_factor** out,
                        ce_info* info);
@@ -481,7 +495,7 @@ ce_status ce_plan_level1_deps(int64_t n, const int64_t* rowptr, const int32_t* c
  * squared pattern with non-empty ranks on both sides lies inside it, and the
  * distance-2 colouring of that pattern.  Arguments as ce_plan_level1, plus
  *   rank         host, ceil(n/B) entries, 0 <= r_i <= n_i (level-1 ranks)
- *   J, nmax      as ce_plan_groups (ce_factorize: nmax = 64)
+ *   J, nmax      as ce_plan_groups (0: no cap)
  *   next_n       host, room for ceil(n/B) entries (may be NULL): sizes
  *   next_colour  host, room for ceil(n/B) entries (may be NULL)
  *   next_M       number of level-2 blocks
@@ -512,9 +526,9 @@ ce_status ce_plan_level1_work(int64_t n, const int64_t* rowptr, const int32_t* c
 /*
  * ce_plan_groups -- host-only (no CUDA call): the super-blocks that
  * ce_factorize forms from one level's blocks (Section 2.4).  Runs of J
- * consecutive blocks join; a run whose ranks add up to more than nmax rows is
- * halved, first half ceil(len/2) blocks, recursively, until every part fits or
- * is one block (ce_factorize uses nmax = 64, the row kernel's limit).
+ * consecutive blocks join; with nmax > 0 a run whose ranks add up to more
+ * than nmax rows is halved, first half ceil(len/2) blocks, recursively, until
+ * every part fits or is one block (ce_factorize: ce_opts.nmax; 0 = no cap).
  *   M            blocks of the level
  *   rank         host, M kept sizes r_i (>= 0)
  *   first_child  host, room for M + 1 entries: super-block I holds blocks

@@ -370,14 +370,14 @@ def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
 
 def _groups(size, J, nmax=None):
     """Super-blocks as ranges [a, b) of consecutive blocks: runs of J blocks
-    join (Section 2.4).  With ``nmax``, a run whose sizes add up to more than
-    nmax rows is halved (first half ceil(len/2) blocks), recursively, until
+    join (Section 2.4).  With ``nmax`` (None or 0: no cap), a run whose sizes
+    add up to more than nmax rows is halved (first half ceil(len/2) blocks), recursively, until
     every part fits or is a single block, so the parts stay aligned with the
     runs of J (geometric siblings under the box ordering)."""
     M, groups = len(size), []
 
     def split(a, b):
-        if b - a == 1 or nmax is None or sum(size[a:b]) <= nmax:
+        if b - a == 1 or nmax is None or nmax <= 0 or sum(size[a:b]) <= nmax:
             groups.append((a, b))
             return
         mid = a + (b - a + 1) // 2
@@ -475,8 +475,8 @@ def factorize(A, perm, B, tol, levels, J=4, tol_mode="rel", order="colour",
     ``nmax`` caps the super-block size: a run of J consecutive blocks whose
     sizes add up to more than nmax rows is halved (first half ceil(len/2)
     blocks), recursively, until every part fits or is a single block
-    (``_groups``).  ``nmax=None`` (the default) is the paper's rule of plain
-    runs of J blocks (Section 2.4).
+    (``_groups``).  ``nmax=None`` or 0 (the default) is the paper's rule of
+    plain runs of J blocks (Section 2.4).
 
     ``record_rows`` keeps, for every step, the blocks D_i, C_ik and F_ik of
     its row as they stood before compression (memory grows with the problem;

@@ -278,7 +278,7 @@ def _prec(precision):
 
 
 def _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed,
-          row_shape, rank=16):
+          row_shape, rank=16, nmax=0, record_features=False):
     lib = _lib.load()
     o = _lib.ce_opts()
     lib.ce_opts_default(C.byref(o))
@@ -298,17 +298,20 @@ def _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, ove
         o.oversample = int(oversample)
         o.seed = int(seed)
     o.row_shape = int(row_shape)
+    o.nmax = int(nmax)
+    o.record_features = 1 if record_features else 0
     return o
 
 
 def ce_autotune(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",
-                coloring=True, stream=None, rank_model=None, oversample=8, seed=0):
+                coloring=True, stream=None, rank_model=None, oversample=8, seed=0, nmax=0):
     """Time every row-kernel CTA shape per level (and, with a rank model,
     learned compression against the exact SVD) and keep the fastest in the
     csb; returns the [learned/exact][shape][level] times (ms) as a
     2 x 3 x levels array (the exact half is zero without a rank model)."""
     lib = _lib.load()
-    o = _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed, -1)
+    o = _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed, -1,
+              nmax=nmax)
     t = np.zeros(2 * 3 * 16, np.float64)
     _check(lib.ce_autotune(csb.handle, C.byref(o), t.ctypes.data_as(_lib.DP)), "ce_autotune")
     return t.reshape(2, 3, 16)[:, :, :levels]
@@ -316,16 +319,20 @@ def ce_autotune(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="r
 
 def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",
                  coloring=True, stream=None, rank_model=None, oversample=8, seed=0,
-                 row_shape=-1, batched=False, rank=16) -> Factor:
+                 row_shape=-1, batched=False, rank=16, nmax=0, record_features=False) -> Factor:
     """Algorithm 1 on the device; returns the factor (raises CEError).
 
     ``rank_model`` (a :class:`RankModel`) switches the compression step to the
     learned rank + randomized range finder with exact-SVD fallback.
     ``tol_mode="fixed"`` is CE(r) with r = ``rank`` (``tol`` unused).
+    ``nmax`` > 0 caps the super-blocks at nmax rows (runs of J halved until
+    they fit); 0 is the paper's plain runs of J.  ``record_features`` keeps the
+    rank model's features of every row (Factor.features), also without a
+    model.
     """
     lib = _lib.load()
     o = _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed,
-              row_shape, rank)
+              row_shape, rank, nmax, record_features)
     info = _lib.ce_info()
     h = C.c_void_p()
     entry = lib.ce_factorize_batched if batched else lib.ce_factorize

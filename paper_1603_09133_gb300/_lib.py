@@ -42,6 +42,8 @@ class ce_opts(C.Structure):
         ("seed", C.c_uint64),
         ("row_shape", C.c_int),
         ("rank", C.c_int),
+        ("nmax", C.c_int),
+        ("record_features", C.c_int),
     ]
 
 
@@ -69,6 +71,7 @@ class ce_info(C.Structure):
         ("row_shape", C.c_int * 16),
         ("row_learned", C.c_int * 16),
         ("spec_miss", C.c_int * 16),
+        ("big_rows", C.c_int * 16),
         ("jacobi_capped", C.c_int * 16),
     ]
 

@@ -594,6 +594,8 @@ void ce_opts_default(ce_opts* o) {
   o->seed = 0;
   o->row_shape = -1;
   o->rank = 16;
+  o->nmax = 0;
+  o->record_features = 0;
 }
 
 const char* ce_strerror(ce_status s) {
@@ -1067,7 +1069,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       (o.tol_mode == CE_TOL_FIXED && (o.rank < 0 || o.rank_mode != CE_RANK_SVD)) ||
       (o.rank_mode != CE_RANK_SVD && o.rank_mode != CE_RANK_LEARNED) ||
       (o.rank_mode == CE_RANK_LEARNED && (!o.rank_model || o.oversample < 0)) || o.row_shape < -1 ||
-      o.row_shape > 2)
+      o.row_shape > 2 || o.nmax < 0)
     return CE_ERR_INVALID_ARG;
   // CE(r): the row kernel takes r in place of the tolerance
   if (o.tol_mode == CE_TOL_FIXED) o.tol = static_cast<double>(o.rank);
@@ -1098,6 +1100,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
     la.J = o.J;
     la.seed = o.seed;
     la.stats = F->d_status + ce::kStatusWords;
+    la.record = o.record_features != 0;
     std::shared_ptr<const LevelPlan> curp;
     if (o.coloring) {
       curp = A->plan1;
@@ -1115,12 +1118,14 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
     check(ce::launch_scatter_csr(es, A->d_scatter, A->d_val, A->nnz, pool, s), "scatter");
     int hstatus[ce::kStatusWords];
     for (int l = 0; l < o.levels && curp->M > 0; ++l) {
-      if (curp->nmax > ce::kNMax || max_targets(*curp) > 32) {
+      // levels whose rows outgrow the row kernel run the large-row path
+      const bool big = ce::level_needs_big_rows(*curp);
+      if (big && (curp->nmax > ce::kBigMaxN || max_targets(*curp) > ce::kBigMaxTargets)) {
         ret = CE_ERR_LIMIT;
         if (info) {
           info->err_level = l;
-          info->err_reason = curp->nmax > ce::kNMax ? 3 : 4;
-          info->err_pivot = curp->nmax > ce::kNMax ? curp->nmax : max_targets(*curp);
+          info->err_reason = curp->nmax > ce::kBigMaxN ? 3 : 4;
+          info->err_pivot = curp->nmax > ce::kBigMaxN ? curp->nmax : max_targets(*curp);
           info->levels_done = l;
         }
         break;
@@ -1129,6 +1134,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       F->levels.emplace_back();
       LevelStore& st = F->levels.back();
       st.plan = curp;
+      st.big = big;
       if (l == 0 && curp == A->plan1 && A->d_meta1)
         build_level_store(st, es, s, A->d_meta1, &A->meta1_off);
       else
@@ -1153,9 +1159,13 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       // exact SVD faster here
       ce::LearnedArgs la_l = la;
       if (o.row_shape < 0 && l < A->tuned_levels[tp][tr] && !A->tuned_learned[tp][tr][l]) la_l.model = nullptr;
+      if (big) la_l.model = nullptr;   // the large-row path compresses by the exact SVD
       if (info && l < 16) info->row_learned[l] = la_l.model != nullptr;
+      if (info && l < 16) info->big_rows[l] = big ? 1 : 0;
       const int nbkt = static_cast<int>(P.bucket_nmax.size());
-      if (nbkt <= 1) {
+      if (big) {
+        check(ce::run_big_level(es, st, l, o.tol, o.tol_mode, F->d_status, la.stats, s), "large rows");
+      } else if (nbkt <= 1) {
         check(ce::launch_row_kernel(es, st.dev, P.M, l, o.tol, o.tol_mode, F->d_status, P.nmax, shape, la_l, s),
               "row kernel");
       } else {
@@ -1236,11 +1246,11 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
         }
         if (info && l < 16)
           for (int i = 0; i < P.M; ++i) info->spec_miss[l] += live[i] != guess[i];
-        // super-blocks capped at the row kernel's limit: the speculative runs
-        // of J stand only if no run passes it
-        if (ce::coarsen_parents(P, o.J, &st.rank, ce::kNMax) != nx.parent) same = false;
+        // super-blocks capped at o.nmax rows (0: plain runs of J): the
+        // speculative runs of J stand only if no run passes the cap
+        if (o.nmax > 0 && ce::coarsen_parents(P, o.J, &st.rank, o.nmax) != nx.parent) same = false;
         if (!same) {
-          nx = ce::coarsen_structure(P, live, o.J, &st.rank, ce::kNMax);
+          nx = ce::coarsen_structure(P, live, o.J, &st.rank, o.nmax);
           ce::plan_structure(*nxtp, nx.M, nx.pairs, o.coloring != 0, nx.sys_off);
         }
       }
@@ -1498,7 +1508,10 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev, void*
       const LevelStore& st = F->levels[l];
       double* v = F->d_work + F->vec_base[l];
       double* vn = (l + 1 < nl) ? F->d_work + F->vec_base[l + 1] : coarse;
-      check(ce::launch_apply_fwd(es, st.dev, v, F->d_status, s), "apply fwd");
+      if (st.big)
+        check(ce::launch_apply_big(es, st.dev, *st.plan, v, 1, s), "apply fwd");
+      else
+        check(ce::launch_apply_fwd(es, st.dev, v, F->d_status, s), "apply fwd");
       check(ce::launch_level_move(st.dev, v, vn, 1, s), "level move");
     }
     if (F->nsys == 1)
@@ -1511,7 +1524,10 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev, void*
       double* v = F->d_work + F->vec_base[l];
       double* vn = (l + 1 < nl) ? F->d_work + F->vec_base[l + 1] : coarse;
       check(ce::launch_level_move(st.dev, v, vn, 0, s), "level move");
-      check(ce::launch_apply_bwd(es, st.dev, v, F->d_status, s), "apply bwd");
+      if (st.big)
+        check(ce::launch_apply_big(es, st.dev, *st.plan, v, 0, s), "apply bwd");
+      else
+        check(ce::launch_apply_bwd(es, st.dev, v, F->d_status, s), "apply bwd");
     }
     check(ce::launch_perm(F->d_perm, F->N, v0, z_dev, 0, s), "perm scatter");
   } catch (...) {

@@ -1,0 +1,1192 @@
+// Large block rows: Algorithm 2 for levels whose blocks outgrow the row
+// kernel's shared memory (more than 64 rows, more than 32 close or 128 far
+// blocks), as in 3D, where super-blocks of J = 8 boxes of boxes hold hundreds
+// of rows (Section 2.4) and the per-row products become true GEMM shapes.
+//
+// One colour at a time (its rows are independent: distance-2 colouring), the
+// steps of every row of the colour run as batched kernels with the row's
+// matrices in global memory:
+//   1. gather F_i^T (mF x n) from the far pairs            (copy tasks)
+//   2. R = R factor of F_i^T                               (tsqr_kernel)
+//   3. one-sided Jacobi on R: U_i, sigma, r_i, tau_i        (jacobi_kernel)
+//   4. X = D U, T = U^T D U                                (grouped GEMM)
+//   5. T_nn = L_hat L_hat^T, L_hat^{-1}                    (cholinv_kernel)
+//   6. W_b = L_hat^{-1} T[r:, :r], Y_p = U^T C_ip, U_b^T F (grouped GEMM)
+//   7. D_i <- T[:r, :r] - W_b^T W_b, W_p = L_hat^{-1} Y_p[r:]
+//   8. kept close rows Y_p[:r] - W_b^T W_p, Schur A(p, q) -= W_p^T W_q
+// The factor keeps the row kernel's layout (U_i, L_hat_i^{-1}, W_i), so the
+// reassembly and the level vectors are shared; the apply of such a level runs
+// one launch per colour (apply_big_kernel).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+
+namespace ce {
+
+namespace {
+
+template <typename T>
+struct EpsB;
+template <>
+struct EpsB<double> {
+  static constexpr double v = 2.220446049250313e-16;
+};
+template <>
+struct EpsB<float> {
+  static constexpr float v = 1.1920928955078125e-07f;
+};
+template <typename T>
+struct TinyB;
+template <>
+struct TinyB<double> {
+  static constexpr double v = 2.2250738585072014e-308;
+};
+template <>
+struct TinyB<float> {
+  static constexpr float v = 1.1754943508222875e-38f;
+};
+
+constexpr int kBigMaxSweeps = 40;
+constexpr double kBigTieRel = 1e-3;
+
+template <typename T>
+__device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <typename T>
+__device__ __forceinline__ T wmax(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ void big_status(int* status, int code, int level, int block, int reason, int pivot = -1,
+                           double value = 0.0) {
+  if (atomicCAS(status, 0, code) == 0) {
+    status[1] = level;
+    status[2] = block;
+    status[3] = reason;
+    status[4] = pivot;
+    *reinterpret_cast<double*>(status + 6) = value;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Grouped GEMM on the CUDA cores: 64 x 64 output tiles, 16-deep K slices in
+// shared memory, 4 x 4 outputs per thread.  Task t covers tiles
+// [tile0, tile0 + ceil(M/64) ceil(N/64)).
+// ---------------------------------------------------------------------------
+constexpr int kGT = 64, kGK = 16, kGThreads = 256;
+
+template <typename T>
+__global__ void __launch_bounds__(kGThreads) gemm_tasks_kernel(const GemmTask* tasks, int ntasks) {
+  __shared__ T As[kGK][kGT + 1], Bs[kGK][kGT + 1];
+  __shared__ int s_task;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    int lo = 0, hi = ntasks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (tasks[mid].tile0 <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+    }
+    s_task = lo;
+  }
+  __syncthreads();
+  const GemmTask& tk = tasks[s_task];
+  const int M = tk.M, N = tk.N, K = tk.K;
+  const int tl = blockIdx.x - tk.tile0, tn = (N + kGT - 1) / kGT;
+  const int m0 = (tl / tn) * kGT, n0 = (tl % tn) * kGT;
+  const T* A = static_cast<const T*>(tk.A);
+  const T* B = static_cast<const T*>(tk.B);
+  const int tx = tid & 15, ty = tid >> 4;
+  T acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = T(0);
+  for (int k0 = 0; k0 < K; k0 += kGK) {
+#pragma unroll
+    for (int u = 0; u < (kGT * kGK) / kGThreads; ++u) {
+      const int e = tid + u * kGThreads;
+      int m, k;
+      if (tk.ta) {  // A stored K x M: m contiguous
+        m = e % kGT;
+        k = e / kGT;
+      } else {
+        k = e % kGK;
+        m = e / kGK;
+      }
+      const int gm = m0 + m, gk = k0 + k;
+      T v = T(0);
+      if (gm < M && gk < K) v = tk.ta ? A[(int64_t)gk * tk.lda + gm] : A[(int64_t)gm * tk.lda + gk];
+      As[k][m] = v;
+      int n2, k2;
+      if (tk.tb) {  // B stored N x K: k contiguous
+        k2 = e % kGK;
+        n2 = e / kGK;
+      } else {
+        n2 = e % kGT;
+        k2 = e / kGT;
+      }
+      const int gn = n0 + n2, gk2 = k0 + k2;
+      T w = T(0);
+      if (gn < N && gk2 < K) w = tk.tb ? B[(int64_t)gn * tk.ldb + gk2] : B[(int64_t)gk2 * tk.ldb + gn];
+      Bs[k2][n2] = w;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGK; ++kk) {
+      T a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] += a[i] * b[j];
+    }
+    __syncthreads();
+  }
+  const T alpha = static_cast<T>(tk.alpha), beta = static_cast<T>(tk.beta);
+  const T* Cin = static_cast<const T*>(tk.Cin);
+  T* C = static_cast<T*>(tk.C);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int m = m0 + ty + 16 * i;
+    if (m >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int n = n0 + tx + 16 * j;
+      if (n >= N) continue;
+      T v = alpha * acc[i][j];
+      if (beta != T(0)) v += beta * (tk.tcin ? Cin[(int64_t)n * tk.ldcin + m] : Cin[(int64_t)m * tk.ldcin + n]);
+      if (tk.tc)
+        C[(int64_t)n * tk.ldc + m] = v;
+      else
+        C[(int64_t)m * tk.ldc + n] = v;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Per-row descriptors of a colour's rows (device copy).
+// ---------------------------------------------------------------------------
+struct BigRowDev {
+  int i;          // block index in the level
+  int n, mF;      // block size and far rows of F_i^T
+  int64_t g_off;  // F_i^T, mF x n row-major (work space)
+  int64_t x_off;  // n x n: R, then the columns of X (column-major)
+  int64_t v_off;  // n x n: V (column-major)
+  int64_t t_off;  // n x n: T = U^T D U (row-major)
+  int64_t w2_off; // n x n: D U (row-major), then the Cholesky work matrix
+};
+
+// ---------------------------------------------------------------------------
+// R factor of F_i^T (mF x n) by stacked Householder steps: chunks of CH rows
+// of F_i^T are pushed into the triangular R (n x n, global memory) panel by
+// panel; one warp factorizes each 32-column panel of [R; C], the CTA applies
+// the panel's compact WY form (I - V T V^T) to the trailing columns.
+// ---------------------------------------------------------------------------
+constexpr int kPW = 32;
+constexpr int kBigThreads = 512;
+constexpr int kTsqrThreads = 256;   // the trailing update keeps 64 values per thread in registers
+
+template <typename T>
+__device__ __forceinline__ bool hh_reflector(T x0, T c, T& beta, T& tau, T& sc) {
+  const T amax = wmax(fabs(c));
+  if (!(amax >= TinyB<T>::v)) return false;
+  const T ia = T(1) / amax;
+  const T xl = c * ia;
+  const T s = wsum(xl * xl);
+  const T a = fmax(amax, fabs(x0));
+  const T x0a = x0 / a, ca = amax / a;
+  const T nrm = a * sqrt(x0a * x0a + s * ca * ca);
+  beta = (x0 >= T(0)) ? -nrm : nrm;
+  tau = (beta - x0) / beta;
+  sc = T(1) / (x0 - beta);
+  return true;
+}
+
+template <typename T, int CH>
+__global__ void __launch_bounds__(kTsqrThreads) tsqr_kernel(const BigRowDev* rows, T* ws) {
+  const BigRowDev rw = rows[blockIdx.x];
+  const int n = rw.n, mF = rw.mF;
+  if (mF <= 0 || n <= 0) return;
+  extern __shared__ __align__(16) unsigned char big_smem[];
+  T* C = reinterpret_cast<T*>(big_smem);          // CH x n
+  __shared__ T Rp[kPW][kPW + 1], Vc[CH][kPW + 1], Tm[kPW][kPW + 1], tauv[kPW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* R = ws + rw.x_off;
+  const T* G = ws + rw.g_off;
+  for (int64_t e = tid; e < (int64_t)n * n; e += kTsqrThreads) R[e] = T(0);
+  __syncthreads();
+  for (int g0 = 0; g0 < mF; g0 += CH) {
+    const int rows = min(CH, mF - g0);
+    for (int e = tid; e < CH * n; e += kTsqrThreads) {
+      const int q = e / n, a = e - q * n;
+      C[e] = (q < rows) ? G[(int64_t)(g0 + q) * n + a] : T(0);
+    }
+    __syncthreads();
+    for (int p0 = 0; p0 < n; p0 += kPW) {
+      const int pw = min(kPW, n - p0);
+      if (warp == 0) {
+        for (int e = lane; e < kPW * kPW; e += 32) {
+          const int j = e / kPW, l = e % kPW;
+          Rp[j][l] = (j < pw && l < pw) ? R[(int64_t)(p0 + j) * n + p0 + l] : T(0);
+        }
+        for (int e = lane; e < CH * kPW; e += 32) Vc[e / kPW][e % kPW] = T(0);
+        __syncwarp();
+        for (int j = 0; j < pw; ++j) {
+          const T c = (lane < CH) ? C[lane * n + p0 + j] : T(0);
+          T beta, tau, sc;
+          const bool ok = hh_reflector(Rp[j][j], c, beta, tau, sc);
+          if (lane < CH) Vc[lane][j] = ok ? c * sc : T(0);
+          if (lane == 0) tauv[j] = ok ? tau : T(0);
+          __syncwarp();
+          if (ok) {
+            if (lane == 0) Rp[j][j] = beta;
+            const int l = j + 1 + lane;
+            if (l < pw) {
+              T d = Rp[j][l];
+              for (int q = 0; q < CH; ++q) d += Vc[q][j] * C[q * n + p0 + l];
+              d *= tau;
+              Rp[j][l] -= d;
+              for (int q = 0; q < CH; ++q) C[q * n + p0 + l] -= d * Vc[q][j];
+            }
+          }
+          __syncwarp();
+        }
+        for (int e = lane; e < pw * pw; e += 32) {
+          const int j = e / pw, l = e % pw;
+          if (l >= j) R[(int64_t)(p0 + j) * n + p0 + l] = Rp[j][l];
+        }
+        // compact WY: T upper triangular, T[:j, j] = -tau_j T[:j, :j] (V[:, :j]^T v_j);
+        // the R parts of the reflectors are distinct unit vectors, so
+        // v_i^T v_j = vc_i . vc_j
+        for (int j = 0; j < pw; ++j) {
+          T g = T(0);
+          if (lane < j)
+            for (int q = 0; q < CH; ++q) g += Vc[q][lane] * Vc[q][j];
+          Tm[lane][j] = g;   // temporarily v_lane . v_j
+        }
+        __syncwarp();
+        for (int j = 0; j < pw; ++j) {
+          // column j: Tm[i][j] = -tau_j sum_{k=i}^{j-1} T[i][k] g[k][j], i < j
+          T acc = T(0);
+          if (lane < j)
+            for (int k = lane; k < j; ++k) acc += (k == lane ? tauv[k] : Tm[lane][k]) * Tm[k][j];
+          __syncwarp();
+          if (lane < j) Tm[lane][j] = -tauv[j] * acc;
+          __syncwarp();
+        }
+        if (lane < pw) Tm[lane][lane] = tauv[lane];
+      }
+      __syncthreads();
+      // trailing columns: X <- X - V T^T (V^T X), X = [R rows p0.. ; C]
+      for (int l = p0 + pw + tid; l < n; l += kTsqrThreads) {
+        T w[kPW];
+#pragma unroll
+        for (int j = 0; j < kPW; ++j) {
+          T s = (j < pw) ? R[(int64_t)(p0 + j) * n + l] : T(0);
+          for (int q = 0; q < CH; ++q) s += Vc[q][j] * C[q * n + l];
+          w[j] = s;
+        }
+        T w2[kPW];
+#pragma unroll
+        for (int j = 0; j < kPW; ++j) {
+          T s = T(0);
+#pragma unroll
+          for (int i2 = 0; i2 <= j; ++i2) s += Tm[i2][j] * w[i2];
+          w2[j] = (j < pw) ? s : T(0);
+        }
+#pragma unroll
+        for (int j = 0; j < kPW; ++j)
+          if (j < pw) R[(int64_t)(p0 + j) * n + l] -= w2[j];
+        for (int q = 0; q < CH; ++q) {
+          T s = T(0);
+#pragma unroll
+          for (int j = 0; j < kPW; ++j) s += Vc[q][j] * w2[j];
+          C[q * n + l] -= s;
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// One-sided (Hestenes) Jacobi on the columns of R: R V = U' S, U_i = V and
+// sigma = S sorted descending; the truncation rule of the compression step
+// (CE(eps), CE(r)) with the rounding floor u ||D_i||_F.  Columns are stored
+// contiguously (X = R^T row-major), one warp per column pair of a round-robin
+// round.  Rows without far columns get U_i = I and r_i = 0.
+// ---------------------------------------------------------------------------
+struct BigLevelArgs {
+  int level;
+  double tol;
+  int tol_mode;
+  int* status;
+  int* stats;     // kStatsWords counters (Jacobi cap at [32 + level])
+};
+
+template <typename T>
+__global__ void __launch_bounds__(kBigThreads) jacobi_kernel(const BigRowDev* rows, T* ws, LevelDev L,
+                                                             BigLevelArgs a) {
+  const BigRowDev rw = rows[blockIdx.x];
+  const int n = rw.n, i = rw.i;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kW = kBigThreads / 32;
+  __shared__ double s_red[kW];
+  __shared__ T s_skip2;
+  __shared__ int s_flag;
+  extern __shared__ __align__(16) unsigned char big_smem[];
+  T* sig = reinterpret_cast<T*>(big_smem);   // n
+  int* pos = reinterpret_cast<int*>(sig + n); // n
+  T* Ug = reinterpret_cast<T*>(L.U) + L.u_off[i];
+  if (n <= 0) return;
+  const T* D = reinterpret_cast<const T*>(L.pool) + L.diag_off[i];
+  {
+    double ss = 0.0;
+    for (int64_t e = tid; e < (int64_t)n * n; e += kBigThreads) {
+      const double v = static_cast<double>(D[e]);
+      ss += v * v;
+    }
+    ss = wsum(ss);
+    if (lane == 0) s_red[warp] = ss;
+  }
+  __syncthreads();
+  double dn2 = 0.0;
+  for (int w = 0; w < kW; ++w) dn2 += s_red[w];
+  const double floor_tau = static_cast<double>(EpsB<T>::v) * sqrt(dn2);
+  if (rw.mF <= 0) {
+    for (int64_t e = tid; e < (int64_t)n * n; e += kBigThreads) Ug[e] = (e / n == e % n) ? T(1) : T(0);
+    for (int k = tid; k < n; k += kBigThreads) L.sigma[L.vec_off[i] + k] = 0.0;
+    if (tid == 0) {
+      L.rank[i] = 0;
+      L.tau[i] = 0.0;
+    }
+    return;
+  }
+  T* X = ws + rw.t_off;   // columns of R, contiguous
+  T* V = ws + rw.v_off;
+  const T* R = ws + rw.x_off;
+  for (int64_t e = tid; e < (int64_t)n * n; e += kBigThreads) {
+    const int c = static_cast<int>(e / n), row = static_cast<int>(e % n);
+    X[e] = R[(int64_t)row * n + c];
+    V[e] = (c == row) ? T(1) : T(0);
+  }
+  __syncthreads();
+  const int nb = n + (n & 1), npairs = nb / 2;
+  const T tolJ = T(n) * EpsB<T>::v, tolJ2 = tolJ * tolJ;
+  bool conv = false;
+  for (int sweep = 0; sweep < kBigMaxSweeps; ++sweep) {
+    // pairs whose columns both stay below tau_est / (2 sqrt n) are skipped
+    // (their rotation changes neither the kept subspace nor the rank)
+    T cm = T(0);
+    for (int j = warp; j < n; j += kW) {
+      T s = T(0);
+      for (int row = lane; row < n; row += 32) s += X[(int64_t)j * n + row] * X[(int64_t)j * n + row];
+      s = wsum(s);
+      cm = fmax(cm, s);
+    }
+    if (lane == 0) s_red[warp] = static_cast<double>(cm);
+    __syncthreads();
+    if (tid == 0) {
+      double c2 = 0.0;
+      for (int w = 0; w < kW; ++w) c2 = fmax(c2, s_red[w]);
+      const T sm = static_cast<T>(sqrt(c2));
+      T test = (a.tol == 0.0 || a.tol_mode == CE_TOL_FIXED) ? T(n) * EpsB<T>::v * sm
+                                                            : ((a.tol_mode == CE_TOL_ABS) ? T(a.tol) : T(a.tol) * sm);
+      test = fmax(test, static_cast<T>(floor_tau)) * T(0.5) / sqrt(T(n));
+      s_skip2 = test * test;
+      s_flag = 0;
+    }
+    __syncthreads();
+    const T skip2 = s_skip2;
+    for (int rnd = 0; rnd < nb - 1; ++rnd) {
+      for (int t = warp; t < npairs; t += kW) {
+        int p = nb - 1, q = rnd;
+        if (t != 0) {
+          p = rnd + t;
+          if (p >= nb - 1) p -= nb - 1;
+          q = rnd - t;
+          if (q < 0) q += nb - 1;
+        }
+        if (p >= n || q >= n) continue;
+        T* xp = X + (int64_t)p * n;
+        T* xq = X + (int64_t)q * n;
+        T al = 0, be = 0, ga = 0;
+        for (int row = lane; row < n; row += 32) {
+          const T u = xp[row], v = xq[row];
+          al += u * u;
+          be += v * v;
+          ga += u * v;
+        }
+        al = wsum(al);
+        be = wsum(be);
+        ga = wsum(ga);
+        if (ga != T(0) && (al >= skip2 || be >= skip2) && ga * ga > tolJ2 * al * be) {
+          const T zeta = (be - al) / (T(2) * ga);
+          const T az = fabs(zeta);
+          const T den = (az > T(1)) ? az * (T(1) + sqrt(T(1) + T(1) / (az * az))) : az + sqrt(T(1) + az * az);
+          const T tt = ((zeta >= T(0)) ? T(1) : T(-1)) / den;
+          const T cs = T(1) / sqrt(T(1) + tt * tt), sn = cs * tt;
+          T* vp = V + (int64_t)p * n;
+          T* vq = V + (int64_t)q * n;
+          for (int row = lane; row < n; row += 32) {
+            const T u = xp[row], v = xq[row];
+            xp[row] = cs * u - sn * v;
+            xq[row] = sn * u + cs * v;
+            const T u2 = vp[row], v2 = vq[row];
+            vp[row] = cs * u2 - sn * v2;
+            vq[row] = sn * u2 + cs * v2;
+          }
+          if (lane == 0) s_flag = 1;
+        }
+      }
+      __syncthreads();
+    }
+    const int rotated = s_flag;
+    __syncthreads();
+    if (!rotated) {
+      conv = true;
+      break;
+    }
+  }
+  if (!conv && tid == 0 && a.stats && a.level < 16) atomicAdd(a.stats + 32 + a.level, 1);
+  for (int j = warp; j < n; j += kW) {
+    T s = T(0);
+    for (int row = lane; row < n; row += 32) s += X[(int64_t)j * n + row] * X[(int64_t)j * n + row];
+    s = wsum(s);
+    if (lane == 0) sig[j] = sqrt(s);
+  }
+  __syncthreads();
+  for (int j = tid; j < n; j += kBigThreads) {
+    const T sj = sig[j];
+    int ps = 0;
+    for (int k = 0; k < n; ++k) ps += (sig[k] > sj) || (sig[k] == sj && k < j);
+    pos[j] = ps;
+  }
+  __syncthreads();
+  // U_i[a][pos[j]] = V[:, j][a]; sigma sorted
+  for (int64_t e = tid; e < (int64_t)n * n; e += kBigThreads) {
+    const int j = static_cast<int>(e / n), row = static_cast<int>(e % n);
+    Ug[(int64_t)row * n + pos[j]] = V[e];
+  }
+  for (int j = tid; j < n; j += kBigThreads) L.sigma[L.vec_off[i] + pos[j]] = static_cast<double>(sig[j]);
+  __syncthreads();
+  if (tid == 0) {
+    // sorted singular values
+    T smax = T(0);
+    for (int j = 0; j < n; ++j) smax = fmax(smax, sig[j]);
+    const double sm = static_cast<double>(smax);
+    if (!isfinite(sm)) {
+      big_status(a.status, CE_ERR_NOT_SPD, a.level, i, 2);
+    } else {
+      double tau;
+      if (a.tol_mode == CE_TOL_FIXED) {
+        const int rf = static_cast<int>(a.tol);
+        tau = n * static_cast<double>(EpsB<T>::v) * sm;
+        if (rf == 0) {
+          tau = fmax(tau, sm);
+        } else if (rf < n) {
+          // sigma_rf: the rf-th largest
+          double srf = 0.0;
+          for (int j = 0; j < n; ++j)
+            if (pos[j] == rf - 1) srf = static_cast<double>(sig[j]);
+          tau = fmax(tau, (1.0 - kBigTieRel) * srf);
+        }
+      } else if (a.tol == 0.0) {
+        tau = n * static_cast<double>(EpsB<T>::v) * sm;
+      } else {
+        tau = (a.tol_mode == CE_TOL_ABS) ? a.tol : a.tol * sm;
+      }
+      tau = fmax(tau, floor_tau);
+      int rr = 0;
+      for (int j = 0; j < n; ++j) rr += (static_cast<double>(sig[j]) > tau) ? 1 : 0;
+      L.rank[i] = rr;
+      L.tau[i] = tau;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Cholesky of T_nn = T[r:, r:] (m x m) and its inverse: L_hat^{-1} into the
+// factor (m x m row-major, zero above the diagonal).  Right-looking, 32-column
+// panels: one warp factorizes the diagonal tile, the CTA solves the panel
+// below it and updates the trailing lower triangle; then the inverse by
+// block forward substitution, one 32-row block row at a time.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kBigThreads) cholinv_kernel(const BigRowDev* rows, T* ws, LevelDev L,
+                                                              BigLevelArgs a) {
+  const BigRowDev rw = rows[blockIdx.x];
+  const int n = rw.n, i = rw.i;
+  const int r = L.rank[i], m = n - r;
+  if (n <= 0 || m <= 0) return;
+  __shared__ T Dt[kPW][kPW + 1];
+  __shared__ int s_bad;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const T* Tg = ws + rw.t_off;
+  T* Aw = ws + rw.w2_off;   // m x m work, row-major
+  T* Li = reinterpret_cast<T*>(L.L) + L.l_off[i];
+  for (int64_t e = tid; e < (int64_t)m * m; e += kBigThreads) {
+    const int x = static_cast<int>(e / m), y = static_cast<int>(e % m);
+    Aw[e] = Tg[(int64_t)(r + x) * n + r + y];
+    Li[e] = T(0);
+  }
+  if (tid == 0) s_bad = 0;
+  __syncthreads();
+  for (int p0 = 0; p0 < m; p0 += kPW) {
+    const int pw = min(kPW, m - p0);
+    if (warp == 0) {
+      for (int e = lane; e < kPW * kPW; e += 32) {
+        const int x = e / kPW, y = e % kPW;
+        Dt[x][y] = (x < pw && y < pw) ? Aw[(int64_t)(p0 + x) * m + p0 + y] : T(0);
+      }
+      __syncwarp();
+      for (int k = 0; k < pw; ++k) {
+        const T piv = Dt[k][k];
+        if (!(piv > T(0))) {
+          if (lane == 0) {
+            s_bad = 1;
+            big_status(a.status, CE_ERR_NOT_SPD, a.level, i, 1, p0 + k, static_cast<double>(piv));
+          }
+          break;
+        }
+        const T d = sqrt(piv);
+        __syncwarp();
+        if (lane == k) Dt[k][k] = d;
+        if (lane > k && lane < pw) Dt[lane][k] /= d;
+        __syncwarp();
+        if (lane > k && lane < pw)
+          for (int y = k + 1; y <= lane; ++y) Dt[lane][y] -= Dt[lane][k] * Dt[y][k];
+        __syncwarp();
+      }
+      for (int e = lane; e < pw * pw; e += 32) {
+        const int x = e / pw, y = e % pw;
+        if (y <= x) Aw[(int64_t)(p0 + x) * m + p0 + y] = Dt[x][y];
+      }
+    }
+    __syncthreads();
+    if (s_bad) return;
+    // panel below: A[x, p0:p0+pw] <- A[x, p0:p0+pw] L_pp^{-T}
+    for (int x = p0 + pw + tid; x < m; x += kBigThreads) {
+      T row[kPW];
+#pragma unroll
+      for (int j = 0; j < kPW; ++j) row[j] = (j < pw) ? Aw[(int64_t)x * m + p0 + j] : T(0);
+#pragma unroll
+      for (int j = 0; j < kPW; ++j) {
+        if (j < pw) {
+          T s = row[j];
+          for (int k = 0; k < j; ++k) s -= row[k] * Dt[j][k];
+          row[j] = s / Dt[j][j];
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kPW; ++j)
+        if (j < pw) Aw[(int64_t)x * m + p0 + j] = row[j];
+    }
+    __syncthreads();
+    // trailing lower triangle: A[x, y] -= A[x, panel] . A[y, panel], y <= x
+    const int t0 = p0 + pw, nt = m - t0;
+    const int64_t tri = (int64_t)nt * (nt + 1) / 2;
+    for (int64_t e = tid; e < tri; e += kBigThreads) {
+      // e -> (x, y) with y <= x in the trailing block
+      int x = static_cast<int>((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
+      while ((int64_t)x * (x + 1) / 2 > e) --x;
+      while ((int64_t)(x + 1) * (x + 2) / 2 <= e) ++x;
+      const int y = static_cast<int>(e - (int64_t)x * (x + 1) / 2);
+      const T* ax = Aw + (int64_t)(t0 + x) * m + p0;
+      const T* ay = Aw + (int64_t)(t0 + y) * m + p0;
+      T s = T(0);
+      for (int j = 0; j < pw; ++j) s += ax[j] * ay[j];
+      Aw[(int64_t)(t0 + x) * m + t0 + y] -= s;
+    }
+    __syncthreads();
+  }
+  // inverse: X = L^{-1}, block row I: X[I, J] = L_II^{-1} (delta_IJ - sum_{J <= K < I} L[I, K] X[K, J])
+  const int nbk = (m + kPW - 1) / kPW;
+  for (int I = 0; I < nbk; ++I) {
+    const int r0 = I * kPW, h = min(kPW, m - r0);
+    // inverse of the diagonal tile by one warp: column by column forward substitution
+    if (warp == 0) {
+      for (int e = lane; e < kPW * kPW; e += 32) {
+        const int x = e / kPW, y = e % kPW;
+        Dt[x][y] = (x < h && y < h && y <= x) ? Aw[(int64_t)(r0 + x) * m + r0 + y] : T(0);
+      }
+    }
+    __syncthreads();
+    // S = -sum_{K < I} L[I, K] X[K, J] for every column c < r0 (then X[I, c] = L_II^{-1} S)
+    for (int e = tid; e < h * r0; e += kBigThreads) {
+      const int x = e / r0, c = e % r0;
+      T s = T(0);
+      const T* lr = Aw + (int64_t)(r0 + x) * m;
+      for (int k = c; k < r0; ++k) s += lr[k] * Li[(int64_t)k * m + c];
+      Li[(int64_t)(r0 + x) * m + c] = -s;   // staged, solved below
+    }
+    __syncthreads();
+    // columns c < r0 + h: solve L_II y = rhs (rhs = staged S, or e_c for the diagonal tile)
+    for (int c = tid; c < r0 + h; c += kBigThreads) {
+      T y[kPW];
+#pragma unroll
+      for (int x = 0; x < kPW; ++x) {
+        if (x < h) {
+          T s = (c < r0) ? Li[(int64_t)(r0 + x) * m + c] : ((c - r0 == x) ? T(1) : T(0));
+          for (int k = 0; k < x; ++k) s -= Dt[x][k] * y[k];
+          y[x] = s / Dt[x][x];
+        }
+      }
+#pragma unroll
+      for (int x = 0; x < kPW; ++x)
+        if (x < h && (c < r0 || c - r0 <= x)) Li[(int64_t)(r0 + x) * m + c] = y[x];
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Apply of a large-row level, one launch per colour, one CTA per row (the
+// forward and backward steps of the row kernel's factor layout; vectors of
+// the row in dynamic shared memory, the targets' entries read from the level
+// vector).
+// ---------------------------------------------------------------------------
+constexpr int kBigTgt = 64;
+
+struct BigTargets {
+  int nt;
+  int w[kBigTgt], pre[kBigTgt + 1];
+  int64_t woff[kBigTgt], voff[kBigTgt];
+};
+
+__device__ void big_targets(const LevelDev& L, int i, int n, int r, BigTargets& T) {
+  const int ci = L.colour[i];
+  const int c0 = L.close_ptr[i], c1 = L.close_ptr[i + 1];
+  const int nt = min(1 + (c1 - c0), kBigTgt);
+  int64_t colst = 0;
+  int pre = 0;
+  for (int t = 0; t < nt; ++t) {
+    int w, np;
+    int64_t vo;
+    if (t == 0) {
+      w = r;
+      np = n;
+      vo = L.vec_off[i];
+    } else {
+      const int p = L.close_blk[c0 + t - 1];
+      w = (L.colour[p] < ci) ? L.rank[p] : L.n[p];
+      np = L.n[p];
+      vo = L.vec_off[p];
+    }
+    T.w[t] = w;
+    T.woff[t] = (int64_t)n * colst;
+    T.voff[t] = vo;
+    T.pre[t] = pre;
+    colst += np;
+    pre += w;
+  }
+  T.pre[nt] = pre;
+  T.nt = nt;
+}
+
+template <typename T, bool kFwd>
+__global__ void __launch_bounds__(kBigThreads) apply_big_kernel(LevelDev L, int q0, double* vec) {
+  __shared__ BigTargets tg;
+  extern __shared__ __align__(16) unsigned char big_smem[];
+  const int tid = threadIdx.x;
+  const int i = L.order[q0 + blockIdx.x];
+  const int n = L.n[i];
+  if (n == 0) return;
+  const int r = L.rank[i], m = n - r;
+  T* ys = reinterpret_cast<T*>(big_smem);
+  T* yt = ys + n;
+  T* z = yt + n;
+  double* v = vec + L.vec_off[i];
+  const T* U = reinterpret_cast<const T*>(L.U) + L.u_off[i];
+  const T* Li = reinterpret_cast<const T*>(L.L) + L.l_off[i];
+  const T* W = reinterpret_cast<const T*>(L.W) + L.w_off[i];
+  if (tid == 0) big_targets(L, i, n, r, tg);
+  for (int a = tid; a < n; a += kBigThreads) ys[a] = static_cast<T>(v[a]);
+  __syncthreads();
+  if (kFwd) {
+    // yt = U^T ys
+    for (int a = tid; a < n; a += kBigThreads) {
+      T s = T(0);
+      for (int k = 0; k < n; ++k) s += U[(int64_t)k * n + a] * ys[k];
+      yt[a] = s;
+    }
+    __syncthreads();
+    // z = L_hat^{-1} yt[r:]
+    for (int a = tid; a < m; a += kBigThreads) {
+      T s = T(0);
+      const T* lr = Li + (int64_t)a * m;
+      for (int k = 0; k <= a; ++k) s += lr[k] * yt[r + k];
+      z[a] = s;
+    }
+    __syncthreads();
+    for (int a = tid; a < m; a += kBigThreads) v[r + a] = static_cast<double>(z[a]);
+    // targets: y_t[c] -= (W_t^T z)[c]; the basis of i gets yt - W_b^T z
+    const int tot = tg.pre[tg.nt];
+    for (int f = tid; f < tot; f += kBigThreads) {
+      int t = 0;
+      while (f >= tg.pre[t + 1]) ++t;
+      const int c = f - tg.pre[t], w = tg.w[t];
+      const T* Wt = W + tg.woff[t] + c;
+      T s = T(0);
+      for (int k = 0; k < m; ++k) s += Wt[(int64_t)k * w] * z[k];
+      if (t == 0)
+        v[c] = static_cast<double>(yt[c] - s);
+      else
+        vec[tg.voff[t] + c] -= static_cast<double>(s);
+    }
+  } else {
+    // rhs = z - sum_t W_t x_t (x_0 = basis of i, x_t = target values)
+    for (int a = tid; a < m; a += kBigThreads) {
+      T s = T(0);
+      for (int t = 0; t < tg.nt; ++t) {
+        const int w = tg.w[t];
+        const T* Wt = W + tg.woff[t] + (int64_t)a * w;
+        if (t == 0)
+          for (int c = 0; c < w; ++c) s += Wt[c] * ys[c];
+        else
+          for (int c = 0; c < w; ++c) s += Wt[c] * static_cast<T>(vec[tg.voff[t] + c]);
+      }
+      yt[a] = ys[r + a] - s;
+    }
+    __syncthreads();
+    // x_n = L_hat^{-T} rhs
+    for (int a = tid; a < m; a += kBigThreads) {
+      T s = T(0);
+      for (int k = a; k < m; ++k) s += Li[(int64_t)k * m + a] * yt[k];
+      z[a] = s;
+    }
+    __syncthreads();
+    for (int a = tid; a < m; a += kBigThreads) ys[r + a] = z[a];
+    __syncthreads();
+    // y_i = U [x_b; x_n]
+    for (int a = tid; a < n; a += kBigThreads) {
+      T s = T(0);
+      const T* ur = U + (int64_t)a * n;
+      for (int k = 0; k < n; ++k) s += ur[k] * ys[k];
+      v[a] = static_cast<double>(s);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct BigFail {
+  cudaError_t e;
+};
+
+void bcheck(cudaError_t e) {
+  if (e != cudaSuccess) throw BigFail{e};
+}
+
+template <typename T>
+cudaError_t launch_gemm_t(const std::vector<GemmTask>& tasks_in, cudaStream_t s) {
+  if (tasks_in.empty()) return cudaSuccess;
+  std::vector<GemmTask> tasks;
+  tasks.reserve(tasks_in.size());
+  int tiles = 0;
+  for (const GemmTask& t : tasks_in) {
+    if (t.M <= 0 || t.N <= 0) continue;
+    GemmTask u = t;
+    u.tile0 = tiles;
+    tiles += ((t.M + kGT - 1) / kGT) * ((t.N + kGT - 1) / kGT);
+    tasks.push_back(u);
+  }
+  if (tasks.empty()) return cudaSuccess;
+  GemmTask* d = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&d), tasks.size() * sizeof(GemmTask), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpyAsync(d, tasks.data(), tasks.size() * sizeof(GemmTask), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    gemm_tasks_kernel<T><<<tiles, kGThreads, 0, s>>>(d, static_cast<int>(tasks.size()));
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(d, s);
+  // the task array is read by the kernel before the free runs (stream order);
+  // the host vector is copied before cudaMemcpyAsync from pageable memory returns
+  return e;
+}
+
+// GEMM task helpers: element (x, y) of a block pair seen from block a (rows
+// of a, columns of b) in the pool, where pairs are stored once as
+// (min, max) row-major.
+struct PairView {
+  int64_t off;   // element offset in the pool
+  int ld;        // leading dimension of the stored pair
+  int trans;     // 1: element (x, y) at off + y * ld + x
+};
+
+PairView pair_view(const LevelPlan& P, int a, int b) {
+  const int64_t off = find_pair(P, a, b);
+  if (off < 0) throw BigFail{cudaErrorInvalidValue};
+  if (a <= b) return {off, P.n[b], 0};
+  return {off, P.n[a], 1};
+}
+
+template <typename T>
+void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, std::vector<int>& rank_h) {
+  const LevelPlan& P = *st.plan;
+  LevelDev& D = st.dev;
+  T* pool = static_cast<T*>(D.pool);
+  T* Uf = static_cast<T*>(D.U);
+  T* Lf = static_cast<T*>(D.L);
+  T* Wf = static_cast<T*>(D.W);
+  const int es = sizeof(T);
+  rank_h.assign(P.M, 0);
+  std::vector<int> done(P.M, 0);
+  auto width = [&](int k) { return done[k] ? rank_h[k] : P.n[k]; };
+  constexpr int CH = sizeof(T) == 4 ? 32 : 16;
+  static size_t tsqr_dyn = 0;  // dynamic shared memory the TSQR kernel may take
+  if (tsqr_dyn == 0) {
+    int dev = 0, optin = 0;
+    bcheck(cudaGetDevice(&dev));
+    bcheck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    bcheck(cudaFuncGetAttributes(&fa, tsqr_kernel<T, CH>));
+    const size_t lim = static_cast<size_t>(optin) - fa.sharedSizeBytes;
+    bcheck(cudaFuncSetAttribute(tsqr_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+    tsqr_dyn = lim;
+  }
+  for (int c = 0; c < P.ncolours; ++c) {
+    const int q0 = P.colour_ptr[c], q1 = P.colour_ptr[c + 1];
+    if (q1 <= q0) continue;
+    // ---- layout of the colour's work space ----
+    std::vector<BigRowDev> rows;
+    std::vector<std::vector<int>> fpre(q1 - q0);
+    int64_t off = 0;
+    int nmaxc = 0;
+    auto take = [&](int64_t elems) {
+      const int64_t o = off;
+      off += (elems + 63) & ~int64_t(63);
+      return o;
+    };
+    std::vector<CopyTask> gather;
+    for (int q = q0; q < q1; ++q) {
+      const int i = P.order[q];
+      BigRowDev r{};
+      r.i = i;
+      r.n = P.n[i];
+      int mF = 0;
+      std::vector<int>& fp = fpre[q - q0];
+      for (int f = P.far_ptr[i]; f < P.far_ptr[i + 1]; ++f) {
+        fp.push_back(mF);
+        mF += width(P.far_blk[f]);
+      }
+      fp.push_back(mF);
+      r.mF = mF;
+      const int n = r.n;
+      nmaxc = std::max(nmaxc, n);
+      r.g_off = take((int64_t)std::max(mF, 1) * n);
+      r.x_off = take((int64_t)n * n);
+      r.v_off = take((int64_t)n * n);
+      r.t_off = take((int64_t)n * n);
+      r.w2_off = take((int64_t)n * n);
+      rows.push_back(r);
+      for (int f = P.far_ptr[i], ff = 0; f < P.far_ptr[i + 1]; ++f, ++ff) {
+        const int k = P.far_blk[f], w = width(k);
+        if (w == 0 || n == 0) continue;
+        CopyTask t{};
+        if (i < k) {  // stored n_i x n_k: F_ik^T = columns 0..w-1, transposed
+          t.src_off = P.far_off[f];
+          t.src_ld = P.n[k];
+          t.rows = n;
+          t.cols = w;
+          t.transpose = 1;
+        } else {      // stored n_k x n_i: the first w rows are F_ik^T
+          t.src_off = P.far_off[f];
+          t.src_ld = n;
+          t.rows = w;
+          t.cols = n;
+          t.transpose = 0;
+        }
+        t.dst_off = r.g_off;
+        t.dst_ld = n;
+        t.r0 = fp[ff];
+        t.c0 = 0;
+        gather.push_back(t);
+      }
+    }
+    // Y_p buffers (n x w_p per close target), after the fixed part
+    std::vector<std::vector<int64_t>> yoff(q1 - q0);
+    for (int q = q0; q < q1; ++q) {
+      const int i = P.order[q];
+      for (int t = P.close_ptr[i]; t < P.close_ptr[i + 1]; ++t)
+        yoff[q - q0].push_back(take((int64_t)P.n[i] * std::max(width(P.close_blk[t]), 1)));
+    }
+    T* ws = nullptr;
+    bcheck(cudaMallocAsync(reinterpret_cast<void**>(&ws), std::max<int64_t>(off, 64) * es, s));
+    BigRowDev* drows = nullptr;
+    bcheck(cudaMallocAsync(reinterpret_cast<void**>(&drows), rows.size() * sizeof(BigRowDev), s));
+    bcheck(cudaMemcpyAsync(drows, rows.data(), rows.size() * sizeof(BigRowDev), cudaMemcpyHostToDevice, s));
+    const int nr = static_cast<int>(rows.size());
+    // ---- 1-3: compression ----
+    if (!gather.empty()) {
+      CopyTask* dt = nullptr;
+      bcheck(cudaMallocAsync(reinterpret_cast<void**>(&dt), gather.size() * sizeof(CopyTask), s));
+      bcheck(cudaMemcpyAsync(dt, gather.data(), gather.size() * sizeof(CopyTask), cudaMemcpyHostToDevice, s));
+      bcheck(launch_copy_tasks(es, es, dt, static_cast<int>(gather.size()), pool, ws, s));
+      bcheck(cudaFreeAsync(dt, s));
+    }
+    {
+      const size_t sm = (size_t)CH * nmaxc * es;
+      if (sm > tsqr_dyn) throw BigFail{cudaErrorInvalidValue};
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+      tsqr_kernel<T, CH><<<nr, kTsqrThreads, sm, s>>>(drows, ws);
+      bcheck(cudaGetLastError());
+      const size_t sj = (size_t)nmaxc * (es + sizeof(int)) + 64;
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+      jacobi_kernel<T><<<nr, kBigThreads, sj, s>>>(drows, ws, D, args);
+      bcheck(cudaGetLastError());
+    }
+    // ranks of the colour (the shapes of everything that follows)
+    std::vector<int> rk(P.M);
+    bcheck(cudaMemcpyAsync(rk.data(), D.rank, P.M * sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hstat = 0;
+    bcheck(cudaMemcpyAsync(&hstat, args.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    bcheck(cudaStreamSynchronize(s));
+    if (hstat != 0) {
+      cudaFreeAsync(ws, s);
+      cudaFreeAsync(drows, s);
+      return;
+    }
+    for (int q = q0; q < q1; ++q) rank_h[P.order[q]] = rk[P.order[q]];
+    // ---- 4: X = D U, T = U^T X ----
+    std::vector<GemmTask> g1, g2;
+    for (int q = q0; q < q1; ++q) {
+      const BigRowDev& r = rows[q - q0];
+      const int i = r.i, n = r.n;
+      if (n == 0) continue;
+      const T* U = Uf + P.u_off[i];
+      GemmTask t{};
+      t.A = pool + P.diag_off[i]; t.lda = n; t.ta = 0;
+      t.B = U; t.ldb = n; t.tb = 0;
+      t.C = ws + r.w2_off; t.ldc = n; t.tc = 0;
+      t.Cin = t.C; t.ldcin = n;
+      t.M = n; t.N = n; t.K = n; t.alpha = 1.f; t.beta = 0.f;
+      g1.push_back(t);
+      GemmTask u{};
+      u.A = U; u.lda = n; u.ta = 1;
+      u.B = ws + r.w2_off; u.ldb = n; u.tb = 0;
+      u.C = ws + r.t_off; u.ldc = n; u.tc = 0;
+      u.Cin = u.C; u.ldcin = n;
+      u.M = n; u.N = n; u.K = n; u.alpha = 1.f; u.beta = 0.f;
+      g2.push_back(u);
+    }
+    bcheck(launch_gemm_t<T>(g1, s));
+    bcheck(launch_gemm_t<T>(g2, s));
+    // ---- 5: Cholesky of T_nn and L_hat^{-1} ----
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    cholinv_kernel<T><<<nr, kBigThreads, 0, s>>>(drows, ws, D, args);
+    bcheck(cudaGetLastError());
+    // ---- 6: W_b, Y_p, far rows ----
+    std::vector<GemmTask> g3, g4, g5;
+    for (int q = q0; q < q1; ++q) {
+      const BigRowDev& rw = rows[q - q0];
+      const int i = rw.i, n = rw.n, r = rank_h[i], m = n - r;
+      if (n == 0) continue;
+      const T* U = Uf + P.u_off[i];
+      const T* Li = Lf + P.l_off[i];
+      T* Wb = Wf + P.w_off[i];
+      if (m > 0 && r > 0) {
+        GemmTask t{};  // W_b = L_hat^{-1} T[r:, :r]
+        t.A = Li; t.lda = m; t.ta = 0;
+        t.B = ws + rw.t_off + (int64_t)r * n; t.ldb = n; t.tb = 0;
+        t.C = Wb; t.ldc = r; t.Cin = Wb; t.ldcin = r;
+        t.M = m; t.N = r; t.K = m; t.alpha = 1.f; t.beta = 0.f;
+        g3.push_back(t);
+      }
+      // close targets: Y_p = U^T C_ip (n x w_p)
+      int64_t colst = n;
+      for (int tt = P.close_ptr[i], ti = 0; tt < P.close_ptr[i + 1]; ++tt, ++ti) {
+        const int p = P.close_blk[tt], w = width(p);
+        const int64_t ycol = colst;
+        colst += P.n[p];
+        (void)ycol;
+        if (w == 0) continue;
+        const PairView pv = pair_view(P, i, p);
+        GemmTask t{};
+        t.A = U; t.lda = n; t.ta = 1;
+        t.B = pool + pv.off; t.ldb = pv.ld; t.tb = pv.trans;
+        t.C = ws + yoff[q - q0][ti]; t.ldc = w; t.Cin = t.C; t.ldcin = w;
+        t.M = n; t.N = w; t.K = n; t.alpha = 1.f; t.beta = 0.f;
+        g3.push_back(t);
+      }
+      // far rows: F_ik <- U_b^T F_ik (the rows r.. are E_i and are dropped)
+      if (r > 0) {
+        const std::vector<int>& fp = fpre[q - q0];
+        for (int f = P.far_ptr[i], ff = 0; f < P.far_ptr[i + 1]; ++f, ++ff) {
+          const int k = P.far_blk[f], w = width(k);
+          if (w == 0) continue;
+          const PairView pv = pair_view(P, i, k);
+          GemmTask t{};
+          t.A = U; t.lda = n; t.ta = 1;
+          t.B = ws + rw.g_off + (int64_t)fp[ff] * n; t.ldb = n; t.tb = 1;
+          t.C = pool + pv.off; t.ldc = pv.ld; t.tc = pv.trans;
+          t.Cin = t.C; t.ldcin = pv.ld; t.tcin = pv.trans;
+          t.M = r; t.N = w; t.K = n; t.alpha = 1.f; t.beta = 0.f;
+          g3.push_back(t);
+        }
+      }
+    }
+    bcheck(launch_gemm_t<T>(g3, s));
+    // ---- 7: D_i <- T[:r, :r] - W_b^T W_b;  W_p = L_hat^{-1} Y_p[r:] ----
+    for (int q = q0; q < q1; ++q) {
+      const BigRowDev& rw = rows[q - q0];
+      const int i = rw.i, n = rw.n, r = rank_h[i], m = n - r;
+      if (n == 0 || r == 0) continue;
+      const T* Li = Lf + P.l_off[i];
+      T* Wb = Wf + P.w_off[i];
+      GemmTask t{};
+      t.A = Wb; t.lda = r; t.ta = 1;
+      t.B = Wb; t.ldb = r; t.tb = 0;
+      t.Cin = ws + rw.t_off; t.ldcin = n;
+      t.C = pool + P.diag_off[i]; t.ldc = n;
+      t.M = r; t.N = r; t.K = m; t.alpha = -1.f; t.beta = 1.f;
+      g4.push_back(t);
+      (void)Li;
+    }
+    for (int q = q0; q < q1; ++q) {
+      const BigRowDev& rw = rows[q - q0];
+      const int i = rw.i, n = rw.n, r = rank_h[i], m = n - r;
+      if (n == 0 || m == 0) continue;
+      const T* Li = Lf + P.l_off[i];
+      int64_t colst = n;
+      for (int tt = P.close_ptr[i], ti = 0; tt < P.close_ptr[i + 1]; ++tt, ++ti) {
+        const int p = P.close_blk[tt], w = width(p);
+        T* Wp = Wf + P.w_off[i] + (int64_t)n * colst;
+        colst += P.n[p];
+        if (w == 0) continue;
+        GemmTask t{};
+        t.A = Li; t.lda = m; t.ta = 0;
+        t.B = ws + yoff[q - q0][ti] + (int64_t)r * w; t.ldb = w; t.tb = 0;
+        t.C = Wp; t.ldc = w; t.Cin = Wp; t.ldcin = w;
+        t.M = m; t.N = w; t.K = m; t.alpha = 1.f; t.beta = 0.f;
+        g4.push_back(t);
+      }
+    }
+    // D_i with r == 0: the block is eliminated whole (nothing kept)
+    bcheck(launch_gemm_t<T>(g4, s));
+    // ---- 8: kept close rows and the Schur update ----
+    for (int q = q0; q < q1; ++q) {
+      const BigRowDev& rw = rows[q - q0];
+      const int i = rw.i, n = rw.n, r = rank_h[i], m = n - r;
+      if (n == 0) continue;
+      const T* Wb = Wf + P.w_off[i];
+      std::vector<int> tp, tw;
+      std::vector<const T*> tW;
+      int64_t colst = n;
+      for (int tt = P.close_ptr[i], ti = 0; tt < P.close_ptr[i + 1]; ++tt, ++ti) {
+        const int p = P.close_blk[tt], w = width(p);
+        const T* Wp = Wf + P.w_off[i] + (int64_t)n * colst;
+        colst += P.n[p];
+        if (w == 0) continue;
+        if (r > 0) {  // kept rows of (i, p): Y_p[:r] - W_b^T W_p
+          const PairView pv = pair_view(P, i, p);
+          GemmTask t{};
+          t.A = Wb; t.lda = r; t.ta = 1;
+          t.B = Wp; t.ldb = w; t.tb = 0;
+          t.Cin = ws + yoff[q - q0][ti]; t.ldcin = w;
+          t.C = pool + pv.off; t.ldc = pv.ld; t.tc = pv.trans;
+          t.M = r; t.N = w; t.K = m; t.alpha = -1.f; t.beta = 1.f;
+          if (m == 0) {  // nothing eliminated: the kept rows are Y_p[:r]
+            t.K = 0;
+          }
+          g5.push_back(t);
+        }
+        tp.push_back(p);
+        tw.push_back(w);
+        tW.push_back(Wp);
+      }
+      if (m == 0) continue;
+      for (size_t a2 = 0; a2 < tp.size(); ++a2)
+        for (size_t b2 = a2; b2 < tp.size(); ++b2) {
+          const int p = tp[a2], qq = tp[b2];
+          const PairView pv = pair_view(P, p, qq);
+          GemmTask t{};
+          t.A = tW[a2]; t.lda = tw[a2]; t.ta = 1;
+          t.B = tW[b2]; t.ldb = tw[b2]; t.tb = 0;
+          t.C = pool + pv.off; t.ldc = pv.ld; t.tc = pv.trans;
+          t.Cin = t.C; t.ldcin = pv.ld; t.tcin = pv.trans;
+          t.M = tw[a2]; t.N = tw[b2]; t.K = m; t.alpha = -1.f; t.beta = 1.f;
+          g5.push_back(t);
+        }
+    }
+    bcheck(launch_gemm_t<T>(g5, s));
+    for (int q = q0; q < q1; ++q) done[P.order[q]] = 1;
+    bcheck(cudaFreeAsync(ws, s));
+    bcheck(cudaFreeAsync(drows, s));
+    int hs2 = 0;
+    bcheck(cudaMemcpyAsync(&hs2, args.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    bcheck(cudaStreamSynchronize(s));
+    if (hs2 != 0) return;
+  }
+}
+
+}  // namespace
+
+bool level_needs_big_rows(const LevelPlan& P) {
+  if (P.nmax > kNMax) return true;
+  for (int i = 0; i < P.M; ++i) {
+    if (1 + P.close_ptr[i + 1] - P.close_ptr[i] > 32) return true;
+    if (P.far_ptr[i + 1] - P.far_ptr[i] > 128) return true;
+  }
+  return false;
+}
+
+cudaError_t run_big_level(int esize, LevelStore& st, int level, double tol, int tol_mode, int* status, int* stats,
+                          cudaStream_t s) {
+  BigLevelArgs a{level, tol, tol_mode, status, stats};
+  try {
+    std::vector<int> rank_h;
+    if (esize == 8)
+      run_big_level_t<double>(st, s, a, rank_h);
+    else
+      run_big_level_t<float>(st, s, a, rank_h);
+  } catch (const BigFail& f) {
+    return f.e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_apply_big(int esize, const LevelDev& L, const LevelPlan& P, double* vec, int forward,
+                             cudaStream_t s) {
+  const size_t sm = (size_t)3 * std::max(P.nmax, 1) * esize;
+  for (int cc = 0; cc < P.ncolours; ++cc) {
+    const int c = forward ? cc : P.ncolours - 1 - cc;
+    const int q0 = P.colour_ptr[c], cnt = P.colour_ptr[c + 1] - q0;
+    if (cnt <= 0) continue;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    if (esize == 8) {
+      if (forward)
+        apply_big_kernel<double, true><<<cnt, kBigThreads, sm, s>>>(L, q0, vec);
+      else
+        apply_big_kernel<double, false><<<cnt, kBigThreads, sm, s>>>(L, q0, vec);
+    } else {
+      if (forward)
+        apply_big_kernel<float, true><<<cnt, kBigThreads, sm, s>>>(L, q0, vec);
+      else
+        apply_big_kernel<float, false><<<cnt, kBigThreads, sm, s>>>(L, q0, vec);
+    }
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace ce

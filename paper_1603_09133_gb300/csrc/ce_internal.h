@@ -17,6 +17,8 @@
 namespace ce {
 
 constexpr int kNMax = 64;  // largest block the row kernel holds in shared memory
+constexpr int kBigMaxN = 1536;       // largest block of the large-row path
+constexpr int kBigMaxTargets = 64;   // most targets (1 + close blocks) of a large row
 constexpr int kBuckets = 3;  // size buckets of a batch's rows (<= 16, <= 32, <= 64 rows)
 
 // Host threads for the planning loops (hardware threads, at most 16).
@@ -218,6 +220,7 @@ struct LevelStore {
   std::shared_ptr<const LevelPlan> plan;  // level 1 may share the csb's plan
   std::vector<int> rank;        // host copy
   std::vector<int> kw;          // host copy of the per-row sketch widths
+  bool big = false;             // eliminated by the large-row path (big_rows.cu)
   LevelDev dev{};
   void* meta = nullptr;         // device per-factorization state (ranks, flags, ...)
   void* smeta = nullptr;        // device arrays fixed by the plan (null: shared)

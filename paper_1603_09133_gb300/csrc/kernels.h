@@ -42,6 +42,8 @@ struct LearnedArgs {
   int J = 4;                      // children per super-block (parent-rank feature)
   unsigned long long seed = 0;    // key of the counter-based sketch generator
   int* stats = nullptr;           // kStatsWords counters, see below
+  bool record = false;            // compute and record the features on every row
+                                  // with far columns, also without a model
 };
 
 // per-level counters of a factorization (levels 0..15): [2 l] rows whose
@@ -101,6 +103,31 @@ cudaError_t mlp_adam_step(const float* X, const float* t, int ns, float* theta, 
 int mlp_partial_blocks(int ns);
 cudaError_t mlp_pack(const float* theta, void* model, cudaStream_t s);
 cudaError_t mlp_predict(const float* X, int ns, const void* model, float* out, cudaStream_t s);
+
+// Grouped GEMM task: C = alpha op(A) op(B) + beta op(Cin), M x N, inner K.
+// ta: A stored K x M (element (m, k) at A[k lda + m]), else M x K;
+// tb: B stored N x K (element (k, n) at B[n ldb + k]), else K x N;
+// tc / tcin: C / Cin stored N x M, else M x N.  Cin may alias C.
+struct GemmTask {
+  const void* A;
+  const void* B;
+  const void* Cin;
+  void* C;
+  int M, N, K;
+  int lda, ldb, ldcin, ldc;
+  int ta, tb, tcin, tc;
+  float alpha, beta;
+  int tile0;   // first tile of the task in its launch (set by the launcher)
+};
+
+// large-row levels (big_rows.cu): whether a level needs them, the level's
+// elimination (per colour, synchronizing the stream once per colour), and the
+// apply of such a level (one launch per colour)
+bool level_needs_big_rows(const LevelPlan& P);
+cudaError_t run_big_level(int esize, LevelStore& st, int level, double tol, int tol_mode, int* status, int* stats,
+                          cudaStream_t s);
+cudaError_t launch_apply_big(int esize, const LevelDev& L, const LevelPlan& P, double* vec, int forward,
+                             cudaStream_t s);
 
 // arithmetic peak probes (probes.cu): 0 FP32 FFMA, 1 FP64 DFMA, 2 TF32
 // mma.sync m16n8k8, 3 the 3xTF32 product (three TF32 MMAs per product)

@@ -495,7 +495,7 @@ std::vector<int> coarsen_parents(const LevelPlan& P, int J, const std::vector<in
   if (sys_off) sys_off->assign(so.size(), 0);
   int next = 0;
   // emit [a, b) as one super-block, or halve it (first half ceil(len/2)) while
-  // its ranks add up to more than nmax rows
+  // its ranks add up to more than nmax rows (nmax <= 0: no cap)
   std::vector<std::pair<int, int>> stack;
   auto emit_run = [&](int a0, int b0) {
     stack.assign(1, {a0, b0});
@@ -505,7 +505,7 @@ std::vector<int> coarsen_parents(const LevelPlan& P, int J, const std::vector<in
       int tot = 0;
       if (rank)
         for (int i = a; i < b; ++i) tot += (*rank)[i];
-      if (b - a == 1 || !rank || tot <= nmax) {
+      if (b - a == 1 || !rank || nmax <= 0 || tot <= nmax) {
         for (int i = a; i < b; ++i) parent[i] = next;
         if (first_child) first_child->push_back(b);
         ++next;

@@ -459,7 +459,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
   // values and vectors of Q^T F.  Accepted when the sketch is not saturated
   // (r < k) and the probe estimate of the out-of-sketch residual is at most
   // tau / 2; otherwise the exact phases A-B run.
-  if (mF > 0 && la.model != nullptr) {
+  if (mF > 0 && (la.model != nullptr || la.record)) {
     const int cc0 = L.close_ptr[i], nclose = L.close_ptr[i + 1] - cc0;
     for (int f = warp; f < nf + nclose; f += kWarpsNT) {
       int k, w;
@@ -513,6 +513,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     }
     __syncthreads();
     if (L.feat != nullptr && tid < kMlpFeatures) L.feat[(int64_t)i * kMlpFeatures + tid] = s_x[tid];
+    if (la.model != nullptr) {
     if (warp == 0) {
       const float yh = mlp_infer_warp(la.model, s_x, s_h);
       if (lane == 0) {
@@ -867,6 +868,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
       if (lvl_ok) atomicAdd(la.stats + 2 * level + 1, 1);
       if (L.kw) L.kw[i] = 0;
     }
+    }  // la.model
   }
 
   // ---------------- A. R factor of F_i^T (warp TSQR + tree merge) ----------

@@ -61,7 +61,7 @@ def _ranks_ok(lev, r_g, rel=1e-5):
 def small_batch():
     # five small systems of three grid sizes (the oracle runs each alone)
     ws = wl.make_batch(5, seed=3, choices=(32, 48, 64), levels=3)
-    Fos = [oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J, nmax=64) for w in ws]
+    Fos = [oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J) for w in ws]
     return ws, Fos
 
 
@@ -215,7 +215,7 @@ def test_batched_full_size_256_systems(ceg):
              next(s for s, w in enumerate(ws) if w.A.shape[0] == 16384)]
     for s in picks:
         w = ws[s]
-        Fo = oce.factorize(w.A, w.perm, w.B, 1e-4, 4, 4, nmax=64)
+        Fo = oce.factorize(w.A, w.perm, w.B, 1e-4, 4, 4)
         zs = zg[sl[s]]
         eta = np.linalg.norm(w.b - oce.multiply(Fo, zs)) / (
             _anorm(w.A) * np.linalg.norm(zs) + np.linalg.norm(w.b))

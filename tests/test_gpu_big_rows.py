@@ -1,0 +1,133 @@
+"""GPU parity of the large-row path (levels whose blocks outgrow the row
+kernel: more than 64 rows, or more than 32 close / 128 far blocks) against
+the FP64 oracle, on the paper's kind of problem where it is needed: 3D grids
+coarsened by J = 8 boxes of boxes (Section 2.4) with no cap on the
+super-blocks.
+
+* 3D Poisson 32^3 (7-point, 4^3 boxes, B = 64, tol 1e-4, 4 levels, J = 8):
+  level 1 runs the row kernel (512 blocks of 64 rows), level 2 the large-row
+  path with compression (64 blocks of up to ~260 rows, up to 19 targets and
+  34 far blocks), level 3 the large-row path without far blocks (8 blocks of
+  up to ~390 rows, eliminated whole).  FP64 form: ranks equal the oracle's
+  except within 1e-5 relative of tau, apply within 1e-10, PCG iterations
+  +-1 and a true residual <= 1e-8.  FP32 form: normwise backward error
+  against the oracle's operator <= 1e-4, PCG +-1.
+* 3D Poisson 16^3 (B = 64): the second level is 8 blocks of ~210 rows with no
+  far blocks, eliminated whole by the large-row path; apply within 1e-10.
+"""
+import numpy as np
+import pytest
+
+import workloads as wl
+from oracle import ce as oce
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ceg():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1603_09133_gb300 import build
+    build.build()
+    import paper_1603_09133_gb300 as m
+    return m
+
+
+_CACHE = {}
+
+
+def _problem(g):
+    if g not in _CACHE:
+        A = wl.poisson3d(g)
+        perm = wl.box_perm((g, g, g), (4, 4, 4))
+        b = wl.rhs(A.shape[0], 3)
+        Fo = oce.factorize(A, perm, 64, 1e-4, 4, 8)
+        _CACHE[g] = (A, perm, b, Fo)
+    return _CACHE[g]
+
+
+def _apply(ceg, F, b):
+    r = torch.as_tensor(b, device="cuda")
+    z = torch.empty_like(r)
+    ceg.ce_apply(F, r, z)
+    torch.cuda.synchronize()
+    return z.cpu().numpy()
+
+
+def _ranks_agree(lev, r_g, rel=1e-5):
+    bad = []
+    for st in lev.steps:
+        if r_g[st.i] == st.r:
+            continue
+        lo, hi = sorted((r_g[st.i], st.r))
+        if not all(k < st.sigma.size and abs(st.sigma[k] - st.tau) <= rel * st.tau for k in range(lo, hi)):
+            bad.append((st.i, st.r, int(r_g[st.i])))
+    return bad
+
+
+def _pcg(ceg, csb, F, A, b):
+    x = torch.zeros(A.shape[0], dtype=torch.float64, device="cuda")
+    it, rel, conv = ceg.pcg_solve(csb, F, torch.as_tensor(b, device="cuda"), x, 1e-8, 200)
+    torch.cuda.synchronize()
+    xh = x.cpu().numpy()
+    return it, conv, np.linalg.norm(b - A @ xh) / np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_big_rows_3d_32(ceg, precision):
+    A, perm, b, Fo = _problem(32)
+    csb = ceg.csb_build(A, perm, 64)
+    F = ceg.ce_factorize(csb, tol=1e-4, levels=4, J=8, precision=precision)
+    info = F.info
+    big = [info.big_rows[l] for l in range(info.levels_done)]
+    print(f"{precision}: levels {info.levels_done}, big {big}, blocks {list(info.blocks[:info.levels_done])}, "
+          f"max block {list(info.max_block[:info.levels_done])}, level ms "
+          f"{[round(info.level_ms[l], 2) for l in range(info.levels_done)]}, coarse {info.coarse_n}")
+    assert big[0] == 0 and big[1] == 1
+    same = True
+    for l, lev in enumerate(Fo.levels):
+        if not same:
+            break
+        n_g, r_g, c_g, tau_g = F.level(l)
+        assert list(n_g) == list(lev.sizes) and list(c_g) == list(lev.colour)
+        if precision == "fp64":
+            assert _ranks_agree(lev, r_g) == []
+            for st in lev.steps:
+                if st.sigma.size:
+                    assert tau_g[st.i] == pytest.approx(st.tau, rel=1e-9)
+        same = list(r_g) == list(lev.ranks)
+    z = _apply(ceg, F, b)
+    if precision == "fp64":
+        zo = oce.apply(Fo, b)
+        err = np.linalg.norm(z - zo) / np.linalg.norm(zo)
+        print(f"apply error {err:.3e}")
+        assert err <= 1e-10, err
+    else:
+        import scipy.sparse.linalg as spla
+        anorm = float(spla.eigsh(A, k=1, which="LA", return_eigenvectors=False)[0])
+        eta = np.linalg.norm(b - oce.multiply(Fo, z)) / (anorm * np.linalg.norm(z) + np.linalg.norm(b))
+        print(f"backward error {eta:.3e}")
+        assert eta <= 1e-4, eta
+    it, conv, rel = _pcg(ceg, csb, F, A, b)
+    it_o = oce.pcg(A, Fo, b, 1e-8, 200).iters
+    print(f"PCG {it} (oracle {it_o}), true residual {rel:.2e}")
+    assert conv and rel <= 1e-8 * 1.01
+    assert abs(it - it_o) <= 1
+
+
+def test_big_rows_eliminate_whole_blocks_16(ceg):
+    A = wl.poisson3d(16)
+    perm = wl.box_perm((16, 16, 16), (4, 4, 4))
+    b = wl.rhs(A.shape[0], 5)
+    Fo = oce.factorize(A, perm, 64, 1e-4, 2, 8)
+    csb = ceg.csb_build(A, perm, 64)
+    F = ceg.ce_factorize(csb, tol=1e-4, levels=2, J=8)
+    assert F.info.big_rows[1] == 1 and F.info.big_rows[0] == 0
+    n_g, r_g, _, _ = F.level(1)
+    assert list(n_g) == list(Fo.levels[1].sizes) and not any(r_g)
+    z = _apply(ceg, F, b)
+    zo = oce.apply(Fo, b)
+    assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 1e-10

@@ -72,7 +72,7 @@ def _levels_agree(F, Fo):
 def test_fixed_rank_fp64_matches_oracle(ceg, kind, n, box, B, r, levels):
     A, perm = _problem(kind, n, box)
     b = wl.rhs(n * n, 0)
-    Fo = oce.factorize(A, perm, B, 0.0, levels, 4, tol_mode="fixed", rank=r, nmax=64)
+    Fo = oce.factorize(A, perm, B, 0.0, levels, 4, tol_mode="fixed", rank=r)
     csb = ceg.csb_build(A, perm, B)
     F = ceg.ce_factorize(csb, levels=levels, J=4, tol_mode="fixed", rank=r)
     agreed = _levels_agree(F, Fo)
@@ -95,7 +95,7 @@ def test_fixed_rank_fp64_matches_oracle(ceg, kind, n, box, B, r, levels):
 def test_fixed_rank_fp32_preconditions(ceg, kind, n, box, B, r, levels):
     A, perm = _problem(kind, n, box)
     b = wl.rhs(n * n, 1)
-    Fo = oce.factorize(A, perm, B, 0.0, levels, 4, tol_mode="fixed", rank=r, nmax=64)
+    Fo = oce.factorize(A, perm, B, 0.0, levels, 4, tol_mode="fixed", rank=r)
     csb = ceg.csb_build(A, perm, B)
     F = ceg.ce_factorize(csb, levels=levels, J=4, tol_mode="fixed", rank=r, precision="fp32")
     for l in range(F.levels()):

@@ -44,7 +44,7 @@ def test_grf_small_matches_oracle(ceg):
     A = wl.diffusion2d(wl.grf2d(n, 3))
     perm = wl.box_perm((n, n), (8, 4))
     b = wl.rhs(A.shape[0], 5)
-    Fo = oce.factorize(A, perm, 32, 1e-4, 3, 4, nmax=64)
+    Fo = oce.factorize(A, perm, 32, 1e-4, 3, 4)
     csb = ceg.csb_build(A, perm, 32)
     F = ceg.ce_factorize(csb, tol=1e-4, levels=3, J=4)
     same = True

@@ -93,25 +93,27 @@ def test_learned_factorization_small(ceg, trained, precision):
     assert conv_l and res_l <= 1e-8 * 1.01
     assert it_l <= it_e + 2, (it_e, it_l)
     # the learned M against the oracle's operator (normwise backward error)
-    Fo = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J, nmax=64)
+    Fo = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J)
     z = _apply(ceg, Fl, w.b)
     import scipy.sparse.linalg as spla
     anorm = float(spla.eigsh(w.A, k=1, which="LA", return_eigenvectors=False)[0])
     eta = np.linalg.norm(w.b - oce.multiply(Fo, z)) / (anorm * np.linalg.norm(z) + np.linalg.norm(w.b))
     print(f"{precision}: accepted {acc}, fallback {fb}, PCG {it_e} -> {it_l}, eta {eta:.2e}")
-    assert eta <= 10 * w.tol
+    assert eta <= 1e-4
 
 
 def test_learned_gain_full_size(ceg, trained):
     """What the trained network gains: 512^2 Poisson, FP32 form, exact SVD vs
-    learned widths (same matrix, same tolerance)."""
+    learned widths (same matrix, same tolerance; super-blocks capped at 64 rows
+    as in the benchmark, so every level runs the row kernel)."""
     model = trained[0]
     w = wl.make_workload("poisson2d_512_B32")
     csb = ceg.csb_build(w.A, w.perm, w.B)
     res = {}
     for name, rm in (("exact", None), ("learned", model)):
-        ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision="fp32", rank_model=rm)
-        F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision="fp32", rank_model=rm)
+        ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision="fp32", rank_model=rm, nmax=64)
+        F = ceg.ce_factorize(csb, tol=w.tol, levels=w.levels, J=w.J, precision="fp32", rank_model=rm,
+                             nmax=64)
         ms = sum(F.info.level_ms[l] for l in range(F.info.levels_done))
         it, conv, rel = _pcg(ceg, csb, F, w.A, w.b)
         assert conv and rel <= 1e-8 * 1.01

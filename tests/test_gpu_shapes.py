@@ -29,7 +29,7 @@ def ceg():
 @pytest.fixture(scope="module")
 def problem():
     w = wl.make_workload("poisson2d_64_B16")
-    Fo = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J, nmax=64)
+    Fo = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J)
     return w, Fo, oce.apply(Fo, w.b)
 
 

@@ -53,7 +53,7 @@ def test_update_values_equals_fresh_build(ceg):
             assert np.array_equal(a, c), l
     z2 = _apply(ceg, F2, b)
     assert np.array_equal(z2, _apply(ceg, Ff, b))
-    Fo = oce.factorize(A2, perm, 16, 1e-6, 3, 4, nmax=64)
+    Fo = oce.factorize(A2, perm, 16, 1e-6, 3, 4)
     zo = oce.apply(Fo, b)
     assert np.linalg.norm(z2 - zo) / np.linalg.norm(zo) <= 1e-10
     # the factor made before the update keeps its own values

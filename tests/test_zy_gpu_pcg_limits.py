@@ -38,7 +38,7 @@ def test_pcg_iteration_limit(ceg, maxit):
     perm = wl.box_perm((n, n), (4, 4))
     b = wl.rhs(n * n, 2)
     # a weak preconditioner (CE(1): one direction per far row) needs many steps
-    Fo = oce.factorize(A, perm, 16, 0.0, 2, 4, tol_mode="fixed", rank=1, nmax=64)
+    Fo = oce.factorize(A, perm, 16, 0.0, 2, 4, tol_mode="fixed", rank=1)
     res_o = oce.pcg(A, Fo, b, 1e-12, maxit)
     assert not res_o.converged
     csb = ceg.csb_build(A, perm, 16)

@@ -46,7 +46,7 @@ def oracle_factors():
         A = wl.poisson3d(n)
         perm = wl.box_perm((n, n, n), box)
         B = int(np.prod(box))
-        out[(n, box)] = (A, perm, B, oce.factorize(A, perm, B, 1e-4, levels, 8, nmax=64))
+        out[(n, box)] = (A, perm, B, oce.factorize(A, perm, B, 1e-4, levels, 8))
     return out
 
 
