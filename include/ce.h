@@ -554,6 +554,21 @@ ce_status ce_plan_groups(int M, const int32_t* rank, int J, int nmax, int32_t* f
  */
 ce_status ce_debug_wait_expiry(int kernel, double limit_ms, int32_t* status_out, void* stream);
 
+/*
+ * ce_debug_gemm -- one product C = alpha op(A) op(B) + beta C through one of
+ * the library's GEMM engines (for tests; not part of the paper):
+ *   engine 0: CUDA cores, FP32; 3: CUDA cores, FP64; 1: tensor cores
+ *   (tcgen05, FP32 operands split into BF16 hi + lo, three products
+ *   hi*hi + hi*lo + lo*hi, FP32 accumulation); 2: tensor cores, one BF16
+ *   product (hi*hi).  Engines 0-2 take FP32 arrays, engine 3 FP64.
+ *   A_dev  M x K (ta = 0, element (m, k) at A[m lda + k]) or K x M (ta = 1)
+ *   B_dev  K x N (tb = 0) or N x K (tb = 1, element (k, n) at B[n ldb + k])
+ *   C_dev  M x N (tc = 0) or N x M (tc = 1), read when beta != 0
+ * Synchronizes the stream.  CE_ERR_CUDA if a tensor-core pipeline wait expired.
+ */
+ce_status ce_debug_gemm(int engine, int M, int N, int K, const void* A_dev, int lda, int ta, const void* B_dev,
+                        int ldb, int tb, void* C_dev, int ldc, int tc, double alpha, double beta, void* stream);
+
 /* Level-1 plan of a csb handle: blocks, colours, colour of every block. */
 int csb_blocks(const ce_csb* A);
 ce_status csb_get_colours(const ce_csb* A, int32_t* colour, int* ncolours);

@@ -131,6 +131,8 @@ SIGNATURES = {
     "csb_get_tuning": (C.c_int, [P, C.c_int, C.c_int, C.POINTER(C.c_int), I32P, I32P]),
     "csb_set_tuning": (C.c_int, [P, C.c_int, C.c_int, C.c_int, I32P, I32P]),
     "ce_debug_wait_expiry": (C.c_int, [C.c_int, C.c_double, I32P, P]),
+    "ce_debug_gemm": (C.c_int, [C.c_int, C.c_int, C.c_int, C.c_int, P, C.c_int, C.c_int, P, C.c_int, C.c_int,
+                                P, C.c_int, C.c_int, C.c_double, C.c_double, P]),
     "ce_plan_level1": (C.c_int, [C.c_int64, I64P, I32P, I32P, C.c_int32, I32P,
                                  C.POINTER(C.c_int), I64P, I64P]),
     "csb_get_colours": (C.c_int, [P, I32P, C.POINTER(C.c_int)]),

@@ -1702,6 +1702,57 @@ ce_status ce_debug_wait_expiry(int kernel, double limit_ms, int32_t* status_out,
   return ret;
 }
 
+ce_status ce_debug_gemm(int engine, int M, int N, int K, const void* A_dev, int lda, int ta, const void* B_dev,
+                        int ldb, int tb, void* C_dev, int ldc, int tc, double alpha, double beta, void* stream) {
+  if (engine < 0 || engine > 3 || M < 0 || N < 0 || K < 0 || !A_dev || !B_dev || !C_dev || lda <= 0 || ldb <= 0 ||
+      ldc <= 0)
+    return CE_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int* err = nullptr;
+  try {
+    ce::GemmTask t{};
+    t.A = A_dev;
+    t.lda = lda;
+    t.ta = ta != 0;
+    t.B = B_dev;
+    t.ldb = ldb;
+    t.tb = tb != 0;
+    t.C = C_dev;
+    t.ldc = ldc;
+    t.tc = tc != 0;
+    t.Cin = C_dev;
+    t.ldcin = ldc;
+    t.tcin = tc != 0;
+    t.M = M;
+    t.N = N;
+    t.K = K;
+    t.alpha = static_cast<float>(alpha);
+    t.beta = static_cast<float>(beta);
+    const std::vector<ce::GemmTask> tasks{t};
+    if (engine == 0 || engine == 3) {
+      check(ce::launch_gemm_cuda(engine == 3 ? 8 : 4, tasks, s), "gemm");
+    } else {
+      err = static_cast<int*>(dalloc(sizeof(int), s));
+      check(cudaMemsetAsync(err, 0, sizeof(int), s), "memset");
+      check(ce::launch_gemm_tc(tasks, engine == 1 ? 3 : 1, err, s), "tcgen05 gemm");
+      int herr = 0;
+      check(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s), "D2H");
+      check(cudaStreamSynchronize(s), "sync");
+      dfree(err, s);
+      err = nullptr;
+      if (herr) {
+        g_last_error = "tcgen05 gemm: a pipeline wait expired";
+        return CE_ERR_CUDA;
+      }
+    }
+    check(cudaStreamSynchronize(s), "sync");
+  } catch (...) {
+    dfree(err, s);
+    return status_of_exception();
+  }
+  return CE_OK;
+}
+
 ce_status ce_factor_get_features(const ce_factor* F, int level, float* feat, int32_t* kw) {
   if (!F || level < 0 || level >= static_cast<int>(F->levels.size())) return CE_ERR_INVALID_ARG;
   const LevelStore& st = F->levels[level];

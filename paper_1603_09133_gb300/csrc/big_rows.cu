@@ -1140,6 +1140,10 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
 
 }  // namespace
 
+cudaError_t launch_gemm_cuda(int esize, const std::vector<GemmTask>& tasks, cudaStream_t s) {
+  return esize == 8 ? launch_gemm_t<double>(tasks, s) : launch_gemm_t<float>(tasks, s);
+}
+
 bool level_needs_big_rows(const LevelPlan& P) {
   if (P.nmax > kNMax) return true;
   for (int i = 0; i < P.M; ++i) {

@@ -8,6 +8,7 @@
 
 #include <atomic>
 #include <string>
+#include <vector>
 
 namespace ce {
 
@@ -119,6 +120,13 @@ struct GemmTask {
   float alpha, beta;
   int tile0;   // first tile of the task in its launch (set by the launcher)
 };
+
+// grouped GEMM engines: CUDA cores (FP32 or FP64 by esize, big_rows.cu) and
+// the tensor cores (tc_gemm.cu: FP32 operands as BF16 hi + lo, TMA-staged,
+// tcgen05.mma into TMEM; passes 3 = hi*hi + hi*lo + lo*hi, 1 = hi*hi; tasks
+// with K = 0 are skipped; *err is set when a pipeline wait expires)
+cudaError_t launch_gemm_cuda(int esize, const std::vector<GemmTask>& tasks, cudaStream_t s);
+cudaError_t launch_gemm_tc(const std::vector<GemmTask>& tasks, int passes, int* err, cudaStream_t s);
 
 // large-row levels (big_rows.cu): whether a level needs them, the level's
 // elimination (per colour, synchronizing the stream once per colour), and the
