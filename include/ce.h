@@ -94,6 +94,12 @@ typedef struct {
   int record_features; /* 1: every row with far columns records the rank
                       model's features (ce_factor_get_features), also on
                       levels that run the exact SVD (default 0)           */
+  int gemm_engine; /* products of the large-row path in the FP32 form:
+                      0 (default) tensor cores, FP32 operands split into
+                      BF16 hi + lo, three products, FP32 accumulation;
+                      1 CUDA cores (FP32 FMA); 2 as 0, but the Schur
+                      updates W_p^T W_q with one BF16 product (FP32
+                      accumulate).  The FP64 form uses the CUDA cores.     */
 } ce_opts;
 
 typedef struct {
@@ -149,7 +155,8 @@ typedef struct {
 
 /* Defaults: tol 1e-4, CE_TOL_REL, levels 4, J 4, FP64, colouring on,
  * CE_RANK_SVD, oversample 8, seed 0, row_shape -1 (autotuned, else a
- * heuristic), rank 16, nmax 0 (no super-block cap), record_features 0. */
+ * heuristic), rank 16, nmax 0 (no super-block cap), record_features 0,
+ * gemm_engine 0. */
 void ce_opts_default(ce_opts* o);
 
 /*

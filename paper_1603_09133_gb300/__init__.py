@@ -277,8 +277,11 @@ def _prec(precision):
     return CE_PREC_FP64 if precision == "fp64" else CE_PREC_FP32
 
 
+_ENGINES = {"tc": 0, "cuda": 1, "tc_bf16_schur": 2}
+
+
 def _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed,
-          row_shape, rank=16, nmax=0, record_features=False):
+          row_shape, rank=16, nmax=0, record_features=False, gemm_engine="tc"):
     lib = _lib.load()
     o = _lib.ce_opts()
     lib.ce_opts_default(C.byref(o))
@@ -300,6 +303,9 @@ def _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, ove
     o.row_shape = int(row_shape)
     o.nmax = int(nmax)
     o.record_features = 1 if record_features else 0
+    if gemm_engine not in _ENGINES:
+        raise ValueError(f"gemm_engine must be one of {sorted(_ENGINES)}")
+    o.gemm_engine = _ENGINES[gemm_engine]
     return o
 
 
@@ -319,7 +325,8 @@ def ce_autotune(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="r
 
 def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",
                  coloring=True, stream=None, rank_model=None, oversample=8, seed=0,
-                 row_shape=-1, batched=False, rank=16, nmax=0, record_features=False) -> Factor:
+                 row_shape=-1, batched=False, rank=16, nmax=0, record_features=False,
+                 gemm_engine="tc") -> Factor:
     """Algorithm 1 on the device; returns the factor (raises CEError).
 
     ``rank_model`` (a :class:`RankModel`) switches the compression step to the
@@ -328,11 +335,13 @@ def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="
     ``nmax`` > 0 caps the super-blocks at nmax rows (runs of J halved until
     they fit); 0 is the paper's plain runs of J.  ``record_features`` keeps the
     rank model's features of every row (Factor.features), also without a
-    model.
+    model.  ``gemm_engine`` picks the engine of the large-row products in the
+    FP32 form: "tc" (tensor cores, three split-BF16 products), "cuda" (FP32 on
+    the CUDA cores) or "tc_bf16_schur" (one BF16 product for the Schur updates).
     """
     lib = _lib.load()
     o = _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed,
-              row_shape, rank, nmax, record_features)
+              row_shape, rank, nmax, record_features, gemm_engine)
     info = _lib.ce_info()
     h = C.c_void_p()
     entry = lib.ce_factorize_batched if batched else lib.ce_factorize

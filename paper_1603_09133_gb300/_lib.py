@@ -44,6 +44,7 @@ class ce_opts(C.Structure):
         ("rank", C.c_int),
         ("nmax", C.c_int),
         ("record_features", C.c_int),
+        ("gemm_engine", C.c_int),
     ]
 
 

@@ -596,6 +596,7 @@ void ce_opts_default(ce_opts* o) {
   o->rank = 16;
   o->nmax = 0;
   o->record_features = 0;
+  o->gemm_engine = 0;
 }
 
 const char* ce_strerror(ce_status s) {
@@ -1069,7 +1070,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       (o.tol_mode == CE_TOL_FIXED && (o.rank < 0 || o.rank_mode != CE_RANK_SVD)) ||
       (o.rank_mode != CE_RANK_SVD && o.rank_mode != CE_RANK_LEARNED) ||
       (o.rank_mode == CE_RANK_LEARNED && (!o.rank_model || o.oversample < 0)) || o.row_shape < -1 ||
-      o.row_shape > 2 || o.nmax < 0)
+      o.row_shape > 2 || o.nmax < 0 || o.gemm_engine < 0 || o.gemm_engine > 2)
     return CE_ERR_INVALID_ARG;
   // CE(r): the row kernel takes r in place of the tolerance
   if (o.tol_mode == CE_TOL_FIXED) o.tol = static_cast<double>(o.rank);
@@ -1164,7 +1165,8 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       if (info && l < 16) info->big_rows[l] = big ? 1 : 0;
       const int nbkt = static_cast<int>(P.bucket_nmax.size());
       if (big) {
-        check(ce::run_big_level(es, st, l, o.tol, o.tol_mode, F->d_status, la.stats, s), "large rows");
+        check(ce::run_big_level(es, st, l, o.tol, o.tol_mode, F->d_status, la.stats, o.gemm_engine, s),
+              "large rows");
       } else if (nbkt <= 1) {
         check(ce::launch_row_kernel(es, st.dev, P.M, l, o.tol, o.tol_mode, F->d_status, P.nmax, shape, la_l, s),
               "row kernel");

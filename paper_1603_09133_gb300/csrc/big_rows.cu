@@ -7,7 +7,7 @@
 // steps of every row of the colour run as batched kernels with the row's
 // matrices in global memory:
 //   1. gather F_i^T (mF x n) from the far pairs            (copy tasks)
-//   2. R = R factor of F_i^T                               (tsqr_kernel)
+//   2. R = R factor of F_i^T: parts on several CTAs, merge tree (tsqr_*_kernel)
 //   3. one-sided Jacobi on R: U_i, sigma, r_i, tau_i        (jacobi_kernel)
 //   4. X = D U, T = U^T D U                                (grouped GEMM)
 //   5. T_nn = L_hat L_hat^T, L_hat^{-1}                    (cholinv_kernel)
@@ -184,8 +184,9 @@ __global__ void __launch_bounds__(kGThreads) gemm_tasks_kernel(const GemmTask* t
 struct BigRowDev {
   int i;          // block index in the level
   int n, mF;      // block size and far rows of F_i^T
+  int parts;      // CTAs of the TSQR of F_i^T (a power of 2)
   int64_t g_off;  // F_i^T, mF x n row-major (work space)
-  int64_t x_off;  // n x n: R, then the columns of X (column-major)
+  int64_t x_off;  // parts x n x n: the TSQR's R_p (R_0 = R, the result)
   int64_t v_off;  // n x n: V (column-major)
   int64_t t_off;  // n x n: T = U^T D U (row-major)
   int64_t w2_off; // n x n: D U (row-major), then the Cholesky work matrix
@@ -200,6 +201,7 @@ struct BigRowDev {
 constexpr int kPW = 32;
 constexpr int kBigThreads = 512;
 constexpr int kTsqrThreads = 256;   // the trailing update keeps 64 values per thread in registers
+constexpr int kJacThreads = 1024;   // Jacobi: 64 column pairs of a round at a time
 
 template <typename T>
 __device__ __forceinline__ bool hh_reflector(T x0, T c, T& beta, T& tau, T& sc) {
@@ -217,110 +219,149 @@ __device__ __forceinline__ bool hh_reflector(T x0, T c, T& beta, T& tau, T& sc) 
   return true;
 }
 
+// Push the CH rows held in shared memory (C, CH x n) into the upper
+// triangular R (n x n, global), panels from column p_start (the columns
+// before it are zero in these rows).
 template <typename T, int CH>
-__global__ void __launch_bounds__(kTsqrThreads) tsqr_kernel(const BigRowDev* rows, T* ws) {
-  const BigRowDev rw = rows[blockIdx.x];
-  const int n = rw.n, mF = rw.mF;
-  if (mF <= 0 || n <= 0) return;
+__device__ void stack_chunk(T* R, int n, T* C, int p_start, T (&Rp)[kPW][kPW + 1], T (&Vc)[CH][kPW + 1],
+                            T (&Tm)[kPW][kPW + 1], T (&tauv)[kPW]) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int p0 = p_start; p0 < n; p0 += kPW) {
+    const int pw = min(kPW, n - p0);
+    if (warp == 0) {
+      for (int e = lane; e < kPW * kPW; e += 32) {
+        const int j = e / kPW, l = e % kPW;
+        Rp[j][l] = (j < pw && l < pw) ? R[(int64_t)(p0 + j) * n + p0 + l] : T(0);
+      }
+      for (int e = lane; e < CH * kPW; e += 32) Vc[e / kPW][e % kPW] = T(0);
+      __syncwarp();
+      for (int j = 0; j < pw; ++j) {
+        const T c = (lane < CH) ? C[lane * n + p0 + j] : T(0);
+        T beta, tau, sc;
+        const bool ok = hh_reflector(Rp[j][j], c, beta, tau, sc);
+        if (lane < CH) Vc[lane][j] = ok ? c * sc : T(0);
+        if (lane == 0) tauv[j] = ok ? tau : T(0);
+        __syncwarp();
+        if (ok) {
+          if (lane == 0) Rp[j][j] = beta;
+          const int l = j + 1 + lane;
+          if (l < pw) {
+            T d = Rp[j][l];
+            for (int q = 0; q < CH; ++q) d += Vc[q][j] * C[q * n + p0 + l];
+            d *= tau;
+            Rp[j][l] -= d;
+            for (int q = 0; q < CH; ++q) C[q * n + p0 + l] -= d * Vc[q][j];
+          }
+        }
+        __syncwarp();
+      }
+      for (int e = lane; e < pw * pw; e += 32) {
+        const int j = e / pw, l = e % pw;
+        if (l >= j) R[(int64_t)(p0 + j) * n + p0 + l] = Rp[j][l];
+      }
+      // compact WY: T upper triangular, T[:j, j] = -tau_j T[:j, :j] (V[:, :j]^T v_j);
+      // the R parts of the reflectors are distinct unit vectors, so
+      // v_i^T v_j = vc_i . vc_j
+      for (int j = 0; j < pw; ++j) {
+        T g = T(0);
+        if (lane < j)
+          for (int q = 0; q < CH; ++q) g += Vc[q][lane] * Vc[q][j];
+        Tm[lane][j] = g;   // temporarily v_lane . v_j
+      }
+      __syncwarp();
+      for (int j = 0; j < pw; ++j) {
+        // column j: Tm[i][j] = -tau_j sum_{k=i}^{j-1} T[i][k] g[k][j], i < j
+        T acc = T(0);
+        if (lane < j)
+          for (int k = lane; k < j; ++k) acc += (k == lane ? tauv[k] : Tm[lane][k]) * Tm[k][j];
+        __syncwarp();
+        if (lane < j) Tm[lane][j] = -tauv[j] * acc;
+        __syncwarp();
+      }
+      if (lane < pw) Tm[lane][lane] = tauv[lane];
+    }
+    __syncthreads();
+    // trailing columns: X <- X - V T^T (V^T X), X = [R rows p0.. ; C]
+    for (int l = p0 + pw + tid; l < n; l += kTsqrThreads) {
+      T w[kPW];
+#pragma unroll
+      for (int j = 0; j < kPW; ++j) {
+        T sacc = (j < pw) ? R[(int64_t)(p0 + j) * n + l] : T(0);
+        for (int q = 0; q < CH; ++q) sacc += Vc[q][j] * C[q * n + l];
+        w[j] = sacc;
+      }
+      T w2[kPW];
+#pragma unroll
+      for (int j = 0; j < kPW; ++j) {
+        T sacc = T(0);
+#pragma unroll
+        for (int i2 = 0; i2 <= j; ++i2) sacc += Tm[i2][j] * w[i2];
+        w2[j] = (j < pw) ? sacc : T(0);
+      }
+#pragma unroll
+      for (int j = 0; j < kPW; ++j)
+        if (j < pw) R[(int64_t)(p0 + j) * n + l] -= w2[j];
+      for (int q = 0; q < CH; ++q) {
+        T sacc = T(0);
+#pragma unroll
+        for (int j = 0; j < kPW; ++j) sacc += Vc[q][j] * w2[j];
+        C[q * n + l] -= sacc;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Part p of the TSQR of F_i^T: rows [p mF / P, (p + 1) mF / P) of F_i^T
+// stacked into R_p (n x n at x_off + p n^2), one CTA per (part, row).
+template <typename T, int CH>
+__global__ void __launch_bounds__(kTsqrThreads) tsqr_part_kernel(const BigRowDev* rows, T* ws) {
+  const BigRowDev rw = rows[blockIdx.y];
+  const int n = rw.n, mF = rw.mF, P = rw.parts, p = blockIdx.x;
+  if (mF <= 0 || n <= 0 || p >= P) return;
   extern __shared__ __align__(16) unsigned char big_smem[];
   T* C = reinterpret_cast<T*>(big_smem);          // CH x n
   __shared__ T Rp[kPW][kPW + 1], Vc[CH][kPW + 1], Tm[kPW][kPW + 1], tauv[kPW];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  T* R = ws + rw.x_off;
+  const int tid = threadIdx.x;
+  T* R = ws + rw.x_off + (int64_t)p * n * n;
   const T* G = ws + rw.g_off;
+  const int r0 = (int)((int64_t)mF * p / P), r1 = (int)((int64_t)mF * (p + 1) / P);
   for (int64_t e = tid; e < (int64_t)n * n; e += kTsqrThreads) R[e] = T(0);
   __syncthreads();
-  for (int g0 = 0; g0 < mF; g0 += CH) {
-    const int rows = min(CH, mF - g0);
+  for (int g0 = r0; g0 < r1; g0 += CH) {
+    const int nr = min(CH, r1 - g0);
     for (int e = tid; e < CH * n; e += kTsqrThreads) {
       const int q = e / n, a = e - q * n;
-      C[e] = (q < rows) ? G[(int64_t)(g0 + q) * n + a] : T(0);
+      C[e] = (q < nr) ? G[(int64_t)(g0 + q) * n + a] : T(0);
     }
     __syncthreads();
-    for (int p0 = 0; p0 < n; p0 += kPW) {
-      const int pw = min(kPW, n - p0);
-      if (warp == 0) {
-        for (int e = lane; e < kPW * kPW; e += 32) {
-          const int j = e / kPW, l = e % kPW;
-          Rp[j][l] = (j < pw && l < pw) ? R[(int64_t)(p0 + j) * n + p0 + l] : T(0);
-        }
-        for (int e = lane; e < CH * kPW; e += 32) Vc[e / kPW][e % kPW] = T(0);
-        __syncwarp();
-        for (int j = 0; j < pw; ++j) {
-          const T c = (lane < CH) ? C[lane * n + p0 + j] : T(0);
-          T beta, tau, sc;
-          const bool ok = hh_reflector(Rp[j][j], c, beta, tau, sc);
-          if (lane < CH) Vc[lane][j] = ok ? c * sc : T(0);
-          if (lane == 0) tauv[j] = ok ? tau : T(0);
-          __syncwarp();
-          if (ok) {
-            if (lane == 0) Rp[j][j] = beta;
-            const int l = j + 1 + lane;
-            if (l < pw) {
-              T d = Rp[j][l];
-              for (int q = 0; q < CH; ++q) d += Vc[q][j] * C[q * n + p0 + l];
-              d *= tau;
-              Rp[j][l] -= d;
-              for (int q = 0; q < CH; ++q) C[q * n + p0 + l] -= d * Vc[q][j];
-            }
-          }
-          __syncwarp();
-        }
-        for (int e = lane; e < pw * pw; e += 32) {
-          const int j = e / pw, l = e % pw;
-          if (l >= j) R[(int64_t)(p0 + j) * n + p0 + l] = Rp[j][l];
-        }
-        // compact WY: T upper triangular, T[:j, j] = -tau_j T[:j, :j] (V[:, :j]^T v_j);
-        // the R parts of the reflectors are distinct unit vectors, so
-        // v_i^T v_j = vc_i . vc_j
-        for (int j = 0; j < pw; ++j) {
-          T g = T(0);
-          if (lane < j)
-            for (int q = 0; q < CH; ++q) g += Vc[q][lane] * Vc[q][j];
-          Tm[lane][j] = g;   // temporarily v_lane . v_j
-        }
-        __syncwarp();
-        for (int j = 0; j < pw; ++j) {
-          // column j: Tm[i][j] = -tau_j sum_{k=i}^{j-1} T[i][k] g[k][j], i < j
-          T acc = T(0);
-          if (lane < j)
-            for (int k = lane; k < j; ++k) acc += (k == lane ? tauv[k] : Tm[lane][k]) * Tm[k][j];
-          __syncwarp();
-          if (lane < j) Tm[lane][j] = -tauv[j] * acc;
-          __syncwarp();
-        }
-        if (lane < pw) Tm[lane][lane] = tauv[lane];
-      }
-      __syncthreads();
-      // trailing columns: X <- X - V T^T (V^T X), X = [R rows p0.. ; C]
-      for (int l = p0 + pw + tid; l < n; l += kTsqrThreads) {
-        T w[kPW];
-#pragma unroll
-        for (int j = 0; j < kPW; ++j) {
-          T s = (j < pw) ? R[(int64_t)(p0 + j) * n + l] : T(0);
-          for (int q = 0; q < CH; ++q) s += Vc[q][j] * C[q * n + l];
-          w[j] = s;
-        }
-        T w2[kPW];
-#pragma unroll
-        for (int j = 0; j < kPW; ++j) {
-          T s = T(0);
-#pragma unroll
-          for (int i2 = 0; i2 <= j; ++i2) s += Tm[i2][j] * w[i2];
-          w2[j] = (j < pw) ? s : T(0);
-        }
-#pragma unroll
-        for (int j = 0; j < kPW; ++j)
-          if (j < pw) R[(int64_t)(p0 + j) * n + l] -= w2[j];
-        for (int q = 0; q < CH; ++q) {
-          T s = T(0);
-#pragma unroll
-          for (int j = 0; j < kPW; ++j) s += Vc[q][j] * w2[j];
-          C[q * n + l] -= s;
-        }
-      }
-      __syncthreads();
+    stack_chunk<T, CH>(R, n, C, 0, Rp, Vc, Tm, tauv);
+  }
+}
+
+// One level of the TSQR merge tree: R_a <- R factor of [R_a; R_b] with
+// a = 2 h j, b = a + h (parts of one row); the rows of the triangular R_b are
+// pushed in chunks, each from the panel of its first row.
+template <typename T, int CH>
+__global__ void __launch_bounds__(kTsqrThreads) tsqr_merge_kernel(const BigRowDev* rows, T* ws, int h) {
+  const BigRowDev rw = rows[blockIdx.y];
+  const int n = rw.n, mF = rw.mF, P = rw.parts;
+  const int a = 2 * h * blockIdx.x, b = a + h;
+  if (mF <= 0 || n <= 0 || b >= P) return;
+  extern __shared__ __align__(16) unsigned char big_smem[];
+  T* C = reinterpret_cast<T*>(big_smem);
+  __shared__ T Rp[kPW][kPW + 1], Vc[CH][kPW + 1], Tm[kPW][kPW + 1], tauv[kPW];
+  const int tid = threadIdx.x;
+  T* Ra = ws + rw.x_off + (int64_t)a * n * n;
+  const T* Rb = ws + rw.x_off + (int64_t)b * n * n;
+  for (int c0 = 0; c0 < n; c0 += CH) {
+    const int nr = min(CH, n - c0);
+    for (int e = tid; e < CH * n; e += kTsqrThreads) {
+      const int q = e / n, col = e - q * n;
+      C[e] = (q < nr && col >= c0 + q) ? Rb[(int64_t)(c0 + q) * n + col] : T(0);
     }
+    __syncthreads();
+    stack_chunk<T, CH>(Ra, n, C, (c0 / kPW) * kPW, Rp, Vc, Tm, tauv);
   }
 }
 
@@ -337,15 +378,18 @@ struct BigLevelArgs {
   int tol_mode;
   int* status;
   int* stats;     // kStatsWords counters (Jacobi cap at [32 + level])
+  int engine;     // FP32 GEMMs: 0 tensor cores (3 split-BF16 products), 1 CUDA cores,
+                  // 2 tensor cores with one BF16 product for the Schur updates
+  int* tc_err;    // set by a tensor-core pipeline wait that expired
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kBigThreads) jacobi_kernel(const BigRowDev* rows, T* ws, LevelDev L,
+__global__ void __launch_bounds__(kJacThreads) jacobi_kernel(const BigRowDev* rows, T* ws, LevelDev L,
                                                              BigLevelArgs a) {
   const BigRowDev rw = rows[blockIdx.x];
   const int n = rw.n, i = rw.i;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int kW = kBigThreads / 32;
+  constexpr int kW = kJacThreads / 32;
   __shared__ double s_red[kW];
   __shared__ T s_skip2;
   __shared__ int s_flag;
@@ -357,7 +401,7 @@ __global__ void __launch_bounds__(kBigThreads) jacobi_kernel(const BigRowDev* ro
   const T* D = reinterpret_cast<const T*>(L.pool) + L.diag_off[i];
   {
     double ss = 0.0;
-    for (int64_t e = tid; e < (int64_t)n * n; e += kBigThreads) {
+    for (int64_t e = tid; e < (int64_t)n * n; e += kJacThreads) {
       const double v = static_cast<double>(D[e]);
       ss += v * v;
     }
@@ -369,8 +413,8 @@ __global__ void __launch_bounds__(kBigThreads) jacobi_kernel(const BigRowDev* ro
   for (int w = 0; w < kW; ++w) dn2 += s_red[w];
   const double floor_tau = static_cast<double>(EpsB<T>::v) * sqrt(dn2);
   if (rw.mF <= 0) {
-    for (int64_t e = tid; e < (int64_t)n * n; e += kBigThreads) Ug[e] = (e / n == e % n) ? T(1) : T(0);
-    for (int k = tid; k < n; k += kBigThreads) L.sigma[L.vec_off[i] + k] = 0.0;
+    for (int64_t e = tid; e < (int64_t)n * n; e += kJacThreads) Ug[e] = (e / n == e % n) ? T(1) : T(0);
+    for (int k = tid; k < n; k += kJacThreads) L.sigma[L.vec_off[i] + k] = 0.0;
     if (tid == 0) {
       L.rank[i] = 0;
       L.tau[i] = 0.0;
@@ -380,7 +424,7 @@ __global__ void __launch_bounds__(kBigThreads) jacobi_kernel(const BigRowDev* ro
   T* X = ws + rw.t_off;   // columns of R, contiguous
   T* V = ws + rw.v_off;
   const T* R = ws + rw.x_off;
-  for (int64_t e = tid; e < (int64_t)n * n; e += kBigThreads) {
+  for (int64_t e = tid; e < (int64_t)n * n; e += kJacThreads) {
     const int c = static_cast<int>(e / n), row = static_cast<int>(e % n);
     X[e] = R[(int64_t)row * n + c];
     V[e] = (c == row) ? T(1) : T(0);
@@ -413,8 +457,11 @@ __global__ void __launch_bounds__(kBigThreads) jacobi_kernel(const BigRowDev* ro
     }
     __syncthreads();
     const T skip2 = s_skip2;
+    const int half = lane >> 4, hl = lane & 15;
     for (int rnd = 0; rnd < nb - 1; ++rnd) {
-      for (int t = warp; t < npairs; t += kW) {
+      // half a warp per column pair of the round-robin round
+      for (int tb = warp * 2; tb < npairs; tb += 2 * kW) {
+        const int t = tb + half;
         int p = nb - 1, q = rnd;
         if (t != 0) {
           p = rnd + t;
@@ -422,20 +469,24 @@ __global__ void __launch_bounds__(kBigThreads) jacobi_kernel(const BigRowDev* ro
           q = rnd - t;
           if (q < 0) q += nb - 1;
         }
-        if (p >= n || q >= n) continue;
-        T* xp = X + (int64_t)p * n;
-        T* xq = X + (int64_t)q * n;
+        const bool valid = t < npairs && p < n && q < n;
+        T* xp = X + (int64_t)(valid ? p : 0) * n;
+        T* xq = X + (int64_t)(valid ? q : 0) * n;
         T al = 0, be = 0, ga = 0;
-        for (int row = lane; row < n; row += 32) {
-          const T u = xp[row], v = xq[row];
-          al += u * u;
-          be += v * v;
-          ga += u * v;
+        if (valid)
+          for (int row = hl; row < n; row += 16) {
+            const T u = xp[row], v = xq[row];
+            al += u * u;
+            be += v * v;
+            ga += u * v;
+          }
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, o);
+          be += __shfl_xor_sync(0xffffffffu, be, o);
+          ga += __shfl_xor_sync(0xffffffffu, ga, o);
         }
-        al = wsum(al);
-        be = wsum(be);
-        ga = wsum(ga);
-        if (ga != T(0) && (al >= skip2 || be >= skip2) && ga * ga > tolJ2 * al * be) {
+        if (valid && ga != T(0) && (al >= skip2 || be >= skip2) && ga * ga > tolJ2 * al * be) {
           const T zeta = (be - al) / (T(2) * ga);
           const T az = fabs(zeta);
           const T den = (az > T(1)) ? az * (T(1) + sqrt(T(1) + T(1) / (az * az))) : az + sqrt(T(1) + az * az);
@@ -443,7 +494,7 @@ __global__ void __launch_bounds__(kBigThreads) jacobi_kernel(const BigRowDev* ro
           const T cs = T(1) / sqrt(T(1) + tt * tt), sn = cs * tt;
           T* vp = V + (int64_t)p * n;
           T* vq = V + (int64_t)q * n;
-          for (int row = lane; row < n; row += 32) {
+          for (int row = hl; row < n; row += 16) {
             const T u = xp[row], v = xq[row];
             xp[row] = cs * u - sn * v;
             xq[row] = sn * u + cs * v;
@@ -451,7 +502,7 @@ __global__ void __launch_bounds__(kBigThreads) jacobi_kernel(const BigRowDev* ro
             vp[row] = cs * u2 - sn * v2;
             vq[row] = sn * u2 + cs * v2;
           }
-          if (lane == 0) s_flag = 1;
+          if (hl == 0) s_flag = 1;
         }
       }
       __syncthreads();
@@ -471,7 +522,7 @@ __global__ void __launch_bounds__(kBigThreads) jacobi_kernel(const BigRowDev* ro
     if (lane == 0) sig[j] = sqrt(s);
   }
   __syncthreads();
-  for (int j = tid; j < n; j += kBigThreads) {
+  for (int j = tid; j < n; j += kJacThreads) {
     const T sj = sig[j];
     int ps = 0;
     for (int k = 0; k < n; ++k) ps += (sig[k] > sj) || (sig[k] == sj && k < j);
@@ -479,11 +530,11 @@ __global__ void __launch_bounds__(kBigThreads) jacobi_kernel(const BigRowDev* ro
   }
   __syncthreads();
   // U_i[a][pos[j]] = V[:, j][a]; sigma sorted
-  for (int64_t e = tid; e < (int64_t)n * n; e += kBigThreads) {
+  for (int64_t e = tid; e < (int64_t)n * n; e += kJacThreads) {
     const int j = static_cast<int>(e / n), row = static_cast<int>(e % n);
     Ug[(int64_t)row * n + pos[j]] = V[e];
   }
-  for (int j = tid; j < n; j += kBigThreads) L.sigma[L.vec_off[i] + pos[j]] = static_cast<double>(sig[j]);
+  for (int j = tid; j < n; j += kJacThreads) L.sigma[L.vec_off[i] + pos[j]] = static_cast<double>(sig[j]);
   __syncthreads();
   if (tid == 0) {
     // sorted singular values
@@ -850,6 +901,19 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
   const int es = sizeof(T);
   rank_h.assign(P.M, 0);
   std::vector<int> done(P.M, 0);
+  // GEMM groups: FP32 on the tensor cores unless the CUDA cores are asked
+  // for (products with K = 0 only apply beta, on the CUDA cores)
+  auto run_gemm = [&](const std::vector<GemmTask>& g, int passes) {
+    if (g.empty()) return;
+    if (sizeof(T) == 8 || args.engine == 1) {
+      bcheck(launch_gemm_t<T>(g, s));
+      return;
+    }
+    std::vector<GemmTask> tc, cc;
+    for (const GemmTask& t : g) (t.K > 0 ? tc : cc).push_back(t);
+    if (!cc.empty()) bcheck(launch_gemm_t<T>(cc, s));
+    if (!tc.empty()) bcheck(launch_gemm_tc(tc, passes, args.tc_err, s));
+  };
   auto width = [&](int k) { return done[k] ? rank_h[k] : P.n[k]; };
   constexpr int CH = sizeof(T) == 4 ? 32 : 16;
   static size_t tsqr_dyn = 0;  // dynamic shared memory the TSQR kernel may take
@@ -857,10 +921,12 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
     int dev = 0, optin = 0;
     bcheck(cudaGetDevice(&dev));
     bcheck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
-    cudaFuncAttributes fa;
-    bcheck(cudaFuncGetAttributes(&fa, tsqr_kernel<T, CH>));
-    const size_t lim = static_cast<size_t>(optin) - fa.sharedSizeBytes;
-    bcheck(cudaFuncSetAttribute(tsqr_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+    cudaFuncAttributes fa, fb;
+    bcheck(cudaFuncGetAttributes(&fa, tsqr_part_kernel<T, CH>));
+    bcheck(cudaFuncGetAttributes(&fb, tsqr_merge_kernel<T, CH>));
+    const size_t lim = static_cast<size_t>(optin) - std::max(fa.sharedSizeBytes, fb.sharedSizeBytes);
+    bcheck(cudaFuncSetAttribute(tsqr_part_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+    bcheck(cudaFuncSetAttribute(tsqr_merge_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
     tsqr_dyn = lim;
   }
   for (int c = 0; c < P.ncolours; ++c) {
@@ -870,7 +936,7 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
     std::vector<BigRowDev> rows;
     std::vector<std::vector<int>> fpre(q1 - q0);
     int64_t off = 0;
-    int nmaxc = 0;
+    int nmaxc = 0, maxparts = 1;
     auto take = [&](int64_t elems) {
       const int64_t o = off;
       off += (elems + 63) & ~int64_t(63);
@@ -892,8 +958,13 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
       r.mF = mF;
       const int n = r.n;
       nmaxc = std::max(nmaxc, n);
+      // TSQR parts: about 8 chunks of F_i^T per part, at most 32 parts
+      int parts = 1;
+      while (parts < 32 && (int64_t)parts * 2 * 8 * CH <= mF) parts *= 2;
+      r.parts = parts;
+      maxparts = std::max(maxparts, parts);
       r.g_off = take((int64_t)std::max(mF, 1) * n);
-      r.x_off = take((int64_t)n * n);
+      r.x_off = take((int64_t)parts * n * n);
       r.v_off = take((int64_t)n * n);
       r.t_off = take((int64_t)n * n);
       r.w2_off = take((int64_t)n * n);
@@ -947,11 +1018,16 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
       const size_t sm = (size_t)CH * nmaxc * es;
       if (sm > tsqr_dyn) throw BigFail{cudaErrorInvalidValue};
       g_launches.fetch_add(1, std::memory_order_relaxed);
-      tsqr_kernel<T, CH><<<nr, kTsqrThreads, sm, s>>>(drows, ws);
+      tsqr_part_kernel<T, CH><<<dim3(maxparts, nr), kTsqrThreads, sm, s>>>(drows, ws);
       bcheck(cudaGetLastError());
+      for (int h = 1; h < maxparts; h *= 2) {
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        tsqr_merge_kernel<T, CH><<<dim3(maxparts / (2 * h), nr), kTsqrThreads, sm, s>>>(drows, ws, h);
+        bcheck(cudaGetLastError());
+      }
       const size_t sj = (size_t)nmaxc * (es + sizeof(int)) + 64;
       g_launches.fetch_add(1, std::memory_order_relaxed);
-      jacobi_kernel<T><<<nr, kBigThreads, sj, s>>>(drows, ws, D, args);
+      jacobi_kernel<T><<<nr, kJacThreads, sj, s>>>(drows, ws, D, args);
       bcheck(cudaGetLastError());
     }
     // ranks of the colour (the shapes of everything that follows)
@@ -988,14 +1064,14 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
       u.M = n; u.N = n; u.K = n; u.alpha = 1.f; u.beta = 0.f;
       g2.push_back(u);
     }
-    bcheck(launch_gemm_t<T>(g1, s));
-    bcheck(launch_gemm_t<T>(g2, s));
+    run_gemm(g1, 3);
+    run_gemm(g2, 3);
     // ---- 5: Cholesky of T_nn and L_hat^{-1} ----
     g_launches.fetch_add(1, std::memory_order_relaxed);
     cholinv_kernel<T><<<nr, kBigThreads, 0, s>>>(drows, ws, D, args);
     bcheck(cudaGetLastError());
     // ---- 6: W_b, Y_p, far rows ----
-    std::vector<GemmTask> g3, g4, g5;
+    std::vector<GemmTask> g3, g4, g5, g6;
     for (int q = q0; q < q1; ++q) {
       const BigRowDev& rw = rows[q - q0];
       const int i = rw.i, n = rw.n, r = rank_h[i], m = n - r;
@@ -1044,7 +1120,7 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
         }
       }
     }
-    bcheck(launch_gemm_t<T>(g3, s));
+    run_gemm(g3, 3);
     // ---- 7: D_i <- T[:r, :r] - W_b^T W_b;  W_p = L_hat^{-1} Y_p[r:] ----
     for (int q = q0; q < q1; ++q) {
       const BigRowDev& rw = rows[q - q0];
@@ -1081,7 +1157,7 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
       }
     }
     // D_i with r == 0: the block is eliminated whole (nothing kept)
-    bcheck(launch_gemm_t<T>(g4, s));
+    run_gemm(g4, 3);
     // ---- 8: kept close rows and the Schur update ----
     for (int q = q0; q < q1; ++q) {
       const BigRowDev& rw = rows[q - q0];
@@ -1124,17 +1200,20 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
           t.C = pool + pv.off; t.ldc = pv.ld; t.tc = pv.trans;
           t.Cin = t.C; t.ldcin = pv.ld; t.tcin = pv.trans;
           t.M = tw[a2]; t.N = tw[b2]; t.K = m; t.alpha = -1.f; t.beta = 1.f;
-          g5.push_back(t);
+          g6.push_back(t);
         }
     }
-    bcheck(launch_gemm_t<T>(g5, s));
+    run_gemm(g5, 3);
+    run_gemm(g6, args.engine == 2 ? 1 : 3);
     for (int q = q0; q < q1; ++q) done[P.order[q]] = 1;
     bcheck(cudaFreeAsync(ws, s));
     bcheck(cudaFreeAsync(drows, s));
-    int hs2 = 0;
-    bcheck(cudaMemcpyAsync(&hs2, args.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    int hs2[2] = {0, 0};
+    bcheck(cudaMemcpyAsync(&hs2[0], args.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    bcheck(cudaMemcpyAsync(&hs2[1], args.tc_err, sizeof(int), cudaMemcpyDeviceToHost, s));
     bcheck(cudaStreamSynchronize(s));
-    if (hs2 != 0) return;
+    if (hs2[1] != 0) throw BigFail{cudaErrorLaunchTimeout};
+    if (hs2[0] != 0) return;
   }
 }
 
@@ -1154,8 +1233,16 @@ bool level_needs_big_rows(const LevelPlan& P) {
 }
 
 cudaError_t run_big_level(int esize, LevelStore& st, int level, double tol, int tol_mode, int* status, int* stats,
-                          cudaStream_t s) {
-  BigLevelArgs a{level, tol, tol_mode, status, stats};
+                          int engine, cudaStream_t s) {
+  int* tc_err = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tc_err), sizeof(int), s);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(tc_err, 0, sizeof(int), s);
+  if (e != cudaSuccess) {
+    cudaFreeAsync(tc_err, s);
+    return e;
+  }
+  BigLevelArgs a{level, tol, tol_mode, status, stats, engine, tc_err};
   try {
     std::vector<int> rank_h;
     if (esize == 8)
@@ -1163,9 +1250,10 @@ cudaError_t run_big_level(int esize, LevelStore& st, int level, double tol, int 
     else
       run_big_level_t<float>(st, s, a, rank_h);
   } catch (const BigFail& f) {
-    return f.e;
+    e = f.e;
   }
-  return cudaSuccess;
+  cudaFreeAsync(tc_err, s);
+  return e;
 }
 
 cudaError_t launch_apply_big(int esize, const LevelDev& L, const LevelPlan& P, double* vec, int forward,

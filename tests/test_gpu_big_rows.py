@@ -10,8 +10,11 @@ super-blocks.
   34 far blocks), level 3 the large-row path without far blocks (8 blocks of
   up to ~390 rows, eliminated whole).  FP64 form: ranks equal the oracle's
   except within 1e-5 relative of tau, apply within 1e-10, PCG iterations
-  +-1 and a true residual <= 1e-8.  FP32 form: normwise backward error
-  against the oracle's operator <= 1e-4, PCG +-1.
+  +-1 and a true residual <= 1e-8.  FP32 form, its products on the tensor
+  cores (three split-BF16 products) and on the CUDA cores: normwise
+  backward error against the oracle's operator <= 1e-4, PCG +-1.  With the
+  Schur updates as one BF16 product (FP32 accumulation) the backward error
+  is reported and PCG must still reach 1e-8.
 * 3D Poisson 16^3 (B = 64): the second level is 8 blocks of ~210 rows (a 2^3
   grid of super-blocks), run by the large-row path; ranks and apply within
   1e-10.
@@ -77,14 +80,14 @@ def _pcg(ceg, csb, F, A, b):
     return it, conv, np.linalg.norm(b - A @ xh) / np.linalg.norm(b)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "fp32"])
-def test_big_rows_3d_32(ceg, precision):
+@pytest.mark.parametrize("precision,engine", [("fp64", "cuda"), ("fp32", "tc"), ("fp32", "cuda")])
+def test_big_rows_3d_32(ceg, precision, engine):
     A, perm, b, Fo = _problem(32)
     csb = ceg.csb_build(A, perm, 64)
-    F = ceg.ce_factorize(csb, tol=1e-4, levels=4, J=8, precision=precision)
+    F = ceg.ce_factorize(csb, tol=1e-4, levels=4, J=8, precision=precision, gemm_engine=engine)
     info = F.info
     big = [info.big_rows[l] for l in range(info.levels_done)]
-    print(f"{precision}: levels {info.levels_done}, big {big}, blocks {list(info.blocks[:info.levels_done])}, "
+    print(f"{precision} {engine}: levels {info.levels_done}, big {big}, blocks {list(info.blocks[:info.levels_done])}, "
           f"max block {list(info.max_block[:info.levels_done])}, level ms "
           f"{[round(info.level_ms[l], 2) for l in range(info.levels_done)]}, coarse {info.coarse_n}")
     assert big[0] == 0 and big[1] == 1
@@ -133,3 +136,18 @@ def test_big_rows_second_level_16(ceg):
     z = _apply(ceg, F, b)
     zo = oce.apply(Fo, b)
     assert np.linalg.norm(z - zo) / np.linalg.norm(zo) <= 1e-10
+
+
+def test_big_rows_bf16_schur_32(ceg):
+    A, perm, b, Fo = _problem(32)
+    csb = ceg.csb_build(A, perm, 64)
+    F = ceg.ce_factorize(csb, tol=1e-4, levels=4, J=8, precision="fp32", gemm_engine="tc_bf16_schur")
+    z = _apply(ceg, F, b)
+    import scipy.sparse.linalg as spla
+    anorm = float(spla.eigsh(A, k=1, which="LA", return_eigenvectors=False)[0])
+    eta = np.linalg.norm(b - oce.multiply(Fo, z)) / (anorm * np.linalg.norm(z) + np.linalg.norm(b))
+    it, conv, rel = _pcg(ceg, csb, F, A, b)
+    it_o = oce.pcg(A, Fo, b, 1e-8, 200).iters
+    print(f"BF16 Schur updates: backward error {eta:.3e}, PCG {it} (oracle {it_o}), true residual {rel:.2e}")
+    assert conv and rel <= 1e-8 * 1.01
+    assert it <= it_o + 10
