@@ -76,7 +76,10 @@ typedef struct {
   int precision;   /* CE_PREC_*                                          */
   int coloring;    /* 1: colour-major order (default); 0: natural order  */
   void* stream;    /* cudaStream_t for all device work                   */
-  int rank_mode;   /* CE_RANK_SVD (default) / CE_RANK_LEARNED            */
+  int rank_mode;   /* CE_RANK_SVD (default) / CE_RANK_LEARNED; on levels
+                      run by the large-row path the learned form (FP32)
+                      sketches each row with width 72, then 144 (at most
+                      3n/4), before the exact SVD                         */
   const void* rank_model; /* device, ce_mlp_nparams() FP16 values from
                              ce_mlp_pack (CE_RANK_LEARNED only)          */
   int oversample;  /* p, sketch columns beyond r_hat (default 8)         */
@@ -141,6 +144,12 @@ typedef struct {
                           kept; otherwise it is planned again)            */
   int big_rows[16];    /* 1: level l ran the large-row path (blocks over 64
                           rows, or over 32 close / 128 far blocks)        */
+  double big_ms[8];    /* device time of the large-row levels by step
+                          (CUDA events, summed over their colours): gather
+                          of F_i^T, randomized range finder (learned form),
+                          exact SVD (TSQR + Jacobi), U^T D U, Cholesky and
+                          inverse, W_b / Y_p / far rows, D_i and W_p,
+                          kept rows and Schur updates                      */
   int jacobi_capped[16]; /* rows of level l whose Jacobi SVD stopped at its
                           sweep cap (40 sweeps) with a pair still above the
                           orthogonality threshold; their singular values

@@ -73,6 +73,7 @@ class ce_info(C.Structure):
         ("row_learned", C.c_int * 16),
         ("spec_miss", C.c_int * 16),
         ("big_rows", C.c_int * 16),
+        ("big_ms", C.c_double * 8),
         ("jacobi_capped", C.c_int * 16),
     ]
 

@@ -1160,12 +1160,14 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       // exact SVD faster here
       ce::LearnedArgs la_l = la;
       if (o.row_shape < 0 && l < A->tuned_levels[tp][tr] && !A->tuned_learned[tp][tr][l]) la_l.model = nullptr;
-      if (big) la_l.model = nullptr;   // the large-row path compresses by the exact SVD
-      if (info && l < 16) info->row_learned[l] = la_l.model != nullptr;
+      // the large-row path runs its own randomized range finder (learned form)
+      if (info && l < 16) info->row_learned[l] = big ? (o.rank_mode == CE_RANK_LEARNED && es == 4) : la_l.model != nullptr;
+      if (big) la_l.model = nullptr;
       if (info && l < 16) info->big_rows[l] = big ? 1 : 0;
       const int nbkt = static_cast<int>(P.bucket_nmax.size());
       if (big) {
-        check(ce::run_big_level(es, st, l, o.tol, o.tol_mode, F->d_status, la.stats, o.gemm_engine, s),
+        check(ce::run_big_level(es, st, l, o.tol, o.tol_mode, F->d_status, la.stats, o.gemm_engine,
+                                info ? info->big_ms : nullptr, o.rank_mode == CE_RANK_LEARNED, o.seed, s),
               "large rows");
       } else if (nbkt <= 1) {
         check(ce::launch_row_kernel(es, st.dev, P.M, l, o.tol, o.tol_mode, F->d_status, P.nmax, shape, la_l, s),

@@ -26,6 +26,7 @@
 #include <vector>
 
 #include "kernels.h"
+#include "rng.cuh"
 
 namespace ce {
 
@@ -190,6 +191,18 @@ struct BigRowDev {
   int64_t v_off;  // n x n: V (column-major)
   int64_t t_off;  // n x n: T = U^T D U (row-major)
   int64_t w2_off; // n x n: D U (row-major), then the Cholesky work matrix
+  int mode;       // Jacobi output: 0 U_i, sigma, r_i, tau_i of block i (exact SVD);
+                  // 1 the sketch's k x k factor: V sorted at u_out, sigma at s_out,
+                  // r and tau in the row's SketchRes
+  int64_t u_out, s_out;
+};
+
+// result of the randomized range finder of one row
+struct SketchRes {
+  double tau;      // threshold from the sketch's sigma_1
+  double probe;    // largest ||(I - Q Q^T) F w|| of the two probe columns
+  int rank;        // #{sigma > tau} of the sketch
+  int accepted;    // rank < k and probe <= tau / 2
 };
 
 // ---------------------------------------------------------------------------
@@ -381,11 +394,14 @@ struct BigLevelArgs {
   int engine;     // FP32 GEMMs: 0 tensor cores (3 split-BF16 products), 1 CUDA cores,
                   // 2 tensor cores with one BF16 product for the Schur updates
   int* tc_err;    // set by a tensor-core pipeline wait that expired
+  double* phase_ms; // host, 8 phase times accumulated (see ce_info.big_ms)
+  int sketch;       // 1: randomized range finder first (learned form, FP32)
+  unsigned long long seed;  // key of the sketch's Gaussians
 };
 
 template <typename T>
 __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(const BigRowDev* rows, T* ws, LevelDev L,
-                                                             BigLevelArgs a) {
+                                                             BigLevelArgs a, int xv_smem, SketchRes* res) {
   const BigRowDev rw = rows[blockIdx.x];
   const int n = rw.n, i = rw.i;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -421,8 +437,9 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(const BigRowDev* ro
     }
     return;
   }
-  T* X = ws + rw.t_off;   // columns of R, contiguous
-  T* V = ws + rw.v_off;
+  // columns of R contiguous; in shared memory when both n x n matrices fit
+  T* X = xv_smem ? reinterpret_cast<T*>(pos + ((n + 3) & ~3)) : ws + rw.t_off;
+  T* V = xv_smem ? X + (int64_t)n * n : ws + rw.v_off;
   const T* R = ws + rw.x_off;
   for (int64_t e = tid; e < (int64_t)n * n; e += kJacThreads) {
     const int c = static_cast<int>(e / n), row = static_cast<int>(e % n);
@@ -530,11 +547,17 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(const BigRowDev* ro
   }
   __syncthreads();
   // U_i[a][pos[j]] = V[:, j][a]; sigma sorted
+  T* Uo = rw.mode ? ws + rw.u_out : Ug;
   for (int64_t e = tid; e < (int64_t)n * n; e += kJacThreads) {
     const int j = static_cast<int>(e / n), row = static_cast<int>(e % n);
-    Ug[(int64_t)row * n + pos[j]] = V[e];
+    Uo[(int64_t)row * n + pos[j]] = V[e];
   }
-  for (int j = tid; j < n; j += kJacThreads) L.sigma[L.vec_off[i] + pos[j]] = static_cast<double>(sig[j]);
+  for (int j = tid; j < n; j += kJacThreads) {
+    if (rw.mode)
+      ws[rw.s_out + pos[j]] = sig[j];
+    else
+      L.sigma[L.vec_off[i] + pos[j]] = static_cast<double>(sig[j]);
+  }
   __syncthreads();
   if (tid == 0) {
     // sorted singular values
@@ -565,9 +588,224 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(const BigRowDev* ro
       tau = fmax(tau, floor_tau);
       int rr = 0;
       for (int j = 0; j < n; ++j) rr += (static_cast<double>(sig[j]) > tau) ? 1 : 0;
-      L.rank[i] = rr;
-      L.tau[i] = tau;
+      if (rw.mode) {
+        res[blockIdx.x].rank = rr;
+        res[blockIdx.x].tau = tau;
+      } else {
+        L.rank[i] = rr;
+        L.tau[i] = tau;
+      }
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Randomized range finder of a large row (FP32 form): Y = F [Omega | w1 w2]
+// with Gaussian Omega (mF x k) and two probe columns, Q = orth(Y[:, :k]),
+// the SVD of Q^T F through the R factor of F^T Q and Jacobi on it (k x k).
+// Accepted when the sketch is not saturated (r < k) and the probe estimate
+// of the out-of-sketch residual ||(I - Q Q^T) F w|| is at most tau / 2, so
+// the dropped part stays near tau; otherwise the exact SVD runs.
+// ---------------------------------------------------------------------------
+struct SketchRowDev {
+  int i, n, mF, k;     // k sketch columns (+ 2 probes)
+  int64_t om_off;      // Omega, mF x (k + 2)
+  int64_t y_off;       // Y, n x (k + 2) (Householder vectors below the diagonal)
+  int64_t q_off;       // explicit Q, n x k
+  int64_t ub_off;      // U_b = Q V_B[:, :r], n x k (r columns used)
+  int64_t s_out;       // sketch singular values (k), sorted
+};
+
+__device__ __forceinline__ unsigned long long big_sketch_key(unsigned long long seed, int level, int i, int g,
+                                                             int c) {
+  return splitmix64(seed ^ splitmix64(((unsigned long long)level << 40) ^ ((unsigned long long)i << 8) ^ 0x5EEDull) ^
+                    splitmix64(((unsigned long long)g << 20) ^ (unsigned long long)c));
+}
+
+template <typename T>
+__global__ void sketch_omega_kernel(const SketchRowDev* rows, T* ws, int level, unsigned long long seed) {
+  const SketchRowDev rw = rows[blockIdx.y];
+  const int kp = rw.k + 2;
+  const int64_t tot = (int64_t)rw.mF * kp;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+    const int g = static_cast<int>(e / kp), c = static_cast<int>(e - (int64_t)g * kp);
+    ws[rw.om_off + e] = static_cast<T>(gauss_from_key(big_sketch_key(seed, level, rw.i, g, c)));
+  }
+}
+
+// Householder QR of Y[:, :k] (n x (k + 2), row-major, global) carried along
+// to the probe columns; the probe residuals; the explicit Q (n x k).
+template <typename T>
+__global__ void __launch_bounds__(kBigThreads) sketch_qr_kernel(const SketchRowDev* rows, T* ws, SketchRes* res) {
+  const SketchRowDev rw = rows[blockIdx.x];
+  const int n = rw.n, k = rw.k, kp = k + 2;
+  T* Y = ws + rw.y_off;
+  T* Q = ws + rw.q_off;
+  __shared__ T s_tau[1024], s_pr[2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kW = kBigThreads / 32;
+  for (int j = 0; j < k; ++j) {
+    if (warp == 0) {
+      // reflector of Y[j:, j]
+      T amax = T(0);
+      for (int a = j + 1 + lane; a < n; a += 32) amax = fmax(amax, fabs(Y[(int64_t)a * kp + j]));
+      amax = wmax(amax);
+      T tau = T(0);
+      if (amax >= TinyB<T>::v) {
+        T ss = T(0);
+        for (int a = j + 1 + lane; a < n; a += 32) {
+          const T v = Y[(int64_t)a * kp + j] / amax;
+          ss += v * v;
+        }
+        ss = wsum(ss);
+        const T x0 = Y[(int64_t)j * kp + j];
+        const T aa = fmax(amax, fabs(x0));
+        const T nrm = aa * sqrt((x0 / aa) * (x0 / aa) + ss * (amax / aa) * (amax / aa));
+        const T beta = (x0 >= T(0)) ? -nrm : nrm;
+        tau = (beta - x0) / beta;
+        const T sc = T(1) / (x0 - beta);
+        for (int a = j + 1 + lane; a < n; a += 32) Y[(int64_t)a * kp + j] *= sc;
+        __syncwarp();
+        if (lane == 0) Y[(int64_t)j * kp + j] = beta;
+      }
+      if (lane == 0) s_tau[j] = tau;
+    }
+    __syncthreads();
+    const T tq = s_tau[j];
+    if (tq != T(0)) {
+      for (int l = j + 1 + warp; l < kp; l += kW) {
+        T d = T(0);
+        for (int a = j + 1 + lane; a < n; a += 32) d += Y[(int64_t)a * kp + j] * Y[(int64_t)a * kp + l];
+        d = wsum(d);
+        d = (d + Y[(int64_t)j * kp + l]) * tq;
+        if (lane == 0) Y[(int64_t)j * kp + l] -= d;
+        for (int a = j + 1 + lane; a < n; a += 32) Y[(int64_t)a * kp + l] -= d * Y[(int64_t)a * kp + j];
+      }
+    }
+    __syncthreads();
+  }
+  if (warp < 2) {  // ||(I - Q Q^T) F w|| = norm of rows k.. of H^T (F w)
+    T ss = T(0);
+    for (int a = k + lane; a < n; a += 32) {
+      const T v = Y[(int64_t)a * kp + k + warp];
+      ss += v * v;
+    }
+    ss = wsum(ss);
+    if (lane == 0) s_pr[warp] = sqrt(ss);
+  }
+  // explicit Q = H_0 ... H_{k-1} [I_k; 0]
+  for (int64_t e = tid; e < (int64_t)n * k; e += kBigThreads) {
+    const int a = static_cast<int>(e / k), c = static_cast<int>(e - (int64_t)a * k);
+    Q[e] = (a == c) ? T(1) : T(0);
+  }
+  __syncthreads();
+  for (int j = k - 1; j >= 0; --j) {
+    const T tq = s_tau[j];
+    if (tq != T(0)) {
+      for (int l = j + warp; l < k; l += kW) {
+        T d = T(0);
+        for (int a = j + 1 + lane; a < n; a += 32) d += Y[(int64_t)a * kp + j] * Q[(int64_t)a * k + l];
+        d = wsum(d);
+        d = (d + Q[(int64_t)j * k + l]) * tq;
+        if (lane == 0) Q[(int64_t)j * k + l] -= d;
+        for (int a = j + 1 + lane; a < n; a += 32) Q[(int64_t)a * k + l] -= d * Y[(int64_t)a * kp + j];
+      }
+    }
+    __syncthreads();
+  }
+  if (tid == 0) res[blockIdx.x].probe = static_cast<double>(fmax(s_pr[0], s_pr[1]));
+}
+
+// acceptance of the sketch; an accepted row gets its rank, threshold and
+// singular values (zeros beyond k) and the sketch width in kw
+template <typename T>
+__global__ void sketch_accept_kernel(const SketchRowDev* rows, const T* ws, SketchRes* res, LevelDev L,
+                                     int* stats, int level) {
+  const SketchRowDev rw = rows[blockIdx.x];
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    SketchRes& r = res[blockIdx.x];
+    const bool ok = isfinite(r.tau) && r.rank < rw.k && r.probe <= 0.5 * r.tau;
+    r.accepted = ok ? 1 : 0;
+    s_ok = ok;
+    if (ok) {
+      L.rank[rw.i] = r.rank;
+      L.tau[rw.i] = r.tau;
+    }
+    if (L.kw) L.kw[rw.i] = ok ? rw.k : -rw.k;
+    if (stats && level < 16) atomicAdd(stats + 2 * level + (ok ? 0 : 1), 1);
+  }
+  __syncthreads();
+  if (s_ok)
+    for (int j = threadIdx.x; j < rw.n; j += blockDim.x)
+      L.sigma[L.vec_off[rw.i] + j] = (j < rw.k) ? static_cast<double>(ws[rw.s_out + j]) : 0.0;
+}
+
+// U_i (n x n orthogonal) whose first r columns span U_b = Q V_B[:, :r]:
+// Householder QR of U_b (n x r, in place), U = H_0 ... H_{r-1} into the factor
+template <typename T>
+__global__ void __launch_bounds__(kBigThreads) complete_u_kernel(const SketchRowDev* rows, T* ws, LevelDev L) {
+  const SketchRowDev rw = rows[blockIdx.x];
+  const int n = rw.n, i = rw.i, r = L.rank[i];
+  T* Ub = ws + rw.ub_off;   // n x r, row-major (ld r)
+  T* U = reinterpret_cast<T*>(L.U) + L.u_off[i];
+  __shared__ T s_tau[1024];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int kW = kBigThreads / 32;
+  for (int j = 0; j < r; ++j) {
+    if (warp == 0) {
+      T amax = T(0);
+      for (int a = j + 1 + lane; a < n; a += 32) amax = fmax(amax, fabs(Ub[(int64_t)a * r + j]));
+      amax = wmax(amax);
+      T tau = T(0);
+      if (amax >= TinyB<T>::v) {
+        T ss = T(0);
+        for (int a = j + 1 + lane; a < n; a += 32) {
+          const T v = Ub[(int64_t)a * r + j] / amax;
+          ss += v * v;
+        }
+        ss = wsum(ss);
+        const T x0 = Ub[(int64_t)j * r + j];
+        const T aa = fmax(amax, fabs(x0));
+        const T nrm = aa * sqrt((x0 / aa) * (x0 / aa) + ss * (amax / aa) * (amax / aa));
+        const T beta = (x0 >= T(0)) ? -nrm : nrm;
+        tau = (beta - x0) / beta;
+        const T sc = T(1) / (x0 - beta);
+        for (int a = j + 1 + lane; a < n; a += 32) Ub[(int64_t)a * r + j] *= sc;
+        __syncwarp();
+        if (lane == 0) Ub[(int64_t)j * r + j] = beta;
+      }
+      if (lane == 0) s_tau[j] = tau;
+    }
+    __syncthreads();
+    const T tq = s_tau[j];
+    if (tq != T(0)) {
+      for (int l = j + 1 + warp; l < r; l += kW) {
+        T d = T(0);
+        for (int a = j + 1 + lane; a < n; a += 32) d += Ub[(int64_t)a * r + j] * Ub[(int64_t)a * r + l];
+        d = wsum(d);
+        d = (d + Ub[(int64_t)j * r + l]) * tq;
+        if (lane == 0) Ub[(int64_t)j * r + l] -= d;
+        for (int a = j + 1 + lane; a < n; a += 32) Ub[(int64_t)a * r + l] -= d * Ub[(int64_t)a * r + j];
+      }
+    }
+    __syncthreads();
+  }
+  for (int64_t e = tid; e < (int64_t)n * n; e += kBigThreads) U[e] = (e / n == e % n) ? T(1) : T(0);
+  __syncthreads();
+  for (int j = r - 1; j >= 0; --j) {
+    const T tq = s_tau[j];
+    if (tq != T(0)) {
+      for (int l = j + warp; l < n; l += kW) {
+        T d = T(0);
+        for (int a = j + 1 + lane; a < n; a += 32) d += Ub[(int64_t)a * r + j] * U[(int64_t)a * n + l];
+        d = wsum(d);
+        d = (d + U[(int64_t)j * n + l]) * tq;
+        if (lane == 0) U[(int64_t)j * n + l] -= d;
+        for (int a = j + 1 + lane; a < n; a += 32) U[(int64_t)a * n + l] -= d * Ub[(int64_t)a * r + j];
+      }
+    }
+    __syncthreads();
   }
 }
 
@@ -901,6 +1139,22 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
   const int es = sizeof(T);
   rank_h.assign(P.M, 0);
   std::vector<int> done(P.M, 0);
+  // device time per phase (CUDA events between the phases of each colour)
+  cudaEvent_t ev[9];
+  for (int k = 0; k < 9; ++k) bcheck(cudaEventCreate(&ev[k]));
+  struct EvGuard {
+    cudaEvent_t* e;
+    ~EvGuard() {
+      for (int k = 0; k < 9; ++k) cudaEventDestroy(e[k]);
+    }
+  } evg{ev};
+  auto mark = [&](int k) { bcheck(cudaEventRecord(ev[k], s)); };
+  auto add_phases = [&](int upto) {  // after a synchronize: phase k = ev[k] .. ev[k+1]
+    for (int k = 0; k < upto; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess && args.phase_ms) args.phase_ms[k] += ms;
+    }
+  };
   // GEMM groups: FP32 on the tensor cores unless the CUDA cores are asked
   // for (products with K = 0 only apply beta, on the CUDA cores)
   auto run_gemm = [&](const std::vector<GemmTask>& g, int passes) {
@@ -929,6 +1183,155 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
     bcheck(cudaFuncSetAttribute(tsqr_merge_kernel<T, CH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
     tsqr_dyn = lim;
   }
+  static size_t jac_dyn = 0;  // dynamic shared memory the Jacobi kernel may take
+  if (jac_dyn == 0) {
+    int dev = 0, optin = 0;
+    bcheck(cudaGetDevice(&dev));
+    bcheck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    cudaFuncAttributes fa;
+    bcheck(cudaFuncGetAttributes(&fa, jacobi_kernel<T>));
+    const size_t lim = static_cast<size_t>(optin) - fa.sharedSizeBytes;
+    bcheck(cudaFuncSetAttribute(jacobi_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim));
+    jac_dyn = lim;
+  }
+  // one attempt of the randomized range finder on the rows cand (indices
+  // into rows) with widths kcur; sets accepted[q] and, for accepted rows,
+  // U_i in the factor (rank, tau, sigma by the accept kernel)
+  auto run_sketch = [&](const std::vector<int>& cand, const std::vector<int>& kcur,
+                        const std::vector<BigRowDev>& rows, T* ws, std::vector<char>& accepted) {
+    std::vector<SketchRowDev> sk;
+    std::vector<BigRowDev> view;   // the TSQR / Jacobi of the k x k problem
+    int64_t o2 = 0;
+    auto take2 = [&](int64_t elems) {
+      const int64_t o = o2;
+      o2 += (elems + 63) & ~int64_t(63);
+      return o;
+    };
+    int maxp = 1, kmx = 1;
+    for (int q : cand) {
+      const BigRowDev& r = rows[q];
+      const int k = kcur[q], kp = k + 2;
+      SketchRowDev d{};
+      d.i = r.i;
+      d.n = r.n;
+      d.mF = r.mF;
+      d.k = k;
+      d.om_off = take2((int64_t)r.mF * kp);
+      d.y_off = take2((int64_t)r.n * kp);
+      d.q_off = take2((int64_t)r.n * k);
+      d.ub_off = take2((int64_t)r.n * k);
+      d.s_out = take2(k);
+      BigRowDev v{};
+      v.i = r.i;
+      v.n = k;
+      v.mF = r.mF;
+      int parts = 1;
+      while (parts < 32 && (int64_t)parts * 2 * 8 * CH <= r.mF) parts *= 2;
+      v.parts = parts;
+      maxp = std::max(maxp, parts);
+      kmx = std::max(kmx, k);
+      v.g_off = take2((int64_t)r.mF * k);      // F^T Q
+      v.x_off = take2((int64_t)parts * k * k);
+      v.v_off = take2((int64_t)k * k);
+      v.t_off = take2((int64_t)k * k);
+      v.w2_off = 0;
+      v.mode = 1;
+      v.u_out = take2((int64_t)k * k);
+      v.s_out = d.s_out;
+      sk.push_back(d);
+      view.push_back(v);
+    }
+    const int ns = static_cast<int>(sk.size());
+    T* ws2 = nullptr;
+    SketchRowDev* dsk = nullptr;
+    BigRowDev* dview = nullptr;
+    SketchRes* dres = nullptr;
+    bcheck(cudaMallocAsync(reinterpret_cast<void**>(&ws2), std::max<int64_t>(o2, 64) * es, s));
+    bcheck(cudaMallocAsync(reinterpret_cast<void**>(&dsk), ns * sizeof(SketchRowDev), s));
+    bcheck(cudaMallocAsync(reinterpret_cast<void**>(&dview), ns * sizeof(BigRowDev), s));
+    bcheck(cudaMallocAsync(reinterpret_cast<void**>(&dres), ns * sizeof(SketchRes), s));
+    bcheck(cudaMemcpyAsync(dsk, sk.data(), ns * sizeof(SketchRowDev), cudaMemcpyHostToDevice, s));
+    bcheck(cudaMemcpyAsync(dview, view.data(), ns * sizeof(BigRowDev), cudaMemcpyHostToDevice, s));
+    bcheck(cudaMemsetAsync(dres, 0, ns * sizeof(SketchRes), s));
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    sketch_omega_kernel<T><<<dim3(64, ns), 256, 0, s>>>(dsk, ws2, args.level, args.seed);
+    bcheck(cudaGetLastError());
+    std::vector<GemmTask> gy, gb;
+    for (int t = 0; t < ns; ++t) {
+      const BigRowDev& r = rows[cand[t]];
+      const int k = sk[t].k, kp = k + 2, n = r.n;
+      GemmTask y{};   // Y = F [Omega | probes] = (F^T)^T Omega
+      y.A = ws + r.g_off; y.lda = n; y.ta = 1;
+      y.B = ws2 + sk[t].om_off; y.ldb = kp; y.tb = 0;
+      y.C = ws2 + sk[t].y_off; y.ldc = kp; y.Cin = y.C; y.ldcin = kp;
+      y.M = n; y.N = kp; y.K = r.mF; y.alpha = 1.f; y.beta = 0.f;
+      gy.push_back(y);
+      GemmTask b{};   // F^T Q
+      b.A = ws + r.g_off; b.lda = n; b.ta = 0;
+      b.B = ws2 + sk[t].q_off; b.ldb = k; b.tb = 0;
+      b.C = ws2 + view[t].g_off; b.ldc = k; b.Cin = b.C; b.ldcin = k;
+      b.M = r.mF; b.N = k; b.K = n; b.alpha = 1.f; b.beta = 0.f;
+      gb.push_back(b);
+    }
+    run_gemm(gy, 3);
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    sketch_qr_kernel<T><<<ns, kBigThreads, 0, s>>>(dsk, ws2, dres);
+    bcheck(cudaGetLastError());
+    run_gemm(gb, 3);
+    const size_t sm = (size_t)CH * kmx * es;
+    if (sm > tsqr_dyn) throw BigFail{cudaErrorInvalidValue};
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    tsqr_part_kernel<T, CH><<<dim3(maxp, ns), kTsqrThreads, sm, s>>>(dview, ws2);
+    bcheck(cudaGetLastError());
+    for (int h = 1; h < maxp; h *= 2) {
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+      tsqr_merge_kernel<T, CH><<<dim3(maxp / (2 * h), ns), kTsqrThreads, sm, s>>>(dview, ws2, h);
+      bcheck(cudaGetLastError());
+    }
+    size_t sj = (size_t)((kmx + 3) & ~3) * (es + sizeof(int)) + 64;
+    const size_t sxv = sj + (size_t)2 * kmx * kmx * es;
+    const int xv = sxv <= jac_dyn ? 1 : 0;
+    if (xv) sj = sxv;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    jacobi_kernel<T><<<ns, kJacThreads, sj, s>>>(dview, ws2, D, args, xv, dres);
+    bcheck(cudaGetLastError());
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    sketch_accept_kernel<T><<<ns, 128, 0, s>>>(dsk, ws2, dres, D, args.stats, args.level);
+    bcheck(cudaGetLastError());
+    std::vector<SketchRes> hres(ns);
+    bcheck(cudaMemcpyAsync(hres.data(), dres, ns * sizeof(SketchRes), cudaMemcpyDeviceToHost, s));
+    bcheck(cudaStreamSynchronize(s));
+    // accepted rows: U_b = Q V_B[:, :r], then its orthogonal completion
+    std::vector<GemmTask> gu;
+    std::vector<SketchRowDev> acc;
+    for (int t = 0; t < ns; ++t) {
+      if (!hres[t].accepted) continue;
+      accepted[cand[t]] = 1;
+      const int r = hres[t].rank, k = sk[t].k;
+      acc.push_back(sk[t]);
+      if (r == 0) continue;
+      GemmTask u{};
+      u.A = ws2 + sk[t].q_off; u.lda = k; u.ta = 0;
+      u.B = ws2 + view[t].u_out; u.ldb = k; u.tb = 0;
+      u.C = ws2 + sk[t].ub_off; u.ldc = r; u.Cin = u.C; u.ldcin = r;
+      u.M = rows[cand[t]].n; u.N = r; u.K = k; u.alpha = 1.f; u.beta = 0.f;
+      gu.push_back(u);
+    }
+    if (!acc.empty()) {
+      run_gemm(gu, 3);
+      SketchRowDev* dacc = nullptr;
+      bcheck(cudaMallocAsync(reinterpret_cast<void**>(&dacc), acc.size() * sizeof(SketchRowDev), s));
+      bcheck(cudaMemcpyAsync(dacc, acc.data(), acc.size() * sizeof(SketchRowDev), cudaMemcpyHostToDevice, s));
+      g_launches.fetch_add(1, std::memory_order_relaxed);
+      complete_u_kernel<T><<<static_cast<int>(acc.size()), kBigThreads, 0, s>>>(dacc, ws2, D);
+      bcheck(cudaGetLastError());
+      bcheck(cudaFreeAsync(dacc, s));
+    }
+    bcheck(cudaFreeAsync(ws2, s));
+    bcheck(cudaFreeAsync(dsk, s));
+    bcheck(cudaFreeAsync(dview, s));
+    bcheck(cudaFreeAsync(dres, s));
+  };
   for (int c = 0; c < P.ncolours; ++c) {
     const int q0 = P.colour_ptr[c], q1 = P.colour_ptr[c + 1];
     if (q1 <= q0) continue;
@@ -1007,6 +1410,7 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
     bcheck(cudaMemcpyAsync(drows, rows.data(), rows.size() * sizeof(BigRowDev), cudaMemcpyHostToDevice, s));
     const int nr = static_cast<int>(rows.size());
     // ---- 1-3: compression ----
+    mark(0);
     if (!gather.empty()) {
       CopyTask* dt = nullptr;
       bcheck(cudaMallocAsync(reinterpret_cast<void**>(&dt), gather.size() * sizeof(CopyTask), s));
@@ -1014,22 +1418,70 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
       bcheck(launch_copy_tasks(es, es, dt, static_cast<int>(gather.size()), pool, ws, s));
       bcheck(cudaFreeAsync(dt, s));
     }
-    {
-      const size_t sm = (size_t)CH * nmaxc * es;
-      if (sm > tsqr_dyn) throw BigFail{cudaErrorInvalidValue};
-      g_launches.fetch_add(1, std::memory_order_relaxed);
-      tsqr_part_kernel<T, CH><<<dim3(maxparts, nr), kTsqrThreads, sm, s>>>(drows, ws);
-      bcheck(cudaGetLastError());
-      for (int h = 1; h < maxparts; h *= 2) {
-        g_launches.fetch_add(1, std::memory_order_relaxed);
-        tsqr_merge_kernel<T, CH><<<dim3(maxparts / (2 * h), nr), kTsqrThreads, sm, s>>>(drows, ws, h);
-        bcheck(cudaGetLastError());
+    mark(1);
+    // randomized range finder (learned form in FP32): up to two attempts,
+    // the second with twice the width for rows that saturated or failed the
+    // probe; accepted rows skip the exact SVD
+    std::vector<char> accepted(nr, 0);
+    if (args.sketch) {
+      std::vector<int> cand, kcur(nr, 0);
+      for (int q = 0; q < nr; ++q) {
+        const int n = rows[q].n;
+        const int kmax = std::min(512, (3 * n) / 4);
+        kcur[q] = std::min(kmax, 64 + 8);
+        if (rows[q].mF > 0 && kcur[q] >= 8 && kcur[q] < n) cand.push_back(q);
       }
-      const size_t sj = (size_t)nmaxc * (es + sizeof(int)) + 64;
-      g_launches.fetch_add(1, std::memory_order_relaxed);
-      jacobi_kernel<T><<<nr, kJacThreads, sj, s>>>(drows, ws, D, args);
-      bcheck(cudaGetLastError());
+      for (int attempt = 0; attempt < 2 && !cand.empty(); ++attempt) {
+        run_sketch(cand, kcur, rows, ws, accepted);
+        std::vector<int> next;
+        for (int q : cand) {
+          if (accepted[q]) continue;
+          const int kmax = std::min(512, (3 * rows[q].n) / 4);
+          if (2 * kcur[q] <= kmax) {
+            kcur[q] *= 2;
+            next.push_back(q);
+          }
+        }
+        cand.swap(next);
+      }
     }
+    mark(2);
+    // exact SVD (TSQR of F_i^T, Jacobi on R) for every other row
+    {
+      std::vector<BigRowDev> ex;
+      int maxp = 1, nmx = 1;
+      for (int q = 0; q < nr; ++q)
+        if (!accepted[q]) {
+          ex.push_back(rows[q]);
+          maxp = std::max(maxp, rows[q].parts);
+          nmx = std::max(nmx, rows[q].n);
+        }
+      if (!ex.empty()) {
+        const int ne = static_cast<int>(ex.size());
+        BigRowDev* dex = nullptr;
+        bcheck(cudaMallocAsync(reinterpret_cast<void**>(&dex), ex.size() * sizeof(BigRowDev), s));
+        bcheck(cudaMemcpyAsync(dex, ex.data(), ex.size() * sizeof(BigRowDev), cudaMemcpyHostToDevice, s));
+        const size_t sm = (size_t)CH * nmx * es;
+        if (sm > tsqr_dyn) throw BigFail{cudaErrorInvalidValue};
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        tsqr_part_kernel<T, CH><<<dim3(maxp, ne), kTsqrThreads, sm, s>>>(dex, ws);
+        bcheck(cudaGetLastError());
+        for (int h = 1; h < maxp; h *= 2) {
+          g_launches.fetch_add(1, std::memory_order_relaxed);
+          tsqr_merge_kernel<T, CH><<<dim3(maxp / (2 * h), ne), kTsqrThreads, sm, s>>>(dex, ws, h);
+          bcheck(cudaGetLastError());
+        }
+        size_t sj = (size_t)((nmx + 3) & ~3) * (es + sizeof(int)) + 64;
+        const size_t sxv = sj + (size_t)2 * nmx * nmx * es;
+        const int xv = sxv <= jac_dyn ? 1 : 0;
+        if (xv) sj = sxv;
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        jacobi_kernel<T><<<ne, kJacThreads, sj, s>>>(dex, ws, D, args, xv, nullptr);
+        bcheck(cudaGetLastError());
+        bcheck(cudaFreeAsync(dex, s));
+      }
+    }
+    mark(3);
     // ranks of the colour (the shapes of everything that follows)
     std::vector<int> rk(P.M);
     bcheck(cudaMemcpyAsync(rk.data(), D.rank, P.M * sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1041,6 +1493,7 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
       cudaFreeAsync(drows, s);
       return;
     }
+    add_phases(3);
     for (int q = q0; q < q1; ++q) rank_h[P.order[q]] = rk[P.order[q]];
     // ---- 4: X = D U, T = U^T X ----
     std::vector<GemmTask> g1, g2;
@@ -1064,12 +1517,15 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
       u.M = n; u.N = n; u.K = n; u.alpha = 1.f; u.beta = 0.f;
       g2.push_back(u);
     }
+    mark(3);
     run_gemm(g1, 3);
     run_gemm(g2, 3);
+    mark(4);
     // ---- 5: Cholesky of T_nn and L_hat^{-1} ----
     g_launches.fetch_add(1, std::memory_order_relaxed);
     cholinv_kernel<T><<<nr, kBigThreads, 0, s>>>(drows, ws, D, args);
     bcheck(cudaGetLastError());
+    mark(5);
     // ---- 6: W_b, Y_p, far rows ----
     std::vector<GemmTask> g3, g4, g5, g6;
     for (int q = q0; q < q1; ++q) {
@@ -1121,6 +1577,7 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
       }
     }
     run_gemm(g3, 3);
+    mark(6);
     // ---- 7: D_i <- T[:r, :r] - W_b^T W_b;  W_p = L_hat^{-1} Y_p[r:] ----
     for (int q = q0; q < q1; ++q) {
       const BigRowDev& rw = rows[q - q0];
@@ -1158,6 +1615,7 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
     }
     // D_i with r == 0: the block is eliminated whole (nothing kept)
     run_gemm(g4, 3);
+    mark(7);
     // ---- 8: kept close rows and the Schur update ----
     for (int q = q0; q < q1; ++q) {
       const BigRowDev& rw = rows[q - q0];
@@ -1205,6 +1663,7 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
     }
     run_gemm(g5, 3);
     run_gemm(g6, args.engine == 2 ? 1 : 3);
+    mark(8);
     for (int q = q0; q < q1; ++q) done[P.order[q]] = 1;
     bcheck(cudaFreeAsync(ws, s));
     bcheck(cudaFreeAsync(drows, s));
@@ -1214,6 +1673,10 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
     bcheck(cudaStreamSynchronize(s));
     if (hs2[1] != 0) throw BigFail{cudaErrorLaunchTimeout};
     if (hs2[0] != 0) return;
+    for (int k = 3; k < 8; ++k) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, ev[k], ev[k + 1]) == cudaSuccess && args.phase_ms) args.phase_ms[k] += ms;
+    }
   }
 }
 
@@ -1233,7 +1696,7 @@ bool level_needs_big_rows(const LevelPlan& P) {
 }
 
 cudaError_t run_big_level(int esize, LevelStore& st, int level, double tol, int tol_mode, int* status, int* stats,
-                          int engine, cudaStream_t s) {
+                          int engine, double* phase_ms, int sketch, unsigned long long seed, cudaStream_t s) {
   int* tc_err = nullptr;
   cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&tc_err), sizeof(int), s);
   if (e != cudaSuccess) return e;
@@ -1242,7 +1705,8 @@ cudaError_t run_big_level(int esize, LevelStore& st, int level, double tol, int 
     cudaFreeAsync(tc_err, s);
     return e;
   }
-  BigLevelArgs a{level, tol, tol_mode, status, stats, engine, tc_err};
+  BigLevelArgs a{level, tol, tol_mode, status, stats, engine, tc_err, phase_ms,
+                 (esize == 4 && sketch && tol_mode != CE_TOL_FIXED) ? 1 : 0, seed};
   try {
     std::vector<int> rank_h;
     if (esize == 8)

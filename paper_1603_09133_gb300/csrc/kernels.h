@@ -133,7 +133,7 @@ cudaError_t launch_gemm_tc(const std::vector<GemmTask>& tasks, int passes, int* 
 // apply of such a level (one launch per colour)
 bool level_needs_big_rows(const LevelPlan& P);
 cudaError_t run_big_level(int esize, LevelStore& st, int level, double tol, int tol_mode, int* status, int* stats,
-                          int engine, cudaStream_t s);
+                          int engine, double* phase_ms, int sketch, unsigned long long seed, cudaStream_t s);
 cudaError_t launch_apply_big(int esize, const LevelDev& L, const LevelPlan& P, double* vec, int forward,
                              cudaStream_t s);
 
