@@ -618,11 +618,13 @@ __global__ void __launch_bounds__(kRed) update_xr_kernel(int64_t n, double* x, d
   if (threadIdx.x == 0) partial[blockIdx.x] = acc;
 }
 
+// p = z on the first pass (p is not read: its memory may hold anything,
+// NaN patterns included), p = z + beta p afterwards
 __global__ void update_p_kernel(int64_t n, double* p, const double* z, const double* scal, int first) {
   const double beta = first ? 0.0 : scal[5];
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
        k += (int64_t)gridDim.x * blockDim.x)
-    p[k] = z[k] + beta * p[k];
+    p[k] = first ? z[k] : z[k] + beta * p[k];
 }
 
 __global__ void pcg_scalars_kernel(double* scal, int stage) {

@@ -119,7 +119,9 @@ __global__ void __launch_bounds__(kT) seg_update_p_kernel(double* p, const doubl
   const int c = blockIdx.x, sy = chunk_sys[c];
   if (done[sy]) return;
   const double beta = first ? 0.0 : sc[sy * kSc + BETA];
-  for (int64_t k = chunk_row[c] + threadIdx.x; k < chunk_row[c + 1]; k += kT) p[k] = z[k] + beta * p[k];
+  // the first pass does not read p (its memory may hold NaN patterns)
+  for (int64_t k = chunk_row[c] + threadIdx.x; k < chunk_row[c + 1]; k += kT)
+    p[k] = first ? z[k] : z[k] + beta * p[k];
 }
 
 // Per-system step on the reduced partials (one CTA; systems in strides):
