@@ -129,6 +129,11 @@ class Problem:
     def __init__(self, name):
         self.name = name
         self.batched = name == BATCH
+        self.is3d = name.startswith("poisson3d")
+        # super-block cap: 64 rows for the 2D grids (every level stays in the
+        # persistent row kernel), none in 3D (the paper's runs of J = 8; the
+        # large blocks run the large-row path)
+        self.nmax = 0 if self.is3d else 64
         if self.batched:
             self.ws = wl.make_batch(BATCH_SYSTEMS)
             w0 = self.ws[0]
@@ -179,11 +184,11 @@ class Problem:
                          / np.linalg.norm(w.b)) for s, w in enumerate(self.ws))
 
 
-def oracle_solve(w):
+def oracle_solve(w, nmax=64):
     """Oracle factorize + PCG of one workload (seconds, PCG iterations)."""
     from oracle import ce as oce
     t0 = time.perf_counter()
-    F = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J, nmax=64)
+    F = oce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J, nmax=nmax)
     res = oce.pcg(w.A, F, w.b, RTOL, 1000)
     t = time.perf_counter() - t0
     assert res.converged
@@ -192,8 +197,17 @@ def oracle_solve(w):
 
 def oracle_step(pb):
     """(seconds for the workload, unknowns timed, PCG iterations, what) of one
-    oracle run: the whole workload for a single system; for the batch, one
-    64x64 system of it, scaled by N (a whole batch is ~250 s of CPU work)."""
+    oracle run: the whole workload for a single 2D system; for the batch, one
+    64x64 system of it, scaled by N (a whole batch is ~250 s of CPU work); in
+    3D the 32^3 grid of the same problem scaled by N (64^3 takes ~20 min in
+    the oracle; its block sizes grow faster than N, so this is a lower bound)."""
+    if pb.is3d:
+        A = wl.poisson3d(32)
+        w = wl.Workload("poisson3d_32_B64", A, wl.box_perm((32, 32, 32), (4, 4, 4)), 64, pb.tol, pb.levels,
+                        pb.J, wl.rhs(A.shape[0], 0), "3D Poisson 7-point 32^3")
+        t, its = oracle_solve(w, nmax=0)
+        return t * pb.N / A.shape[0], A.shape[0], its, \
+            f"the 32^3 grid of the same problem ({pb.levels} levels), scaled linearly to N={pb.N} (a lower bound)"
     if pb.batched:
         w = next(w for w in pb.ws if w.A.shape[0] == 64 * 64)
         t, its = oracle_solve(w)
@@ -291,14 +305,19 @@ def run_ours(args, rank, world):
     # measured arithmetic peaks of this GPU (the roofline denominators)
     peaks = {k: ceg.measure_peak(k) for k in ("fp32_fma", "fp64_fma", "tf32_mma", "tf32x3_mma")}
     # row-kernel CTA shape (and learned or exact per level) chosen by
-    # measurement for both forms (setup, untimed)
-    tune_ms = ceg.ce_autotune(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=args.precision,
-                              rank_model=model)
-    tune_ms_plain = ceg.ce_autotune(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision="fp64")
+    # measurement for both forms (setup, untimed); in 3D a factorization
+    # takes seconds, so the heuristic shapes are kept
+    tune_ms = tune_ms_plain = np.zeros((2, 3, pb.levels))
+    if not pb.is3d:
+        tune_ms = ceg.ce_autotune(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=args.precision,
+                                  rank_model=model, nmax=pb.nmax)
+        tune_ms_plain = ceg.ce_autotune(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision="fp64",
+                                        nmax=pb.nmax)
     tuning = csb.tuning(args.precision, learned=model is not None)
 
     def step(prec, rm=None):
-        F = ceg.ce_factorize(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=prec, rank_model=rm)
+        F = ceg.ce_factorize(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=prec, rank_model=rm,
+                             nmax=pb.nmax)
         it, conv = pb.solve(csb, F, b, x)
         return F, it, conv
 
@@ -329,7 +348,12 @@ def run_ours(args, rank, world):
 
     # plain FP64 form with exact SVDs (the comparison), then the chosen form,
     # each autotuned and timed with the same steps, warm-up and clock sampling
-    t_other, last_other, _, clocks_other = timed("fp64", args.steps, args.warmup)
+    # (in 3D the plain form's exact SVD of blocks of ~700 rows in FP64 takes
+    # minutes per factorization and is not timed)
+    if pb.is3d:
+        t_other, last_other, clocks_other = [float("nan")], (None, None, None), None
+    else:
+        t_other, last_other, _, clocks_other = timed("fp64", args.steps, args.warmup)
     times, last, launches, clocks = timed(args.precision, args.steps, args.warmup, model)
     F, it, conv = last
     true_rel = pb.true_relres(x.cpu().numpy())
@@ -373,7 +397,7 @@ def run_ours(args, rank, world):
         csb2 = pb.build(arrays)
         csb2.set_tuning(tuning, args.precision, learned=model is not None)
         F2 = ceg.ce_factorize(csb2, tol=pb.tol, levels=pb.levels, J=pb.J, precision=args.precision,
-                              rank_model=model)
+                              rank_model=model, nmax=pb.nmax)
         bd = b_host.to(dev, non_blocking=True)
         xd = torch.empty_like(bd)
         pb.solve(csb2, F2, bd, xd)
@@ -400,6 +424,9 @@ def run_ours(args, rank, world):
                   "autotune_ms": np.round(tune_ms, 3).tolist(),
                   "autotune_ms_plain_fp64": np.round(tune_ms_plain, 3).tolist(),
                   "jacobi_capped": [info.jacobi_capped[l] for l in range(nl)],
+                  "big_rows": [info.big_rows[l] for l in range(nl)],
+                  "big_steps_ms": dict(zip(["gather", "sketch", "exact_svd", "UtDU", "chol_inv", "W_Y_far",
+                                            "D_Wp", "kept_schur"], [round(v, 2) for v in info.big_ms])),
                   "host_ms": [round(info.host_ms[l], 3) for l in range(nl)],
                   "factor_wall_ms": round(info.total_ms, 3),
                   "coarse_n": info.coarse_n, "coarse_ms": round(info.coarse_ms, 3),
@@ -413,7 +440,8 @@ def run_ours(args, rank, world):
                       "systems": len(pb.ws),
                       "form": f"{args.ranks} ranks + {args.precision} factor + fp64 PCG",
                       "pcg_iters": it, "final_relres": true_rel,
-                      "plain_fp64_form_s": statistics.mean(t_other) / 1e3,
+                      "nmax": pb.nmax,
+                      "plain_fp64_form_s": None if pb.is3d else statistics.mean(t_other) / 1e3,
                       "plain_fp64_form_pcg_iters": last_other[1],
                       "plain_fp64_form_clocks": clocks_other,
                       "plain_fp64_form_timing": "autotuned (exact SVD, FP64), same steps, warm-up, "

@@ -78,8 +78,9 @@ typedef struct {
   void* stream;    /* cudaStream_t for all device work                   */
   int rank_mode;   /* CE_RANK_SVD (default) / CE_RANK_LEARNED; on levels
                       run by the large-row path the learned form (FP32)
-                      sketches each row with width 72, then 144 (at most
-                      3n/4), before the exact SVD                         */
+                      sketches each row with width 72, doubled after a
+                      rejection up to min(512, 3n/4), before the exact
+                      SVD                                                 */
   const void* rank_model; /* device, ce_mlp_nparams() FP16 values from
                              ce_mlp_pack (CE_RANK_LEARNED only)          */
   int oversample;  /* p, sketch columns beyond r_hat (default 8)         */

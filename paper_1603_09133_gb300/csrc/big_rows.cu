@@ -1419,9 +1419,9 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
       bcheck(cudaFreeAsync(dt, s));
     }
     mark(1);
-    // randomized range finder (learned form in FP32): up to two attempts,
-    // the second with twice the width for rows that saturated or failed the
-    // probe; accepted rows skip the exact SVD
+    // randomized range finder (learned form in FP32): width 72, doubled for
+    // the rows that saturated or failed the probe, up to min(512, 3n/4);
+    // accepted rows skip the exact SVD
     std::vector<char> accepted(nr, 0);
     if (args.sketch) {
       std::vector<int> cand, kcur(nr, 0);
@@ -1431,14 +1431,15 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
         kcur[q] = std::min(kmax, 64 + 8);
         if (rows[q].mF > 0 && kcur[q] >= 8 && kcur[q] < n) cand.push_back(q);
       }
-      for (int attempt = 0; attempt < 2 && !cand.empty(); ++attempt) {
+      while (!cand.empty()) {
         run_sketch(cand, kcur, rows, ws, accepted);
         std::vector<int> next;
         for (int q : cand) {
           if (accepted[q]) continue;
           const int kmax = std::min(512, (3 * rows[q].n) / 4);
-          if (2 * kcur[q] <= kmax) {
-            kcur[q] *= 2;
+          const int kn = std::min(kmax, 2 * kcur[q]);
+          if (kn > kcur[q]) {
+            kcur[q] = kn;
             next.push_back(q);
           }
         }
