@@ -4,9 +4,13 @@
 // FP64 Cholesky of the dense remainder A_K (Algorithm 1, last step).
 #include <cuda_runtime.h>
 
+#include <cooperative_groups.h>
+
 #include <algorithm>
 
 #include "kernels.h"
+
+namespace cg = cooperative_groups;
 
 namespace ce {
 
@@ -118,157 +122,187 @@ __device__ __forceinline__ double rsqrt_nr(double x) {
   return y;
 }
 
-// Cholesky of the diagonal tile, then its inverse (for the TRSM below):
-// tile inverse of system y at Tinv[y * NB * NB] (row-major, lower)
-__global__ void __launch_bounds__(256) potrf_tile_kernel(double* A, const int64_t* desc, int nsys, int k0,
-                                                         int level, int* status, double* Tinv) {
-  if (*status) return;
-  int n;
-  if (!coarse_sys(A, n, desc, nsys, k0)) return;
-  __shared__ double t[NB * NBL];
-  __shared__ double x[NB * NBL];
-  const int nb = min(NB, n - k0);
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    int a = e / nb, b = e - a * nb;
-    t[a * NBL + b] = A[(int64_t)(k0 + a) * n + k0 + b];
-  }
-  __syncthreads();
+// Cholesky of the nb x nb tile t (shared memory, lower, ld NBL) by one warp
+// without CTA barriers: lane a holds row a; step k scales column k below the
+// pivot and updates the trailing lower triangle.  false (and the failing
+// pivot) when a pivot is not positive.
+__device__ bool warp_potrf(double* t, int nb, int lane, int& bad_k, double& bad_v) {
   for (int k = 0; k < nb; ++k) {
     const double piv = t[k * NBL + k];
     if (!(piv > 0.0)) {
-      if (threadIdx.x == 0) set_status(status, CE_ERR_NOT_SPD, level, -1 - (int)blockIdx.y, 1, k0 + k, piv);
-      return;
+      bad_k = k;
+      bad_v = piv;
+      return false;
     }
     const double inv = rsqrt_nr(piv);
-    // column k below the pivot (each thread scales the entries it reads next)
-    const int rem = nb - k - 1;
-    for (int e = threadIdx.x; e < rem * rem; e += blockDim.x) {
-      const int a = k + 1 + e / rem, b = k + 1 + e % rem;
-      if (b <= a) t[a * NBL + b] -= (t[a * NBL + k] * inv) * (t[b * NBL + k] * inv);
-    }
-    __syncthreads();
-    for (int a = k + 1 + threadIdx.x; a < nb; a += blockDim.x) t[a * NBL + k] *= inv;
-    if (threadIdx.x == 0) t[k * NBL + k] = piv * inv;
-    __syncthreads();
+    double lak = 0.0;
+    if (lane > k && lane < nb) lak = t[lane * NBL + k] * inv;
+    __syncwarp();
+    if (lane > k && lane < nb) t[lane * NBL + k] = lak;
+    if (lane == k) t[k * NBL + k] = piv * inv;
+    __syncwarp();
+    if (lane > k && lane < nb)
+      for (int b = k + 1; b <= lane; ++b) t[lane * NBL + b] -= lak * t[b * NBL + k];
+    __syncwarp();
   }
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    int a = e / nb, b = e - a * nb;
-    A[(int64_t)(k0 + a) * n + k0 + b] = (b <= a) ? t[a * NBL + b] : 0.0;
-  }
-  // inverse of the lower tile: column j by forward substitution (thread j),
-  // with the reciprocals of the diagonal formed once, in parallel
-  __shared__ double rd[NB];
-  if (threadIdx.x < nb) rd[threadIdx.x] = 1.0 / t[threadIdx.x * NBL + threadIdx.x];
-  __syncthreads();
-  const int j = threadIdx.x;
-  if (j < nb) {
-    for (int a = 0; a < j; ++a) x[a * NBL + j] = 0.0;
-    for (int a = j; a < nb; ++a) {
-      double s0 = (a == j) ? 1.0 : 0.0, s1 = 0.0;
-      int k = j;
-      for (; k + 1 < a; k += 2) {
-        s0 -= t[a * NBL + k] * x[k * NBL + j];
-        s1 -= t[a * NBL + k + 1] * x[(k + 1) * NBL + j];
-      }
-      if (k < a) s0 -= t[a * NBL + k] * x[k * NBL + j];
-      x[a * NBL + j] = (s0 + s1) * rd[a];
-    }
-  }
-  __syncthreads();
-  double* Ti = Tinv + (size_t)blockIdx.y * NB * NB;
-  for (int e = threadIdx.x; e < nb * nb; e += blockDim.x) {
-    int a = e / nb, b = e - a * nb;
-    Ti[a * NB + b] = x[a * NBL + b];
-  }
+  return true;
 }
 
-// L_ik = A_ik L_kk^{-T} for the 32-row tiles below the diagonal tile k0, as a
-// product with the tile inverse: L_ik[a][b] = sum_{c <= b} A_ik[a][c] Tinv[b][c]
-__global__ void __launch_bounds__(256) trsm_tile_kernel(double* A, const int64_t* desc, int nsys, int k0,
-                                                        const int* status, const double* Tinv) {
-  if (*status) return;
-  int n;
-  if (!coarse_sys(A, n, desc, nsys, k0)) return;
-  __shared__ double Ti[NB * NBL];
-  __shared__ double X[NB * NBL];
+// Work items of a panel step for system y (n_y rows, panel at k0): the
+// diagonal tile and the row tiles below it (phase A); the copy of the
+// factored diagonal tile and the trailing lower tile pairs (phase B).
+__device__ __forceinline__ int panel_tiles(int n, int k0) {
+  if (k0 >= n) return -1;
   const int nb = min(NB, n - k0);
-  const int i0 = k0 + nb + blockIdx.x * NB;
-  if (i0 >= n) return;
-  const int rows = min(NB, n - i0);
-  const double* T = Tinv + (size_t)blockIdx.y * NB * NB;
-  for (int e = threadIdx.x; e < nb * nb; e += 256) {
-    int a = e / nb, b = e - a * nb;
-    Ti[a * NBL + b] = T[a * NB + b];
-  }
-  for (int e = threadIdx.x; e < rows * nb; e += 256) {
-    int a = e / nb, b = e - a * nb;
-    X[a * NBL + b] = A[(int64_t)(i0 + a) * n + k0 + b];
-  }
-  __syncthreads();
-  double out[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int e = threadIdx.x + u * 256, a = e / NB, b = e % NB;
-    double s0 = 0.0, s1 = 0.0;
-    if (a < rows && b < nb) {
-      int c = 0;
-      for (; c + 1 <= b; c += 2) {
-        s0 += X[a * NBL + c] * Ti[b * NBL + c];
-        s1 += X[a * NBL + c + 1] * Ti[b * NBL + c + 1];
-      }
-      if (c <= b) s0 += X[a * NBL + c] * Ti[b * NBL + c];
-    }
-    out[u] = s0 + s1;
-  }
-#pragma unroll
-  for (int u = 0; u < 4; ++u) {
-    const int e = threadIdx.x + u * 256, a = e / NB, b = e % NB;
-    if (a < rows && b < nb) A[(int64_t)(i0 + a) * n + k0 + b] = out[u];
-  }
+  return (n - k0 - nb + NB - 1) / NB;
 }
 
-// A_ij -= L_ik L_jk^T for the trailing 32 x 32 tiles j <= i (2 x 2 outputs
-// per thread)
-__global__ void __launch_bounds__(256) syrk_tile_kernel(double* A, const int64_t* desc, int nsys, int k0,
-                                                        const int* status) {
-  if (*status) return;
-  int n;
-  if (!coarse_sys(A, n, desc, nsys, k0)) return;
-  __shared__ double Li[NB * NBL];
-  __shared__ double Lj[NB * NBL];
-  const int nb = min(NB, n - k0);
-  const int t0 = k0 + nb;
-  // blockIdx.x enumerates the lower-triangular tile pairs (ti >= tj)
-  int ti = 0, idx = blockIdx.x;
-  while (idx > ti) {
-    idx -= ti + 1;
-    ++ti;
+constexpr int kCC = 256;
+
+// Dense FP64 Cholesky of every system's coarse matrix in one cooperative
+// launch: per 32-column panel, phase A factors the diagonal tile (each work
+// item redundantly, by one warp) and solves its own 32-row tile below it
+// (L_ik = A_ik L_kk^{-T}, forward substitution per row); the factored tile is
+// staged in Tfac[y] because other items still read the original; a grid
+// barrier; phase B copies the staged tile and updates the trailing lower
+// tiles A_ij -= L_ik L_jk^T; a grid barrier.  A recorded failure turns the
+// remaining work off (every CTA still meets every barrier).
+__global__ void __launch_bounds__(kCC) coarse_chol_coop_kernel(double* A, const int64_t* desc, int nsys, int nmax,
+                                                               int level, int* status, double* Tfac) {
+  cg::grid_group grid = cg::this_grid();
+  __shared__ double t[NB * NBL], X[NB * NBL], rd[NB];
+  __shared__ int s_stop;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int k0 = 0; k0 < nmax; k0 += NB) {
+    // ---- phase A ----
+    int total = 0;
+    for (int y = 0; y < nsys; ++y) {
+      const int T = panel_tiles(static_cast<int>(desc[y]), k0);
+      if (T >= 0) total += 1 + T;
+    }
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+      if (tid == 0) s_stop = *(volatile int*)status;   // one reading per CTA: the exit is uniform
+      __syncthreads();
+      if (s_stop) break;
+      int y = 0, r = it;
+      for (;; ++y) {
+        const int T = panel_tiles(static_cast<int>(desc[y]), k0);
+        if (T < 0) continue;
+        if (r < 1 + T) break;
+        r -= 1 + T;
+      }
+      const int n = static_cast<int>(desc[y]);
+      double* Ay = A + desc[nsys + y];
+      const int nb = min(NB, n - k0);
+      for (int e = tid; e < nb * nb; e += kCC) {
+        const int a = e / nb, c = e - a * nb;
+        t[a * NBL + c] = Ay[(int64_t)(k0 + a) * n + k0 + c];
+      }
+      __syncthreads();
+      __shared__ int s_ok;
+      if (warp == 0) {
+        int bk = 0;
+        double bv = 0.0;
+        const bool ok = warp_potrf(t, nb, lane, bk, bv);
+        if (lane == 0) {
+          s_ok = ok;
+          if (!ok && r == 0) set_status(status, CE_ERR_NOT_SPD, level, -1 - y, 1, k0 + bk, bv);
+        }
+        if (ok && lane < nb) rd[lane] = 1.0 / t[lane * NBL + lane];
+      }
+      __syncthreads();
+      if (!s_ok) continue;
+      if (r == 0) {
+        double* Tf = Tfac + (size_t)y * NB * NB;
+        for (int e = tid; e < NB * NB; e += kCC) {
+          const int a = e / NB, c = e - a * NB;
+          Tf[e] = (a < nb && c <= a) ? t[a * NBL + c] : 0.0;
+        }
+      } else {
+        const int i0 = k0 + nb + (r - 1) * NB, rows = min(NB, n - i0);
+        for (int e = tid; e < rows * nb; e += kCC) {
+          const int a = e / nb, c = e - a * nb;
+          X[a * NBL + c] = Ay[(int64_t)(i0 + a) * n + k0 + c];
+        }
+        __syncthreads();
+        if (tid < rows) {
+          for (int c = 0; c < nb; ++c) {
+            double s0 = X[tid * NBL + c];
+            for (int q = 0; q < c; ++q) s0 -= X[tid * NBL + q] * t[c * NBL + q];
+            X[tid * NBL + c] = s0 * rd[c];
+          }
+        }
+        __syncthreads();
+        for (int e = tid; e < rows * nb; e += kCC) {
+          const int a = e / nb, c = e - a * nb;
+          Ay[(int64_t)(i0 + a) * n + k0 + c] = X[a * NBL + c];
+        }
+      }
+      __syncthreads();
+    }
+    grid.sync();
+    // ---- phase B ----
+    total = 0;
+    for (int y = 0; y < nsys; ++y) {
+      const int T = panel_tiles(static_cast<int>(desc[y]), k0);
+      if (T >= 0) total += 1 + T * (T + 1) / 2;
+    }
+    for (int it = blockIdx.x; it < total; it += gridDim.x) {
+      if (tid == 0) s_stop = *(volatile int*)status;
+      __syncthreads();
+      if (s_stop) break;
+      int y = 0, r = it;
+      for (;; ++y) {
+        const int T = panel_tiles(static_cast<int>(desc[y]), k0);
+        if (T < 0) continue;
+        if (r < 1 + T * (T + 1) / 2) break;
+        r -= 1 + T * (T + 1) / 2;
+      }
+      const int n = static_cast<int>(desc[y]);
+      double* Ay = A + desc[nsys + y];
+      const int nb = min(NB, n - k0);
+      if (r == 0) {
+        const double* Tf = Tfac + (size_t)y * NB * NB;
+        for (int e = tid; e < nb * nb; e += kCC) {
+          const int a = e / nb, c = e - a * nb;
+          Ay[(int64_t)(k0 + a) * n + k0 + c] = Tf[a * NB + c];
+        }
+        __syncthreads();
+        continue;
+      }
+      int ti = 0, idx = r - 1;
+      while (idx > ti) {
+        idx -= ti + 1;
+        ++ti;
+      }
+      const int tj = idx;
+      const int t0 = k0 + nb, i0 = t0 + ti * NB, j0 = t0 + tj * NB;
+      const int ri = min(NB, n - i0), rj = min(NB, n - j0);
+      for (int e = tid; e < NB * nb; e += kCC) {
+        const int a = e / nb, c = e - a * nb;
+        t[a * NBL + c] = a < ri ? Ay[(int64_t)(i0 + a) * n + k0 + c] : 0.0;
+        X[a * NBL + c] = a < rj ? Ay[(int64_t)(j0 + a) * n + k0 + c] : 0.0;
+      }
+      __syncthreads();
+      const int a0 = (tid / 16) * 2, b0 = (tid % 16) * 2;
+      double c00 = 0, c01 = 0, c10 = 0, c11 = 0;
+      for (int c = 0; c < nb; ++c) {
+        const double x0 = t[a0 * NBL + c], x1 = t[(a0 + 1) * NBL + c];
+        const double y0 = X[b0 * NBL + c], y1 = X[(b0 + 1) * NBL + c];
+        c00 += x0 * y0;
+        c01 += x0 * y1;
+        c10 += x1 * y0;
+        c11 += x1 * y1;
+      }
+      double* C = Ay + (int64_t)i0 * n + j0;
+      if (a0 < ri && b0 < rj) C[(int64_t)a0 * n + b0] -= c00;
+      if (a0 < ri && b0 + 1 < rj) C[(int64_t)a0 * n + b0 + 1] -= c01;
+      if (a0 + 1 < ri && b0 < rj) C[(int64_t)(a0 + 1) * n + b0] -= c10;
+      if (a0 + 1 < ri && b0 + 1 < rj) C[(int64_t)(a0 + 1) * n + b0 + 1] -= c11;
+      __syncthreads();
+    }
+    grid.sync();
   }
-  const int tj = idx;
-  const int i0 = t0 + ti * NB, j0 = t0 + tj * NB;
-  if (i0 >= n) return;
-  const int ri = min(NB, n - i0), rj = min(NB, n - j0);
-  for (int e = threadIdx.x; e < NB * nb; e += 256) {
-    int a = e / nb, b = e - a * nb;
-    Li[a * NBL + b] = a < ri ? A[(int64_t)(i0 + a) * n + k0 + b] : 0.0;
-    Lj[a * NBL + b] = a < rj ? A[(int64_t)(j0 + a) * n + k0 + b] : 0.0;
-  }
-  __syncthreads();
-  const int a0 = (threadIdx.x / 16) * 2, b0 = (threadIdx.x % 16) * 2;
-  double c00 = 0, c01 = 0, c10 = 0, c11 = 0;
-  for (int c = 0; c < nb; ++c) {
-    const double x0 = Li[a0 * NBL + c], x1 = Li[(a0 + 1) * NBL + c];
-    const double y0 = Lj[b0 * NBL + c], y1 = Lj[(b0 + 1) * NBL + c];
-    c00 += x0 * y0;
-    c01 += x0 * y1;
-    c10 += x1 * y0;
-    c11 += x1 * y1;
-  }
-  double* C = A + (int64_t)i0 * n + j0;
-  if (a0 < ri && b0 < rj) C[(int64_t)a0 * n + b0] -= c00;
-  if (a0 < ri && b0 + 1 < rj) C[(int64_t)a0 * n + b0 + 1] -= c01;
-  if (a0 + 1 < ri && b0 < rj) C[(int64_t)(a0 + 1) * n + b0] -= c10;
-  if (a0 + 1 < ri && b0 + 1 < rj) C[(int64_t)(a0 + 1) * n + b0 + 1] -= c11;
 }
 
 }  // namespace
@@ -302,22 +336,24 @@ cudaError_t launch_copy_tasks(int esize_src, int esize_dst, const CopyTask* task
 
 cudaError_t coarse_cholesky(double* A, const int64_t* desc, int nsys, int nmax, int level, int* status,
                             double* tinv, cudaStream_t s) {
-  // the grids cover the largest system; smaller ones return early
-  for (int k0 = 0; k0 < nmax; k0 += NB) {
-    g_launches.fetch_add(1, std::memory_order_relaxed);
-    potrf_tile_kernel<<<dim3(1, nsys), 256, 0, s>>>(A, desc, nsys, k0, level, status, tinv);
-    const int nb = std::min(NB, nmax - k0);
-    const int below = nmax - k0 - nb;
-    if (below > 0) {
-      const int tiles = (below + NB - 1) / NB;
-      g_launches.fetch_add(2, std::memory_order_relaxed);
-      trsm_tile_kernel<<<dim3(tiles, nsys), 256, 0, s>>>(A, desc, nsys, k0, status, tinv);
-      syrk_tile_kernel<<<dim3(tiles * (tiles + 1) / 2, nsys), 256, 0, s>>>(A, desc, nsys, k0, status);
-    }
-    cudaError_t e = cudaGetLastError();
+  if (nmax <= 0) return cudaSuccess;
+  // one resident wave of cooperative CTAs (every CTA meets every grid barrier)
+  static int cap = 0;
+  if (cap == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, coarse_chol_coop_kernel, kCC, 0);
     if (e != cudaSuccess) return e;
+    cap = std::max(1, std::min(per_sm, 2)) * sms;
   }
-  return cudaSuccess;
+  // enough CTAs for the largest panel step's work, at most one wave
+  const int T = (nmax + NB - 1) / NB;
+  const int64_t work = (int64_t)nsys * (1 + (int64_t)T * (T + 1) / 2);
+  const int grid = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(cap, work)));
+  void* args[] = {&A, const_cast<int64_t**>(&desc), &nsys, &nmax, &level, &status, &tinv};
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  return cudaLaunchCooperativeKernel((const void*)coarse_chol_coop_kernel, dim3(grid), dim3(kCC), args, 0, s);
 }
 
 size_t coarse_tile_scratch(int nsys) { return (size_t)nsys * NB * NB * sizeof(double); }
