@@ -53,6 +53,8 @@ def parse():
     p.add_argument("--ranks", default="learned", choices=["learned", "svd"])
     p.add_argument("--workload", default=WORKLOAD)
     p.add_argument("--no-baseline", action="store_true", help="skip the oracle timing")
+    p.add_argument("--coloring", type=int, default=1, choices=[1, 2],
+                   help="elimination order: 1 distance-2 colours, 2 distance-1 colours")
     return p.parse_args()
 
 
@@ -310,14 +312,14 @@ def run_ours(args, rank, world):
     tune_ms = tune_ms_plain = np.zeros((2, 3, pb.levels))
     if not pb.is3d:
         tune_ms = ceg.ce_autotune(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=args.precision,
-                                  rank_model=model, nmax=pb.nmax)
+                                  rank_model=model, nmax=pb.nmax, coloring=args.coloring)
         tune_ms_plain = ceg.ce_autotune(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision="fp64",
-                                        nmax=pb.nmax)
+                                        nmax=pb.nmax, coloring=args.coloring)
     tuning = csb.tuning(args.precision, learned=model is not None)
 
     def step(prec, rm=None):
         F = ceg.ce_factorize(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=prec, rank_model=rm,
-                             nmax=pb.nmax)
+                             nmax=pb.nmax, coloring=args.coloring)
         it, conv = pb.solve(csb, F, b, x)
         return F, it, conv
 
@@ -397,7 +399,7 @@ def run_ours(args, rank, world):
         csb2 = pb.build(arrays)
         csb2.set_tuning(tuning, args.precision, learned=model is not None)
         F2 = ceg.ce_factorize(csb2, tol=pb.tol, levels=pb.levels, J=pb.J, precision=args.precision,
-                              rank_model=model, nmax=pb.nmax)
+                              rank_model=model, nmax=pb.nmax, coloring=args.coloring)
         bd = b_host.to(dev, non_blocking=True)
         xd = torch.empty_like(bd)
         pb.solve(csb2, F2, bd, xd)
@@ -441,6 +443,7 @@ def run_ours(args, rank, world):
                       "form": f"{args.ranks} ranks + {args.precision} factor + fp64 PCG",
                       "pcg_iters": it, "final_relres": true_rel,
                       "nmax": pb.nmax,
+                      "coloring": {1: "distance-2", 2: "distance-1"}[args.coloring],
                       "plain_fp64_form_s": None if pb.is3d else statistics.mean(t_other) / 1e3,
                       "plain_fp64_form_pcg_iters": last_other[1],
                       "plain_fp64_form_clocks": clocks_other,

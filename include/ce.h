@@ -74,7 +74,13 @@ typedef struct {
   int levels;      /* K, number of compress-and-eliminate sweeps         */
   int J;           /* super-block size: J consecutive blocks join        */
   int precision;   /* CE_PREC_*                                          */
-  int coloring;    /* 1: colour-major order (default); 0: natural order  */
+  int coloring;    /* elimination order within a level: 1 (default)
+                      colour-major order of a distance-2 colouring (rows
+                      of a colour touch disjoint block pairs); 2 of a
+                      distance-1 colouring (fewer colours; rows of a
+                      colour may share Schur targets, updated atomically,
+                      so sums of shared targets are order-dependent at the
+                      rounding level); 0 natural order                    */
   void* stream;    /* cudaStream_t for all device work                   */
   int rank_mode;   /* CE_RANK_SVD (default) / CE_RANK_LEARNED; on levels
                       run by the large-row path the learned form (FP32)

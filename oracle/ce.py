@@ -61,8 +61,10 @@ Readings of points the paper leaves open:
   (fill that cancelled to roundoff) carries no direction worth keeping.
 * Elimination order inside a level: colour-major order of a greedy distance-2
   colouring of the level's block graph, the blocks visited breadth-first from a
-  block of least degree (ascending block index inside a colour).  The paper's
-  natural order (Algorithm 2) is ``order='natural'``; both are permutations P,
+  block of least degree (ascending block index inside a colour);
+  ``order='colour1'`` uses a distance-1 colouring in the same visit order
+  (fewer colours; rows of a colour may share Schur targets).  The paper's
+  natural order (Algorithm 2) is ``order='natural'``; all are permutations P,
   which the paper leaves free (Section 2).
 * Super-blocks: runs of J consecutive blocks (Section 2.4); with ``nmax`` a run
   over nmax rows is halved until its parts fit (they stay aligned with the
@@ -175,6 +177,24 @@ def distance2_colouring(nbr):
     return colour
 
 
+def distance1_colouring(nbr):
+    """Greedy distance-1 colouring in the same breadth-first order: block i
+    takes the smallest colour not held by an adjacent, already coloured block.
+    Blocks of one colour are not adjacent: the row of one never holds a block
+    of another, so neither row's compression or elimination reads what the
+    other writes; they may share close neighbours, whose pairs both rows'
+    Schur updates then add to (in any order: the sums commute)."""
+    M = len(nbr)
+    colour = [-1] * M
+    for i in bfs_order(nbr):
+        seen = {colour[j] for j in nbr[i] if j != i and colour[j] >= 0}
+        c = 0
+        while c in seen:
+            c += 1
+        colour[i] = c
+    return colour
+
+
 # --------------------------------------------------------------------------
 # factor records
 # --------------------------------------------------------------------------
@@ -279,7 +299,7 @@ def _one_level(S, sizes, tol, tol_mode, order_mode, level_no,
         colour = [0] * M
         order = list(range(M))
     else:
-        colour = distance2_colouring(close)
+        colour = distance1_colouring(close) if order_mode == "colour1" else distance2_colouring(close)
         order = sorted(range(M), key=lambda i: (colour[i], i))
         if shuffle_rng is not None:     # self-test: any order inside a colour
             order = []

@@ -293,7 +293,8 @@ def _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, ove
     o.levels = int(levels)
     o.J = int(J)
     o.precision = CE_PREC_FP64 if precision == "fp64" else CE_PREC_FP32
-    o.coloring = 1 if coloring else 0
+    # True / 1: distance-2 colours, 2: distance-1 colours, False / 0: natural order
+    o.coloring = 2 if coloring == 2 else (1 if coloring else 0)
     o.stream = _stream_ptr(stream)
     if rank_model is not None:
         o.rank_mode = CE_RANK_LEARNED

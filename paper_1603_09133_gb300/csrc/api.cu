@@ -420,6 +420,7 @@ void build_level_store(LevelStore& st, int esize, cudaStream_t s, const void* sh
   D.fdone = reinterpret_cast<int*>(b + o_fd);
   D.bdone = reinterpret_cast<int*>(b + o_bd);
   D.wait_ns = 2000000000ull;  // 2 s: never reached unless a row's neighbours stall
+  D.accumulate = P.coloring == 2 ? 1 : 0;
   D.kw = reinterpret_cast<int*>(b + o_kw);
   D.feat = reinterpret_cast<float*>(b + o_feat);
   D.aq = nullptr;
@@ -1070,7 +1071,8 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       (o.tol_mode == CE_TOL_FIXED && (o.rank < 0 || o.rank_mode != CE_RANK_SVD)) ||
       (o.rank_mode != CE_RANK_SVD && o.rank_mode != CE_RANK_LEARNED) ||
       (o.rank_mode == CE_RANK_LEARNED && (!o.rank_model || o.oversample < 0)) || o.row_shape < -1 ||
-      o.row_shape > 2 || o.nmax < 0 || o.gemm_engine < 0 || o.gemm_engine > 2)
+      o.row_shape > 2 || o.nmax < 0 || o.gemm_engine < 0 || o.gemm_engine > 2 || o.coloring < 0 ||
+      o.coloring > 2)
     return CE_ERR_INVALID_ARG;
   // CE(r): the row kernel takes r in place of the tolerance
   if (o.tol_mode == CE_TOL_FIXED) o.tol = static_cast<double>(o.rank);
@@ -1103,15 +1105,15 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
     la.stats = F->d_status + ce::kStatusWords;
     la.record = o.record_features != 0;
     std::shared_ptr<const LevelPlan> curp;
-    if (o.coloring) {
+    if (o.coloring == 1) {
       curp = A->plan1;
-    } else {
+    } else {   // natural order or distance-1 colours: the same pairs, another order
       const LevelPlan& P1 = *A->plan1;
       std::vector<std::pair<int, int>> pr;
       for (size_t p = 0; p < P1.pair_i.size(); ++p)
         if (P1.pair_close[p]) pr.emplace_back(P1.pair_i[p], P1.pair_k[p]);
       auto np = std::make_shared<LevelPlan>();
-      ce::plan_level(*np, P1.n, pr, false, P1.sys_off);
+      ce::plan_level(*np, P1.n, pr, o.coloring, P1.sys_off);
       curp = np;
     }
     pool = dalloc(curp->pool_elems * es, s);
@@ -1215,7 +1217,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       }
       ce::NextLevel nx = ce::coarsen_structure(P, guess, o.J);
       auto nxtp = std::make_shared<LevelPlan>();
-      ce::plan_structure(*nxtp, nx.M, nx.pairs, o.coloring != 0, nx.sys_off);
+      ce::plan_structure(*nxtp, nx.M, nx.pairs, o.coloring, nx.sys_off);
       check(cudaStreamSynchronize(s), "level sync");
       t_host = clk::now();
       st.rank.assign(hread, hread + P.M);
@@ -1255,7 +1257,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
         if (o.nmax > 0 && ce::coarsen_parents(P, o.J, &st.rank, o.nmax) != nx.parent) same = false;
         if (!same) {
           nx = ce::coarsen_structure(P, live, o.J, &st.rank, o.nmax);
-          ce::plan_structure(*nxtp, nx.M, nx.pairs, o.coloring != 0, nx.sys_off);
+          ce::plan_structure(*nxtp, nx.M, nx.pairs, o.coloring, nx.sys_off);
         }
       }
       ce::coarsen_sizes(P, st.rank, nx);

@@ -189,6 +189,8 @@ __device__ __forceinline__ void fwd_block(const LevelDev& L, const int i, double
         const int t = target_of(tg, f), c = f - tg.pre[t];
         if (t == 0)
           v[c] = static_cast<double>(yt[c] - s);
+        else if (L.accumulate)   // rows of a distance-1 colour may share target t
+          atomicAdd(&vec[tg.voff[t] + c], -static_cast<double>(s));
         else
           vec[tg.voff[t] + c] -= static_cast<double>(s);
       },

@@ -170,11 +170,13 @@ __global__ void __launch_bounds__(kGThreads) gemm_tasks_kernel(const GemmTask* t
       const int n = n0 + tx + 16 * j;
       if (n >= N) continue;
       T v = alpha * acc[i][j];
+      T* dst = tk.tc ? &C[(int64_t)n * tk.ldc + m] : &C[(int64_t)m * tk.ldc + n];
+      if (tk.atomic) {
+        atomicAdd(dst, v);
+        continue;
+      }
       if (beta != T(0)) v += beta * (tk.tcin ? Cin[(int64_t)n * tk.ldcin + m] : Cin[(int64_t)m * tk.ldcin + n]);
-      if (tk.tc)
-        C[(int64_t)n * tk.ldc + m] = v;
-      else
-        C[(int64_t)m * tk.ldc + n] = v;
+      *dst = v;
     }
   }
 }
@@ -1035,6 +1037,8 @@ __global__ void __launch_bounds__(kBigThreads) apply_big_kernel(LevelDev L, int 
       for (int k = 0; k < m; ++k) s += Wt[(int64_t)k * w] * z[k];
       if (t == 0)
         v[c] = static_cast<double>(yt[c] - s);
+      else if (L.accumulate)
+        atomicAdd(&vec[tg.voff[t] + c], -static_cast<double>(s));
       else
         vec[tg.voff[t] + c] -= static_cast<double>(s);
     }
@@ -1659,6 +1663,7 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
           t.C = pool + pv.off; t.ldc = pv.ld; t.tc = pv.trans;
           t.Cin = t.C; t.ldcin = pv.ld; t.tcin = pv.trans;
           t.M = tw[a2]; t.N = tw[b2]; t.K = m; t.alpha = -1.f; t.beta = 1.f;
+          t.atomic = D.accumulate;   // rows of a distance-1 colour may share (p, q)
           g6.push_back(t);
         }
     }

@@ -60,6 +60,7 @@ void parallel_for(int64_t n, int64_t grain, F&& f) {
 // ---------------------------------------------------------------------------
 struct LevelPlan {
   int M = 0;
+  int coloring = 1;              // 0 natural order, 1 distance-2, 2 distance-1 colours
   std::vector<int> n;            // block sizes
   std::vector<int> colour;
   int ncolours = 0;
@@ -113,10 +114,13 @@ struct LevelPlan {
 // does everything that depends on the pattern alone (colouring, squared
 // pattern, lists, dependencies), plan_layout what depends on the sizes
 // (pool, factor and vector offsets); plan_level is both.
+// coloring: 0 natural order (each block its own step), 1 distance-2 colours
+// (no two rows of a colour share a block), 2 distance-1 colours (rows of a
+// colour may share Schur targets, which they then update atomically)
 void plan_level(LevelPlan& P, const std::vector<int>& n,
-                const std::vector<std::pair<int, int>>& close_pairs, bool coloring,
+                const std::vector<std::pair<int, int>>& close_pairs, int coloring,
                 const std::vector<int>& sys_off = {});
-void plan_structure(LevelPlan& P, int M, const std::vector<std::pair<int, int>>& close_pairs, bool coloring,
+void plan_structure(LevelPlan& P, int M, const std::vector<std::pair<int, int>>& close_pairs, int coloring,
                     const std::vector<int>& sys_off);
 void plan_layout(LevelPlan& P, const std::vector<int>& n);
 int find_pair_idx(const LevelPlan& P, int a, int b);
@@ -203,6 +207,9 @@ struct LevelDev {
                         // (k accepted, -k rejected for the exact SVD, 0 none)
   const int* epoch;     // epoch of the running apply
   unsigned long long wait_ns;  // a row's wait for its neighbours gives up after this long
+  int accumulate;       // 1: rows of a colour may share Schur targets (distance-1
+                        // colours): their updates of shared pairs and vector
+                        // entries are atomic
   void* pool;           // pair values (T)
   void* U;              // factor (T): U_i
   void* L;              //   L_hat_i^{-1} (m_i x m_i, lower)

@@ -119,6 +119,8 @@ struct GemmTask {
   int ta, tb, tcin, tc;
   float alpha, beta;
   int tile0;   // first tile of the task in its launch (set by the launcher)
+  int atomic;  // 1: C += alpha op(A) op(B) by atomic additions (Cin = C, beta = 1;
+               //    for products of several tasks into one C)
 };
 
 // grouped GEMM engines: CUDA cores (FP32 or FP64 by esize, big_rows.cu) and

@@ -160,10 +160,12 @@ Csr adjacency(int M, const std::vector<std::pair<int, int>>& pairs) {
   return A;
 }
 
-// greedy distance-2 colouring of blocks [b0, b1), visited in breadth-first
-// order: every component starts at its block of least degree (lowest index on
-// ties), neighbours are queued in ascending index
-void colour_range(const Csr& adj, int b0, int b1, std::vector<int>& colour) {
+// greedy colouring of blocks [b0, b1), visited in breadth-first order: every
+// component starts at its block of least degree (lowest index on ties),
+// neighbours are queued in ascending index; a block takes the smallest colour
+// not held within distance `dist` (2: no two blocks of a colour share a
+// neighbour; 1: only adjacent blocks differ)
+void colour_range(const Csr& adj, int b0, int b1, std::vector<int>& colour, int dist) {
   const int nb = b1 - b0;
   std::vector<int> roots(nb);
   std::iota(roots.begin(), roots.end(), b0);
@@ -178,13 +180,20 @@ void colour_range(const Csr& adj, int b0, int b1, std::vector<int>& colour) {
     queue.assign(1, root);
     for (size_t h = 0; h < queue.size(); ++h) {
       const int i = queue[h];
-      for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j)
-        for (const int* k = adj.row(*j); k != adj.row(*j) + adj.deg(*j); ++k)
-          if (*k != i && colour[*k] >= 0) {
-            const int c = colour[*k];
-            if (c >= static_cast<int>(mark.size())) mark.resize(c + 1, -1);
-            mark[c] = i;
-          }
+      auto take = [&](int k) {
+        if (k != i && colour[k] >= 0) {
+          const int c = colour[k];
+          if (c >= static_cast<int>(mark.size())) mark.resize(c + 1, -1);
+          mark[c] = i;
+        }
+      };
+      for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j) {
+        if (dist == 1) {
+          take(*j);
+          continue;
+        }
+        for (const int* k = adj.row(*j); k != adj.row(*j) + adj.deg(*j); ++k) take(*k);
+      }
       int c = 0;
       while (c < static_cast<int>(mark.size()) && mark[c] == i) ++c;
       colour[i] = c;
@@ -233,20 +242,22 @@ int64_t find_pair(const LevelPlan& P, int a, int b) {
   return p < 0 ? -1 : P.pair_off[p];
 }
 
-void plan_structure(LevelPlan& P, int M, const std::vector<std::pair<int, int>>& close_pairs, bool coloring,
+void plan_structure(LevelPlan& P, int M, const std::vector<std::pair<int, int>>& close_pairs, int coloring,
                     const std::vector<int>& sys_off) {
   P = LevelPlan();
   P.M = M;
   P.sys_off = sys_off;
+  P.coloring = coloring;
   const Csr adj = adjacency(M, close_pairs);
 
-  // ---- greedy distance-2 colouring, ascending block index ----------------
+  // ---- greedy colouring (distance 2, or 1 with shared Schur targets) ------
   P.colour.assign(M, -1);
   if (coloring) {
     std::vector<int> so = sys_off.empty() ? std::vector<int>{0, M} : sys_off;
     const int ns = static_cast<int>(so.size()) - 1;
+    const int dist = coloring == 2 ? 1 : 2;
     parallel_for(ns, 1, [&](int64_t b, int64_t e) {
-      for (int64_t s = b; s < e; ++s) colour_range(adj, so[s], so[s + 1], P.colour);
+      for (int64_t s = b; s < e; ++s) colour_range(adj, so[s], so[s + 1], P.colour, dist);
     });
   } else {
     // natural order: every block is its own step
@@ -479,7 +490,7 @@ void plan_layout(LevelPlan& P, const std::vector<int>& n) {
 }
 
 void plan_level(LevelPlan& P, const std::vector<int>& n,
-                const std::vector<std::pair<int, int>>& close_pairs, bool coloring,
+                const std::vector<std::pair<int, int>>& close_pairs, int coloring,
                 const std::vector<int>& sys_off) {
   plan_structure(P, static_cast<int>(n.size()), close_pairs, coloring, sys_off);
   plan_layout(P, n);

@@ -1232,10 +1232,16 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
       T* Xg = pool + L.schur_off[L.schur_ptr[i] + nt + p];
       const int ld = L.n[s_tgt[b]];
       const int tt = t - s_pt[p], tn = (wb + 7) >> 3;
+      const bool acc = L.accumulate != 0;
       warp_tile_tc(wa, wb, m, [&](int x, int k) { return static_cast<float>(Wa[k * wa + x]); },
                    [&](int k, int y) { return static_cast<float>(Wb[k * wb + y]); },
-                   [&](int x, int y, float v) { Xg[(int64_t)x * ld + y] -= static_cast<T>(v); }, (tt / tn) * 16,
-                   (tt % tn) * 8);
+                   [&](int x, int y, float v) {
+                     if (acc)
+                       atomicAdd(&Xg[(int64_t)x * ld + y], -static_cast<T>(v));
+                     else
+                       Xg[(int64_t)x * ld + y] -= static_cast<T>(v);
+                   },
+                   (tt / tn) * 16, (tt % tn) * 8);
     }
   } else if (m > 0) {
     int idx = L.schur_ptr[i] + nt;   // skip the row of the basis of i
@@ -1246,9 +1252,15 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
         const T* Wb = Wbase + (int64_t)n * s_colst[b];
         T* Xg = pool + L.schur_off[idx];
         const int ld = L.n[s_tgt[b]];
+        const bool acc = L.accumulate != 0;
         cta_mm<T, NT>(tc, wa, wb, m, [&](int x, int k) { return Wa[k * wa + x]; },
                     [&](int k, int y) { return Wb[k * wb + y]; },
-                    [&](int x, int y, T v) { Xg[(int64_t)x * ld + y] -= v; });
+                    [&](int x, int y, T v) {
+                      if (acc)
+                        atomicAdd(&Xg[(int64_t)x * ld + y], -v);
+                      else
+                        Xg[(int64_t)x * ld + y] -= v;
+                    });
       }
     }
   }

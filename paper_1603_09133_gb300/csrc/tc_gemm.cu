@@ -47,7 +47,7 @@ struct TcTask {
   int a_row, b_row;   // first row of the A / B panel in the hi plane
   int M, N, kb;       // output size, K blocks of 64
   int tile0;
-  int ldc, ldcin, tc, tcin;
+  int ldc, ldcin, tc, tcin, atomic;
   float alpha, beta;
   void* C;
   const void* Cin;
@@ -242,12 +242,14 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
           const int n = n0 + c0 + j;
           if (n < tk.N) {
             float o = tk.alpha * v[j];
-            if (tk.beta != 0.f)
-              o += tk.beta * (tk.tcin ? Cin[(int64_t)n * tk.ldcin + m] : Cin[(int64_t)m * tk.ldcin + n]);
-            if (tk.tc)
-              C[(int64_t)n * tk.ldc + m] = o;
-            else
-              C[(int64_t)m * tk.ldc + n] = o;
+            float* dst = tk.tc ? &C[(int64_t)n * tk.ldc + m] : &C[(int64_t)m * tk.ldc + n];
+            if (tk.atomic) {
+              atomicAdd(dst, o);
+            } else {
+              if (tk.beta != 0.f)
+                o += tk.beta * (tk.tcin ? Cin[(int64_t)n * tk.ldcin + m] : Cin[(int64_t)m * tk.ldcin + n]);
+              *dst = o;
+            }
           }
         }
       }
@@ -340,6 +342,7 @@ cudaError_t launch_gemm_tc(const std::vector<GemmTask>& tasks_in, int passes, in
     u.ldcin = t.ldcin;
     u.tc = t.tc;
     u.tcin = t.tcin;
+    u.atomic = t.atomic;
     u.alpha = t.alpha;
     u.beta = t.beta;
     u.C = t.C;
