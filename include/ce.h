@@ -77,10 +77,13 @@ typedef struct {
   int coloring;    /* elimination order within a level: 1 (default)
                       colour-major order of a distance-2 colouring (rows
                       of a colour touch disjoint block pairs); 2 of a
-                      distance-1 colouring (fewer colours; rows of a
-                      colour may share Schur targets, updated atomically,
-                      so sums of shared targets are order-dependent at the
-                      rounding level); 0 natural order                    */
+                      colouring whose colours hold adjacent blocks apart
+                      and let two blocks share a neighbour only if its
+                      colour is higher (no fill block between two rows of
+                      a colour; fewer colours; rows of a colour may share
+                      Schur targets, updated atomically, so sums of shared
+                      targets are order-dependent at the rounding level);
+                      0 natural order                                     */
   void* stream;    /* cudaStream_t for all device work                   */
   int rank_mode;   /* CE_RANK_SVD (default) / CE_RANK_LEARNED; on levels
                       run by the large-row path the learned form (FP32)
@@ -332,7 +335,8 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev,
 
 /*
  * pcg_solve -- preconditioned conjugate gradients in FP64 with M = Q^T L L^T Q
- * (replaces the paper's MINRES, Section 4; valid because M is SPD).
+ * (the paper's experiments use MINRES, Section 4, which minres_solve runs;
+ * CG is valid here because A and M are SPD).
  * x0 = 0; stops when ||r||_2 <= rtol ||b||_2 or after maxit iterations.
  *   b_dev, x_dev  device arrays of n doubles (original ordering)
  *   info          optional
@@ -343,6 +347,30 @@ ce_status ce_apply(const ce_factor* F, const double* r_dev, double* z_dev,
 ce_status pcg_solve(const ce_csb* A, const ce_factor* F, const double* b_dev,
                     double* x_dev, double rtol, int maxit, ce_pcg_info* info,
                     void* stream);
+
+/*
+ * minres_solve -- preconditioned MINRES in FP64 with M = Q^T L L^T Q, the
+ * Krylov method of the paper's experiments (Section 4): the Lanczos process
+ * preconditioned by M, the QR factorization of its tridiagonal matrix kept
+ * by Givens rotations, and the iterate updated along the directions w of
+ * Paige and Saunders (1975).  x0 = 0; stops when the preconditioned
+ * residual norm ||r||_{M^{-1}} (the recurrence's phibar) is <= rtol times
+ * ||b||_{M^{-1}}, when the Krylov space is exhausted, or after maxit
+ * iterations.  M must be SPD (a factor from ce_factorize is); A only
+ * symmetric.
+ *   b_dev, x_dev  device arrays of n doubles (original ordering)
+ *   info          optional: iterations, the final phibar / ||b||_{M^{-1}}
+ *                 (relres), converged
+ * One system per call: a batch handle is rejected with CE_ERR_INVALID_ARG.
+ * Allocates six work vectors (stream-ordered) and frees them on return;
+ * reads two dot products to the host per iteration.  Applies F, so it must
+ * not overlap other work on F (see ce_apply).  CE_ERR_NOT_SPD if a
+ * preconditioned inner product r^T M^{-1} r is negative or not finite;
+ * CE_ERR_NO_CONVERGENCE if maxit is reached (x_dev holds the last iterate).
+ */
+ce_status minres_solve(const ce_csb* A, const ce_factor* F, const double* b_dev,
+                       double* x_dev, double rtol, int maxit, ce_pcg_info* info,
+                       void* stream);
 
 /*
  * pcg_solve_batched -- pcg_solve for a batch from csb_build_batched: one CG
@@ -490,6 +518,18 @@ ce_status ce_factor_get_sigma(const ce_factor* F, int level, double* sigma);
 ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col,
                          const int32_t* perm, int32_t B, int32_t* colour,
                          int* ncolours, int64_t* npairs, int64_t* nclose);
+
+/*
+ * ce_plan_colours -- host-only (no CUDA call): level 1's elimination order
+ * as ce_factorize plans it for ce_opts.coloring (0 natural: block i is colour
+ * i; 1 distance 2; 2 the order whose colours separate adjacent blocks and
+ * blocks with a common neighbour of a lower colour, see ce_opts.coloring).
+ * Arguments as ce_plan_level1; colour (host, ceil(n/B) entries) and ncolours
+ * may be NULL.  CE_ERR_INVALID_ARG as ce_plan_level1 or for another coloring.
+ */
+ce_status ce_plan_colours(int64_t n, const int64_t* rowptr, const int32_t* col,
+                          const int32_t* perm, int32_t B, int coloring,
+                          int32_t* colour, int* ncolours);
 
 /*
  * ce_plan_level1_deps -- host-only (no CUDA call): the waits of level 1's

@@ -23,6 +23,9 @@ as the library steps:
 * ``multiply``       -- M x = Q^T L L^T Q x (Proposition CE_L), independent
                         of ``apply``.
 * ``pcg``            -- preconditioned conjugate gradients with M = Q^T L L^T Q.
+* ``minres``         -- preconditioned MINRES (the paper's Krylov method,
+                        Section 4) written as its defining minimisation over
+                        the Krylov space, not as the short recurrence.
 
 Pins (each function checked against something other than itself; the tests
 named are under tests/):
@@ -44,6 +47,11 @@ named are under tests/):
 * ``block_features``: against their definitions on the oracle's own steps
   (test_mlp_pins).
 * ``pcg``: its iterates equal SciPy's CG with the same preconditioner.
+* ``minres``: its iterates equal SciPy's MINRES with the same preconditioner
+  (and without one); the exact preconditioner C = A^{-1} converges in one
+  step; on a symmetric indefinite matrix with d distinct eigenvalues it
+  reaches A^{-1} b in d steps with a non-increasing residual
+  (test_oracle_pins).
 
 Readings of points the paper leaves open:
 
@@ -62,8 +70,10 @@ Readings of points the paper leaves open:
 * Elimination order inside a level: colour-major order of a greedy distance-2
   colouring of the level's block graph, the blocks visited breadth-first from a
   block of least degree (ascending block index inside a colour);
-  ``order='colour1'`` uses a distance-1 colouring in the same visit order
-  (fewer colours; rows of a colour may share Schur targets).  The paper's
+  ``order='colour1'`` uses a colouring that separates only adjacent blocks
+  and blocks with an earlier common neighbour, in the same visit order
+  (``distance1_colouring``: fewer colours; rows of a colour may share Schur
+  targets).  The paper's
   natural order (Algorithm 2) is ``order='natural'``; all are permutations P,
   which the paper leaves free (Section 2).
 * Super-blocks: runs of J consecutive blocks (Section 2.4); with ``nmax`` a run
@@ -178,20 +188,44 @@ def distance2_colouring(nbr):
 
 
 def distance1_colouring(nbr):
-    """Greedy distance-1 colouring in the same breadth-first order: block i
-    takes the smallest colour not held by an adjacent, already coloured block.
-    Blocks of one colour are not adjacent: the row of one never holds a block
-    of another, so neither row's compression or elimination reads what the
-    other writes; they may share close neighbours, whose pairs both rows'
-    Schur updates then add to (in any order: the sums commute)."""
+    """Greedy colouring for an elimination order whose colours hold adjacent
+    blocks apart but let blocks at distance 2 share a colour, in the same
+    breadth-first order as ``distance2_colouring``.
+
+    Two rows i, k of one colour must not touch a block that the other's
+    compression or elimination changes.  Adjacent rows would (each row holds
+    the other's block), and so would rows at distance 2 whose common
+    neighbour j ran before them: j's Schur update created the fill block
+    (i, k), which both rows would then compress.  Shared close targets are
+    harmless (both rows' Schur updates add to them, in either order).  So a
+    valid colouring has
+      (1) colour[i] != colour[k] for adjacent i, k;
+      (2) colour[j] > colour[i] for every block j with two neighbours i, k of
+          one colour (the fill between them comes after both ran).
+    Block x takes the smallest colour c that keeps (1) and (2) with the blocks
+    coloured so far: c is not held by a neighbour; c exceeds every colour held
+    by two of x's neighbours (x would be their earlier common neighbour); and c
+    is not held by another neighbour k of a neighbour j that holds a colour
+    below c (j would be the earlier common neighbour of x and k)."""
     M = len(nbr)
     colour = [-1] * M
-    for i in bfs_order(nbr):
-        seen = {colour[j] for j in nbr[i] if j != i and colour[j] >= 0}
-        c = 0
-        while c in seen:
+    for x in bfs_order(nbr):
+        held = [colour[j] for j in nbr[x] if j != x and colour[j] >= 0]
+        taken = set(held)
+        lowest = 0
+        for d in taken:
+            if held.count(d) >= 2:
+                lowest = max(lowest, d + 1)
+        for j in nbr[x]:
+            if j == x or colour[j] < 0:
+                continue
+            for k in nbr[j]:
+                if k != x and colour[k] > colour[j]:
+                    taken.add(colour[k])
+        c = lowest
+        while c in taken:
             c += 1
-        colour[i] = c
+        colour[x] = c
     return colour
 
 
@@ -692,4 +726,73 @@ def pcg(A, F, b, rtol=1e-8, maxit=1000, precond=None):
         rz_new = r @ z
         p = z + (rz_new / rz) * p
         rz = rz_new
+    return PCGResult(x, maxit, hist[-1], False, hist)
+
+
+def minres(A, F, b, rtol=1e-10, maxit=1000, precond=None):
+    """Preconditioned MINRES (Paige and Saunders, 1975), the Krylov method of
+    the paper's experiments (Section 4), written as its definition: with
+    C = M^{-1} (``apply(F, .)``, or ``precond``), the k-th iterate x_k is the
+    vector of the Krylov space K_k(C A, C b) whose residual b - A x has the
+    least C-norm ||r||_C = sqrt(r^T C r).  x0 = 0; stops when
+    ||b - A x_k||_C <= rtol ||b||_C (the residual computed afresh), or when
+    the Krylov space stops growing (then x_k is the solution).
+
+    Each step adds the next Krylov direction to a Euclidean-orthonormal basis
+    Q (Gram-Schmidt, done twice), orthonormalises P = A Q in the C-inner
+    product (P = Z R, Z^T C Z = I, Gram-Schmidt done twice), and solves the
+    least-squares problem in that basis: z = Z^T C b, y = R^{-1} z, x = Q y.
+    No short recurrence, so a slip in one would show against the library's.
+    """
+    A = sp.csr_matrix(A)
+    Cop = precond if precond is not None else (lambda v: apply(F, v))
+    b = np.asarray(b, dtype=np.float64)
+    n = b.size
+    x = np.zeros_like(b)
+    Cb = Cop(b)
+    bC = float(np.sqrt(b @ Cb))
+    hist = [1.0]
+    if bC == 0.0:
+        return PCGResult(x, 0, 0.0, True, hist)
+    Q, Z, CZ = [], [], []
+    R = np.zeros((0, 0))
+    v = Cb.copy()
+    for it in range(1, maxit + 1):
+        # next direction of K_k(C A, C b), orthogonal to the basis so far
+        v0 = np.linalg.norm(v)
+        for _ in range(2):
+            for q in Q:
+                v -= (q @ v) * q
+        nv = np.linalg.norm(v)
+        if nv <= 1e-14 * v0:           # the Krylov space is invariant
+            return PCGResult(x, it - 1, hist[-1], True, hist)
+        q = v / nv
+        Q.append(q)
+        p = A @ q
+        w = Cop(p)                     # C A q: also the next Krylov direction
+        v = w.copy()
+        # C-orthonormalise p against Z (R gains a column)
+        col = np.zeros(len(Z) + 1)
+        pz, wz = p.copy(), w.copy()
+        for _ in range(2):
+            for j in range(len(Z)):
+                c = CZ[j] @ pz
+                col[j] += c
+                pz -= c * Z[j]
+                wz -= c * CZ[j]
+        col[-1] = np.sqrt(pz @ wz)
+        Z.append(pz / col[-1])
+        CZ.append(wz / col[-1])
+        Rn = np.zeros((len(Z), len(Z)))
+        Rn[:-1, :-1] = R
+        Rn[:, -1] = col
+        R = Rn
+        z = np.array([cz @ b for cz in CZ])
+        y = sla.solve_triangular(R, z)
+        x = np.stack(Q, axis=1) @ y
+        r = b - A @ x
+        rel = float(np.sqrt(max(r @ Cop(r), 0.0))) / bC
+        hist.append(rel)
+        if rel <= rtol:
+            return PCGResult(x, it, rel, True, hist)
     return PCGResult(x, maxit, hist[-1], False, hist)

@@ -384,6 +384,19 @@ def pcg_solve(csb: CSB, F: Factor, b, x, rtol=1e-8, maxit=1000, stream=None, che
     return info.iters, info.relres, bool(info.converged)
 
 
+def minres_solve(csb: CSB, F: Factor, b, x, rtol=1e-10, maxit=1000, stream=None, check=True):
+    """FP64 preconditioned MINRES on the device (the Krylov method of the
+    paper's Section 4); returns (iters, relres, converged) with relres the
+    preconditioned residual norm over ||b||_{M^{-1}}."""
+    lib = _lib.load()
+    info = _lib.ce_pcg_info()
+    st = lib.minres_solve(csb.handle, F.handle, _dev_ptr(b, "b"), _dev_ptr(x, "x"), float(rtol),
+                          int(maxit), C.byref(info), _stream_ptr(stream))
+    if check and st not in (CE_OK, CE_ERR_NO_CONVERGENCE):
+        raise CEError(st, "minres_solve")
+    return info.iters, info.relres, bool(info.converged)
+
+
 def pcg_solve_batched(csb: CSB, F: Factor, b, x, rtol=1e-8, maxit=1000, stream=None, check=True):
     """Per-system FP64 PCG of a batch; returns (iters, relres, converged)
     as numpy arrays with one entry per system."""

@@ -95,6 +95,7 @@ SIGNATURES = {
     "csb_build": (C.c_int, [C.c_int64, I64P, I32P, DP, I32P, C.c_int32, PP]),
     "csb_build_batched": (C.c_int, [C.c_int, I64P, I64P, I32P, DP, I32P, I32P, PP]),
     "csb_update_values": (C.c_int, [P, DP, P]),
+    "ce_plan_colours": (C.c_int, [C.c_int64, I64P, I32P, I32P, C.c_int32, C.c_int, I32P, C.POINTER(C.c_int)]),
     "ce_plan_level1_deps": (C.c_int, [C.c_int64, I64P, I32P, I32P, C.c_int32, I64P, I32P, C.c_int64,
                                       I64P]),
     "ce_plan_next_level": (C.c_int, [C.c_int64, I64P, I32P, I32P, C.c_int32, I32P, C.c_int, C.c_int, I32P,
@@ -111,6 +112,7 @@ SIGNATURES = {
     "pcg_solve_batched": (C.c_int, [P, P, P, P, C.c_double, C.c_int, I32P, DP, I32P,
                                     C.POINTER(ce_pcg_info), P]),
     "pcg_solve_noalloc": (C.c_int, [P, P, P, P, C.c_double, C.c_int, C.POINTER(ce_pcg_info), P]),
+    "minres_solve": (C.c_int, [P, P, P, P, C.c_double, C.c_int, C.POINTER(ce_pcg_info), P]),
     "ce_csb_destroy": (None, [P]),
     "ce_factor_destroy": (None, [P]),
     "ce_strerror": (C.c_char_p, [C.c_int]),

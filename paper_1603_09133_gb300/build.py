@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcegpu.so")
-SOURCES = ["api.cu", "row_kernel.cu", "factor_kernels.cu", "apply_kernels.cu", "pcg_noalloc.cu", "pcg_batched.cu",
+SOURCES = ["api.cu", "row_kernel.cu", "factor_kernels.cu", "apply_kernels.cu", "pcg_noalloc.cu", "pcg_batched.cu", "minres.cu",
            "mlp.cu", "probes.cu", "big_rows.cu", "tc_gemm.cu", "plan.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

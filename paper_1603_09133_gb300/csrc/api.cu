@@ -918,7 +918,7 @@ namespace {
 // Level-1 symbolic plan of host CSR + permutation, no CUDA call (the host
 // introspection entry points below); may throw std::bad_alloc.
 ce_status plan1_host(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, int32_t B,
-                     LevelPlan& P) {
+                     LevelPlan& P, int coloring = 1) {
   if (n <= 0 || !rowptr || !col || !perm || B <= 0 || n > INT32_MAX || rowptr[0] != 0)
     return CE_ERR_INVALID_ARG;
   std::vector<int32_t> iperm(n, -1);
@@ -936,7 +936,7 @@ ce_status plan1_host(int64_t n, const int64_t* rowptr, const int32_t* col, const
   for (int b2 = 0; b2 <= M; ++b2) blkptr[b2] = std::min<int64_t>(n, (int64_t)b2 * B);
   for (int64_t r = 0; r < n; ++r) blk_of[r] = static_cast<int>(r / B);
   std::vector<std::pair<int, int>> pairs = block_pairs(rowptr, col, perm, iperm, blkptr, blk_of);
-  ce::plan_level(P, sizes, pairs, true);
+  ce::plan_level(P, sizes, pairs, coloring);
   return CE_OK;
 }
 
@@ -958,6 +958,21 @@ ce_status ce_plan_level1(int64_t n, const int64_t* rowptr, const int32_t* col, c
       for (char x : P.pair_close) c += x;
       *nclose = c;
     }
+  } catch (...) {
+    return status_of_exception();
+  }
+  return CE_OK;
+}
+
+ce_status ce_plan_colours(int64_t n, const int64_t* rowptr, const int32_t* col, const int32_t* perm, int32_t B,
+                          int coloring, int32_t* colour, int* ncolours) {
+  if (coloring < 0 || coloring > 2) return CE_ERR_INVALID_ARG;
+  try {
+    LevelPlan P;
+    const ce_status st = plan1_host(n, rowptr, col, perm, B, P, coloring);
+    if (st != CE_OK) return st;
+    if (colour) std::copy(P.colour.begin(), P.colour.end(), colour);
+    if (ncolours) *ncolours = P.ncolours;
   } catch (...) {
     return status_of_exception();
   }

@@ -163,8 +163,10 @@ Csr adjacency(int M, const std::vector<std::pair<int, int>>& pairs) {
 // greedy colouring of blocks [b0, b1), visited in breadth-first order: every
 // component starts at its block of least degree (lowest index on ties),
 // neighbours are queued in ascending index; a block takes the smallest colour
-// not held within distance `dist` (2: no two blocks of a colour share a
-// neighbour; 1: only adjacent blocks differ)
+// not held within distance `dist`.  dist 2: no two blocks of a colour share a
+// neighbour.  dist 1: adjacent blocks differ, and two blocks of a colour share
+// only neighbours of a higher colour (an earlier common neighbour would create
+// the fill block between them, which both rows would then compress).
 void colour_range(const Csr& adj, int b0, int b1, std::vector<int>& colour, int dist) {
   const int nb = b1 - b0;
   std::vector<int> roots(nb);
@@ -187,14 +189,29 @@ void colour_range(const Csr& adj, int b0, int b1, std::vector<int>& colour, int 
           mark[c] = i;
         }
       };
-      for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j) {
-        if (dist == 1) {
-          take(*j);
-          continue;
-        }
-        for (const int* k = adj.row(*j); k != adj.row(*j) + adj.deg(*j); ++k) take(*k);
-      }
       int c = 0;
+      if (dist == 1) {
+        // colours of the neighbours; a colour held by two of them must lie
+        // below i's (i would be their earlier common neighbour and create the
+        // fill block between them before they compress it)
+        for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j) {
+          if (*j == i || colour[*j] < 0) continue;
+          const int cj = colour[*j];
+          if (cj < static_cast<int>(mark.size()) && mark[cj] == i) c = std::max(c, cj + 1);
+          take(*j);
+        }
+        // a neighbour j coloured below i's colour is the earlier common
+        // neighbour of i and each other neighbour k of j: k's colour is out
+        // if it lies above j's
+        for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j) {
+          if (*j == i || colour[*j] < 0) continue;
+          for (const int* k = adj.row(*j); k != adj.row(*j) + adj.deg(*j); ++k)
+            if (colour[*k] > colour[*j]) take(*k);
+        }
+      } else {
+        for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j)
+          for (const int* k = adj.row(*j); k != adj.row(*j) + adj.deg(*j); ++k) take(*k);
+      }
       while (c < static_cast<int>(mark.size()) && mark[c] == i) ++c;
       colour[i] = c;
       for (const int* j = adj.row(i); j != adj.row(i) + adj.deg(i); ++j)

@@ -26,7 +26,7 @@ def lib():
 def _declared_functions():
     src = open(os.path.join(ROOT, "include", "ce.h")).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    names = set(re.findall(r"\b((?:ce|csb|pcg)_\w+)\s*\(", src))
+    names = set(re.findall(r"\b((?:ce|csb|pcg|minres)_\w+)\s*\(", src))
     return names
 
 
@@ -121,6 +121,33 @@ def test_host_colouring_matches_oracle(lib, name):
                 if a <= b:
                     sq.add((a, b))
     assert npairs == len(sq)
+
+
+@pytest.mark.parametrize("name", ["poisson2d_64_B16", "poisson2d_512_B32", "poisson3d_64_B64"])
+def test_host_colourings_match_oracle(lib, name):
+    """The three elimination orders of ce_opts.coloring as the planner makes
+    them: natural (block i is colour i), distance 2, and the distance-1 order
+    (adjacent blocks differ; neighbours of a block that share a colour lie
+    below it), each equal to the oracle's."""
+    w = wl.make_workload(name)
+    S, sizes = oce.initial_blocks(w.A, w.perm, w.B)
+    nbr = oce._block_graph(S, len(sizes))
+    A = w.A.tocsr()
+    rp = np.ascontiguousarray(A.indptr, np.int64)
+    ci = np.ascontiguousarray(A.indices, np.int32)
+    pm = np.ascontiguousarray(w.perm, np.int32)
+    want = {0: list(range(len(sizes))), 1: oce.distance2_colouring(nbr), 2: oce.distance1_colouring(nbr)}
+    for coloring, ocol in want.items():
+        col = np.zeros(len(sizes), np.int32)
+        nc = C.c_int()
+        st = lib.ce_plan_colours(A.shape[0], rp.ctypes.data_as(_lib.I64P), ci.ctypes.data_as(_lib.I32P),
+                                 pm.ctypes.data_as(_lib.I32P), w.B, coloring, col.ctypes.data_as(_lib.I32P),
+                                 C.byref(nc))
+        assert st == _lib.CE_OK
+        assert list(col) == list(ocol), coloring
+        assert nc.value == max(ocol) + 1
+    assert lib.ce_plan_colours(A.shape[0], rp.ctypes.data_as(_lib.I64P), ci.ctypes.data_as(_lib.I32P),
+                               pm.ctypes.data_as(_lib.I32P), w.B, 3, None, None) == _lib.CE_ERR_INVALID_ARG
 
 
 def test_host_plan_ragged_and_natural(lib):

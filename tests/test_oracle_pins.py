@@ -413,26 +413,70 @@ def test_capped_coarsening_stays_exact():
 def test_paper_experiment_iteration_trends():
     """Table num_it on the paper's own problem (Section 4: -div(k grad u) = 1 on
     [0, 1]^3, k = diag(x_d^2 + 0.5), N = 8192 and 16384 on 16x16x32 and
-    16x32x32 grids), with PCG to 1e-10 in place of MINRES.  B = 8 (2^3 boxes)
-    so that the table's CE(r), r = 4, is r = B/2; J = 8, 3 levels.  The paper's
-    trends: plain CG needs many more iterations and more as N grows; CE(1e-3)
-    needs a handful (4-6 there), flat in N; CE(4) needs more than CE(1e-3) and
-    grows mildly (23 -> 25 there)."""
-    its = {"cg": [], "eps": [], "r": []}
+    16x32x32 grids) with the paper's MINRES to 1e-10.  B = 8 (2^3 boxes) so
+    that the table's CE(r), r = 4, is r = B/2; J = 8, 3 levels.  The paper's
+    trends: MINRES without a preconditioner needs many more iterations and
+    more as N grows; CE(1e-3) needs a handful (4-6 there), flat in N; CE(4)
+    needs more than CE(1e-3) and grows mildly (23 -> 25 there)."""
+    its = {"none": [], "eps": [], "r": []}
     for shape in [(16, 16, 32), (16, 32, 32)]:
         A = wl.diffusion3d_tensor(*shape)
         perm = wl.box_perm(shape, (2, 2, 2))
         b = np.ones(A.shape[0])
-        its["cg"].append(ce.pcg(A, None, b, 1e-10, 5000, precond=lambda r: r).iters)
+        its["none"].append(ce.minres(A, None, b, 1e-10, 5000, precond=lambda r: r).iters)
         F = ce.factorize(A, perm, 8, 1e-3, 3, 8)
-        its["eps"].append(ce.pcg(A, F, b, 1e-10, 500).iters)
+        its["eps"].append(ce.minres(A, F, b, 1e-10, 500).iters)
         F = ce.factorize(A, perm, 8, 0.0, 3, 8, tol_mode="fixed", rank=4)
-        its["r"].append(ce.pcg(A, F, b, 1e-10, 500).iters)
-    cg, e, r = its["cg"], its["eps"], its["r"]
-    assert cg[1] > cg[0] > 5 * max(r), its
+        its["r"].append(ce.minres(A, F, b, 1e-10, 500).iters)
+    none, e, r = its["none"], its["eps"], its["r"]
+    assert none[1] > none[0] > 5 * max(r), its
     assert max(e) <= 6 and abs(e[1] - e[0]) <= 1, its
     assert all(r[j] > e[j] for j in range(2)), its
     assert r[0] <= r[1] <= 1.5 * r[0], its
+
+
+def test_minres_is_the_library_minres():
+    """The oracle's MINRES (the Krylov minimisation written out) against
+    SciPy's MINRES (the Paige-Saunders recurrence) with the same
+    preconditioner and without one: the same iterate after every step."""
+    import scipy.sparse.linalg as spla
+    w = wl.make_workload("poisson2d_64_B16")
+    F = ce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J)
+    N = w.A.shape[0]
+    Mop = spla.LinearOperator((N, N), matvec=lambda v: ce.apply(F, v))
+    cases = [(Mop, None, None, 4), (None, None, lambda r: r, 30)]
+    for M, Fc, pre, K in cases:
+        its = []
+        spla.minres(w.A, w.b, rtol=1e-15, maxiter=K, M=M, callback=lambda xk: its.append(xk.copy()))
+        assert len(its) >= min(K, 4)
+        for k in sorted({1, 2, len(its) // 2, len(its)}):
+            res = ce.minres(w.A, F if M is not None else Fc, w.b, 0.0, k, precond=pre)
+            assert np.linalg.norm(its[k - 1] - res.x) <= 1e-12 * np.linalg.norm(res.x), k
+
+
+def test_minres_special_cases():
+    """Closed forms: with the exact preconditioner C = A^{-1} MINRES ends in one
+    step at A^{-1} b; on a symmetric indefinite matrix with d distinct
+    eigenvalues (two of them negative) it reaches A^{-1} b in d steps, its
+    residual never growing; b = 0 returns x = 0 at once."""
+    rng = np.random.default_rng(11)
+    A = wl.poisson2d(12).toarray()
+    b = rng.standard_normal(144)
+    Ainv = np.linalg.inv(A)
+    res = ce.minres(sp.csr_matrix(A), None, b, 1e-12, 10, precond=lambda r: Ainv @ r)
+    assert res.converged and res.iters == 1
+    assert np.linalg.norm(res.x - np.linalg.solve(A, b)) <= 1e-12 * np.linalg.norm(res.x)
+    Qm, _ = np.linalg.qr(rng.standard_normal((60, 60)))
+    lam = np.repeat([-3.0, -0.5, 1.0, 2.5, 7.0], 12)
+    Ai = (Qm * lam) @ Qm.T
+    Ai = 0.5 * (Ai + Ai.T)
+    bi = rng.standard_normal(60)
+    res = ce.minres(sp.csr_matrix(Ai), None, bi, 1e-11, 50, precond=lambda r: r)
+    assert res.converged and res.iters <= 5
+    assert np.linalg.norm(res.x - np.linalg.solve(Ai, bi)) <= 1e-9 * np.linalg.norm(res.x)
+    assert all(h2 <= h1 * (1 + 1e-12) for h1, h2 in zip(res.history, res.history[1:]))
+    z = ce.minres(sp.csr_matrix(A), None, np.zeros(144), 1e-10, 10, precond=lambda r: r)
+    assert z.converged and z.iters == 0 and not np.any(z.x)
 
 
 def test_pcg_is_the_library_cg():
@@ -490,22 +534,74 @@ def test_dropped_block_is_the_truncated_svd_tail(kind):
     assert checked > 20
 
 
+def _fill_aware_valid(nbr, c):
+    """Rules of the distance-1 order, checked pair by pair: adjacent blocks
+    differ; two neighbours of a block j that share a colour lie below j."""
+    for j, nj in enumerate(nbr):
+        for a in nj:
+            if a == j:
+                continue
+            if c[a] == c[j]:
+                return False
+            for b in nj:
+                if b != j and b != a and c[a] == c[b] and c[j] < c[a]:
+                    return False
+    return True
+
+
 def test_distance1_colouring_is_valid_and_fewer():
-    """Distance-1 colours: adjacent blocks differ; on the 2D grids they need
-    fewer colours than distance 2 (2 instead of 5+ on the 4-neighbour box
-    pattern, 4 instead of 9+ on the 8-neighbour one)."""
+    """The distance-1 order's colouring keeps its two rules on the 2D and 3D
+    box patterns and on random graphs, and needs fewer colours than distance
+    2 on the grids (6 instead of 7 on the 4-neighbour 2D box pattern, 8
+    instead of 10 in 3D)."""
+    for name, want in [("poisson2d_64_B16", (6, 7)), ("poisson2d_512_B32", (6, 7))]:
+        w = wl.make_workload(name)
+        S, sizes = ce.initial_blocks(w.A, w.perm, w.B)
+        nbr = ce._block_graph(S, len(sizes))
+        c1 = ce.distance1_colouring(nbr)
+        c2 = ce.distance2_colouring(nbr)
+        assert _fill_aware_valid(nbr, c1)
+        assert (max(c1) + 1, max(c2) + 1) == want
+    A, perm, B = _problem("p3", 16, (4, 4, 4))
+    S, sizes = ce.initial_blocks(A, perm, B)
+    nbr = ce._block_graph(S, len(sizes))
+    c1 = ce.distance1_colouring(nbr)
+    assert _fill_aware_valid(nbr, c1)
+    assert max(c1) + 1 < max(ce.distance2_colouring(nbr)) + 1
+    rng = np.random.default_rng(4)
+    for trial in range(20):
+        M = 40
+        nbr = [{i} for i in range(M)]
+        for _ in range(int(rng.integers(20, 120))):
+            a, b = rng.integers(0, M, 2)
+            nbr[a].add(int(b))
+            nbr[b].add(int(a))
+        assert _fill_aware_valid(nbr, ce.distance1_colouring(nbr))
+    # the plain distance-1 rule (adjacent blocks differ) breaks rule 2 on the
+    # 2D grid: a row of the first colour would share fill with another
     w = wl.make_workload("poisson2d_64_B16")
     S, sizes = ce.initial_blocks(w.A, w.perm, w.B)
     nbr = ce._block_graph(S, len(sizes))
-    c1 = ce.distance1_colouring(nbr)
-    c2 = ce.distance2_colouring(nbr)
-    for i, ni in enumerate(nbr):
-        for j in ni:
-            if j != i:
-                assert c1[i] != c1[j]
-    assert max(c1) + 1 == 2 and max(c2) + 1 >= 5
-    F = ce.factorize(w.A, w.perm, w.B, w.tol, 2, 4, order="colour1")
-    assert max(F.levels[1].colour) + 1 <= 4 < max(ce.factorize(w.A, w.perm, w.B, w.tol, 2, 4).levels[1].colour) + 1
+    plain = [-1] * len(nbr)
+    for i in ce.bfs_order(nbr):
+        seen = {plain[j] for j in nbr[i] if j != i}
+        plain[i] = min(set(range(len(nbr) + 1)) - seen)
+    assert not _fill_aware_valid(nbr, plain)
+
+
+def test_distance1_order_is_free_inside_a_colour():
+    """Rows of one colour of the distance-1 order touch no common block but
+    shared Schur targets, whose updates add up: any order inside the colours
+    gives the same factor up to rounding (the GPU runs a colour's rows
+    concurrently)."""
+    w = wl.make_workload("poisson2d_64_B16")
+    F1 = ce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J, order="colour1")
+    F2 = ce.factorize(w.A, w.perm, w.B, w.tol, w.levels, w.J, order="colour1",
+                      shuffle_rng=np.random.default_rng(5))
+    assert F1.levels[0].order != F2.levels[0].order
+    assert [l.ranks for l in F1.levels] == [l.ranks for l in F2.levels]
+    x1, x2 = ce.apply(F1, w.b), ce.apply(F2, w.b)
+    assert np.linalg.norm(x1 - x2) / np.linalg.norm(x1) < 1e-12
 
 
 def test_distance1_order_gives_the_same_operator():
