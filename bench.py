@@ -309,7 +309,7 @@ def run_ours(args, rank, world):
     # row-kernel CTA shape (and learned or exact per level) chosen by
     # measurement for both forms (setup, untimed); in 3D a factorization
     # takes seconds, so the heuristic shapes are kept
-    tune_ms = tune_ms_plain = np.zeros((2, 3, pb.levels))
+    tune_ms = tune_ms_plain = np.zeros((2, 4, pb.levels))
     if not pb.is3d:
         tune_ms = ceg.ce_autotune(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=args.precision,
                                   rank_model=model, nmax=pb.nmax, coloring=args.coloring)
@@ -365,11 +365,20 @@ def run_ours(args, rank, world):
     # per level): algorithmic flops (counted from the actual sizes, ranks,
     # widths and sketch widths) over its CUDA-event time, against the measured
     # FP32 FFMA (FP64: DFMA) rate of this GPU
+    # (levels run by the large-row path are reported beside it)
     info = F.info
-    nl = info.levels_done
-    lms = sum(info.level_ms[l] for l in range(nl))
-    lfl = sum(info.level_flops[l] for l in range(nl))
-    lby = sum(info.level_bytes[l] for l in range(nl))
+    rk = [l for l in range(info.levels_done) if not info.big_rows[l]]
+    bg = [l for l in range(info.levels_done) if info.big_rows[l]]
+    nl = len(rk)
+    lms = sum(info.level_ms[l] for l in rk)
+    lfl = sum(info.level_flops[l] for l in rk)
+    lby = sum(info.level_bytes[l] for l in rk)
+    big_levels = None
+    if bg:
+        bms = sum(info.level_ms[l] for l in bg)
+        bfl = sum(info.level_flops[l] for l in bg)
+        big_levels = {"levels": bg, "ms_per_step": bms, "algorithmic_flops": bfl,
+                      "achieved_tflops": bfl / (bms * 1e-3) / 1e12 if bms > 0 else None}
     pk = "fp32_fma" if args.precision == "fp32" else "fp64_fma"
     peak = peaks[pk]
     achieved = lfl / (lms * 1e-3) / 1e12
@@ -384,7 +393,7 @@ def run_ours(args, rank, world):
                 "traffic_note": traffic["note"] if traffic else
                 "no ncu capture of this kernel source committed under profiles/",
                 "peak_note": f"of measured: ce_measure_peak {pk} on this GPU",
-                "measured_peaks_tflops": peaks}
+                "measured_peaks_tflops": peaks, "large_row_levels": big_levels}
 
     # end to end through the public API with host buffers: csb_build from the
     # host CSR (with the tuning measured above set on the new handle), the

@@ -98,7 +98,10 @@ typedef struct {
                       autotuned choice per level (ce_autotune), else a
                       heuristic; 0: 256 threads, 72 KB shared memory;
                       1: 512 threads, all shared memory; 2: 128 threads,
-                      40 KB                                              */
+                      40 KB; 3: the large-row path instead of the row
+                      kernel (per colour, batched kernels that spread
+                      each row over the whole GPU: fewer, wider launches
+                      pay off on levels with few rows per colour)       */
   int rank;        /* r of CE(r) (CE_TOL_FIXED only; >= 0, default 16)    */
   int nmax;        /* super-block cap: a run of J blocks whose sizes add up
                       to more than nmax rows is halved until its parts fit
@@ -297,7 +300,8 @@ ce_status ce_factorize_simple(int64_t n, const int64_t* rowptr,
  * threads (and the rounding of in-row reductions); the exact SVD instead of
  * the learned sketch on a level gives ranks at least as tight under the same
  * tolerance.
- *   level_ms  optional host array of 2 x 3 x 16 doubles:
+ * Shape 3 (the large-row path) is one of the candidates.
+ *   level_ms  optional host array of 2 x 4 x 16 doubles:
  *             [learned, exact][shape][level] times (ms)
  * Not part of the paper (launch configuration of this implementation).
  */
@@ -307,7 +311,7 @@ ce_status ce_autotune(ce_csb* A, const ce_opts* o, double* level_ms);
  * csb_get_tuning / csb_set_tuning -- the choices ce_autotune keeps in a csb
  * for one precision (CE_PREC_*) and rank mode (CE_RANK_*), host-only: the
  * number of tuned levels, and per level (16 entries each) the row kernel's CTA
- * shape (0..2) and whether the learned compression runs (1) or the exact SVD
+ * shape (0..3, see ce_opts.row_shape) and whether the learned compression runs (1) or the exact SVD
  * (0).  A tuning measured on one csb can be set on another csb of the same
  * matrix (e.g. one rebuilt from host arrays) so that it runs the same
  * schedule.  CE_ERR_INVALID_ARG on a bad precision, mode, count or value.

@@ -312,16 +312,17 @@ def _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, ove
 
 def ce_autotune(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",
                 coloring=True, stream=None, rank_model=None, oversample=8, seed=0, nmax=0):
-    """Time every row-kernel CTA shape per level (and, with a rank model,
-    learned compression against the exact SVD) and keep the fastest in the
-    csb; returns the [learned/exact][shape][level] times (ms) as a
-    2 x 3 x levels array (the exact half is zero without a rank model)."""
+    """Time every row-kernel CTA shape per level, and the large-row path as
+    shape 3 (and, with a rank model, learned compression against the exact
+    SVD), and keep the fastest in the csb; returns the
+    [learned/exact][shape][level] times (ms) as a 2 x 4 x levels array (the
+    exact half is zero without a rank model)."""
     lib = _lib.load()
     o = _opts(tol, levels, J, precision, tol_mode, coloring, stream, rank_model, oversample, seed, -1,
               nmax=nmax)
-    t = np.zeros(2 * 3 * 16, np.float64)
+    t = np.zeros(2 * 4 * 16, np.float64)
     _check(lib.ce_autotune(csb.handle, C.byref(o), t.ctypes.data_as(_lib.DP)), "ce_autotune")
-    return t.reshape(2, 3, 16)[:, :, :levels]
+    return t.reshape(2, 4, 16)[:, :, :levels]
 
 
 def ce_factorize(csb: CSB, tol=1e-4, levels=4, J=4, precision="fp64", tol_mode="rel",

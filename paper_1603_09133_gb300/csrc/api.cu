@@ -1058,7 +1058,7 @@ ce_status csb_set_tuning(ce_csb* A, int precision, int rank_mode, int levels, co
       (levels > 0 && (!shape || !learned)))
     return CE_ERR_INVALID_ARG;
   for (int l = 0; l < levels; ++l)
-    if (shape[l] < 0 || shape[l] > 2 || (learned[l] != 0 && learned[l] != 1)) return CE_ERR_INVALID_ARG;
+    if (shape[l] < 0 || shape[l] > 3 || (learned[l] != 0 && learned[l] != 1)) return CE_ERR_INVALID_ARG;
   for (int l = 0; l < 16; ++l) {
     A->tuned_shape[precision][rank_mode][l] = l < levels ? shape[l] : 0;
     A->tuned_learned[precision][rank_mode][l] = l < levels ? learned[l] : 0;
@@ -1086,7 +1086,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       (o.tol_mode == CE_TOL_FIXED && (o.rank < 0 || o.rank_mode != CE_RANK_SVD)) ||
       (o.rank_mode != CE_RANK_SVD && o.rank_mode != CE_RANK_LEARNED) ||
       (o.rank_mode == CE_RANK_LEARNED && (!o.rank_model || o.oversample < 0)) || o.row_shape < -1 ||
-      o.row_shape > 2 || o.nmax < 0 || o.gemm_engine < 0 || o.gemm_engine > 2 || o.coloring < 0 ||
+      o.row_shape > 3 || o.nmax < 0 || o.gemm_engine < 0 || o.gemm_engine > 2 || o.coloring < 0 ||
       o.coloring > 2)
     return CE_ERR_INVALID_ARG;
   // CE(r): the row kernel takes r in place of the tolerance
@@ -1136,8 +1136,9 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
     check(ce::launch_scatter_csr(es, A->d_scatter, A->d_val, A->nnz, pool, s), "scatter");
     int hstatus[ce::kStatusWords];
     for (int l = 0; l < o.levels && curp->M > 0; ++l) {
-      // levels whose rows outgrow the row kernel run the large-row path
-      const bool big = ce::level_needs_big_rows(*curp);
+      // levels whose rows outgrow the row kernel run the large-row path (and
+      // so does a level whose shape is 3, forced or autotuned)
+      bool big = ce::level_needs_big_rows(*curp);
       if (big && (curp->nmax > ce::kBigMaxN || max_targets(*curp) > ce::kBigMaxTargets)) {
         ret = CE_ERR_LIMIT;
         if (info) {
@@ -1152,7 +1153,6 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       F->levels.emplace_back();
       LevelStore& st = F->levels.back();
       st.plan = curp;
-      st.big = big;
       if (l == 0 && curp == A->plan1 && A->d_meta1)
         build_level_store(st, es, s, A->d_meta1, &A->meta1_off);
       else
@@ -1172,19 +1172,22 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
         shape = o.row_shape;
       else if (l < A->tuned_levels[tp][tr])
         shape = A->tuned_shape[tp][tr][l];
+      if (shape == 3) big = true;
+      st.big = big;
       if (info && l < 16) info->row_shape[l] = shape;
       // learned compression on this level unless the autotuner measured the
       // exact SVD faster here
       ce::LearnedArgs la_l = la;
       if (o.row_shape < 0 && l < A->tuned_levels[tp][tr] && !A->tuned_learned[tp][tr][l]) la_l.model = nullptr;
       // the large-row path runs its own randomized range finder (learned form)
-      if (info && l < 16) info->row_learned[l] = big ? (o.rank_mode == CE_RANK_LEARNED && es == 4) : la_l.model != nullptr;
+      const bool big_sketch = la_l.model != nullptr && es == 4;
+      if (info && l < 16) info->row_learned[l] = big ? big_sketch : la_l.model != nullptr;
       if (big) la_l.model = nullptr;
       if (info && l < 16) info->big_rows[l] = big ? 1 : 0;
       const int nbkt = static_cast<int>(P.bucket_nmax.size());
       if (big) {
         check(ce::run_big_level(es, st, l, o.tol, o.tol_mode, F->d_status, la.stats, o.gemm_engine,
-                                info ? info->big_ms : nullptr, o.rank_mode == CE_RANK_LEARNED, o.seed, s),
+                                info ? info->big_ms : nullptr, big_sketch, o.seed, s),
               "large rows");
       } else if (nbkt <= 1) {
         check(ce::launch_row_kernel(es, st.dev, P.M, l, o.tol, o.tol_mode, F->d_status, P.nmax, shape, la_l, s),
@@ -1432,9 +1435,9 @@ ce_status ce_autotune(ce_csb* A, const ce_opts* o_in, double* level_ms) {
   if ((o.precision != CE_PREC_FP64 && o.precision != CE_PREC_FP32) ||
       (o.rank_mode != CE_RANK_SVD && o.rank_mode != CE_RANK_LEARNED))
     return CE_ERR_INVALID_ARG;
-  // configurations: CTA shape x (learned compression on | exact SVD), the
-  // latter only when a rank model is given
-  constexpr int kShapes = 3, kReps = 3;
+  // configurations: CTA shape (3: the large-row path) x (learned compression
+  // on | exact SVD), the latter only when a rank model is given
+  constexpr int kShapes = 4, kReps = 3;
   const bool learned = o.rank_mode == CE_RANK_LEARNED;
   const int nmodes = learned ? 2 : 1;
   double t[2][kShapes][16];

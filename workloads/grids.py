@@ -253,6 +253,7 @@ WORKLOADS = {
     "poisson2d_64_B16": ("p2", (64, 64), (4, 4), 1e-3, 2, 4, 0),
     "poisson2d_256_B32": ("p2", (256, 256), (8, 4), 1e-4, 4, 4, 0),
     "poisson2d_512_B32": ("p2", (512, 512), (8, 4), 1e-4, 4, 4, 0),
+    "poisson3d_32_B64": ("p3", (32, 32, 32), (4, 4, 4), 1e-4, 4, 8, 0),
     "poisson3d_64_B64": ("p3", (64, 64, 64), (4, 4, 4), 1e-4, 4, 8, 0),
     "grf2d_1024_B32": ("grf", (1024, 1024), (8, 4), 1e-4, 4, 4, 100),
 }
