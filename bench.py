@@ -367,9 +367,10 @@ def run_ours(args, rank, world):
     # FP32 FFMA (FP64: DFMA) rate of this GPU
     # (levels run by the large-row path are reported beside it)
     info = F.info
-    rk = [l for l in range(info.levels_done) if not info.big_rows[l]]
-    bg = [l for l in range(info.levels_done) if info.big_rows[l]]
-    nl = len(rk)
+    nl = info.levels_done
+    rk = [l for l in range(nl) if not info.big_rows[l]]
+    bg = [l for l in range(nl) if info.big_rows[l]]
+    nrk = max(len(rk), 1)
     lms = sum(info.level_ms[l] for l in rk)
     lfl = sum(info.level_flops[l] for l in rk)
     lby = sum(info.level_bytes[l] for l in rk)
@@ -381,15 +382,15 @@ def run_ours(args, rank, world):
                       "achieved_tflops": bfl / (bms * 1e-3) / 1e12 if bms > 0 else None}
     pk = "fp32_fma" if args.precision == "fp32" else "fp64_fma"
     peak = peaks[pk]
-    achieved = lfl / (lms * 1e-3) / 1e12
+    achieved = lfl / (lms * 1e-3) / 1e12 if lms > 0 else 0.0
     kname = f"ce_row_kernel<{'float' if args.precision == 'fp32' else 'double'}>"
     traffic = committed_traffic(kname, args.workload, args.precision)
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
                 "traffic": traffic["bytes_per_launch"] if traffic else None,
-                "kernel": kname, "launches_per_step": nl,
-                "kernel_ms_per_step": lms, "algorithmic_flops_per_launch": lfl / nl,
-                "algorithmic_bytes_per_launch": lby / nl, "achieved_gbs": lby / (lms * 1e-3) / 1e9,
+                "kernel": kname, "launches_per_step": len(rk),
+                "kernel_ms_per_step": lms, "algorithmic_flops_per_launch": lfl / nrk,
+                "algorithmic_bytes_per_launch": lby / nrk, "achieved_gbs": lby / (lms * 1e-3) / 1e9 if lms > 0 else 0.0,
                 "traffic_note": traffic["note"] if traffic else
                 "no ncu capture of this kernel source committed under profiles/",
                 "peak_note": f"of measured: ce_measure_peak {pk} on this GPU",
@@ -435,6 +436,9 @@ def run_ours(args, rank, world):
                   "autotune_ms": np.round(tune_ms, 3).tolist(),
                   "autotune_ms_plain_fp64": np.round(tune_ms_plain, 3).tolist(),
                   "jacobi_capped": [info.jacobi_capped[l] for l in range(nl)],
+                  "row_phase_ms": {k: [round(info.row_phase_ms[l][p], 2) for l in range(nl)] for p, k in
+                                   enumerate(["wait", "setup", "learned", "R", "jacobi", "transform", "close",
+                                              "far", "schur"])},
                   "big_rows": [info.big_rows[l] for l in range(nl)],
                   "big_steps_ms": dict(zip(["gather", "sketch", "exact_svd", "UtDU", "chol_inv", "W_Y_far",
                                             "D_Wp", "kept_schur"], [round(v, 2) for v in info.big_ms])),

@@ -425,6 +425,7 @@ void build_level_store(LevelStore& st, int esize, cudaStream_t s, const void* sh
   D.feat = reinterpret_cast<float*>(b + o_feat);
   D.aq = nullptr;
   D.epoch = nullptr;
+  D.prof = nullptr;
   const size_t ub = P.u_elems * esize, lb = P.l_elems * esize, wb = P.w_elems * esize;
   st.fac_bytes = ub + lb + wb + 3 * 256;
   st.fac = dalloc(st.fac_bytes, s);
@@ -1110,8 +1111,13 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
   void* pool = nullptr;
   ce_status ret = CE_OK;
   try {
-    F->d_status = static_cast<int*>(dalloc((ce::kStatusWords + ce::kStatsWords) * sizeof(int), s));
-    check(cudaMemsetAsync(F->d_status, 0, (ce::kStatusWords + ce::kStatsWords) * sizeof(int), s), "memset");
+    // status words, counters, then the row-phase cycle sums (16 levels)
+    const size_t status_bytes = (ce::kStatusWords + ce::kStatsWords) * sizeof(int) +
+                                16 * ce::kProfSlots * sizeof(unsigned long long);
+    F->d_status = static_cast<int*>(dalloc(status_bytes, s));
+    check(cudaMemsetAsync(F->d_status, 0, status_bytes, s), "memset");
+    unsigned long long* d_prof =
+        reinterpret_cast<unsigned long long*>(F->d_status + ce::kStatusWords + ce::kStatsWords);
     ce::LearnedArgs la;
     if (o.rank_mode == CE_RANK_LEARNED) la.model = static_cast<const __half*>(o.rank_model);
     la.oversample = o.oversample;
@@ -1158,6 +1164,7 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       else
         build_level_store(st, es, s);
       st.dev.pool = pool;
+      st.dev.prof = d_prof;
       const double host_ms = ms_since(t_host);
       const LevelPlan& P = *st.plan;
       cudaEvent_t ev0, ev1;
@@ -1371,11 +1378,29 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       F->bytes = bytes;
       int lstat[ce::kStatsWords];
       check(cudaMemcpy(lstat, F->d_status + ce::kStatusWords, sizeof(lstat), cudaMemcpyDeviceToHost), "D2H");
+      unsigned long long prof[16 * ce::kProfSlots];
+      check(cudaMemcpy(prof, d_prof, sizeof(prof), cudaMemcpyDeviceToHost), "D2H");
       if (info) {
+        int dev = 0, khz = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) !=
+                                                      cudaSuccess || khz <= 0)
+          khz = 1;
+        for (int l = 0; l < 16; ++l) {
+          const unsigned long long* pl = prof + l * ce::kProfSlots;
+          for (int p = 0; p < ce::kRowPhases; ++p) info->row_phase_ms[l][p] = static_cast<double>(pl[p]) / khz;
+          for (int k = 0; k < 2; ++k) {
+            const unsigned long long sw = pl[ce::kRowPhases + 2 * k], rows = pl[ce::kRowPhases + 2 * k + 1];
+            info->jacobi_sweeps[l][k] = rows ? static_cast<double>(sw) / rows : 0.0;
+          }
+        }
         for (int l = 0; l < 16; ++l) {
           info->learned_rows[l] = lstat[2 * l];
           info->fallback_rows[l] = lstat[2 * l + 1];
           info->jacobi_capped[l] = lstat[32 + l];
+          if (l < (int)F->levels.size() && F->levels[l].big) {
+            info->jacobi_sweeps[l][0] = lstat[64 + l] ? static_cast<double>(lstat[48 + l]) / lstat[64 + l] : 0.0;
+            info->jacobi_sweeps[l][1] = 0.0;
+          }
         }
         info->levels_done = (int)F->levels.size();
         info->coarse_n = F->nc;

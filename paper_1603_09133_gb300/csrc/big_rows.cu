@@ -17,6 +17,7 @@
 // The factor keeps the row kernel's layout (U_i, L_hat_i^{-1}, W_i), so the
 // reassembly and the level vectors are shared; the apply of such a level runs
 // one launch per colour (apply_big_kernel).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -31,6 +32,8 @@
 namespace ce {
 
 namespace {
+
+namespace cg = cooperative_groups;
 
 template <typename T>
 struct EpsB;
@@ -403,7 +406,8 @@ struct BigLevelArgs {
 
 template <typename T>
 __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(const BigRowDev* rows, T* ws, LevelDev L,
-                                                             BigLevelArgs a, int xv_smem, SketchRes* res) {
+                                                             BigLevelArgs a, int xv_smem, SketchRes* res,
+                                                             int presolved) {
   const BigRowDev rw = rows[blockIdx.x];
   const int n = rw.n, i = rw.i;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -440,19 +444,22 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(const BigRowDev* ro
     return;
   }
   // columns of R contiguous; in shared memory when both n x n matrices fit
+  // (presolved: block_jacobi_kernel already rotated X and V in the workspace)
   T* X = xv_smem ? reinterpret_cast<T*>(pos + ((n + 3) & ~3)) : ws + rw.t_off;
   T* V = xv_smem ? X + (int64_t)n * n : ws + rw.v_off;
   const T* R = ws + rw.x_off;
-  for (int64_t e = tid; e < (int64_t)n * n; e += kJacThreads) {
-    const int c = static_cast<int>(e / n), row = static_cast<int>(e % n);
-    X[e] = R[(int64_t)row * n + c];
-    V[e] = (c == row) ? T(1) : T(0);
-  }
+  if (!presolved)
+    for (int64_t e = tid; e < (int64_t)n * n; e += kJacThreads) {
+      const int c = static_cast<int>(e / n), row = static_cast<int>(e % n);
+      X[e] = R[(int64_t)row * n + c];
+      V[e] = (c == row) ? T(1) : T(0);
+    }
   __syncthreads();
   const int nb = n + (n & 1), npairs = nb / 2;
   const T tolJ = T(n) * EpsB<T>::v, tolJ2 = tolJ * tolJ;
-  bool conv = false;
-  for (int sweep = 0; sweep < kBigMaxSweeps; ++sweep) {
+  bool conv = presolved != 0;
+  int nsw = kBigMaxSweeps;
+  for (int sweep = 0; sweep < kBigMaxSweeps && !presolved; ++sweep) {
     // pairs whose columns both stay below tau_est / (2 sqrt n) are skipped
     // (their rotation changes neither the kept subspace nor the rank)
     T cm = T(0);
@@ -529,11 +536,17 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(const BigRowDev* ro
     const int rotated = s_flag;
     __syncthreads();
     if (!rotated) {
+      nsw = sweep + 1;
       conv = true;
       break;
     }
   }
   if (!conv && tid == 0 && a.stats && a.level < 16) atomicAdd(a.stats + 32 + a.level, 1);
+  if (!presolved && tid == 0 && a.stats && a.level < 16) {
+    atomicAdd(a.stats + 48 + a.level, nsw);
+    atomicAdd(a.stats + 64 + a.level, 1);
+  }
+  __syncthreads();
   for (int j = warp; j < n; j += kW) {
     T s = T(0);
     for (int row = lane; row < n; row += 32) s += X[(int64_t)j * n + row] * X[(int64_t)j * n + row];
@@ -599,6 +612,225 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(const BigRowDev* ro
       }
     }
   }
+}
+
+// ---------------------------------------------------------------------------
+// Block one-sided Jacobi for rows whose R and V (n x n each) do not fit in
+// one CTA's shared memory.  The n columns form blocks of B; each round of a
+// round-robin tournament over the blocks pairs them up, and one CTA takes a
+// pair of blocks: it stages their 2B columns of X (= R at the start) and of
+// V in shared memory, runs one cyclic sweep of column rotations over them (a
+// warp per column pair, the same pair test and rotation as jacobi_kernel),
+// and writes them back.  All block pairs of a round, of every row of the
+// colour, run at once; grid barriers (cooperative launch) separate the
+// rounds.  A row has converged when one sweep over all its block pairs
+// rotated nothing, the stopping rule of the one-CTA kernel; jacobi_kernel
+// then reads sigma, the order, U and the rank from the rotated X and V.
+// Columns move between CTAs from round to round, so they are read past L1.
+// ---------------------------------------------------------------------------
+struct BJRow {
+  int sweeps;                // sweeps run (until converged or capped)
+  double dn2;                // ||D_i||_F^2 (rounding floor of tau)
+  unsigned long long cm;     // largest column norm^2 at the sweep's start (double bits)
+  unsigned long long cmn;    // ... gathered during the sweep's last round
+  int flag;                  // a rotation in this sweep
+  int conv;                  // converged
+};
+
+template <typename T, int B>
+__global__ void __launch_bounds__(32 * B) block_jacobi_kernel(const BigRowDev* rows, int nrows,
+                                                              const int* item_ptr, int max_rounds, T* ws,
+                                                              LevelDev L, BigLevelArgs a, BJRow* st) {
+  constexpr int NT = 32 * B;
+  cg::grid_group grid = cg::this_grid();
+  extern __shared__ __align__(16) unsigned char bj_smem[];
+  __shared__ double s_red[2][B];
+  __shared__ int s_rot;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  // X = R (column-major), V = I, ||D_i||_F^2 and the largest column norm
+  for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
+    const BigRowDev rw = rows[r];
+    const int n = rw.n;
+    T* X = ws + rw.t_off;
+    T* V = ws + rw.v_off;
+    const T* R = ws + rw.x_off;
+    const T* D = reinterpret_cast<const T*>(L.pool) + L.diag_off[rw.i];
+    double ss = 0.0;
+    for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
+      const int c = static_cast<int>(e / n), row = static_cast<int>(e % n);
+      X[e] = R[(int64_t)row * n + c];
+      V[e] = (c == row) ? T(1) : T(0);
+      const double d = static_cast<double>(D[e]);
+      ss += d * d;
+    }
+    __syncthreads();
+    double cm = 0.0;
+    for (int c = warp; c < n; c += B) {
+      T sc = T(0);
+      for (int row = lane; row < n; row += 32) sc += X[(int64_t)c * n + row] * X[(int64_t)c * n + row];
+      cm = fmax(cm, static_cast<double>(wsum(sc)));
+    }
+    ss = wsum(ss);
+    if (lane == 0) {
+      s_red[0][warp] = ss;
+      s_red[1][warp] = cm;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double t0 = 0.0, t1 = 0.0;
+      for (int w = 0; w < B; ++w) {
+        t0 += s_red[0][w];
+        t1 = fmax(t1, s_red[1][w]);
+      }
+      st[r].dn2 = t0;
+      st[r].cm = static_cast<unsigned long long>(__double_as_longlong(t1));
+      st[r].cmn = 0ull;
+      st[r].flag = 0;
+      st[r].conv = 0;
+      st[r].sweeps = 0;
+    }
+    __syncthreads();
+  }
+  grid.sync();
+  const int nitems = item_ptr[nrows];
+  T* Xs = reinterpret_cast<T*>(bj_smem);
+  bool all_conv = false;
+  for (int sweep = 0; sweep < kBigMaxSweeps && !all_conv; ++sweep) {
+    for (int rnd = 0; rnd < max_rounds; ++rnd) {
+      for (int it = blockIdx.x; it < nitems; it += gridDim.x) {
+        int lo = 0, hi = nrows - 1;  // the row whose items hold it
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (item_ptr[mid] <= it) lo = mid; else hi = mid - 1;
+        }
+        const int r = lo, t = it - item_ptr[r];
+        const BigRowDev rw = rows[r];
+        const int n = rw.n;
+        const int nbk = (n + B - 1) / B, nbp = nbk + (nbk & 1);
+        if (__ldcg(&st[r].conv) || rnd >= nbp - 1) continue;   // CTA-uniform
+        int I = nbp - 1, J = rnd;
+        if (t != 0) {
+          I = rnd + t;
+          if (I >= nbp - 1) I -= nbp - 1;
+          J = rnd - t;
+          if (J < 0) J += nbp - 1;
+        }
+        // a block paired with the empty block (odd block count, or a single
+        // block) sweeps over its own columns alone
+        const bool vi = I < nbk, vj = J < nbk;
+        if (!vi && !vj) continue;
+        const int c0 = (vi ? I : J) * B, w0 = min(B, n - c0);
+        const int c1 = (vi && vj) ? J * B : 0, w1 = (vi && vj) ? min(B, n - c1) : 0;
+        const int nc = w0 + w1;
+        T* Vs = Xs + (int64_t)2 * B * n;
+        T* X = ws + rw.t_off;
+        T* V = ws + rw.v_off;
+        for (int64_t e = tid; e < (int64_t)nc * n; e += NT) {
+          const int c = static_cast<int>(e / n), row = static_cast<int>(e % n);
+          const int64_t g = (int64_t)(c < w0 ? c0 + c : c1 + c - w0) * n + row;
+          Xs[e] = __ldcg(X + g);
+          Vs[e] = __ldcg(V + g);
+        }
+        // pair-skipping threshold of the sweep (see jacobi_kernel)
+        const double dn2 = __ldcg(&st[r].dn2);
+        const double cmv = __longlong_as_double(static_cast<long long>(__ldcg(&st[r].cm)));
+        const T sm = static_cast<T>(sqrt(cmv));
+        T test = (a.tol == 0.0 || a.tol_mode == CE_TOL_FIXED) ? T(n) * EpsB<T>::v * sm
+                                                              : ((a.tol_mode == CE_TOL_ABS) ? T(a.tol) : T(a.tol) * sm);
+        test = fmax(test, static_cast<T>(static_cast<double>(EpsB<T>::v) * sqrt(dn2))) * T(0.5) / sqrt(T(n));
+        const T skip2 = test * test;
+        const T tolJ = T(n) * EpsB<T>::v, tolJ2 = tolJ * tolJ;
+        if (tid == 0) s_rot = 0;
+        __syncthreads();
+        const int ncb = nc + (nc & 1), np = ncb / 2;
+        for (int ir = 0; ir < ncb - 1; ++ir) {
+          if (warp < np) {
+            int p = ncb - 1, q = ir;
+            if (warp != 0) {
+              p = ir + warp;
+              if (p >= ncb - 1) p -= ncb - 1;
+              q = ir - warp;
+              if (q < 0) q += ncb - 1;
+            }
+            if (p < nc && q < nc) {
+              T* xp = Xs + (int64_t)p * n;
+              T* xq = Xs + (int64_t)q * n;
+              T al = 0, be = 0, ga = 0;
+              for (int row = lane; row < n; row += 32) {
+                const T u = xp[row], v = xq[row];
+                al += u * u;
+                be += v * v;
+                ga += u * v;
+              }
+              al = wsum(al);
+              be = wsum(be);
+              ga = wsum(ga);
+              if (ga != T(0) && (al >= skip2 || be >= skip2) && ga * ga > tolJ2 * al * be) {
+                const T zeta = (be - al) / (T(2) * ga);
+                const T az = fabs(zeta);
+                const T den = (az > T(1)) ? az * (T(1) + sqrt(T(1) + T(1) / (az * az))) : az + sqrt(T(1) + az * az);
+                const T tt = ((zeta >= T(0)) ? T(1) : T(-1)) / den;
+                const T cs = T(1) / sqrt(T(1) + tt * tt), sn = cs * tt;
+                T* vp = Vs + (int64_t)p * n;
+                T* vq = Vs + (int64_t)q * n;
+                for (int row = lane; row < n; row += 32) {
+                  const T u = xp[row], v = xq[row];
+                  xp[row] = cs * u - sn * v;
+                  xq[row] = sn * u + cs * v;
+                  const T u2 = vp[row], v2 = vq[row];
+                  vp[row] = cs * u2 - sn * v2;
+                  vq[row] = sn * u2 + cs * v2;
+                }
+                if (lane == 0) s_rot = 1;
+              }
+            }
+          }
+          __syncthreads();
+        }
+        for (int64_t e = tid; e < (int64_t)nc * n; e += NT) {
+          const int c = static_cast<int>(e / n), row = static_cast<int>(e % n);
+          const int64_t g = (int64_t)(c < w0 ? c0 + c : c1 + c - w0) * n + row;
+          __stcg(X + g, Xs[e]);
+          __stcg(V + g, Vs[e]);
+        }
+        if (rnd == nbp - 2) {   // the sweep's last round: column norms for the next sweep
+          double cm = 0.0;
+          for (int c = warp; c < nc; c += B) {
+            T sc = T(0);
+            for (int row = lane; row < n; row += 32) sc += Xs[(int64_t)c * n + row] * Xs[(int64_t)c * n + row];
+            cm = fmax(cm, static_cast<double>(wsum(sc)));
+          }
+          if (lane == 0) atomicMax(&st[r].cmn, static_cast<unsigned long long>(__double_as_longlong(cm)));
+        }
+        if (tid == 0 && s_rot) atomicOr(&st[r].flag, 1);
+        __syncthreads();
+      }
+      grid.sync();
+    }
+    // end of the sweep: a row without a rotation has converged
+    if (blockIdx.x == 0)
+      for (int r = tid; r < nrows; r += NT)
+        if (!st[r].conv) {
+          st[r].sweeps = sweep + 1;
+          if (__ldcg(&st[r].flag) == 0) {
+            st[r].conv = 1;
+          } else {
+            st[r].flag = 0;
+            st[r].cm = __ldcg(&st[r].cmn);
+            st[r].cmn = 0ull;
+          }
+        }
+    grid.sync();
+    int left = 0;
+    for (int r = tid; r < nrows; r += NT) left |= __ldcg(&st[r].conv) == 0;
+    all_conv = __syncthreads_or(left) == 0;
+  }
+  if (blockIdx.x == 0 && a.stats && a.level < 16)
+    for (int r = tid; r < nrows; r += NT) {
+      if (!__ldcg(&st[r].conv)) atomicAdd(a.stats + 32 + a.level, 1);
+      atomicAdd(a.stats + 48 + a.level, st[r].sweeps);
+      atomicAdd(a.stats + 64 + a.level, 1);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1132,6 +1364,75 @@ PairView pair_view(const LevelPlan& P, int a, int b) {
   return {off, P.n[a], 1};
 }
 
+// Block Jacobi of the rows `rv` (device copy `drv`) in the workspace `wsb`:
+// the widest column block B in {32, 16, 8, 4} whose 2B columns of X and V
+// fit in shared memory, one cooperative launch (a resident wave of CTAs).
+template <typename T, int B>
+void launch_block_jacobi_b(const std::vector<BigRowDev>& rv, const BigRowDev* drv, T* wsb, const LevelDev& D,
+                           const BigLevelArgs& args, size_t smem, cudaStream_t s) {
+  static size_t attr = 0;
+  if (attr < smem) {
+    bcheck(cudaFuncSetAttribute(block_jacobi_kernel<T, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    attr = smem;
+  }
+  const int nr = static_cast<int>(rv.size());
+  std::vector<int> ptr(nr + 1, 0);
+  int max_rounds = 1;
+  for (int q = 0; q < nr; ++q) {
+    const int nbk = (rv[q].n + B - 1) / B, nbp = nbk + (nbk & 1);
+    ptr[q + 1] = ptr[q] + nbp / 2;
+    max_rounds = std::max(max_rounds, nbp - 1);
+  }
+  void* buf = nullptr;
+  const size_t pb = (nr + 1) * sizeof(int), sb = nr * sizeof(BJRow);
+  bcheck(cudaMallocAsync(&buf, sb + pb, s));
+  BJRow* dst = static_cast<BJRow*>(buf);
+  int* dptr = reinterpret_cast<int*>(static_cast<char*>(buf) + sb);
+  bcheck(cudaMemcpyAsync(dptr, ptr.data(), pb, cudaMemcpyHostToDevice, s));
+  int dev = 0, per_sm = 0;
+  bcheck(cudaGetDevice(&dev));
+  bcheck(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, block_jacobi_kernel<T, B>, 32 * B, smem));
+  if (per_sm < 1) throw BigFail{cudaErrorInvalidConfiguration};
+  const int grid = std::max(1, std::min(std::max(ptr[nr], nr), per_sm * device_sms()));
+  int nrr = nr;
+  LevelDev Dv = D;
+  BigLevelArgs av = args;
+  void* kargs[] = {(void*)&drv, (void*)&nrr, (void*)&dptr, (void*)&max_rounds, (void*)&wsb,
+                   (void*)&Dv, (void*)&av, (void*)&dst};
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  bcheck(cudaLaunchCooperativeKernel((const void*)block_jacobi_kernel<T, B>, dim3(grid), dim3(32 * B), kargs,
+                                     smem, s));
+  bcheck(cudaFreeAsync(buf, s));
+}
+
+// Column blocks of 8 by default: a colour holds few large rows, and small
+// blocks give each row many block pairs (CTAs) per round; wider blocks
+// (fewer rounds, fewer grid barriers) once the pairs of B = 8 would fill two
+// waves of the GPU; narrower ones when 8 columns of X and V do not fit.
+template <typename T>
+void launch_block_jacobi(const std::vector<BigRowDev>& rv, const BigRowDev* drv, T* wsb, const LevelDev& D,
+                         const BigLevelArgs& args, size_t smem_limit, cudaStream_t s) {
+  int nmx = 1;
+  for (const BigRowDev& r : rv) nmx = std::max(nmx, r.n);
+  auto need = [&](int b) { return (size_t)4 * b * nmx * sizeof(T) + 256; };
+  auto items = [&](int b) {
+    int64_t t = 0;
+    for (const BigRowDev& r : rv) {
+      const int nbk = (r.n + b - 1) / b;
+      t += (nbk + (nbk & 1)) / 2;
+    }
+    return t;
+  };
+  const int64_t wave = 2LL * device_sms();
+  if (items(16) >= wave && need(32) <= smem_limit)
+    return launch_block_jacobi_b<T, 32>(rv, drv, wsb, D, args, need(32), s);
+  if (items(8) >= wave && need(16) <= smem_limit)
+    return launch_block_jacobi_b<T, 16>(rv, drv, wsb, D, args, need(16), s);
+  if (need(8) <= smem_limit) return launch_block_jacobi_b<T, 8>(rv, drv, wsb, D, args, need(8), s);
+  if (need(4) <= smem_limit) return launch_block_jacobi_b<T, 4>(rv, drv, wsb, D, args, need(4), s);
+  throw BigFail{cudaErrorInvalidValue};
+}
+
 template <typename T>
 void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, std::vector<int>& rank_h) {
   const LevelPlan& P = *st.plan;
@@ -1296,8 +1597,9 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
     const size_t sxv = sj + (size_t)2 * kmx * kmx * es;
     const int xv = sxv <= jac_dyn ? 1 : 0;
     if (xv) sj = sxv;
+    if (!xv) launch_block_jacobi<T>(view, dview, ws2, D, args, jac_dyn, s);
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    jacobi_kernel<T><<<ns, kJacThreads, sj, s>>>(dview, ws2, D, args, xv, dres);
+    jacobi_kernel<T><<<ns, kJacThreads, sj, s>>>(dview, ws2, D, args, xv, dres, xv ? 0 : 1);
     bcheck(cudaGetLastError());
     g_launches.fetch_add(1, std::memory_order_relaxed);
     sketch_accept_kernel<T><<<ns, 128, 0, s>>>(dsk, ws2, dres, D, args.stats, args.level);
@@ -1480,8 +1782,11 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
         const size_t sxv = sj + (size_t)2 * nmx * nmx * es;
         const int xv = sxv <= jac_dyn ? 1 : 0;
         if (xv) sj = sxv;
+        // rows whose X and V do not fit in shared memory: block Jacobi over
+        // many CTAs first, then jacobi_kernel only reads the result
+        if (!xv) launch_block_jacobi<T>(ex, dex, ws, D, args, jac_dyn, s);
         g_launches.fetch_add(1, std::memory_order_relaxed);
-        jacobi_kernel<T><<<ne, kJacThreads, sj, s>>>(dex, ws, D, args, xv, nullptr);
+        jacobi_kernel<T><<<ne, kJacThreads, sj, s>>>(dex, ws, D, args, xv, nullptr, xv ? 0 : 1);
         bcheck(cudaGetLastError());
         bcheck(cudaFreeAsync(dex, s));
       }

@@ -210,6 +210,8 @@ struct LevelDev {
   int accumulate;       // 1: rows of a colour may share Schur targets (distance-1
                         // colours): their updates of shared pairs and vector
                         // entries are atomic
+  unsigned long long* prof;  // SM cycles per (level, row phase), summed over
+                             // rows (ce_row_kernel; null: not recorded)
   void* pool;           // pair values (T)
   void* U;              // factor (T): U_i
   void* L;              //   L_hat_i^{-1} (m_i x m_i, lower)

@@ -36,6 +36,14 @@ inline int device_sms() {
 // [6..7] = pivot value (double bits)
 constexpr int kStatusWords = 8;
 
+// row phases timed by ce_row_kernel per level (ce_info.row_phase_ms): wait
+// for the neighbourhood, setup, learned sketch, R of F^T, Jacobi SVD,
+// transform + Cholesky + L_hat^{-1}, close rows, far rows, Schur updates
+constexpr int kRowPhases = 9;
+// per level: the kRowPhases cycle sums, then Jacobi sweeps summed over rows
+// and rows that ran a Jacobi SVD (exact SVD; learned sketch's k x k factor)
+constexpr int kProfSlots = kRowPhases + 4;
+
 // learned compression (randomized range finder with an MLP-predicted width)
 struct LearnedArgs {
   const __half* model = nullptr;  // FP16 rank model; null: exact SVD for every row
@@ -50,8 +58,9 @@ struct LearnedArgs {
 // per-level counters of a factorization (levels 0..15): [2 l] rows whose
 // sketch was accepted, [2 l + 1] rows sent to the exact SVD, [32 + l] rows
 // whose Jacobi iteration reached its sweep cap before every pair was
-// orthogonal (their singular values are still used)
-constexpr int kStatsWords = 48;
+// orthogonal (their singular values are still used); large-row levels:
+// [48 + l] Jacobi sweeps summed over rows, [64 + l] rows that ran one
+constexpr int kStatsWords = 80;
 
 // All `count` rows of a level (order[0, count)) in one persistent launch;
 // shape 0: 256-thread CTAs with a 72 KB budget, 1: 512-thread CTAs with the

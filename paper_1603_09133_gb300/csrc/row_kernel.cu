@@ -368,7 +368,8 @@ __device__ void store_row_tile(const T* sm, T* X, int i, int k, int n, int nk, i
 // One block row i of the level (Algorithm 2 for one i), by the whole CTA.
 template <typename T, int NT>
 __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int level, double tol, int tol_mode,
-                                          int* status, int nmax, int LD, int QW, const LearnedArgs& la) {
+                                          int* status, int nmax, int LD, int QW, const LearnedArgs& la,
+                                          long long& t_row) {
   constexpr int kWarpsNT = NT / 32;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int NL = nmax * LD;
@@ -401,6 +402,14 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
   const int n = L.n[i];
   const int ci = L.colour[i];
   const bool tc = nmax > 32;
+  // phase timer (thread 0; the marks sit where every thread passes)
+  auto mark = [&](int ph) {
+    if (L.prof && tid == 0 && level < 16) {
+      const long long t = clock64();
+      atomicAdd(L.prof + level * kProfSlots + ph, static_cast<unsigned long long>(t - t_row));
+      t_row = t;
+    }
+  };
   T* pool = reinterpret_cast<T*>(L.pool);
   if (n == 0) {
     if (tid == 0) {
@@ -443,6 +452,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
   }
   __syncthreads();
   const int mF = s_fpre[nf];
+  mark(1);
 
   int r = 0;
   double tau = 0.0;
@@ -683,6 +693,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
         const int half = lane >> 4, hl = lane & 15;
         const T tolJ = T(k) * Eps<T>::v, tolJ2 = tolJ * tolJ;
         bool jconv = false;
+        int nsw = kMaxSweeps;
         for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
           // same negligible-pair rule as the exact path, with k columns
           for (int j = warp; j < k; j += kWarpsNT) {
@@ -752,11 +763,16 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
           const int rotated = s_flag;
           __syncthreads();
           if (!rotated) {
+            nsw = sweep + 1;
             jconv = true;
             break;
           }
         }
         if (!jconv && tid == 0 && lvl_ok) atomicAdd(la.stats + 32 + level, 1);
+        if (L.prof && tid == 0 && level < 16) {
+          atomicAdd(L.prof + level * kProfSlots + kRowPhases + 2, static_cast<unsigned long long>(nsw));
+          atomicAdd(L.prof + level * kProfSlots + kRowPhases + 3, 1ull);
+        }
       }
       for (int j = tid; j < k; j += NT) {
         T sv = 0;
@@ -871,6 +887,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     }  // la.model
   }
 
+  mark(2);
   // ---------------- A. R factor of F_i^T (warp TSQR + tree merge) ----------
   if (mF > 0 && !have_u) {
     const int nchunks = (mF + kChunk - 1) / kChunk;
@@ -897,6 +914,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
       __syncthreads();
     }
 
+    mark(3);
     // ---------------- B. one-sided Jacobi on R (= X) ------------------------
     for (int e = tid; e < n * n; e += NT) {
       int a = e / n, b = e - a * n;
@@ -913,6 +931,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     const double floor_tau = static_cast<double>(Eps<T>::v) * sqrt(dn2);
     const T floor_tau_t = static_cast<T>(floor_tau);
     bool jconv = false;
+    int nsw = kMaxSweeps;
     for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
       // Columns whose norm stays below tau_est / (2 sqrt n) form a group whose
       // singular values are all below tau / 2: rotating two of them changes
@@ -988,11 +1007,16 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
       const int rotated = s_flag;
       __syncthreads();
       if (!rotated) {
+        nsw = sweep + 1;
         jconv = true;
         break;
       }
     }
     if (!jconv && tid == 0 && level < 16 && la.stats) atomicAdd(la.stats + 32 + level, 1);
+    if (L.prof && tid == 0 && level < 16) {
+      atomicAdd(L.prof + level * kProfSlots + kRowPhases, static_cast<unsigned long long>(nsw));
+      atomicAdd(L.prof + level * kProfSlots + kRowPhases + 1, 1ull);
+    }
     for (int j = tid; j < n; j += NT) {
       T s = 0;
       for (int row = 0; row < n; ++row) s += X[row * LD + j] * X[row * LD + j];
@@ -1047,6 +1071,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     for (int k = tid; k < n; k += NT) sig[k] = T(0);
   }
   __syncthreads();
+  mark(4);
   const int m = n - r;
   if (tid == 0) {
     L.rank[i] = r;
@@ -1129,6 +1154,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
   cta_mm<T, NT>(tc, r, r, m, [&](int a, int k) { return Tm[(r + k) * LD + a]; },
               [&](int k, int b) { return Tm[(r + k) * LD + b]; },
               [&](int a, int b, T v) { Dg[(int64_t)a * n + b] = Tm[a * LD + b] - v; });
+  mark(5);
   // target bookkeeping
   const int c0 = L.close_ptr[i], c1 = L.close_ptr[i + 1];
   const int nt = 1 + (c1 - c0);
@@ -1182,6 +1208,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     store_row_tile<T, NT>(Y, Xg, i, p, n, np, r, w, LD);
     __syncthreads();
   }
+  mark(6);
   // far rows: keep U_b^T F (rows r.. of U^T F are E_i and are dropped)
   for (int f = 0; f < nf; ++f) {
     const int k = s_fk[f], w = s_fw[f];
@@ -1196,6 +1223,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
     store_row_tile<T, NT>(Y, Xg, i, k, n, L.n[k], r, w, LD);
     __syncthreads();
   }
+  mark(7);
   // Schur update between close targets: A(p, q) -= W_p^T W_q
   if (m > 0 && std::is_same<T, float>::value && tc) {
     // tensor cores: the 16 x 8 tiles of all pairs (p, q) in one list, so the
@@ -1300,7 +1328,9 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : NT >= 256 ? 3 : 6))
                   int QW, LearnedArgs la) {
   __shared__ int s_q;
   const int tid = threadIdx.x, lane = tid & 31;
+  const bool prof = L.prof != nullptr && tid == 0 && level < 16;
   for (;;) {
+    long long t_row = prof ? clock64() : 0;
     if (tid < 32) {  // warp 0 takes the next row and waits for its neighbourhood
       int q = 0;
       if (lane == 0) {
@@ -1341,8 +1371,14 @@ __global__ void __launch_bounds__(NT, (NT >= 512 ? 2 : NT >= 256 ? 3 : 6))
     if (q < 0) return;
     __threadfence();
     const int i = L.order[q];
-    row_block<T, NT>(L, i, level, tol, tol_mode, status, nmax, LD, QW, la);
+    if (prof) {
+      const long long t = clock64();
+      atomicAdd(L.prof + level * kProfSlots, static_cast<unsigned long long>(t - t_row));
+      t_row = t;
+    }
+    row_block<T, NT>(L, i, level, tol, tol_mode, status, nmax, LD, QW, la, t_row);
     __syncthreads();
+    if (prof) atomicAdd(L.prof + level * kProfSlots + 8, static_cast<unsigned long long>(clock64() - t_row));
     if (tid == 0) {
       __threadfence();
       st_release(L.done + i, 1);

@@ -41,6 +41,19 @@ def main():
     nl = F.info.levels_done
     print("row kernel ms per level:", [round(F.info.level_ms[l], 3) for l in range(nl)],
           "shapes:", list(F.info.row_shape[:nl]))
+    names = ["wait", "setup", "learned", "R", "jacobi", "transform", "close", "far", "schur"]
+    steps = ["gather", "sketch", "exact_svd", "UtDU", "chol_inv", "W_Y_far", "D_Wp", "kept_schur"]
+    if any(F.info.big_rows[l] for l in range(nl)):
+        print("large-row levels: steps ms", {k: round(F.info.big_ms[j], 1) for j, k in enumerate(steps)},
+              "mean Jacobi sweeps", [round(F.info.jacobi_sweeps[l][0], 2) for l in range(nl) if F.info.big_rows[l]])
+    for l in range(nl):
+        if F.info.big_rows[l]:
+            continue
+        ph = [F.info.row_phase_ms[l][p] for p in range(9)]
+        tot = sum(ph) or 1.0
+        print(f"level {l}: row-phase SM time (ms summed over rows)",
+              {k: f"{v:.1f} ({100 * v / tot:.0f}%)" for k, v in zip(names, ph)},
+              "Jacobi sweeps (exact, learned):", [round(F.info.jacobi_sweeps[l][k], 2) for k in range(2)])
     if args.solve:
         b = torch.as_tensor(w.b, device="cuda")
         x = torch.zeros_like(b)
