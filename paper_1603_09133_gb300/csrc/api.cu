@@ -296,6 +296,34 @@ std::vector<std::pair<int, int>> block_pairs(const int64_t* rowptr, const int32_
 // in one flat copy; lookups are binary searches.
 bool csr_symmetric(int64_t n, const int64_t* rowptr, const int32_t* col, const double* val) {
   const int64_t nnz = rowptr[n];
+  // rows already in ascending column order (the usual CSR) are searched in
+  // place; otherwise every row is sorted into a copy first
+  std::atomic<bool> sorted{true};
+  ce::parallel_for(n, 8192, [&](int64_t a0, int64_t a1) {
+    for (int64_t a = a0; a < a1 && sorted.load(std::memory_order_relaxed); ++a)
+      for (int64_t e = rowptr[a] + 1; e < rowptr[a + 1]; ++e)
+        if (col[e] <= col[e - 1]) {
+          sorted.store(false);
+          break;
+        }
+  });
+  if (sorted.load()) {
+    std::atomic<bool> ok{true};
+    ce::parallel_for(n, 8192, [&](int64_t a0, int64_t a1) {
+      for (int64_t a = a0; a < a1 && ok.load(std::memory_order_relaxed); ++a)
+        for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
+          const int32_t b = col[e];
+          const int32_t* lo = col + rowptr[b];
+          const int32_t* hi = col + rowptr[b + 1];
+          const int32_t* it = std::lower_bound(lo, hi, static_cast<int32_t>(a));
+          if (it == hi || *it != a || val[it - col] != val[e]) {
+            ok.store(false);
+            break;
+          }
+        }
+    });
+    return ok.load();
+  }
   std::vector<std::pair<int32_t, double>> cv(nnz);
   ce::parallel_for(n, 8192, [&](int64_t a0, int64_t a1) {
     for (int64_t a = a0; a < a1; ++a) {

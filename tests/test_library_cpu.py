@@ -76,6 +76,51 @@ def test_csb_build_rejects_bad_input(lib):
                          None) == _lib.CE_ERR_INVALID_ARG
 
 
+def _build_raw(lib, n, rp, ci, v, perm, B):
+    h = C.c_void_p()
+    pm = np.ascontiguousarray(perm, np.int32)
+    return lib.csb_build(n, rp.ctypes.data_as(_lib.I64P), ci.ctypes.data_as(_lib.I32P), v.ctypes.data_as(_lib.DP),
+                         pm.ctypes.data_as(_lib.I32P), B, C.byref(h))
+
+
+def test_symmetry_check_sorted_and_unsorted_rows(lib):
+    """csb_build rejects a matrix that is not symmetric, in value or in
+    pattern, whether its rows come in ascending column order (searched in
+    place) or not (sorted into a copy first); the check runs before any CUDA
+    call."""
+    A = wl.poisson2d(8).tocsr()
+    A.sort_indices()
+    n, perm = A.shape[0], np.arange(64)
+    rp = np.ascontiguousarray(A.indptr, np.int64)
+    ci = np.ascontiguousarray(A.indices, np.int32)
+    v = np.ascontiguousarray(A.data, np.float64)
+    rng = np.random.default_rng(0)
+
+    def shuffled(ci, v):
+        ci2, v2 = ci.copy(), v.copy()
+        for a in range(n):
+            idx = np.arange(rp[a], rp[a + 1])
+            p = rng.permutation(idx)
+            ci2[idx], v2[idx] = ci[p], v[p]
+        return ci2, v2
+
+    for unsorted in (False, True):
+        c0, v0 = shuffled(ci, v) if unsorted else (ci, v)
+        # one value changed on one side of the diagonal
+        v1 = v0.copy()
+        e = next(q for q in range(rp[0], rp[1]) if c0[q] == 1)
+        v1[e] = -2.0
+        assert _build_raw(lib, n, rp, c0, v1, perm, 16) == _lib.CE_ERR_INVALID_ARG, unsorted
+    # a pattern entry (0, 9) without its mirror (9, 0)
+    An = A.tolil()
+    An[0, 9] = -0.5
+    An = An.tocsr()
+    An.sort_indices()
+    rp2 = np.ascontiguousarray(An.indptr, np.int64)
+    assert _build_raw(lib, n, rp2, np.ascontiguousarray(An.indices, np.int32),
+                      np.ascontiguousarray(An.data, np.float64), perm, 16) == _lib.CE_ERR_INVALID_ARG
+
+
 def test_wait_expiry_hook_validates_before_any_cuda_call(lib):
     status = np.zeros(8, np.int32)
     for kernel, ms in ((2, 20.0), (0, 0.0), (0, 5000.0), (1, -1.0)):

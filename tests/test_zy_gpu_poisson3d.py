@@ -1,16 +1,14 @@
-"""GPU: the 3D 7-point Laplacian against the FP64 oracle, on grids whose
-levels fit the row kernel (blocks of at most 64 rows, at most 32 targets and
-128 far blocks per row).
+"""GPU: the 3D 7-point Laplacian against the FP64 oracle on grids whose levels
+fit the row kernel (blocks of at most 64 rows, at most 32 targets and 128 far
+blocks per row); levels that outgrow it run the large-row path, covered by
+test_gpu_big_rows.py.
 
-The full 64^3 workload (B = 64, J = 8) runs levels 1 and 2 and then stops
-with CE_ERR_LIMIT (a level-3 row has more close blocks than the kernel
-holds); these smaller grids check the 3D arithmetic itself: the same
-distance-2 colouring, the same ranks (away from the threshold: every oracle
-singular value here lies at least 7e-4 relative from tau), the FP64 apply
-within 1e-10, PCG iterations within +-1 and a true residual <= 1e-8; the FP32
-form (on the grid whose singular values keep clear of tau by more than FP32
-rounding) by its backward error against the oracle's operator (<= 1e-4).
-(The file sorts last so that a failure here stops no other GPU test.)
+Checks the 3D arithmetic of the row kernel: the same distance-2 colouring,
+the same ranks (away from the threshold: every oracle singular value here
+lies at least 7e-4 relative from tau), the FP64 apply within 1e-10, PCG
+iterations within +-1 and a true residual <= 1e-8; the FP32 form (on the grid
+whose singular values keep clear of tau by more than FP32 rounding) by its
+backward error against the oracle's operator (<= 1e-4).
 """
 import numpy as np
 import pytest
