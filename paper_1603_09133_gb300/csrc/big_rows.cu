@@ -384,11 +384,12 @@ __global__ void __launch_bounds__(kTsqrThreads) tsqr_merge_kernel(const BigRowDe
 }
 
 // ---------------------------------------------------------------------------
-// One-sided (Hestenes) Jacobi on the columns of R: R V = U' S, U_i = V and
-// sigma = S sorted descending; the truncation rule of the compression step
-// (CE(eps), CE(r)) with the rounding floor u ||D_i||_F.  Columns are stored
-// contiguously (X = R^T row-major), one warp per column pair of a round-robin
-// round.  Rows without far columns get U_i = I and r_i = 0.
+// One-sided (Hestenes) Jacobi on the columns of X = R3^T, starting from the
+// pivoted-QR preconditioner's X and V = Q3 (qrcp_precond_kernel): X V' = U' S,
+// U_i = Q3 V' (accumulated in V) and sigma = S sorted descending; the
+// truncation rule of the compression step (CE(eps), CE(r)) with the rounding
+// floor u ||D_i||_F.  Columns are stored contiguously, half a warp per column
+// pair of a round-robin round.  Rows without far columns get U_i = I, r_i = 0.
 // ---------------------------------------------------------------------------
 struct BigLevelArgs {
   int level;
@@ -403,6 +404,161 @@ struct BigLevelArgs {
   int sketch;       // 1: randomized range finder first (learned form, FP32)
   unsigned long long seed;  // key of the sketch's Gaussians
 };
+
+// ---------------------------------------------------------------------------
+// Preconditioning of the large-row Jacobi by a QR factorization with column
+// pivoting (Drmac and Veselic, "New fast and accurate Jacobi SVD algorithm",
+// SIAM J. Matrix Anal. Appl. 29, 2008): with R from the TSQR of F_i^T and
+// R^T P = Q3 R3, the left singular vectors of F_i are Q3 times those of R3,
+// and one-sided Jacobi on the columns of X = R3^T (accumulating into V = Q3)
+// yields them directly, in a few sweeps because the pivoted factor is graded.
+// One CTA per row; R^T is R's row-major buffer read as column-major, factored
+// in place; X and V are written to the Jacobi's workspace.  Column norms are
+// recomputed after every step (no downdating); a pivot ties to the lowest
+// index.
+// ---------------------------------------------------------------------------
+constexpr int kQrThreads = 512;
+
+template <typename T>
+__global__ void __launch_bounds__(kQrThreads) qrcp_precond_kernel(const BigRowDev* rows, T* ws) {
+  const BigRowDev rw = rows[blockIdx.x];
+  const int n = rw.n;
+  if (n <= 0 || rw.mF <= 0) return;
+  constexpr int kW = kQrThreads / 32;
+  extern __shared__ __align__(16) unsigned char qr_smem[];
+  T* nrm = reinterpret_cast<T*>(qr_smem);   // n: squared norms of the trailing columns
+  T* tau = nrm + n;                          // n: reflector scalars
+  __shared__ int s_piv;
+  __shared__ T s_red[kW];
+  __shared__ int s_idx[kW];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* Z = ws + rw.x_off;   // column j at Z + j n (R^T)
+  for (int j = warp; j < n; j += kW) {
+    T sc = T(0);
+    for (int i = lane; i < n; i += 32) sc += Z[(int64_t)j * n + i] * Z[(int64_t)j * n + i];
+    sc = wsum(sc);
+    if (lane == 0) nrm[j] = sc;
+  }
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    // pivot: the trailing column of largest norm
+    {
+      T best = T(-1);
+      int bi = n;
+      for (int j = k + tid; j < n; j += kQrThreads)
+        if (nrm[j] > best) {
+          best = nrm[j];
+          bi = j;
+        }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (ob > best || (ob == best && oi < bi)) {
+          best = ob;
+          bi = oi;
+        }
+      }
+      if (lane == 0) {
+        s_red[warp] = best;
+        s_idx[warp] = bi;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        T b = s_red[0];
+        int ix = s_idx[0];
+        for (int w = 1; w < kW; ++w)
+          if (s_red[w] > b || (s_red[w] == b && s_idx[w] < ix)) {
+            b = s_red[w];
+            ix = s_idx[w];
+          }
+        s_piv = (ix < n) ? ix : k;
+      }
+      __syncthreads();
+    }
+    const int pv = s_piv;
+    if (pv != k) {   // swap columns k and pv (and their norms)
+      for (int i = tid; i < n; i += kQrThreads) {
+        const T a = Z[(int64_t)k * n + i], b = Z[(int64_t)pv * n + i];
+        Z[(int64_t)k * n + i] = b;
+        Z[(int64_t)pv * n + i] = a;
+      }
+      if (tid == 0) {
+        const T t = nrm[k];
+        nrm[k] = nrm[pv];
+        nrm[pv] = t;
+      }
+      __syncthreads();
+    }
+    // reflector of Z[k:, k] (warp 0): Z[k][k] <- beta, v = Z[k+1:, k] / (alpha - beta)
+    if (warp == 0) {
+      T x2 = T(0);
+      for (int i = k + 1 + lane; i < n; i += 32) x2 += Z[(int64_t)k * n + i] * Z[(int64_t)k * n + i];
+      x2 = wsum(x2);
+      const T alpha = Z[(int64_t)k * n + k];
+      T tk = T(0);
+      if (x2 > T(0)) {
+        const T beta = (alpha >= T(0)) ? -sqrt(alpha * alpha + x2) : sqrt(alpha * alpha + x2);
+        tk = (beta - alpha) / beta;
+        const T sc = T(1) / (alpha - beta);
+        for (int i = k + 1 + lane; i < n; i += 32) Z[(int64_t)k * n + i] *= sc;
+        __syncwarp();
+        if (lane == 0) Z[(int64_t)k * n + k] = beta;
+      }
+      if (lane == 0) tau[k] = tk;
+    }
+    __syncthreads();
+    const T tk = tau[k];
+    // apply H_k = I - tau [1; v][1; v]^T to the trailing columns; their norms afresh
+    for (int j = k + 1 + warp; j < n; j += kW) {
+      T* zj = Z + (int64_t)j * n;
+      const T* v = Z + (int64_t)k * n;
+      T w = T(0);
+      if (tk != T(0)) {
+        for (int i = k + 1 + lane; i < n; i += 32) w += v[i] * zj[i];
+        w = wsum(w) + zj[k];
+        w *= tk;
+      }
+      T sc = T(0);
+      for (int i = k + 1 + lane; i < n; i += 32) {
+        const T z = zj[i] - w * v[i];
+        zj[i] = z;
+        sc += z * z;
+      }
+      sc = wsum(sc);
+      if (lane == 0) {
+        zj[k] -= w;
+        nrm[j] = sc;
+      }
+    }
+    __syncthreads();
+  }
+  // X = R3^T (column-major): X[c][r] = R3[c][r] = Z[r n + c] for c <= r
+  T* X = ws + rw.t_off;
+  T* V = ws + rw.v_off;
+  for (int64_t e = tid; e < (int64_t)n * n; e += kQrThreads) {
+    const int c = static_cast<int>(e / n), r = static_cast<int>(e % n);
+    X[e] = (c <= r) ? Z[(int64_t)r * n + c] : T(0);
+    V[e] = (c == r) ? T(1) : T(0);
+  }
+  __syncthreads();
+  // V = Q3 = H_0 ... H_{n-1} (backward accumulation on the identity)
+  for (int k = n - 1; k >= 0; --k) {
+    const T tk = tau[k];
+    if (tk != T(0)) {
+      const T* v = Z + (int64_t)k * n;
+      for (int j = k + warp; j < n; j += kW) {
+        T* vj = V + (int64_t)j * n;
+        T w = T(0);
+        for (int i = k + 1 + lane; i < n; i += 32) w += v[i] * vj[i];
+        w = (wsum(w) + vj[k]) * tk;
+        for (int i = k + 1 + lane; i < n; i += 32) vj[i] -= w * v[i];
+        if (lane == 0) vj[k] -= w;
+      }
+    }
+    __syncthreads();
+  }
+}
 
 template <typename T>
 __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(const BigRowDev* rows, T* ws, LevelDev L,
@@ -444,15 +600,14 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(const BigRowDev* ro
     return;
   }
   // columns of R contiguous; in shared memory when both n x n matrices fit
-  // (presolved: block_jacobi_kernel already rotated X and V in the workspace)
+  // X and V start as the pivoted-QR preconditioner left them in the
+  // workspace (presolved: block_jacobi_kernel already rotated them there)
   T* X = xv_smem ? reinterpret_cast<T*>(pos + ((n + 3) & ~3)) : ws + rw.t_off;
   T* V = xv_smem ? X + (int64_t)n * n : ws + rw.v_off;
-  const T* R = ws + rw.x_off;
-  if (!presolved)
+  if (xv_smem)
     for (int64_t e = tid; e < (int64_t)n * n; e += kJacThreads) {
-      const int c = static_cast<int>(e / n), row = static_cast<int>(e % n);
-      X[e] = R[(int64_t)row * n + c];
-      V[e] = (c == row) ? T(1) : T(0);
+      X[e] = ws[rw.t_off + e];
+      V[e] = ws[rw.v_off + e];
     }
   __syncthreads();
   const int nb = n + (n & 1), npairs = nb / 2;
@@ -618,8 +773,9 @@ __global__ void __launch_bounds__(kJacThreads) jacobi_kernel(const BigRowDev* ro
 // Block one-sided Jacobi for rows whose R and V (n x n each) do not fit in
 // one CTA's shared memory.  The n columns form blocks of B; each round of a
 // round-robin tournament over the blocks pairs them up, and one CTA takes a
-// pair of blocks: it stages their 2B columns of X (= R at the start) and of
-// V in shared memory, runs one cyclic sweep of column rotations over them (a
+// pair of blocks: it stages their 2B columns of X (from the pivoted-QR
+// preconditioner at the start) and of V in shared memory, runs one cyclic
+// sweep of column rotations over them (a
 // warp per column pair, the same pair test and rotation as jacobi_kernel),
 // and writes them back.  All block pairs of a round, of every row of the
 // colour, run at once; grid barriers (cooperative launch) separate the
@@ -647,19 +803,25 @@ __global__ void __launch_bounds__(32 * B) block_jacobi_kernel(const BigRowDev* r
   __shared__ double s_red[2][B];
   __shared__ int s_rot;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  // X = R (column-major), V = I, ||D_i||_F^2 and the largest column norm
+  // ||D_i||_F^2 and the largest column norm of X
   for (int r = blockIdx.x; r < nrows; r += gridDim.x) {
     const BigRowDev rw = rows[r];
     const int n = rw.n;
-    T* X = ws + rw.t_off;
-    T* V = ws + rw.v_off;
-    const T* R = ws + rw.x_off;
+    if (rw.mF <= 0) {   // no far columns: nothing to rotate (U_i = I)
+      if (tid == 0) {
+        st[r].dn2 = 0.0;
+        st[r].cm = 0ull;
+        st[r].cmn = 0ull;
+        st[r].flag = 0;
+        st[r].conv = 1;
+        st[r].sweeps = 0;
+      }
+      continue;
+    }
+    const T* X = ws + rw.t_off;   // X and V from the pivoted-QR preconditioner
     const T* D = reinterpret_cast<const T*>(L.pool) + L.diag_off[rw.i];
     double ss = 0.0;
     for (int64_t e = tid; e < (int64_t)n * n; e += NT) {
-      const int c = static_cast<int>(e / n), row = static_cast<int>(e % n);
-      X[e] = R[(int64_t)row * n + c];
-      V[e] = (c == row) ? T(1) : T(0);
       const double d = static_cast<double>(D[e]);
       ss += d * d;
     }
@@ -1597,6 +1759,9 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
     const size_t sxv = sj + (size_t)2 * kmx * kmx * es;
     const int xv = sxv <= jac_dyn ? 1 : 0;
     if (xv) sj = sxv;
+    g_launches.fetch_add(1, std::memory_order_relaxed);
+    qrcp_precond_kernel<T><<<ns, kQrThreads, (size_t)2 * kmx * es, s>>>(dview, ws2);
+    bcheck(cudaGetLastError());
     if (!xv) launch_block_jacobi<T>(view, dview, ws2, D, args, jac_dyn, s);
     g_launches.fetch_add(1, std::memory_order_relaxed);
     jacobi_kernel<T><<<ns, kJacThreads, sj, s>>>(dview, ws2, D, args, xv, dres, xv ? 0 : 1);
@@ -1782,6 +1947,9 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
         const size_t sxv = sj + (size_t)2 * nmx * nmx * es;
         const int xv = sxv <= jac_dyn ? 1 : 0;
         if (xv) sj = sxv;
+        g_launches.fetch_add(1, std::memory_order_relaxed);
+        qrcp_precond_kernel<T><<<ne, kQrThreads, (size_t)2 * nmx * es, s>>>(dex, ws);
+        bcheck(cudaGetLastError());
         // rows whose X and V do not fit in shared memory: block Jacobi over
         // many CTAs first, then jacobi_kernel only reads the result
         if (!xv) launch_block_jacobi<T>(ex, dex, ws, D, args, jac_dyn, s);
