@@ -1031,54 +1031,109 @@ __global__ void sketch_omega_kernel(const SketchRowDev* rows, T* ws, int level, 
 
 // Householder QR of Y[:, :k] (n x (k + 2), row-major, global) carried along
 // to the probe columns; the probe residuals; the explicit Q (n x k).
+// Householder steps on a row-major matrix M (leading dimension ld): lanes run
+// over columns, so every load and store of a row segment is coalesced; the
+// rows below the pivot are split among warps when the columns are few.
+// Reflector of column j (rows j..n-1): M[j][j] <- beta, v = M[j+1:, j] / (x0 -
+// beta) stored in M and in s_v; returns tau (0: no reflection).
+template <typename T>
+__device__ T house_reflect_col(T* M, int ld, int n, int j, T* s_v) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  __shared__ T s_t;
+  __syncthreads();   // every thread is done with the previous s_t and s_v
+  if (warp == 0) {
+    T amax = T(0);
+    for (int a = j + 1 + lane; a < n; a += 32) amax = fmax(amax, fabs(M[(int64_t)a * ld + j]));
+    amax = wmax(amax);
+    T tau = T(0);
+    if (amax >= TinyB<T>::v) {
+      T ss = T(0);
+      for (int a = j + 1 + lane; a < n; a += 32) {
+        const T v = M[(int64_t)a * ld + j] / amax;
+        ss += v * v;
+      }
+      ss = wsum(ss);
+      const T x0 = M[(int64_t)j * ld + j];
+      const T aa = fmax(amax, fabs(x0));
+      const T nrm = aa * sqrt((x0 / aa) * (x0 / aa) + ss * (amax / aa) * (amax / aa));
+      const T beta = (x0 >= T(0)) ? -nrm : nrm;
+      tau = (beta - x0) / beta;
+      const T sc = T(1) / (x0 - beta);
+      for (int a = j + 1 + lane; a < n; a += 32) {
+        const T v = M[(int64_t)a * ld + j] * sc;
+        M[(int64_t)a * ld + j] = v;
+        s_v[a] = v;
+      }
+      __syncwarp();
+      if (lane == 0) M[(int64_t)j * ld + j] = beta;
+    }
+    if (lane == 0) s_t = tau;
+  }
+  __syncthreads();
+  return s_t;
+}
+
+// M[j:, c0:c1] <- (I - tau [1; v][1; v]^T) M[j:, c0:c1], v = s_v[j+1 .. n)
+template <typename T, int NT>
+__device__ void house_apply_cols(T* M, int ld, int n, int j, int c0, int c1, const T* s_v, T tau, T* red,
+                                 T* dcol) {
+  constexpr int W = NT / 32;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nc = c1 - c0;
+  if (nc <= 0 || tau == T(0)) return;   // uniform
+  const int G = (nc + 31) / 32;
+  if (G >= W) {
+    for (int g = warp; g < G; g += W) {
+      const int l = c0 + 32 * g + lane;
+      if (l < c1) {
+        T d = M[(int64_t)j * ld + l];
+        for (int a = j + 1; a < n; ++a) d += s_v[a] * M[(int64_t)a * ld + l];
+        d *= tau;
+        M[(int64_t)j * ld + l] -= d;
+        for (int a = j + 1; a < n; ++a) M[(int64_t)a * ld + l] -= d * s_v[a];
+      }
+    }
+    __syncthreads();
+    return;
+  }
+  const int S = W / G, g = warp % G, sp = warp / G;
+  const int R = n - j - 1, chunk = (R + S - 1) / S;
+  const int a0 = j + 1 + sp * chunk, a1 = min(n, a0 + chunk);
+  const int l = c0 + 32 * g + lane;
+  const bool act = sp < S && l < c1;
+  T part = T(0);
+  if (act)
+    for (int a = a0; a < a1; ++a) part += s_v[a] * M[(int64_t)a * ld + l];
+  red[warp * 32 + lane] = part;
+  __syncthreads();
+  if (sp == 0 && l < c1) {
+    T d = M[(int64_t)j * ld + l];
+    for (int q = 0; q < S; ++q) d += red[(g + q * G) * 32 + lane];
+    d *= tau;
+    dcol[32 * g + lane] = d;
+    M[(int64_t)j * ld + l] -= d;
+  }
+  __syncthreads();
+  if (act) {
+    const T d = dcol[32 * g + lane];
+    for (int a = a0; a < a1; ++a) M[(int64_t)a * ld + l] -= d * s_v[a];
+  }
+  __syncthreads();
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kBigThreads) sketch_qr_kernel(const SketchRowDev* rows, T* ws, SketchRes* res) {
   const SketchRowDev rw = rows[blockIdx.x];
   const int n = rw.n, k = rw.k, kp = k + 2;
   T* Y = ws + rw.y_off;
   T* Q = ws + rw.q_off;
-  __shared__ T s_tau[1024], s_pr[2];
+  __shared__ T s_tau[1024], s_pr[2], s_v[kBigMaxN], red[kBigThreads], dcol[kBigThreads];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int kW = kBigThreads / 32;
+  // Householder QR of Y[:, :k]; the two probe columns are carried along
   for (int j = 0; j < k; ++j) {
-    if (warp == 0) {
-      // reflector of Y[j:, j]
-      T amax = T(0);
-      for (int a = j + 1 + lane; a < n; a += 32) amax = fmax(amax, fabs(Y[(int64_t)a * kp + j]));
-      amax = wmax(amax);
-      T tau = T(0);
-      if (amax >= TinyB<T>::v) {
-        T ss = T(0);
-        for (int a = j + 1 + lane; a < n; a += 32) {
-          const T v = Y[(int64_t)a * kp + j] / amax;
-          ss += v * v;
-        }
-        ss = wsum(ss);
-        const T x0 = Y[(int64_t)j * kp + j];
-        const T aa = fmax(amax, fabs(x0));
-        const T nrm = aa * sqrt((x0 / aa) * (x0 / aa) + ss * (amax / aa) * (amax / aa));
-        const T beta = (x0 >= T(0)) ? -nrm : nrm;
-        tau = (beta - x0) / beta;
-        const T sc = T(1) / (x0 - beta);
-        for (int a = j + 1 + lane; a < n; a += 32) Y[(int64_t)a * kp + j] *= sc;
-        __syncwarp();
-        if (lane == 0) Y[(int64_t)j * kp + j] = beta;
-      }
-      if (lane == 0) s_tau[j] = tau;
-    }
-    __syncthreads();
-    const T tq = s_tau[j];
-    if (tq != T(0)) {
-      for (int l = j + 1 + warp; l < kp; l += kW) {
-        T d = T(0);
-        for (int a = j + 1 + lane; a < n; a += 32) d += Y[(int64_t)a * kp + j] * Y[(int64_t)a * kp + l];
-        d = wsum(d);
-        d = (d + Y[(int64_t)j * kp + l]) * tq;
-        if (lane == 0) Y[(int64_t)j * kp + l] -= d;
-        for (int a = j + 1 + lane; a < n; a += 32) Y[(int64_t)a * kp + l] -= d * Y[(int64_t)a * kp + j];
-      }
-    }
-    __syncthreads();
+    const T tq = house_reflect_col(Y, kp, n, j, s_v);
+    if (tid == 0) s_tau[j] = tq;
+    house_apply_cols<T, kBigThreads>(Y, kp, n, j, j + 1, kp, s_v, tq, red, dcol);
   }
   if (warp < 2) {  // ||(I - Q Q^T) F w|| = norm of rows k.. of H^T (F w)
     T ss = T(0);
@@ -1098,16 +1153,10 @@ __global__ void __launch_bounds__(kBigThreads) sketch_qr_kernel(const SketchRowD
   for (int j = k - 1; j >= 0; --j) {
     const T tq = s_tau[j];
     if (tq != T(0)) {
-      for (int l = j + warp; l < k; l += kW) {
-        T d = T(0);
-        for (int a = j + 1 + lane; a < n; a += 32) d += Y[(int64_t)a * kp + j] * Q[(int64_t)a * k + l];
-        d = wsum(d);
-        d = (d + Q[(int64_t)j * k + l]) * tq;
-        if (lane == 0) Q[(int64_t)j * k + l] -= d;
-        for (int a = j + 1 + lane; a < n; a += 32) Q[(int64_t)a * k + l] -= d * Y[(int64_t)a * kp + j];
-      }
+      for (int a = j + 1 + tid; a < n; a += kBigThreads) s_v[a] = Y[(int64_t)a * kp + j];
+      __syncthreads();
+      house_apply_cols<T, kBigThreads>(Q, k, n, j, j, k, s_v, tq, red, dcol);
     }
-    __syncthreads();
   }
   if (tid == 0) res[blockIdx.x].probe = static_cast<double>(fmax(s_pr[0], s_pr[1]));
 }
@@ -1145,63 +1194,22 @@ __global__ void __launch_bounds__(kBigThreads) complete_u_kernel(const SketchRow
   const int n = rw.n, i = rw.i, r = L.rank[i];
   T* Ub = ws + rw.ub_off;   // n x r, row-major (ld r)
   T* U = reinterpret_cast<T*>(L.U) + L.u_off[i];
-  __shared__ T s_tau[1024];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  constexpr int kW = kBigThreads / 32;
+  __shared__ T s_tau[1024], s_v[kBigMaxN], red[kBigThreads], dcol[kBigThreads];
+  const int tid = threadIdx.x;
   for (int j = 0; j < r; ++j) {
-    if (warp == 0) {
-      T amax = T(0);
-      for (int a = j + 1 + lane; a < n; a += 32) amax = fmax(amax, fabs(Ub[(int64_t)a * r + j]));
-      amax = wmax(amax);
-      T tau = T(0);
-      if (amax >= TinyB<T>::v) {
-        T ss = T(0);
-        for (int a = j + 1 + lane; a < n; a += 32) {
-          const T v = Ub[(int64_t)a * r + j] / amax;
-          ss += v * v;
-        }
-        ss = wsum(ss);
-        const T x0 = Ub[(int64_t)j * r + j];
-        const T aa = fmax(amax, fabs(x0));
-        const T nrm = aa * sqrt((x0 / aa) * (x0 / aa) + ss * (amax / aa) * (amax / aa));
-        const T beta = (x0 >= T(0)) ? -nrm : nrm;
-        tau = (beta - x0) / beta;
-        const T sc = T(1) / (x0 - beta);
-        for (int a = j + 1 + lane; a < n; a += 32) Ub[(int64_t)a * r + j] *= sc;
-        __syncwarp();
-        if (lane == 0) Ub[(int64_t)j * r + j] = beta;
-      }
-      if (lane == 0) s_tau[j] = tau;
-    }
-    __syncthreads();
-    const T tq = s_tau[j];
-    if (tq != T(0)) {
-      for (int l = j + 1 + warp; l < r; l += kW) {
-        T d = T(0);
-        for (int a = j + 1 + lane; a < n; a += 32) d += Ub[(int64_t)a * r + j] * Ub[(int64_t)a * r + l];
-        d = wsum(d);
-        d = (d + Ub[(int64_t)j * r + l]) * tq;
-        if (lane == 0) Ub[(int64_t)j * r + l] -= d;
-        for (int a = j + 1 + lane; a < n; a += 32) Ub[(int64_t)a * r + l] -= d * Ub[(int64_t)a * r + j];
-      }
-    }
-    __syncthreads();
+    const T tq = house_reflect_col(Ub, r, n, j, s_v);
+    if (tid == 0) s_tau[j] = tq;
+    house_apply_cols<T, kBigThreads>(Ub, r, n, j, j + 1, r, s_v, tq, red, dcol);
   }
   for (int64_t e = tid; e < (int64_t)n * n; e += kBigThreads) U[e] = (e / n == e % n) ? T(1) : T(0);
   __syncthreads();
   for (int j = r - 1; j >= 0; --j) {
     const T tq = s_tau[j];
     if (tq != T(0)) {
-      for (int l = j + warp; l < n; l += kW) {
-        T d = T(0);
-        for (int a = j + 1 + lane; a < n; a += 32) d += Ub[(int64_t)a * r + j] * U[(int64_t)a * n + l];
-        d = wsum(d);
-        d = (d + U[(int64_t)j * n + l]) * tq;
-        if (lane == 0) U[(int64_t)j * n + l] -= d;
-        for (int a = j + 1 + lane; a < n; a += 32) U[(int64_t)a * n + l] -= d * Ub[(int64_t)a * r + j];
-      }
+      for (int a = j + 1 + tid; a < n; a += kBigThreads) s_v[a] = Ub[(int64_t)a * r + j];
+      __syncthreads();
+      house_apply_cols<T, kBigThreads>(U, n, n, j, j, n, s_v, tq, red, dcol);
     }
-    __syncthreads();
   }
 }
 
