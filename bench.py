@@ -308,13 +308,28 @@ def run_ours(args, rank, world):
     peaks = {k: ceg.measure_peak(k) for k in ("fp32_fma", "fp64_fma", "tf32_mma", "tf32x3_mma")}
     # row-kernel CTA shape (and learned or exact per level) chosen by
     # measurement for both forms (setup, untimed); in 3D a factorization
-    # takes seconds, so the heuristic shapes are kept
-    tune_ms = tune_ms_plain = np.zeros((2, 4, pb.levels))
+    # takes seconds, so the heuristic shapes are kept and only learned or
+    # exact compression is chosen per level, from one factorization of each
+    tune_ms, tune_ms_plain = np.zeros((2, 4, pb.levels)), np.zeros((2, 4, pb.levels))
     if not pb.is3d:
         tune_ms = ceg.ce_autotune(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision=args.precision,
                                   rank_model=model, nmax=pb.nmax, coloring=args.coloring)
         tune_ms_plain = ceg.ce_autotune(csb, tol=pb.tol, levels=pb.levels, J=pb.J, precision="fp64",
                                         nmax=pb.nmax, coloring=args.coloring)
+    elif model is not None:
+        kw = dict(tol=pb.tol, levels=pb.levels, J=pb.J, precision=args.precision, nmax=pb.nmax,
+                  coloring=args.coloring)
+        Fl = ceg.ce_factorize(csb, rank_model=model, **kw)
+        Fe = ceg.ce_factorize(csb, **kw)
+        nlv = min(Fl.info.levels_done, Fe.info.levels_done)
+        shp = np.array([Fl.info.row_shape[l] if l < nlv else 0 for l in range(16)], np.int32)
+        lrn = np.array([int(Fl.info.level_ms[l] <= Fe.info.level_ms[l]) if l < nlv else 0 for l in range(16)],
+                       np.int32)
+        for l in range(min(nlv, pb.levels)):
+            tune_ms[0, shp[l], l] = Fl.info.level_ms[l]
+            tune_ms[1, shp[l], l] = Fe.info.level_ms[l]
+        csb.set_tuning((nlv, shp, lrn), args.precision, learned=True)
+        del Fl, Fe
     tuning = csb.tuning(args.precision, learned=model is not None)
 
     def step(prec, rm=None):
