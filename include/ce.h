@@ -647,6 +647,28 @@ ce_status ce_debug_wait_expiry(int kernel, double limit_ms, int32_t* status_out,
 ce_status ce_debug_gemm(int engine, int M, int N, int K, const void* A_dev, int lda, int ta, const void* B_dev,
                         int ldb, int tb, void* C_dev, int ldc, int tc, double alpha, double beta, void* stream);
 
+/*
+ * ce_debug_svd -- the SVD steps of the compression of a large row (Section
+ * 2.2: U_i and sigma of a far row through the R factor of F_i^T) on one
+ * n x n upper triangular R, for tests: the QR factorization with column
+ * pivoting of R^T (R^T P = Q3 R3), then block one-sided Jacobi with column
+ * blocks of `block` (4, 8, 16 or 32) on X = R3^T, rotations accumulated into
+ * V = Q3.  On return the columns of X are the left singular vectors of R^T
+ * scaled by the singular values (in no particular order) and V holds the
+ * unit vectors: R^T R V = V diag(||X_j||^2) up to rounding.
+ *   esize   4 (FP32) or 8 (FP64) for every array
+ *   R_dev   n x n row-major (zero below the diagonal), not modified
+ *   D_dev   n x n: ||D||_F sets the rounding floor of the pair-skipping rule
+ *   tol     eps of the rule (0: only rounding-level pairs are skipped)
+ *   X_dev, V_dev  n x n each, column-major (column j at j n)
+ *   sweeps  optional host int: sweeps run
+ * Synchronizes the stream.  CE_ERR_INVALID_ARG for another esize or block,
+ * n outside 1..1536, or when 4 block n values do not fit in shared memory.
+ * Not part of the paper's interface.
+ */
+ce_status ce_debug_svd(int esize, int block, int n, const void* R_dev, const void* D_dev, double tol, void* X_dev,
+                       void* V_dev, int* sweeps, void* stream);
+
 /* Level-1 plan of a csb handle: blocks, colours, colour of every block. */
 int csb_blocks(const ce_csb* A);
 ce_status csb_get_colours(const ce_csb* A, int32_t* colour, int* ncolours);

@@ -114,6 +114,7 @@ SIGNATURES = {
     "pcg_solve_batched": (C.c_int, [P, P, P, P, C.c_double, C.c_int, I32P, DP, I32P,
                                     C.POINTER(ce_pcg_info), P]),
     "pcg_solve_noalloc": (C.c_int, [P, P, P, P, C.c_double, C.c_int, C.POINTER(ce_pcg_info), P]),
+    "ce_debug_svd": (C.c_int, [C.c_int, C.c_int, C.c_int, P, P, C.c_double, P, P, C.POINTER(C.c_int), P]),
     "minres_solve": (C.c_int, [P, P, P, P, C.c_double, C.c_int, C.POINTER(ce_pcg_info), P]),
     "ce_csb_destroy": (None, [P]),
     "ce_factor_destroy": (None, [P]),

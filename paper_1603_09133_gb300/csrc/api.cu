@@ -1779,6 +1779,24 @@ ce_status ce_debug_wait_expiry(int kernel, double limit_ms, int32_t* status_out,
   return ret;
 }
 
+ce_status ce_debug_svd(int esize, int block, int n, const void* R_dev, const void* D_dev, double tol, void* X_dev,
+                       void* V_dev, int* sweeps, void* stream) {
+  if ((esize != 4 && esize != 8) || (block != 4 && block != 8 && block != 16 && block != 32) || n < 1 ||
+      n > ce::kBigMaxN || !R_dev || !D_dev || !X_dev || !V_dev || tol < 0)
+    return CE_ERR_INVALID_ARG;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const cudaError_t e = ce::debug_svd(esize, block, n, R_dev, D_dev, tol, X_dev, V_dev, sweeps, s);
+  if (e == cudaErrorInvalidValue) {
+    g_last_error = "ce_debug_svd: 4 x block x n values do not fit in shared memory";
+    return CE_ERR_INVALID_ARG;
+  }
+  if (e != cudaSuccess) {
+    g_last_error = std::string("ce_debug_svd: ") + cudaGetErrorString(e);
+    return CE_ERR_CUDA;
+  }
+  return CE_OK;
+}
+
 ce_status ce_debug_gemm(int engine, int M, int N, int K, const void* A_dev, int lda, int ta, const void* B_dev,
                         int ldb, int tb, void* C_dev, int ldc, int tc, double alpha, double beta, void* stream) {
   if (engine < 0 || engine > 3 || M < 0 || N < 0 || K < 0 || !A_dev || !B_dev || !C_dev || lda <= 0 || ldb <= 0 ||

@@ -2182,6 +2182,78 @@ bool level_needs_big_rows(const LevelPlan& P) {
   return false;
 }
 
+// The SVD steps of a large row on one n x n R (tests): the pivoted-QR
+// preconditioner, then block Jacobi with column blocks of B; X and V copied
+// out (column-major), the sweeps run into *sweeps.
+template <typename T>
+void debug_svd_t(int B, int n, const void* R, const void* Dm, double tol, void* X, void* V, int* sweeps,
+                 cudaStream_t s) {
+  const int64_t nn = (int64_t)n * n;
+  T* ws = nullptr;
+  void* aux = nullptr;
+  bcheck(cudaMallocAsync(reinterpret_cast<void**>(&ws), 3 * nn * sizeof(T), s));
+  bcheck(cudaMallocAsync(&aux, sizeof(BigRowDev) + sizeof(int64_t) + (kStatusWords + kStatsWords) * sizeof(int), s));
+  BigRowDev* drow = static_cast<BigRowDev*>(aux);
+  int64_t* ddiag = reinterpret_cast<int64_t*>(static_cast<char*>(aux) + sizeof(BigRowDev));
+  int* dstat = reinterpret_cast<int*>(ddiag + 1);
+  BigRowDev r{};
+  r.i = 0;
+  r.n = n;
+  r.mF = 1;
+  r.parts = 1;
+  r.x_off = 0;
+  r.v_off = nn;
+  r.t_off = 2 * nn;
+  const int64_t zero = 0;
+  bcheck(cudaMemcpyAsync(drow, &r, sizeof(r), cudaMemcpyHostToDevice, s));
+  bcheck(cudaMemcpyAsync(ddiag, &zero, sizeof(zero), cudaMemcpyHostToDevice, s));
+  bcheck(cudaMemsetAsync(dstat, 0, (kStatusWords + kStatsWords) * sizeof(int), s));
+  bcheck(cudaMemcpyAsync(ws, R, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  LevelDev D{};
+  D.pool = const_cast<void*>(Dm);
+  D.diag_off = ddiag;
+  BigLevelArgs a{};
+  a.level = 0;
+  a.tol = tol;
+  a.tol_mode = CE_TOL_REL;
+  a.status = dstat;
+  a.stats = dstat + kStatusWords;
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  qrcp_precond_kernel<T><<<1, kQrThreads, (size_t)2 * n * sizeof(T), s>>>(drow, ws);
+  bcheck(cudaGetLastError());
+  const std::vector<BigRowDev> rv{r};
+  const size_t sm = (size_t)4 * B * n * sizeof(T) + 256;
+  int dev = 0, optin = 0;
+  bcheck(cudaGetDevice(&dev));
+  bcheck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  if (sm + 2048 > (size_t)optin) throw BigFail{cudaErrorInvalidValue};
+  if (B == 32) launch_block_jacobi_b<T, 32>(rv, drow, ws, D, a, sm, s);
+  else if (B == 16) launch_block_jacobi_b<T, 16>(rv, drow, ws, D, a, sm, s);
+  else if (B == 8) launch_block_jacobi_b<T, 8>(rv, drow, ws, D, a, sm, s);
+  else launch_block_jacobi_b<T, 4>(rv, drow, ws, D, a, sm, s);
+  bcheck(cudaMemcpyAsync(X, ws + 2 * nn, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  bcheck(cudaMemcpyAsync(V, ws + nn, nn * sizeof(T), cudaMemcpyDeviceToDevice, s));
+  int hs[kStatsWords];
+  bcheck(cudaMemcpyAsync(hs, dstat + kStatusWords, sizeof(hs), cudaMemcpyDeviceToHost, s));
+  bcheck(cudaStreamSynchronize(s));
+  if (sweeps) *sweeps = hs[48];
+  cudaFreeAsync(ws, s);
+  cudaFreeAsync(aux, s);
+}
+
+cudaError_t debug_svd(int esize, int B, int n, const void* R, const void* Dm, double tol, void* X, void* V,
+                      int* sweeps, cudaStream_t s) {
+  try {
+    if (esize == 8)
+      debug_svd_t<double>(B, n, R, Dm, tol, X, V, sweeps, s);
+    else
+      debug_svd_t<float>(B, n, R, Dm, tol, X, V, sweeps, s);
+  } catch (const BigFail& f) {
+    return f.e;
+  }
+  return cudaSuccess;
+}
+
 cudaError_t run_big_level(int esize, LevelStore& st, int level, double tol, int tol_mode, int* status, int* stats,
                           int engine, double* phase_ms, int sketch, unsigned long long seed, cudaStream_t s) {
   int* tc_err = nullptr;

@@ -143,6 +143,10 @@ cudaError_t launch_gemm_tc(const std::vector<GemmTask>& tasks, int passes, int* 
 // elimination (per colour, synchronizing the stream once per colour), and the
 // apply of such a level (one launch per colour)
 bool level_needs_big_rows(const LevelPlan& P);
+// the large-row SVD steps (pivoted-QR preconditioner + block Jacobi) on one
+// n x n R, for tests (ce_debug_svd)
+cudaError_t debug_svd(int esize, int B, int n, const void* R, const void* Dm, double tol, void* X, void* V,
+                      int* sweeps, cudaStream_t s);
 cudaError_t run_big_level(int esize, LevelStore& st, int level, double tol, int tol_mode, int* status, int* stats,
                           int engine, double* phase_ms, int sketch, unsigned long long seed, cudaStream_t s);
 cudaError_t launch_apply_big(int esize, const LevelDev& L, const LevelPlan& P, double* vec, int forward,
