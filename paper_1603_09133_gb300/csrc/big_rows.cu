@@ -1073,6 +1073,34 @@ __device__ T house_reflect_col(T* M, int ld, int n, int j, T* s_v) {
   return s_t;
 }
 
+// sum_{a0 <= a < a1} v[a] M[a][l]: eight independent partial sums, so eight
+// row loads are in flight at a time (the rows are ld apart in memory)
+template <typename T>
+__device__ __forceinline__ T col_dot(const T* M, int ld, int l, const T* v, int a0, int a1) {
+  T p[8] = {T(0), T(0), T(0), T(0), T(0), T(0), T(0), T(0)};
+  int a = a0;
+  for (; a + 8 <= a1; a += 8) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) p[u] += v[a + u] * M[(int64_t)(a + u) * ld + l];
+  }
+  for (; a < a1; ++a) p[0] += v[a] * M[(int64_t)a * ld + l];
+  return ((p[0] + p[1]) + (p[2] + p[3])) + ((p[4] + p[5]) + (p[6] + p[7]));
+}
+
+// M[a][l] -= d v[a] for a0 <= a < a1, eight rows at a time
+template <typename T>
+__device__ __forceinline__ void col_axpy(T* M, int ld, int l, const T* v, int a0, int a1, T d) {
+  int a = a0;
+  for (; a + 8 <= a1; a += 8) {
+    T x[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) x[u] = M[(int64_t)(a + u) * ld + l];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) M[(int64_t)(a + u) * ld + l] = x[u] - d * v[a + u];
+  }
+  for (; a < a1; ++a) M[(int64_t)a * ld + l] -= d * v[a];
+}
+
 // M[j:, c0:c1] <- (I - tau [1; v][1; v]^T) M[j:, c0:c1], v = s_v[j+1 .. n)
 template <typename T, int NT>
 __device__ void house_apply_cols(T* M, int ld, int n, int j, int c0, int c1, const T* s_v, T tau, T* red,
@@ -1086,11 +1114,9 @@ __device__ void house_apply_cols(T* M, int ld, int n, int j, int c0, int c1, con
     for (int g = warp; g < G; g += W) {
       const int l = c0 + 32 * g + lane;
       if (l < c1) {
-        T d = M[(int64_t)j * ld + l];
-        for (int a = j + 1; a < n; ++a) d += s_v[a] * M[(int64_t)a * ld + l];
-        d *= tau;
+        const T d = tau * (M[(int64_t)j * ld + l] + col_dot(M, ld, l, s_v, j + 1, n));
         M[(int64_t)j * ld + l] -= d;
-        for (int a = j + 1; a < n; ++a) M[(int64_t)a * ld + l] -= d * s_v[a];
+        col_axpy(M, ld, l, s_v, j + 1, n, d);
       }
     }
     __syncthreads();
@@ -1101,9 +1127,7 @@ __device__ void house_apply_cols(T* M, int ld, int n, int j, int c0, int c1, con
   const int a0 = j + 1 + sp * chunk, a1 = min(n, a0 + chunk);
   const int l = c0 + 32 * g + lane;
   const bool act = sp < S && l < c1;
-  T part = T(0);
-  if (act)
-    for (int a = a0; a < a1; ++a) part += s_v[a] * M[(int64_t)a * ld + l];
+  const T part = act ? col_dot(M, ld, l, s_v, a0, a1) : T(0);
   red[warp * 32 + lane] = part;
   __syncthreads();
   if (sp == 0 && l < c1) {
@@ -1114,10 +1138,7 @@ __device__ void house_apply_cols(T* M, int ld, int n, int j, int c0, int c1, con
     M[(int64_t)j * ld + l] -= d;
   }
   __syncthreads();
-  if (act) {
-    const T d = dcol[32 * g + lane];
-    for (int a = a0; a < a1; ++a) M[(int64_t)a * ld + l] -= d * s_v[a];
-  }
+  if (act) col_axpy(M, ld, l, s_v, a0, a1, dcol[32 * g + lane]);
   __syncthreads();
 }
 
@@ -1222,7 +1243,11 @@ __global__ void __launch_bounds__(kBigThreads) complete_u_kernel(const SketchRow
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kBigThreads) cholinv_kernel(const BigRowDev* rows, T* ws, LevelDev L,
-                                                              BigLevelArgs a) {
+                                                              BigLevelArgs a, int stage) {
+  // stage: the panel's rows below the diagonal tile are copied into dynamic
+  // shared memory (m x (kPW + 1)) before the trailing update reads them
+  extern __shared__ __align__(16) unsigned char ci_smem[];
+  T* Ps = reinterpret_cast<T*>(ci_smem);
   const BigRowDev rw = rows[blockIdx.x];
   const int n = rw.n, i = rw.i;
   const int r = L.rank[i], m = n - r;
@@ -1294,16 +1319,30 @@ __global__ void __launch_bounds__(kBigThreads) cholinv_kernel(const BigRowDev* r
     // trailing lower triangle: A[x, y] -= A[x, panel] . A[y, panel], y <= x
     const int t0 = p0 + pw, nt = m - t0;
     const int64_t tri = (int64_t)nt * (nt + 1) / 2;
+    if (stage && nt > 0) {
+      for (int e = tid; e < nt * kPW; e += kBigThreads) {
+        const int x = e / kPW, j = e % kPW;
+        Ps[x * (kPW + 1) + j] = (j < pw) ? Aw[(int64_t)(t0 + x) * m + p0 + j] : T(0);
+      }
+      __syncthreads();
+    }
     for (int64_t e = tid; e < tri; e += kBigThreads) {
       // e -> (x, y) with y <= x in the trailing block
       int x = static_cast<int>((sqrt(8.0 * e + 1.0) - 1.0) * 0.5);
       while ((int64_t)x * (x + 1) / 2 > e) --x;
       while ((int64_t)(x + 1) * (x + 2) / 2 <= e) ++x;
       const int y = static_cast<int>(e - (int64_t)x * (x + 1) / 2);
-      const T* ax = Aw + (int64_t)(t0 + x) * m + p0;
-      const T* ay = Aw + (int64_t)(t0 + y) * m + p0;
       T s = T(0);
-      for (int j = 0; j < pw; ++j) s += ax[j] * ay[j];
+      if (stage) {
+        const T* ax = Ps + x * (kPW + 1);
+        const T* ay = Ps + y * (kPW + 1);
+#pragma unroll 8
+        for (int j = 0; j < kPW; ++j) s += ax[j] * ay[j];
+      } else {
+        const T* ax = Aw + (int64_t)(t0 + x) * m + p0;
+        const T* ay = Aw + (int64_t)(t0 + y) * m + p0;
+        for (int j = 0; j < pw; ++j) s += ax[j] * ay[j];
+      }
       Aw[(int64_t)(t0 + x) * m + t0 + y] -= s;
     }
     __syncthreads();
@@ -1323,10 +1362,17 @@ __global__ void __launch_bounds__(kBigThreads) cholinv_kernel(const BigRowDev* r
     // S = -sum_{K < I} L[I, K] X[K, J] for every column c < r0 (then X[I, c] = L_II^{-1} S)
     for (int e = tid; e < h * r0; e += kBigThreads) {
       const int x = e / r0, c = e % r0;
-      T s = T(0);
+      T s0 = T(0), s1 = T(0), s2 = T(0), s3 = T(0);
       const T* lr = Aw + (int64_t)(r0 + x) * m;
-      for (int k = c; k < r0; ++k) s += lr[k] * Li[(int64_t)k * m + c];
-      Li[(int64_t)(r0 + x) * m + c] = -s;   // staged, solved below
+      int k = c;
+      for (; k + 4 <= r0; k += 4) {
+        s0 += lr[k] * Li[(int64_t)k * m + c];
+        s1 += lr[k + 1] * Li[(int64_t)(k + 1) * m + c];
+        s2 += lr[k + 2] * Li[(int64_t)(k + 2) * m + c];
+        s3 += lr[k + 3] * Li[(int64_t)(k + 3) * m + c];
+      }
+      for (; k < r0; ++k) s0 += lr[k] * Li[(int64_t)k * m + c];
+      Li[(int64_t)(r0 + x) * m + c] = -((s0 + s1) + (s2 + s3));   // staged, solved below
     }
     __syncthreads();
     // columns c < r0 + h: solve L_II y = rhs (rhs = staged S, or e_c for the diagonal tile)
@@ -2009,7 +2055,24 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
     mark(4);
     // ---- 5: Cholesky of T_nn and L_hat^{-1} ----
     g_launches.fetch_add(1, std::memory_order_relaxed);
-    cholinv_kernel<T><<<nr, kBigThreads, 0, s>>>(drows, ws, D, args);
+    {
+      // stage the panel rows in shared memory when they fit
+      static size_t ci_dyn = 0;
+      if (ci_dyn == 0) {
+        int dev = 0, optin = 0;
+        bcheck(cudaGetDevice(&dev));
+        bcheck(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        cudaFuncAttributes fa;
+        bcheck(cudaFuncGetAttributes(&fa, cholinv_kernel<T>));
+        ci_dyn = static_cast<size_t>(optin) - fa.sharedSizeBytes;
+        bcheck(cudaFuncSetAttribute(cholinv_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ci_dyn));
+      }
+      int mmax = 1;
+      for (int q = 0; q < nr; ++q) mmax = std::max(mmax, rows[q].n);
+      const size_t need = (size_t)mmax * (kPW + 1) * es;
+      const int stage = need <= ci_dyn ? 1 : 0;
+      cholinv_kernel<T><<<nr, kBigThreads, stage ? need : 0, s>>>(drows, ws, D, args, stage);
+    }
     bcheck(cudaGetLastError());
     mark(5);
     // ---- 6: W_b, Y_p, far rows ----
