@@ -453,7 +453,7 @@ def run_ours(args, rank, world):
                   "jacobi_capped": [info.jacobi_capped[l] for l in range(nl)],
                   "row_phase_ms": {k: [round(info.row_phase_ms[l][p], 2) for l in range(nl)] for p, k in
                                    enumerate(["wait", "setup", "learned", "R", "jacobi", "transform", "close",
-                                              "far", "schur"])},
+                                              "far", "schur", "sketch_Y", "sketch_QR", "sketch_TSQR"])},
                   "big_rows": [info.big_rows[l] for l in range(nl)],
                   "big_steps_ms": dict(zip(["gather", "sketch", "exact_svd", "UtDU", "chol_inv", "W_Y_far",
                                             "D_Wp", "kept_schur"], [round(v, 2) for v in info.big_ms])),

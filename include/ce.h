@@ -167,14 +167,18 @@ typedef struct {
                           sweep cap (40 sweeps) with a pair still above the
                           orthogonality threshold; their singular values
                           and vectors are used as they stand             */
-  double row_phase_ms[16][9]; /* row-kernel levels: SM time of each row
+  double row_phase_ms[16][12]; /* row-kernel levels: SM time of each row
                           phase summed over the level's rows (ms at the
                           maximum SM clock; divide by the resident CTAs to
                           compare with level_ms): 0 wait for the lower-
                           colour neighbourhood, 1 setup (norms, far-row
-                          layout, features), 2 learned sketch, 3 R of F_i^T,
-                          4 Jacobi SVD, 5 transform, Cholesky, L_hat^{-1},
-                          W_b, 6 close rows, 7 far rows, 8 Schur updates  */
+                          layout), 2 learned sketch: features, MLP, Jacobi
+                          on its k x k factor, completion of U, 3 R of
+                          F_i^T, 4 Jacobi SVD, 5 transform, Cholesky,
+                          L_hat^{-1}, W_b, 6 close rows, 7 far rows,
+                          8 Schur updates, 9 sketch Y = F_i Omega, 10 its
+                          Householder QR and explicit Q, 11 its TSQR of
+                          F_i^T Q                                         */
   double jacobi_sweeps[16][2]; /* row-kernel levels: mean Jacobi sweeps per
                           row of the exact SVD [0] and of the learned
                           sketch's k x k factor [1] (0: none ran)         */

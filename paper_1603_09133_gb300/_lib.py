@@ -75,7 +75,7 @@ class ce_info(C.Structure):
         ("big_rows", C.c_int * 16),
         ("big_ms", C.c_double * 8),
         ("jacobi_capped", C.c_int * 16),
-        ("row_phase_ms", (C.c_double * 9) * 16),
+        ("row_phase_ms", (C.c_double * 12) * 16),
         ("jacobi_sweeps", (C.c_double * 2) * 16),
     ]
 

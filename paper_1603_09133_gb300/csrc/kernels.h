@@ -37,9 +37,11 @@ inline int device_sms() {
 constexpr int kStatusWords = 8;
 
 // row phases timed by ce_row_kernel per level (ce_info.row_phase_ms): wait
-// for the neighbourhood, setup, learned sketch, R of F^T, Jacobi SVD,
-// transform + Cholesky + L_hat^{-1}, close rows, far rows, Schur updates
-constexpr int kRowPhases = 9;
+// for the neighbourhood, setup, learned sketch (features, MLP, its k x k
+// Jacobi and the completion of U), R of F^T, Jacobi SVD, transform +
+// Cholesky + L_hat^{-1}, close rows, far rows, Schur updates; then the
+// learned sketch's Y = F Omega, its Householder QR, its TSQR of F^T Q
+constexpr int kRowPhases = 12;
 // per level: the kRowPhases cycle sums, then Jacobi sweeps summed over rows
 // and rows that ran a Jacobi SVD (exact SVD; learned sketch's k x k factor)
 constexpr int kProfSlots = kRowPhases + 4;

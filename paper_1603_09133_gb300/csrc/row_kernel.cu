@@ -533,6 +533,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
       }
     }
     __syncthreads();
+    mark(2);
     const int k = s_k;
     const int kk = k + 2;
     const bool lvl_ok = level < 16 && la.stats != nullptr;
@@ -575,6 +576,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
         }
         __syncthreads();
       }
+      mark(9);
       // Householder QR of Q[:, :k], applied to the probe columns as well
       for (int j = 0; j < k; ++j) {
         if (warp == 0) {
@@ -635,6 +637,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
       }
       for (int e = tid; e < n * LD; e += NT) Q[e] = Qx[e];   // Q <- explicit basis
       __syncthreads();
+      mark(10);
       // TSQR of the rows of F^T Q (k columns), one R per warp, tree merge
       const int nchunks = (mF + kChunk - 1) / kChunk;
       const int qw = min(qwl, nchunks);
@@ -680,6 +683,7 @@ __device__ __forceinline__ void row_block(const LevelDev& L, const int i, int le
         }
         __syncthreads();
       }
+      mark(11);
       // one-sided Jacobi on the k x k factor R (= wbase), V in Vb
       T* Xr = wbase;                 // R (k x k, ld LK)
       T* Vb = wbase + k * LK;        // warp 0's row buffers, free now (k x k, ld LK)

@@ -41,7 +41,8 @@ def main():
     nl = F.info.levels_done
     print("row kernel ms per level:", [round(F.info.level_ms[l], 3) for l in range(nl)],
           "shapes:", list(F.info.row_shape[:nl]))
-    names = ["wait", "setup", "learned", "R", "jacobi", "transform", "close", "far", "schur"]
+    names = ["wait", "setup", "learned", "R", "jacobi", "transform", "close", "far", "schur", "sketch_Y",
+             "sketch_QR", "sketch_TSQR"]
     steps = ["gather", "sketch", "exact_svd", "UtDU", "chol_inv", "W_Y_far", "D_Wp", "kept_schur"]
     if any(F.info.big_rows[l] for l in range(nl)):
         print("large-row levels: steps ms", {k: round(F.info.big_ms[j], 1) for j, k in enumerate(steps)},
@@ -49,7 +50,7 @@ def main():
     for l in range(nl):
         if F.info.big_rows[l]:
             continue
-        ph = [F.info.row_phase_ms[l][p] for p in range(9)]
+        ph = [F.info.row_phase_ms[l][p] for p in range(12)]
         tot = sum(ph) or 1.0
         print(f"level {l}: row-phase SM time (ms summed over rows)",
               {k: f"{v:.1f} ({100 * v / tot:.0f}%)" for k, v in zip(names, ph)},
