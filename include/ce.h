@@ -127,8 +127,9 @@ typedef struct {
                           5: a row's wait for its neighbours timed out
                           (CE_ERR_CUDA; never expected);
                           CE_ERR_LIMIT: 3 a block over 1536 rows, 4 a
-                          row with over 63 close blocks (err_pivot: the
-                          size or count)                                 */
+                          row with over 63 close blocks, 8 a colour of a
+                          large-row level with over 65535 rows
+                          (err_pivot: the size or count)                 */
   int err_pivot;
   double err_value;
   int coarse_n;        /* size of the dense remainder A_K                 */

@@ -1184,6 +1184,43 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
         break;
       }
       clk::time_point t_host = clk::now();
+      // CTA shape: forced, autotuned for this csb, or 256-thread CTAs when
+      // the average colour fills two waves of them
+      int shape = (curp->ncolours > 0 && curp->M / curp->ncolours >= 2 * ce::device_sms()) ? 0 : 1;
+      const int tp = o.precision, tr = o.rank_mode;
+      if (o.row_shape >= 0)
+        shape = o.row_shape;
+      else if (l < A->tuned_levels[tp][tr])
+        shape = A->tuned_shape[tp][tr][l];
+      if (shape == 3) big = true;
+      if (big) {
+        // the large-row kernels take a colour's rows in one grid dimension
+        int widest = 0;
+        for (int c = 0; c < curp->ncolours; ++c)
+          widest = std::max(widest, curp->colour_ptr[c + 1] - curp->colour_ptr[c]);
+        if (widest > 65535) {
+          g_last_error = "ce_factorize: a colour of a large-row level holds " + std::to_string(widest) +
+                         " rows (at most 65535)";
+          ret = CE_ERR_LIMIT;
+          if (info) {
+            info->err_level = l;
+            info->err_reason = 8;
+            info->err_pivot = widest;
+            info->levels_done = l;
+          }
+          break;
+        }
+      }
+      if (big && curp->bucket_nmax.size() > 1) {
+        // the large-row path walks the colours in order; a batch's size
+        // buckets reorder the rows, so this level gets a colour-major copy
+        auto cp = std::make_shared<LevelPlan>(*curp);
+        std::stable_sort(cp->order.begin(), cp->order.end(),
+                         [&](int a, int b) { return cp->colour[a] < cp->colour[b]; });
+        cp->bucket_ptr = {0, cp->M};
+        cp->bucket_nmax = {cp->nmax};
+        curp = cp;
+      }
       F->levels.emplace_back();
       LevelStore& st = F->levels.back();
       st.plan = curp;
@@ -1199,15 +1236,6 @@ ce_status ce_factorize(const ce_csb* A, const ce_opts* o_in, ce_factor** out, ce
       check(cudaEventCreate(&ev0), "event");
       check(cudaEventCreate(&ev1), "event");
       check(cudaEventRecord(ev0, s), "event");
-      // CTA shape: forced, autotuned for this csb, or 256-thread CTAs when
-      // the average colour fills two waves of them
-      int shape = (P.ncolours > 0 && P.M / P.ncolours >= 2 * ce::device_sms()) ? 0 : 1;
-      const int tp = o.precision, tr = o.rank_mode;
-      if (o.row_shape >= 0)
-        shape = o.row_shape;
-      else if (l < A->tuned_levels[tp][tr])
-        shape = A->tuned_shape[tp][tr][l];
-      if (shape == 3) big = true;
       st.big = big;
       if (info && l < 16) info->row_shape[l] = shape;
       // learned compression on this level unless the autotuner measured the
@@ -1508,6 +1536,12 @@ ce_status ce_autotune(ce_csb* A, const ce_opts* o_in, double* level_ms) {
         ce_factor* F = nullptr;
         ce_info info;
         ce_status st = ce_factorize(A, &oc, &F, &info);
+        if (st != CE_OK && sh == 3) {
+          // the large-row path is only a candidate: where it cannot run this
+          // problem (a limit of its launches), it is left out of the choice
+          for (int l = 0; l < 16; ++l) t[md][sh][l] = 1e300;
+          break;
+        }
         if (st != CE_OK) return st;
         ce_factor_destroy(F);
         nl = std::min(nl, info.levels_done);

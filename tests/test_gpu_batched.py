@@ -104,6 +104,42 @@ def test_batched_fp64_matches_oracle_per_system(ceg, small_batch):
         assert rel[s] <= 1e-8
 
 
+def test_batched_large_row_path_matches_oracle(ceg, small_batch):
+    """Every level of the batch through the large-row path (row_shape 3): it
+    walks each level's colours in order although a batch's size buckets
+    reorder the rows; the same FP64 bar per system.  Then the autotuner
+    (which tries that path as shape 3) on the batch, and a solve with its
+    choice."""
+    ws, Fos = small_batch
+    csb = ceg.csb_build_batched([(w.A, w.perm, w.B) for w in ws])
+    F = ceg.ce_factorize_batched(csb, tol=ws[0].tol, levels=ws[0].levels, J=ws[0].J, row_shape=3)
+    assert all(F.info.big_rows[l] == 1 for l in range(F.info.levels_done))
+    for l in range(ws[0].levels):
+        n_g, r_g, c_g, _ = F.level(l)
+        o = 0
+        for Fo in Fos:
+            lev = Fo.levels[l]
+            M = len(lev.sizes)
+            assert list(n_g[o:o + M]) == list(lev.sizes)
+            assert _ranks_ok(lev, r_g[o:o + M])
+            o += M
+    b = np.concatenate([w.b for w in ws])
+    z = torch.empty(b.size, dtype=torch.float64, device="cuda")
+    ceg.ce_apply(F, _dev(b), z)
+    zg = z.cpu().numpy()
+    sl = _slices(ws)
+    for s, (w, Fo) in enumerate(zip(ws, Fos)):
+        zo = oce.apply(Fo, w.b)
+        err = np.linalg.norm(zg[sl[s]] - zo) / np.linalg.norm(zo)
+        assert err <= 1e-10, (s, err)
+    t = ceg.ce_autotune(csb, tol=ws[0].tol, levels=ws[0].levels, J=ws[0].J)
+    assert t.shape[1] == 4 and (t[0, 3] > 0).all()
+    F2 = ceg.ce_factorize_batched(csb, tol=ws[0].tol, levels=ws[0].levels, J=ws[0].J)
+    x = torch.zeros(b.size, dtype=torch.float64, device="cuda")
+    its, rel, conv = ceg.pcg_solve_batched(csb, F2, _dev(b), x, 1e-8, 500)
+    assert conv.all()
+
+
 def test_batched_fp32_learned_backward_error(ceg, small_batch):
     ws, Fos = small_batch
     model = ceg.trained_rank_model(steps=1500)
