@@ -2254,6 +2254,15 @@ void debug_svd_t(int B, int n, const void* R, const void* Dm, double tol, void* 
   const int64_t nn = (int64_t)n * n;
   T* ws = nullptr;
   void* aux = nullptr;
+  struct Free {   // the buffers go back to the pool on every exit
+    T*& w;
+    void*& x;
+    cudaStream_t st;
+    ~Free() {
+      if (w) cudaFreeAsync(w, st);
+      if (x) cudaFreeAsync(x, st);
+    }
+  } guard{ws, aux, s};
   bcheck(cudaMallocAsync(reinterpret_cast<void**>(&ws), 3 * nn * sizeof(T), s));
   bcheck(cudaMallocAsync(&aux, sizeof(BigRowDev) + sizeof(int64_t) + (kStatusWords + kStatsWords) * sizeof(int), s));
   BigRowDev* drow = static_cast<BigRowDev*>(aux);
@@ -2300,8 +2309,6 @@ void debug_svd_t(int B, int n, const void* R, const void* Dm, double tol, void* 
   bcheck(cudaMemcpyAsync(hs, dstat + kStatusWords, sizeof(hs), cudaMemcpyDeviceToHost, s));
   bcheck(cudaStreamSynchronize(s));
   if (sweeps) *sweeps = hs[48];
-  cudaFreeAsync(ws, s);
-  cudaFreeAsync(aux, s);
 }
 
 cudaError_t debug_svd(int esize, int B, int n, const void* R, const void* Dm, double tol, void* X, void* V,
