@@ -16,46 +16,6 @@ namespace ce {
 
 namespace {
 
-constexpr int kThreads = 256;
-constexpr int kWarps = kThreads / 32;
-constexpr int LD = kNMax + 1;   // shared-memory leading dimension
-constexpr int kChunk = kNMax;   // rows of F_i^T per Householder pass
-constexpr int kMaxSweeps = 40;  // Jacobi sweep cap (bounded loop)
-constexpr int kMaxTargets = 32;
-
-template <typename T>
-struct Eps;
-template <>
-struct Eps<double> {
-  static constexpr double v = 2.220446049250313e-16;
-};
-template <>
-struct Eps<float> {
-  static constexpr float v = 1.1920928955078125e-07f;
-};
-
-template <typename T>
-struct Tiny;  // smallest normal number
-template <>
-struct Tiny<double> {
-  static constexpr double v = 2.2250738585072014e-308;
-};
-template <>
-struct Tiny<float> {
-  static constexpr float v = 1.1754943508222875e-38f;
-};
-
-template <typename T>
-__device__ __forceinline__ T warp_sum(T v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-__device__ __forceinline__ int width_of(const LevelDev& L, int k, int ci) {
-  return (L.colour[k] < ci) ? L.rank[k] : L.n[k];
-}
-
 __device__ void set_status(int* status, int code, int level, int block, int reason = 0,
                            int pivot = -1, double value = 0.0) {
   if (atomicCAS(status, 0, code) == 0) {
@@ -101,13 +61,6 @@ __global__ void copy_tasks_kernel(const CopyTask* tasks, const Ts* src, Td* dst)
 // to spread it over all SMs.
 constexpr int NB = 32;
 constexpr int NBL = NB + 1;
-
-__device__ __forceinline__ bool coarse_sys(double*& A, int& n, const int64_t* desc, int nsys, int k0) {
-  const int y = blockIdx.y;
-  n = static_cast<int>(desc[y]);
-  A += desc[nsys + y];
-  return k0 < n;
-}
 
 // 1 / sqrt(x) for x > 0 in FP64: a single-precision estimate refined by two
 // Newton-Raphson steps y <- y (3 - x y^2) / 2 (each doubles the correct bits,
