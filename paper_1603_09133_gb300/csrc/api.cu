@@ -780,21 +780,34 @@ ce_status build_csb(int64_t n, const int64_t* rowptr, const int32_t* col, const 
   A->n = n;
   A->B = B0;
   A->nnz = nnz;
-  A->h_rowptr.assign(rowptr, rowptr + n + 1);
-  A->h_col.assign(col, col + nnz);
+  // host copy of the pattern (csb_update_values checks new values against
+  // it), filled in parallel
+  A->h_rowptr.resize(n + 1);
+  A->h_col.resize(nnz);
+  ce::parallel_for(n + 1, 1 << 16, [&](int64_t b, int64_t e) {
+    std::memcpy(A->h_rowptr.data() + b, rowptr + b, (e - b) * sizeof(int64_t));
+  });
+  ce::parallel_for(nnz, 1 << 17, [&](int64_t b, int64_t e) {
+    std::memcpy(A->h_col.data() + b, col + b, (e - b) * sizeof(int32_t));
+  });
   A->nsys = static_cast<int>(sys_row.size()) - 1;
   A->sys_row = sys_row;
   try {
     A->plan1 = std::make_shared<LevelPlan>();
     ce::plan_level(*A->plan1, sizes, pairs, true, sys_blk);
     const LevelPlan& P1 = *A->plan1;
-    std::vector<int64_t> scatter(nnz, -1);
+    // every entry is written below (-1: the mirror of a stored pair), so the
+    // array is not zero-filled first
+    std::unique_ptr<int64_t[]> scatter(new int64_t[std::max<int64_t>(nnz, 1)]);
     ce::parallel_for(n, 8192, [&](int64_t a0, int64_t a1) {
       for (int64_t a = a0; a < a1; ++a)
         for (int64_t e = rowptr[a]; e < rowptr[a + 1]; ++e) {
           const int pa = iperm[a], pb = iperm[col[e]];
           const int bi = blk_of[pa], bk = blk_of[pb];
-          if (bi > bk) continue;
+          if (bi > bk) {
+            scatter[e] = -1;
+            continue;
+          }
           const int64_t po = pair_offset(P1, bi, bk);
           scatter[e] = po + (int64_t)(pa - blkptr[bi]) * P1.n[bk] + (pb - blkptr[bk]);
         }
@@ -819,7 +832,7 @@ ce_status build_csb(int64_t n, const int64_t* rowptr, const int32_t* col, const 
                {A->d_col, col, nnz * sizeof(int32_t)},
                {A->d_val, val, nnz * sizeof(double)},
                {A->d_perm, perm, n * sizeof(int32_t)},
-               {A->d_scatter, scatter.data(), nnz * sizeof(int64_t)},
+               {A->d_scatter, scatter.get(), nnz * sizeof(int64_t)},
                {A->d_sys_of_row, sys_of_row.data(), n * sizeof(int32_t)}};
     size_t off[7] = {0};
     for (int u = 0; u < 6; ++u) off[u + 1] = off[u] + ((ups[u].bytes + 255) & ~size_t(255));
