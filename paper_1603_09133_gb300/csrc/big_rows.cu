@@ -1747,7 +1747,7 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
       v.n = k;
       v.mF = r.mF;
       int parts = 1;
-      while (parts < 32 && (int64_t)parts * 2 * 8 * CH <= r.mF) parts *= 2;
+      while (parts < 64 && (int64_t)parts * 2 * 4 * CH <= r.mF) parts *= 2;
       v.parts = parts;
       maxp = std::max(maxp, parts);
       kmx = std::max(kmx, k);
@@ -1886,9 +1886,9 @@ void run_big_level_t(LevelStore& st, cudaStream_t s, const BigLevelArgs& args, s
       r.mF = mF;
       const int n = r.n;
       nmaxc = std::max(nmaxc, n);
-      // TSQR parts: about 8 chunks of F_i^T per part, at most 32 parts
+      // TSQR parts: about 4 chunks of F_i^T per part, at most 64 parts
       int parts = 1;
-      while (parts < 32 && (int64_t)parts * 2 * 8 * CH <= mF) parts *= 2;
+      while (parts < 64 && (int64_t)parts * 2 * 4 * CH <= mF) parts *= 2;
       r.parts = parts;
       maxparts = std::max(maxparts, parts);
       r.g_off = take((int64_t)std::max(mF, 1) * n);
