@@ -261,12 +261,12 @@ def run_reference(args, rank):
 
 def committed_traffic(kernel, workload, precision):
     """DRAM traffic per launch of `kernel` from the committed ncu summary
-    (profiles/ce_row_kernel_traffic.md), if that capture was taken of the
+    (profiles/ce_row_kernel_traffic_poisson2d_512.md), if that capture was taken of the
     current kernel source (its SHA-256 is recorded with the numbers); None
     otherwise.  Lines read: `source_sha256: <hex>`, and per captured form
     `traffic: <kernel> <workload> <precision> <bytes per launch>`."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "ce_row_kernel_traffic.md")
+    path = os.path.join(ROOT, "profiles", "ce_row_kernel_traffic_poisson2d_512.md")
     src = os.path.join(ROOT, "paper_1603_09133_gb300", "csrc", "row_kernel.cu")
     if not os.path.exists(path):
         return None
@@ -282,7 +282,7 @@ def committed_traffic(kernel, workload, precision):
         return None
     return {"bytes_per_launch": val,
             "note": "dram__bytes_read.sum + dram__bytes_write.sum per launch, mean over the level "
-                    "launches of one factorization (profiles/ce_row_kernel_traffic.md)"}
+                    "launches of one factorization (profiles/ce_row_kernel_traffic_poisson2d_512.md)"}
 
 
 # --------------------------------------------------------------------------
