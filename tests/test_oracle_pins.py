@@ -454,6 +454,27 @@ def test_minres_is_the_library_minres():
             assert np.linalg.norm(its[k - 1] - res.x) <= 1e-12 * np.linalg.norm(res.x), k
 
 
+def test_minres_preconditioned_indefinite_is_the_library_minres():
+    """An indefinite symmetric matrix with an SPD (diagonal) preconditioner:
+    the oracle's minimisation and SciPy's recurrence give the same iterate
+    after every step."""
+    import scipy.sparse.linalg as spla
+    rng = np.random.default_rng(3)
+    n = 80
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.concatenate([-np.linspace(1, 5, n // 4), np.linspace(0.5, 20, n - n // 4)])
+    A = sp.csr_matrix((Q * lam) @ Q.T)
+    A = sp.csr_matrix(0.5 * (A + A.T))
+    dinv = 1.0 / (1.0 + rng.random(n))
+    b = rng.standard_normal(n)
+    Mop = spla.LinearOperator((n, n), matvec=lambda v: dinv * v)
+    its = []
+    spla.minres(A, b, rtol=1e-15, maxiter=25, M=Mop, callback=lambda xk: its.append(xk.copy()))
+    for k in (1, 5, 12, len(its)):
+        res = ce.minres(A, None, b, 0.0, k, precond=lambda v: dinv * v)
+        assert np.linalg.norm(its[k - 1] - res.x) <= 1e-10 * np.linalg.norm(res.x), k
+
+
 def test_minres_special_cases():
     """Closed forms: with the exact preconditioner C = A^{-1} MINRES ends in one
     step at A^{-1} b; on a symmetric indefinite matrix with d distinct
